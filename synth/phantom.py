@@ -1,0 +1,202 @@
+"""Seeded generators for damped-exponential image series and their undersampled k-space.
+
+Signal model (Sec. II-B, Eq. signal-model): every pixel r of frame n holds
+    x[n, r] = rho(r) * sum_i f_i(r) * exp(-t_n / T2_i(r)),
+i.e. a sum of L damped exponentials whose decay rates vary smoothly in space.
+
+Measurement model (Sec. II-A, Eq. measurement-model, single coil): frame n is observed as
+    b_n = mask_n * (F x_n + eta_n),
+with F the unitary 2-D DFT (forward sign e^{-2 pi i}, natural frequency order, no fftshift),
+mask_n in {0,1} a per-frame Cartesian point mask, and eta_n complex white Gaussian noise.
+
+Layouts: image series and k-space are complex arrays of shape (T, P, Q) (Q fastest);
+masks are uint8 arrays of the same shape.
+
+Seeds (base seed S): rho uses S+1, relaxation/fraction fields S+2, mask of frame n S+10+n,
+noise S+99, served request i S+1000*i.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """One synthetic reconstruction problem and the solver settings it is run with."""
+
+    name: str
+    P: int
+    Q: int
+    T: int
+    times_ms: tuple            # echo / spin-lock times t_n, length T
+    n_ellipses: int
+    t2_ranges: tuple           # ((lo, hi), ...) one range per exponential component, ms
+    frac_range: tuple          # (lo, hi) of the first component's fraction (two components only)
+    R: float                   # undersampling factor: P*Q/R samples per frame
+    N1: int
+    N2: int
+    M: int
+    lam: float
+    p: float
+    n_irls: int
+    n_cg: int
+    snr_db: float = 30.0
+    seed: int = 0
+
+    @property
+    def shape(self):
+        return (self.T, self.P, self.Q)
+
+    @property
+    def taps(self):
+        return self.N1 * self.N2 * self.M
+
+
+def _tiny():
+    return Workload(
+        name="tiny_32x32x8", P=32, Q=32, T=8,
+        times_ms=tuple(5.0 + 5.0 * n for n in range(8)),
+        n_ellipses=6, t2_ranges=((20.0, 120.0),), frac_range=(1.0, 1.0),
+        R=4.0, N1=5, N2=5, M=2, lam=1e-3, p=0.0, n_irls=20, n_cg=10)
+
+
+def _perf():
+    return Workload(
+        name="perf_256x256x16", P=256, Q=256, T=16,
+        times_ms=tuple(1.0 + 59.0 * n / 15.0 for n in range(16)),
+        n_ellipses=10, t2_ranges=((10.0, 40.0), (50.0, 150.0)), frac_range=(0.2, 0.8),
+        R=8.0, N1=9, N2=9, M=3, lam=1e-3, p=0.0, n_irls=30, n_cg=15)
+
+
+WORKLOADS = {w.name: w for w in (_tiny(), _perf())}
+
+
+def workload(name: str, **overrides) -> Workload:
+    """Named workload, optionally with fields replaced (e.g. smaller iteration counts)."""
+    return dataclasses.replace(WORKLOADS[name], **overrides)
+
+
+def ellipse_phantom(P: int, Q: int, n: int, rng: np.random.Generator) -> np.ndarray:
+    """Additive sum of n random filled ellipses (centres in the central 60 %, semi-axes
+    3-12 px at 32x32 scaled with the grid, angle U[0, pi), intensity U[0.2, 1])."""
+    scale = min(P, Q) / 32.0
+    yy, xx = np.meshgrid(np.arange(P, dtype=np.float64), np.arange(Q, dtype=np.float64),
+                         indexing="ij")
+    img = np.zeros((P, Q), dtype=np.float64)
+    for _ in range(n):
+        cy = rng.uniform(0.2 * P, 0.8 * P)
+        cx = rng.uniform(0.2 * Q, 0.8 * Q)
+        a = rng.uniform(3.0, 12.0) * scale
+        b = rng.uniform(3.0, 12.0) * scale
+        th = rng.uniform(0.0, math.pi)
+        amp = rng.uniform(0.2, 1.0)
+        dy, dx = yy - cy, xx - cx
+        u = (dx * math.cos(th) + dy * math.sin(th)) / a
+        v = (-dx * math.sin(th) + dy * math.cos(th)) / b
+        img += amp * ((u * u + v * v) <= 1.0)
+    return img
+
+
+def smooth_field(P: int, Q: int, sigma: float, lo: float, hi: float,
+                 rng: np.random.Generator) -> np.ndarray:
+    """White N(0,1) noise blurred by a periodic Gaussian of width sigma (px), then min-max
+    mapped onto [lo, hi]."""
+    w = rng.standard_normal((P, Q))
+    f1 = np.fft.fftfreq(P)[:, None]
+    f2 = np.fft.fftfreq(Q)[None, :]
+    g = np.exp(-2.0 * (math.pi * sigma) ** 2 * (f1 * f1 + f2 * f2))
+    s = np.real(np.fft.ifft2(np.fft.fft2(w) * g))
+    s = (s - s.min()) / max(s.max() - s.min(), 1e-300)
+    return lo + (hi - lo) * s
+
+
+def vd_mask(P: int, Q: int, R: float, rng: np.random.Generator) -> np.ndarray:
+    """Variable-density Cartesian point mask with round(P*Q/R) samples, natural FFT order.
+
+    A c x c block around DC is fully sampled (c = max(4, P//32)); the remaining samples are drawn
+    without replacement with probability proportional to 1 / (1 + (|k| / (P/8))^2), |k| the
+    centred frequency radius in grid units."""
+    n_target = int(round(P * Q / R))
+    k1 = np.fft.fftfreq(P) * P
+    k2 = np.fft.fftfreq(Q) * Q
+    K1, K2 = np.meshgrid(k1, k2, indexing="ij")
+    c = max(4, P // 32)
+    centre = (K1 >= -c // 2) & (K1 < c - c // 2) & (K2 >= -c // 2) & (K2 < c - c // 2)
+    mask = centre.copy()
+    need = n_target - int(mask.sum())
+    if need > 0:
+        rad = np.sqrt(K1 * K1 + K2 * K2)
+        wgt = 1.0 / (1.0 + (rad / (P / 8.0)) ** 2)
+        wgt[mask] = 0.0
+        flat = wgt.ravel() / wgt.sum()
+        pick = rng.choice(P * Q, size=need, replace=False, p=flat)
+        mask.ravel()[pick] = True
+    return mask.astype(np.uint8)
+
+
+def make_series(w: Workload) -> np.ndarray:
+    """Ground-truth image series x_true, complex128 of shape (T, P, Q)."""
+    S = w.seed
+    rho = ellipse_phantom(w.P, w.Q, w.n_ellipses, np.random.default_rng(S + 1))
+    rng = np.random.default_rng(S + 2)
+    sigma = 3.0 * w.P / 32.0
+    t = np.asarray(w.times_ms, dtype=np.float64)[:, None, None]
+    if len(w.t2_ranges) == 1:
+        lo, hi = w.t2_ranges[0]
+        t2 = smooth_field(w.P, w.Q, sigma, lo, hi, rng)
+        x = rho[None] * np.exp(-t / t2[None])
+    else:
+        (alo, ahi), (blo, bhi) = w.t2_ranges
+        t2a = smooth_field(w.P, w.Q, sigma, alo, ahi, rng)
+        t2b = smooth_field(w.P, w.Q, sigma, blo, bhi, rng)
+        f = rng.uniform(w.frac_range[0], w.frac_range[1], size=(w.P, w.Q))
+        x = rho[None] * (f[None] * np.exp(-t / t2a[None]) + (1.0 - f[None]) * np.exp(-t / t2b[None]))
+    return x.astype(np.complex128)
+
+
+def make_problem(w: Workload) -> dict:
+    """Seeded problem: x_true (T,P,Q) complex128, masks (T,P,Q) uint8, kspace (T,P,Q) complex128.
+
+    kspace = mask * (F x_true + eta); eta is complex Gaussian on the sampled entries, scaled so
+    that 20 log10(||mask * F x_true|| / ||eta||) equals w.snr_db exactly."""
+    S = w.seed
+    x = make_series(w)
+    masks = np.stack([vd_mask(w.P, w.Q, w.R, np.random.default_rng(S + 10 + n))
+                      for n in range(w.T)])
+    clean = masks * np.fft.fft2(x, norm="ortho")
+    rng = np.random.default_rng(S + 99)
+    eta = (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)) * masks
+    scale = np.linalg.norm(clean) * 10.0 ** (-w.snr_db / 20.0) / max(np.linalg.norm(eta), 1e-300)
+    kspace = clean + scale * eta
+    return {"x_true": x, "masks": masks, "kspace": kspace, "workload": w}
+
+
+def served_mix(n_requests: int = 512, rate_hz: float = 20.0, seed: int = 0,
+               sizes=(64, 128, 192, 256)) -> list:
+    """Served-mix request list: Poisson arrivals and seeded per-request workloads.
+
+    Each entry is (arrival_s, Workload). Sizes uniform over `sizes`, frames U{8..24},
+    1-2 components, undersampling U[4, 10], filter N1=N2 in {5,7,9}, M in {2,3}."""
+    rng = np.random.default_rng(seed + 7)
+    gaps = rng.exponential(1.0 / rate_hz, size=n_requests)
+    t_arr = np.cumsum(gaps)
+    out = []
+    for i in range(n_requests):
+        r = np.random.default_rng(seed + 1000 * i)
+        P = int(r.choice(sizes))
+        T = int(r.integers(8, 25))
+        L = int(r.integers(1, 3))
+        R = float(r.uniform(4.0, 10.0))
+        N = int(r.choice([5, 7, 9]))
+        M = int(r.choice([2, 3]))
+        times = tuple(1.0 + 59.0 * n / (T - 1) for n in range(T))
+        ranges = ((20.0, 120.0),) if L == 1 else ((10.0, 40.0), (50.0, 150.0))
+        w = Workload(name=f"req{i}", P=P, Q=P, T=T, times_ms=times, n_ellipses=8,
+                     t2_ranges=ranges, frac_range=(0.2, 0.8), R=R, N1=N, N2=N, M=M,
+                     lam=1e-3, p=0.0, n_irls=30, n_cg=15, seed=seed + 1000 * i)
+        out.append((float(t_arr[i]), w))
+    return out

@@ -1,0 +1,139 @@
+"""Pins of the oracle's Gram matrix, weight, sum-of-squares operator and CG.
+
+- FFT Gram (Eq. P-ij-modified) == Tm^H Tm from the explicit lifting, including the aliasing case
+  where the filter is as wide as the grid (the special case of Sec. II-E, P = N1).
+- H = (G + eps I)^(p/2-1) against scipy's fractional matrix power and, for p = 0, H (G+eps I) = I.
+- Sum-of-squares identity: sum_i ||Tm h_i^*||^2 with the explicit filters h_i of Sec. III-B ==
+  Re <x, W x> computed through the summed diagonals and the per-pixel S(r) (Eq. grad-ls).
+- W Hermitian PSD, and the finite-difference derivative of Tr(H G(x)) equals 2 Re <v, W x>.
+- CG reaches the dense direct solution; the Tikhonov reduction N1 = N2 = M = 1 has a closed form.
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import slr
+
+
+def _crandn(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+CASES = [(4, 8, 8, 3, 2, 2), (5, 6, 10, 3, 3, 3), (3, 5, 4, 5, 4, 1), (6, 8, 8, 2, 2, 4)]
+
+
+@pytest.mark.parametrize("dims", CASES)
+def test_gram_fft_equals_brute(rng, dims):
+    T, P, Q, N1, N2, M = dims
+    x = _crandn(rng, T, P, Q)
+    Gb = slr.gram_brute(x, N1, N2, M)
+    Gf = slr.gram_fft(x, N1, N2, M)
+    assert np.linalg.norm(Gf - Gb) <= 1e-12 * np.linalg.norm(Gb)
+    assert np.allclose(Gf, Gf.conj().T, atol=1e-12 * np.abs(Gf).max())
+    assert np.linalg.eigvalsh(Gf)[0] >= -1e-10 * np.abs(Gf).max()
+
+
+@pytest.mark.parametrize("p", [0.0, 0.6, 1.0])
+def test_weight_matches_matrix_power(rng, p):
+    X = _crandn(rng, 30, 12)
+    G = X.conj().T @ X
+    eps = 0.05 * np.linalg.eigvalsh(G)[-1]
+    H, lam = slr.weight_H(G, eps, p)
+    ref = scipy.linalg.fractional_matrix_power(G + eps * np.eye(12), p / 2 - 1)
+    assert np.linalg.norm(H - ref) <= 1e-10 * np.linalg.norm(ref)
+    if p == 0.0:
+        assert np.allclose(H @ (G + eps * np.eye(12)), np.eye(12), atol=1e-10)
+    Hh = slr.filters_from_H(G, eps, p)
+    assert np.linalg.norm(Hh.conj().T @ Hh - H) <= 1e-10 * np.linalg.norm(H)
+
+
+def _random_weight(rng, x, N1, N2, M, p):
+    G = slr.gram_fft(x, N1, N2, M)
+    eps = 0.01 * np.linalg.eigvalsh(G)[-1]
+    return G, eps
+
+
+@pytest.mark.parametrize("dims", CASES)
+@pytest.mark.parametrize("p", [0.0, 0.7])
+def test_sum_of_squares_identity(rng, dims, p):
+    T, P, Q, N1, N2, M = dims
+    x_w = _crandn(rng, T, P, Q)             # iterate the weight is built from
+    x = _crandn(rng, T, P, Q)               # point where the penalty is evaluated
+    G, eps = _random_weight(rng, x_w, N1, N2, M, p)
+    H, _ = slr.weight_H(G, eps, p)
+    S = slr.weight_S(slr.diag_sums(H, N1, N2, M), P, Q)
+    direct = slr.penalty_filters(x, slr.filters_from_H(G, eps, p), N1, N2, M)
+    quad = np.vdot(x, slr.apply_W(x, S))
+    assert abs(quad.imag) <= 1e-10 * abs(quad.real)
+    assert abs(quad.real - direct) <= 1e-10 * direct
+    # S(r) is Hermitian at every pixel
+    assert np.allclose(S, np.conj(np.swapaxes(S, 0, 1)), atol=1e-10 * np.abs(S).max())
+
+
+def test_W_hermitian_psd_and_gradient(rng):
+    T, P, Q, N1, N2, M = 5, 8, 6, 3, 2, 3
+    x_w = _crandn(rng, T, P, Q)
+    G, eps = _random_weight(rng, x_w, N1, N2, M, 0.0)
+    H, _ = slr.weight_H(G, eps, 0.0)
+    S = slr.weight_S(slr.diag_sums(H, N1, N2, M), P, Q)
+    x = _crandn(rng, T, P, Q)
+    y = _crandn(rng, T, P, Q)
+    Wx, Wy = slr.apply_W(x, S), slr.apply_W(y, S)
+    assert abs(np.vdot(y, Wx) - np.conj(np.vdot(x, Wy))) <= 1e-10 * abs(np.vdot(y, Wx))
+    assert np.vdot(x, Wx).real > 0
+    # d/dt Tr(H G(x + t v)) at t = 0 == 2 Re <v, W x>, with G from the FFT Gram
+    v = _crandn(rng, T, P, Q)
+    h = 1e-4
+
+    def J(z):
+        return float(np.real(np.trace(H @ slr.gram_fft(z, N1, N2, M))))
+
+    fd = (J(x + h * v) - J(x - h * v)) / (2 * h)
+    assert abs(fd - 2 * np.vdot(v, Wx).real) <= 1e-7 * abs(fd)
+
+
+def test_cg_reaches_dense_solution(rng):
+    T, P, Q, N1, N2, M = 3, 4, 4, 2, 2, 2
+    masks = (rng.random((T, P, Q)) < 0.5).astype(np.uint8)
+    x_w = _crandn(rng, T, P, Q)
+    G, eps = _random_weight(rng, x_w, N1, N2, M, 0.0)
+    H, _ = slr.weight_H(G, eps, 0.0)
+    S = slr.weight_S(slr.diag_sums(H, N1, N2, M), P, Q)
+    lam = 0.3 * eps
+    n = T * P * Q
+    op = lambda v: slr.normal_op(v, masks, S, lam)  # noqa: E731
+    E = np.eye(n).reshape(n, T, P, Q)
+    Amat = np.stack([op(E[i].astype(np.complex128)).ravel() for i in range(n)], axis=1)
+    assert np.allclose(Amat, Amat.conj().T, atol=1e-10 * np.abs(Amat).max())
+    rhs = _crandn(rng, T, P, Q)
+    want = np.linalg.solve(Amat, rhs.ravel()).reshape(T, P, Q)
+    got = slr.cg(op, rhs, np.zeros_like(rhs), 4 * n)
+    assert np.linalg.norm(got - want) <= 1e-8 * np.linalg.norm(want)
+
+
+def test_tikhonov_reduction_closed_form(rng):
+    """N1 = N2 = M = 1: s = 1, G = ||x||^2 (all frames), H = (G + eps)^(p/2-1), W = H I. One IRLS
+    step with an exact least-squares solve is x_hat = mask b / (mask + lam H) per k-sample."""
+    T, P, Q = 4, 8, 8
+    x0 = _crandn(rng, T, P, Q)
+    assert np.isclose(slr.gram_fft(x0, 1, 1, 1)[0, 0].real, np.linalg.norm(x0) ** 2, rtol=1e-13)
+    masks = (rng.random((T, P, Q)) < 0.4).astype(np.uint8)
+    b = masks * _crandn(rng, T, P, Q)
+    lam, p = 0.7, 0.5
+    rhs = slr.AH(b, masks)
+    eps = slr.initial_eps(rhs, 1, 1, 1)
+    assert np.isclose(eps, 0.01 * np.linalg.norm(rhs) ** 2)
+    Hval = (np.linalg.norm(rhs) ** 2 + eps) ** (p / 2 - 1)
+    # two distinct eigenvalues (1 + lam H on sampled, lam H on the rest): CG is exact in 2 steps
+    x1 = slr.irls(b, masks, 1, 1, 1, lam, p, n_irls=1, n_cg=2)
+    want = slr.F2H(masks * b / (masks + lam * Hval))
+    assert np.linalg.norm(x1 - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_full_sampling_small_lambda_returns_adjoint(rng):
+    T, P, Q = 4, 8, 8
+    masks = np.ones((T, P, Q), dtype=np.uint8)
+    b = _crandn(rng, T, P, Q)
+    x = slr.irls(b, masks, 3, 3, 2, lam=1e-12, p=0.0, n_irls=2, n_cg=3)
+    assert np.linalg.norm(x - slr.F2H(b)) <= 1e-9 * np.linalg.norm(b)
