@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the IRLS reconstruction (Algorithm 1) on the 256x256x16 workload.
+
+One step = one complete reconstruction through the C ABI: x0 = A^H b, then 30 IRLS iterations
+(Gram, FP64 eigendecomposition, weight, S(r), residual carry, 15 CG steps each) of a seeded
+two-component T2 phantom, 8x variable-density mask, 9x9x3 filter, lambda = 1e-3, p = 0.
+Metric: IRLS iterations per second (whole job: all ranks' iterations / max rank time).
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 NumPy oracle instead, on the
+host cores, on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IRLS iterations/s, 256x256x16 series, 9x9x3 filter, 15 CG steps per iteration"
+UNIT = "IRLS iter/s"
+WORKLOAD = "perf_256x256x16"
+
+# kernels launched per profiled scope (eig is the cuSOLVER library call and is not counted)
+KERNELS_PER_SCOPE = {"adjoint": 2, "gram": 2, "eps": 1, "diag_sums": 2, "weight_S": 2,
+                     "resid_carry": 1, "cg_row_fwd": 1, "cg_col_mask": 1, "cg_row_inv_w": 1,
+                     "cg_update": 1}
+
+
+def alg_bytes(kind: str, w, n_cg: int) -> float:
+    """Algorithmic bytes per launch (complex64 elements E = T*P*Q, pixels N = P*Q)."""
+    E = w.T * w.P * w.Q
+    N = w.P * w.Q
+    npair = w.M * (w.M + 1) // 2
+    if kind == "cg_row_fwd":      # read r (+ p), write p and t
+        return (24.0 * E + 32.0 * E * (n_cg - 1)) / n_cg
+    if kind == "cg_col_mask":     # read t, mask; write t
+        return 17.0 * E
+    if kind == "cg_row_inv_w":    # read t, p, S; write q
+        return 24.0 * E + 8.0 * npair * N
+    if kind == "cg_update":       # read x, r, p, q; write x, r
+        return 48.0 * E
+    if kind == "resid_carry":     # read x, r, S_old, S_new; write r (first: no r, S_old)
+        return 24.0 * E + 16.0 * npair * N
+    if kind == "gram":            # read x
+        return 8.0 * E
+    if kind == "adjoint":         # read b, mask, write t; read t, write x
+        return 33.0 * E
+    return 0.0
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(w, prob, budget_s: float = 12.0, max_iters: int = 6):
+    """FP64 oracle IRLS iterations/s on the host cores (bounded sample)."""
+    import numpy as np
+    from oracle import slr
+    b = prob["kspace"].astype(np.complex64).astype(np.complex128)
+    masks = prob["masks"]
+    rhs = slr.AH(b, masks)
+    x = rhs.copy()
+    eps = slr.initial_eps(x, w.N1, w.N2, w.M)
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_iters:
+        S = slr.weight_from_x(x, w.N1, w.N2, w.M, eps, w.p)
+        x = slr.cg(lambda v: slr.normal_op(v, masks, S, w.lam), rhs, x, w.n_cg)
+        eps /= 1.4
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return n / dt, n, dt, cores
+
+
+def run_reference(args, rank: int):
+    import synth
+    if rank != 0:
+        return
+    w = synth.workload(WORKLOAD)
+    prob = synth.make_problem(w)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, prob, budget_s=0.0, max_iters=1)
+    rates, times = [], []
+    cores = 1
+    for _ in range(args.steps):
+        r, n, dt, cores = cpu_oracle_rate(w, prob, budget_s=0.0, max_iters=1)
+        rates.append(r)
+        times.append(dt)
+    value = len(times) / sum(times)
+    sample = (f"{WORKLOAD}: 1 IRLS iteration per step (Gram + eigh + weight + {w.n_cg} CG), "
+              "FP64 NumPy oracle; numpy.fft single-threaded, eigh on the BLAS threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "irls": 1, "cg": w.n_cg, "filter": [w.N1, w.N2, w.M]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--irls", type=int, default=None, help="override IRLS iterations (testing)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1704_04511_gb300 import recon
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = synth.workload(WORKLOAD)
+    if args.irls is not None:
+        w = synth.workload(WORKLOAD, n_irls=args.irls)
+    prob = synth.make_problem(w)
+    b_host = torch.from_numpy(np.ascontiguousarray(prob["kspace"], dtype=np.complex64)).pin_memory()
+    m_host = torch.from_numpy(np.ascontiguousarray(prob["masks"])).pin_memory()
+    b = b_host.to(dev)
+    m = m_host.to(dev)
+    out = torch.empty(tuple(m.shape), dtype=torch.complex64, device=dev)
+    out_host = torch.empty(tuple(m.shape), dtype=torch.complex64).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    ctx = recon.Context(local_rank, cuda_stream=stream.cuda_stream)
+    filt = (w.N1, w.N2, w.M)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_id if rank == 0 else None) if rank == 0 else None
+
+    # ---- timed region: K device-resident solves, L2 flushed before each (outside the events)
+    recon.recon_profile(ctx.h, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop() if sampler else None
+    prof = {}
+    for k in range(recon.PROF_KINDS):
+        ms, n = recon.recon_profile_read(ctx.h, k)
+        prof[recon.recon_profile_name(k)] = (ms, n)
+    recon.recon_profile(ctx.h, False)
+    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    t_max_ms = float(t_local.item())
+    value = world * args.steps * w.n_irls / (t_max_ms / 1000.0)
+
+    # ---- end to end: pinned host buffers, copies inside the timed region
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.copy_(b_host, non_blocking=True)
+        m.copy_(m_host, non_blocking=True)
+        step()
+        out_host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps * w.n_irls / (float(e2e_ms.item()) / 1000.0)
+
+    if rank != 0:
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # dominant kernel of this library (the eigensolver is a cuSOLVER call and reported apart)
+    mine = {k: v for k, v in prof.items() if k in KERNELS_PER_SCOPE}
+    dom = max(mine, key=lambda k: mine[k][0])
+    dom_ms, dom_n = mine[dom]
+    peak, peak_src = load_peaks()
+    bytes_per_launch = alg_bytes(dom, w, w.n_cg)
+    achieved = bytes_per_launch / (dom_ms / dom_n / 1000.0) / 1e9 if dom_n else 0.0
+    launches = sum(n * KERNELS_PER_SCOPE[k] for k, (ms, n) in mine.items())
+    step_ms_profiled = sum(ms for ms, n in prof.values())
+    phase = {k: {"ms_per_step": round(ms / args.steps, 4), "launches_per_step": n // args.steps,
+                 "share": round(ms / step_ms_profiled, 4) if step_ms_profiled else None}
+             for k, (ms, n) in prof.items() if n}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (eigensolver and weight in f64)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "T": w.T, "P": w.P, "Q": w.Q,
+                   "filter": [w.N1, w.N2, w.M], "irls": w.n_irls, "cg": w.n_cg,
+                   "lambda": w.lam, "p": w.p, "undersampling": w.R,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "256 MiB buffer written before every timed step (outside the events)"},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_source": peak_src,
+                     "alg_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
+                     "traffic": None},
+        "phases": phase,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(b.numel() * 8 + m.numel()),
+                "d2h_bytes_per_step": int(out.numel() * 8)},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        rate, n, dt, cores = cpu_oracle_rate(w, prob)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} IRLS iterations of {WORKLOAD} (Gram + eigh + weight + {w.n_cg} CG) "
+                      f"in {dt:.1f} s, FP64 NumPy; numpy.fft single-threaded, eigh on BLAS threads"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * recon.h -- C ABI of the GB300 IRLS reconstruction of damped-exponential image series by
+ * structured low-rank matrix completion (Balachandrasekaran, Magnotta, Jacob, arXiv 1704.04511).
+ *
+ * Problem (Sec. II-D, Eq. problem-formulation-relaxed, solved by Algorithm 1 of Sec. III):
+ *     x* = argmin_x  ||T(F x)||_p  +  (1/lam) * ||A x - b||^2-style data term,
+ * implemented as the IRLS alternation of Eq. x-update / Eq. weight-update:
+ *     weight:  G = T^H T (Gram of the lifted matrix),  H = (G + eps I)^(p/2 - 1)
+ *     x-step:  (A^H A + lam W_H) x = A^H b by a fixed number of CG steps, warm-started,
+ * with x0 = A^H b, eps0 = eps0_frac * lambda_max(G(x0)), eps <- eps / gamma per iteration
+ * (Sec. III-C).
+ *
+ * Conventions shared by every entry point:
+ *  - Image series and k-space are [T][P][Q] arrays (Q fastest) of complex64 (interleaved
+ *    float re, im). k-space may instead be bfloat16 pairs (kspace_bf16 = 1).
+ *  - F is the unitary 2-D DFT per frame, forward sign e^{-2 pi i}, natural frequency order
+ *    (DC at index 0, no fftshift). A = mask * F per frame (one coil, Eq. measurement-ij).
+ *  - Masks are [T][P][Q] uint8, nonzero = sampled (treated as exactly 1).
+ *  - Filter support N1 x N2 spatial taps x M frame taps (s = N1 N2 M columns of the lifted
+ *    matrix; column index a = (m N1 + l1) N2 + l2). The lifting is circular in space and a valid
+ *    linear convolution over frames (the hybrid approximation of Sec. III-A), k = T - M + 1.
+ *  - Every data pointer is a DEVICE pointer on the context's device unless stated otherwise,
+ *    owned by the caller, and must stay valid until the call returns. Calls are synchronous:
+ *    they return after the device work finished (results readable).
+ *  - Supported sizes: P, Q in {16, 32, 64, 128, 192, 256, 512}; 1 <= M <= 6, M <= T;
+ *    1 <= N1 <= P, 1 <= N2 <= Q; T * Q <= 8738 (fused row/W pass).
+ *  - Return value: RECON_OK (0) or a negative RECON_E* code; recon_last_error() describes it.
+ *    A failed call never reports partial output as valid.
+ */
+#ifndef RECON_H
+#define RECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RECON_OK 0
+#define RECON_EINVAL (-1)   /* bad dims / filter / parameters / null pointer            */
+#define RECON_ENOMEM (-2)   /* request exceeds the context budget or allocation failed  */
+#define RECON_ECUDA (-3)    /* CUDA runtime or library error                            */
+#define RECON_ENUMERIC (-4) /* NaN / Inf in the iteration, or eigensolver failure       */
+
+typedef struct recon_ctx recon_ctx;
+
+typedef struct {
+    int P, Q, T; /* grid P x Q (Q fastest), T frames */
+} recon_dims;
+
+typedef struct {
+    int N1, N2, M; /* filter support: N1 x N2 spatial taps, M frame taps */
+} recon_filter;
+
+typedef struct {
+    int irls;         /* IRLS iterations (Algorithm 1 outer loop), >= 0            */
+    int cg;           /* CG steps per IRLS iteration (Algorithm 1, step 2), >= 1   */
+    double lambda;    /* weight of the structured penalty, > 0                     */
+    double p;         /* Schatten-p exponent, 0 <= p <= 1 (Eq. problem-formulation-relaxed) */
+    double gamma;     /* eps decay factor, > 1 (Sec. III-C uses 1.4)               */
+    double eps0_frac; /* eps0 = eps0_frac * lambda_max(G(x0)) (Sec. III-C uses 0.01) */
+    int kspace_bf16;  /* 1: kspace holds bfloat16 (re, im) pairs; 0: complex64      */
+} recon_params;
+
+/* Create a context on `device`. It owns device workspace (grown on demand, never beyond
+ * mem_budget_bytes; 0 = no limit), the twiddle tables and an eigensolver handle, and issues all
+ * work on `cuda_stream` (a cudaStream_t; NULL = a stream the context creates). One context must
+ * not be used by two host threads at once. Returns RECON_OK and sets *out, or an error code. */
+int recon_create(recon_ctx** out, int device, size_t mem_budget_bytes, void* cuda_stream);
+
+/* Release the context and all its device memory. NULL is ignored. */
+void recon_destroy(recon_ctx* c);
+
+/* Description of the last error on this context (static storage; never NULL). */
+const char* recon_last_error(const recon_ctx* c);
+
+/* Device bytes of workspace recon_solve needs for this problem (the admission formula). */
+size_t recon_bytes_needed(recon_dims d, recon_filter f, int kspace_bf16);
+
+/* Full reconstruction, Algorithm 1 (Sec. III): x0 = A^H b, then prm->irls iterations of
+ * [Gram (Eq. P-ij-modified) -> FP64 eigendecomposition -> weight (Eq. weight-update) ->
+ * per-pixel S(r) -> prm->cg CG steps on Eq. grad-ls]. kspace: [T][P][Q] complex64 or bf16
+ * pairs; masks: [T][P][Q] uint8; image_out: [T][P][Q] complex64, receives x. */
+int recon_solve(recon_ctx* c, recon_dims d, const void* kspace, const uint8_t* masks,
+                recon_filter f, const recon_params* prm, void* image_out);
+
+/* ---- stage entry points (the same kernels recon_solve runs; used for parity checks) ---- */
+
+/* x = A^H b = F^H (mask * b) (Sec. II-A). */
+int recon_adjoint(recon_ctx* c, recon_dims d, const void* kspace, int kspace_bf16,
+                  const uint8_t* masks, void* x_out);
+
+/* y = F x (inverse = 0) or F^H x (inverse = 1), every frame; x and y complex64 [T][P][Q];
+ * y may equal x. */
+int recon_fft2(recon_ctx* c, recon_dims d, const void* x, void* y, int inverse);
+
+/* Gram matrix of the lifted matrix of F x (Sec. III-B, Eq. block-expression-for-R,
+ * Eq. P-ij-modified): G_out, s x s complex128 column-major (both triangles written);
+ * lags_out (may be NULL): npair x (2N1-1) x (2N2-1) complex128, pair (a <= b) at index
+ * a(2M-a+1)/2 + (b-a), lag (d1, d2) at offset (N1-1, N2-1):
+ * lag_ab[d] = sum_r sum_{j<k} conj(x_{j+M-1-a}(r)) x_{j+M-1-b}(r) e^{-2 pi i (d1 r1/P + d2 r2/Q)}. */
+int recon_gram(recon_ctx* c, recon_dims d, recon_filter f, const void* x, void* G_out,
+               void* lags_out);
+
+/* Weight step (Sec. III-B, Eq. weight-update): eigendecomposition of G_in (s x s complex128,
+ * column-major, Hermitian; not modified) in FP64, H = U diag((lambda+eps)^(p/2-1)) U^H, summed
+ * diagonals d_ab[delta] = sum_{l-l'=delta} H[(l',b),(l,a)] and the per-pixel weight
+ * S_ab(r) = sum_delta d_ab[delta] e^{-2 pi i (delta.r)}.
+ * eps: if eps_in >= 0 it is used; else eps = -eps_in * lambda_max(G) (so -0.01 gives the
+ * Sec. III-C initial value). S_out: npair x P x Q complex64 (pair layout as above);
+ * dsum_out (may be NULL): npair x (2N1-1) x (2N2-1) complex128; evals_out (may be NULL): s
+ * doubles ascending; eps_out (host pointer, may be NULL) receives the eps used. */
+int recon_weight(recon_ctx* c, recon_dims d, recon_filter f, const void* G_in, double eps_in,
+                 double p, void* S_out, void* dsum_out, void* evals_out, double* eps_out);
+
+/* y = (A^H A + lambda W_S) x with W_S the per-pixel banded frame operator of Eq. grad-ls:
+ * (W x)_n(r) = sum_{a: 0 <= n-M+1+a < k} sum_b S_ab(r) x_{n+a-b}(r). S as from recon_weight.
+ * lambda = 0 gives A^H A x. y must not alias x. */
+int recon_apply_normal(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
+                       const void* S, double lambda, const void* x, void* y);
+
+/* y = W_S x (no lambda, no data term). y must not alias x. */
+int recon_apply_w(recon_ctx* c, recon_dims d, recon_filter f, const void* S, const void* x,
+                  void* y);
+
+/* One least-squares step of Algorithm 1 as recon_solve runs it: residual carry
+ * r <- (S_old == NULL ? 0 : r) + lambda W_{S_old - S_new} x   (S_old == NULL: r = -lambda W x,
+ * valid when x = A^H b), then n_cg CG steps on (A^H A + lambda W_{S_new}) with x, r updated in
+ * place. rr_hist (host, may be NULL) receives n_cg + 1 values |r_c|^2. */
+int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
+             const void* S_old, const void* S_new, double lambda, void* x, void* r, int n_cg,
+             double* rr_hist);
+
+/* ---- measurement ---- */
+
+/* Launch classes timed by recon_profile (one pair of CUDA events on the context's stream around
+ * every launch of the class; the eigensolver class brackets the whole library call). */
+#define RECON_PROF_ADJOINT 0      /* x0 = A^H b: column + row pass                       */
+#define RECON_PROF_GRAM 1         /* Gram lags + fill of G                                */
+#define RECON_PROF_EIG 2          /* FP64 eigendecomposition (cuSOLVER zheevd)            */
+#define RECON_PROF_EPS 3          /* eps schedule                                         */
+#define RECON_PROF_DIAG 4         /* summed diagonals of H (FP64)                         */
+#define RECON_PROF_S 5            /* per-pixel S(r)                                       */
+#define RECON_PROF_RESID 6        /* residual carry between IRLS iterations               */
+#define RECON_PROF_CG_ROWFWD 7    /* CG pass A: p update + row FFT                        */
+#define RECON_PROF_CG_COL 8       /* CG pass B: column FFT, mask, column IFFT             */
+#define RECON_PROF_CG_ROWINVW 9   /* CG pass C: row IFFT + lambda W p + <p, q> partials    */
+#define RECON_PROF_CG_UPDATE 10   /* CG pass D: x, r update + |r|^2 partials               */
+#define RECON_PROF_KINDS 11
+
+/* Enable (1) or disable (0) per-launch event timing on this context; resets the totals. */
+int recon_profile(recon_ctx* c, int enable);
+/* Total device milliseconds and launch count of one class since the last recon_profile call
+ * (waits for the recorded events). */
+int recon_profile_read(recon_ctx* c, int kind, double* total_ms, long long* launches);
+/* Name of a launch class ("" if out of range). */
+const char* recon_profile_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECON_H */

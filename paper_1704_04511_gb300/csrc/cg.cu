@@ -1,0 +1,307 @@
+// CG operator tail, CG vector updates and the warm-start residual carry (Sec. III-A,
+// Eq. grad-ls; Algorithm 1, step 2).
+//
+// The sum-of-squares weight acts per pixel r as a banded frame operator built from the M x M
+// Hermitian matrix S(r) (the precomputed G of Eq. grad-ls, the sum of k shifted copies of one
+// block product):
+//     (W x)_n(r) = sum_{a : 0 <= n-M+1+a < k} sum_b S_ab(r) x_{n+a-b}(r),
+// which is sum_j E_j^T S(r) E_j x(r) with (E_j x)(r)[m] = x_{j+M-1-m}(r). S is stored as its
+// upper triangle, pair (a <= b) at index a(2M-a+1)/2 + (b-a), layout [pair][P][Q] complex64.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace recon {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxM = 6;
+constexpr int kVecParts = 304;
+
+RECON_DEV int pair_index(int a, int b, int M) { return a * (2 * M - a + 1) / 2 + (b - a); }
+
+// Load S(r) (full M x M from the stored upper triangle) into registers.
+template <int M>
+RECON_DEV void load_S(const float2* __restrict__ S, size_t npix, size_t px, float2 (&s)[M][M]) {
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = a; b < M; ++b) {
+            const float2 v = S[(size_t)(a * (2 * M - a + 1) / 2 + (b - a)) * npix + px];
+            s[a][b] = v;
+            s[b][a] = cconj(v);
+        }
+}
+
+// Pass C of a CG step. One CTA per image row r1 holds that row of every frame: it inverse-
+// transforms the k-space rows of t (giving A^H A p; the 1/(PQ) scale was applied with the mask),
+// adds lam W p from the p rows, writes q over t and emits the partial Re <p, q> of its row.
+template <int N, int M>
+__global__ void __launch_bounds__(kThreads)
+row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
+                 float lam, int T, int P, double* __restrict__ part_pq,
+                 const float2* __restrict__ tw_g) {
+    extern __shared__ float2 sm[];
+    __shared__ double red[kThreads / 32];
+    float2* a = sm;
+    float2* b = a + (size_t)T * N;
+    float2* pt = b + (size_t)T * N;
+    float2* tw = pt + (size_t)T * N;
+    const int r1 = blockIdx.x;
+    const size_t npix = (size_t)P * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int n = e / N, c = e % N;
+        const size_t g = (size_t)n * npix + (size_t)r1 * N + c;
+        a[e] = t[g];
+        pt[e] = p[g];
+    }
+    __syncthreads();
+    float2* res = fft_smem<N, true, false>(a, b, T, N, 1, tw);
+    const int k = T - M + 1;
+    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        float2 s[M][M];
+        load_S<M>(S, npix, (size_t)r1 * N + c, s);
+        for (int n = 0; n < T; ++n) {
+            float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int aa = 0; aa < M; ++aa) {
+                const int j = n - M + 1 + aa;
+                if (j < 0 || j >= k) continue;
+#pragma unroll
+                for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(n + aa - bb) * N + c], w);
+            }
+            float2 q = res[n * N + c];
+            q.x = fmaf(lam, w.x, q.x);
+            q.y = fmaf(lam, w.y, q.y);
+            res[n * N + c] = q;
+            const float2 pv = pt[n * N + c];
+            const float term = fmaf(pv.x, q.x, pv.y * q.y) - comp;
+            const float sum = acc + term;
+            comp = (sum - acc) - term;
+            acc = sum;
+        }
+    }
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) part_pq[r1] = tot;
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int n = e / N, c = e % N;
+        t[(size_t)n * npix + (size_t)r1 * N + c] = res[e];
+    }
+}
+
+// Pass D: alpha = |r|^2 / Re <p, q>; x += alpha p; r -= alpha q; partial |r_new|^2.
+__global__ void __launch_bounds__(kThreads)
+cg_update_kernel(float4* __restrict__ x, float4* __restrict__ r, const float4* __restrict__ p,
+                 const float4* __restrict__ q, size_t n4, const double* __restrict__ part_rr_in,
+                 const double* __restrict__ part_pq, int nparts_pq,
+                 double* __restrict__ part_rr_out, int nparts, double* __restrict__ hist) {
+    __shared__ double red[kThreads / 32];
+    const double rr = block_sum_array(part_rr_in, nparts, red);
+    const double pq = block_sum_array(part_pq, nparts_pq, red);
+    const double alpha_d = rr / pq;
+    const float alpha = (float)alpha_d;
+    if (hist && blockIdx.x == 0 && threadIdx.x == 0) {
+        hist[0] = rr;
+        hist[1] = pq;
+        hist[2] = alpha_d;
+    }
+    float acc = 0.f, comp = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float4 xv = x[i], rv = r[i];
+        const float4 pv = p[i], qv = q[i];
+        xv.x = fmaf(alpha, pv.x, xv.x);
+        xv.y = fmaf(alpha, pv.y, xv.y);
+        xv.z = fmaf(alpha, pv.z, xv.z);
+        xv.w = fmaf(alpha, pv.w, xv.w);
+        rv.x = fmaf(-alpha, qv.x, rv.x);
+        rv.y = fmaf(-alpha, qv.y, rv.y);
+        rv.z = fmaf(-alpha, qv.z, rv.z);
+        rv.w = fmaf(-alpha, qv.w, rv.w);
+        x[i] = xv;
+        r[i] = rv;
+        const float term = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w))) - comp;
+        const float sum = acc + term;
+        comp = (sum - acc) - term;
+        acc = sum;
+    }
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) part_rr_out[blockIdx.x] = tot;
+}
+
+// Residual carry between IRLS iterations: r = (first ? 0 : r) + lam W_{dS} x with
+// dS = S_old - S_new (or -S_new when first); partial |r|^2. One thread per pixel, all frames.
+template <int M>
+__global__ void __launch_bounds__(kThreads)
+resid_carry_kernel(float2* __restrict__ r, const float2* __restrict__ x,
+                   const float2* __restrict__ S_old, const float2* __restrict__ S_new, float lam,
+                   int first, int T, size_t npix, double* __restrict__ part_rr) {
+    __shared__ double red[kThreads / 32];
+    const int k = T - M + 1;
+    float acc = 0.f, comp = 0.f;
+    for (size_t px = (size_t)blockIdx.x * blockDim.x + threadIdx.x; px < npix;
+         px += (size_t)gridDim.x * blockDim.x) {
+        float2 s[M][M];
+        load_S<M>(S_new, npix, px, s);
+        if (first) {
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int b = 0; b < M; ++b) s[a][b] = make_float2(-s[a][b].x, -s[a][b].y);
+        } else {
+            float2 so[M][M];
+            load_S<M>(S_old, npix, px, so);
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int b = 0; b < M; ++b) s[a][b] = csub(so[a][b], s[a][b]);
+        }
+        for (int n = 0; n < T; ++n) {
+            float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                const int j = n - M + 1 + a;
+                if (j < 0 || j >= k) continue;
+#pragma unroll
+                for (int b = 0; b < M; ++b) w = cfma(s[a][b], x[(size_t)(n + a - b) * npix + px], w);
+            }
+            float2 rv = first ? make_float2(0.f, 0.f) : r[(size_t)n * npix + px];
+            rv.x = fmaf(lam, w.x, rv.x);
+            rv.y = fmaf(lam, w.y, rv.y);
+            r[(size_t)n * npix + px] = rv;
+            const float term = fmaf(rv.x, rv.x, rv.y * rv.y) - comp;
+            const float sum = acc + term;
+            comp = (sum - acc) - term;
+            acc = sum;
+        }
+    }
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) part_rr[blockIdx.x] = tot;
+}
+
+// y = W_S x (no lambda); parity tests only.
+template <int M>
+__global__ void __launch_bounds__(kThreads)
+apply_w_kernel(const float2* __restrict__ x, const float2* __restrict__ S, float2* __restrict__ y,
+               int T, size_t npix) {
+    const int k = T - M + 1;
+    for (size_t px = (size_t)blockIdx.x * blockDim.x + threadIdx.x; px < npix;
+         px += (size_t)gridDim.x * blockDim.x) {
+        float2 s[M][M];
+        load_S<M>(S, npix, px, s);
+        for (int n = 0; n < T; ++n) {
+            float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                const int j = n - M + 1 + a;
+                if (j < 0 || j >= k) continue;
+#pragma unroll
+                for (int b = 0; b < M; ++b) w = cfma(s[a][b], x[(size_t)(n + a - b) * npix + px], w);
+            }
+            y[(size_t)n * npix + px] = w;
+        }
+    }
+}
+
+template <int N, int M>
+cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                                const float2* S, float lam, double* part_pq, cudaStream_t st) {
+    auto k = row_inv_w_kernel<N, M>;
+    const size_t smem = ((size_t)3 * d.T * N + N) * sizeof(float2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<d.P, kThreads, smem, st>>>(t, p, S, lam, d.T, d.P, part_pq, tw.twQ);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_row_inv_w_N(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                               const float2* S, float lam, double* part_pq, cudaStream_t st) {
+    switch (d.M) {
+        case 1: return launch_row_inv_w_NM<N, 1>(d, tw, t, p, S, lam, part_pq, st);
+        case 2: return launch_row_inv_w_NM<N, 2>(d, tw, t, p, S, lam, part_pq, st);
+        case 3: return launch_row_inv_w_NM<N, 3>(d, tw, t, p, S, lam, part_pq, st);
+        case 4: return launch_row_inv_w_NM<N, 4>(d, tw, t, p, S, lam, part_pq, st);
+        case 5: return launch_row_inv_w_NM<N, 5>(d, tw, t, p, S, lam, part_pq, st);
+        case 6: return launch_row_inv_w_NM<N, 6>(d, tw, t, p, S, lam, part_pq, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int pix_grid(size_t npix) {
+    const size_t g = (npix + kThreads - 1) / kThreads;
+    return (int)(g < (size_t)kVecParts ? g : (size_t)kVecParts);
+}
+
+}  // namespace
+
+int w_max_M() { return kMaxM; }
+int w_max_frames_times_q() { return (200 * 1024) / (3 * (int)sizeof(float2)); }
+int vec_parts() { return kVecParts; }
+
+cudaError_t launch_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                             const float2* S, float lam, double* part_pq, cudaStream_t st) {
+    switch (d.Q) {
+        case 16: return launch_row_inv_w_N<16>(d, tw, t, p, S, lam, part_pq, st);
+        case 32: return launch_row_inv_w_N<32>(d, tw, t, p, S, lam, part_pq, st);
+        case 64: return launch_row_inv_w_N<64>(d, tw, t, p, S, lam, part_pq, st);
+        case 128: return launch_row_inv_w_N<128>(d, tw, t, p, S, lam, part_pq, st);
+        case 192: return launch_row_inv_w_N<192>(d, tw, t, p, S, lam, part_pq, st);
+        case 256: return launch_row_inv_w_N<256>(d, tw, t, p, S, lam, part_pq, st);
+        case 512: return launch_row_inv_w_N<512>(d, tw, t, p, S, lam, part_pq, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* p,
+                             const float2* q, const double* part_rr_in, const double* part_pq,
+                             int nparts_pq, double* part_rr_out, int nparts, double* hist,
+                             cudaStream_t st) {
+    const size_t n4 = d.elems() / 2;  // two complex values per float4
+    cg_update_kernel<<<nparts, kThreads, 0, st>>>(
+        reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(r),
+        reinterpret_cast<const float4*>(p), reinterpret_cast<const float4*>(q), n4, part_rr_in,
+        part_pq, nparts_pq, part_rr_out, nparts, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const float2* S_old,
+                               const float2* S_new, float lam, int first, double* part_rr_out,
+                               int nparts, cudaStream_t st) {
+    // zero the partials that a small pixel grid does not reach
+    const int g = pix_grid(d.pixels());
+    if (g < nparts) {
+        cudaError_t e = cudaMemsetAsync(part_rr_out + g, 0, (size_t)(nparts - g) * sizeof(double), st);
+        if (e != cudaSuccess) return e;
+    }
+#define CASE(MM)                                                                              \
+    case MM:                                                                                  \
+        resid_carry_kernel<MM><<<g, kThreads, 0, st>>>(r, x, S_old, S_new, lam, first, d.T,   \
+                                                       d.pixels(), part_rr_out);              \
+        break;
+    switch (d.M) {
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_w(const Dims& d, const float2* x, const float2* S, float2* y,
+                           cudaStream_t st) {
+    const int g = pix_grid(d.pixels());
+#define CASE(MM)                                                                        \
+    case MM: apply_w_kernel<MM><<<g, kThreads, 0, st>>>(x, S, y, d.T, d.pixels()); break;
+    switch (d.M) {
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CASE
+    return cudaGetLastError();
+}
+
+}  // namespace recon

@@ -1,0 +1,225 @@
+// Device helpers shared by the recon kernels: complex arithmetic, warp reductions and the
+// in-shared-memory Stockham FFT used by the row and column passes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define RECON_DEV __device__ __forceinline__
+
+// ------------------------------------------------------------------------------------------
+// complex helpers (float2 / double2 hold (re, im))
+// ------------------------------------------------------------------------------------------
+RECON_DEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+RECON_DEV float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+RECON_DEV float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+RECON_DEV float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+RECON_DEV float2 cmulcj(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+RECON_DEV float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// acc += a * b
+RECON_DEV float2 cfma(float2 a, float2 b, float2 acc) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    return acc;
+}
+// acc += conj(a) * b
+RECON_DEV float2 cfmacj(float2 a, float2 b, float2 acc) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(-a.y, b.x, acc.y);
+    return acc;
+}
+
+RECON_DEV double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+RECON_DEV double2 zmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+RECON_DEV double2 zfma(double2 a, double2 b, double2 acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+// acc += a * conj(b)
+RECON_DEV double2 zfmacj2(double2 a, double2 b, double2 acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.y, b.x, acc.y);
+    acc.y = fma(-a.x, b.y, acc.y);
+    return acc;
+}
+RECON_DEV double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+
+RECON_DEV float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+RECON_DEV double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of one double per thread (fixed tree order -> deterministic). `red` needs
+// blockDim.x / 32 doubles of shared memory. Every thread gets the result.
+RECON_DEV double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < nw ? red[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) red[0] = t;
+    }
+    __syncthreads();
+    t = red[0];
+    __syncthreads();
+    return t;
+}
+
+// Deterministic sum of n doubles in global memory by the whole block (every thread gets it).
+RECON_DEV double block_sum_array(const double* a, int n, double* red) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += a[i];
+    return block_sum(v, red);
+}
+
+// ------------------------------------------------------------------------------------------
+// Small DFTs in registers: U[f] = sum_t u[t] e^{s 2 pi i t f / R}, s = -1 forward, +1 inverse.
+// ------------------------------------------------------------------------------------------
+template <bool INV>
+RECON_DEV float2 mul_mi(float2 a) {  // a * (-i) forward, a * (+i) inverse
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int R, bool INV>
+struct SmallDFT;
+
+template <bool INV>
+struct SmallDFT<2, INV> {
+    RECON_DEV static void run(float2* u) {
+        float2 a = u[0], b = u[1];
+        u[0] = cadd(a, b);
+        u[1] = csub(a, b);
+    }
+};
+
+template <bool INV>
+struct SmallDFT<3, INV> {
+    RECON_DEV static void run(float2* u) {
+        const float c = 0.86602540378443864676f;  // sqrt(3)/2
+        float2 s = cadd(u[1], u[2]);
+        float2 d = csub(u[1], u[2]);
+        float2 t = make_float2(u[0].x - 0.5f * s.x, u[0].y - 0.5f * s.y);
+        float2 id = mul_mi<INV>(d);              // -i d forward
+        u[0] = cadd(u[0], s);
+        u[1] = make_float2(t.x + c * id.x, t.y + c * id.y);
+        u[2] = make_float2(t.x - c * id.x, t.y - c * id.y);
+    }
+};
+
+template <bool INV>
+struct SmallDFT<4, INV> {
+    RECON_DEV static void run(float2* u) {
+        float2 a0 = cadd(u[0], u[2]), a1 = csub(u[0], u[2]);
+        float2 a2 = cadd(u[1], u[3]), a3 = mul_mi<INV>(csub(u[1], u[3]));
+        u[0] = cadd(a0, a2);
+        u[2] = csub(a0, a2);
+        u[1] = cadd(a1, a3);
+        u[3] = csub(a1, a3);
+    }
+};
+
+template <bool INV>
+struct SmallDFT<8, INV> {
+    RECON_DEV static void run(float2* u) {
+        float2 e[4] = {u[0], u[2], u[4], u[6]};
+        float2 o[4] = {u[1], u[3], u[5], u[7]};
+        SmallDFT<4, INV>::run(e);
+        SmallDFT<4, INV>::run(o);
+        const float h = 0.70710678118654752440f;
+        // w8^f for f = 0..3, w8 = e^{-i pi/4} forward
+        float2 o1 = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                        : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+        float2 o2 = mul_mi<INV>(o[2]);
+        float2 o3 = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                        : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+        u[0] = cadd(e[0], o[0]);
+        u[4] = csub(e[0], o[0]);
+        u[1] = cadd(e[1], o1);
+        u[5] = csub(e[1], o1);
+        u[2] = cadd(e[2], o2);
+        u[6] = csub(e[2], o2);
+        u[3] = cadd(e[3], o3);
+        u[7] = csub(e[3], o3);
+    }
+};
+
+__host__ __device__ constexpr int fft_radix_at(int n, int p) {
+    return ((n / p) % 8 == 0) ? 8 : ((n / p) % 4 == 0) ? 4 : ((n / p) % 3 == 0) ? 3 : 2;
+}
+__host__ __device__ constexpr int fft_num_stages(int n, int p = 1) {
+    return p >= n ? 0 : 1 + fft_num_stages(n, p * fft_radix_at(n, p));
+}
+
+// One Stockham autosort pass (radix R, span p) over `nseq` independent length-N sequences.
+// Element e of sequence s lives at buf[s * ss + e * es]. `tw` holds e^{-2 pi i j / N}, j < N,
+// in shared memory. SEQ_FAST selects the thread mapping: sequence index fastest (column
+// layouts, es > 1) or butterfly index fastest (row layouts, es == 1).
+template <int N, int R, bool INV, bool SEQ_FAST>
+RECON_DEV void stockham_pass(const float2* __restrict__ src, float2* __restrict__ dst, int p,
+                             int nseq, int ss, int es, const float2* __restrict__ tw) {
+    constexpr int NR = N / R;
+    const int total = nseq * NR;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        int s, i;
+        if (SEQ_FAST) { s = w % nseq; i = w / nseq; }
+        else          { s = w / NR;   i = w % NR; }
+        const int k = i % p;
+        const float2* in = src + s * ss;
+        float2 u[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) u[t] = in[(i + t * NR) * es];
+        if (p > 1) {
+            const int step = N / (p * R);
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                float2 w_ = tw[t * k * step];
+                if (INV) w_.y = -w_.y;
+                u[t] = cmul(u[t], w_);
+            }
+        }
+        SmallDFT<R, INV>::run(u);
+        const int j = (i - k) * R + k;
+        float2* out = dst + s * ss;
+#pragma unroll
+        for (int t = 0; t < R; ++t) out[(j + t * p) * es] = u[t];
+    }
+}
+
+// Full length-N FFT of nseq sequences, ping-ponging between a and b (both in shared memory).
+// Returns the buffer that holds the result. Ends with __syncthreads().
+template <int N, bool INV, bool SEQ_FAST, int P = 1>
+RECON_DEV float2* fft_smem(float2* a, float2* b, int nseq, int ss, int es, const float2* tw) {
+    if constexpr (P >= N) {
+        return a;
+    } else {
+        constexpr int R = fft_radix_at(N, P);
+        stockham_pass<N, R, INV, SEQ_FAST>(a, b, P, nseq, ss, es, tw);
+        __syncthreads();
+        return fft_smem<N, INV, SEQ_FAST, P * R>(b, a, nseq, ss, es, tw);
+    }
+}

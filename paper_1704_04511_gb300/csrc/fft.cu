@@ -1,0 +1,244 @@
+// Row and column passes of the unitary 2-D DFT used by the forward model A = mask * F
+// (Sec. II-A, Eq. measurement-ij with one coil) and by the CG operator (Sec. III-A, Eq. grad-ls).
+//
+// Layout: frames [T][P][Q] complex64, Q contiguous. A row pass transforms length-Q rows
+// (ROWS rows per CTA, staged in shared memory); a column pass transforms a P x 16 tile of
+// 16 adjacent columns of one frame (128-byte row segments, coalesced), optionally applying the
+// sampling mask between a forward and an inverse transform so that A^H A needs one column pass.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace recon {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kColTile = 16;
+
+template <int N>
+__host__ __device__ constexpr int rows_per_cta() { return N >= 2048 ? 1 : 2048 / N; }
+
+enum ColMode { COL_FWD = 0, COL_INV = 1, COL_MASK_OP = 2, COL_ADJ_C64 = 3, COL_ADJ_BF16 = 4 };
+
+template <int N, bool INV>
+__global__ void __launch_bounds__(kThreads)
+row_fft_kernel(const float2* in, float2* out, int nrows, float scale,
+               const float2* __restrict__ tw_g) {
+    constexpr int ROWS = rows_per_cta<N>();
+    extern __shared__ float2 sm[];
+    float2* a = sm;
+    float2* b = a + ROWS * N;
+    float2* tw = b + ROWS * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    const int row0 = blockIdx.x * ROWS;
+    const int nr = min(ROWS, nrows - row0);
+    const size_t base = (size_t)row0 * N;
+    for (int e = threadIdx.x; e < nr * N; e += blockDim.x) a[e] = in[base + e];
+    __syncthreads();
+    float2* res = fft_smem<N, INV, false>(a, b, nr, N, 1, tw);
+    for (int e = threadIdx.x; e < nr * N; e += blockDim.x) out[base + e] = cscale(res[e], scale);
+}
+
+// Pass A of a CG step: p = r (first) or r + beta p with beta = |r_c|^2 / |r_{c-1}|^2 from the
+// partial sums; p is written back and its row FFT goes to t.
+template <int N>
+__global__ void __launch_bounds__(kThreads)
+row_fwd_pupdate_kernel(const float2* __restrict__ r, float2* __restrict__ p,
+                       float2* __restrict__ t, int nrows, const double* __restrict__ part_num,
+                       const double* __restrict__ part_den, int nparts, int first,
+                       const float2* __restrict__ tw_g) {
+    constexpr int ROWS = rows_per_cta<N>();
+    extern __shared__ float2 sm[];
+    __shared__ double red[kThreads / 32];
+    float2* a = sm;
+    float2* b = a + ROWS * N;
+    float2* tw = b + ROWS * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    float beta = 0.f;
+    if (!first) {
+        const double num = block_sum_array(part_num, nparts, red);
+        const double den = block_sum_array(part_den, nparts, red);
+        beta = (float)(num / den);
+    }
+    const int row0 = blockIdx.x * ROWS;
+    const int nr = min(ROWS, nrows - row0);
+    const size_t base = (size_t)row0 * N;
+    for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
+        float2 v = r[base + e];
+        if (!first) {
+            const float2 pv = p[base + e];
+            v.x = fmaf(beta, pv.x, v.x);
+            v.y = fmaf(beta, pv.y, v.y);
+        }
+        p[base + e] = v;
+        a[e] = v;
+    }
+    __syncthreads();
+    float2* res = fft_smem<N, false, false>(a, b, nr, N, 1, tw);
+    for (int e = threadIdx.x; e < nr * N; e += blockDim.x) t[base + e] = res[e];
+}
+
+// Column pass over a P x 16 tile (frame blockIdx.y, columns 16*blockIdx.x ..).
+template <int N, int MODE>
+__global__ void __launch_bounds__(kThreads)
+col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
+           int Q, float scale, const float2* __restrict__ tw_g) {
+    constexpr int C = kColTile;
+    extern __shared__ float2 sm[];
+    float2* a = sm;
+    float2* b = a + N * C;
+    float2* tw = b + N * C;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    const int c0 = blockIdx.x * C;
+    const size_t fbase = (size_t)blockIdx.y * N * Q;
+    for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
+        const int i = e / C, c = e % C;
+        const size_t g = fbase + (size_t)i * Q + c0 + c;
+        float2 v;
+        if constexpr (MODE == COL_ADJ_BF16) {
+            const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162*>(in_)[g];
+            v = __bfloat1622float2(h);
+        } else {
+            v = reinterpret_cast<const float2*>(in_)[g];
+        }
+        if constexpr (MODE == COL_ADJ_C64 || MODE == COL_ADJ_BF16) {
+            v = mask[g] ? cscale(v, scale) : make_float2(0.f, 0.f);
+        }
+        a[e] = v;
+    }
+    __syncthreads();
+    float2* res;
+    if constexpr (MODE == COL_FWD) {
+        res = fft_smem<N, false, true>(a, b, C, 1, C, tw);
+    } else if constexpr (MODE == COL_INV || MODE == COL_ADJ_C64 || MODE == COL_ADJ_BF16) {
+        res = fft_smem<N, true, true>(a, b, C, 1, C, tw);
+    } else {  // COL_MASK_OP
+        float2* f = fft_smem<N, false, true>(a, b, C, 1, C, tw);
+        for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
+            const int i = e / C, c = e % C;
+            const uint8_t m = mask[fbase + (size_t)i * Q + c0 + c];
+            f[e] = m ? cscale(f[e], scale) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        res = fft_smem<N, true, true>(f, f == a ? b : a, C, 1, C, tw);
+    }
+    const float osc = (MODE == COL_FWD || MODE == COL_INV) ? scale : 1.f;
+    for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
+        const int i = e / C, c = e % C;
+        out[fbase + (size_t)i * Q + c0 + c] = cscale(res[e], osc);
+    }
+}
+
+template <int N>
+size_t row_smem() { return (size_t)(2 * rows_per_cta<N>() * N + N) * sizeof(float2); }
+template <int N>
+size_t col_smem() { return (size_t)(2 * N * kColTile + N) * sizeof(float2); }
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+    if (bytes > 48 * 1024)
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+// ---- size dispatch ----
+#define RECON_FFT_SIZES(X) X(16) X(32) X(64) X(128) X(192) X(256) X(512)
+
+template <bool INV>
+cudaError_t row_fft(int n, const float2* in, float2* out, int nrows, float scale,
+                    const float2* tw, cudaStream_t st) {
+    switch (n) {
+#define CASE(N)                                                                          \
+    case N: {                                                                            \
+        auto k = row_fft_kernel<N, INV>;                                                 \
+        cudaError_t e = set_smem(k, row_smem<N>());                                      \
+        if (e != cudaSuccess) return e;                                                  \
+        const int grid = (nrows + rows_per_cta<N>() - 1) / rows_per_cta<N>();            \
+        k<<<grid, kThreads, row_smem<N>(), st>>>(in, out, nrows, scale, tw);             \
+        return cudaGetLastError();                                                       \
+    }
+        RECON_FFT_SIZES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int MODE>
+cudaError_t col_pass(int n, int Q, int T, const void* in, float2* out, const uint8_t* mask,
+                     float scale, const float2* tw, cudaStream_t st) {
+    switch (n) {
+#define CASE(N)                                                                          \
+    case N: {                                                                            \
+        auto k = col_kernel<N, MODE>;                                                    \
+        cudaError_t e = set_smem(k, col_smem<N>());                                      \
+        if (e != cudaSuccess) return e;                                                  \
+        dim3 grid(Q / kColTile, T);                                                      \
+        k<<<grid, kThreads, col_smem<N>(), st>>>(in, out, mask, Q, scale, tw);           \
+        return cudaGetLastError();                                                       \
+    }
+        RECON_FFT_SIZES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool fft_size_supported(int n) {
+    switch (n) {
+#define CASE(N) case N: return true;
+        RECON_FFT_SIZES(CASE)
+#undef CASE
+        default: return false;
+    }
+}
+
+cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, float2* y, int inv,
+                        cudaStream_t st) {
+    const float sq = 1.0f / sqrtf((float)d.Q), sp = 1.0f / sqrtf((float)d.P);
+    cudaError_t e = inv ? row_fft<true>(d.Q, x, y, d.T * d.P, sq, tw.twQ, st)
+                        : row_fft<false>(d.Q, x, y, d.T * d.P, sq, tw.twQ, st);
+    if (e != cudaSuccess) return e;
+    return inv ? col_pass<COL_INV>(d.P, d.Q, d.T, y, y, nullptr, sp, tw.twP, st)
+               : col_pass<COL_FWD>(d.P, d.Q, d.T, y, y, nullptr, sp, tw.twP, st);
+}
+
+cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int b_bf16,
+                           const uint8_t* mask, float2* t, float2* x, cudaStream_t st) {
+    const float sc = 1.0f / sqrtf((float)d.P * (float)d.Q);
+    cudaError_t e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, d.Q, d.T, b, t, mask, sc, tw.twP, st)
+                           : col_pass<COL_ADJ_C64>(d.P, d.Q, d.T, b, t, mask, sc, tw.twP, st);
+    if (e != cudaSuccess) return e;
+    return row_fft<true>(d.Q, t, x, d.T * d.P, 1.0f, tw.twQ, st);
+}
+
+cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
+                                   float2* t, const double* rr_num, const double* rr_den,
+                                   int nparts, int first, cudaStream_t st) {
+    const int nrows = d.T * d.P;
+    switch (d.Q) {
+#define CASE(N)                                                                              \
+    case N: {                                                                                \
+        auto k = row_fwd_pupdate_kernel<N>;                                                  \
+        cudaError_t e = set_smem(k, row_smem<N>());                                          \
+        if (e != cudaSuccess) return e;                                                      \
+        const int grid = (nrows + rows_per_cta<N>() - 1) / rows_per_cta<N>();                \
+        k<<<grid, kThreads, row_smem<N>(), st>>>(r, p, t, nrows, rr_num, rr_den, nparts,     \
+                                                 first, tw.twQ);                             \
+        return cudaGetLastError();                                                           \
+    }
+        RECON_FFT_SIZES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
+                            cudaStream_t st) {
+    const float sc = 1.0f / ((float)d.P * (float)d.Q);
+    return col_pass<COL_MASK_OP>(d.P, d.Q, d.T, t, t, mask, sc, tw.twP, st);
+}
+
+}  // namespace recon

@@ -1,0 +1,93 @@
+// Internal launch interface between the C-ABI layer (recon.cu) and the kernel files.
+// Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace recon {
+
+// Geometry of one problem: image series [T][P][Q] complex64, filter N1 x N2 x M taps.
+struct Dims {
+    int T, P, Q;
+    int N1, N2, M;
+    int k() const { return T - M + 1; }
+    int npair() const { return M * (M + 1) / 2; }
+    int L1() const { return 2 * N1 - 1; }
+    int L2() const { return 2 * N2 - 1; }
+    int s() const { return N1 * N2 * M; }
+    size_t pixels() const { return (size_t)P * Q; }
+    size_t elems() const { return (size_t)T * P * Q; }
+};
+
+// Twiddle tables e^{-2 pi i j / n}, j < n, for the two grid lengths (device memory).
+struct Twiddles {
+    const float2* twP;   // length P, FP32
+    const float2* twQ;   // length Q, FP32
+    const double2* twPd; // length P, FP64
+    const double2* twQd; // length Q, FP64
+};
+
+bool fft_size_supported(int n);
+int w_max_M();
+int w_max_frames_times_q();  // bound on T * Q for the fused row/W kernel
+
+// ---- fft.cu ----
+// t = F^H (mask * b) / sqrt(PQ) (adjoint, Sec. II-A); b may be complex64 or bf16 pairs.
+cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int b_bf16,
+                           const uint8_t* mask, float2* t, float2* x, cudaStream_t st);
+// y = unitary forward (inv = 0) or inverse (inv = 1) 2-D DFT of every frame of x (in place ok)
+cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, float2* y, int inv,
+                        cudaStream_t st);
+// CG step, pass A: p = r (first) or r + beta p; t = row-FFT(p).
+cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
+                                   float2* t, const double* rr_num, const double* rr_den,
+                                   int nparts, int first, cudaStream_t st);
+// CG step, pass B: t = column-IFFT(mask * column-FFT(t)) / (PQ), in place.
+cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
+                            cudaStream_t st);
+
+// ---- cg.cu ----
+// CG step, pass C: q = row-IFFT(t) + lam W p written over t; part_pq[row] = Re <p, q> partials.
+cudaError_t launch_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                             const float2* S, float lam, double* part_pq, cudaStream_t st);
+// q = (A^H A + lam W) p with the same three passes (used by tests, scratch t == q)
+// CG step, pass D: alpha = rr / pq; x += alpha p; r -= alpha q; part_rr_out = |r|^2 partials.
+cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* p,
+                             const float2* q, const double* part_rr_in, const double* part_pq,
+                             int nparts_pq, double* part_rr_out, int nparts, double* hist,
+                             cudaStream_t st);
+// Residual carry: r = (first ? 0 : r) + lam W_{S_old - S_new} x (S_old ignored when first);
+// part_rr_out = |r|^2 partials.
+cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const float2* S_old,
+                               const float2* S_new, float lam, int first, double* part_rr_out,
+                               int nparts, cudaStream_t st);
+// y = W_S x alone (tests)
+cudaError_t launch_apply_w(const Dims& d, const float2* x, const float2* S, float2* y,
+                           cudaStream_t st);
+int vec_parts();  // number of partial sums the vector kernels write
+
+// ---- gram.cu ----
+// Lags of the Gram matrix (Sec. III-B): per-block partials then deterministic reduction and
+// Hermitian fill of G (column-major s x s complex128).
+size_t gram_scratch_bytes(const Dims& d, int nblocks);
+int gram_blocks(const Dims& d);
+cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, double2* lag_part,
+                        int nblocks, double2* lags, double2* G, cudaStream_t st);
+
+// ---- weight.cu ----
+// eps update: first -> eps = frac * lambda_max, else eps /= gamma
+cudaError_t launch_eps(const double* evals, int s, double* eps, int first, double frac,
+                       double gamma, cudaStream_t st);
+// Summed diagonals of H = U diag((lambda + eps)^(p/2-1)) U^H: d[pair][L1][L2] (complex128)
+size_t diag_scratch_bytes(const Dims& d);
+cudaError_t launch_diag_sums(const Dims& d, const double2* U, const double* evals,
+                             const double* eps, double p, double2* dpart, double2* dsum,
+                             cudaStream_t st);
+// S[pair][P][Q] (complex64) from the summed diagonals
+size_t s_scratch_bytes(const Dims& d);
+cudaError_t launch_weight_S(const Dims& d, const Twiddles& tw, const double2* dsum, double2* Z,
+                            float2* S, cudaStream_t st);
+
+}  // namespace recon

@@ -1,0 +1,702 @@
+// C ABI (include/recon.h): context, workspace, argument checks and the IRLS orchestration of
+// Algorithm 1 (Sec. III) over the kernels of fft.cu, gram.cu, weight.cu and cg.cu.
+//
+// Per IRLS iteration n (all on the context's stream, no host synchronisation):
+//   Gram of x^(n-1) -> G (FP64)                                  [gram.cu]
+//   G = U diag(lambda) U^H, FP64 (cuSOLVER zheevd)                [library call]
+//   eps: n = 1 -> eps0_frac * lambda_max, else eps / gamma        [Sec. III-C]
+//   summed diagonals of H, per-pixel S(r)                         [weight.cu]
+//   residual carry, then `cg` CG steps (4 passes each)            [cg.cu, fft.cu]
+// The CG warm-start residual is carried from the previous iteration's CG,
+//   r0^(1) = -lam W^(1) x0   (A^H A A^H b = A^H b for 0/1 masks),
+//   r0^(n+1) = r_end^(n) + lam (W^(n) - W^(n+1)) x^(n),
+// which equals A^H b - (A^H A + lam W^(n+1)) x^(n) in exact arithmetic but avoids forming it by
+// cancellation in FP32 (the two terms agree to ~1e-5 relative near convergence).
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/recon.h"
+#include "kernels.h"
+
+using recon::Dims;
+using recon::Twiddles;
+
+namespace {
+
+struct Buf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct TwTable {
+    float2* f = nullptr;
+    double2* d = nullptr;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct recon_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t allocated = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cusolverDnHandle_t solver = nullptr;
+    std::string err;
+    std::map<int, TwTable> tw;
+    std::map<std::string, Buf> bufs;
+    // optional per-launch CUDA-event timing (recon_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, size_t>> prof_pending;  // (kind, index of start event)
+    double prof_ms[RECON_PROF_KINDS] = {0};
+    long long prof_n[RECON_PROF_KINDS] = {0};
+};
+
+namespace {
+
+int fail(recon_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(recon_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, RECON_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define RC_CUDA(call)                                                \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);       \
+    } while (0)
+
+// Bracket one launch of `kind` with two events when profiling is on.
+struct ProfScope {
+    recon_ctx* c;
+    int kind;
+    size_t i0 = 0;
+    bool on = false;
+    ProfScope(recon_ctx* c_, int kind_) : c(c_), kind(kind_) {
+        if (!c->prof) return;
+        if (c->ev_used + 2 > c->ev_pool.size()) {
+            for (int k = 0; k < 256; ++k) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+                c->ev_pool.push_back(e);
+            }
+        }
+        i0 = c->ev_used;
+        c->ev_used += 2;
+        cudaEventRecord(c->ev_pool[i0], c->stream);
+        on = true;
+    }
+    ~ProfScope() {
+        if (!on) return;
+        cudaEventRecord(c->ev_pool[i0 + 1], c->stream);
+        c->prof_pending.push_back({kind, i0});
+    }
+};
+
+// Fold the recorded event pairs into the per-kind totals (synchronises on the events).
+void prof_collect(recon_ctx* c) {
+    for (auto& pk : c->prof_pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(c->ev_pool[pk.second + 1]);
+        if (cudaEventElapsedTime(&ms, c->ev_pool[pk.second], c->ev_pool[pk.second + 1]) == cudaSuccess) {
+            c->prof_ms[pk.first] += ms;
+            c->prof_n[pk.first] += 1;
+        }
+    }
+    c->prof_pending.clear();
+    c->ev_used = 0;
+}
+
+// Device buffer `name` of at least `bytes` (contents undefined on growth).
+int ensure(recon_ctx* c, const char* name, size_t bytes, void** out) {
+    Buf& b = c->bufs[name];
+    if (b.bytes >= bytes && b.ptr) {
+        *out = b.ptr;
+        return RECON_OK;
+    }
+    if (b.ptr) {
+        cudaFree(b.ptr);
+        c->allocated -= b.bytes;
+        b = Buf{};
+    }
+    const size_t want = bytes < 256 ? 256 : bytes;
+    if (c->budget && c->allocated + want > c->budget)
+        return fail(c, RECON_ENOMEM, std::string("workspace budget exceeded allocating ") + name);
+    cudaError_t e = cudaMalloc(&b.ptr, want);
+    if (e != cudaSuccess) {
+        b = Buf{};
+        cudaGetLastError();
+        return fail(c, RECON_ENOMEM, std::string("cudaMalloc failed for ") + name + ": " +
+                                         cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    c->allocated += want;
+    *out = b.ptr;
+    return RECON_OK;
+}
+
+int twiddles(recon_ctx* c, int n, TwTable* out) {
+    auto it = c->tw.find(n);
+    if (it != c->tw.end()) {
+        *out = it->second;
+        return RECON_OK;
+    }
+    std::vector<float2> hf(n);
+    std::vector<double2> hd(n);
+    for (int j = 0; j < n; ++j) {
+        // e^{-2 pi i j / n}; exact at the quarter points
+        double cr, ci;
+        if ((4 * j) % n == 0) {
+            const int q = (4 * j) / n;
+            const double cs[4] = {1.0, 0.0, -1.0, 0.0}, sn[4] = {0.0, -1.0, 0.0, 1.0};
+            cr = cs[q];
+            ci = sn[q];
+        } else {
+            const double ang = 2.0 * M_PI * (double)j / (double)n;
+            cr = std::cos(ang);
+            ci = -std::sin(ang);
+        }
+        hd[j] = make_double2(cr, ci);
+        hf[j] = make_float2((float)cr, (float)ci);
+    }
+    TwTable t;
+    RC_CUDA(cudaMalloc(&t.f, n * sizeof(float2)));
+    RC_CUDA(cudaMalloc(&t.d, n * sizeof(double2)));
+    RC_CUDA(cudaMemcpy(t.f, hf.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    RC_CUDA(cudaMemcpy(t.d, hd.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+    c->tw[n] = t;
+    *out = t;
+    return RECON_OK;
+}
+
+int get_twiddles(recon_ctx* c, const Dims& d, Twiddles* tw) {
+    TwTable tp, tq;
+    int rc = twiddles(c, d.P, &tp);
+    if (rc) return rc;
+    rc = twiddles(c, d.Q, &tq);
+    if (rc) return rc;
+    tw->twP = tp.f;
+    tw->twQ = tq.f;
+    tw->twPd = tp.d;
+    tw->twQd = tq.d;
+    return RECON_OK;
+}
+
+size_t gram_smem_bytes(const Dims& d) {
+    return (size_t)d.npair() * d.L1() * d.L2() * sizeof(double2) +
+           ((size_t)d.T * d.Q + (size_t)d.npair() * d.Q + d.Q) * sizeof(float2) + 2 * d.npair() * sizeof(int);
+}
+
+int check_dims(recon_ctx* c, recon_dims dd, const recon_filter* f, Dims* d) {
+    if (dd.P <= 0 || dd.Q <= 0 || dd.T <= 0) return fail(c, RECON_EINVAL, "P, Q, T must be positive");
+    if (!recon::fft_size_supported(dd.P) || !recon::fft_size_supported(dd.Q))
+        return fail(c, RECON_EINVAL, "P and Q must be one of 16, 32, 64, 128, 192, 256, 512");
+    d->T = dd.T;
+    d->P = dd.P;
+    d->Q = dd.Q;
+    d->N1 = d->N2 = d->M = 1;
+    if (f) {
+        if (f->M < 1 || f->M > recon::w_max_M() || f->M > dd.T)
+            return fail(c, RECON_EINVAL, "need 1 <= M <= min(6, T)");
+        if (f->N1 < 1 || f->N1 > dd.P || f->N2 < 1 || f->N2 > dd.Q)
+            return fail(c, RECON_EINVAL, "need 1 <= N1 <= P and 1 <= N2 <= Q");
+        d->N1 = f->N1;
+        d->N2 = f->N2;
+        d->M = f->M;
+        if (gram_smem_bytes(*d) > 220 * 1024)
+            return fail(c, RECON_EINVAL, "filter / frame count too large for the Gram kernel");
+    }
+    if ((long long)dd.T * dd.Q > recon::w_max_frames_times_q())
+        return fail(c, RECON_EINVAL, "T * Q too large for the fused row pass");
+    return RECON_OK;
+}
+
+struct Work {
+    float2 *r, *p, *t, *S0, *S1;
+    double2 *G, *lag_part, *lags, *dpart, *dsum, *Z, *eigwork;
+    double *evals, *part_pq, *part_rr, *eps, *hist;
+    int* info;
+    int lwork;
+    int gblocks;
+};
+
+int eig_lwork(recon_ctx* c, int s, double2* G, double* evals, int* lwork) {
+    cusolverStatus_t st = cusolverDnZheevd_bufferSize(
+        c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, s,
+        reinterpret_cast<cuDoubleComplex*>(G), s, evals, lwork);
+    if (st != CUSOLVER_STATUS_SUCCESS) return fail(c, RECON_ECUDA, "zheevd_bufferSize failed");
+    return RECON_OK;
+}
+
+// Allocate (or reuse) the workspace of one solve. n_info: number of eigensolves to record.
+int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_info, bool vectors, Work* w) {
+    void* ptr;
+    int rc;
+    const size_t vec = d.elems() * sizeof(float2);
+    const size_t sbytes = (size_t)d.npair() * d.pixels() * sizeof(float2);
+    const int s = d.s();
+    const size_t nlag = (size_t)d.npair() * d.L1() * d.L2();
+    w->gblocks = recon::gram_blocks(d);
+#define GET(name, bytes, field, type)                         \
+    rc = ensure(c, name, (bytes), &ptr);                      \
+    if (rc) return rc;                                        \
+    w->field = reinterpret_cast<type>(ptr);
+    if (vectors) {
+        GET("r", vec, r, float2*);
+        GET("p", vec, p, float2*);
+        GET("t", vec, t, float2*);
+        GET("S0", sbytes, S0, float2*);
+        GET("S1", sbytes, S1, float2*);
+    }
+    GET("G", (size_t)s * s * sizeof(double2), G, double2*);
+    GET("evals", (size_t)s * sizeof(double), evals, double*);
+    GET("lag_part", recon::gram_scratch_bytes(d, w->gblocks), lag_part, double2*);
+    GET("lags", nlag * sizeof(double2), lags, double2*);
+    GET("dpart", recon::diag_scratch_bytes(d), dpart, double2*);
+    GET("dsum", nlag * sizeof(double2), dsum, double2*);
+    GET("Z", recon::s_scratch_bytes(d), Z, double2*);
+    GET("part_pq", (size_t)d.P * sizeof(double), part_pq, double*);
+    GET("part_rr", (size_t)2 * recon::vec_parts() * sizeof(double), part_rr, double*);
+    GET("eps", sizeof(double), eps, double*);
+    GET("hist", (size_t)3 * (n_cg + 1) * sizeof(double), hist, double*);
+    GET("info", (size_t)(n_info < 1 ? 1 : n_info) * sizeof(int), info, int*);
+    rc = eig_lwork(c, s, w->G, w->evals, &w->lwork);
+    if (rc) return rc;
+    GET("eigwork", (size_t)(w->lwork < 1 ? 1 : w->lwork) * sizeof(double2), eigwork, double2*);
+#undef GET
+    return RECON_OK;
+}
+
+int run_eig(recon_ctx* c, int s, Work& w, int* info) {
+    cusolverStatus_t st = cusolverDnZheevd(
+        c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, s,
+        reinterpret_cast<cuDoubleComplex*>(w.G), s, w.evals,
+        reinterpret_cast<cuDoubleComplex*>(w.eigwork), w.lwork, info);
+    if (st != CUSOLVER_STATUS_SUCCESS) return fail(c, RECON_ECUDA, "cusolverDnZheevd failed");
+    return RECON_OK;
+}
+
+// Weight step on w.G (overwritten by eigenvectors): eps update, summed diagonals, S.
+int weight_step(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, double p, int eps_first,
+                double eps_frac, double gamma, int eps_mode_set, double eps_value, float2* S,
+                int* info) {
+    int rc;
+    {
+        ProfScope ps(c, RECON_PROF_EIG);
+        rc = run_eig(c, d.s(), w, info);
+    }
+    if (rc) return rc;
+    if (eps_mode_set) {
+        RC_CUDA(cudaMemcpyAsync(w.eps, &eps_value, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    } else {
+        ProfScope ps(c, RECON_PROF_EPS);
+        RC_CUDA(recon::launch_eps(w.evals, d.s(), w.eps, eps_first, eps_frac, gamma, c->stream));
+    }
+    {
+        ProfScope ps(c, RECON_PROF_DIAG);
+        RC_CUDA(recon::launch_diag_sums(d, w.G, w.evals, w.eps, p, w.dpart, w.dsum, c->stream));
+    }
+    {
+        ProfScope ps(c, RECON_PROF_S);
+        RC_CUDA(recon::launch_weight_S(d, tw, w.dsum, w.Z, S, c->stream));
+    }
+    return RECON_OK;
+}
+
+// Residual carry + n_cg CG steps on x (in place).
+int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uint8_t* mask,
+             const float2* S_old, const float2* S_new, float lam, float2* x, int first, int n_cg) {
+    const int nv = recon::vec_parts();
+    double* prr[2] = {w.part_rr, w.part_rr + nv};
+    {
+        ProfScope ps(c, RECON_PROF_RESID);
+        RC_CUDA(recon::launch_resid_carry(d, w.r, x, S_old, S_new, lam, first, prr[0], nv, c->stream));
+    }
+    for (int it = 0; it < n_cg; ++it) {
+        {
+            ProfScope ps(c, RECON_PROF_CG_ROWFWD);
+            RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, prr[it & 1], prr[(it + 1) & 1],
+                                                  nv, it == 0, c->stream));
+        }
+        {
+            ProfScope ps(c, RECON_PROF_CG_COL);
+            RC_CUDA(recon::launch_col_mask(d, tw, w.t, mask, c->stream));
+        }
+        {
+            ProfScope ps(c, RECON_PROF_CG_ROWINVW);
+            RC_CUDA(recon::launch_row_inv_w(d, tw, w.t, w.p, S_new, lam, w.part_pq, c->stream));
+        }
+        {
+            ProfScope ps(c, RECON_PROF_CG_UPDATE);
+            RC_CUDA(recon::launch_cg_update(d, x, w.r, w.p, w.t, prr[it & 1], w.part_pq, d.P,
+                                            prr[(it + 1) & 1], nv, w.hist + 3 * it, c->stream));
+        }
+    }
+    return RECON_OK;
+}
+
+int set_device(recon_ctx* c) {
+    RC_CUDA(cudaSetDevice(c->device));
+    return RECON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int recon_create(recon_ctx** out, int device, size_t mem_budget_bytes, void* cuda_stream) {
+    if (!out) return RECON_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        g_create_error = "no such CUDA device";
+        return RECON_ECUDA;
+    }
+    recon_ctx* c = new recon_ctx();
+    c->device = device;
+    c->budget = mem_budget_bytes;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        g_create_error = "cudaSetDevice failed";
+        delete c;
+        return RECON_ECUDA;
+    }
+    if (cuda_stream) {
+        c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            g_create_error = "cudaStreamCreate failed";
+            delete c;
+            return RECON_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    if (cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS) {
+        g_create_error = "cusolverDnCreate failed";
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return RECON_ECUDA;
+    }
+    *out = c;
+    return RECON_OK;
+}
+
+void recon_destroy(recon_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->bufs)
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    for (auto& kv : c->tw) {
+        cudaFree(kv.second.f);
+        cudaFree(kv.second.d);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->solver) cusolverDnDestroy(c->solver);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* recon_last_error(const recon_ctx* c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+size_t recon_bytes_needed(recon_dims dd, recon_filter f, int kspace_bf16) {
+    (void)kspace_bf16;  // k-space stays in the caller's buffer
+    Dims d{dd.T, dd.P, dd.Q, f.N1, f.N2, f.M};
+    if (d.T <= 0 || d.P <= 0 || d.Q <= 0 || d.M <= 0 || d.N1 <= 0 || d.N2 <= 0) return 0;
+    const size_t vec = d.elems() * sizeof(float2);
+    const size_t s = d.s();
+    const size_t nlag = (size_t)d.npair() * d.L1() * d.L2();
+    size_t b = 3 * vec + 2 * (size_t)d.npair() * d.pixels() * sizeof(float2);
+    b += s * s * sizeof(double2) * 3 + s * sizeof(double);  // G + eigensolver work (estimate)
+    b += recon::gram_scratch_bytes(d, recon::gram_blocks(d)) + recon::diag_scratch_bytes(d) +
+         2 * nlag * sizeof(double2) + recon::s_scratch_bytes(d);
+    b += (size_t)(d.P + 2 * recon::vec_parts() + 256) * sizeof(double);
+    return b;
+}
+
+int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* masks,
+                recon_filter f, const recon_params* prm, void* image_out) {
+    if (!c) return RECON_EINVAL;
+    if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    if (prm->irls < 0 || prm->cg < 1) return fail(c, RECON_EINVAL, "need irls >= 0, cg >= 1");
+    if (!(prm->lambda > 0.0) || !std::isfinite(prm->lambda))
+        return fail(c, RECON_EINVAL, "lambda must be positive and finite");
+    if (!(prm->p >= 0.0 && prm->p <= 1.0)) return fail(c, RECON_EINVAL, "need 0 <= p <= 1");
+    if (!(prm->gamma >= 1.0) || !std::isfinite(prm->gamma)) return fail(c, RECON_EINVAL, "need gamma >= 1");
+    if (!(prm->eps0_frac > 0.0) || !std::isfinite(prm->eps0_frac))
+        return fail(c, RECON_EINVAL, "eps0_frac must be positive");
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    Work w;
+    rc = get_work(c, d, prm->cg, prm->irls, true, &w);
+    if (rc) return rc;
+    float2* x = reinterpret_cast<float2*>(image_out);
+    const float lam = (float)prm->lambda;
+    {
+        ProfScope ps(c, RECON_PROF_ADJOINT);
+        RC_CUDA(recon::launch_adjoint(d, tw, kspace, prm->kspace_bf16, masks, w.t, x, c->stream));
+    }
+    float2* S[2] = {w.S0, w.S1};
+    for (int n = 0; n < prm->irls; ++n) {
+        float2* S_new = S[n & 1];
+        const float2* S_old = n == 0 ? nullptr : S[(n + 1) & 1];
+        {
+            ProfScope ps(c, RECON_PROF_GRAM);
+            RC_CUDA(recon::launch_gram(d, tw, x, w.lag_part, w.gblocks, nullptr, w.G, c->stream));
+        }
+        rc = weight_step(c, d, tw, w, prm->p, n == 0, prm->eps0_frac, prm->gamma, 0, 0.0, S_new,
+                         w.info + n);
+        if (rc) return rc;
+        rc = cg_block(c, d, tw, w, masks, S_old, S_new, lam, x, n == 0, prm->cg);
+        if (rc) return rc;
+    }
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    if (prm->irls > 0) {
+        std::vector<int> info(prm->irls);
+        RC_CUDA(cudaMemcpy(info.data(), w.info, prm->irls * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int n = 0; n < prm->irls; ++n)
+            if (info[n] != 0) return fail(c, RECON_ENUMERIC, "eigensolver failed (info != 0)");
+        const int nv = recon::vec_parts();
+        std::vector<double> part(nv);
+        RC_CUDA(cudaMemcpy(part.data(), w.part_rr + (prm->cg & 1) * nv, nv * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+        double rr = 0.0;
+        for (double v : part) rr += v;
+        double eps = 0.0;
+        RC_CUDA(cudaMemcpy(&eps, w.eps, sizeof(double), cudaMemcpyDeviceToHost));
+        if (!std::isfinite(rr) || !std::isfinite(eps))
+            return fail(c, RECON_ENUMERIC, "non-finite residual or eps in the iteration");
+    }
+    return RECON_OK;
+}
+
+int recon_adjoint(recon_ctx* c, recon_dims dd, const void* kspace, int kspace_bf16,
+                  const uint8_t* masks, void* x_out) {
+    if (!c) return RECON_EINVAL;
+    if (!kspace || !masks || !x_out) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims(c, dd, nullptr, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    void* t;
+    rc = ensure(c, "t", d.elems() * sizeof(float2), &t);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_adjoint(d, tw, kspace, kspace_bf16, masks, (float2*)t, (float2*)x_out,
+                                  c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int recon_fft2(recon_ctx* c, recon_dims dd, const void* x, void* y, int inverse) {
+    if (!c) return RECON_EINVAL;
+    if (!x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims(c, dd, nullptr, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_fft2(d, tw, (const float2*)x, (float2*)y, inverse, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int recon_gram(recon_ctx* c, recon_dims dd, recon_filter f, const void* x, void* G_out,
+               void* lags_out) {
+    if (!c) return RECON_EINVAL;
+    if (!x || !G_out) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    void* lp;
+    const int nb = recon::gram_blocks(d);
+    rc = ensure(c, "lag_part", recon::gram_scratch_bytes(d, nb), &lp);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_gram(d, tw, (const float2*)x, (double2*)lp, nb, (double2*)lags_out,
+                               (double2*)G_out, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int recon_weight(recon_ctx* c, recon_dims dd, recon_filter f, const void* G_in, double eps_in,
+                 double p, void* S_out, void* dsum_out, void* evals_out, double* eps_out) {
+    if (!c) return RECON_EINVAL;
+    if (!G_in || !S_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (!std::isfinite(eps_in) || !(p >= 0.0 && p <= 1.0)) return fail(c, RECON_EINVAL, "bad eps or p");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    Work w;
+    rc = get_work(c, d, 1, 1, false, &w);
+    if (rc) return rc;
+    const size_t gbytes = (size_t)d.s() * d.s() * sizeof(double2);
+    RC_CUDA(cudaMemcpyAsync(w.G, G_in, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+    const bool set = eps_in >= 0.0;
+    rc = weight_step(c, d, tw, w, p, 1, set ? 0.0 : -eps_in, 1.0, set, eps_in, (float2*)S_out, w.info);
+    if (rc) return rc;
+    if (dsum_out)
+        RC_CUDA(cudaMemcpyAsync(dsum_out, w.dsum, (size_t)d.npair() * d.L1() * d.L2() * sizeof(double2),
+                                cudaMemcpyDeviceToDevice, c->stream));
+    if (evals_out)
+        RC_CUDA(cudaMemcpyAsync(evals_out, w.evals, (size_t)d.s() * sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    int info = 0;
+    RC_CUDA(cudaMemcpy(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost));
+    if (info != 0) return fail(c, RECON_ENUMERIC, "eigensolver failed (info != 0)");
+    if (eps_out) RC_CUDA(cudaMemcpy(eps_out, w.eps, sizeof(double), cudaMemcpyDeviceToHost));
+    return RECON_OK;
+}
+
+int recon_apply_normal(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks,
+                       const void* S, double lambda, const void* x, void* y) {
+    if (!c) return RECON_EINVAL;
+    if (!masks || !S || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    void *pp, *part;
+    rc = ensure(c, "p", d.elems() * sizeof(float2), &pp);
+    if (rc) return rc;
+    rc = ensure(c, "part_pq", (size_t)d.P * sizeof(double), &part);
+    if (rc) return rc;
+    // pass A with first = 1 copies x into p and row-transforms it into y; passes B and C follow.
+    RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y, nullptr,
+                                          nullptr, 0, 1, c->stream));
+    RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
+    RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
+                                    (float)lambda, (double*)part, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int recon_apply_w(recon_ctx* c, recon_dims dd, recon_filter f, const void* S, const void* x,
+                  void* y) {
+    if (!c) return RECON_EINVAL;
+    if (!S || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_apply_w(d, (const float2*)x, (const float2*)S, (float2*)y, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, const void* S_old,
+             const void* S_new, double lambda, void* x, void* r, int n_cg, double* rr_hist) {
+    if (!c) return RECON_EINVAL;
+    if (!masks || !S_new || !x || !r) return fail(c, RECON_EINVAL, "null pointer");
+    if (n_cg < 0) return fail(c, RECON_EINVAL, "n_cg must be >= 0");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    Work w;
+    rc = get_work(c, d, n_cg, 1, true, &w);
+    if (rc) return rc;
+    // the caller's r is the residual buffer for this call
+    float2* r_save = w.r;
+    w.r = (float2*)r;
+    rc = cg_block(c, d, tw, w, masks, (const float2*)S_old, (const float2*)S_new, (float)lambda,
+                  (float2*)x, S_old == nullptr, n_cg);
+    w.r = r_save;
+    if (rc) return rc;
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    if (rr_hist) {
+        const int nv = recon::vec_parts();
+        std::vector<double> hist(3 * (size_t)(n_cg + 1));
+        if (n_cg > 0)
+            RC_CUDA(cudaMemcpy(hist.data(), w.hist, 3 * (size_t)n_cg * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n_cg; ++i) rr_hist[i] = hist[3 * i];
+        std::vector<double> part(nv);
+        RC_CUDA(cudaMemcpy(part.data(), w.part_rr + (n_cg & 1) * nv, nv * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+        double rr = 0.0;
+        for (double v : part) rr += v;
+        rr_hist[n_cg] = rr;
+    }
+    return RECON_OK;
+}
+
+int recon_profile(recon_ctx* c, int enable) {
+    if (!c) return RECON_EINVAL;
+    prof_collect(c);
+    for (int k = 0; k < RECON_PROF_KINDS; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+    }
+    c->prof = enable != 0;
+    return RECON_OK;
+}
+
+int recon_profile_read(recon_ctx* c, int kind, double* total_ms, long long* launches) {
+    if (!c) return RECON_EINVAL;
+    if (kind < 0 || kind >= RECON_PROF_KINDS || !total_ms || !launches)
+        return fail(c, RECON_EINVAL, "bad profile kind or null pointer");
+    prof_collect(c);
+    *total_ms = c->prof_ms[kind];
+    *launches = c->prof_n[kind];
+    return RECON_OK;
+}
+
+const char* recon_profile_name(int kind) {
+    static const char* names[RECON_PROF_KINDS] = {
+        "adjoint", "gram", "eig", "eps", "diag_sums", "weight_S", "resid_carry",
+        "cg_row_fwd", "cg_col_mask", "cg_row_inv_w", "cg_update"};
+    return (kind >= 0 && kind < RECON_PROF_KINDS) ? names[kind] : "";
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Weight update after the FP64 eigendecomposition G = U diag(lambda) U^H (Sec. III-B; epsilon
+// schedule of Sec. III-C):
+//   H = U diag((lambda_i + eps)^(p/2 - 1)) U^H                                 (Eq. weight-update)
+//   d_ab[delta] = sum_{l - l' = delta} H[(l', b), (l, a)]                        (summed diagonals)
+//   S_ab(r) = sum_delta d_ab[delta] e^{-2 pi i (delta1 r1 / P + delta2 r2 / Q)}    (per-pixel S)
+// d is formed straight from the eigenvectors, V = U diag(sqrt f):
+//   d_ab[delta] = sum_i sum_{l'} V[(l', b), i] conj(V[(l' + delta, a), i]),
+// in FP64, in chunks of eigenvectors (one CTA per chunk and pair), then reduced in a fixed
+// order. S is a pruned 2-D DFT evaluated separably: FP64 along Q, FP32 along P.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace recon {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 2;  // eigenvectors per CTA
+
+__global__ void eps_kernel(const double* __restrict__ evals, int s, double* eps, int first,
+                           double frac, double gamma) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (first) eps[0] = frac * evals[s - 1];
+        else eps[0] = eps[0] / gamma;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+diag_part_kernel(const double2* __restrict__ U, const double* __restrict__ evals,
+                 const double* __restrict__ eps_p, double p, int N1, int N2, int M,
+                 double2* __restrict__ dpart) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double2* V = reinterpret_cast<double2*>(smraw);  // [kChunk][s]
+    const int s = N1 * N2 * M;
+    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1;
+    const int i0 = blockIdx.x * kChunk;
+    const int nc = min(kChunk, s - i0);
+    const int pr = blockIdx.y;
+    int a = 0, e = pr;
+    while (e >= M - a) { e -= M - a; ++a; }
+    const int b = a + e;
+    const double eps = eps_p[0];
+    for (int t = threadIdx.x; t < nc * s; t += blockDim.x) {
+        const int c = t / s, row = t % s;
+        const double lam = evals[i0 + c] + eps;
+        // sqrt((lambda + eps)^(p/2 - 1)) = (lambda + eps)^(p/4 - 1/2)
+        const double sf = (p == 0.0) ? 1.0 / sqrt(lam) : pow(lam, 0.25 * p - 0.5);
+        const double2 u = U[(size_t)(i0 + c) * s + row];
+        V[t] = make_double2(u.x * sf, u.y * sf);
+    }
+    __syncthreads();
+    const int nlag = L1 * L2;
+    double2* out = dpart + ((size_t)blockIdx.x * gridDim.y + pr) * nlag;
+    for (int o = threadIdx.x; o < nlag; o += blockDim.x) {
+        const int d1 = o / L2 - (N1 - 1), d2 = o % L2 - (N2 - 1);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = 0; c < nc; ++c) {
+            const double2* v = V + (size_t)c * s;
+            for (int lp1 = max(0, -d1); lp1 < min(N1, N1 - d1); ++lp1)
+                for (int lp2 = max(0, -d2); lp2 < min(N2, N2 - d2); ++lp2) {
+                    const double2 vb = v[((size_t)b * N1 + lp1) * N2 + lp2];
+                    const double2 va = v[((size_t)a * N1 + lp1 + d1) * N2 + lp2 + d2];
+                    acc = zfmacj2(vb, va, acc);
+                }
+        }
+        out[o] = acc;
+    }
+}
+
+__global__ void diag_reduce_kernel(const double2* __restrict__ dpart, int nchunks, int nout,
+                                   double2* __restrict__ dsum) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nout) return;
+    double2 v = make_double2(0.0, 0.0);
+    for (int c = 0; c < nchunks; ++c) v = zadd(v, dpart[(size_t)c * nout + o]);
+    dsum[o] = v;
+}
+
+// Z[pair][i1][r2] = sum_{d2} d[pair][i1][d2] w_Q^{d2 r2}  (FP64, rounded to FP32 on store)
+__global__ void __launch_bounds__(kThreads)
+s_stage1_kernel(const double2* __restrict__ dsum, int N1, int N2, int Q,
+                const double2* __restrict__ twQd, float2* __restrict__ Z) {
+    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1;
+    const int row = blockIdx.x;  // pair * L1 + i1
+    const double2* drow = dsum + (size_t)row * L2;
+    for (int r2 = threadIdx.x; r2 < Q; r2 += blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int i2 = 0; i2 < L2; ++i2) {
+            const int d2 = i2 - (N2 - 1);
+            const int ti = (int)((((long long)d2 % Q + Q) % Q * r2) % Q);
+            acc = zfma(drow[i2], twQd[ti], acc);
+        }
+        Z[(size_t)row * Q + r2] = make_float2((float)acc.x, (float)acc.y);
+    }
+}
+
+// S[pair][r1][r2] = sum_{d1} Z[pair][d1][r2] w_P^{d1 r1}  (FP32)
+__global__ void __launch_bounds__(kThreads)
+s_stage2_kernel(const float2* __restrict__ Z, int N1, int P, int Q,
+                const float2* __restrict__ twP, float2* __restrict__ S) {
+    const int L1 = 2 * N1 - 1;
+    const int r1 = blockIdx.x, pr = blockIdx.y;
+    const float2* zp = Z + (size_t)pr * L1 * Q;
+    for (int r2 = threadIdx.x; r2 < Q; r2 += blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i1 = 0; i1 < L1; ++i1) {
+            const int d1 = i1 - (N1 - 1);
+            const int ti = (int)((((long long)d1 % P + P) % P * r1) % P);
+            acc = cfma(zp[(size_t)i1 * Q + r2], twP[ti], acc);
+        }
+        S[((size_t)pr * P + r1) * Q + r2] = acc;
+    }
+}
+
+int nchunks(const Dims& d) { return (d.s() + kChunk - 1) / kChunk; }
+
+}  // namespace
+
+cudaError_t launch_eps(const double* evals, int s, double* eps, int first, double frac,
+                       double gamma, cudaStream_t st) {
+    eps_kernel<<<1, 32, 0, st>>>(evals, s, eps, first, frac, gamma);
+    return cudaGetLastError();
+}
+
+size_t diag_scratch_bytes(const Dims& d) {
+    return (size_t)nchunks(d) * d.npair() * d.L1() * d.L2() * sizeof(double2);
+}
+
+cudaError_t launch_diag_sums(const Dims& d, const double2* U, const double* evals,
+                             const double* eps, double p, double2* dpart, double2* dsum,
+                             cudaStream_t st) {
+    const size_t smem = (size_t)kChunk * d.s() * sizeof(double2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(diag_part_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(nchunks(d), d.npair());
+    diag_part_kernel<<<grid, kThreads, smem, st>>>(U, evals, eps, p, d.N1, d.N2, d.M, dpart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nout = d.npair() * d.L1() * d.L2();
+    diag_reduce_kernel<<<(nout + 127) / 128, 128, 0, st>>>(dpart, nchunks(d), nout, dsum);
+    return cudaGetLastError();
+}
+
+size_t s_scratch_bytes(const Dims& d) {
+    return (size_t)d.npair() * d.L1() * d.Q * sizeof(float2);
+}
+
+cudaError_t launch_weight_S(const Dims& d, const Twiddles& tw, const double2* dsum, double2* Z_,
+                            float2* S, cudaStream_t st) {
+    float2* Z = reinterpret_cast<float2*>(Z_);
+    s_stage1_kernel<<<d.npair() * d.L1(), kThreads, 0, st>>>(dsum, d.N1, d.N2, d.Q, tw.twQd, Z);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid(d.P, d.npair());
+    s_stage2_kernel<<<grid, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, tw.twP, S);
+    return cudaGetLastError();
+}
+
+}  // namespace recon

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of include/recon.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and forwards device pointers of
+torch CUDA tensors; all arithmetic runs in librecon.so. Importing this module does not touch the
+GPU; the first call that needs the library loads it and raises if it was not built
+(`python -m paper_1704_04511_gb300.build`) -- there is no fallback path.
+
+Tensor conventions: image series / k-space are torch.complex64 tensors of shape (T, P, Q)
+(bfloat16 k-space: shape (T, P, Q, 2)); masks are torch.uint8 (T, P, Q); the Gram matrix is
+torch.complex128 (s, s) stored column-major, i.e. the C array G[i + j*s] is tensor element
+[j, i] of a row-major (s, s) tensor (use .T to read it as G[i, j]); S is complex64
+(npair, P, Q); lags and summed diagonals are complex128 (npair, 2N1-1, 2N2-1).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "librecon.so")
+
+RECON_OK = 0
+RECON_EINVAL = -1
+RECON_ENOMEM = -2
+RECON_ECUDA = -3
+RECON_ENUMERIC = -4
+
+_ERR_NAMES = {RECON_EINVAL: "RECON_EINVAL", RECON_ENOMEM: "RECON_ENOMEM",
+              RECON_ECUDA: "RECON_ECUDA", RECON_ENUMERIC: "RECON_ENUMERIC"}
+
+EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_needed",
+            "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
+            "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
+            "recon_profile_read", "recon_profile_name")
+
+PROF_KINDS = 11
+
+
+class ReconError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class recon_dims(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int), ("Q", ctypes.c_int), ("T", ctypes.c_int)]
+
+
+class recon_filter(ctypes.Structure):
+    _fields_ = [("N1", ctypes.c_int), ("N2", ctypes.c_int), ("M", ctypes.c_int)]
+
+
+class recon_params(ctypes.Structure):
+    _fields_ = [("irls", ctypes.c_int), ("cg", ctypes.c_int), ("lambda_", ctypes.c_double),
+                ("p", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("eps0_frac", ctypes.c_double), ("kspace_bf16", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librecon.so (once) and declare the C signatures. Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with "
+                              "`python -m paper_1704_04511_gb300.build` (needs nvcc)")
+        lib = ctypes.CDLL(path)
+        vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        dims, filt = recon_dims, recon_filter
+        sig = {
+            "recon_create": (i, [ctypes.POINTER(vp), i, sz, vp]),
+            "recon_destroy": (None, [vp]),
+            "recon_last_error": (ctypes.c_char_p, [vp]),
+            "recon_bytes_needed": (sz, [dims, filt, i]),
+            "recon_solve": (i, [vp, dims, vp, vp, filt, ctypes.POINTER(recon_params), vp]),
+            "recon_adjoint": (i, [vp, dims, vp, i, vp, vp]),
+            "recon_fft2": (i, [vp, dims, vp, vp, i]),
+            "recon_gram": (i, [vp, dims, filt, vp, vp, vp]),
+            "recon_weight": (i, [vp, dims, filt, vp, d, d, vp, vp, vp, ctypes.POINTER(d)]),
+            "recon_apply_normal": (i, [vp, dims, filt, vp, vp, d, vp, vp]),
+            "recon_apply_w": (i, [vp, dims, filt, vp, vp, vp]),
+            "recon_cg": (i, [vp, dims, filt, vp, vp, vp, d, vp, vp, i, ctypes.POINTER(d)]),
+            "recon_profile": (i, [vp, i]),
+            "recon_profile_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
+            "recon_profile_name": (ctypes.c_char_p, [i]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(ctx, rc: int):
+    if rc != RECON_OK:
+        msg = load_library().recon_last_error(ctx).decode(errors="replace")
+        raise ReconError(rc, msg)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dims(x) -> recon_dims:
+    T, P, Q = x.shape[:3]
+    return recon_dims(P=int(P), Q=int(Q), T=int(T))
+
+
+def _filt(f) -> recon_filter:
+    N1, N2, M = f
+    return recon_filter(N1=int(N1), N2=int(N2), M=int(M))
+
+
+# ------------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ------------------------------------------------------------------------------------------
+
+def recon_create(device: int = 0, mem_budget_bytes: int = 0, cuda_stream: int | None = None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rc = lib.recon_create(ctypes.byref(h), int(device), int(mem_budget_bytes),
+                          ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+    if rc != RECON_OK:
+        raise ReconError(rc, lib.recon_last_error(None).decode(errors="replace"))
+    return h
+
+
+def recon_destroy(ctx) -> None:
+    if ctx:
+        load_library().recon_destroy(ctx)
+
+
+def recon_last_error(ctx) -> str:
+    return load_library().recon_last_error(ctx).decode(errors="replace")
+
+
+def recon_bytes_needed(shape, filt, kspace_bf16: bool = False) -> int:
+    T, P, Q = shape
+    return int(load_library().recon_bytes_needed(recon_dims(P=P, Q=Q, T=T), _filt(filt),
+                                                  int(kspace_bf16)))
+
+
+def recon_solve(ctx, kspace, masks, filt, lam: float, p: float, irls: int, cg: int,
+                image_out, gamma: float = 1.4, eps0_frac: float = 0.01) -> None:
+    import torch
+    bf16 = kspace.dtype == torch.bfloat16
+    prm = recon_params(irls=int(irls), cg=int(cg), lambda_=float(lam), p=float(p),
+                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=int(bf16))
+    _check(ctx, load_library().recon_solve(ctx, _dims(masks), _ptr(kspace), _ptr(masks),
+                                           _filt(filt), ctypes.byref(prm), _ptr(image_out)))
+
+
+def recon_adjoint(ctx, kspace, masks, x_out) -> None:
+    import torch
+    bf16 = kspace.dtype == torch.bfloat16
+    _check(ctx, load_library().recon_adjoint(ctx, _dims(masks), _ptr(kspace), int(bf16),
+                                             _ptr(masks), _ptr(x_out)))
+
+
+def recon_fft2(ctx, x, y, inverse: bool = False) -> None:
+    _check(ctx, load_library().recon_fft2(ctx, _dims(x), _ptr(x), _ptr(y), int(inverse)))
+
+
+def recon_gram(ctx, x, filt, G_out, lags_out=None) -> None:
+    _check(ctx, load_library().recon_gram(ctx, _dims(x), _filt(filt), _ptr(x), _ptr(G_out),
+                                          _ptr(lags_out)))
+
+
+def recon_weight(ctx, shape, filt, G_in, eps_in: float, p: float, S_out, dsum_out=None,
+                 evals_out=None) -> float:
+    T, P, Q = shape
+    eps_used = ctypes.c_double(0.0)
+    _check(ctx, load_library().recon_weight(ctx, recon_dims(P=P, Q=Q, T=T), _filt(filt),
+                                            _ptr(G_in), float(eps_in), float(p), _ptr(S_out),
+                                            _ptr(dsum_out), _ptr(evals_out),
+                                            ctypes.byref(eps_used)))
+    return eps_used.value
+
+
+def recon_apply_normal(ctx, masks, filt, S, lam: float, x, y) -> None:
+    _check(ctx, load_library().recon_apply_normal(ctx, _dims(x), _filt(filt), _ptr(masks), _ptr(S),
+                                                  float(lam), _ptr(x), _ptr(y)))
+
+
+def recon_apply_w(ctx, filt, S, x, y) -> None:
+    _check(ctx, load_library().recon_apply_w(ctx, _dims(x), _filt(filt), _ptr(S), _ptr(x), _ptr(y)))
+
+
+def recon_cg(ctx, masks, filt, S_old, S_new, lam: float, x, r, n_cg: int):
+    hist = (ctypes.c_double * (n_cg + 1))()
+    _check(ctx, load_library().recon_cg(ctx, _dims(x), _filt(filt), _ptr(masks), _ptr(S_old),
+                                        _ptr(S_new), float(lam), _ptr(x), _ptr(r), int(n_cg), hist))
+    return list(hist)
+
+
+def recon_profile(ctx, enable: bool) -> None:
+    _check(ctx, load_library().recon_profile(ctx, int(enable)))
+
+
+def recon_profile_read(ctx, kind: int):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _check(ctx, load_library().recon_profile_read(ctx, int(kind), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def recon_profile_name(kind: int) -> str:
+    return load_library().recon_profile_name(int(kind)).decode()
+
+
+# ------------------------------------------------------------------------------------------
+# convenience wrapper
+# ------------------------------------------------------------------------------------------
+
+class Context:
+    """Owns one recon context (device workspace, eigensolver handle, stream)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, cuda_stream: int | None = None):
+        self.h = recon_create(device, mem_budget_bytes, cuda_stream)
+        self.device = device
+
+    def close(self):
+        if self.h:
+            recon_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, kspace, masks, filt, lam, p, irls, cg, gamma=1.4, eps0_frac=0.01, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(tuple(masks.shape), dtype=torch.complex64, device=masks.device)
+        recon_solve(self.h, kspace, masks, filt, lam, p, irls, cg, out, gamma, eps0_frac)
+        return out

@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle on seeded inputs.
+
+Tolerances (relative Frobenius unless stated):
+  FFT / adjoint      2e-6   FP32 radix-8/4/2 Stockham: ~log2(N) * 6e-8 per transform
+  Gram G, lags       1e-5   stated target for the Gram matrix (FP32 products, FP64 sums)
+  summed diagonals   1e-8   FP64 eigensolver on the same FP64 G (condition ~1e3-1e4 here)
+  S(r)               2e-6   FP64 lags, last DFT stage in FP32
+  normal operator    1e-5   FP32 FFTs and banded weight
+  one CG block       1e-5   FP32 CG vs FP64 CG, 10 steps from the same start
+  full IRLS          1e-4   stated target for the final image (the oracle run through FP32
+                            rounding alone moves it ~4e-6 with the carried residual);
+                            T2 map 0.5 % (stated target)
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import slr, t2fit
+
+from gpu_util import c64, crandn, lags_pairs, pairs_from_full, rel, to_dev
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_04511_gb300 import recon
+    ctx = recon.Context(0)
+    yield recon, ctx
+    ctx.close()
+
+
+def _problem(name, **kw):
+    w = synth.workload(name, **kw)
+    return w, synth.make_problem(w)
+
+
+@pytest.mark.parametrize("T,P,Q", [(3, 16, 32), (2, 64, 64), (5, 32, 16), (2, 192, 256),
+                                   (4, 256, 256), (1, 512, 128)])
+def test_fft2_parity(R, T, P, Q):
+    recon, ctx = R
+    rng = np.random.default_rng(T * 1000 + P + Q)
+    x = c64(crandn(rng, T, P, Q))
+    xd = to_dev(x)
+    y = torch.empty_like(xd)
+    recon.recon_fft2(ctx.h, xd, y, inverse=False)
+    assert rel(y.cpu().numpy(), slr.F2(x.astype(np.complex128))) < 2e-6
+    recon.recon_fft2(ctx.h, xd, y, inverse=True)
+    assert rel(y.cpu().numpy(), slr.F2H(x.astype(np.complex128))) < 2e-6
+    # in place
+    z = xd.clone()
+    recon.recon_fft2(ctx.h, z, z, inverse=False)
+    assert rel(z.cpu().numpy(), slr.F2(x.astype(np.complex128))) < 2e-6
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_adjoint_parity(R, bf16):
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8")
+    b = c64(prob["kspace"])
+    masks = prob["masks"]
+    if bf16:
+        bt = torch.view_as_real(torch.from_numpy(b)).to(torch.bfloat16).contiguous()
+        b_ref = torch.view_as_complex(bt.float()).numpy().astype(np.complex128)
+        bd = bt.cuda()
+    else:
+        b_ref = b.astype(np.complex128)
+        bd = to_dev(b)
+    x = torch.empty(masks.shape, dtype=torch.complex64, device="cuda")
+    recon.recon_adjoint(ctx.h, bd, to_dev(masks), x)
+    assert rel(x.cpu().numpy(), slr.AH(b_ref, masks)) < 2e-6
+
+
+GRAM_CASES = [
+    ("tiny", 8, 32, 32, 5, 5, 2),
+    ("odd", 7, 16, 64, 3, 4, 3),
+    ("wide-filter", 4, 16, 16, 16, 3, 1),   # N1 = P: lags alias on the circular grid
+    ("tikhonov", 6, 32, 16, 1, 1, 1),
+    ("M=T", 3, 16, 32, 2, 2, 3),
+    ("perf", 16, 256, 256, 9, 9, 3),
+]
+
+
+@pytest.mark.parametrize("case", GRAM_CASES, ids=[c[0] for c in GRAM_CASES])
+def test_gram_parity(R, case):
+    recon, ctx = R
+    _, T, P, Q, N1, N2, M = case
+    rng = np.random.default_rng(P * Q + T)
+    x = c64(crandn(rng, T, P, Q))
+    s = N1 * N2 * M
+    npair = M * (M + 1) // 2
+    G = torch.empty((s, s), dtype=torch.complex128, device="cuda")
+    lags = torch.empty((npair, 2 * N1 - 1, 2 * N2 - 1), dtype=torch.complex128, device="cuda")
+    recon.recon_gram(ctx.h, to_dev(x), (N1, N2, M), G, lags)
+    xr = x.astype(np.complex128)
+    G_ref = slr.gram_fft(xr, N1, N2, M)
+    G_gpu = G.cpu().numpy().T              # column-major storage
+    assert rel(G_gpu, G_ref) < 1e-5
+    assert rel(lags.cpu().numpy(), lags_pairs(slr.gram_lags(xr, N1, N2, M))) < 1e-5
+
+
+def test_gram_matches_brute_force_lifting(R):
+    """GPU Gram against T^H T of the explicit lifting (independent of the oracle's FFT Gram)."""
+    recon, ctx = R
+    rng = np.random.default_rng(3)
+    T, P, Q, N1, N2, M = 5, 16, 16, 3, 3, 2
+    x = c64(crandn(rng, T, P, Q))
+    s = N1 * N2 * M
+    G = torch.empty((s, s), dtype=torch.complex128, device="cuda")
+    recon.recon_gram(ctx.h, to_dev(x), (N1, N2, M), G, None)
+    assert rel(G.cpu().numpy().T, slr.gram_brute(x.astype(np.complex128), N1, N2, M)) < 1e-5
+
+
+WEIGHT_CASES = [("tiny-p0", 8, 32, 32, 5, 5, 2, 0.0), ("p0.7", 6, 16, 32, 3, 4, 3, 0.7),
+                ("perf-p0", 16, 256, 256, 9, 9, 3, 0.0), ("M1", 4, 16, 16, 4, 4, 1, 0.5)]
+
+
+@pytest.mark.parametrize("case", WEIGHT_CASES, ids=[c[0] for c in WEIGHT_CASES])
+def test_weight_parity(R, case):
+    recon, ctx = R
+    _, T, P, Q, N1, N2, M, p = case
+    rng = np.random.default_rng(11 + P + M)
+    x = crandn(rng, T, P, Q)
+    G = slr.gram_fft(x, N1, N2, M)
+    s = N1 * N2 * M
+    npair = M * (M + 1) // 2
+    Gd = to_dev(np.ascontiguousarray(G.T))   # column-major
+    S = torch.empty((npair, P, Q), dtype=torch.complex64, device="cuda")
+    dsum = torch.empty((npair, 2 * N1 - 1, 2 * N2 - 1), dtype=torch.complex128, device="cuda")
+    ev = torch.empty((s,), dtype=torch.float64, device="cuda")
+    eps = recon.recon_weight(ctx.h, (T, P, Q), (N1, N2, M), Gd, -0.01, p, S, dsum, ev)
+    lam = np.linalg.eigvalsh(G)
+    assert abs(eps - 0.01 * lam[-1]) <= 1e-12 * lam[-1]
+    assert np.allclose(ev.cpu().numpy(), lam, rtol=0, atol=1e-11 * lam[-1])
+    H, _ = slr.weight_H(G, eps, p)
+    d_ref = slr.diag_sums(H, N1, N2, M)
+    assert rel(dsum.cpu().numpy(), lags_pairs(d_ref)) < 1e-8
+    S_ref = pairs_from_full(slr.weight_S(d_ref, P, Q))
+    assert rel(S.cpu().numpy(), S_ref) < 2e-6
+    # explicit eps
+    eps2 = recon.recon_weight(ctx.h, (T, P, Q), (N1, N2, M), Gd, 0.5 * eps, p, S, dsum, None)
+    assert eps2 == 0.5 * eps
+    H2, _ = slr.weight_H(G, 0.5 * eps, p)
+    assert rel(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H2, N1, N2, M))) < 1e-8
+
+
+def _oracle_S(x, N1, N2, M, eps_frac=0.01, p=0.0):
+    G = slr.gram_fft(x, N1, N2, M)
+    eps = eps_frac * np.linalg.eigvalsh(G)[-1]
+    H, _ = slr.weight_H(G, eps, p)
+    return slr.weight_S(slr.diag_sums(H, N1, N2, M), x.shape[1], x.shape[2])
+
+
+OP_CASES = [("tiny", "tiny_32x32x8", {}), ("perf", "perf_256x256x16", {})]
+
+
+@pytest.mark.parametrize("case", OP_CASES, ids=[c[0] for c in OP_CASES])
+def test_normal_operator_parity(R, case):
+    recon, ctx = R
+    _, name, kw = case
+    w, prob = _problem(name, **kw)
+    masks = prob["masks"]
+    x0 = slr.AH(prob["kspace"], masks)
+    S_full = _oracle_S(x0, w.N1, w.N2, w.M).astype(np.complex64).astype(np.complex128)
+    rng = np.random.default_rng(7)
+    v = c64(crandn(rng, *masks.shape))
+    vr = v.astype(np.complex128)
+    Sd = to_dev(c64(pairs_from_full(S_full)))
+    md = to_dev(masks)
+    y = torch.empty_like(to_dev(v))
+    lam = 10.0 * w.lam
+    recon.recon_apply_normal(ctx.h, md, (w.N1, w.N2, w.M), Sd, lam, to_dev(v), y)
+    assert rel(y.cpu().numpy(), slr.normal_op(vr, masks, S_full, lam)) < 1e-5
+    recon.recon_apply_w(ctx.h, (w.N1, w.N2, w.M), Sd, to_dev(v), y)
+    assert rel(y.cpu().numpy(), slr.apply_W(vr, S_full)) < 1e-5
+
+
+def _oracle_cg_block(x, r, masks, S_old, S_new, lam, n_cg):
+    """Residual carry + plain CG, FP64 (the formulation the library runs)."""
+    if S_old is None:
+        r = -lam * slr.apply_W(x, S_new)
+    else:
+        r = r + lam * (slr.apply_W(x, S_old) - slr.apply_W(x, S_new))
+    p = r.copy()
+    rr = slr.vdot(r, r).real
+    hist = [rr]
+    for _ in range(n_cg):
+        q = slr.normal_op(p, masks, S_new, lam)
+        a = rr / slr.vdot(p, q).real
+        x = x + a * p
+        r = r - a * q
+        rn = slr.vdot(r, r).real
+        p = r + (rn / rr) * p
+        rr = rn
+        hist.append(rr)
+    return x, r, hist
+
+
+def test_cg_block_parity(R):
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8")
+    masks = prob["masks"]
+    x0 = c64(slr.AH(prob["kspace"], masks))
+    x0r = x0.astype(np.complex128)
+    S1 = _oracle_S(x0r, w.N1, w.N2, w.M).astype(np.complex64).astype(np.complex128)
+    xd = to_dev(x0)
+    rd = torch.zeros_like(xd)
+    Sd1 = to_dev(c64(pairs_from_full(S1)))
+    md = to_dev(masks)
+    hist = recon.recon_cg(ctx.h, md, (w.N1, w.N2, w.M), None, Sd1, w.lam, xd, rd, w.n_cg)
+    x_ref, r_ref, h_ref = _oracle_cg_block(x0r, None, masks, None, S1, w.lam, w.n_cg)
+    assert rel(xd.cpu().numpy(), x_ref) < 1e-5
+    assert np.allclose(hist, h_ref, rtol=1e-3)
+    # second block: residual carried with a new weight
+    x1 = xd.cpu().numpy().astype(np.complex128)
+    S2 = _oracle_S(x1, w.N1, w.N2, w.M, eps_frac=0.01 / 1.4).astype(np.complex64).astype(np.complex128)
+    Sd2 = to_dev(c64(pairs_from_full(S2)))
+    r1 = rd.cpu().numpy().astype(np.complex128)
+    recon.recon_cg(ctx.h, md, (w.N1, w.N2, w.M), Sd1, Sd2, w.lam, xd, rd, w.n_cg)
+    x_ref2, _, _ = _oracle_cg_block(x1, r1, masks, S1, S2, w.lam, w.n_cg)
+    assert rel(xd.cpu().numpy(), x_ref2) < 1e-5
+
+
+def _solve_gpu(recon, ctx, w, prob, irls=None, cg=None):
+    out = torch.empty(prob["masks"].shape, dtype=torch.complex64, device="cuda")
+    recon.recon_solve(ctx.h, to_dev(c64(prob["kspace"])), to_dev(prob["masks"]),
+                      (w.N1, w.N2, w.M), w.lam, w.p, w.n_irls if irls is None else irls,
+                      w.n_cg if cg is None else cg, out)
+    return out.cpu().numpy()
+
+
+def _check_solve(x_gpu, x_ref, prob, w):
+    xt = prob["x_true"]
+    assert rel(x_gpu, x_ref) < 1e-4
+    nrmse_gpu = np.linalg.norm(x_gpu - xt) / np.linalg.norm(xt)
+    nrmse_ref = np.linalg.norm(x_ref - xt) / np.linalg.norm(xt)
+    assert abs(nrmse_gpu - nrmse_ref) < 1e-4
+    fg = t2fit.foreground(prob["x_true"])
+    t2_ref = t2fit.fit_t2(x_ref, w.times_ms, fg)
+    t2_gpu = t2fit.fit_t2(x_gpu, w.times_ms, fg)
+    assert t2fit.t2_rel_l2(t2_ref, t2_gpu) < 5e-3
+
+
+def test_solve_parity_tiny(R):
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8")
+    x_gpu = _solve_gpu(recon, ctx, w, prob)
+    x_ref = slr.irls(prob["kspace"].astype(np.complex64).astype(np.complex128), prob["masks"],
+                     w.N1, w.N2, w.M, w.lam, w.p, w.n_irls, w.n_cg)
+    _check_solve(x_gpu, x_ref, prob, w)
+
+
+def test_solve_parity_tiny_p07(R):
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8", p=0.7, n_irls=8)
+    x_gpu = _solve_gpu(recon, ctx, w, prob)
+    x_ref = slr.irls(prob["kspace"].astype(np.complex64).astype(np.complex128), prob["masks"],
+                     w.N1, w.N2, w.M, w.lam, w.p, w.n_irls, w.n_cg)
+    _check_solve(x_gpu, x_ref, prob, w)
+
+
+def test_solve_irls0_is_adjoint(R):
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8")
+    x_gpu = _solve_gpu(recon, ctx, w, prob, irls=0)
+    assert rel(x_gpu, slr.AH(prob["kspace"], prob["masks"])) < 2e-6
+
+
+def test_solve_deterministic(R):
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8", n_irls=4)
+    a = _solve_gpu(recon, ctx, w, prob)
+    b = _solve_gpu(recon, ctx, w, prob)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.slow
+def test_solve_parity_perf(R):
+    """256x256x16, 9x9x3 filter, 30 IRLS x 15 CG: the workload the benchmark times."""
+    recon, ctx = R
+    w, prob = _problem("perf_256x256x16")
+    x_gpu = _solve_gpu(recon, ctx, w, prob)
+    x_ref = slr.irls(prob["kspace"].astype(np.complex64).astype(np.complex128), prob["masks"],
+                     w.N1, w.N2, w.M, w.lam, w.p, w.n_irls, w.n_cg)
+    _check_solve(x_gpu, x_ref, prob, w)
+
+
+def test_errors(R):
+    recon, ctx = R
+    x = torch.zeros((2, 24, 32), dtype=torch.complex64, device="cuda")
+    with pytest.raises(recon.ReconError) as e:
+        recon.recon_fft2(ctx.h, x, x)
+    assert e.value.code == recon.RECON_EINVAL
+    x = torch.zeros((2, 16, 16), dtype=torch.complex64, device="cuda")
+    G = torch.zeros((8, 8), dtype=torch.complex128, device="cuda")
+    with pytest.raises(recon.ReconError) as e:
+        recon.recon_gram(ctx.h, x, (2, 2, 3), G)          # M > T
+    assert e.value.code == recon.RECON_EINVAL
+    with pytest.raises(recon.ReconError):
+        recon.recon_gram(ctx.h, x, (17, 1, 1), G)         # N1 > P
+    m = torch.ones((2, 16, 16), dtype=torch.uint8, device="cuda")
+    with pytest.raises(recon.ReconError):
+        recon.recon_solve(ctx.h, x, m, (2, 2, 1), -1.0, 0.0, 1, 1, x.clone())   # lambda <= 0
+    small = recon.Context(0, mem_budget_bytes=1024)
+    try:
+        with pytest.raises(recon.ReconError) as e:
+            recon.recon_solve(small.h, x, m, (2, 2, 1), 1e-3, 0.0, 1, 1, x.clone())
+        assert e.value.code == recon.RECON_ENOMEM
+    finally:
+        small.close()
