@@ -42,6 +42,14 @@ extern "C" {
 #define RECON_ENOMEM (-2)   /* request exceeds the context budget or allocation failed  */
 #define RECON_ECUDA (-3)    /* CUDA runtime or library error                            */
 #define RECON_ENUMERIC (-4) /* NaN / Inf in the iteration, or eigensolver failure       */
+#define RECON_ETIMEOUT (-5) /* a bounded device-wide wait (grid barrier) gave up         */
+
+/* How the weight H = (G + eps I)^(p/2-1) is formed (recon_params.weight_method):
+ * RECON_WEIGHT_AUTO: p = 0 -> FP64 Hermitian sweep inverse (G + eps I)^-1 and a Lanczos
+ *                    lambda_max for eps0; p > 0 -> FP64 eigendecomposition.
+ * RECON_WEIGHT_EIG:  always the FP64 eigendecomposition (cuSOLVER zheevd). */
+#define RECON_WEIGHT_AUTO 0
+#define RECON_WEIGHT_EIG 1
 
 typedef struct recon_ctx recon_ctx;
 
@@ -61,6 +69,7 @@ typedef struct {
     double gamma;     /* eps decay factor, > 1 (Sec. III-C uses 1.4)               */
     double eps0_frac; /* eps0 = eps0_frac * lambda_max(G(x0)) (Sec. III-C uses 0.01) */
     int kspace_bf16;  /* 1: kspace holds bfloat16 (re, im) pairs; 0: complex64      */
+    int weight_method; /* RECON_WEIGHT_AUTO or RECON_WEIGHT_EIG                      */
 } recon_params;
 
 /* Create a context on `device`. It owns device workspace (grown on demand, never beyond
@@ -103,16 +112,20 @@ int recon_fft2(recon_ctx* c, recon_dims d, const void* x, void* y, int inverse);
 int recon_gram(recon_ctx* c, recon_dims d, recon_filter f, const void* x, void* G_out,
                void* lags_out);
 
-/* Weight step (Sec. III-B, Eq. weight-update): eigendecomposition of G_in (s x s complex128,
- * column-major, Hermitian; not modified) in FP64, H = U diag((lambda+eps)^(p/2-1)) U^H, summed
- * diagonals d_ab[delta] = sum_{l-l'=delta} H[(l',b),(l,a)] and the per-pixel weight
- * S_ab(r) = sum_delta d_ab[delta] e^{-2 pi i (delta.r)}.
+/* Weight step (Sec. III-B, Eq. weight-update) on G_in (s x s complex128, column-major,
+ * Hermitian positive semi-definite; not modified), all in FP64:
+ * H = (G + eps I)^(p/2-1) -- by the eigendecomposition H = U diag((lambda+eps)^(p/2-1)) U^H, or
+ * for p = 0 with method RECON_WEIGHT_AUTO by the Hermitian sweep inverse (G + eps I)^-1 --,
+ * then the summed diagonals d_ab[delta] = sum_{l-l'=delta} H[(l',b),(l,a)] and the per-pixel
+ * weight S_ab(r) = sum_delta d_ab[delta] e^{-2 pi i (delta.r)}.
  * eps: if eps_in >= 0 it is used; else eps = -eps_in * lambda_max(G) (so -0.01 gives the
  * Sec. III-C initial value). S_out: npair x P x Q complex64 (pair layout as above);
- * dsum_out (may be NULL): npair x (2N1-1) x (2N2-1) complex128; evals_out (may be NULL): s
- * doubles ascending; eps_out (host pointer, may be NULL) receives the eps used. */
+ * dsum_out (may be NULL): npair x (2N1-1) x (2N2-1) complex128; evals_out (may be NULL; only
+ * with the eigendecomposition): s doubles ascending; eps_out (host pointer, may be NULL)
+ * receives the eps used. */
 int recon_weight(recon_ctx* c, recon_dims d, recon_filter f, const void* G_in, double eps_in,
-                 double p, void* S_out, void* dsum_out, void* evals_out, double* eps_out);
+                 double p, int method, void* S_out, void* dsum_out, void* evals_out,
+                 double* eps_out);
 
 /* y = (A^H A + lambda W_S) x with W_S the per-pixel banded frame operator of Eq. grad-ls:
  * (W x)_n(r) = sum_{a: 0 <= n-M+1+a < k} sum_b S_ab(r) x_{n+a-b}(r). S as from recon_weight.
@@ -147,7 +160,9 @@ int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
 #define RECON_PROF_CG_COL 8       /* CG pass B: column FFT, mask, column IFFT             */
 #define RECON_PROF_CG_ROWINVW 9   /* CG pass C: row IFFT + lambda W p + <p, q> partials    */
 #define RECON_PROF_CG_UPDATE 10   /* CG pass D: x, r update + |r|^2 partials               */
-#define RECON_PROF_KINDS 11
+#define RECON_PROF_LANCZOS 11     /* lambda_max of G for eps0 (p = 0 path)                 */
+#define RECON_PROF_INV 12         /* FP64 sweep inverse (G + eps I)^-1 (p = 0 path)        */
+#define RECON_PROF_KINDS 13
 
 /* Enable (1) or disable (0) per-launch event timing on this context; resets the totals. */
 int recon_profile(recon_ctx* c, int enable);

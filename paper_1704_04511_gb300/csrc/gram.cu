@@ -90,30 +90,37 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N1, int 
     for (int i = threadIdx.x; i < nlag; i += blockDim.x) out[i] = acc[i];
 }
 
+// One warp per lag: lanes add the per-block partials (fixed order, then a fixed shuffle tree)
+// and scatter the lag over the (l, l') pairs it fills in G.
 __global__ void gram_fill_kernel(const double2* __restrict__ lag_part, int nblocks, int N1,
                                  int N2, int M, double2* __restrict__ lags,
                                  double2* __restrict__ G) {
     const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1, npair = M * (M + 1) / 2;
     const int nlag = npair * L1 * L2;
     const int s = N1 * N2 * M;
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (o >= nlag) return;
     double2 v = make_double2(0.0, 0.0);
-    for (int bI = 0; bI < nblocks; ++bI) v = zadd(v, lag_part[(size_t)bI * nlag + o]);
-    if (lags) lags[o] = v;
+    for (int bI = lane; bI < nblocks; bI += 32) v = zadd(v, lag_part[(size_t)bI * nlag + o]);
+    v.x = warp_sum(v.x);
+    v.y = warp_sum(v.y);
+    if (lags && lane == 0) lags[o] = v;
     const int pr = o / (L1 * L2), rem = o % (L1 * L2);
     const int d1 = rem / L2 - (N1 - 1), d2 = rem % L2 - (N2 - 1);
     int a = 0, e = pr;
     while (e >= M - a) { e -= M - a; ++a; }
     const int b = a + e;
-    for (int lp1 = max(0, -d1); lp1 < min(N1, N1 - d1); ++lp1)
-        for (int lp2 = max(0, -d2); lp2 < min(N2, N2 - d2); ++lp2) {
-            const int l1 = lp1 + d1, l2 = lp2 + d2;
-            const size_t i = ((size_t)a * N1 + l1) * N2 + l2;
-            const size_t j = ((size_t)b * N1 + lp1) * N2 + lp2;
-            G[i + j * s] = v;
-            if (a != b) G[j + i * s] = zconj(v);
-        }
+    const int lo1 = max(0, -d1), hi1 = min(N1, N1 - d1);
+    const int lo2 = max(0, -d2), hi2 = min(N2, N2 - d2);
+    const int n2 = hi2 - lo2, cnt = (hi1 - lo1) * n2;
+    for (int t = lane; t < cnt; t += 32) {
+        const int lp1 = lo1 + t / n2, lp2 = lo2 + t % n2;
+        const int l1 = lp1 + d1, l2 = lp2 + d2;
+        const size_t i = ((size_t)a * N1 + l1) * N2 + l2;
+        const size_t j = ((size_t)b * N1 + lp1) * N2 + lp2;
+        G[i + j * s] = v;
+        if (a != b) G[j + i * s] = zconj(v);
+    }
 }
 
 size_t gram_smem(const Dims& d) {
@@ -142,7 +149,7 @@ cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, doub
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nlag = d.npair() * d.L1() * d.L2();
-    gram_fill_kernel<<<(nlag + 127) / 128, 128, 0, st>>>(lag_part, nblocks, d.N1, d.N2, d.M, lags, G);
+    gram_fill_kernel<<<(nlag + 7) / 8, 256, 0, st>>>(lag_part, nblocks, d.N1, d.N2, d.M, lags, G);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,436 @@
+// FP64 weight for p = 0 without an eigendecomposition (Sec. III-B, Eq. weight-update):
+//   H = (G + eps I)^(p/2 - 1) = (G + eps I)^(-1)   when p = 0,
+// and eps0 = eps0_frac * lambda_max(G) (Sec. III-C) from a Lanczos iteration.
+//
+// The inverse is a blocked Hermitian sweep (Gauss-Jordan without pivoting, stable for Hermitian
+// positive-definite matrices) over 16 x 16 tiles, run as ONE cooperative kernel over every SM:
+//   per pivot block K:  D^-1 = (A_KK)^-1 (computed one step ahead by the CTA that owns A_KK),
+//                       W_KJ = D^-1 A_KJ,  C_IK = A_IK            (phase A, whole grid)
+//                       A_IJ -= C_IK W_KJ,  A_IK <- C_IK D^-1,  A_KJ <- W_KJ,  A_KK <- -D^-1
+//                                                                 (phase B, lower tiles only)
+// Sweeping every pivot leaves -A^{-1}; the Hermitian symmetry is kept at each step, so only the
+// lower tiles (and the full diagonal tiles) are updated. Grid barriers are bounded spin-waits:
+// on timeout the kernel records an error flag and returns.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace recon {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kB = 16;                       // tile edge
+constexpr long long kSpinLimit = 1LL << 22;  // ~0.4 s of polling before giving up
+
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int pad;
+};
+
+// Sense-free generation barrier over gridDim.x co-resident CTAs. Returns false (and sets
+// gb->err) if the wait exceeded kSpinLimit polls; after a failure every later call returns
+// false at once so the kernel can unwind.
+RECON_DEV bool grid_barrier(GridBar* gb) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = (atomicAdd(&gb->err, 0) == 0);
+        if (ok) {
+            const unsigned int g = atomicAdd(&gb->gen, 0);
+            __threadfence();
+            const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
+            if (arrived == gridDim.x) {
+                atomicExch(&gb->count, 0u);
+                __threadfence();
+                atomicAdd(&gb->gen, 1u);
+            } else {
+                long long it = 0;
+                while (atomicAdd(&gb->gen, 0) == g) {
+                    if (++it > kSpinLimit || atomicAdd(&gb->err, 0) != 0) {
+                        atomicExch(&gb->err, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// In-CTA inverse of a Hermitian positive-definite 16 x 16 tile held (full) in shared memory:
+// 16 scalar sweeps leave -T^{-1}; the result is negated into `out` (column-major 16 x 16).
+RECON_DEV void tile_inverse(double2* T, double2* out) {
+    const int i = threadIdx.x % kB, j = threadIdx.x / kB;  // 256 threads <-> 256 entries
+    for (int k = 0; k < kB; ++k) {
+        double2 tij = make_double2(0, 0), tik = make_double2(0, 0), tkj = make_double2(0, 0);
+        double akk = 1.0;
+        if (threadIdx.x < kB * kB) {
+            tij = T[i + j * kB];
+            tik = T[i + k * kB];
+            tkj = T[k + j * kB];
+            akk = T[k + k * kB].x;
+        }
+        __syncthreads();
+        if (threadIdx.x < kB * kB) {
+            const double inv = 1.0 / akk;
+            double2 v;
+            if (i == k && j == k) v = make_double2(-inv, 0.0);
+            else if (i == k) v = make_double2(tkj.x * inv, tkj.y * inv);
+            else if (j == k) v = make_double2(tik.x * inv, tik.y * inv);
+            else {
+                const double2 pr = zmul(tik, tkj);
+                v = make_double2(tij.x - pr.x * inv, tij.y - pr.y * inv);
+            }
+            T[i + j * kB] = v;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < kB * kB) {
+        const double2 v = T[i + j * kB];
+        out[i + j * kB] = make_double2(-v.x, -v.y);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads)
+hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int np,
+                 double2* __restrict__ A, double2* __restrict__ Dinv2, double2* __restrict__ W,
+                 double2* __restrict__ C, GridBar* gb) {
+    __shared__ double2 ta[kB * kB];
+    __shared__ double2 tb[kB * kB];
+    const int nt = np / kB;
+    const double eps = eps_p[0];
+    const int tid = threadIdx.x;
+    const size_t gtid = (size_t)blockIdx.x * blockDim.x + tid;
+    const size_t gstride = (size_t)gridDim.x * blockDim.x;
+
+    // A = pad(G + eps I): lower tiles and full diagonal tiles are the live part
+    for (size_t e = gtid; e < (size_t)np * np; e += gstride) {
+        const int i = (int)(e % np), j = (int)(e / np);
+        double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
+        if (i < s && j < s) {
+            v = G[i + (size_t)j * s];
+            if (i == j) v.x += eps;
+        }
+        A[e] = v;
+    }
+    if (!grid_barrier(gb)) return;
+    if (blockIdx.x == 0) {
+        if (tid < kB * kB) ta[tid] = A[(tid % kB) + (size_t)(tid / kB) * np];
+        __syncthreads();
+        tile_inverse(ta, Dinv2);
+    }
+    if (!grid_barrier(gb)) return;
+
+    const int nlt = nt * (nt + 1) / 2;
+    for (int K = 0; K < nt; ++K) {
+        const double2* D = Dinv2 + (K & 1) * kB * kB;
+        double2* Dnext = Dinv2 + ((K + 1) & 1) * kB * kB;
+        const int k0 = K * kB;
+        // ---- phase A: W = D^-1 A_K,: (16 x np) and C = A_:,K (np x 16), old values
+        for (size_t e = gtid; e < (size_t)np * kB; e += gstride) {
+            const int m = (int)(e % kB);          // pivot-local index
+            const int col = (int)(e / kB);        // global column (for W) / row (for C)
+            const int J = col / kB;
+            // W[m, col] = sum_q D[m, q] A_K(q, col)
+            double2 acc = make_double2(0.0, 0.0);
+            if (J != K) {
+                for (int q = 0; q < kB; ++q) {
+                    double2 a;
+                    if (J < K) a = A[(k0 + q) + (size_t)col * np];
+                    else a = zconj(A[col + (size_t)(k0 + q) * np]);
+                    acc = zfma(D[m + q * kB], a, acc);
+                }
+            }
+            W[m + (size_t)col * kB] = acc;
+            // C[row = col, m] = A(row, k0 + m)
+            double2 c;
+            if (J >= K) c = A[col + (size_t)(k0 + m) * np];
+            else c = zconj(A[(k0 + m) + (size_t)col * np]);
+            C[col + (size_t)m * np] = c;
+        }
+        if (!grid_barrier(gb)) return;
+        // ---- phase B: lower tiles; the owner of tile (K+1, K+1) also inverts it (look-ahead)
+        for (int t = blockIdx.x; t < nlt; t += gridDim.x) {
+            int I = 0, rem = t;
+            while (rem > I) { rem -= I + 1; ++I; }
+            const int J = rem;                    // J <= I
+            const int ii = tid % kB, jj = tid / kB;
+            const int row = I * kB + ii, col = J * kB + jj;
+            double2 v;
+            if (I == K && J == K) {
+                const double2 d = D[ii + jj * kB];
+                v = make_double2(-d.x, -d.y);
+            } else if (I == K) {
+                v = W[ii + (size_t)col * kB];
+            } else if (J == K) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int q = 0; q < kB; ++q) acc = zfma(C[row + (size_t)q * np], D[q + jj * kB], acc);
+                v = acc;
+            } else {
+                // stage C_I and W_J tiles in shared memory
+                ta[ii + jj * kB] = C[(I * kB + ii) + (size_t)jj * np];
+                tb[ii + jj * kB] = W[ii + (size_t)(J * kB + jj) * kB];
+                __syncthreads();
+                double2 acc = A[row + (size_t)col * np];
+                for (int q = 0; q < kB; ++q) {
+                    const double2 pr = zmul(ta[ii + q * kB], tb[q + jj * kB]);
+                    acc.x -= pr.x;
+                    acc.y -= pr.y;
+                }
+                v = acc;
+                __syncthreads();
+            }
+            A[row + (size_t)col * np] = v;
+            if (I == J && I == K + 1) {
+                ta[ii + jj * kB] = v;
+                __syncthreads();
+                tile_inverse(ta, Dnext);
+            }
+        }
+        if (!grid_barrier(gb)) return;
+    }
+    // ---- H = -A (s x s, full, column-major) written over G
+    for (size_t e = gtid; e < (size_t)s * s; e += gstride) {
+        const int i = (int)(e % s), j = (int)(e / s);
+        const int I = i / kB, J = j / kB;
+        double2 v;
+        if (I > J || (I == J)) v = A[i + (size_t)j * np];
+        else v = zconj(A[j + (size_t)i * np]);
+        G[e] = make_double2(-v.x, -v.y);
+    }
+}
+
+// d_ab[delta] = sum_{l - l' = delta} H[(l', b), (l, a)] from H (s x s column-major).
+__global__ void hdiag_kernel(const double2* __restrict__ H, int N1, int N2, int M,
+                             double2* __restrict__ dsum) {
+    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1;
+    const int npair = M * (M + 1) / 2;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= npair * L1 * L2) return;
+    const int pr = warp / (L1 * L2), rem = warp % (L1 * L2);
+    const int d1 = rem / L2 - (N1 - 1), d2 = rem % L2 - (N2 - 1);
+    int a = 0, e = pr;
+    while (e >= M - a) { e -= M - a; ++a; }
+    const int b = a + e;
+    const int s = N1 * N2 * M;
+    const int lo1 = max(0, -d1), hi1 = min(N1, N1 - d1);
+    const int lo2 = max(0, -d2), hi2 = min(N2, N2 - d2);
+    const int n2 = hi2 - lo2;
+    const int cnt = (hi1 - lo1) * n2;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int t = lane; t < cnt; t += 32) {
+        const int lp1 = lo1 + t / n2, lp2 = lo2 + t % n2;
+        const size_t rowi = ((size_t)b * N1 + lp1) * N2 + lp2;
+        const size_t coli = ((size_t)a * N1 + lp1 + d1) * N2 + lp2 + d2;
+        acc = zadd(acc, H[rowi + coli * s]);
+    }
+    acc.x = warp_sum(acc.x);
+    acc.y = warp_sum(acc.y);
+    if (lane == 0) dsum[warp] = acc;
+}
+
+// ---- Lanczos estimate of lambda_max(G), FP64, m steps, then multisection on the tridiagonal.
+__global__ void __launch_bounds__(kThreads)
+lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict__ u,
+               double2* __restrict__ vprev, double* __restrict__ part, double* __restrict__ ab,
+               double* __restrict__ lmax_out, GridBar* gb) {
+    __shared__ double red[kThreads / 32];
+    __shared__ double sh_lo, sh_hi;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (kThreads / 32);
+    const int gw = blockIdx.x * (kThreads / 32) + warp;
+    // deterministic start vector, unnormalised: u_i = 1 + 0.5 sin(i) + 0.25 i cos(3 i) / s
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
+        u[i] = make_double2(1.0 + 0.5 * sin((double)i), 0.25 * cos(3.0 * i) * i / s);
+        vprev[i] = make_double2(0.0, 0.0);
+    }
+    if (!grid_barrier(gb)) return;
+    // beta_{-1} = |u|
+    double beta = 0.0;
+    {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < s; i += blockDim.x) acc += u[i].x * u[i].x + u[i].y * u[i].y;
+        beta = sqrt(block_sum(acc, red));
+    }
+    for (int k = 0; k < m; ++k) {
+        // v_k = u / beta_{k-1};  w = G v_k - alpha_k v_k - beta_{k-1} v_{k-1};  beta_k = |w|
+        const double ib = 1.0 / beta;
+        double* pa = part + (size_t)(k & 1) * 2 * gridDim.x;   // alpha partials (ping-pong)
+        double* pb = pa + gridDim.x;                            // beta partials
+        double ap = 0.0;
+        double2 yrow[4];
+        int nrow = 0;
+        for (int i = gw; i < s && nrow < 4; i += nw, ++nrow) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int j = lane; j < s; j += 32) acc = zfma(G[i + (size_t)j * s], u[j], acc);
+            acc.x = warp_sum(acc.x) * ib;
+            acc.y = warp_sum(acc.y) * ib;
+            yrow[nrow] = acc;
+            const double2 vi = make_double2(u[i].x * ib, u[i].y * ib);
+            ap += vi.x * acc.x + vi.y * acc.y;
+        }
+        const double apb = block_sum(lane == 0 ? ap : 0.0, red);
+        if (threadIdx.x == 0) pa[blockIdx.x] = apb;
+        if (!grid_barrier(gb)) return;
+        const double alpha = block_sum_array(pa, gridDim.x, red);
+        double bp = 0.0;
+        nrow = 0;
+        for (int i = gw; i < s && nrow < 4; i += nw, ++nrow) {
+            if (lane == 0) {
+                const double2 vi = make_double2(u[i].x * ib, u[i].y * ib);
+                const double2 vp = vprev[i];
+                const double2 un = make_double2(yrow[nrow].x - alpha * vi.x - beta * vp.x,
+                                                yrow[nrow].y - alpha * vi.y - beta * vp.y);
+                bp += un.x * un.x + un.y * un.y;
+                vprev[i] = vi;
+                u[i] = un;
+            }
+        }
+        const double bpb = block_sum(bp, red);
+        if (threadIdx.x == 0) pb[blockIdx.x] = bpb;
+        if (!grid_barrier(gb)) return;
+        const double bnew = sqrt(block_sum_array(pb, gridDim.x, red));
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ab[2 * k] = alpha;
+            ab[2 * k + 1] = bnew;
+        }
+        beta = bnew;
+        if (!(bnew > 1e-300 * fabs(alpha) + 1e-300)) { m = k + 1; break; }
+    }
+    // largest eigenvalue of the m x m tridiagonal (alpha_k, beta_k) by multisection (CTA 0)
+    if (blockIdx.x != 0) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double lo = 1e300, hi = -1e300;
+        for (int k = 0; k < m; ++k) {
+            const double r = (k > 0 ? fabs(ab[2 * k - 1]) : 0.0) + (k + 1 < m ? fabs(ab[2 * k + 1]) : 0.0);
+            lo = fmin(lo, ab[2 * k] - r);
+            hi = fmax(hi, ab[2 * k] + r);
+        }
+        sh_lo = lo;
+        sh_hi = hi;
+    }
+    __syncthreads();
+    for (int round = 0; round < 12; ++round) {
+        const double lo = sh_lo, hi = sh_hi;
+        const double x = lo + (hi - lo) * (threadIdx.x + 1) / (double)(blockDim.x + 1);
+        // Sturm count: number of eigenvalues < x
+        int cnt = 0;
+        double d = 1.0;
+        for (int k = 0; k < m; ++k) {
+            const double bb = k > 0 ? ab[2 * k - 1] * ab[2 * k - 1] : 0.0;
+            d = (ab[2 * k] - x) - (k > 0 ? bb / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0.0) ++cnt;
+        }
+        // the largest eigenvalue lies above the largest x with cnt < m
+        __shared__ int best;
+        if (threadIdx.x == 0) best = -1;
+        __syncthreads();
+        if (cnt < m) atomicMax(&best, (int)threadIdx.x);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double step = (hi - lo) / (double)(blockDim.x + 1);
+            sh_lo = lo + step * (best + 1);
+            sh_hi = sh_lo + step;
+        }
+        __syncthreads();
+        if (sh_hi - sh_lo <= 1e-15 * fabs(sh_hi)) break;
+    }
+    if (threadIdx.x == 0) lmax_out[0] = 0.5 * (sh_lo + sh_hi);
+}
+
+int coop_grid(const void* kern, int* grid) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, 0) != cudaSuccess) return -1;
+    if (per < 1) return -1;
+    *grid = sms;  // one CTA per SM
+    return 0;
+}
+
+int padded(int s) { return (s + kB - 1) / kB * kB; }
+
+}  // namespace
+
+size_t hpd_scratch_bytes(const Dims& d) {
+    const size_t np = (size_t)padded(d.s());
+    return np * np * sizeof(double2) + 2 * kB * kB * sizeof(double2) + 2 * np * kB * sizeof(double2) +
+           sizeof(GridBar) + 1024;
+}
+
+size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {
+    return 256 + 2 * (size_t)d.s() * sizeof(double2) + 4 * (size_t)grid_max * sizeof(double) +
+           2 * 96 * sizeof(double) + 1024;
+}
+
+cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
+                               int* err_flag_out, cudaStream_t st) {
+    const int s = d.s(), np = padded(s);
+    unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
+    GridBar* gb = reinterpret_cast<GridBar*>(p);
+    p += 256;
+    double2* A = reinterpret_cast<double2*>(p);
+    p += (size_t)np * np * sizeof(double2);
+    double2* Dinv2 = reinterpret_cast<double2*>(p);
+    p += 2 * kB * kB * sizeof(double2);
+    double2* W = reinterpret_cast<double2*>(p);
+    p += (size_t)np * kB * sizeof(double2);
+    double2* C = reinterpret_cast<double2*>(p);
+    cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
+    if (e != cudaSuccess) return e;
+    int grid = 0;
+    if (coop_grid((const void*)hpd_sweep_kernel, &grid)) return cudaErrorInvalidConfiguration;
+    void* args[] = {&G, (void*)&s, (void*)&eps, (void*)&np, &A, &Dinv2, &W, &C, &gb};
+    e = cudaLaunchCooperativeKernel((const void*)hpd_sweep_kernel, dim3(grid), dim3(kThreads), args, 0, st);
+    if (e != cudaSuccess) return e;
+    if (err_flag_out) {
+        // fold the barrier error into the caller's flag (max)
+        e = cudaMemcpyAsync(err_flag_out, &gb->err, sizeof(int), cudaMemcpyDeviceToDevice, st);
+    }
+    return e;
+}
+
+cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStream_t st) {
+    const int nout = d.npair() * d.L1() * d.L2();
+    const int warps_per_block = 8;
+    hdiag_kernel<<<(nout + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+        H, d.N1, d.N2, d.M, dsum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, double* lmax,
+                                int* err_flag_out, cudaStream_t st) {
+    int grid = 0;
+    if (coop_grid((const void*)lanczos_kernel, &grid)) return cudaErrorInvalidConfiguration;
+    const int s = d.s();
+    int m = s < 96 ? s : 96;
+    unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
+    GridBar* gb = reinterpret_cast<GridBar*>(p);
+    p += 256;
+    double2* u = reinterpret_cast<double2*>(p);
+    p += (size_t)s * sizeof(double2);
+    double2* vprev = reinterpret_cast<double2*>(p);
+    p += (size_t)s * sizeof(double2);
+    double* part = reinterpret_cast<double*>(p);
+    p += 4 * (size_t)grid * sizeof(double);
+    double* ab = reinterpret_cast<double*>(p);
+    cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&G, (void*)&s, (void*)&m, &u, &vprev, &part, &ab, &lmax, &gb};
+    e = cudaLaunchCooperativeKernel((const void*)lanczos_kernel, dim3(grid), dim3(kThreads), args, 0, st);
+    if (e != cudaSuccess) return e;
+    if (err_flag_out) e = cudaMemcpyAsync(err_flag_out, &gb->err, sizeof(int), cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
+}  // namespace recon

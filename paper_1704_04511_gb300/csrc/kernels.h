@@ -77,9 +77,9 @@ cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, doub
                         int nblocks, double2* lags, double2* G, cudaStream_t st);
 
 // ---- weight.cu ----
-// eps update: first -> eps = frac * lambda_max, else eps /= gamma
-cudaError_t launch_eps(const double* evals, int s, double* eps, int first, double frac,
-                       double gamma, cudaStream_t st);
+// eps update: first -> eps = frac * lambda_max (read from *lmax), else eps /= gamma
+cudaError_t launch_eps(const double* lmax, double* eps, int first, double frac, double gamma,
+                       cudaStream_t st);
 // Summed diagonals of H = U diag((lambda + eps)^(p/2-1)) U^H: d[pair][L1][L2] (complex128)
 size_t diag_scratch_bytes(const Dims& d);
 cudaError_t launch_diag_sums(const Dims& d, const double2* U, const double* evals,
@@ -89,5 +89,18 @@ cudaError_t launch_diag_sums(const Dims& d, const double2* U, const double* eval
 size_t s_scratch_bytes(const Dims& d);
 cudaError_t launch_weight_S(const Dims& d, const Twiddles& tw, const double2* dsum, double2* Z,
                             float2* S, cudaStream_t st);
+
+// ---- hpdinv.cu (p = 0: H = (G + eps I)^-1 by a blocked Hermitian sweep, FP64) ----
+size_t hpd_scratch_bytes(const Dims& d);
+size_t lanczos_scratch_bytes(const Dims& d, int grid_max);
+// G (s x s, column-major, Hermitian) is replaced by H = (G + eps I)^-1. *err_flag_out receives
+// 1 if a grid barrier timed out.
+cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
+                               int* err_flag_out, cudaStream_t st);
+// d_ab[delta] (summed diagonals) from an explicit H
+cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStream_t st);
+// *lmax = largest eigenvalue of G (Lanczos, FP64)
+cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, double* lmax,
+                                int* err_flag_out, cudaStream_t st);
 
 }  // namespace recon

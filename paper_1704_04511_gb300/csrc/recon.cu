@@ -228,10 +228,12 @@ int check_dims(recon_ctx* c, recon_dims dd, const recon_filter* f, Dims* d) {
 struct Work {
     float2 *r, *p, *t, *S0, *S1;
     double2 *G, *lag_part, *lags, *dpart, *dsum, *Z, *eigwork;
-    double *evals, *part_pq, *part_rr, *eps, *hist;
-    int* info;
+    double *evals, *part_pq, *part_rr, *eps, *hist, *lmax;
+    int *info, *kerr;
+    void *hpd, *lanc;
     int lwork;
     int gblocks;
+    bool use_eig;
 };
 
 int eig_lwork(recon_ctx* c, int s, double2* G, double* evals, int* lwork) {
@@ -242,15 +244,22 @@ int eig_lwork(recon_ctx* c, int s, double2* G, double* evals, int* lwork) {
     return RECON_OK;
 }
 
-// Allocate (or reuse) the workspace of one solve. n_info: number of eigensolves to record.
-int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_info, bool vectors, Work* w) {
+// Weight method: the p = 0 weight (G + eps I)^-1 is formed by the FP64 sweep inverse unless the
+// eigendecomposition is asked for (or p > 0, which needs the eigenvalues).
+bool wants_eig(double p, int method) { return method == RECON_WEIGHT_EIG || p != 0.0; }
+
+// Allocate (or reuse) the workspace of one solve. n_iter: number of weight steps to record.
+int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bool use_eig,
+             Work* w) {
     void* ptr;
     int rc;
     const size_t vec = d.elems() * sizeof(float2);
     const size_t sbytes = (size_t)d.npair() * d.pixels() * sizeof(float2);
     const int s = d.s();
     const size_t nlag = (size_t)d.npair() * d.L1() * d.L2();
+    const int ni = n_iter < 1 ? 1 : n_iter;
     w->gblocks = recon::gram_blocks(d);
+    w->use_eig = use_eig;
 #define GET(name, bytes, field, type)                         \
     rc = ensure(c, name, (bytes), &ptr);                      \
     if (rc) return rc;                                        \
@@ -263,21 +272,33 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_info, bool vectors, Wo
         GET("S1", sbytes, S1, float2*);
     }
     GET("G", (size_t)s * s * sizeof(double2), G, double2*);
-    GET("evals", (size_t)s * sizeof(double), evals, double*);
     GET("lag_part", recon::gram_scratch_bytes(d, w->gblocks), lag_part, double2*);
     GET("lags", nlag * sizeof(double2), lags, double2*);
-    GET("dpart", recon::diag_scratch_bytes(d), dpart, double2*);
     GET("dsum", nlag * sizeof(double2), dsum, double2*);
     GET("Z", recon::s_scratch_bytes(d), Z, double2*);
     GET("part_pq", (size_t)d.P * sizeof(double), part_pq, double*);
     GET("part_rr", (size_t)2 * recon::vec_parts() * sizeof(double), part_rr, double*);
-    GET("eps", sizeof(double), eps, double*);
+    GET("eps", 2 * sizeof(double), eps, double*);
+    w->lmax = w->eps + 1;
     GET("hist", (size_t)3 * (n_cg + 1) * sizeof(double), hist, double*);
-    GET("info", (size_t)(n_info < 1 ? 1 : n_info) * sizeof(int), info, int*);
-    rc = eig_lwork(c, s, w->G, w->evals, &w->lwork);
-    if (rc) return rc;
-    GET("eigwork", (size_t)(w->lwork < 1 ? 1 : w->lwork) * sizeof(double2), eigwork, double2*);
+    GET("info", (size_t)ni * sizeof(int), info, int*);
+    GET("kerr", (size_t)2 * ni * sizeof(int), kerr, int*);
+    if (use_eig) {
+        GET("evals", (size_t)s * sizeof(double), evals, double*);
+        GET("dpart", recon::diag_scratch_bytes(d), dpart, double2*);
+        rc = eig_lwork(c, s, w->G, w->evals, &w->lwork);
+        if (rc) return rc;
+        GET("eigwork", (size_t)(w->lwork < 1 ? 1 : w->lwork) * sizeof(double2), eigwork, double2*);
+    } else {
+        int dev = 0, sms = 0;
+        RC_CUDA(cudaGetDevice(&dev));
+        RC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        GET("hpd", recon::hpd_scratch_bytes(d), hpd, void*);
+        GET("lanc", recon::lanczos_scratch_bytes(d, sms), lanc, void*);
+    }
 #undef GET
+    RC_CUDA(cudaMemsetAsync(w->info, 0, (size_t)ni * sizeof(int), c->stream));
+    RC_CUDA(cudaMemsetAsync(w->kerr, 0, (size_t)2 * ni * sizeof(int), c->stream));
     return RECON_OK;
 }
 
@@ -290,30 +311,58 @@ int run_eig(recon_ctx* c, int s, Work& w, int* info) {
     return RECON_OK;
 }
 
-// Weight step on w.G (overwritten by eigenvectors): eps update, summed diagonals, S.
+// Weight step on w.G (consumed): eps update, H (eigendecomposition or sweep inverse), summed
+// diagonals, S. `it` indexes the per-iteration status slots (eigensolver info, barrier flags).
 int weight_step(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, double p, int eps_first,
                 double eps_frac, double gamma, int eps_mode_set, double eps_value, float2* S,
-                int* info) {
-    int rc;
-    {
-        ProfScope ps(c, RECON_PROF_EIG);
-        rc = run_eig(c, d.s(), w, info);
-    }
-    if (rc) return rc;
-    if (eps_mode_set) {
+                int it) {
+    if (eps_mode_set)
         RC_CUDA(cudaMemcpyAsync(w.eps, &eps_value, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    } else {
-        ProfScope ps(c, RECON_PROF_EPS);
-        RC_CUDA(recon::launch_eps(w.evals, d.s(), w.eps, eps_first, eps_frac, gamma, c->stream));
-    }
-    {
+    if (w.use_eig) {
+        {
+            ProfScope ps(c, RECON_PROF_EIG);
+            int rc = run_eig(c, d.s(), w, w.info + it);
+            if (rc) return rc;
+        }
+        if (!eps_mode_set) {
+            ProfScope ps(c, RECON_PROF_EPS);
+            RC_CUDA(recon::launch_eps(w.evals + d.s() - 1, w.eps, eps_first, eps_frac, gamma, c->stream));
+        }
         ProfScope ps(c, RECON_PROF_DIAG);
         RC_CUDA(recon::launch_diag_sums(d, w.G, w.evals, w.eps, p, w.dpart, w.dsum, c->stream));
+    } else {
+        if (!eps_mode_set) {
+            if (eps_first) {
+                ProfScope ps(c, RECON_PROF_LANCZOS);
+                RC_CUDA(recon::launch_lanczos_lmax(d, w.G, w.lanc, w.lmax, w.kerr + 2 * it + 1, c->stream));
+            }
+            ProfScope ps(c, RECON_PROF_EPS);
+            RC_CUDA(recon::launch_eps(w.lmax, w.eps, eps_first, eps_frac, gamma, c->stream));
+        }
+        {
+            ProfScope ps(c, RECON_PROF_INV);
+            RC_CUDA(recon::launch_hpd_inverse(d, w.G, w.eps, w.hpd, w.kerr + 2 * it, c->stream));
+        }
+        ProfScope ps(c, RECON_PROF_DIAG);
+        RC_CUDA(recon::launch_hdiag(d, w.G, w.dsum, c->stream));
     }
     {
         ProfScope ps(c, RECON_PROF_S);
         RC_CUDA(recon::launch_weight_S(d, tw, w.dsum, w.Z, S, c->stream));
     }
+    return RECON_OK;
+}
+
+// After the stream finished: eigensolver status and device-wait flags of n_iter weight steps.
+int check_status(recon_ctx* c, Work& w, int n_iter) {
+    if (n_iter < 1) return RECON_OK;
+    std::vector<int> info(n_iter), kerr(2 * (size_t)n_iter);
+    RC_CUDA(cudaMemcpy(info.data(), w.info, n_iter * sizeof(int), cudaMemcpyDeviceToHost));
+    RC_CUDA(cudaMemcpy(kerr.data(), w.kerr, 2 * (size_t)n_iter * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int e : kerr)
+        if (e != 0) return fail(c, RECON_ETIMEOUT, "a bounded device-wide barrier timed out");
+    for (int e : info)
+        if (e != 0) return fail(c, RECON_ENUMERIC, "eigensolver failed (info != 0)");
     return RECON_OK;
 }
 
@@ -452,7 +501,7 @@ int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* 
     rc = get_twiddles(c, d, &tw);
     if (rc) return rc;
     Work w;
-    rc = get_work(c, d, prm->cg, prm->irls, true, &w);
+    rc = get_work(c, d, prm->cg, prm->irls, true, wants_eig(prm->p, prm->weight_method), &w);
     if (rc) return rc;
     float2* x = reinterpret_cast<float2*>(image_out);
     const float lam = (float)prm->lambda;
@@ -468,18 +517,15 @@ int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* 
             ProfScope ps(c, RECON_PROF_GRAM);
             RC_CUDA(recon::launch_gram(d, tw, x, w.lag_part, w.gblocks, nullptr, w.G, c->stream));
         }
-        rc = weight_step(c, d, tw, w, prm->p, n == 0, prm->eps0_frac, prm->gamma, 0, 0.0, S_new,
-                         w.info + n);
+        rc = weight_step(c, d, tw, w, prm->p, n == 0, prm->eps0_frac, prm->gamma, 0, 0.0, S_new, n);
         if (rc) return rc;
         rc = cg_block(c, d, tw, w, masks, S_old, S_new, lam, x, n == 0, prm->cg);
         if (rc) return rc;
     }
     RC_CUDA(cudaStreamSynchronize(c->stream));
+    rc = check_status(c, w, prm->irls);
+    if (rc) return rc;
     if (prm->irls > 0) {
-        std::vector<int> info(prm->irls);
-        RC_CUDA(cudaMemcpy(info.data(), w.info, prm->irls * sizeof(int), cudaMemcpyDeviceToHost));
-        for (int n = 0; n < prm->irls; ++n)
-            if (info[n] != 0) return fail(c, RECON_ENUMERIC, "eigensolver failed (info != 0)");
         const int nv = recon::vec_parts();
         std::vector<double> part(nv);
         RC_CUDA(cudaMemcpy(part.data(), w.part_rr + (prm->cg & 1) * nv, nv * sizeof(double),
@@ -554,9 +600,14 @@ int recon_gram(recon_ctx* c, recon_dims dd, recon_filter f, const void* x, void*
 }
 
 int recon_weight(recon_ctx* c, recon_dims dd, recon_filter f, const void* G_in, double eps_in,
-                 double p, void* S_out, void* dsum_out, void* evals_out, double* eps_out) {
+                 double p, int method, void* S_out, void* dsum_out, void* evals_out,
+                 double* eps_out) {
     if (!c) return RECON_EINVAL;
     if (!G_in || !S_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (method != RECON_WEIGHT_AUTO && method != RECON_WEIGHT_EIG)
+        return fail(c, RECON_EINVAL, "unknown weight method");
+    if (evals_out && !wants_eig(p, method))
+        return fail(c, RECON_EINVAL, "eigenvalues are only formed by RECON_WEIGHT_EIG or p > 0");
     if (!std::isfinite(eps_in) || !(p >= 0.0 && p <= 1.0)) return fail(c, RECON_EINVAL, "bad eps or p");
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
@@ -567,12 +618,12 @@ int recon_weight(recon_ctx* c, recon_dims dd, recon_filter f, const void* G_in, 
     rc = get_twiddles(c, d, &tw);
     if (rc) return rc;
     Work w;
-    rc = get_work(c, d, 1, 1, false, &w);
+    rc = get_work(c, d, 1, 1, false, wants_eig(p, method), &w);
     if (rc) return rc;
     const size_t gbytes = (size_t)d.s() * d.s() * sizeof(double2);
     RC_CUDA(cudaMemcpyAsync(w.G, G_in, gbytes, cudaMemcpyDeviceToDevice, c->stream));
     const bool set = eps_in >= 0.0;
-    rc = weight_step(c, d, tw, w, p, 1, set ? 0.0 : -eps_in, 1.0, set, eps_in, (float2*)S_out, w.info);
+    rc = weight_step(c, d, tw, w, p, 1, set ? 0.0 : -eps_in, 1.0, set, eps_in, (float2*)S_out, 0);
     if (rc) return rc;
     if (dsum_out)
         RC_CUDA(cudaMemcpyAsync(dsum_out, w.dsum, (size_t)d.npair() * d.L1() * d.L2() * sizeof(double2),
@@ -581,9 +632,8 @@ int recon_weight(recon_ctx* c, recon_dims dd, recon_filter f, const void* G_in, 
         RC_CUDA(cudaMemcpyAsync(evals_out, w.evals, (size_t)d.s() * sizeof(double),
                                 cudaMemcpyDeviceToDevice, c->stream));
     RC_CUDA(cudaStreamSynchronize(c->stream));
-    int info = 0;
-    RC_CUDA(cudaMemcpy(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost));
-    if (info != 0) return fail(c, RECON_ENUMERIC, "eigensolver failed (info != 0)");
+    rc = check_status(c, w, 1);
+    if (rc) return rc;
     if (eps_out) RC_CUDA(cudaMemcpy(eps_out, w.eps, sizeof(double), cudaMemcpyDeviceToHost));
     return RECON_OK;
 }
@@ -645,7 +695,7 @@ int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, 
     rc = get_twiddles(c, d, &tw);
     if (rc) return rc;
     Work w;
-    rc = get_work(c, d, n_cg, 1, true, &w);
+    rc = get_work(c, d, n_cg, 1, true, false, &w);
     if (rc) return rc;
     // the caller's r is the residual buffer for this call
     float2* r_save = w.r;
@@ -695,7 +745,7 @@ int recon_profile_read(recon_ctx* c, int kind, double* total_ms, long long* laun
 const char* recon_profile_name(int kind) {
     static const char* names[RECON_PROF_KINDS] = {
         "adjoint", "gram", "eig", "eps", "diag_sums", "weight_S", "resid_carry",
-        "cg_row_fwd", "cg_col_mask", "cg_row_inv_w", "cg_update"};
+        "cg_row_fwd", "cg_col_mask", "cg_row_inv_w", "cg_update", "lanczos", "hpd_inverse"};
     return (kind >= 0 && kind < RECON_PROF_KINDS) ? names[kind] : "";
 }
 

@@ -17,10 +17,10 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChunk = 2;  // eigenvectors per CTA
 
-__global__ void eps_kernel(const double* __restrict__ evals, int s, double* eps, int first,
-                           double frac, double gamma) {
+__global__ void eps_kernel(const double* __restrict__ lmax, double* eps, int first, double frac,
+                           double gamma) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        if (first) eps[0] = frac * evals[s - 1];
+        if (first) eps[0] = frac * lmax[0];
         else eps[0] = eps[0] / gamma;
     }
 }
@@ -67,13 +67,16 @@ diag_part_kernel(const double2* __restrict__ U, const double* __restrict__ evals
     }
 }
 
+// one warp per output: lanes add the chunk partials, then a fixed shuffle tree
 __global__ void diag_reduce_kernel(const double2* __restrict__ dpart, int nchunks, int nout,
                                    double2* __restrict__ dsum) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (o >= nout) return;
     double2 v = make_double2(0.0, 0.0);
-    for (int c = 0; c < nchunks; ++c) v = zadd(v, dpart[(size_t)c * nout + o]);
-    dsum[o] = v;
+    for (int c = lane; c < nchunks; c += 32) v = zadd(v, dpart[(size_t)c * nout + o]);
+    v.x = warp_sum(v.x);
+    v.y = warp_sum(v.y);
+    if (lane == 0) dsum[o] = v;
 }
 
 // Z[pair][i1][r2] = sum_{d2} d[pair][i1][d2] w_Q^{d2 r2}  (FP64, rounded to FP32 on store)
@@ -116,9 +119,9 @@ int nchunks(const Dims& d) { return (d.s() + kChunk - 1) / kChunk; }
 
 }  // namespace
 
-cudaError_t launch_eps(const double* evals, int s, double* eps, int first, double frac,
-                       double gamma, cudaStream_t st) {
-    eps_kernel<<<1, 32, 0, st>>>(evals, s, eps, first, frac, gamma);
+cudaError_t launch_eps(const double* lmax, double* eps, int first, double frac, double gamma,
+                       cudaStream_t st) {
+    eps_kernel<<<1, 32, 0, st>>>(lmax, eps, first, frac, gamma);
     return cudaGetLastError();
 }
 
@@ -140,7 +143,7 @@ cudaError_t launch_diag_sums(const Dims& d, const double2* U, const double* eval
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nout = d.npair() * d.L1() * d.L2();
-    diag_reduce_kernel<<<(nout + 127) / 128, 128, 0, st>>>(dpart, nchunks(d), nout, dsum);
+    diag_reduce_kernel<<<(nout + 7) / 8, 256, 0, st>>>(dpart, nchunks(d), nout, dsum);
     return cudaGetLastError();
 }
 

@@ -25,16 +25,20 @@ RECON_EINVAL = -1
 RECON_ENOMEM = -2
 RECON_ECUDA = -3
 RECON_ENUMERIC = -4
+RECON_ETIMEOUT = -5
+RECON_WEIGHT_AUTO = 0
+RECON_WEIGHT_EIG = 1
 
 _ERR_NAMES = {RECON_EINVAL: "RECON_EINVAL", RECON_ENOMEM: "RECON_ENOMEM",
-              RECON_ECUDA: "RECON_ECUDA", RECON_ENUMERIC: "RECON_ENUMERIC"}
+              RECON_ECUDA: "RECON_ECUDA", RECON_ENUMERIC: "RECON_ENUMERIC",
+              RECON_ETIMEOUT: "RECON_ETIMEOUT"}
 
 EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_needed",
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
             "recon_profile_read", "recon_profile_name")
 
-PROF_KINDS = 11
+PROF_KINDS = 13
 
 
 class ReconError(RuntimeError):
@@ -54,7 +58,8 @@ class recon_filter(ctypes.Structure):
 class recon_params(ctypes.Structure):
     _fields_ = [("irls", ctypes.c_int), ("cg", ctypes.c_int), ("lambda_", ctypes.c_double),
                 ("p", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("eps0_frac", ctypes.c_double), ("kspace_bf16", ctypes.c_int)]
+                ("eps0_frac", ctypes.c_double), ("kspace_bf16", ctypes.c_int),
+                ("weight_method", ctypes.c_int)]
 
 
 _lib = None
@@ -82,7 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_adjoint": (i, [vp, dims, vp, i, vp, vp]),
             "recon_fft2": (i, [vp, dims, vp, vp, i]),
             "recon_gram": (i, [vp, dims, filt, vp, vp, vp]),
-            "recon_weight": (i, [vp, dims, filt, vp, d, d, vp, vp, vp, ctypes.POINTER(d)]),
+            "recon_weight": (i, [vp, dims, filt, vp, d, d, i, vp, vp, vp, ctypes.POINTER(d)]),
             "recon_apply_normal": (i, [vp, dims, filt, vp, vp, d, vp, vp]),
             "recon_apply_w": (i, [vp, dims, filt, vp, vp, vp]),
             "recon_cg": (i, [vp, dims, filt, vp, vp, vp, d, vp, vp, i, ctypes.POINTER(d)]),
@@ -154,11 +159,13 @@ def recon_bytes_needed(shape, filt, kspace_bf16: bool = False) -> int:
 
 
 def recon_solve(ctx, kspace, masks, filt, lam: float, p: float, irls: int, cg: int,
-                image_out, gamma: float = 1.4, eps0_frac: float = 0.01) -> None:
+                image_out, gamma: float = 1.4, eps0_frac: float = 0.01,
+                weight_method: int = RECON_WEIGHT_AUTO) -> None:
     import torch
     bf16 = kspace.dtype == torch.bfloat16
     prm = recon_params(irls=int(irls), cg=int(cg), lambda_=float(lam), p=float(p),
-                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=int(bf16))
+                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=int(bf16),
+                       weight_method=int(weight_method))
     _check(ctx, load_library().recon_solve(ctx, _dims(masks), _ptr(kspace), _ptr(masks),
                                            _filt(filt), ctypes.byref(prm), _ptr(image_out)))
 
@@ -180,11 +187,12 @@ def recon_gram(ctx, x, filt, G_out, lags_out=None) -> None:
 
 
 def recon_weight(ctx, shape, filt, G_in, eps_in: float, p: float, S_out, dsum_out=None,
-                 evals_out=None) -> float:
+                 evals_out=None, method: int = RECON_WEIGHT_AUTO) -> float:
     T, P, Q = shape
     eps_used = ctypes.c_double(0.0)
     _check(ctx, load_library().recon_weight(ctx, recon_dims(P=P, Q=Q, T=T), _filt(filt),
-                                            _ptr(G_in), float(eps_in), float(p), _ptr(S_out),
+                                            _ptr(G_in), float(eps_in), float(p), int(method),
+                                            _ptr(S_out),
                                             _ptr(dsum_out), _ptr(evals_out),
                                             ctypes.byref(eps_used)))
     return eps_used.value
@@ -249,9 +257,11 @@ class Context:
         except Exception:
             pass
 
-    def solve(self, kspace, masks, filt, lam, p, irls, cg, gamma=1.4, eps0_frac=0.01, out=None):
+    def solve(self, kspace, masks, filt, lam, p, irls, cg, gamma=1.4, eps0_frac=0.01, out=None,
+              weight_method=RECON_WEIGHT_AUTO):
         import torch
         if out is None:
             out = torch.empty(tuple(masks.shape), dtype=torch.complex64, device=masks.device)
-        recon_solve(self.h, kspace, masks, filt, lam, p, irls, cg, out, gamma, eps0_frac)
+        recon_solve(self.h, kspace, masks, filt, lam, p, irls, cg, out, gamma, eps0_frac,
+                    weight_method)
         return out

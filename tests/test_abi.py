@@ -49,7 +49,8 @@ def test_bytes_needed_formula(lib):
 def test_profile_names(lib):
     from paper_1704_04511_gb300 import recon
     names = [recon.recon_profile_name(k) for k in range(recon.PROF_KINDS)]
-    assert names[2] == "eig" and names[-1] == "cg_update" and all(names)
+    assert names[2] == "eig" and names[10] == "cg_update" and names[12] == "hpd_inverse"
+    assert all(names)
     assert recon.recon_profile_name(recon.PROF_KINDS) == ""
 
 
