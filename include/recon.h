@@ -164,8 +164,12 @@ int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
 #define RECON_PROF_INV 12         /* FP64 sweep inverse (G + eps I)^-1 (p = 0 path)        */
 #define RECON_PROF_KINDS 13
 
-/* Enable (1) or disable (0) per-launch event timing on this context; resets the totals. */
-int recon_profile(recon_ctx* c, int enable);
+#define RECON_PROF_ALL ((1u << RECON_PROF_KINDS) - 1u)
+
+/* Time the launch classes whose bit (1u << kind) is set in kind_mask (0 = off,
+ * RECON_PROF_ALL = every class); resets the totals. Only the selected classes pay for the event
+ * records. */
+int recon_profile(recon_ctx* c, unsigned int kind_mask);
 /* Total device milliseconds and launch count of one class since the last recon_profile call
  * (waits for the recorded events). */
 int recon_profile_read(recon_ctx* c, int kind, double* total_ms, long long* launches);

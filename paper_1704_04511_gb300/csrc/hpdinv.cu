@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kB = 16;                       // tile edge
-constexpr long long kSpinLimit = 1LL << 22;  // ~0.4 s of polling before giving up
+constexpr long long kSpinLimit = 1LL << 24;  // ~1 s of polling before giving up
 
 struct GridBar {
     unsigned int count;
@@ -29,16 +29,28 @@ struct GridBar {
     int pad;
 };
 
-// Sense-free generation barrier over gridDim.x co-resident CTAs. Returns false (and sets
-// gb->err) if the wait exceeded kSpinLimit polls; after a failure every later call returns
-// false at once so the kernel can unwind.
+RECON_DEV unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+RECON_DEV int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Generation barrier over gridDim.x co-resident CTAs (cooperative launch). Thread 0 of each CTA
+// arrives with one atomic and then polls the generation word with plain acquire loads. Returns
+// false (and sets gb->err) if the wait exceeded kSpinLimit polls; after a failure every later
+// call returns false at once so the kernel can unwind.
 RECON_DEV bool grid_barrier(GridBar* gb) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = (atomicAdd(&gb->err, 0) == 0);
+        int ok = (ld_acquire(&gb->err) == 0);
         if (ok) {
-            const unsigned int g = atomicAdd(&gb->gen, 0);
+            const unsigned int g = ld_acquire(&gb->gen);
             __threadfence();
             const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
             if (arrived == gridDim.x) {
@@ -47,13 +59,17 @@ RECON_DEV bool grid_barrier(GridBar* gb) {
                 atomicAdd(&gb->gen, 1u);
             } else {
                 long long it = 0;
-                while (atomicAdd(&gb->gen, 0) == g) {
-                    if (++it > kSpinLimit || atomicAdd(&gb->err, 0) != 0) {
+                while (ld_acquire(&gb->gen) == g) {
+                    if (++it > kSpinLimit) {
                         atomicExch(&gb->err, 1);
                         ok = 0;
                         break;
                     }
-                    __nanosleep(64);
+                    if ((it & 1023) == 0 && ld_acquire(&gb->err) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (it > 64) __nanosleep(32);
                 }
             }
             __threadfence();

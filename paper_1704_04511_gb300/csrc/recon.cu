@@ -54,8 +54,8 @@ struct recon_ctx {
     std::string err;
     std::map<int, TwTable> tw;
     std::map<std::string, Buf> bufs;
-    // optional per-launch CUDA-event timing (recon_profile)
-    bool prof = false;
+    // optional per-launch CUDA-event timing (recon_profile): bit k times launch class k
+    unsigned int prof = 0;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, size_t>> prof_pending;  // (kind, index of start event)
@@ -87,7 +87,7 @@ struct ProfScope {
     size_t i0 = 0;
     bool on = false;
     ProfScope(recon_ctx* c_, int kind_) : c(c_), kind(kind_) {
-        if (!c->prof) return;
+        if (!(c->prof & (1u << kind))) return;
         if (c->ev_used + 2 > c->ev_pool.size()) {
             for (int k = 0; k < 256; ++k) {
                 cudaEvent_t e;
@@ -721,14 +721,14 @@ int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, 
     return RECON_OK;
 }
 
-int recon_profile(recon_ctx* c, int enable) {
+int recon_profile(recon_ctx* c, unsigned int kind_mask) {
     if (!c) return RECON_EINVAL;
     prof_collect(c);
     for (int k = 0; k < RECON_PROF_KINDS; ++k) {
         c->prof_ms[k] = 0.0;
         c->prof_n[k] = 0;
     }
-    c->prof = enable != 0;
+    c->prof = kind_mask & ((1u << RECON_PROF_KINDS) - 1u);
     return RECON_OK;
 }
 

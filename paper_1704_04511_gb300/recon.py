@@ -91,7 +91,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_apply_normal": (i, [vp, dims, filt, vp, vp, d, vp, vp]),
             "recon_apply_w": (i, [vp, dims, filt, vp, vp, vp]),
             "recon_cg": (i, [vp, dims, filt, vp, vp, vp, d, vp, vp, i, ctypes.POINTER(d)]),
-            "recon_profile": (i, [vp, i]),
+            "recon_profile": (i, [vp, ctypes.c_uint]),
             "recon_profile_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
             "recon_profile_name": (ctypes.c_char_p, [i]),
         }
@@ -214,8 +214,12 @@ def recon_cg(ctx, masks, filt, S_old, S_new, lam: float, x, r, n_cg: int):
     return list(hist)
 
 
-def recon_profile(ctx, enable: bool) -> None:
-    _check(ctx, load_library().recon_profile(ctx, int(enable)))
+PROF_ALL = (1 << 13) - 1
+
+
+def recon_profile(ctx, kind_mask: int) -> None:
+    """Time the launch classes whose bit is set (0 = off, PROF_ALL = all)."""
+    _check(ctx, load_library().recon_profile(ctx, int(kind_mask) & PROF_ALL))
 
 
 def recon_profile_read(ctx, kind: int):
