@@ -145,6 +145,32 @@ int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
              const void* S_old, const void* S_new, double lambda, void* x, void* r, int n_cg,
              double* rr_hist);
 
+/* ---- Gram matrix without device allocation ----
+ *
+ * Some callers may not allocate device memory once they are running: a reconstruction service
+ * whose device memory is planned when it starts and must not grow, or a program that shares the
+ * GPU with other streams and cannot accept the device-wide synchronisation that cudaMalloc and
+ * cudaFree can cause. recon_gram_static gives them the same Gram matrix and lags as recon_gram
+ * (same kernels) without a context: its scratch (per-block lag partials and twiddle tables)
+ * lives in one fixed device array of RECON_GRAM_STATIC_BYTES inside the library, which every
+ * GPU that loads the library holds until the process exits. The paper has no counterpart; this
+ * is a deployment aid, not part of the method.
+ *  - Arguments as for recon_gram, plus cuda_stream (a cudaStream_t; NULL = the default stream);
+ *    x, G_out, lags_out are device pointers on the current device. The call is synchronous.
+ *  - The first call on each device (with that device current) looks up the array's device
+ *    address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ *    capture.
+ *  - A problem whose scratch exceeds RECON_GRAM_STATIC_BYTES is rejected with RECON_EINVAL and a
+ *    message naming the bytes it needs (recon_last_error(NULL)); use recon_gram for it. The
+ *    256x256x16 series with a 9x9x3 filter needs about 3.6 MB.
+ *  - Every call uses the same array and it keeps the last call's contents; each call writes
+ *    everything it reads first. Calls that overlap on the GPU (other host threads or streams)
+ *    race on the array and must be serialised by the caller.
+ *  - Allocates no device memory (no cudaMalloc / cudaFree or allocating library call). */
+#define RECON_GRAM_STATIC_BYTES (4u * 1024u * 1024u)
+int recon_gram_static(recon_dims d, recon_filter f, const void* x, void* G_out, void* lags_out,
+                      void* cuda_stream);
+
 /* ---- measurement ---- */
 
 /* Launch classes timed by recon_profile (one pair of CUDA events on the context's stream around

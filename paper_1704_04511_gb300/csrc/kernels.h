@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace recon {
 
 // Geometry of one problem: image series [T][P][Q] complex64, filter N1 x N2 x M taps.
@@ -30,6 +32,8 @@ struct Twiddles {
 };
 
 bool fft_size_supported(int n);
+// Message returned by recon_last_error(NULL) (calls that have no context).
+void set_context_free_error(const std::string& msg);
 int w_max_M();
 int w_max_frames_times_q();  // bound on T * Q for the fused row/W kernel
 

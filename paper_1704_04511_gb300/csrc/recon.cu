@@ -44,6 +44,10 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+namespace recon {
+void set_context_free_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace recon
+
 struct recon_ctx {
     int device = 0;
     size_t budget = 0;

@@ -36,7 +36,7 @@ _ERR_NAMES = {RECON_EINVAL: "RECON_EINVAL", RECON_ENOMEM: "RECON_ENOMEM",
 EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_needed",
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
-            "recon_profile_read", "recon_profile_name")
+            "recon_profile_read", "recon_profile_name", "recon_gram_static")
 
 PROF_KINDS = 13
 
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_profile": (i, [vp, ctypes.c_uint]),
             "recon_profile_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
             "recon_profile_name": (ctypes.c_char_p, [i]),
+            "recon_gram_static": (i, [dims, filt, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -184,6 +185,15 @@ def recon_fft2(ctx, x, y, inverse: bool = False) -> None:
 def recon_gram(ctx, x, filt, G_out, lags_out=None) -> None:
     _check(ctx, load_library().recon_gram(ctx, _dims(x), _filt(filt), _ptr(x), _ptr(G_out),
                                           _ptr(lags_out)))
+
+
+def recon_gram_static(x, filt, G_out, lags_out=None, cuda_stream: int | None = None) -> None:
+    """Gram matrix and lags as recon_gram, without a context and without allocating device
+    memory (scratch in a fixed array inside the library; see include/recon.h)."""
+    rc = load_library().recon_gram_static(_dims(x), _filt(filt), _ptr(x), _ptr(G_out),
+                                           _ptr(lags_out),
+                                           ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+    _check(None, rc)
 
 
 def recon_weight(ctx, shape, filt, G_in, eps_in: float, p: float, S_out, dsum_out=None,

@@ -1,0 +1,63 @@
+"""recon_gram_static, the Gram entry point that allocates no device memory, against recon_gram.
+
+A reconstruction service with a device-memory plan fixed at start-up, or a program sharing the
+GPU that must avoid the device-wide synchronisation of cudaMalloc / cudaFree, cannot use the
+context's growing workspace; recon_gram_static keeps its scratch in a fixed array inside the
+library instead. Through the C ABI, two calls in a row (different problems, then the first one
+again) must each reproduce the allocating entry point's G and lags within the Gram tolerance of
+the parity tests (1e-5 relative Frobenius). Runs alone in a fresh process or after the others.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+GRAM_TOL = 1e-5
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _gram_both(recon, ctx, x, filt):
+    N1, N2, M = filt
+    s, npair = N1 * N2 * M, M * (M + 1) // 2
+    shape_l = (npair, 2 * N1 - 1, 2 * N2 - 1)
+    G_ref = torch.empty((s, s), dtype=torch.complex128, device="cuda")
+    l_ref = torch.empty(shape_l, dtype=torch.complex128, device="cuda")
+    G_st = torch.full((s, s), float("nan"), dtype=torch.complex128, device="cuda")
+    l_st = torch.full(shape_l, float("nan"), dtype=torch.complex128, device="cuda")
+    recon.recon_gram(ctx.h, x, filt, G_ref, l_ref)
+    recon.recon_gram_static(x, filt, G_st, l_st)
+    return (G_st.cpu().numpy(), G_ref.cpu().numpy(), l_st.cpu().numpy(), l_ref.cpu().numpy())
+
+
+def test_gram_static_matches_gram_on_consecutive_calls():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_04511_gb300 import recon
+    ctx = recon.Context(0)
+    try:
+        rng = np.random.default_rng(2024)
+        cases = [((16, 256, 256), (9, 9, 3)), ((8, 32, 64), (5, 3, 2))]
+        xs = []
+        for (T, P, Q), filt in cases:
+            x = (rng.standard_normal((T, P, Q)) + 1j * rng.standard_normal((T, P, Q))).astype(np.complex64)
+            xs.append((torch.from_numpy(x).cuda(), filt))
+        for x, filt in xs + xs[:1]:
+            G_st, G_ref, l_st, l_ref = _gram_both(recon, ctx, x, filt)
+            assert np.isfinite(G_st).all() and np.isfinite(l_st).all()
+            assert _rel(G_st, G_ref) < GRAM_TOL
+            assert _rel(l_st, l_ref) < GRAM_TOL
+        # a problem whose scratch exceeds the fixed array is refused with a clear message
+        x = torch.zeros((8, 32, 32), dtype=torch.complex64, device="cuda")
+        G = torch.zeros((15 * 15 * 6, 15 * 15 * 6), dtype=torch.complex128, device="cuda")
+        with pytest.raises(recon.ReconError) as e:
+            recon.recon_gram_static(x, (15, 15, 6), G)
+        assert e.value.code == recon.RECON_EINVAL
+        assert "RECON_GRAM_STATIC_BYTES" in str(e.value)
+    finally:
+        ctx.close()
