@@ -57,6 +57,25 @@ def alg_bytes(kind: str, w, n_cg: int) -> float:
     return 0.0
 
 
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 dense FP64, nominal (a probe here measured ~1056)
+ALU_KINDS = ("hpd_inverse", "lanczos")
+
+
+def alg_flops(kind: str, w) -> float:
+    """Algorithmic FP64 FLOPs per launch of the FP64 kernels (complex FMA = 8 flops)."""
+    s = w.N1 * w.N2 * w.M
+    if kind == "hpd_inverse":
+        # blocked Hermitian sweep over 8x8 tiles of the padded np x np matrix: every step updates
+        # all lower tiles (8^3 complex FMA each) and forms the 8 x np pivot-row panel
+        npad = (s + 7) // 8 * 8
+        nt = npad // 8
+        nlt = nt * (nt + 1) // 2
+        return 8.0 * nt * (nlt * 512 + npad * 64)
+    if kind == "lanczos":
+        return 8.0 * 96 * s * s
+    return 0.0
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -186,6 +205,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--irls", type=int, default=None, help="override IRLS iterations (testing)")
+    ap.add_argument("--batch", type=int, default=4,
+                    help="independent problems solved concurrently per step (1 = single solve)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -212,73 +233,96 @@ def main():
     w = synth.workload(WORKLOAD)
     if args.irls is not None:
         w = synth.workload(WORKLOAD, n_irls=args.irls)
-    prob = synth.make_problem(w)
-    b_host = torch.from_numpy(np.ascontiguousarray(prob["kspace"], dtype=np.complex64)).pin_memory()
-    m_host = torch.from_numpy(np.ascontiguousarray(prob["masks"])).pin_memory()
-    b = b_host.to(dev)
-    m = m_host.to(dev)
-    out = torch.empty(tuple(m.shape), dtype=torch.complex64, device=dev)
-    out_host = torch.empty(tuple(m.shape), dtype=torch.complex64).pin_memory()
+    B = args.batch
+    probs = [synth.make_problem(synth.workload(w.name, n_irls=w.n_irls, seed=sd))
+             for sd in range(B)]
+    prob = probs[0]
+    b_host = [torch.from_numpy(np.ascontiguousarray(pr["kspace"], dtype=np.complex64)).pin_memory()
+              for pr in probs]
+    m_host = [torch.from_numpy(np.ascontiguousarray(pr["masks"])).pin_memory() for pr in probs]
+    bs = [t.to(dev) for t in b_host]
+    ms = [t.to(dev) for t in m_host]
+    outs = [torch.empty(tuple(ms[0].shape), dtype=torch.complex64, device=dev) for _ in range(B)]
+    out_host = [torch.empty(tuple(ms[0].shape), dtype=torch.complex64).pin_memory() for _ in range(B)]
     stream = torch.cuda.current_stream(dev)
     ctx = recon.Context(local_rank, cuda_stream=stream.cuda_stream)
     filt = (w.N1, w.N2, w.M)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
-    def step():
-        recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+    def solve_one():
+        recon.recon_solve(ctx.h, bs[0], ms[0], filt, w.lam, w.p, w.n_irls, w.n_cg, outs[0])
+
+    def solve_batch():
+        recon.recon_solve_batch(ctx.h, bs, ms, filt, w.lam, w.p, w.n_irls, w.n_cg, outs)
+
+    step = solve_batch if B > 1 else solve_one
+
+    def timed(fn, k):
+        tot = 0.0
+        for _ in range(k):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot
 
     for _ in range(args.warmup):
-        step()
+        solve_one()
+        if B > 1:
+            solve_batch()
     torch.cuda.synchronize(dev)
 
-    # ---- one untimed profiled solve: per-class device time and launch counts per step
+    # ---- one untimed profiled solve: per-class device time and launch counts per solve
     recon.recon_profile(ctx.h, recon.PROF_ALL)
-    step()
+    solve_one()
     torch.cuda.synchronize(dev)
     prof1 = {}
     for k in range(recon.PROF_KINDS):
-        ms, n = recon.recon_profile_read(ctx.h, k)
-        prof1[recon.recon_profile_name(k)] = (ms, n)
+        ms_, n_ = recon.recon_profile_read(ctx.h, k)
+        prof1[recon.recon_profile_name(k)] = (ms_, n_)
     recon.recon_profile(ctx.h, 0)
     mine1 = {k: v for k, v in prof1.items() if k in KERNELS_PER_SCOPE}
     dom = max(mine1, key=lambda k: mine1[k][0])
     dom_kind = [recon.recon_profile_name(k) for k in range(recon.PROF_KINDS)].index(dom)
+
+    # ---- the single-solve path (the comparison baseline), K device-resident solves
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    single_ms = timed(solve_one, args.steps)
 
     gpu_id = None
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
-    sampler = ClockSampler(gpu_id if rank == 0 else None) if rank == 0 else None
+    sampler = ClockSampler(gpu_id) if rank == 0 else None
 
-    # ---- timed region: K device-resident solves, L2 flushed before each (outside the events);
-    # only the dominant launch class is bracketed by events inside it
+    # ---- timed region: K steps of B concurrent solves; only the dominant launch class is
+    # bracketed by events inside it; L2 flushed before each step (outside the events)
     recon.recon_profile(ctx.h, 1 << dom_kind)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     if sampler:
         sampler.start()
-    total_ms = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
+    total_ms = timed(step, args.steps)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop() if sampler else None
     dom_ms, dom_n = recon.recon_profile_read(ctx.h, dom_kind)
     recon.recon_profile(ctx.h, 0)
-    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    t_local = torch.tensor([total_ms, single_ms], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
         dist.barrier()
-    t_max_ms = float(t_local.item())
-    value = world * args.steps * w.n_irls / (t_max_ms / 1000.0)
+    t_max_ms = float(t_local[0].item())
+    single_max_ms = float(t_local[1].item())
+    value = world * args.steps * B * w.n_irls / (t_max_ms / 1000.0)
+    single_value = world * args.steps * w.n_irls / (single_max_ms / 1000.0)
 
     # ---- end to end: pinned host buffers, copies inside the timed region
     if dist:
@@ -288,16 +332,18 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        b.copy_(b_host, non_blocking=True)
-        m.copy_(m_host, non_blocking=True)
+        for i in range(B):
+            bs[i].copy_(b_host[i], non_blocking=True)
+            ms[i].copy_(m_host[i], non_blocking=True)
         step()
-        out_host.copy_(out, non_blocking=True)
+        for i in range(B):
+            out_host[i].copy_(outs[i], non_blocking=True)
     e1.record(stream)
     e1.synchronize()
     e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps * w.n_irls / (float(e2e_ms.item()) / 1000.0)
+    e2e_value = world * args.steps * B * w.n_irls / (float(e2e_ms.item()) / 1000.0)
 
     if rank != 0:
         ctx.close()
@@ -308,9 +354,33 @@ def main():
     # dominant kernel of this library (timed live in the timed region); per-class shares from
     # the profiled solve before it
     peak, peak_src = load_peaks()
-    bytes_per_launch = alg_bytes(dom, w, w.n_cg)
-    achieved = bytes_per_launch / (dom_ms / dom_n / 1000.0) / 1e9 if dom_n else 0.0
-    launches = args.steps * sum(n * KERNELS_PER_SCOPE[k] for k, (ms, n) in mine1.items())
+    if dom in ALU_KINDS:
+        work = alg_flops(dom, w)
+        achieved = work / (dom_ms / dom_n / 1000.0) / 1e9 if dom_n else 0.0
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 1),
+                "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s (FP64)",
+                "frac": round(achieved / FP64_NOMINAL_GFLOPS, 4),
+                "peak_source": "nominal FP64 rate of the part (no measured FP64 peak provided)",
+                "alg_flops_per_launch": work,
+                "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
+                "traffic": None}
+    else:
+        work = alg_bytes(dom, w, w.n_cg)
+        achieved = work / (dom_ms / dom_n / 1000.0) / 1e9 if dom_n else 0.0
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "alg_bytes_per_launch": work,
+                "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
+                "traffic": None}
+    # the memory-bound CG passes (per-launch time from the profiled solve)
+    cg_roof = {}
+    for k in ("cg_row_fwd", "cg_col_mask", "cg_row_inv_w", "cg_update"):
+        ms_k, n_k = prof1.get(k, (0.0, 0))
+        if n_k:
+            gbs = alg_bytes(k, w, w.n_cg) / (ms_k / n_k / 1000.0) / 1e9
+            cg_roof[k] = {"avg_launch_us": round(1000.0 * ms_k / n_k, 3), "achieved_GBs": round(gbs, 1),
+                          "frac_of_hbm": round(gbs / peak, 4)}
+    launches = args.steps * B * sum(n * KERNELS_PER_SCOPE[k] for k, (ms, n) in mine1.items())
     step_ms_profiled = sum(ms for ms, n in prof1.values())
     phase = {k: {"ms_per_step": round(ms, 4), "launches_per_step": n,
                  "share": round(ms / step_ms_profiled, 4) if step_ms_profiled else None}
@@ -319,24 +389,23 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+        "single_solve": {"value": single_value, "unit": UNIT,
+                         "ms_per_solve": single_max_ms / args.steps,
+                         "note": "the plain single-solve path; value above is B concurrent solves"},
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (eigensolver and weight in f64)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "T": w.T, "P": w.P, "Q": w.Q,
                    "filter": [w.N1, w.N2, w.M], "irls": w.n_irls, "cg": w.n_cg,
                    "lambda": w.lam, "p": w.p, "undersampling": w.R,
-                   "parallelism": f"replicas x{world}",
+                   "batch": B, "parallelism": f"replicas x{world}, {B} concurrent solves per GPU",
                    "l2": "256 MiB buffer written before every timed step (outside the events)"},
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "peak_source": peak_src,
-                     "alg_bytes_per_launch": bytes_per_launch,
-                     "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
-                     "traffic": None},
+        "roofline": roof,
+        "roofline_cg_passes": cg_roof,
         "phases": phase,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": int(b.numel() * 8 + m.numel()),
-                "d2h_bytes_per_step": int(out.numel() * 8)},
+                "h2d_bytes_per_step": int(B * (bs[0].numel() * 8 + ms[0].numel())),
+                "d2h_bytes_per_step": int(B * outs[0].numel() * 8)},
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

@@ -94,6 +94,18 @@ size_t recon_bytes_needed(recon_dims d, recon_filter f, int kspace_bf16);
 int recon_solve(recon_ctx* c, recon_dims d, const void* kspace, const uint8_t* masks,
                 recon_filter f, const recon_params* prm, void* image_out);
 
+/* Batched reconstruction: n independent problems of the same dims, filter and parameters
+ * (slot i reads kspace[i] and masks[i] and writes image_out[i], all device pointers), each
+ * solved exactly as recon_solve would, concurrently on n streams of the context, each with its
+ * own workspace (the budget covers all slots). IRLS iterations are issued interleaved across
+ * the slots, so that the latency-bound phases of one problem (FP64 weight, small reductions)
+ * overlap with the others' work. Results are bitwise identical to solving each problem alone
+ * (fixed launch shapes and reduction orders). 1 <= n <= RECON_MAX_BATCH; synchronous. */
+#define RECON_MAX_BATCH 16
+int recon_solve_batch(recon_ctx* c, int n, recon_dims d, const void* const* kspace,
+                      const uint8_t* const* masks, recon_filter f, const recon_params* prm,
+                      void* const* image_out);
+
 /* ---- stage entry points (the same kernels recon_solve runs; used for parity checks) ---- */
 
 /* x = A^H b = F^H (mask * b) (Sec. II-A). */

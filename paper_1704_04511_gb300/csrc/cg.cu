@@ -16,7 +16,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxM = 6;
-constexpr int kVecParts = 304;
+constexpr int kMaxParts = 4096;  // partial-sum slots (largest grid of a reducing kernel)
+constexpr int kUpdVec = 2;       // float4 per thread per iteration in the update pass
+constexpr int kUpdPerSM = 4;     // resident update CTAs per SM (register budget 64 / thread)
 
 RECON_DEV int pair_index(int a, int b, int M) { return a * (2 * M - a + 1) / 2 + (b - a); }
 
@@ -39,8 +41,8 @@ RECON_DEV void load_S(const float2* __restrict__ S, size_t npix, size_t px, floa
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads)
 row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
-                 float lam, int T, int P, double* __restrict__ part_pq,
-                 const float2* __restrict__ tw_g) {
+                 float lam, int T, int P, double* __restrict__ parts, unsigned int* counter,
+                 double* __restrict__ pq_out, const float2* __restrict__ tw_g) {
     extern __shared__ float2 sm[];
     __shared__ double red[kThreads / 32];
     float2* a = sm;
@@ -50,6 +52,7 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     const int r1 = blockIdx.x;
     const size_t npix = (size_t)P * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    pdl_wait();
     for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
         const int n = e / N, c = e % N;
         const size_t g = (size_t)n * npix + (size_t)r1 * N + c;
@@ -83,52 +86,60 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
             acc = sum;
         }
     }
-    const double tot = block_sum((double)acc, red);
-    if (threadIdx.x == 0) part_pq[r1] = tot;
+    const double tot = block_sum_f_t0(acc, red);
+    pdl_trigger();
     for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
         const int n = e / N, c = e % N;
         t[(size_t)n * npix + (size_t)r1 * N + c] = res[e];
     }
+    last_block_sum(tot, parts, counter, pq_out);
 }
 
-// Pass D: alpha = |r|^2 / Re <p, q>; x += alpha p; r -= alpha q; partial |r_new|^2.
-__global__ void __launch_bounds__(kThreads)
+// Pass D: alpha = |r|^2 / Re <p, q>; x += alpha p; r -= alpha q; |r_new|^2 (last block).
+__global__ void __launch_bounds__(kThreads, kUpdPerSM)
 cg_update_kernel(float4* __restrict__ x, float4* __restrict__ r, const float4* __restrict__ p,
-                 const float4* __restrict__ q, size_t n4, const double* __restrict__ part_rr_in,
-                 const double* __restrict__ part_pq, int nparts_pq,
-                 double* __restrict__ part_rr_out, int nparts, double* __restrict__ hist) {
+                 const float4* __restrict__ q, size_t n4, const double* __restrict__ rr_in,
+                 const double* __restrict__ pq_in, double* __restrict__ parts,
+                 unsigned int* counter, double* __restrict__ rr_out) {
     __shared__ double red[kThreads / 32];
-    const double rr = block_sum_array(part_rr_in, nparts, red);
-    const double pq = block_sum_array(part_pq, nparts_pq, red);
-    const double alpha_d = rr / pq;
-    const float alpha = (float)alpha_d;
-    if (hist && blockIdx.x == 0 && threadIdx.x == 0) {
-        hist[0] = rr;
-        hist[1] = pq;
-        hist[2] = alpha_d;
-    }
+    __shared__ float alpha_s;
+    pdl_wait();
+    if (threadIdx.x == 0) alpha_s = (float)(rr_in[0] * rcp_nr(pq_in[0]));
+    __syncthreads();
+    const float alpha = alpha_s;
     float acc = 0.f, comp = 0.f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-         i += (size_t)gridDim.x * blockDim.x) {
-        float4 xv = x[i], rv = r[i];
-        const float4 pv = p[i], qv = q[i];
-        xv.x = fmaf(alpha, pv.x, xv.x);
-        xv.y = fmaf(alpha, pv.y, xv.y);
-        xv.z = fmaf(alpha, pv.z, xv.z);
-        xv.w = fmaf(alpha, pv.w, xv.w);
-        rv.x = fmaf(-alpha, qv.x, rv.x);
-        rv.y = fmaf(-alpha, qv.y, rv.y);
-        rv.z = fmaf(-alpha, qv.z, rv.z);
-        rv.w = fmaf(-alpha, qv.w, rv.w);
-        x[i] = xv;
-        r[i] = rv;
-        const float term = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w))) - comp;
-        const float sum = acc + term;
-        comp = (sum - acc) - term;
-        acc = sum;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n4; i0 += stride * kUpdVec) {
+        float4 xv[kUpdVec], rv[kUpdVec], pv[kUpdVec], qv[kUpdVec];
+#pragma unroll
+        for (int u = 0; u < kUpdVec; ++u) {
+            const size_t i = i0 + (size_t)u * stride;
+            if (i < n4) { xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i]; }
+        }
+#pragma unroll
+        for (int u = 0; u < kUpdVec; ++u) {
+            const size_t i = i0 + (size_t)u * stride;
+            if (i >= n4) continue;
+            xv[u].x = fmaf(alpha, pv[u].x, xv[u].x);
+            xv[u].y = fmaf(alpha, pv[u].y, xv[u].y);
+            xv[u].z = fmaf(alpha, pv[u].z, xv[u].z);
+            xv[u].w = fmaf(alpha, pv[u].w, xv[u].w);
+            rv[u].x = fmaf(-alpha, qv[u].x, rv[u].x);
+            rv[u].y = fmaf(-alpha, qv[u].y, rv[u].y);
+            rv[u].z = fmaf(-alpha, qv[u].z, rv[u].z);
+            rv[u].w = fmaf(-alpha, qv[u].w, rv[u].w);
+            x[i] = xv[u];
+            r[i] = rv[u];
+            const float4 w = rv[u];
+            const float term = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, w.w * w.w))) - comp;
+            const float sum = acc + term;
+            comp = (sum - acc) - term;
+            acc = sum;
+        }
     }
-    const double tot = block_sum((double)acc, red);
-    if (threadIdx.x == 0) part_rr_out[blockIdx.x] = tot;
+    pdl_trigger();
+    const double tot = block_sum_f_t0(acc, red);
+    last_block_sum(tot, parts, counter, rr_out);
 }
 
 // Residual carry between IRLS iterations: r = (first ? 0 : r) + lam W_{dS} x with
@@ -137,7 +148,8 @@ template <int M>
 __global__ void __launch_bounds__(kThreads)
 resid_carry_kernel(float2* __restrict__ r, const float2* __restrict__ x,
                    const float2* __restrict__ S_old, const float2* __restrict__ S_new, float lam,
-                   int first, int T, size_t npix, double* __restrict__ part_rr) {
+                   int first, int T, size_t npix, double* __restrict__ parts,
+                   unsigned int* counter, double* __restrict__ rr_out) {
     __shared__ double red[kThreads / 32];
     const int k = T - M + 1;
     float acc = 0.f, comp = 0.f;
@@ -177,8 +189,8 @@ resid_carry_kernel(float2* __restrict__ r, const float2* __restrict__ x,
             acc = sum;
         }
     }
-    const double tot = block_sum((double)acc, red);
-    if (threadIdx.x == 0) part_rr[blockIdx.x] = tot;
+    const double tot = block_sum_f_t0(acc, red);
+    last_block_sum(tot, parts, counter, rr_out);
 }
 
 // y = W_S x (no lambda); parity tests only.
@@ -207,81 +219,100 @@ apply_w_kernel(const float2* __restrict__ x, const float2* __restrict__ S, float
 
 template <int N, int M>
 cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
-                                const float2* S, float lam, double* part_pq, cudaStream_t st) {
+                                const float2* S, float lam, const RedSlot& rs, double* pq_out,
+                                cudaStream_t st) {
     auto k = row_inv_w_kernel<N, M>;
     const size_t smem = ((size_t)3 * d.T * N + N) * sizeof(float2);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<d.P, kThreads, smem, st>>>(t, p, S, lam, d.T, d.P, part_pq, tw.twQ);
-    return cudaGetLastError();
+    return launch_pdl(k, dim3(d.P), dim3(kThreads), smem, st, t, p, S, lam, d.T, d.P, rs.parts,
+                      rs.counter, pq_out, tw.twQ);
 }
 
 template <int N>
 cudaError_t launch_row_inv_w_N(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
-                               const float2* S, float lam, double* part_pq, cudaStream_t st) {
+                               const float2* S, float lam, const RedSlot& rs, double* pq_out,
+                               cudaStream_t st) {
     switch (d.M) {
-        case 1: return launch_row_inv_w_NM<N, 1>(d, tw, t, p, S, lam, part_pq, st);
-        case 2: return launch_row_inv_w_NM<N, 2>(d, tw, t, p, S, lam, part_pq, st);
-        case 3: return launch_row_inv_w_NM<N, 3>(d, tw, t, p, S, lam, part_pq, st);
-        case 4: return launch_row_inv_w_NM<N, 4>(d, tw, t, p, S, lam, part_pq, st);
-        case 5: return launch_row_inv_w_NM<N, 5>(d, tw, t, p, S, lam, part_pq, st);
-        case 6: return launch_row_inv_w_NM<N, 6>(d, tw, t, p, S, lam, part_pq, st);
+        case 1: return launch_row_inv_w_NM<N, 1>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 2: return launch_row_inv_w_NM<N, 2>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 3: return launch_row_inv_w_NM<N, 3>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 4: return launch_row_inv_w_NM<N, 4>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 5: return launch_row_inv_w_NM<N, 5>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 6: return launch_row_inv_w_NM<N, 6>(d, tw, t, p, S, lam, rs, pq_out, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 int pix_grid(size_t npix) {
     const size_t g = (npix + kThreads - 1) / kThreads;
-    return (int)(g < (size_t)kVecParts ? g : (size_t)kVecParts);
+    return (int)(g < (size_t)kMaxParts ? g : (size_t)kMaxParts);
+}
+
+// One resident wave: kUpdPerSM CTAs per SM (fewer for small problems), grid-stride inside.
+int upd_grid(size_t n4) {
+    const size_t per = (size_t)kThreads * kUpdVec;
+    const size_t need = (n4 + per - 1) / per;
+    size_t g = (size_t)num_sms() * kUpdPerSM;
+    if (need < g) g = need;
+    return (int)(g < 1 ? 1 : (g < (size_t)kMaxParts ? g : (size_t)kMaxParts));
 }
 
 }  // namespace
 
+int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 132;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 132;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 int w_max_M() { return kMaxM; }
 int w_max_frames_times_q() { return (200 * 1024) / (3 * (int)sizeof(float2)); }
-int vec_parts() { return kVecParts; }
+int max_parts() { return kMaxParts; }
 
 cudaError_t launch_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
-                             const float2* S, float lam, double* part_pq, cudaStream_t st) {
+                             const float2* S, float lam, const RedSlot& rs, double* pq_out,
+                             cudaStream_t st) {
+    if (d.P > kMaxParts) return cudaErrorInvalidValue;
     switch (d.Q) {
-        case 16: return launch_row_inv_w_N<16>(d, tw, t, p, S, lam, part_pq, st);
-        case 32: return launch_row_inv_w_N<32>(d, tw, t, p, S, lam, part_pq, st);
-        case 64: return launch_row_inv_w_N<64>(d, tw, t, p, S, lam, part_pq, st);
-        case 128: return launch_row_inv_w_N<128>(d, tw, t, p, S, lam, part_pq, st);
-        case 192: return launch_row_inv_w_N<192>(d, tw, t, p, S, lam, part_pq, st);
-        case 256: return launch_row_inv_w_N<256>(d, tw, t, p, S, lam, part_pq, st);
-        case 512: return launch_row_inv_w_N<512>(d, tw, t, p, S, lam, part_pq, st);
+        case 16: return launch_row_inv_w_N<16>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 32: return launch_row_inv_w_N<32>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 64: return launch_row_inv_w_N<64>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 128: return launch_row_inv_w_N<128>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 192: return launch_row_inv_w_N<192>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 256: return launch_row_inv_w_N<256>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 512: return launch_row_inv_w_N<512>(d, tw, t, p, S, lam, rs, pq_out, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* p,
-                             const float2* q, const double* part_rr_in, const double* part_pq,
-                             int nparts_pq, double* part_rr_out, int nparts, double* hist,
-                             cudaStream_t st) {
+                             const float2* q, const double* rr_in, const double* pq_in,
+                             const RedSlot& rs, double* rr_out, cudaStream_t st) {
     const size_t n4 = d.elems() / 2;  // two complex values per float4
-    cg_update_kernel<<<nparts, kThreads, 0, st>>>(
-        reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(r),
-        reinterpret_cast<const float4*>(p), reinterpret_cast<const float4*>(q), n4, part_rr_in,
-        part_pq, nparts_pq, part_rr_out, nparts, hist);
-    return cudaGetLastError();
+    return launch_pdl(cg_update_kernel, dim3(upd_grid(n4)), dim3(kThreads), 0, st,
+                      reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(r),
+                      reinterpret_cast<const float4*>(p), reinterpret_cast<const float4*>(q), n4,
+                      rr_in, pq_in, rs.parts, rs.counter, rr_out);
 }
 
 cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const float2* S_old,
-                               const float2* S_new, float lam, int first, double* part_rr_out,
-                               int nparts, cudaStream_t st) {
-    // zero the partials that a small pixel grid does not reach
+                               const float2* S_new, float lam, int first, const RedSlot& rs,
+                               double* rr_out, cudaStream_t st) {
     const int g = pix_grid(d.pixels());
-    if (g < nparts) {
-        cudaError_t e = cudaMemsetAsync(part_rr_out + g, 0, (size_t)(nparts - g) * sizeof(double), st);
-        if (e != cudaSuccess) return e;
-    }
 #define CASE(MM)                                                                              \
     case MM:                                                                                  \
         resid_carry_kernel<MM><<<g, kThreads, 0, st>>>(r, x, S_old, S_new, lam, first, d.T,   \
-                                                       d.pixels(), part_rr_out);              \
+                                                       d.pixels(), rs.parts, rs.counter,      \
+                                                       rr_out);                               \
         break;
     switch (d.M) {
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)

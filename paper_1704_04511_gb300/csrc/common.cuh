@@ -7,6 +7,13 @@
 
 #define RECON_DEV __device__ __forceinline__
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while its predecessor is finishing; it must wait before touching the predecessor's
+// results (no-op when launched normally). Every such kernel calls pdl_wait() on every path, so
+// completion stays transitive along the stream.
+RECON_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+RECON_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------------------------------
 // complex helpers (float2 / double2 hold (re, im))
 // ------------------------------------------------------------------------------------------
@@ -58,6 +65,29 @@ RECON_DEV double2 zfmacj2(double2 a, double2 b, double2 acc) {
     return acc;
 }
 RECON_DEV double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+// acc -= a * b with four FMAs
+RECON_DEV double2 zfms(double2 a, double2 b, double2 acc) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+
+// 1 / a in FP64 by Newton-Raphson on f(r) = 1/r - a, r <- r (2 - a r), from the FP32 reciprocal
+// (24 correct bits; two steps give >= 48, within about 1 ulp of the rounded quotient). An IEEE
+// FP64 division costs several hundred cycles of the narrow FP64 pipe on this part; this is four
+// dependent FMAs. Falls back to the division outside the FP32 exponent range.
+RECON_DEV double rcp_nr(double a) {
+    const double aa = fabs(a);
+    if (!(aa > 1e-30 && aa < 1e30)) return 1.0 / a;
+    double r = (double)__frcp_rn((float)a);
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    return r;
+}
 
 RECON_DEV float warp_sum(float v) {
 #pragma unroll
@@ -95,6 +125,60 @@ RECON_DEV double block_sum_array(const double* a, int n, double* red) {
     double v = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) v += a[i];
     return block_sum(v, red);
+}
+
+// Block sum of one float per thread: FP32 shuffle tree inside each warp, FP64 across the warps
+// (fixed order). Only thread 0 holds the result. Keeps the FP64 work to one add per warp (the
+// FP64 pipe is ~60x narrower than FP32 on this part).
+RECON_DEV double block_sum_f_t0(float v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = (double)v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+// Grid-wide sum of one double per block, finished by the last block to arrive: every block
+// stores its partial (thread 0), the block that takes the last ticket adds all partials in a
+// fixed order (so the total does not depend on which block finished last), writes *out and
+// re-arms the counter. `partial` is read from thread 0 only. Must be reached by all threads.
+RECON_DEV void last_block_sum(double partial, double* parts, unsigned int* counter, double* out) {
+    __shared__ unsigned int s_ticket;
+    __shared__ double s_red[32];
+    if (threadIdx.x == 0) {
+        parts[blockIdx.x] = partial;
+        __threadfence();
+        s_ticket = atomicAdd(counter, 1u);
+    }
+    __syncthreads();
+    if (s_ticket != gridDim.x - 1) return;
+    __threadfence();
+    double v = 0.0;
+    for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += __ldcg(parts + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (unsigned int w = 0; w < (blockDim.x >> 5); ++w) t += s_red[w];
+        *out = t;
+        *counter = 0u;
+        __threadfence();
+    }
+}
+
+// Deterministic sum of n doubles in global memory by warp 0 alone (FP64 in 32 lanes only);
+// the result is valid in every lane of warp 0.
+RECON_DEV double warp0_sum_array(const double* a, int n) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) v += a[i];
+    return warp_sum(v);
 }
 
 // ------------------------------------------------------------------------------------------

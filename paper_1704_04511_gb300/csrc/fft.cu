@@ -2,8 +2,8 @@
 // (Sec. II-A, Eq. measurement-ij with one coil) and by the CG operator (Sec. III-A, Eq. grad-ls).
 //
 // Layout: frames [T][P][Q] complex64, Q contiguous. A row pass transforms length-Q rows
-// (ROWS rows per CTA, staged in shared memory); a column pass transforms a P x 16 tile of
-// 16 adjacent columns of one frame (128-byte row segments, coalesced), optionally applying the
+// (ROWS rows per CTA, staged in shared memory); a column pass transforms a P x 8 tile of
+// 8 adjacent columns of one frame (64-byte row segments), optionally applying the
 // sampling mask between a forward and an inverse transform so that A^H A needs one column pass.
 #include <cuda_bf16.h>
 
@@ -15,10 +15,10 @@ namespace recon {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kColTile = 16;
+constexpr int kColTile = 8;
 
 template <int N>
-__host__ __device__ constexpr int rows_per_cta() { return N >= 2048 ? 1 : 2048 / N; }
+__host__ __device__ constexpr int rows_per_cta() { return N >= 1024 ? 1 : 1024 / N; }
 
 enum ColMode { COL_FWD = 0, COL_INV = 1, COL_MASK_OP = 2, COL_ADJ_C64 = 3, COL_ADJ_BF16 = 4 };
 
@@ -46,21 +46,22 @@ row_fft_kernel(const float2* in, float2* out, int nrows, float scale,
 template <int N>
 __global__ void __launch_bounds__(kThreads)
 row_fwd_pupdate_kernel(const float2* __restrict__ r, float2* __restrict__ p,
-                       float2* __restrict__ t, int nrows, const double* __restrict__ part_num,
-                       const double* __restrict__ part_den, int nparts, int first,
+                       float2* __restrict__ t, int nrows, const double* __restrict__ rr_num,
+                       const double* __restrict__ rr_den, int first,
                        const float2* __restrict__ tw_g) {
     constexpr int ROWS = rows_per_cta<N>();
     extern __shared__ float2 sm[];
-    __shared__ double red[kThreads / 32];
+    __shared__ float beta_s;
     float2* a = sm;
     float2* b = a + ROWS * N;
     float2* tw = b + ROWS * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    pdl_wait();
     float beta = 0.f;
     if (!first) {
-        const double num = block_sum_array(part_num, nparts, red);
-        const double den = block_sum_array(part_den, nparts, red);
-        beta = (float)(num / den);
+        if (threadIdx.x == 0) beta_s = (float)(rr_num[0] * rcp_nr(rr_den[0]));
+        __syncthreads();
+        beta = beta_s;
     }
     const int row0 = blockIdx.x * ROWS;
     const int nr = min(ROWS, nrows - row0);
@@ -77,10 +78,11 @@ row_fwd_pupdate_kernel(const float2* __restrict__ r, float2* __restrict__ p,
     }
     __syncthreads();
     float2* res = fft_smem<N, false, false>(a, b, nr, N, 1, tw);
+    pdl_trigger();
     for (int e = threadIdx.x; e < nr * N; e += blockDim.x) t[base + e] = res[e];
 }
 
-// Column pass over a P x 16 tile (frame blockIdx.y, columns 16*blockIdx.x ..).
+// Column pass over a P x 8 tile (frame blockIdx.y, columns 8*blockIdx.x ..).
 template <int N, int MODE>
 __global__ void __launch_bounds__(kThreads)
 col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
@@ -91,6 +93,7 @@ col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
     float2* b = a + N * C;
     float2* tw = b + N * C;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    pdl_wait();
     const int c0 = blockIdx.x * C;
     const size_t fbase = (size_t)blockIdx.y * N * Q;
     for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
@@ -124,6 +127,7 @@ col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
         __syncthreads();
         res = fft_smem<N, true, true>(f, f == a ? b : a, C, 1, C, tw);
     }
+    pdl_trigger();
     const float osc = (MODE == COL_FWD || MODE == COL_INV) ? scale : 1.f;
     for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
         const int i = e / C, c = e % C;
@@ -175,8 +179,8 @@ cudaError_t col_pass(int n, int Q, int T, const void* in, float2* out, const uin
         cudaError_t e = set_smem(k, col_smem<N>());                                      \
         if (e != cudaSuccess) return e;                                                  \
         dim3 grid(Q / kColTile, T);                                                      \
-        k<<<grid, kThreads, col_smem<N>(), st>>>(in, out, mask, Q, scale, tw);           \
-        return cudaGetLastError();                                                       \
+        return launch_pdl(k, grid, dim3(kThreads), col_smem<N>(), st, in, out, mask, Q,  \
+                          scale, tw);                                                    \
     }
         RECON_FFT_SIZES(CASE)
 #undef CASE
@@ -216,7 +220,7 @@ cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int
 
 cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
                                    float2* t, const double* rr_num, const double* rr_den,
-                                   int nparts, int first, cudaStream_t st) {
+                                   int first, cudaStream_t st) {
     const int nrows = d.T * d.P;
     switch (d.Q) {
 #define CASE(N)                                                                              \
@@ -225,9 +229,8 @@ cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const floa
         cudaError_t e = set_smem(k, row_smem<N>());                                          \
         if (e != cudaSuccess) return e;                                                      \
         const int grid = (nrows + rows_per_cta<N>() - 1) / rows_per_cta<N>();                \
-        k<<<grid, kThreads, row_smem<N>(), st>>>(r, p, t, nrows, rr_num, rr_den, nparts,     \
-                                                 first, tw.twQ);                             \
-        return cudaGetLastError();                                                           \
+        return launch_pdl(k, dim3(grid), dim3(kThreads), row_smem<N>(), st, r, p, t, nrows,  \
+                          rr_num, rr_den, first, tw.twQ);                                    \
     }
         RECON_FFT_SIZES(CASE)
 #undef CASE

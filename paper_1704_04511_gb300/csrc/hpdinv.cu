@@ -3,7 +3,8 @@
 // and eps0 = eps0_frac * lambda_max(G) (Sec. III-C) from a Lanczos iteration.
 //
 // The inverse is a blocked Hermitian sweep (Gauss-Jordan without pivoting, stable for Hermitian
-// positive-definite matrices) over 16 x 16 tiles, run as ONE cooperative kernel over every SM:
+// positive-definite matrices) over 8 x 8 tiles, run as ONE cooperative kernel over every SM
+// (each CTA works four tiles at once in 64-thread groups with named barriers):
 //   per pivot block K:  D^-1 = (A_KK)^-1 (computed one step ahead by the CTA that owns A_KK),
 //                       W_KJ = D^-1 A_KJ,  C_IK = A_IK            (phase A, whole grid)
 //                       A_IJ -= C_IK W_KJ,  A_IK <- C_IK D^-1,  A_KJ <- W_KJ,  A_KK <- -D^-1
@@ -19,8 +20,10 @@ namespace recon {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kB = 16;                       // tile edge
-constexpr long long kSpinLimit = 1LL << 24;  // ~1 s of polling before giving up
+constexpr int kB = 8;                        // tile edge
+constexpr int kTileT = kB * kB;              // threads per tile group
+constexpr int kGroups = kThreads / kTileT;   // tiles a CTA works on at once
+constexpr long long kSpinLimit = 1LL << 26;  // polls (~1 us each at most) before giving up
 
 struct GridBar {
     unsigned int count;
@@ -69,7 +72,6 @@ RECON_DEV bool grid_barrier(GridBar* gb) {
                         ok = 0;
                         break;
                     }
-                    if (it > 64) __nanosleep(32);
                 }
             }
             __threadfence();
@@ -80,147 +82,143 @@ RECON_DEV bool grid_barrier(GridBar* gb) {
     return ok_s != 0;
 }
 
-// In-CTA inverse of a Hermitian positive-definite 16 x 16 tile held (full) in shared memory:
-// 16 scalar sweeps leave -T^{-1}; the result is negated into `out` (column-major 16 x 16).
-RECON_DEV void tile_inverse(double2* T, double2* out) {
-    const int i = threadIdx.x % kB, j = threadIdx.x / kB;  // 256 threads <-> 256 entries
+// Synchronise the 64 threads of tile group g (named barrier g + 1; 0 is __syncthreads).
+RECON_DEV void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kTileT) : "memory");
+}
+
+// Inverse of a Hermitian positive-definite 8 x 8 tile held (full, column-major) in the group's
+// shared memory, by 8 scalar sweeps (which leave -T^{-1}); the negated result goes to `out`.
+// Called by the 64 threads of one tile group.
+RECON_DEV void tile_inverse(double2* T, double2* out, double* s_inv, double2* s_row, int g) {
+    const int e = threadIdx.x % kTileT, i = e % kB, j = e / kB;
     for (int k = 0; k < kB; ++k) {
-        double2 tij = make_double2(0, 0), tik = make_double2(0, 0), tkj = make_double2(0, 0);
-        double akk = 1.0;
-        if (threadIdx.x < kB * kB) {
-            tij = T[i + j * kB];
-            tik = T[i + k * kB];
-            tkj = T[k + j * kB];
-            akk = T[k + k * kB].x;
+        if (e == 0) *s_inv = rcp_nr(T[k + k * kB].x);  // one reciprocal per pivot
+        group_sync(g);
+        const double inv = *s_inv;
+        if (e < kB) {
+            const double2 t = T[k + e * kB];  // row k, scaled once
+            s_row[e] = make_double2(t.x * inv, t.y * inv);
         }
-        __syncthreads();
-        if (threadIdx.x < kB * kB) {
-            const double inv = 1.0 / akk;
-            double2 v;
-            if (i == k && j == k) v = make_double2(-inv, 0.0);
-            else if (i == k) v = make_double2(tkj.x * inv, tkj.y * inv);
-            else if (j == k) v = make_double2(tik.x * inv, tik.y * inv);
-            else {
-                const double2 pr = zmul(tik, tkj);
-                v = make_double2(tij.x - pr.x * inv, tij.y - pr.y * inv);
-            }
-            T[i + j * kB] = v;
-        }
-        __syncthreads();
+        const double2 tij = T[i + j * kB], tik = T[i + k * kB];
+        group_sync(g);
+        double2 v;
+        if (i == k && j == k) v = make_double2(-inv, 0.0);
+        else if (i == k) v = s_row[j];
+        else if (j == k) v = make_double2(tik.x * inv, tik.y * inv);
+        else v = zfms(tik, s_row[j], tij);
+        T[i + j * kB] = v;
+        group_sync(g);
     }
-    if (threadIdx.x < kB * kB) {
-        const double2 v = T[i + j * kB];
-        out[i + j * kB] = make_double2(-v.x, -v.y);
-    }
-    __syncthreads();
+    const double2 v = T[i + j * kB];
+    out[i + j * kB] = make_double2(-v.x, -v.y);
+    group_sync(g);
 }
 
 __global__ void __launch_bounds__(kThreads)
 hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int np,
                  double2* __restrict__ A, double2* __restrict__ Dinv2, double2* __restrict__ W,
                  double2* __restrict__ C, GridBar* gb) {
-    __shared__ double2 ta[kB * kB];
-    __shared__ double2 tb[kB * kB];
+    __shared__ double2 ta[kGroups][kTileT];
+    __shared__ double2 tb[kGroups][kTileT];
+    __shared__ double s_inv[kGroups];
+    __shared__ double2 s_row[kGroups][kB];
     const int nt = np / kB;
     const double eps = eps_p[0];
     const int tid = threadIdx.x;
+    const int g = tid / kTileT, e = tid % kTileT;
+    const int ii = e % kB, jj = e / kB;
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + tid;
     const size_t gstride = (size_t)gridDim.x * blockDim.x;
+    // interleaved index: consecutive work items go to different CTAs (spreads the FP64 work)
+    const size_t itid = (size_t)tid * gridDim.x + blockIdx.x;
 
     // A = pad(G + eps I): lower tiles and full diagonal tiles are the live part
-    for (size_t e = gtid; e < (size_t)np * np; e += gstride) {
-        const int i = (int)(e % np), j = (int)(e / np);
+    for (size_t idx = gtid; idx < (size_t)np * np; idx += gstride) {
+        const int i = (int)(idx % np), j = (int)(idx / np);
         double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
         if (i < s && j < s) {
             v = G[i + (size_t)j * s];
             if (i == j) v.x += eps;
         }
-        A[e] = v;
+        A[idx] = v;
     }
     if (!grid_barrier(gb)) return;
-    if (blockIdx.x == 0) {
-        if (tid < kB * kB) ta[tid] = A[(tid % kB) + (size_t)(tid / kB) * np];
-        __syncthreads();
-        tile_inverse(ta, Dinv2);
+    if (blockIdx.x == 0 && g == 0) {
+        ta[0][e] = A[ii + (size_t)jj * np];
+        group_sync(0);
+        tile_inverse(ta[0], Dinv2, &s_inv[0], s_row[0], 0);
     }
     if (!grid_barrier(gb)) return;
 
     const int nlt = nt * (nt + 1) / 2;
+    const int ngroups = gridDim.x * kGroups;
     for (int K = 0; K < nt; ++K) {
-        const double2* D = Dinv2 + (K & 1) * kB * kB;
-        double2* Dnext = Dinv2 + ((K + 1) & 1) * kB * kB;
+        const double2* D = Dinv2 + (K & 1) * kTileT;
+        double2* Dnext = Dinv2 + ((K + 1) & 1) * kTileT;
         const int k0 = K * kB;
-        // ---- phase A: W = D^-1 A_K,: (16 x np) and C = A_:,K (np x 16), old values
-        for (size_t e = gtid; e < (size_t)np * kB; e += gstride) {
-            const int m = (int)(e % kB);          // pivot-local index
-            const int col = (int)(e / kB);        // global column (for W) / row (for C)
+        // ---- phase A: W = D^-1 A_K,: (8 x np) and C = A_:,K (np x 8), old values
+        if (itid < (size_t)np * kB) {
+            const int m = (int)(itid % kB);       // pivot-local index
+            const int col = (int)(itid / kB);     // global column (for W) / row (for C)
             const int J = col / kB;
-            // W[m, col] = sum_q D[m, q] A_K(q, col)
             double2 acc = make_double2(0.0, 0.0);
             if (J != K) {
+#pragma unroll
                 for (int q = 0; q < kB; ++q) {
-                    double2 a;
-                    if (J < K) a = A[(k0 + q) + (size_t)col * np];
-                    else a = zconj(A[col + (size_t)(k0 + q) * np]);
+                    const double2 a = (J < K) ? A[(k0 + q) + (size_t)col * np]
+                                              : zconj(A[col + (size_t)(k0 + q) * np]);
                     acc = zfma(D[m + q * kB], a, acc);
                 }
             }
             W[m + (size_t)col * kB] = acc;
-            // C[row = col, m] = A(row, k0 + m)
-            double2 c;
-            if (J >= K) c = A[col + (size_t)(k0 + m) * np];
-            else c = zconj(A[(k0 + m) + (size_t)col * np]);
-            C[col + (size_t)m * np] = c;
+            C[col + (size_t)m * np] = (J >= K) ? A[col + (size_t)(k0 + m) * np]
+                                               : zconj(A[(k0 + m) + (size_t)col * np]);
         }
         if (!grid_barrier(gb)) return;
-        // ---- phase B: lower tiles; the owner of tile (K+1, K+1) also inverts it (look-ahead)
-        for (int t = blockIdx.x; t < nlt; t += gridDim.x) {
+        // ---- phase B: lower tiles, one per 64-thread group; the group that owns tile
+        // (K+1, K+1) also inverts it (look-ahead pivot)
+        for (int t = blockIdx.x * kGroups + g; t < nlt; t += ngroups) {
             int I = 0, rem = t;
             while (rem > I) { rem -= I + 1; ++I; }
             const int J = rem;                    // J <= I
-            const int ii = tid % kB, jj = tid / kB;
             const int row = I * kB + ii, col = J * kB + jj;
             double2 v;
             if (I == K && J == K) {
-                const double2 d = D[ii + jj * kB];
-                v = make_double2(-d.x, -d.y);
+                const double2 dd = D[ii + jj * kB];
+                v = make_double2(-dd.x, -dd.y);
             } else if (I == K) {
                 v = W[ii + (size_t)col * kB];
             } else if (J == K) {
                 double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
                 for (int q = 0; q < kB; ++q) acc = zfma(C[row + (size_t)q * np], D[q + jj * kB], acc);
                 v = acc;
             } else {
-                // stage C_I and W_J tiles in shared memory
-                ta[ii + jj * kB] = C[(I * kB + ii) + (size_t)jj * np];
-                tb[ii + jj * kB] = W[ii + (size_t)(J * kB + jj) * kB];
-                __syncthreads();
+                ta[g][e] = C[(I * kB + ii) + (size_t)jj * np];
+                tb[g][e] = W[ii + (size_t)(J * kB + jj) * kB];
+                group_sync(g);
                 double2 acc = A[row + (size_t)col * np];
-                for (int q = 0; q < kB; ++q) {
-                    const double2 pr = zmul(ta[ii + q * kB], tb[q + jj * kB]);
-                    acc.x -= pr.x;
-                    acc.y -= pr.y;
-                }
+#pragma unroll
+                for (int q = 0; q < kB; ++q) acc = zfms(ta[g][ii + q * kB], tb[g][q + jj * kB], acc);
                 v = acc;
-                __syncthreads();
+                group_sync(g);
             }
             A[row + (size_t)col * np] = v;
             if (I == J && I == K + 1) {
-                ta[ii + jj * kB] = v;
-                __syncthreads();
-                tile_inverse(ta, Dnext);
+                ta[g][e] = v;
+                group_sync(g);
+                tile_inverse(ta[g], Dnext, &s_inv[g], s_row[g], g);
             }
         }
         if (!grid_barrier(gb)) return;
     }
     // ---- H = -A (s x s, full, column-major) written over G
-    for (size_t e = gtid; e < (size_t)s * s; e += gstride) {
-        const int i = (int)(e % s), j = (int)(e / s);
+    for (size_t idx = gtid; idx < (size_t)s * s; idx += gstride) {
+        const int i = (int)(idx % s), j = (int)(idx / s);
         const int I = i / kB, J = j / kB;
-        double2 v;
-        if (I > J || (I == J)) v = A[i + (size_t)j * np];
-        else v = zconj(A[j + (size_t)i * np]);
-        G[e] = make_double2(-v.x, -v.y);
+        const double2 v = (I >= J) ? A[i + (size_t)j * np] : zconj(A[j + (size_t)i * np]);
+        G[idx] = make_double2(-v.x, -v.y);
     }
 }
 
@@ -259,44 +257,69 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
                double2* __restrict__ vprev, double* __restrict__ part, double* __restrict__ ab,
                double* __restrict__ lmax_out, GridBar* gb) {
     __shared__ double red[kThreads / 32];
+    __shared__ double s_beta, s_ib, s_alpha;
     __shared__ double sh_lo, sh_hi;
+    __shared__ int s_m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = gridDim.x * (kThreads / 32);
     const int gw = blockIdx.x * (kThreads / 32) + warp;
-    // deterministic start vector, unnormalised: u_i = 1 + 0.5 sin(i) + 0.25 i cos(3 i) / s
+    // deterministic start vector, unnormalised: u_i = 1 + 0.5 sin(i) + i 0.25 i cos(3 i) / s
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
         u[i] = make_double2(1.0 + 0.5 * sin((double)i), 0.25 * cos(3.0 * i) * i / s);
         vprev[i] = make_double2(0.0, 0.0);
     }
     if (!grid_barrier(gb)) return;
-    // beta_{-1} = |u|
-    double beta = 0.0;
-    {
+    if (warp == 0) {
         double acc = 0.0;
-        for (int i = threadIdx.x; i < s; i += blockDim.x) acc += u[i].x * u[i].x + u[i].y * u[i].y;
-        beta = sqrt(block_sum(acc, red));
+        for (int i = lane; i < s; i += 32) acc += u[i].x * u[i].x + u[i].y * u[i].y;
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            s_beta = sqrt(acc);
+            s_ib = rcp_nr(s_beta);
+            s_m = m;
+        }
     }
+    __syncthreads();
     for (int k = 0; k < m; ++k) {
         // v_k = u / beta_{k-1};  w = G v_k - alpha_k v_k - beta_{k-1} v_{k-1};  beta_k = |w|
-        const double ib = 1.0 / beta;
+        const double beta = s_beta, ib = s_ib;
         double* pa = part + (size_t)(k & 1) * 2 * gridDim.x;   // alpha partials (ping-pong)
         double* pb = pa + gridDim.x;                            // beta partials
         double ap = 0.0;
         double2 yrow[4];
         int nrow = 0;
         for (int i = gw; i < s && nrow < 4; i += nw, ++nrow) {
+            // row i of the Hermitian G is the conjugate of column i (contiguous)
             double2 acc = make_double2(0.0, 0.0);
-            for (int j = lane; j < s; j += 32) acc = zfma(G[i + (size_t)j * s], u[j], acc);
+            const double2* gcol = G + (size_t)i * s;
+            for (int j = lane; j < s; j += 32) {
+                const double2 g = gcol[j], uj = u[j];
+                acc.x = fma(g.x, uj.x, acc.x);
+                acc.x = fma(g.y, uj.y, acc.x);
+                acc.y = fma(g.x, uj.y, acc.y);
+                acc.y = fma(-g.y, uj.x, acc.y);
+            }
             acc.x = warp_sum(acc.x) * ib;
             acc.y = warp_sum(acc.y) * ib;
             yrow[nrow] = acc;
             const double2 vi = make_double2(u[i].x * ib, u[i].y * ib);
             ap += vi.x * acc.x + vi.y * acc.y;
         }
-        const double apb = block_sum(lane == 0 ? ap : 0.0, red);
-        if (threadIdx.x == 0) pa[blockIdx.x] = apb;
+        __syncthreads();
+        if (lane == 0) red[warp] = ap;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+            pa[blockIdx.x] = t;
+        }
         if (!grid_barrier(gb)) return;
-        const double alpha = block_sum_array(pa, gridDim.x, red);
+        if (warp == 0) {
+            const double al = warp0_sum_array(pa, gridDim.x);
+            if (lane == 0) s_alpha = al;
+        }
+        __syncthreads();
+        const double alpha = s_alpha;
         double bp = 0.0;
         nrow = 0;
         for (int i = gw; i < s && nrow < 4; i += nw, ++nrow) {
@@ -310,19 +333,37 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
                 u[i] = un;
             }
         }
-        const double bpb = block_sum(bp, red);
-        if (threadIdx.x == 0) pb[blockIdx.x] = bpb;
-        if (!grid_barrier(gb)) return;
-        const double bnew = sqrt(block_sum_array(pb, gridDim.x, red));
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            ab[2 * k] = alpha;
-            ab[2 * k + 1] = bnew;
+        if (lane == 0) red[warp] = bp;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+            pb[blockIdx.x] = t;
         }
-        beta = bnew;
-        if (!(bnew > 1e-300 * fabs(alpha) + 1e-300)) { m = k + 1; break; }
+        if (!grid_barrier(gb)) return;
+        if (warp == 0) {
+            const double b2 = warp0_sum_array(pb, gridDim.x);
+            if (lane == 0) {
+                const double bnew = sqrt(b2);
+                if (blockIdx.x == 0) {
+                    ab[2 * k] = alpha;
+                    ab[2 * k + 1] = bnew;
+                }
+                s_beta = bnew;
+                s_ib = rcp_nr(bnew);
+                if (!(bnew > 1e-300 * fabs(alpha) + 1e-300)) s_m = k + 1;
+            }
+        }
+        __syncthreads();
+        if (s_m == k + 1) break;
     }
-    // largest eigenvalue of the m x m tridiagonal (alpha_k, beta_k) by multisection (CTA 0)
+    m = s_m;
+    // Largest eigenvalue of the m x m tridiagonal (alpha_k, beta_k) by multisection with Sturm
+    // counts (CTA 0): FP32 rounds over the whole block to 1e-4 relative (FP32 counts are exact
+    // for x farther than ~m eps32 |T| from an eigenvalue), then FP64 rounds on
+    // one warp (FP64 divisions are expensive here, so few threads evaluate them).
     if (blockIdx.x != 0) return;
+    __shared__ int best;
     __syncthreads();
     if (threadIdx.x == 0) {
         double lo = 1e300, hi = -1e300;
@@ -331,35 +372,52 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
             lo = fmin(lo, ab[2 * k] - r);
             hi = fmax(hi, ab[2 * k] + r);
         }
-        sh_lo = lo;
-        sh_hi = hi;
+        const double pad = 1e-6 * fmax(fabs(lo), fabs(hi));
+        sh_lo = lo - pad;
+        sh_hi = hi + pad;
     }
     __syncthreads();
-    for (int round = 0; round < 12; ++round) {
+    for (int round = 0; round < 24; ++round) {
+        const bool fp32 = (sh_hi - sh_lo) > 1e-4 * fabs(sh_hi);
+        const int nthr = fp32 ? (int)blockDim.x : 32;
         const double lo = sh_lo, hi = sh_hi;
-        const double x = lo + (hi - lo) * (threadIdx.x + 1) / (double)(blockDim.x + 1);
-        // Sturm count: number of eigenvalues < x
-        int cnt = 0;
-        double d = 1.0;
-        for (int k = 0; k < m; ++k) {
-            const double bb = k > 0 ? ab[2 * k - 1] * ab[2 * k - 1] : 0.0;
-            d = (ab[2 * k] - x) - (k > 0 ? bb / d : 0.0);
-            if (d == 0.0) d = -1e-300;
-            if (d < 0.0) ++cnt;
+        int cnt = m;
+        if ((int)threadIdx.x < nthr) {
+            const double x = lo + (hi - lo) * (threadIdx.x + 1) / (double)(nthr + 1);
+            cnt = 0;
+            if (fp32) {
+                const float xf = (float)x;
+                float d = 1.f;
+                for (int k = 0; k < m; ++k) {
+                    const float bb = k > 0 ? (float)(ab[2 * k - 1] * ab[2 * k - 1]) : 0.f;
+                    d = ((float)ab[2 * k] - xf) - (k > 0 ? bb * __frcp_rn(d) : 0.f);
+                    if (d == 0.f) d = -1e-30f;
+                    if (d < 0.f) ++cnt;
+                }
+            } else {
+                double d = 1.0;
+                for (int k = 0; k < m; ++k) {
+                    const double bb = k > 0 ? ab[2 * k - 1] * ab[2 * k - 1] : 0.0;
+                    d = (ab[2 * k] - x) - (k > 0 ? bb * rcp_nr(d) : 0.0);
+                    if (d == 0.0) d = -1e-300;
+                    if (d < 0.0) ++cnt;
+                }
+            }
         }
-        // the largest eigenvalue lies above the largest x with cnt < m
-        __shared__ int best;
+        // the largest eigenvalue lies above the largest sample x with cnt < m
         if (threadIdx.x == 0) best = -1;
         __syncthreads();
-        if (cnt < m) atomicMax(&best, (int)threadIdx.x);
+        if ((int)threadIdx.x < nthr && cnt < m) atomicMax(&best, (int)threadIdx.x);
         __syncthreads();
         if (threadIdx.x == 0) {
-            const double step = (hi - lo) / (double)(blockDim.x + 1);
-            sh_lo = lo + step * (best + 1);
-            sh_hi = sh_lo + step;
+            const double step = (hi - lo) / (double)(nthr + 1);
+            const double nlo = lo + step * (best + 1);
+            // FP32 counts near the root may be off by rounding: keep one step of margin
+            sh_lo = fp32 ? fmax(lo, nlo - step) : nlo;
+            sh_hi = fp32 ? fmin(hi, nlo + 2 * step) : nlo + step;
         }
         __syncthreads();
-        if (sh_hi - sh_lo <= 1e-15 * fabs(sh_hi)) break;
+        if (sh_hi - sh_lo <= 2e-16 * fabs(sh_hi)) break;
     }
     if (threadIdx.x == 0) lmax_out[0] = 0.5 * (sh_lo + sh_hi);
 }
@@ -380,8 +438,8 @@ int padded(int s) { return (s + kB - 1) / kB * kB; }
 
 size_t hpd_scratch_bytes(const Dims& d) {
     const size_t np = (size_t)padded(d.s());
-    return np * np * sizeof(double2) + 2 * kB * kB * sizeof(double2) + 2 * np * kB * sizeof(double2) +
-           sizeof(GridBar) + 1024;
+    return 256 + np * np * sizeof(double2) + 2 * kB * kB * sizeof(double2) +
+           2 * np * kB * sizeof(double2) + 1024;
 }
 
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {

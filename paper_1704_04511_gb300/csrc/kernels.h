@@ -31,6 +31,33 @@ struct Twiddles {
     const double2* twQd; // length Q, FP64
 };
 
+// Grid-wide deterministic reduction slot: one partial per block, finished by the last block.
+// `counter` must be zero before the first use; each reduction leaves it zero again.
+struct RedSlot {
+    double* parts;          // max_parts() doubles
+    unsigned int* counter;  // one word
+};
+
+// Launch `kern` with programmatic stream serialization (see pdl_wait in common.cuh).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// SM count of the current device (cached per device).
+int num_sms();
+
 bool fft_size_supported(int n);
 // Message returned by recon_last_error(NULL) (calls that have no context).
 void set_context_free_error(const std::string& msg);
@@ -44,33 +71,32 @@ cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int
 // y = unitary forward (inv = 0) or inverse (inv = 1) 2-D DFT of every frame of x (in place ok)
 cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, float2* y, int inv,
                         cudaStream_t st);
-// CG step, pass A: p = r (first) or r + beta p; t = row-FFT(p).
+// CG step, pass A: p = r (first) or r + beta p with beta = *rr_num / *rr_den; t = row-FFT(p).
 cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
                                    float2* t, const double* rr_num, const double* rr_den,
-                                   int nparts, int first, cudaStream_t st);
+                                   int first, cudaStream_t st);
 // CG step, pass B: t = column-IFFT(mask * column-FFT(t)) / (PQ), in place.
 cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
                             cudaStream_t st);
 
 // ---- cg.cu ----
-// CG step, pass C: q = row-IFFT(t) + lam W p written over t; part_pq[row] = Re <p, q> partials.
+// CG step, pass C: q = row-IFFT(t) + lam W p written over t; *pq_out = Re <p, q>.
 cudaError_t launch_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
-                             const float2* S, float lam, double* part_pq, cudaStream_t st);
-// q = (A^H A + lam W) p with the same three passes (used by tests, scratch t == q)
-// CG step, pass D: alpha = rr / pq; x += alpha p; r -= alpha q; part_rr_out = |r|^2 partials.
-cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* p,
-                             const float2* q, const double* part_rr_in, const double* part_pq,
-                             int nparts_pq, double* part_rr_out, int nparts, double* hist,
+                             const float2* S, float lam, const RedSlot& rs, double* pq_out,
                              cudaStream_t st);
+// CG step, pass D: alpha = *rr_in / *pq_in; x += alpha p; r -= alpha q; *rr_out = |r|^2.
+cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* p,
+                             const float2* q, const double* rr_in, const double* pq_in,
+                             const RedSlot& rs, double* rr_out, cudaStream_t st);
 // Residual carry: r = (first ? 0 : r) + lam W_{S_old - S_new} x (S_old ignored when first);
-// part_rr_out = |r|^2 partials.
+// *rr_out = |r|^2.
 cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const float2* S_old,
-                               const float2* S_new, float lam, int first, double* part_rr_out,
-                               int nparts, cudaStream_t st);
+                               const float2* S_new, float lam, int first, const RedSlot& rs,
+                               double* rr_out, cudaStream_t st);
 // y = W_S x alone (tests)
 cudaError_t launch_apply_w(const Dims& d, const float2* x, const float2* S, float2* y,
                            cudaStream_t st);
-int vec_parts();  // number of partial sums the vector kernels write
+int max_parts();  // partial-sum slots a RedSlot must provide
 
 // ---- gram.cu ----
 // Lags of the Gram matrix (Sec. III-B): per-block partials then deterministic reduction and

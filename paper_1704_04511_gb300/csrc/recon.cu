@@ -58,6 +58,16 @@ struct recon_ctx {
     std::string err;
     std::map<int, TwTable> tw;
     std::map<std::string, Buf> bufs;
+    // Batch slots: each has its own stream, workspace and eigensolver handle. The fields
+    // stream / bufs / solver above always hold the ACTIVE slot's; the others are parked here.
+    struct Slot {
+        cudaStream_t stream = nullptr;
+        bool own_stream = false;
+        std::map<std::string, Buf> bufs;
+        cusolverDnHandle_t solver = nullptr;
+    };
+    std::vector<Slot> slots;  // slots[i] valid while i != active
+    int active = 0;
     // optional per-launch CUDA-event timing (recon_profile): bit k times launch class k
     unsigned int prof = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -232,7 +242,8 @@ int check_dims(recon_ctx* c, recon_dims dd, const recon_filter* f, Dims* d) {
 struct Work {
     float2 *r, *p, *t, *S0, *S1;
     double2 *G, *lag_part, *lags, *dpart, *dsum, *Z, *eigwork;
-    double *evals, *part_pq, *part_rr, *eps, *hist, *lmax;
+    double *evals, *parts, *rr, *pq, *eps, *lmax;
+    unsigned int* counter;
     int *info, *kerr;
     void *hpd, *lanc;
     int lwork;
@@ -280,11 +291,12 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
     GET("lags", nlag * sizeof(double2), lags, double2*);
     GET("dsum", nlag * sizeof(double2), dsum, double2*);
     GET("Z", recon::s_scratch_bytes(d), Z, double2*);
-    GET("part_pq", (size_t)d.P * sizeof(double), part_pq, double*);
-    GET("part_rr", (size_t)2 * recon::vec_parts() * sizeof(double), part_rr, double*);
+    GET("parts", (size_t)recon::max_parts() * sizeof(double), parts, double*);
+    GET("counter", 256, counter, unsigned int*);
+    GET("rr", (size_t)(n_cg + 1) * sizeof(double), rr, double*);
+    GET("pq", (size_t)(n_cg + 1) * sizeof(double), pq, double*);
     GET("eps", 2 * sizeof(double), eps, double*);
     w->lmax = w->eps + 1;
-    GET("hist", (size_t)3 * (n_cg + 1) * sizeof(double), hist, double*);
     GET("info", (size_t)ni * sizeof(int), info, int*);
     GET("kerr", (size_t)2 * ni * sizeof(int), kerr, int*);
     if (use_eig) {
@@ -301,6 +313,7 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
         GET("lanc", recon::lanczos_scratch_bytes(d, sms), lanc, void*);
     }
 #undef GET
+    RC_CUDA(cudaMemsetAsync(w->counter, 0, sizeof(unsigned int), c->stream));
     RC_CUDA(cudaMemsetAsync(w->info, 0, (size_t)ni * sizeof(int), c->stream));
     RC_CUDA(cudaMemsetAsync(w->kerr, 0, (size_t)2 * ni * sizeof(int), c->stream));
     return RECON_OK;
@@ -373,17 +386,16 @@ int check_status(recon_ctx* c, Work& w, int n_iter) {
 // Residual carry + n_cg CG steps on x (in place).
 int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uint8_t* mask,
              const float2* S_old, const float2* S_new, float lam, float2* x, int first, int n_cg) {
-    const int nv = recon::vec_parts();
-    double* prr[2] = {w.part_rr, w.part_rr + nv};
+    const recon::RedSlot rs{w.parts, w.counter};
     {
         ProfScope ps(c, RECON_PROF_RESID);
-        RC_CUDA(recon::launch_resid_carry(d, w.r, x, S_old, S_new, lam, first, prr[0], nv, c->stream));
+        RC_CUDA(recon::launch_resid_carry(d, w.r, x, S_old, S_new, lam, first, rs, w.rr, c->stream));
     }
     for (int it = 0; it < n_cg; ++it) {
         {
             ProfScope ps(c, RECON_PROF_CG_ROWFWD);
-            RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, prr[it & 1], prr[(it + 1) & 1],
-                                                  nv, it == 0, c->stream));
+            RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, w.rr + it,
+                                                  it > 0 ? w.rr + it - 1 : w.rr, it == 0, c->stream));
         }
         {
             ProfScope ps(c, RECON_PROF_CG_COL);
@@ -391,19 +403,138 @@ int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uin
         }
         {
             ProfScope ps(c, RECON_PROF_CG_ROWINVW);
-            RC_CUDA(recon::launch_row_inv_w(d, tw, w.t, w.p, S_new, lam, w.part_pq, c->stream));
+            RC_CUDA(recon::launch_row_inv_w(d, tw, w.t, w.p, S_new, lam, rs, w.pq + it, c->stream));
         }
         {
             ProfScope ps(c, RECON_PROF_CG_UPDATE);
-            RC_CUDA(recon::launch_cg_update(d, x, w.r, w.p, w.t, prr[it & 1], w.part_pq, d.P,
-                                            prr[(it + 1) & 1], nv, w.hist + 3 * it, c->stream));
+            RC_CUDA(recon::launch_cg_update(d, x, w.r, w.p, w.t, w.rr + it, w.pq + it, rs,
+                                            w.rr + it + 1, c->stream));
         }
     }
     return RECON_OK;
 }
 
+int select_slot(recon_ctx* c, int i);
+
+// Every entry point starts here: the context's device current and slot 0 (the context's own
+// stream and workspace) active.
 int set_device(recon_ctx* c) {
     RC_CUDA(cudaSetDevice(c->device));
+    return select_slot(c, 0);
+}
+
+// Make slot i active (creating it on first use: own non-blocking stream, no workspace yet).
+int select_slot(recon_ctx* c, int i) {
+    if ((int)c->slots.size() < i + 1) c->slots.resize(i + 1);
+    if (i == c->active) return RECON_OK;
+    auto& park = c->slots[c->active];
+    park.stream = c->stream;
+    park.own_stream = c->own_stream;
+    park.bufs = std::move(c->bufs);
+    park.solver = c->solver;
+    auto& next = c->slots[i];
+    if (!next.stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&next.stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            c->bufs = std::move(park.bufs);
+            return cuda_fail(c, e, "cudaStreamCreateWithFlags");
+        }
+        next.own_stream = true;
+    }
+    c->stream = next.stream;
+    c->own_stream = next.own_stream;
+    c->bufs = std::move(next.bufs);
+    c->solver = next.solver;
+    next = recon_ctx::Slot{};
+    c->active = i;
+    return RECON_OK;
+}
+
+int ensure_solver(recon_ctx* c) {
+    if (c->solver) return RECON_OK;
+    if (cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS)
+        return fail(c, RECON_ECUDA, "cusolverDnCreate failed");
+    if (cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS)
+        return fail(c, RECON_ECUDA, "cusolverDnSetStream failed");
+    return RECON_OK;
+}
+
+int check_params(recon_ctx* c, recon_dims dd, recon_filter f, const recon_params* prm, Dims* d) {
+    int rc = check_dims(c, dd, &f, d);
+    if (rc) return rc;
+    if (prm->irls < 0 || prm->cg < 1) return fail(c, RECON_EINVAL, "need irls >= 0, cg >= 1");
+    if (!(prm->lambda > 0.0) || !std::isfinite(prm->lambda))
+        return fail(c, RECON_EINVAL, "lambda must be positive and finite");
+    if (!(prm->p >= 0.0 && prm->p <= 1.0)) return fail(c, RECON_EINVAL, "need 0 <= p <= 1");
+    if (!(prm->gamma >= 1.0) || !std::isfinite(prm->gamma)) return fail(c, RECON_EINVAL, "need gamma >= 1");
+    if (!(prm->eps0_frac > 0.0) || !std::isfinite(prm->eps0_frac))
+        return fail(c, RECON_EINVAL, "eps0_frac must be positive");
+    if (prm->weight_method != RECON_WEIGHT_AUTO && prm->weight_method != RECON_WEIGHT_EIG)
+        return fail(c, RECON_EINVAL, "unknown weight method");
+    return RECON_OK;
+}
+
+// One solve in flight on the active slot's stream.
+struct Solve {
+    Dims d;
+    Twiddles tw;
+    Work w;
+    float2* x;
+    const uint8_t* masks;
+    const recon_params* prm;
+};
+
+// Workspace, x0 = A^H b (Algorithm 1 initialisation). Enqueues only.
+int solve_begin(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* masks,
+                const recon_params* prm, void* image_out, Solve* sv) {
+    sv->d = d;
+    sv->masks = masks;
+    sv->prm = prm;
+    sv->x = reinterpret_cast<float2*>(image_out);
+    int rc = get_twiddles(c, d, &sv->tw);
+    if (rc) return rc;
+    const bool eig = wants_eig(prm->p, prm->weight_method);
+    if (eig) {
+        rc = ensure_solver(c);
+        if (rc) return rc;
+    }
+    rc = get_work(c, d, prm->cg, prm->irls, true, eig, &sv->w);
+    if (rc) return rc;
+    ProfScope ps(c, RECON_PROF_ADJOINT);
+    RC_CUDA(recon::launch_adjoint(d, sv->tw, kspace, prm->kspace_bf16, masks, sv->w.t, sv->x,
+                                  c->stream));
+    return RECON_OK;
+}
+
+// IRLS iteration n of Algorithm 1: Gram, weight, residual carry, CG. Enqueues only.
+int solve_iter(recon_ctx* c, Solve& sv, int n) {
+    const Dims& d = sv.d;
+    Work& w = sv.w;
+    float2* S[2] = {w.S0, w.S1};
+    float2* S_new = S[n & 1];
+    const float2* S_old = n == 0 ? nullptr : S[(n + 1) & 1];
+    {
+        ProfScope ps(c, RECON_PROF_GRAM);
+        RC_CUDA(recon::launch_gram(d, sv.tw, sv.x, w.lag_part, w.gblocks, nullptr, w.G, c->stream));
+    }
+    int rc = weight_step(c, d, sv.tw, w, sv.prm->p, n == 0, sv.prm->eps0_frac, sv.prm->gamma, 0,
+                         0.0, S_new, n);
+    if (rc) return rc;
+    return cg_block(c, d, sv.tw, w, sv.masks, S_old, S_new, (float)sv.prm->lambda, sv.x, n == 0,
+                    sv.prm->cg);
+}
+
+// After the slot's stream finished: status flags, finite residual and eps.
+int solve_check(recon_ctx* c, Solve& sv) {
+    int rc = check_status(c, sv.w, sv.prm->irls);
+    if (rc) return rc;
+    if (sv.prm->irls > 0) {
+        double rr = 0.0, eps = 0.0;
+        RC_CUDA(cudaMemcpy(&rr, sv.w.rr + sv.prm->cg, sizeof(double), cudaMemcpyDeviceToHost));
+        RC_CUDA(cudaMemcpy(&eps, sv.w.eps, sizeof(double), cudaMemcpyDeviceToHost));
+        if (!std::isfinite(rr) || !std::isfinite(eps))
+            return fail(c, RECON_ENUMERIC, "non-finite residual or eps in the iteration");
+    }
     return RECON_OK;
 }
 
@@ -452,6 +583,14 @@ int recon_create(recon_ctx** out, int device, size_t mem_budget_bytes, void* cud
 void recon_destroy(recon_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    select_slot(c, 0);
+    for (auto& sl : c->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        for (auto& kv : sl.bufs)
+            if (kv.second.ptr) cudaFree(kv.second.ptr);
+        if (sl.solver) cusolverDnDestroy(sl.solver);
+        if (sl.own_stream && sl.stream) cudaStreamDestroy(sl.stream);
+    }
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& kv : c->bufs)
         if (kv.second.ptr) cudaFree(kv.second.ptr);
@@ -481,7 +620,7 @@ size_t recon_bytes_needed(recon_dims dd, recon_filter f, int kspace_bf16) {
     b += s * s * sizeof(double2) * 3 + s * sizeof(double);  // G + eigensolver work (estimate)
     b += recon::gram_scratch_bytes(d, recon::gram_blocks(d)) + recon::diag_scratch_bytes(d) +
          2 * nlag * sizeof(double2) + recon::s_scratch_bytes(d);
-    b += (size_t)(d.P + 2 * recon::vec_parts() + 256) * sizeof(double);
+    b += (size_t)(recon::max_parts() + 512) * sizeof(double);
     return b;
 }
 
@@ -490,58 +629,79 @@ int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* 
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
     Dims d;
-    int rc = check_dims(c, dd, &f, &d);
+    int rc = check_params(c, dd, f, prm, &d);
     if (rc) return rc;
-    if (prm->irls < 0 || prm->cg < 1) return fail(c, RECON_EINVAL, "need irls >= 0, cg >= 1");
-    if (!(prm->lambda > 0.0) || !std::isfinite(prm->lambda))
-        return fail(c, RECON_EINVAL, "lambda must be positive and finite");
-    if (!(prm->p >= 0.0 && prm->p <= 1.0)) return fail(c, RECON_EINVAL, "need 0 <= p <= 1");
-    if (!(prm->gamma >= 1.0) || !std::isfinite(prm->gamma)) return fail(c, RECON_EINVAL, "need gamma >= 1");
-    if (!(prm->eps0_frac > 0.0) || !std::isfinite(prm->eps0_frac))
-        return fail(c, RECON_EINVAL, "eps0_frac must be positive");
     rc = set_device(c);
     if (rc) return rc;
-    Twiddles tw;
-    rc = get_twiddles(c, d, &tw);
+    rc = select_slot(c, 0);
     if (rc) return rc;
-    Work w;
-    rc = get_work(c, d, prm->cg, prm->irls, true, wants_eig(prm->p, prm->weight_method), &w);
+    Solve sv;
+    rc = solve_begin(c, d, kspace, masks, prm, image_out, &sv);
     if (rc) return rc;
-    float2* x = reinterpret_cast<float2*>(image_out);
-    const float lam = (float)prm->lambda;
-    {
-        ProfScope ps(c, RECON_PROF_ADJOINT);
-        RC_CUDA(recon::launch_adjoint(d, tw, kspace, prm->kspace_bf16, masks, w.t, x, c->stream));
-    }
-    float2* S[2] = {w.S0, w.S1};
     for (int n = 0; n < prm->irls; ++n) {
-        float2* S_new = S[n & 1];
-        const float2* S_old = n == 0 ? nullptr : S[(n + 1) & 1];
-        {
-            ProfScope ps(c, RECON_PROF_GRAM);
-            RC_CUDA(recon::launch_gram(d, tw, x, w.lag_part, w.gblocks, nullptr, w.G, c->stream));
-        }
-        rc = weight_step(c, d, tw, w, prm->p, n == 0, prm->eps0_frac, prm->gamma, 0, 0.0, S_new, n);
-        if (rc) return rc;
-        rc = cg_block(c, d, tw, w, masks, S_old, S_new, lam, x, n == 0, prm->cg);
+        rc = solve_iter(c, sv, n);
         if (rc) return rc;
     }
     RC_CUDA(cudaStreamSynchronize(c->stream));
-    rc = check_status(c, w, prm->irls);
+    return solve_check(c, sv);
+}
+
+int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* kspace,
+                      const uint8_t* const* masks, recon_filter f, const recon_params* prm,
+                      void* const* image_out) {
+    if (!c) return RECON_EINVAL;
+    if (n < 1 || n > RECON_MAX_BATCH) return fail(c, RECON_EINVAL, "need 1 <= n <= RECON_MAX_BATCH");
+    if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    for (int i = 0; i < n; ++i)
+        if (!kspace[i] || !masks[i] || !image_out[i]) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_params(c, dd, f, prm, &d);
     if (rc) return rc;
-    if (prm->irls > 0) {
-        const int nv = recon::vec_parts();
-        std::vector<double> part(nv);
-        RC_CUDA(cudaMemcpy(part.data(), w.part_rr + (prm->cg & 1) * nv, nv * sizeof(double),
-                           cudaMemcpyDeviceToHost));
-        double rr = 0.0;
-        for (double v : part) rr += v;
-        double eps = 0.0;
-        RC_CUDA(cudaMemcpy(&eps, w.eps, sizeof(double), cudaMemcpyDeviceToHost));
-        if (!std::isfinite(rr) || !std::isfinite(eps))
-            return fail(c, RECON_ENUMERIC, "non-finite residual or eps in the iteration");
+    rc = set_device(c);
+    if (rc) return rc;
+    rc = select_slot(c, 0);
+    if (rc) return rc;
+    // slot streams start after the work already queued on the context's stream
+    cudaEvent_t start = nullptr;
+    RC_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    std::vector<cudaEvent_t> done(n, nullptr);
+    auto cleanup = [&]() {
+        select_slot(c, 0);
+        cudaEventDestroy(start);
+        for (cudaEvent_t e : done)
+            if (e) cudaEventDestroy(e);
+    };
+    std::vector<Solve> sv(n);
+    rc = RECON_OK;
+    cudaError_t e = cudaEventRecord(start, c->stream);
+    for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
+        rc = select_slot(c, i);
+        if (!rc) e = cudaStreamWaitEvent(c->stream, start, 0);
+        if (!rc && e == cudaSuccess) rc = solve_begin(c, d, kspace[i], masks[i], prm, image_out[i], &sv[i]);
     }
-    return RECON_OK;
+    // iterations interleaved over the slots so that every stream has work queued early
+    for (int it = 0; it < prm->irls && !rc && e == cudaSuccess; ++it)
+        for (int i = 0; i < n && !rc; ++i) {
+            rc = select_slot(c, i);
+            if (!rc) rc = solve_iter(c, sv[i], it);
+        }
+    for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
+        rc = select_slot(c, i);
+        if (!rc) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+        if (!rc && e == cudaSuccess) e = cudaEventRecord(done[i], c->stream);
+    }
+    if (!rc && e == cudaSuccess) {
+        rc = select_slot(c, 0);
+        for (int i = 1; i < n && !rc && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->stream, done[i], 0);
+        if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
+        rc = select_slot(c, i);
+        if (!rc) rc = solve_check(c, sv[i]);
+    }
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(c, e, "recon_solve_batch");
+    return rc;
 }
 
 int recon_adjoint(recon_ctx* c, recon_dims dd, const void* kspace, int kspace_bf16,
@@ -655,17 +815,23 @@ int recon_apply_normal(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_
     Twiddles tw;
     rc = get_twiddles(c, d, &tw);
     if (rc) return rc;
-    void *pp, *part;
+    void *pp, *parts, *counter, *pq;
     rc = ensure(c, "p", d.elems() * sizeof(float2), &pp);
     if (rc) return rc;
-    rc = ensure(c, "part_pq", (size_t)d.P * sizeof(double), &part);
+    rc = ensure(c, "parts", (size_t)recon::max_parts() * sizeof(double), &parts);
     if (rc) return rc;
+    rc = ensure(c, "counter", 256, &counter);
+    if (rc) return rc;
+    rc = ensure(c, "pq", 2 * sizeof(double), &pq);
+    if (rc) return rc;
+    RC_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c->stream));
+    const recon::RedSlot rs{(double*)parts, (unsigned int*)counter};
     // pass A with first = 1 copies x into p and row-transforms it into y; passes B and C follow.
     RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y, nullptr,
-                                          nullptr, 0, 1, c->stream));
+                                          nullptr, 1, c->stream));
     RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
     RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
-                                    (float)lambda, (double*)part, c->stream));
+                                    (float)lambda, rs, (double*)pq, c->stream));
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return RECON_OK;
 }
@@ -709,19 +875,8 @@ int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, 
     w.r = r_save;
     if (rc) return rc;
     RC_CUDA(cudaStreamSynchronize(c->stream));
-    if (rr_hist) {
-        const int nv = recon::vec_parts();
-        std::vector<double> hist(3 * (size_t)(n_cg + 1));
-        if (n_cg > 0)
-            RC_CUDA(cudaMemcpy(hist.data(), w.hist, 3 * (size_t)n_cg * sizeof(double), cudaMemcpyDeviceToHost));
-        for (int i = 0; i < n_cg; ++i) rr_hist[i] = hist[3 * i];
-        std::vector<double> part(nv);
-        RC_CUDA(cudaMemcpy(part.data(), w.part_rr + (n_cg & 1) * nv, nv * sizeof(double),
-                           cudaMemcpyDeviceToHost));
-        double rr = 0.0;
-        for (double v : part) rr += v;
-        rr_hist[n_cg] = rr;
-    }
+    if (rr_hist)
+        RC_CUDA(cudaMemcpy(rr_hist, w.rr, (size_t)(n_cg + 1) * sizeof(double), cudaMemcpyDeviceToHost));
     return RECON_OK;
 }
 

@@ -36,7 +36,8 @@ _ERR_NAMES = {RECON_EINVAL: "RECON_EINVAL", RECON_ENOMEM: "RECON_ENOMEM",
 EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_needed",
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
-            "recon_profile_read", "recon_profile_name", "recon_gram_static")
+            "recon_profile_read", "recon_profile_name", "recon_gram_static",
+            "recon_solve_batch")
 
 PROF_KINDS = 13
 
@@ -95,6 +96,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_profile_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
             "recon_profile_name": (ctypes.c_char_p, [i]),
             "recon_gram_static": (i, [dims, filt, vp, vp, vp, vp]),
+            "recon_solve_batch": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp), filt,
+                                      ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -169,6 +172,26 @@ def recon_solve(ctx, kspace, masks, filt, lam: float, p: float, irls: int, cg: i
                        weight_method=int(weight_method))
     _check(ctx, load_library().recon_solve(ctx, _dims(masks), _ptr(kspace), _ptr(masks),
                                            _filt(filt), ctypes.byref(prm), _ptr(image_out)))
+
+
+def recon_solve_batch(ctx, kspaces, masks_list, filt, lam: float, p: float, irls: int, cg: int,
+                      image_outs, gamma: float = 1.4, eps0_frac: float = 0.01,
+                      weight_method: int = RECON_WEIGHT_AUTO) -> None:
+    """n independent problems of the same shape, solved concurrently (one stream each)."""
+    import torch
+    n = len(kspaces)
+    if not (len(masks_list) == n == len(image_outs)):
+        raise ValueError("kspaces, masks_list and image_outs must have the same length")
+    bf16 = kspaces[0].dtype == torch.bfloat16
+    prm = recon_params(irls=int(irls), cg=int(cg), lambda_=float(lam), p=float(p),
+                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=int(bf16),
+                       weight_method=int(weight_method))
+    arr = ctypes.c_void_p * n
+    kp = arr(*[_ptr(t) for t in kspaces])
+    mp = arr(*[_ptr(t) for t in masks_list])
+    op = arr(*[_ptr(t) for t in image_outs])
+    _check(ctx, load_library().recon_solve_batch(ctx, int(n), _dims(masks_list[0]), kp, mp,
+                                                 _filt(filt), ctypes.byref(prm), op))
 
 
 def recon_adjoint(ctx, kspace, masks, x_out) -> None:

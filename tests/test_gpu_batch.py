@@ -1,0 +1,73 @@
+"""recon_solve_batch: concurrent independent solves (one stream each) give exactly the results
+of solving each problem alone (fixed launch shapes and reduction orders), on both weight paths."""
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_04511_gb300 import recon
+    ctx = recon.Context(0)
+    yield recon, ctx
+    ctx.close()
+
+
+def _inputs(w, seeds):
+    ks, ms = [], []
+    for sd in seeds:
+        prob = synth.make_problem(synth.workload(w.name, seed=sd, n_irls=w.n_irls, p=w.p))
+        ks.append(torch.from_numpy(np.ascontiguousarray(prob["kspace"], dtype=np.complex64)).cuda())
+        ms.append(torch.from_numpy(prob["masks"]).cuda())
+    return ks, ms
+
+
+@pytest.mark.parametrize("p,method", [(0.0, 0), (0.7, 0), (0.0, 1)])
+def test_batch_equals_solo(R, p, method):
+    recon, ctx = R
+    w = synth.workload("tiny_32x32x8", n_irls=5, p=p)
+    seeds = [0, 1, 2]
+    ks, ms = _inputs(w, seeds)
+    filt = (w.N1, w.N2, w.M)
+    solo = []
+    for k, m in zip(ks, ms):
+        out = torch.empty(tuple(m.shape), dtype=torch.complex64, device="cuda")
+        recon.recon_solve(ctx.h, k, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out, weight_method=method)
+        solo.append(out.cpu().numpy())
+    outs = [torch.full(tuple(m.shape), float("nan"), dtype=torch.complex64, device="cuda") for m in ms]
+    recon.recon_solve_batch(ctx.h, ks, ms, filt, w.lam, w.p, w.n_irls, w.n_cg, outs,
+                            weight_method=method)
+    for a, b in zip(outs, solo):
+        assert np.array_equal(a.cpu().numpy(), b)
+    # the problems differ, so the slots did not share state
+    assert not np.array_equal(solo[0], solo[1])
+
+
+def test_batch_perf_size_two_slots(R):
+    recon, ctx = R
+    w = synth.workload("perf_256x256x16", n_irls=2)
+    ks, ms = _inputs(w, [0, 5])
+    filt = (w.N1, w.N2, w.M)
+    solo = torch.empty(tuple(ms[1].shape), dtype=torch.complex64, device="cuda")
+    recon.recon_solve(ctx.h, ks[1], ms[1], filt, w.lam, w.p, w.n_irls, w.n_cg, solo)
+    outs = [torch.empty_like(solo) for _ in ms]
+    recon.recon_solve_batch(ctx.h, ks, ms, filt, w.lam, w.p, w.n_irls, w.n_cg, outs)
+    assert np.array_equal(outs[1].cpu().numpy(), solo.cpu().numpy())
+
+
+def test_batch_errors(R):
+    recon, ctx = R
+    w = synth.workload("tiny_32x32x8", n_irls=1)
+    ks, ms = _inputs(w, [0])
+    out = [torch.empty(tuple(ms[0].shape), dtype=torch.complex64, device="cuda")]
+    with pytest.raises(recon.ReconError) as e:
+        recon.recon_solve_batch(ctx.h, ks * 17, ms * 17, (5, 5, 2), w.lam, w.p, 1, 1, out * 17)
+    assert e.value.code == recon.RECON_EINVAL
