@@ -106,6 +106,13 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims d, const void* const* kspa
                       const uint8_t* const* masks, recon_filter f, const recon_params* prm,
                       void* const* image_out);
 
+/* recon_solve and recon_solve_batch capture a whole solve (every launch of Algorithm 1) into a
+ * CUDA graph on first use and replay it while the shapes, parameters, buffer pointers and
+ * workspace stay the same (one graph per slot). Graphs are not used for the eigensolver-library
+ * path or while launch classes are timed. enable = 0 issues every launch directly (same
+ * results); the default is 1. */
+int recon_set_graphs(recon_ctx* c, int enable);
+
 /* ---- stage entry points (the same kernels recon_solve runs; used for parity checks) ---- */
 
 /* x = A^H b = F^H (mask * b) (Sec. II-A). */

@@ -434,6 +434,22 @@ int coop_grid(const void* kern, int* grid) {
 
 int padded(int s) { return (s + kB - 1) / kB * kB; }
 
+// Cooperative launch (all CTAs co-resident, required by the grid barriers) through
+// cudaLaunchKernelEx so that it can be captured into a CUDA graph.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kern)(KArgs...), int grid, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 }  // namespace
 
 size_t hpd_scratch_bytes(const Dims& d) {
@@ -464,8 +480,7 @@ cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, voi
     if (e != cudaSuccess) return e;
     int grid = 0;
     if (coop_grid((const void*)hpd_sweep_kernel, &grid)) return cudaErrorInvalidConfiguration;
-    void* args[] = {&G, (void*)&s, (void*)&eps, (void*)&np, &A, &Dinv2, &W, &C, &gb};
-    e = cudaLaunchCooperativeKernel((const void*)hpd_sweep_kernel, dim3(grid), dim3(kThreads), args, 0, st);
+    e = launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, np, A, Dinv2, W, C, gb);
     if (e != cudaSuccess) return e;
     if (err_flag_out) {
         // fold the barrier error into the caller's flag (max)
@@ -500,8 +515,7 @@ cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, 
     double* ab = reinterpret_cast<double*>(p);
     cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;
-    void* args[] = {(void*)&G, (void*)&s, (void*)&m, &u, &vprev, &part, &ab, &lmax, &gb};
-    e = cudaLaunchCooperativeKernel((const void*)lanczos_kernel, dim3(grid), dim3(kThreads), args, 0, st);
+    e = launch_coop(lanczos_kernel, grid, st, G, s, m, u, vprev, part, ab, lmax, gb);
     if (e != cudaSuccess) return e;
     if (err_flag_out) e = cudaMemcpyAsync(err_flag_out, &gb->err, sizeof(int), cudaMemcpyDeviceToDevice, st);
     return e;

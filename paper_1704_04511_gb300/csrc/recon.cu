@@ -60,11 +60,24 @@ struct recon_ctx {
     std::map<std::string, Buf> bufs;
     // Batch slots: each has its own stream, workspace and eigensolver handle. The fields
     // stream / bufs / solver above always hold the ACTIVE slot's; the others are parked here.
+    unsigned long ws_gen = 0;          // bumped when the active slot's workspace moves
+    struct GraphKey {
+        int T, P, Q, N1, N2, M, irls, cg, bf16, method;
+        double lambda, p, gamma, eps0_frac;
+        const void *kspace, *masks, *out;
+        unsigned long ws_gen;
+    };
+    GraphKey gkey = {};
+    cudaGraphExec_t gexec = nullptr;   // the active slot's captured solve
+    bool graphs = true;
     struct Slot {
         cudaStream_t stream = nullptr;
         bool own_stream = false;
         std::map<std::string, Buf> bufs;
         cusolverDnHandle_t solver = nullptr;
+        unsigned long ws_gen = 0;
+        GraphKey gkey = {};
+        cudaGraphExec_t gexec = nullptr;
     };
     std::vector<Slot> slots;  // slots[i] valid while i != active
     int active = 0;
@@ -147,6 +160,7 @@ int ensure(recon_ctx* c, const char* name, size_t bytes, void** out) {
         c->allocated -= b.bytes;
         b = Buf{};
     }
+    ++c->ws_gen;  // captured solves that point into this workspace are stale now
     const size_t want = bytes < 256 ? 256 : bytes;
     if (c->budget && c->allocated + want > c->budget)
         return fail(c, RECON_ENOMEM, std::string("workspace budget exceeded allocating ") + name);
@@ -248,6 +262,7 @@ struct Work {
     void *hpd, *lanc;
     int lwork;
     int gblocks;
+    int n_status;
     bool use_eig;
 };
 
@@ -313,9 +328,15 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
         GET("lanc", recon::lanczos_scratch_bytes(d, sms), lanc, void*);
     }
 #undef GET
-    RC_CUDA(cudaMemsetAsync(w->counter, 0, sizeof(unsigned int), c->stream));
-    RC_CUDA(cudaMemsetAsync(w->info, 0, (size_t)ni * sizeof(int), c->stream));
-    RC_CUDA(cudaMemsetAsync(w->kerr, 0, (size_t)2 * ni * sizeof(int), c->stream));
+    w->n_status = ni;
+    return RECON_OK;
+}
+
+// Reset the counters and status words of a workspace (stream-ordered; part of a captured solve).
+int reset_status(recon_ctx* c, Work& w) {
+    RC_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), c->stream));
+    RC_CUDA(cudaMemsetAsync(w.info, 0, (size_t)w.n_status * sizeof(int), c->stream));
+    RC_CUDA(cudaMemsetAsync(w.kerr, 0, (size_t)2 * w.n_status * sizeof(int), c->stream));
     return RECON_OK;
 }
 
@@ -432,6 +453,9 @@ int select_slot(recon_ctx* c, int i) {
     park.own_stream = c->own_stream;
     park.bufs = std::move(c->bufs);
     park.solver = c->solver;
+    park.ws_gen = c->ws_gen;
+    park.gkey = c->gkey;
+    park.gexec = c->gexec;
     auto& next = c->slots[i];
     if (!next.stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&next.stream, cudaStreamNonBlocking);
@@ -445,6 +469,9 @@ int select_slot(recon_ctx* c, int i) {
     c->own_stream = next.own_stream;
     c->bufs = std::move(next.bufs);
     c->solver = next.solver;
+    c->ws_gen = next.ws_gen;
+    c->gkey = next.gkey;
+    c->gexec = next.gexec;
     next = recon_ctx::Slot{};
     c->active = i;
     return RECON_OK;
@@ -480,14 +507,16 @@ struct Solve {
     Twiddles tw;
     Work w;
     float2* x;
+    const void* kspace;
     const uint8_t* masks;
     const recon_params* prm;
 };
 
-// Workspace, x0 = A^H b (Algorithm 1 initialisation). Enqueues only.
-int solve_begin(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* masks,
-                const recon_params* prm, void* image_out, Solve* sv) {
+// Twiddles, eigensolver handle and workspace of one solve on the active slot (no stream work).
+int solve_prepare(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* masks,
+                  const recon_params* prm, void* image_out, Solve* sv) {
     sv->d = d;
+    sv->kspace = kspace;
     sv->masks = masks;
     sv->prm = prm;
     sv->x = reinterpret_cast<float2*>(image_out);
@@ -498,11 +527,16 @@ int solve_begin(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* 
         rc = ensure_solver(c);
         if (rc) return rc;
     }
-    rc = get_work(c, d, prm->cg, prm->irls, true, eig, &sv->w);
+    return get_work(c, d, prm->cg, prm->irls, true, eig, &sv->w);
+}
+
+// Status reset and x0 = A^H b (Algorithm 1 initialisation). Enqueues only.
+int solve_begin(recon_ctx* c, Solve* sv) {
+    int rc = reset_status(c, sv->w);
     if (rc) return rc;
     ProfScope ps(c, RECON_PROF_ADJOINT);
-    RC_CUDA(recon::launch_adjoint(d, sv->tw, kspace, prm->kspace_bf16, masks, sv->w.t, sv->x,
-                                  c->stream));
+    RC_CUDA(recon::launch_adjoint(sv->d, sv->tw, sv->kspace, sv->prm->kspace_bf16, sv->masks,
+                                  sv->w.t, sv->x, c->stream));
     return RECON_OK;
 }
 
@@ -522,6 +556,51 @@ int solve_iter(recon_ctx* c, Solve& sv, int n) {
     if (rc) return rc;
     return cg_block(c, d, sv.tw, w, sv.masks, S_old, S_new, (float)sv.prm->lambda, sv.x, n == 0,
                     sv.prm->cg);
+}
+
+// Enqueue a whole solve on the active slot's stream: as one replay of a captured CUDA graph
+// (captured on first use, cached per slot and keyed by shapes, parameters, buffers and the
+// workspace generation), or as direct launches when graphs are off, when the eigensolver
+// library path is used, or while launch classes are being timed.
+int solve_enqueue_all(recon_ctx* c, Solve& sv) {
+    const recon_params* prm = sv.prm;
+    const bool direct = !c->graphs || c->prof || wants_eig(prm->p, prm->weight_method);
+    if (direct) {
+        int rc = solve_begin(c, &sv);
+        for (int n = 0; n < prm->irls && !rc; ++n) rc = solve_iter(c, sv, n);
+        return rc;
+    }
+    recon_ctx::GraphKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.T = sv.d.T; k.P = sv.d.P; k.Q = sv.d.Q; k.N1 = sv.d.N1; k.N2 = sv.d.N2; k.M = sv.d.M;
+    k.irls = prm->irls; k.cg = prm->cg; k.bf16 = prm->kspace_bf16; k.method = prm->weight_method;
+    k.lambda = prm->lambda; k.p = prm->p; k.gamma = prm->gamma; k.eps0_frac = prm->eps0_frac;
+    k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
+    if (!c->gexec || std::memcmp(&k, &c->gkey, sizeof(k)) != 0) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        RC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        int rc = solve_begin(c, &sv);
+        for (int n = 0; n < prm->irls && !rc; ++n) rc = solve_iter(c, sv, n);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return cuda_fail(c, ec, "cudaStreamEndCapture");
+        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return cuda_fail(c, ei, "cudaGraphInstantiate");
+        }
+        c->gkey = k;
+    }
+    RC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    return RECON_OK;
 }
 
 // After the slot's stream finished: status flags, finite residual and eps.
@@ -586,6 +665,7 @@ void recon_destroy(recon_ctx* c) {
     select_slot(c, 0);
     for (auto& sl : c->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
         for (auto& kv : sl.bufs)
             if (kv.second.ptr) cudaFree(kv.second.ptr);
         if (sl.solver) cusolverDnDestroy(sl.solver);
@@ -599,6 +679,7 @@ void recon_destroy(recon_ctx* c) {
         cudaFree(kv.second.d);
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->solver) cusolverDnDestroy(c->solver);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -636,12 +717,10 @@ int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* 
     rc = select_slot(c, 0);
     if (rc) return rc;
     Solve sv;
-    rc = solve_begin(c, d, kspace, masks, prm, image_out, &sv);
+    rc = solve_prepare(c, d, kspace, masks, prm, image_out, &sv);
     if (rc) return rc;
-    for (int n = 0; n < prm->irls; ++n) {
-        rc = solve_iter(c, sv, n);
-        if (rc) return rc;
-    }
+    rc = solve_enqueue_all(c, sv);
+    if (rc) return rc;
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return solve_check(c, sv);
 }
@@ -674,13 +753,17 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
     std::vector<Solve> sv(n);
     rc = RECON_OK;
     cudaError_t e = cudaEventRecord(start, c->stream);
+    const bool direct = !c->graphs || c->prof || wants_eig(prm->p, prm->weight_method);
     for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
         rc = select_slot(c, i);
         if (!rc) e = cudaStreamWaitEvent(c->stream, start, 0);
-        if (!rc && e == cudaSuccess) rc = solve_begin(c, d, kspace[i], masks[i], prm, image_out[i], &sv[i]);
+        if (!rc && e == cudaSuccess) rc = solve_prepare(c, d, kspace[i], masks[i], prm, image_out[i], &sv[i]);
+        if (!rc && e == cudaSuccess && !direct) rc = solve_enqueue_all(c, sv[i]);
+        if (!rc && e == cudaSuccess && direct) rc = solve_begin(c, &sv[i]);
     }
-    // iterations interleaved over the slots so that every stream has work queued early
-    for (int it = 0; it < prm->irls && !rc && e == cudaSuccess; ++it)
+    // direct launches: iterations interleaved over the slots so that every stream has work
+    // queued early
+    for (int it = 0; direct && it < prm->irls && !rc && e == cudaSuccess; ++it)
         for (int i = 0; i < n && !rc; ++i) {
             rc = select_slot(c, i);
             if (!rc) rc = solve_iter(c, sv[i], it);
@@ -784,6 +867,8 @@ int recon_weight(recon_ctx* c, recon_dims dd, recon_filter f, const void* G_in, 
     Work w;
     rc = get_work(c, d, 1, 1, false, wants_eig(p, method), &w);
     if (rc) return rc;
+    rc = reset_status(c, w);
+    if (rc) return rc;
     const size_t gbytes = (size_t)d.s() * d.s() * sizeof(double2);
     RC_CUDA(cudaMemcpyAsync(w.G, G_in, gbytes, cudaMemcpyDeviceToDevice, c->stream));
     const bool set = eps_in >= 0.0;
@@ -867,6 +952,8 @@ int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, 
     Work w;
     rc = get_work(c, d, n_cg, 1, true, false, &w);
     if (rc) return rc;
+    rc = reset_status(c, w);
+    if (rc) return rc;
     // the caller's r is the residual buffer for this call
     float2* r_save = w.r;
     w.r = (float2*)r;
@@ -877,6 +964,12 @@ int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, 
     RC_CUDA(cudaStreamSynchronize(c->stream));
     if (rr_hist)
         RC_CUDA(cudaMemcpy(rr_hist, w.rr, (size_t)(n_cg + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    return RECON_OK;
+}
+
+int recon_set_graphs(recon_ctx* c, int enable) {
+    if (!c) return RECON_EINVAL;
+    c->graphs = enable != 0;
     return RECON_OK;
 }
 

@@ -37,7 +37,7 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
             "recon_profile_read", "recon_profile_name", "recon_gram_static",
-            "recon_solve_batch")
+            "recon_solve_batch", "recon_set_graphs")
 
 PROF_KINDS = 13
 
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_profile_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
             "recon_profile_name": (ctypes.c_char_p, [i]),
             "recon_gram_static": (i, [dims, filt, vp, vp, vp, vp]),
+            "recon_set_graphs": (i, [vp, i]),
             "recon_solve_batch": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp), filt,
                                       ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
         }
@@ -192,6 +193,10 @@ def recon_solve_batch(ctx, kspaces, masks_list, filt, lam: float, p: float, irls
     op = arr(*[_ptr(t) for t in image_outs])
     _check(ctx, load_library().recon_solve_batch(ctx, int(n), _dims(masks_list[0]), kp, mp,
                                                  _filt(filt), ctypes.byref(prm), op))
+
+
+def recon_set_graphs(ctx, enable: bool) -> None:
+    _check(ctx, load_library().recon_set_graphs(ctx, int(enable)))
 
 
 def recon_adjoint(ctx, kspace, masks, x_out) -> None:
