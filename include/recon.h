@@ -106,12 +106,19 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims d, const void* const* kspa
                       const uint8_t* const* masks, recon_filter f, const recon_params* prm,
                       void* const* image_out);
 
-/* recon_solve and recon_solve_batch capture a whole solve (every launch of Algorithm 1) into a
- * CUDA graph on first use and replay it while the shapes, parameters, buffer pointers and
- * workspace stay the same (one graph per slot). Graphs are not used for the eigensolver-library
- * path or while launch classes are timed. enable = 0 issues every launch directly (same
- * results); the default is 1. */
-int recon_set_graphs(recon_ctx* c, int enable);
+/* Context options (value 0 = off, 1 = on; results are the same either way up to floating-point
+ * rounding of the operator, see the parity tests):
+ * RECON_OPT_GRAPHS: recon_solve and recon_solve_batch capture a whole solve (every launch of
+ *   Algorithm 1) into a CUDA graph on first use and replay it while the shapes, parameters,
+ *   buffer pointers and workspace stay the same (one graph per slot). Not used for the
+ *   eigensolver-library path or while launch classes are timed.
+ * RECON_OPT_CLUSTER_FFT: for square frames (P = Q in {32, 64, 128, 192, 256}) the CG operator
+ *   runs each frame's 2-D transform, mask and inverse in one kernel on an 8-CTA cluster
+ *   (distributed shared memory), followed by a pixel-parallel W pass; off = the row / column
+ *   passes used for every other shape. */
+#define RECON_OPT_GRAPHS 1      /* default on  */
+#define RECON_OPT_CLUSTER_FFT 2 /* default off */
+int recon_set_option(recon_ctx* c, int option, int value);
 
 /* ---- stage entry points (the same kernels recon_solve runs; used for parity checks) ---- */
 
@@ -207,7 +214,9 @@ int recon_gram_static(recon_dims d, recon_filter f, const void* x, void* G_out, 
 #define RECON_PROF_CG_UPDATE 10   /* CG pass D: x, r update + |r|^2 partials               */
 #define RECON_PROF_LANCZOS 11     /* lambda_max of G for eps0 (p = 0 path)                 */
 #define RECON_PROF_INV 12         /* FP64 sweep inverse (G + eps I)^-1 (p = 0 path)        */
-#define RECON_PROF_KINDS 13
+#define RECON_PROF_CG_FRAME 13    /* CG, square frames: p update + cluster F^H M F per frame */
+#define RECON_PROF_CG_WCOMB 14    /* CG, square frames: q = t + lambda W p, <p, q>          */
+#define RECON_PROF_KINDS 15
 
 #define RECON_PROF_ALL ((1u << RECON_PROF_KINDS) - 1u)
 

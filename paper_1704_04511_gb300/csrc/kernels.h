@@ -133,4 +133,14 @@ cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStr
 cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, double* lmax,
                                 int* err_flag_out, cudaStream_t st);
 
+// ---- frame_op.cu (square frames: cluster 2-D transform per frame + pixel-parallel W) ----
+bool frame_op_supported(const Dims& d);
+// p = r (first) or r + beta p; t = F^H (mask * F p) frame by frame (one 8-CTA cluster per frame)
+cudaError_t launch_frame_aha(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
+                             float2* t, const uint8_t* mask, const double* rr_num,
+                             const double* rr_den, int first, cudaStream_t st);
+// q = t + lam W_S p written over t; *pq_out = Re <p, q>
+cudaError_t launch_w_combine(const Dims& d, float2* t, const float2* p, const float2* S, float lam,
+                             const RedSlot& rs, double* pq_out, cudaStream_t st);
+
 }  // namespace recon

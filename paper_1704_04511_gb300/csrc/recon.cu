@@ -70,6 +70,7 @@ struct recon_ctx {
     GraphKey gkey = {};
     cudaGraphExec_t gexec = nullptr;   // the active slot's captured solve
     bool graphs = true;
+    bool cluster_fft = false;          // square frames: cluster 2-D transform kernel (opt-in)
     struct Slot {
         cudaStream_t stream = nullptr;
         bool own_stream = false;
@@ -412,7 +413,24 @@ int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uin
         ProfScope ps(c, RECON_PROF_RESID);
         RC_CUDA(recon::launch_resid_carry(d, w.r, x, S_old, S_new, lam, first, rs, w.rr, c->stream));
     }
-    for (int it = 0; it < n_cg; ++it) {
+    const bool fused = c->cluster_fft && recon::frame_op_supported(d);
+    for (int it = 0; fused && it < n_cg; ++it) {
+        {
+            ProfScope ps(c, RECON_PROF_CG_FRAME);
+            RC_CUDA(recon::launch_frame_aha(d, tw, w.r, w.p, w.t, mask, w.rr + it,
+                                            it > 0 ? w.rr + it - 1 : w.rr, it == 0, c->stream));
+        }
+        {
+            ProfScope ps(c, RECON_PROF_CG_WCOMB);
+            RC_CUDA(recon::launch_w_combine(d, w.t, w.p, S_new, lam, rs, w.pq + it, c->stream));
+        }
+        {
+            ProfScope ps(c, RECON_PROF_CG_UPDATE);
+            RC_CUDA(recon::launch_cg_update(d, x, w.r, w.p, w.t, w.rr + it, w.pq + it, rs,
+                                            w.rr + it + 1, c->stream));
+        }
+    }
+    for (int it = 0; !fused && it < n_cg; ++it) {
         {
             ProfScope ps(c, RECON_PROF_CG_ROWFWD);
             RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, w.rr + it,
@@ -911,12 +929,19 @@ int recon_apply_normal(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_
     if (rc) return rc;
     RC_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c->stream));
     const recon::RedSlot rs{(double*)parts, (unsigned int*)counter};
-    // pass A with first = 1 copies x into p and row-transforms it into y; passes B and C follow.
-    RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y, nullptr,
-                                          nullptr, 1, c->stream));
-    RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
-    RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
-                                    (float)lambda, rs, (double*)pq, c->stream));
+    // the CG operator passes with first = 1 (p = x); y receives (A^H A + lambda W) x
+    if (c->cluster_fft && recon::frame_op_supported(d)) {
+        RC_CUDA(recon::launch_frame_aha(d, tw, (const float2*)x, (float2*)pp, (float2*)y, masks,
+                                        nullptr, nullptr, 1, c->stream));
+        RC_CUDA(recon::launch_w_combine(d, (float2*)y, (const float2*)pp, (const float2*)S,
+                                        (float)lambda, rs, (double*)pq, c->stream));
+    } else {
+        RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y,
+                                              nullptr, nullptr, 1, c->stream));
+        RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
+        RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
+                                        (float)lambda, rs, (double*)pq, c->stream));
+    }
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return RECON_OK;
 }
@@ -967,10 +992,13 @@ int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, 
     return RECON_OK;
 }
 
-int recon_set_graphs(recon_ctx* c, int enable) {
+int recon_set_option(recon_ctx* c, int option, int value) {
     if (!c) return RECON_EINVAL;
-    c->graphs = enable != 0;
-    return RECON_OK;
+    switch (option) {
+        case RECON_OPT_GRAPHS: c->graphs = value != 0; return RECON_OK;
+        case RECON_OPT_CLUSTER_FFT: c->cluster_fft = value != 0; return RECON_OK;
+        default: return fail(c, RECON_EINVAL, "unknown option");
+    }
 }
 
 int recon_profile(recon_ctx* c, unsigned int kind_mask) {
@@ -997,7 +1025,8 @@ int recon_profile_read(recon_ctx* c, int kind, double* total_ms, long long* laun
 const char* recon_profile_name(int kind) {
     static const char* names[RECON_PROF_KINDS] = {
         "adjoint", "gram", "eig", "eps", "diag_sums", "weight_S", "resid_carry",
-        "cg_row_fwd", "cg_col_mask", "cg_row_inv_w", "cg_update", "lanczos", "hpd_inverse"};
+        "cg_row_fwd", "cg_col_mask", "cg_row_inv_w", "cg_update", "lanczos", "hpd_inverse",
+        "cg_frame_aha", "cg_w_combine"};
     return (kind >= 0 && kind < RECON_PROF_KINDS) ? names[kind] : "";
 }
 

@@ -37,9 +37,9 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
             "recon_profile_read", "recon_profile_name", "recon_gram_static",
-            "recon_solve_batch", "recon_set_graphs")
+            "recon_solve_batch", "recon_set_option")
 
-PROF_KINDS = 13
+PROF_KINDS = 15
 
 
 class ReconError(RuntimeError):
@@ -96,7 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_profile_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
             "recon_profile_name": (ctypes.c_char_p, [i]),
             "recon_gram_static": (i, [dims, filt, vp, vp, vp, vp]),
-            "recon_set_graphs": (i, [vp, i]),
+            "recon_set_option": (i, [vp, i, i]),
             "recon_solve_batch": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp), filt,
                                       ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
         }
@@ -195,8 +195,12 @@ def recon_solve_batch(ctx, kspaces, masks_list, filt, lam: float, p: float, irls
                                                  _filt(filt), ctypes.byref(prm), op))
 
 
-def recon_set_graphs(ctx, enable: bool) -> None:
-    _check(ctx, load_library().recon_set_graphs(ctx, int(enable)))
+RECON_OPT_GRAPHS = 1
+RECON_OPT_CLUSTER_FFT = 2
+
+
+def recon_set_option(ctx, option: int, value: int) -> None:
+    _check(ctx, load_library().recon_set_option(ctx, int(option), int(value)))
 
 
 def recon_adjoint(ctx, kspace, masks, x_out) -> None:
@@ -252,7 +256,7 @@ def recon_cg(ctx, masks, filt, S_old, S_new, lam: float, x, r, n_cg: int):
     return list(hist)
 
 
-PROF_ALL = (1 << 13) - 1
+PROF_ALL = (1 << 15) - 1
 
 
 def recon_profile(ctx, kind_mask: int) -> None:

@@ -86,9 +86,9 @@ def test_graph_replay_matches_direct_launches(R):
         return out.cpu().numpy()
 
     shape = tuple(ms[0].shape)
-    recon.recon_set_graphs(ctx.h, False)
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_GRAPHS, 0)
     direct = run(torch.empty(shape, dtype=torch.complex64, device="cuda"))
-    recon.recon_set_graphs(ctx.h, True)
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_GRAPHS, 1)
     o1 = torch.empty(shape, dtype=torch.complex64, device="cuda")
     first = run(o1)
     o1.fill_(float("nan"))

@@ -206,6 +206,27 @@ def test_normal_operator_parity(R, case):
     assert rel(y.cpu().numpy(), slr.apply_W(vr, S_full)) < 1e-5
 
 
+@pytest.mark.parametrize("name", ["tiny_32x32x8", "perf_256x256x16"])
+def test_cluster_operator_matches_row_column_passes(R, name):
+    """The square-frame cluster kernel and the row / column passes compute the same operator."""
+    recon, ctx = R
+    w, prob = _problem(name)
+    masks = prob["masks"]
+    rng = np.random.default_rng(17)
+    npair = w.M * (w.M + 1) // 2
+    S = to_dev(c64(crandn(rng, npair, w.P, w.Q)))
+    v = to_dev(c64(crandn(rng, *masks.shape)))
+    md = to_dev(masks)
+    ys = []
+    for opt in (1, 0):
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_CLUSTER_FFT, opt)
+        y = torch.empty_like(v)
+        recon.recon_apply_normal(ctx.h, md, (w.N1, w.N2, w.M), S, 0.37, v, y)
+        ys.append(y.cpu().numpy())
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_CLUSTER_FFT, 0)
+    assert rel(ys[0], ys[1]) < 2e-6
+
+
 def _oracle_cg_block(x, r, masks, S_old, S_new, lam, n_cg):
     """Residual carry + plain CG, FP64 (the formulation the library runs)."""
     if S_old is None:
