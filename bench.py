@@ -149,6 +149,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def whole_job_rate(local_ms: float, units_per_rank: float, dist=None, device=None):
+    """Max of the per-rank timed milliseconds over all ranks and the whole-job rate
+    (units of every rank / that time). Replicas: each rank does units_per_rank."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    tmax = float(t.item())
+    return tmax, world * units_per_rank / (tmax / 1000.0)
+
+
 def cpu_oracle_rate(w, prob, budget_s: float = 12.0, max_iters: int = 6):
     """FP64 oracle IRLS iterations/s on the host cores (bounded sample)."""
     import numpy as np
@@ -239,7 +252,7 @@ def main():
     if args.irls is not None:
         w = synth.workload(WORKLOAD, n_irls=args.irls)
     B = args.batch
-    probs = [synth.make_problem(synth.workload(w.name, n_irls=w.n_irls, seed=sd))
+    probs = [synth.make_problem(synth.workload(w.name, n_irls=w.n_irls, seed=100 * rank + sd))
              for sd in range(B)]
     prob = probs[0]
     b_host = [torch.from_numpy(np.ascontiguousarray(pr["kspace"], dtype=np.complex64)).pin_memory()
@@ -320,14 +333,10 @@ def main():
     clocks = sampler.stop() if sampler else None
     dom_ms, dom_n = recon.recon_profile_read(ctx.h, dom_kind)
     recon.recon_profile(ctx.h, 0)
-    t_local = torch.tensor([total_ms, single_ms], dtype=torch.float64, device=dev)
+    t_max_ms, value = whole_job_rate(total_ms, args.steps * B * w.n_irls, dist, dev)
+    single_max_ms, single_value = whole_job_rate(single_ms, args.steps * w.n_irls, dist, dev)
     if dist:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
         dist.barrier()
-    t_max_ms = float(t_local[0].item())
-    single_max_ms = float(t_local[1].item())
-    value = world * args.steps * B * w.n_irls / (t_max_ms / 1000.0)
-    single_value = world * args.steps * w.n_irls / (single_max_ms / 1000.0)
 
     # ---- end to end: pinned host buffers, copies inside the timed region
     if dist:
@@ -345,10 +354,7 @@ def main():
             out_host[i].copy_(outs[i], non_blocking=True)
     e1.record(stream)
     e1.synchronize()
-    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps * B * w.n_irls / (float(e2e_ms.item()) / 1000.0)
+    _, e2e_value = whole_job_rate(e0.elapsed_time(e1), args.steps * B * w.n_irls, dist, dev)
 
     if rank != 0:
         ctx.close()
