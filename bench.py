@@ -185,6 +185,35 @@ def cpu_oracle_rate(w, prob, budget_s: float = 12.0, max_iters: int = 6):
     return n / dt, n, dt, cores
 
 
+def run_served(n_requests: int, device: int) -> dict:
+    """Continuous batching over the served mix: n requests, Poisson arrivals at 20/s, sizes
+    {64, 128, 192, 256}^2, 8-24 frames, filters 5-9 x 2-3, 30 IRLS x 15 CG each."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1704_04511_gb300 import serve
+    mix = synth.served_mix(n_requests, rate_hz=20.0, seed=0)
+    reqs = []
+    for arrival, w in mix:
+        pr = synth.make_problem(w)
+        k = torch.from_numpy(np.ascontiguousarray(pr["kspace"], dtype=np.complex64)).cuda(device)
+        m = torch.from_numpy(pr["masks"]).cuda(device)
+        out = torch.empty(tuple(m.shape), dtype=torch.complex64, device=f"cuda:{device}")
+        reqs.append(serve.Request(arrival_s=arrival, kspace=k, masks=m, out=out,
+                                  filt=(w.N1, w.N2, w.M), lam=w.lam, p=w.p, irls=w.n_irls,
+                                  cg=w.n_cg))
+    srv = serve.Server(device, mem_budget_bytes=8 << 30, max_inflight=8)
+    try:
+        stats = srv.run(reqs)
+    finally:
+        srv.close()
+    stats["arrival_rate_hz"] = 20.0
+    stats["mix"] = "sizes {64,128,192,256}^2, T 8-24, filter {5,7,9}^2 x {2,3}, 30 IRLS x 15 CG"
+    stats["max_inflight"] = 8
+    return stats
+
+
 def run_reference(args, rank: int):
     import synth
     if rank != 0:
@@ -225,6 +254,9 @@ def main():
     ap.add_argument("--irls", type=int, default=None, help="override IRLS iterations (testing)")
     ap.add_argument("--batch", type=int, default=4,
                     help="independent problems solved concurrently per step (1 = single solve)")
+    ap.add_argument("--served", type=int, default=48,
+                    help="requests of the served mix (Poisson 20/s, mixed sizes) to serve after "
+                         "the timed steps, reported as p50/p99 latency; 0 = skip, 512 = full mix")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -420,6 +452,8 @@ def main():
                 "d2h_bytes_per_step": int(B * outs[0].numel() * 8)},
         "clocks": clocks,
     }
+    if args.served > 0:
+        line["served"] = run_served(args.served, local_rank)
     if not args.no_cpu_baseline:
         rate, n, dt, cores = cpu_oracle_rate(w, prob)
         line["cpu_baseline"] = {

@@ -43,6 +43,7 @@ extern "C" {
 #define RECON_ECUDA (-3)    /* CUDA runtime or library error                            */
 #define RECON_ENUMERIC (-4) /* NaN / Inf in the iteration, or eigensolver failure       */
 #define RECON_ETIMEOUT (-5) /* a bounded device-wide wait (grid barrier) gave up         */
+#define RECON_EBUSY (-6)    /* serving: no free request slot or workspace budget; retry  */
 
 /* How the weight H = (G + eps I)^(p/2-1) is formed (recon_params.weight_method):
  * RECON_WEIGHT_AUTO: p = 0 -> FP64 Hermitian sweep inverse (G + eps I)^-1 and a Lanczos
@@ -105,6 +106,22 @@ int recon_solve(recon_ctx* c, recon_dims d, const void* kspace, const uint8_t* m
 int recon_solve_batch(recon_ctx* c, int n, recon_dims d, const void* const* kspace,
                       const uint8_t* const* masks, recon_filter f, const recon_params* prm,
                       void* const* image_out);
+
+/* ---- serving: asynchronous requests (continuous batching) ----
+ * recon_submit queues one reconstruction (arguments as recon_solve; buffers must stay valid
+ * until the request completes) on a free request slot -- its own stream and workspace -- and
+ * returns at once with a ticket. Requests in flight overlap on the device; a new one can be
+ * submitted whenever a slot is free and its workspace (recon_bytes_needed) fits the context's
+ * budget next to the requests in flight (idle slots return their cached workspace first).
+ * Otherwise RECON_EBUSY: poll and retry. Up to RECON_MAX_BATCH requests in flight. Results are
+ * bitwise identical to recon_solve of the same request. Not for use from several host threads
+ * at once (like every call on one context). */
+int recon_submit(recon_ctx* c, recon_dims d, const void* kspace, const uint8_t* masks,
+                 recon_filter f, const recon_params* prm, void* image_out, int* ticket);
+/* Non-blocking completion check: *done = 0 while the request runs; once it finished, *done = 1,
+ * the ticket is released and the return value is the request's own status (RECON_OK or the
+ * error recon_solve would have returned). */
+int recon_poll(recon_ctx* c, int ticket, int* done);
 
 /* Context options (value 0 = off, 1 = on; results are the same either way up to floating-point
  * rounding of the operator, see the parity tests):

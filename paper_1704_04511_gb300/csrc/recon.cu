@@ -82,6 +82,9 @@ struct recon_ctx {
     };
     std::vector<Slot> slots;  // slots[i] valid while i != active
     int active = 0;
+    // asynchronous requests (recon_submit / recon_poll) use slots 1..RECON_MAX_BATCH
+    struct Pending;
+    std::vector<Pending*> pending;
     // optional per-launch CUDA-event timing (recon_profile): bit k times launch class k
     unsigned int prof = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -622,6 +625,7 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
 }
 
 // After the slot's stream finished: status flags, finite residual and eps.
+int solve_check(recon_ctx* c, Solve& sv);
 int solve_check(recon_ctx* c, Solve& sv) {
     int rc = check_status(c, sv.w, sv.prm->irls);
     if (rc) return rc;
@@ -633,6 +637,37 @@ int solve_check(recon_ctx* c, Solve& sv) {
             return fail(c, RECON_ENUMERIC, "non-finite residual or eps in the iteration");
     }
     return RECON_OK;
+}
+
+}  // namespace
+
+// One asynchronous request in flight on slot `slot`.
+struct recon_ctx::Pending {
+    int slot = 0;
+    bool busy = false;
+    recon_params prm = {};
+    Solve sv;
+    cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+// Free the workspaces of serving slots that have nothing in flight (memory-based admission).
+void release_idle(recon_ctx* c) {
+    for (size_t k = 0; k < c->pending.size(); ++k) {
+        recon_ctx::Pending* pd = c->pending[k];
+        if (!pd || pd->busy) continue;
+        const int i = pd->slot;
+        if (i == c->active || i >= (int)c->slots.size()) continue;
+        auto& sl = c->slots[i];
+        for (auto& kv : sl.bufs)
+            if (kv.second.ptr) {
+                cudaFree(kv.second.ptr);
+                c->allocated -= kv.second.bytes;
+            }
+        sl.bufs.clear();
+        ++sl.ws_gen;
+    }
 }
 
 }  // namespace
@@ -697,6 +732,10 @@ void recon_destroy(recon_ctx* c) {
         cudaFree(kv.second.d);
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (auto* pd : c->pending) {
+        if (pd && pd->done) cudaEventDestroy(pd->done);
+        delete pd;
+    }
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->solver) cusolverDnDestroy(c->solver);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -803,6 +842,92 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
     cleanup();
     if (e != cudaSuccess) return cuda_fail(c, e, "recon_solve_batch");
     return rc;
+}
+
+int recon_submit(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* masks,
+                 recon_filter f, const recon_params* prm, void* image_out, int* ticket) {
+    if (!c) return RECON_EINVAL;
+    if (!kspace || !masks || !prm || !image_out || !ticket) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_params(c, dd, f, prm, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    if (c->pending.empty()) {
+        c->pending.resize(RECON_MAX_BATCH, nullptr);
+        for (int k = 0; k < RECON_MAX_BATCH; ++k) {
+            c->pending[k] = new recon_ctx::Pending();
+            c->pending[k]->slot = k + 1;
+        }
+    }
+    recon_ctx::Pending* pd = nullptr;
+    for (auto* q : c->pending)
+        if (!q->busy) { pd = q; break; }
+    if (!pd) return fail(c, RECON_EBUSY, "every request slot is in flight; poll and retry");
+    // admission by memory: the request's workspace must fit the budget next to the requests in
+    // flight; idle slots give their cached workspaces back first
+    if (c->budget) {
+        const size_t need = recon_bytes_needed(dd, f, prm->kspace_bf16);
+        if (need > c->budget) return fail(c, RECON_ENOMEM, "request larger than the whole budget");
+        if (c->allocated + need > c->budget) release_idle(c);
+        if (c->allocated + need > c->budget)
+            return fail(c, RECON_EBUSY, "not enough workspace budget while other requests run");
+    }
+    pd->prm = *prm;
+    rc = select_slot(c, pd->slot);
+    if (!rc) rc = solve_prepare(c, d, kspace, masks, &pd->prm, image_out, &pd->sv);
+    if (rc == RECON_ENOMEM && c->budget) {
+        // the workspace did not fit next to the requests in flight: give idle slots' memory
+        // back and try once more, else report a transient refusal
+        select_slot(c, 0);
+        release_idle(c);
+        rc = select_slot(c, pd->slot);
+        if (!rc) rc = solve_prepare(c, d, kspace, masks, &pd->prm, image_out, &pd->sv);
+        if (rc == RECON_ENOMEM) {
+            select_slot(c, 0);
+            return fail(c, RECON_EBUSY, "not enough workspace budget while other requests run");
+        }
+    }
+    if (!rc) {
+        rc = solve_begin(c, &pd->sv);
+        for (int n = 0; n < pd->prm.irls && !rc; ++n) rc = solve_iter(c, pd->sv, n);
+    }
+    if (!rc && !pd->done) {
+        cudaError_t e = cudaEventCreateWithFlags(&pd->done, cudaEventDisableTiming);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "cudaEventCreate");
+    }
+    if (!rc) {
+        cudaError_t e = cudaEventRecord(pd->done, c->stream);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "cudaEventRecord");
+    }
+    const int rc0 = select_slot(c, 0);
+    if (rc) {
+        if (rc == RECON_ENOMEM) c->err += " (request not admitted)";
+        return rc;
+    }
+    if (rc0) return rc0;
+    pd->busy = true;
+    *ticket = pd->slot;
+    return RECON_OK;
+}
+
+int recon_poll(recon_ctx* c, int ticket, int* done) {
+    if (!c || !done) return RECON_EINVAL;
+    *done = 0;
+    if (ticket < 1 || ticket > (int)c->pending.size() || !c->pending[ticket - 1]->busy)
+        return fail(c, RECON_EINVAL, "no request in flight with this ticket");
+    recon_ctx::Pending* pd = c->pending[ticket - 1];
+    int rc = set_device(c);
+    if (rc) return rc;
+    const cudaError_t q = cudaEventQuery(pd->done);
+    if (q == cudaErrorNotReady) return RECON_OK;
+    pd->busy = false;
+    *done = 1;
+    if (q != cudaSuccess) return cuda_fail(c, q, "request stream");
+    rc = select_slot(c, pd->slot);
+    if (!rc) rc = solve_check(c, pd->sv);
+    const int rc0 = select_slot(c, 0);
+    return rc ? rc : rc0;
 }
 
 int recon_adjoint(recon_ctx* c, recon_dims dd, const void* kspace, int kspace_bf16,

@@ -26,18 +26,19 @@ RECON_ENOMEM = -2
 RECON_ECUDA = -3
 RECON_ENUMERIC = -4
 RECON_ETIMEOUT = -5
+RECON_EBUSY = -6
 RECON_WEIGHT_AUTO = 0
 RECON_WEIGHT_EIG = 1
 
 _ERR_NAMES = {RECON_EINVAL: "RECON_EINVAL", RECON_ENOMEM: "RECON_ENOMEM",
               RECON_ECUDA: "RECON_ECUDA", RECON_ENUMERIC: "RECON_ENUMERIC",
-              RECON_ETIMEOUT: "RECON_ETIMEOUT"}
+              RECON_ETIMEOUT: "RECON_ETIMEOUT", RECON_EBUSY: "RECON_EBUSY"}
 
 EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_needed",
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
             "recon_profile_read", "recon_profile_name", "recon_gram_static",
-            "recon_solve_batch", "recon_set_option")
+            "recon_solve_batch", "recon_set_option", "recon_submit", "recon_poll")
 
 PROF_KINDS = 15
 
@@ -97,6 +98,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_profile_name": (ctypes.c_char_p, [i]),
             "recon_gram_static": (i, [dims, filt, vp, vp, vp, vp]),
             "recon_set_option": (i, [vp, i, i]),
+            "recon_submit": (i, [vp, dims, vp, vp, filt, ctypes.POINTER(recon_params), vp,
+                                 ctypes.POINTER(i)]),
+            "recon_poll": (i, [vp, i, ctypes.POINTER(i)]),
             "recon_solve_batch": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp), filt,
                                       ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
         }
@@ -201,6 +205,32 @@ RECON_OPT_CLUSTER_FFT = 2
 
 def recon_set_option(ctx, option: int, value: int) -> None:
     _check(ctx, load_library().recon_set_option(ctx, int(option), int(value)))
+
+
+def recon_submit(ctx, kspace, masks, filt, lam: float, p: float, irls: int, cg: int, image_out,
+                 gamma: float = 1.4, eps0_frac: float = 0.01,
+                 weight_method: int = RECON_WEIGHT_AUTO):
+    """Queue one reconstruction; returns a ticket, or None when no slot / budget is free now."""
+    import torch
+    bf16 = kspace.dtype == torch.bfloat16
+    prm = recon_params(irls=int(irls), cg=int(cg), lambda_=float(lam), p=float(p),
+                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=int(bf16),
+                       weight_method=int(weight_method))
+    t = ctypes.c_int(0)
+    rc = load_library().recon_submit(ctx, _dims(masks), _ptr(kspace), _ptr(masks), _filt(filt),
+                                     ctypes.byref(prm), _ptr(image_out), ctypes.byref(t))
+    if rc == RECON_EBUSY:
+        return None
+    _check(ctx, rc)
+    return t.value
+
+
+def recon_poll(ctx, ticket: int) -> bool:
+    """True once the request finished (raises its error if it failed), False while it runs."""
+    done = ctypes.c_int(0)
+    rc = load_library().recon_poll(ctx, int(ticket), ctypes.byref(done))
+    _check(ctx, rc)
+    return bool(done.value)
 
 
 def recon_adjoint(ctx, kspace, masks, x_out) -> None:
