@@ -3,15 +3,22 @@
 // and eps0 = eps0_frac * lambda_max(G) (Sec. III-C) from a Lanczos iteration.
 //
 // The inverse is a blocked Hermitian sweep (Gauss-Jordan without pivoting, stable for Hermitian
-// positive-definite matrices) over 8 x 8 tiles, run as ONE cooperative kernel over every SM
-// (each CTA works four tiles at once in 64-thread groups with named barriers):
-//   per pivot block K:  D^-1 = (A_KK)^-1 (computed one step ahead by the CTA that owns A_KK),
-//                       W_KJ = D^-1 A_KJ,  C_IK = A_IK            (phase A, whole grid)
-//                       A_IJ -= C_IK W_KJ,  A_IK <- C_IK D^-1,  A_KJ <- W_KJ,  A_KK <- -D^-1
-//                                                                 (phase B, lower tiles only)
-// Sweeping every pivot leaves -A^{-1}; the Hermitian symmetry is kept at each step, so only the
-// lower tiles (and the full diagonal tiles) are updated. Grid barriers are bounded spin-waits:
-// on timeout the kernel records an error flag and returns.
+// positive-definite matrices) over 8 x 8 tiles of the padded matrix. Sweeping pivot block K with
+// D = (A_KK)^-1 maps, for I, J != K,
+//     A_IJ -> A_IJ - A_IK D A_KJ,   A_IK -> A_IK D,   A_KJ -> D A_KJ,   A_KK -> -D,
+// and sweeping every pivot leaves -A^{-1}. Hermitian symmetry holds after every step, so only the
+// lower tiles are kept (tile-major, 1 KB per tile). The kernel is ONE cooperative launch, one grid
+// barrier per pivot step, the lower tiles ping-ponging between two buffers so that a step reads
+// only the previous step's values:
+//   - "diagonal" CTAs own the diagonal tiles; the owner of tile (K+1, K+1) updates it first with
+//     the whole CTA and inverts it (the next pivot, D_{K+1}) while its other warps update the
+//     CTA's remaining diagonal tiles, so the serial pivot chain never waits behind bulk work;
+//   - the other CTAs each own chunks of up to four tiles of one tile row I: the chunk forms
+//     X = A_IK D_K once (split over the CTA's eight warps) and each 64-thread group applies
+//     A_IJ - X A_KJ to its tile.
+// FP64 on this part issues one warp instruction per ~19 cycles per SM whatever the active lanes,
+// so the products use full warps and the work is spread over every SM. Grid barriers are bounded
+// spin-waits: on timeout the kernel records an error flag and returns.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -21,15 +28,16 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kB = 8;                        // tile edge
-constexpr int kTileT = kB * kB;              // threads per tile group
-constexpr int kGroups = kThreads / kTileT;   // tiles a CTA works on at once
+constexpr int kTileT = kB * kB;              // elements of a tile = threads of a tile group
+constexpr int kGroups = kThreads / kTileT;   // tile groups per CTA
+constexpr int kChunk = 4;                    // off-diagonal tiles of one row handled per CTA pass
+constexpr int kMaxChunks = 128;              // chunks one off-diagonal CTA may own
 constexpr long long kSpinLimit = 1LL << 26;  // polls (~1 us each at most) before giving up
 
 struct GridBar {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int word;  // bit 31 flips when the last CTA arrives; bits 0-30 count arrivals
     int err;
-    int pad;
+    unsigned int pad[2];
 };
 
 RECON_DEV unsigned int ld_acquire(const unsigned int* p) {
@@ -42,36 +50,36 @@ RECON_DEV int ld_acquire(const int* p) {
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+RECON_DEV unsigned int atom_add_release(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
-// Generation barrier over gridDim.x co-resident CTAs (cooperative launch). Thread 0 of each CTA
-// arrives with one atomic and then polls the generation word with plain acquire loads. Returns
-// false (and sets gb->err) if the wait exceeded kSpinLimit polls; after a failure every later
-// call returns false at once so the kernel can unwind.
+// Barrier over gridDim.x co-resident CTAs (cooperative launch) with one atomic per CTA: CTA 0 adds
+// 2^31 - (gridDim.x - 1) and every other CTA adds 1, so bit 31 of the word flips exactly when the
+// last CTA arrives and the low bits return to zero. Thread 0 of each CTA then polls the word with
+// acquire loads. Returns false (and sets gb->err) if the wait exceeded kSpinLimit polls; after a
+// failure every later call returns false at once so the kernel can unwind.
 RECON_DEV bool grid_barrier(GridBar* gb) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = (ld_acquire(&gb->err) == 0);
         if (ok) {
-            const unsigned int g = ld_acquire(&gb->gen);
             __threadfence();
-            const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
-            if (arrived == gridDim.x) {
-                atomicExch(&gb->count, 0u);
-                __threadfence();
-                atomicAdd(&gb->gen, 1u);
-            } else {
-                long long it = 0;
-                while (ld_acquire(&gb->gen) == g) {
-                    if (++it > kSpinLimit) {
-                        atomicExch(&gb->err, 1);
-                        ok = 0;
-                        break;
-                    }
-                    if ((it & 1023) == 0 && ld_acquire(&gb->err) != 0) {
-                        ok = 0;
-                        break;
-                    }
+            const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+            const unsigned int old = atom_add_release(&gb->word, inc);
+            long long it = 0;
+            while (((ld_acquire(&gb->word) ^ old) & 0x80000000u) == 0u) {
+                if (++it > kSpinLimit) {
+                    atomicExch(&gb->err, 1);
+                    ok = 0;
+                    break;
+                }
+                if ((it & 1023) == 0 && ld_acquire(&gb->err) != 0) {
+                    ok = 0;
+                    break;
                 }
             }
             __threadfence();
@@ -115,109 +123,218 @@ RECON_DEV void tile_inverse(double2* T, double2* out, double* s_inv, double2* s_
     group_sync(g);
 }
 
-__global__ void __launch_bounds__(kThreads)
-hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int np,
-                 double2* __restrict__ A, double2* __restrict__ Dinv2, double2* __restrict__ W,
-                 double2* __restrict__ C, GridBar* gb) {
-    __shared__ double2 ta[kGroups][kTileT];
-    __shared__ double2 tb[kGroups][kTileT];
-    __shared__ double s_inv[kGroups];
-    __shared__ double2 s_row[kGroups][kB];
-    const int nt = np / kB;
-    const double eps = eps_p[0];
+// Lower tile (I, J), J <= I: offset of its 64 elements, element (i, j) at i + 8 j.
+RECON_DEV size_t tile_off(int I, int J) { return ((size_t)I * (I + 1) / 2 + J) * kTileT; }
+
+// Element e = i + 8 q of the block (I, K) of the full Hermitian matrix held as lower tiles.
+RECON_DEV double2 block_elem(const double2* A, int I, int K, int e) {
+    if (I >= K) return A[tile_off(I, K) + e];
+    return zconj(A[tile_off(K, I) + e / kB + kB * (e % kB)]);
+}
+
+// (I, J) of lower tile number t in row-major order of the lower triangle.
+RECON_DEV void tile_ij(int t, int* I, int* J) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    *I = r;
+    *J = t - r * (r + 1) / 2;
+}
+
+struct SweepSmem {
+    double2 D[kTileT];              // D_K
+    double2 P[kGroups][kTileT];     // A_IK per group (diagonal CTAs) / per chunk (slot 0)
+    double2 B[kGroups][kTileT];     // A_KJ per group
+    double2 X[kGroups][kTileT];     // X = A_IK D_K per group / per chunk (slot 0)
+    double2 Xp[kGroups][kTileT];    // partial products over quarters of q
+    double s_inv[kGroups];
+    double2 s_row[kGroups][kB];
+    int chunk[kMaxChunks];          // (I << 16) | (J0 << 4) | nj of this CTA's chunks
+    int nchunk;
+};
+
+// One diagonal tile I at step K by the 64-thread group g (not the next pivot).
+RECON_DEV void diag_tile_group(SweepSmem& sm, const double2* Ain, double2* Aout, const double2* DK,
+                               int I, int K, int g) {
+    const int e = threadIdx.x % kTileT, i = e % kB, j = e / kB;
+    if (I == K) {
+        const double2 d = DK[e];
+        Aout[tile_off(K, K) + e] = make_double2(-d.x, -d.y);
+        return;
+    }
+    const double2 own = Ain[tile_off(I, I) + e];
+    sm.P[g][e] = block_elem(Ain, I, K, e);
+    sm.B[g][e] = DK[e];
+    group_sync(g);
+    double2 x = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < kB; ++q) x = zfma(sm.P[g][i + kB * q], sm.B[g][q + kB * j], x);
+    sm.X[g][e] = x;
+    group_sync(g);
+    // A_KI = (A_IK)^H:  new = own - X (A_IK)^H
+    double2 v = own;
+#pragma unroll
+    for (int q = 0; q < kB; ++q) v = zfms(sm.X[g][i + kB * q], zconj(sm.P[g][j + kB * q]), v);
+    Aout[tile_off(I, I) + e] = v;
+    group_sync(g);
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt, int ndc,
+                 double2* __restrict__ A0, double2* __restrict__ A1, double2* __restrict__ Dbuf,
+                 GridBar* gb) {
+    __shared__ SweepSmem sm;
     const int tid = threadIdx.x;
     const int g = tid / kTileT, e = tid % kTileT;
-    const int ii = e % kB, jj = e / kB;
+    const int i = e % kB, j = e / kB;
+    const int h = g;  // quarter of the q range in the split products
+    const int nlt = nt * (nt + 1) / 2;
+    const double eps = eps_p[0];
+    const bool diag_cta = (int)blockIdx.x < ndc;
+    const int noc = (int)gridDim.x - ndc;
+
+    // this CTA's off-diagonal chunks: row I (1..nt-1), columns J0 .. J0 + nj - 1 (J0 < I)
+    if (tid == 0) {
+        int n = 0;
+        if (!diag_cta) {
+            int ch = 0;
+            for (int I = 1; I < nt; ++I)
+                for (int J0 = 0; J0 < I; J0 += kChunk, ++ch)
+                    if (ch % noc == (int)blockIdx.x - ndc && n < kMaxChunks)
+                        sm.chunk[n++] = (I << 16) | (J0 << 4) | min(kChunk, I - J0);
+        }
+        sm.nchunk = n;
+    }
+    // A0 = pad(G + eps I), lower tiles; padding is the identity
+    for (int t = blockIdx.x * kGroups + g; t < nlt; t += gridDim.x * kGroups) {
+        int I, J;
+        tile_ij(t, &I, &J);
+        const int r = I * kB + i, c = J * kB + j;
+        double2 v = make_double2(r == c ? 1.0 : 0.0, 0.0);
+        if (r < s && c < s) {
+            v = G[r + (size_t)c * s];
+            if (r == c) v.x += eps;
+        }
+        A0[tile_off(I, J) + e] = v;
+    }
+    if (!grid_barrier(gb)) return;
+    if (blockIdx.x == 0 && g == 0) {  // D_0, by the owner of tile (0, 0)
+        sm.X[0][e] = A0[e];
+        group_sync(0);
+        tile_inverse(sm.X[0], Dbuf, &sm.s_inv[0], sm.s_row[0], 0);
+    }
+    if (!grid_barrier(gb)) return;
+
+    for (int K = 0; K < nt; ++K) {
+        const double2* Ain = (K & 1) ? A1 : A0;
+        double2* Aout = (K & 1) ? A0 : A1;
+        const double2* DK = Dbuf + (K & 1) * kTileT;
+        double2* Dnext = Dbuf + ((K + 1) & 1) * kTileT;
+        if (diag_cta) {
+            const int c = blockIdx.x;
+            const int piv = K + 1;
+            const bool has_piv = piv < nt && piv % ndc == c;
+            if (has_piv) {
+                // next pivot tile (K+1, K+1) with all eight warps: X = A_{K+1,K} D_K (quarters
+                // of q), then new = own - X (A_{K+1,K})^H, then its inverse D_{K+1}
+                if (tid < kTileT) sm.D[e] = DK[e];
+                else if (tid < 2 * kTileT) sm.P[0][e] = Ain[tile_off(piv, K) + e];
+                const double2 own = Ain[tile_off(piv, piv) + e];
+                __syncthreads();
+                double2 x = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int q = 2 * h; q < 2 * h + 2; ++q) x = zfma(sm.P[0][i + kB * q], sm.D[q + kB * j], x);
+                sm.Xp[h][e] = x;
+                __syncthreads();
+                if (tid < kTileT)
+                    sm.X[0][e] = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
+                __syncthreads();
+                double2 u = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int q = 2 * h; q < 2 * h + 2; ++q)
+                    u = zfma(sm.X[0][i + kB * q], zconj(sm.P[0][j + kB * q]), u);
+                sm.Xp[h][e] = u;
+                __syncthreads();
+                if (tid < kTileT) {
+                    const double2 sum = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
+                    const double2 v = make_double2(own.x - sum.x, own.y - sum.y);
+                    Aout[tile_off(piv, piv) + e] = v;
+                    sm.Xp[0][e] = v;  // the same thread read slot (0, e) above
+                }
+                __syncthreads();
+                if (g == 0) {
+                    tile_inverse(sm.Xp[0], Dnext, &sm.s_inv[0], sm.s_row[0], 0);
+                } else {
+                    // the CTA's other diagonal tiles on groups 1..3 meanwhile
+                    int m = 0;
+                    for (int I = c; I < nt; I += ndc) {
+                        if (I == piv) continue;
+                        if (m++ % (kGroups - 1) == g - 1) diag_tile_group(sm, Ain, Aout, DK, I, K, g);
+                    }
+                }
+            } else {
+                int m = 0;
+                for (int I = c; I < nt; I += ndc)
+                    if (m++ % kGroups == g) diag_tile_group(sm, Ain, Aout, DK, I, K, g);
+            }
+        } else {
+            for (int ci = 0; ci < sm.nchunk; ++ci) {
+                const int code = sm.chunk[ci];
+                const int I = code >> 16, J0 = (code >> 4) & 0xfff, nj = code & 15;
+                const int J = J0 + g;
+                const bool mine = g < nj;
+                if (tid < kTileT) sm.D[e] = DK[e];
+                else if (tid < 2 * kTileT && I != K) sm.P[0][e] = block_elem(Ain, I, K, e);
+                double2 own = make_double2(0.0, 0.0);
+                if (mine) {
+                    own = Ain[tile_off(I, J) + e];
+                    if (I == K) sm.B[g][e] = own;
+                    else if (J != K) sm.B[g][e] = block_elem(Ain, K, J, e);
+                }
+                __syncthreads();
+                if (I == K) {
+                    // row K: new = D_K A_KJ
+                    if (mine) {
+                        double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+                        for (int q = 0; q < kB; ++q) v = zfma(sm.D[i + kB * q], sm.B[g][q + kB * j], v);
+                        Aout[tile_off(I, J) + e] = v;
+                    }
+                } else {
+                    double2 x = make_double2(0.0, 0.0);
+#pragma unroll
+                    for (int q = 2 * h; q < 2 * h + 2; ++q) x = zfma(sm.P[0][i + kB * q], sm.D[q + kB * j], x);
+                    sm.Xp[h][e] = x;
+                    __syncthreads();
+                    if (tid < kTileT)
+                        sm.X[0][e] = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
+                    __syncthreads();
+                    if (mine) {
+                        double2 v;
+                        if (J == K) {
+                            v = sm.X[0][e];  // column K: new = A_IK D_K
+                        } else {
+                            v = own;
+#pragma unroll
+                            for (int q = 0; q < kB; ++q) v = zfms(sm.X[0][i + kB * q], sm.B[g][q + kB * j], v);
+                        }
+                        Aout[tile_off(I, J) + e] = v;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (!grid_barrier(gb)) return;
+    }
+    // H = -A (s x s, full, column-major) written over G
+    const double2* Af = (nt & 1) ? A1 : A0;
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + tid;
     const size_t gstride = (size_t)gridDim.x * blockDim.x;
-    // interleaved index: consecutive work items go to different CTAs (spreads the FP64 work)
-    const size_t itid = (size_t)tid * gridDim.x + blockIdx.x;
-
-    // A = pad(G + eps I): lower tiles and full diagonal tiles are the live part
-    for (size_t idx = gtid; idx < (size_t)np * np; idx += gstride) {
-        const int i = (int)(idx % np), j = (int)(idx / np);
-        double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
-        if (i < s && j < s) {
-            v = G[i + (size_t)j * s];
-            if (i == j) v.x += eps;
-        }
-        A[idx] = v;
-    }
-    if (!grid_barrier(gb)) return;
-    if (blockIdx.x == 0 && g == 0) {
-        ta[0][e] = A[ii + (size_t)jj * np];
-        group_sync(0);
-        tile_inverse(ta[0], Dinv2, &s_inv[0], s_row[0], 0);
-    }
-    if (!grid_barrier(gb)) return;
-
-    const int nlt = nt * (nt + 1) / 2;
-    const int ngroups = gridDim.x * kGroups;
-    for (int K = 0; K < nt; ++K) {
-        const double2* D = Dinv2 + (K & 1) * kTileT;
-        double2* Dnext = Dinv2 + ((K + 1) & 1) * kTileT;
-        const int k0 = K * kB;
-        // ---- phase A: W = D^-1 A_K,: (8 x np) and C = A_:,K (np x 8), old values
-        if (itid < (size_t)np * kB) {
-            const int m = (int)(itid % kB);       // pivot-local index
-            const int col = (int)(itid / kB);     // global column (for W) / row (for C)
-            const int J = col / kB;
-            double2 acc = make_double2(0.0, 0.0);
-            if (J != K) {
-#pragma unroll
-                for (int q = 0; q < kB; ++q) {
-                    const double2 a = (J < K) ? A[(k0 + q) + (size_t)col * np]
-                                              : zconj(A[col + (size_t)(k0 + q) * np]);
-                    acc = zfma(D[m + q * kB], a, acc);
-                }
-            }
-            W[m + (size_t)col * kB] = acc;
-            C[col + (size_t)m * np] = (J >= K) ? A[col + (size_t)(k0 + m) * np]
-                                               : zconj(A[(k0 + m) + (size_t)col * np]);
-        }
-        if (!grid_barrier(gb)) return;
-        // ---- phase B: lower tiles, one per 64-thread group; the group that owns tile
-        // (K+1, K+1) also inverts it (look-ahead pivot)
-        for (int t = blockIdx.x * kGroups + g; t < nlt; t += ngroups) {
-            int I = 0, rem = t;
-            while (rem > I) { rem -= I + 1; ++I; }
-            const int J = rem;                    // J <= I
-            const int row = I * kB + ii, col = J * kB + jj;
-            double2 v;
-            if (I == K && J == K) {
-                const double2 dd = D[ii + jj * kB];
-                v = make_double2(-dd.x, -dd.y);
-            } else if (I == K) {
-                v = W[ii + (size_t)col * kB];
-            } else if (J == K) {
-                double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-                for (int q = 0; q < kB; ++q) acc = zfma(C[row + (size_t)q * np], D[q + jj * kB], acc);
-                v = acc;
-            } else {
-                ta[g][e] = C[(I * kB + ii) + (size_t)jj * np];
-                tb[g][e] = W[ii + (size_t)(J * kB + jj) * kB];
-                group_sync(g);
-                double2 acc = A[row + (size_t)col * np];
-#pragma unroll
-                for (int q = 0; q < kB; ++q) acc = zfms(ta[g][ii + q * kB], tb[g][q + jj * kB], acc);
-                v = acc;
-                group_sync(g);
-            }
-            A[row + (size_t)col * np] = v;
-            if (I == J && I == K + 1) {
-                ta[g][e] = v;
-                group_sync(g);
-                tile_inverse(ta[g], Dnext, &s_inv[g], s_row[g], g);
-            }
-        }
-        if (!grid_barrier(gb)) return;
-    }
-    // ---- H = -A (s x s, full, column-major) written over G
     for (size_t idx = gtid; idx < (size_t)s * s; idx += gstride) {
-        const int i = (int)(idx % s), j = (int)(idx / s);
-        const int I = i / kB, J = j / kB;
-        const double2 v = (I >= J) ? A[i + (size_t)j * np] : zconj(A[j + (size_t)i * np]);
+        const int r = (int)(idx % s), c = (int)(idx / s);
+        const int I = r / kB, J = c / kB;
+        const double2 v = (I >= J) ? Af[tile_off(I, J) + r % kB + kB * (c % kB)]
+                                   : zconj(Af[tile_off(J, I) + c % kB + kB * (r % kB)]);
         G[idx] = make_double2(-v.x, -v.y);
     }
 }
@@ -432,7 +549,10 @@ int coop_grid(const void* kern, int* grid) {
     return 0;
 }
 
-int padded(int s) { return (s + kB - 1) / kB * kB; }
+int tiles_per_side(int s) { return (s + kB - 1) / kB; }
+
+// Diagonal CTAs of the sweep: two diagonal tiles each where the grid allows.
+int sweep_diag_ctas(int nt, int grid) { return max(1, min((nt + 1) / 2, grid / 8)); }
 
 // Cooperative launch (all CTAs co-resident, required by the grid barriers) through
 // cudaLaunchKernelEx so that it can be captured into a CUDA graph.
@@ -453,9 +573,9 @@ cudaError_t launch_coop(void (*kern)(KArgs...), int grid, cudaStream_t st, Args.
 }  // namespace
 
 size_t hpd_scratch_bytes(const Dims& d) {
-    const size_t np = (size_t)padded(d.s());
-    return 256 + np * np * sizeof(double2) + 2 * kB * kB * sizeof(double2) +
-           2 * np * kB * sizeof(double2) + 1024;
+    const size_t nt = (size_t)tiles_per_side(d.s());
+    const size_t nlt = nt * (nt + 1) / 2;
+    return 256 + 2 * nlt * kTileT * sizeof(double2) + 2 * kTileT * sizeof(double2) + 1024;
 }
 
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {
@@ -465,25 +585,29 @@ size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {
 
 cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
                                int* err_flag_out, cudaStream_t st) {
-    const int s = d.s(), np = padded(s);
+    const int s = d.s(), nt = tiles_per_side(s);
+    const size_t nlt = (size_t)nt * (nt + 1) / 2;
+    int grid = 0;
+    if (coop_grid((const void*)hpd_sweep_kernel, &grid) || grid < 2) return cudaErrorInvalidConfiguration;
+    const int ndc = sweep_diag_ctas(nt, grid);
+    // every off-diagonal chunk must fit the per-CTA chunk table
+    long long nch = 0;
+    for (int I = 1; I < nt; ++I) nch += (I + kChunk - 1) / kChunk;
+    if ((nch + (grid - ndc) - 1) / (grid - ndc) > kMaxChunks) return cudaErrorInvalidValue;
     unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
     GridBar* gb = reinterpret_cast<GridBar*>(p);
     p += 256;
-    double2* A = reinterpret_cast<double2*>(p);
-    p += (size_t)np * np * sizeof(double2);
-    double2* Dinv2 = reinterpret_cast<double2*>(p);
-    p += 2 * kB * kB * sizeof(double2);
-    double2* W = reinterpret_cast<double2*>(p);
-    p += (size_t)np * kB * sizeof(double2);
-    double2* C = reinterpret_cast<double2*>(p);
+    double2* A0 = reinterpret_cast<double2*>(p);
+    p += nlt * kTileT * sizeof(double2);
+    double2* A1 = reinterpret_cast<double2*>(p);
+    p += nlt * kTileT * sizeof(double2);
+    double2* Dbuf = reinterpret_cast<double2*>(p);
     cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;
-    int grid = 0;
-    if (coop_grid((const void*)hpd_sweep_kernel, &grid)) return cudaErrorInvalidConfiguration;
-    e = launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, np, A, Dinv2, W, C, gb);
+    e = launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, nt, ndc, A0, A1, Dbuf, gb);
     if (e != cudaSuccess) return e;
     if (err_flag_out) {
-        // fold the barrier error into the caller's flag (max)
+        // fold the barrier error into the caller's flag
         e = cudaMemcpyAsync(err_flag_out, &gb->err, sizeof(int), cudaMemcpyDeviceToDevice, st);
     }
     return e;
