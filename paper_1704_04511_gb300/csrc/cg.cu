@@ -9,6 +9,7 @@
 // upper triangle, pair (a <= b) at index a(2M-a+1)/2 + (b-a), layout [pair][P][Q] complex64.
 #include "common.cuh"
 #include "kernels.h"
+#include "regfft.cuh"
 
 namespace recon {
 
@@ -91,6 +92,79 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
         const int n = e / N, c = e % N;
         t[(size_t)n * npix + (size_t)r1 * N + c] = res[e];
+    }
+    last_block_sum(tot, parts, counter, pq_out);
+}
+
+// Pass C for 256-point rows: one CTA per image row r1 with 16 threads per frame (T * 16 threads);
+// the inverse row transforms run in registers (regfft.cuh), the rest as in row_inv_w_kernel.
+// Shared memory: p rows [T][256], then the exchange buffers [T'][16 x 17] (T' = T rounded up to
+// even: the block has whole warps) which afterwards hold the transformed rows [T][256].
+template <int M>
+__global__ void __launch_bounds__(1024)
+row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
+                     float lam, int T, int P, double* __restrict__ parts, unsigned int* counter,
+                     double* __restrict__ pq_out, const float2* __restrict__ tw_g) {
+    constexpr int N = 256;
+    extern __shared__ float2 sm[];
+    __shared__ float2 tw2[256];
+    __shared__ double red[32];
+    float2* pt = sm;
+    float2* res = sm + (size_t)T * N;
+    fill_tw256(tw2, tw_g);
+    pdl_wait();
+    const int n = threadIdx.x / 16, j = threadIdx.x % 16;
+    const bool live = n < T;  // the block is padded to whole warps (an odd T leaves a half-warp)
+    const int r1 = blockIdx.x;
+    const size_t npix = (size_t)P * N;
+    const size_t g0 = (size_t)n * npix + (size_t)r1 * N + j;
+    float2 u[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        u[n1] = make_float2(0.f, 0.f);
+        if (live) {
+            u[n1] = t[g0 + 16 * n1];
+            pt[n * N + 16 * n1 + j] = p[g0 + 16 * n1];
+        }
+    }
+    __syncthreads();  // tw2
+    row_dft256<true>(u, res + n * (16 * 17), tw2, j);
+    __syncthreads();  // every exchange buffer read
+    if (live) {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) res[n * N + j + 16 * k2] = u[k2];
+    }
+    __syncthreads();
+    const int k = T - M + 1;
+    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        float2 s[M][M];
+        load_S<M>(S, npix, (size_t)r1 * N + c, s);
+        for (int nn = 0; nn < T; ++nn) {
+            float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int aa = 0; aa < M; ++aa) {
+                const int jw = nn - M + 1 + aa;
+                if (jw < 0 || jw >= k) continue;
+#pragma unroll
+                for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(nn + aa - bb) * N + c], w);
+            }
+            float2 q = res[nn * N + c];
+            q.x = fmaf(lam, w.x, q.x);
+            q.y = fmaf(lam, w.y, q.y);
+            res[nn * N + c] = q;
+            const float2 pv = pt[nn * N + c];
+            const float term = fmaf(pv.x, q.x, pv.y * q.y) - comp;
+            const float sum = acc + term;
+            comp = (sum - acc) - term;
+            acc = sum;
+        }
+    }
+    const double tot = block_sum_f_t0(acc, red);
+    pdl_trigger();
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int nn = e / N, c = e % N;
+        t[(size_t)nn * npix + (size_t)r1 * N + c] = res[e];
     }
     last_block_sum(tot, parts, counter, pq_out);
 }
@@ -221,6 +295,20 @@ template <int N, int M>
 cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
                                 const float2* S, float lam, const RedSlot& rs, double* pq_out,
                                 cudaStream_t st) {
+    if constexpr (N == 256) {
+        const int tpad = (d.T + 1) / 2 * 2;
+        const size_t smem256 = ((size_t)d.T * N + (size_t)tpad * 16 * 17) * sizeof(float2);
+        if (tpad * 16 <= 1024 && smem256 <= 200 * 1024) {
+            auto k = row_inv_w_256_kernel<M>;
+            if (smem256 > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem256);
+                if (e != cudaSuccess) return e;
+            }
+            return launch_pdl(k, dim3(d.P), dim3(tpad * 16), smem256, st, t, p, S, lam, d.T, d.P,
+                              rs.parts, rs.counter, pq_out, tw.twQ);
+        }
+    }
     auto k = row_inv_w_kernel<N, M>;
     const size_t smem = ((size_t)3 * d.T * N + N) * sizeof(float2);
     if (smem > 48 * 1024) {

@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "regfft.cuh"
 
 namespace recon {
 
@@ -135,6 +136,103 @@ col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
     }
 }
 
+// ---- 256-point specialisations: transforms held in registers (regfft.cuh) ----
+constexpr int kR256Rows = 4;  // rows per 64-thread CTA, one half-warp per row
+
+// Pass A of a CG step for 256-point rows (same contract as row_fwd_pupdate_kernel).
+__global__ void __launch_bounds__(64)
+row_fwd_pupdate_256_kernel(const float2* __restrict__ r, float2* __restrict__ p,
+                           float2* __restrict__ t, int nrows, const double* __restrict__ rr_num,
+                           const double* __restrict__ rr_den, int first,
+                           const float2* __restrict__ tw_g) {
+    __shared__ float2 tw2[256];
+    __shared__ float2 sx[kR256Rows][16 * 17];
+    __shared__ float beta_s;
+    fill_tw256(tw2, tw_g);
+    pdl_wait();
+    if (!first && threadIdx.x == 0) beta_s = (float)(rr_num[0] * rcp_nr(rr_den[0]));
+    const int lr = threadIdx.x / 16, j = threadIdx.x % 16;
+    const int row = blockIdx.x * kR256Rows + lr;
+    const bool ok = row < nrows;
+    const size_t base = (size_t)row * 256 + j;
+    float2 u[16], pv[16];
+    if (ok) {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) u[n1] = r[base + 16 * n1];
+        if (!first) {
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) pv[n1] = p[base + 16 * n1];
+        }
+    } else {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) u[n1] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();  // tw2, beta
+    if (!first) {
+        const float beta = beta_s;
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) {
+            u[n1].x = fmaf(beta, pv[n1].x, u[n1].x);
+            u[n1].y = fmaf(beta, pv[n1].y, u[n1].y);
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) p[base + 16 * n1] = u[n1];
+    }
+    row_dft256<false>(u, sx[lr], tw2, j);
+    pdl_trigger();
+    if (ok) {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) t[base + 16 * k2] = u[k2];
+    }
+}
+
+// Column pass with the sampling mask for 256-point columns: 8 adjacent columns of one frame per
+// 128-thread CTA, thread (c, j) holding rows j + 16 n1 of column c. Forward DFT, mask and the
+// 1/(PQ) scale, inverse DFT, all in registers; two exchanges through shared memory, laid out as
+// c + 8 (17 a + b) so that both the writes and the reads are conflict-free.
+__global__ void __launch_bounds__(128)
+col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, float scale,
+                    const float2* __restrict__ tw_g) {
+    __shared__ float2 tw2[256];
+    __shared__ float2 buf[8 * 17 * 16];
+    fill_tw256(tw2, tw_g);
+    pdl_wait();
+    const int c = threadIdx.x % 8, j = threadIdx.x / 8;
+    const int col = blockIdx.x * 8 + c;
+    const size_t fbase = (size_t)blockIdx.y * 256 * Q;
+    float2 u[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) u[n1] = t[fbase + (size_t)(16 * n1 + j) * Q + col];
+    uint8_t mk[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) mk[k2] = mask[fbase + (size_t)(j + 16 * k2) * Q + col];
+    __syncthreads();  // tw2
+    dft16<false>(u);
+    twiddle256<false>(u, tw2, j);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) buf[c + 8 * (17 * k1 + j)] = u[k1];
+    __syncthreads();
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) u[n2] = buf[c + 8 * (17 * j + n2)];
+    dft16<false>(u);  // u[k2] = X[j + 16 k2]
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) u[k2] = mk[k2] ? cscale(u[k2], scale) : make_float2(0.f, 0.f);
+    dft16<true>(u);  // u[n1] = sum_k2 X[j + 16 k2] w16^(-k2 n1)
+    twiddle256<true>(u, tw2, j);
+    __syncthreads();  // first exchange fully read
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) buf[c + 8 * (17 * n1 + j)] = u[n1];
+    __syncthreads();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) u[k1] = buf[c + 8 * (17 * j + k1)];
+    dft16<true>(u);  // u[n2] = x[j + 16 n2]
+    pdl_trigger();
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) t[fbase + (size_t)(j + 16 * n2) * Q + col] = u[n2];
+}
+
 template <int N>
 size_t row_smem() { return (size_t)(2 * rows_per_cta<N>() * N + N) * sizeof(float2); }
 template <int N>
@@ -222,6 +320,11 @@ cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const floa
                                    float2* t, const double* rr_num, const double* rr_den,
                                    int first, cudaStream_t st) {
     const int nrows = d.T * d.P;
+    if (d.Q == 256) {
+        const int grid = (nrows + kR256Rows - 1) / kR256Rows;
+        return launch_pdl(row_fwd_pupdate_256_kernel, dim3(grid), dim3(64), 0, st, r, p, t, nrows,
+                          rr_num, rr_den, first, tw.twQ);
+    }
     switch (d.Q) {
 #define CASE(N)                                                                              \
     case N: {                                                                                \
@@ -241,6 +344,9 @@ cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const floa
 cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
                             cudaStream_t st) {
     const float sc = 1.0f / ((float)d.P * (float)d.Q);
+    if (d.P == 256)
+        return launch_pdl(col_mask_256_kernel, dim3(d.Q / kColTile, d.T), dim3(128), 0, st, t, mask,
+                          d.Q, sc, tw.twP);
     return col_pass<COL_MASK_OP>(d.P, d.Q, d.T, t, t, mask, sc, tw.twP, st);
 }
 

@@ -183,7 +183,16 @@ def _oracle_S(x, N1, N2, M, eps_frac=0.01, p=0.0):
     return slr.weight_S(slr.diag_sums(H, N1, N2, M), x.shape[1], x.shape[2])
 
 
-OP_CASES = [("tiny", "tiny_32x32x8", {}), ("perf", "perf_256x256x16", {})]
+def _times(T):
+    return tuple(1.0 + 59.0 * n / 15.0 for n in range(T))
+
+
+# the 256-point register transforms (rows when Q = 256, columns when P = 256) next to the
+# generic Stockham passes, with an odd frame count (the fused row pass pads to whole warps)
+OP_CASES = [("tiny", "tiny_32x32x8", {}), ("perf", "perf_256x256x16", {}),
+            ("perf-T5", "perf_256x256x16", {"T": 5, "times_ms": _times(5)}),
+            ("rows256-cols64", "perf_256x256x16", {"P": 64, "T": 6, "times_ms": _times(6)}),
+            ("rows128-cols256", "perf_256x256x16", {"Q": 128, "T": 7, "times_ms": _times(7)})]
 
 
 @pytest.mark.parametrize("case", OP_CASES, ids=[c[0] for c in OP_CASES])
