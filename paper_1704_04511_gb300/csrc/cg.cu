@@ -19,7 +19,8 @@ constexpr int kThreads = 256;
 constexpr int kMaxM = 6;
 constexpr int kMaxParts = 4096;  // partial-sum slots (largest grid of a reducing kernel)
 constexpr int kUpdVec = 2;       // float4 per thread per iteration in the update pass
-constexpr int kUpdPerSM = 4;     // resident update CTAs per SM (register budget 64 / thread)
+constexpr int kUpdThreads = 512;
+constexpr int kUpdPerSM = 2;     // update CTAs per SM (few partials for the next pass to add)
 
 RECON_DEV int pair_index(int a, int b, int M) { return a * (2 * M - a + 1) / 2 + (b - a); }
 
@@ -42,8 +43,8 @@ RECON_DEV void load_S(const float2* __restrict__ S, size_t npix, size_t px, floa
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads)
 row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
-                 float lam, int T, int P, double* __restrict__ parts, unsigned int* counter,
-                 double* __restrict__ pq_out, const float2* __restrict__ tw_g) {
+                 float lam, int T, int P, double* __restrict__ pq_parts,
+                 const float2* __restrict__ tw_g) {
     extern __shared__ float2 sm[];
     __shared__ double red[kThreads / 32];
     float2* a = sm;
@@ -93,7 +94,7 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
         const int n = e / N, c = e % N;
         t[(size_t)n * npix + (size_t)r1 * N + c] = res[e];
     }
-    last_block_sum(tot, parts, counter, pq_out);
+    if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
 // Pass C for 256-point rows: one CTA per image row r1 with 16 threads per frame (T * 16 threads);
@@ -103,8 +104,8 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
 template <int M>
 __global__ void __launch_bounds__(1024)
 row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
-                     float lam, int T, int P, double* __restrict__ parts, unsigned int* counter,
-                     double* __restrict__ pq_out, const float2* __restrict__ tw_g) {
+                     float lam, int T, int P, double* __restrict__ pq_parts,
+                     const float2* __restrict__ tw_g) {
     constexpr int N = 256;
     extern __shared__ float2 sm[];
     __shared__ float2 tw2[256];
@@ -166,19 +167,21 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
         const int nn = e / N, c = e % N;
         t[(size_t)nn * npix + (size_t)r1 * N + c] = res[e];
     }
-    last_block_sum(tot, parts, counter, pq_out);
+    if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
-// Pass D: alpha = |r|^2 / Re <p, q>; x += alpha p; r -= alpha q; |r_new|^2 (last block).
-__global__ void __launch_bounds__(kThreads, kUpdPerSM)
+// Pass D: alpha = |r|^2 / Re <p, q> (Re <p, q> summed here from pass C's partials); x += alpha p;
+// r -= alpha q; per-CTA partials of |r_new|^2 for the next pass A.
+__global__ void __launch_bounds__(kUpdThreads, kUpdPerSM)
 cg_update_kernel(float4* __restrict__ x, float4* __restrict__ r, const float4* __restrict__ p,
                  const float4* __restrict__ q, size_t n4, const double* __restrict__ rr_in,
-                 const double* __restrict__ pq_in, double* __restrict__ parts,
-                 unsigned int* counter, double* __restrict__ rr_out) {
-    __shared__ double red[kThreads / 32];
+                 const double* __restrict__ pq_parts, int n_pq, double* __restrict__ rr_parts) {
+    __shared__ double red[kUpdThreads / 32];
+    __shared__ double s_pq;
     __shared__ float alpha_s;
     pdl_wait();
-    if (threadIdx.x == 0) alpha_s = (float)(rr_in[0] * rcp_nr(pq_in[0]));
+    const double pq = sum_partials(pq_parts, n_pq, &s_pq);
+    if (threadIdx.x == 0) alpha_s = (float)(rr_in[0] * rcp_nr(pq));
     __syncthreads();
     const float alpha = alpha_s;
     float acc = 0.f, comp = 0.f;
@@ -213,7 +216,12 @@ cg_update_kernel(float4* __restrict__ x, float4* __restrict__ r, const float4* _
     }
     pdl_trigger();
     const double tot = block_sum_f_t0(acc, red);
-    last_block_sum(tot, parts, counter, rr_out);
+    if (threadIdx.x == 0) rr_parts[blockIdx.x] = tot;
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ parts, int n, double* __restrict__ out) {
+    const double v = warp0_sum_array(parts, n);
+    if (threadIdx.x == 0) out[0] = v;
 }
 
 // Residual carry between IRLS iterations: r = (first ? 0 : r) + lam W_{dS} x with
@@ -293,8 +301,8 @@ apply_w_kernel(const float2* __restrict__ x, const float2* __restrict__ S, float
 
 template <int N, int M>
 cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
-                                const float2* S, float lam, const RedSlot& rs, double* pq_out,
-                                cudaStream_t st) {
+                                const float2* S, float lam, Partials* pq, cudaStream_t st) {
+    pq->n = d.P;
     if constexpr (N == 256) {
         const int tpad = (d.T + 1) / 2 * 2;
         const size_t smem256 = ((size_t)d.T * N + (size_t)tpad * 16 * 17) * sizeof(float2);
@@ -306,7 +314,7 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
                 if (e != cudaSuccess) return e;
             }
             return launch_pdl(k, dim3(d.P), dim3(tpad * 16), smem256, st, t, p, S, lam, d.T, d.P,
-                              rs.parts, rs.counter, pq_out, tw.twQ);
+                              pq->parts, tw.twQ);
         }
     }
     auto k = row_inv_w_kernel<N, M>;
@@ -315,21 +323,20 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    return launch_pdl(k, dim3(d.P), dim3(kThreads), smem, st, t, p, S, lam, d.T, d.P, rs.parts,
-                      rs.counter, pq_out, tw.twQ);
+    return launch_pdl(k, dim3(d.P), dim3(kThreads), smem, st, t, p, S, lam, d.T, d.P, pq->parts,
+                      tw.twQ);
 }
 
 template <int N>
 cudaError_t launch_row_inv_w_N(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
-                               const float2* S, float lam, const RedSlot& rs, double* pq_out,
-                               cudaStream_t st) {
+                               const float2* S, float lam, Partials* pq, cudaStream_t st) {
     switch (d.M) {
-        case 1: return launch_row_inv_w_NM<N, 1>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 2: return launch_row_inv_w_NM<N, 2>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 3: return launch_row_inv_w_NM<N, 3>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 4: return launch_row_inv_w_NM<N, 4>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 5: return launch_row_inv_w_NM<N, 5>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 6: return launch_row_inv_w_NM<N, 6>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 1: return launch_row_inv_w_NM<N, 1>(d, tw, t, p, S, lam, pq, st);
+        case 2: return launch_row_inv_w_NM<N, 2>(d, tw, t, p, S, lam, pq, st);
+        case 3: return launch_row_inv_w_NM<N, 3>(d, tw, t, p, S, lam, pq, st);
+        case 4: return launch_row_inv_w_NM<N, 4>(d, tw, t, p, S, lam, pq, st);
+        case 5: return launch_row_inv_w_NM<N, 5>(d, tw, t, p, S, lam, pq, st);
+        case 6: return launch_row_inv_w_NM<N, 6>(d, tw, t, p, S, lam, pq, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -341,7 +348,7 @@ int pix_grid(size_t npix) {
 
 // One resident wave: kUpdPerSM CTAs per SM (fewer for small problems), grid-stride inside.
 int upd_grid(size_t n4) {
-    const size_t per = (size_t)kThreads * kUpdVec;
+    const size_t per = (size_t)kUpdThreads * kUpdVec;
     const size_t need = (n4 + per - 1) / per;
     size_t g = (size_t)num_sms() * kUpdPerSM;
     if (need < g) g = need;
@@ -367,29 +374,35 @@ int w_max_frames_times_q() { return (200 * 1024) / (3 * (int)sizeof(float2)); }
 int max_parts() { return kMaxParts; }
 
 cudaError_t launch_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
-                             const float2* S, float lam, const RedSlot& rs, double* pq_out,
-                             cudaStream_t st) {
+                             const float2* S, float lam, Partials* pq, cudaStream_t st) {
     if (d.P > kMaxParts) return cudaErrorInvalidValue;
     switch (d.Q) {
-        case 16: return launch_row_inv_w_N<16>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 32: return launch_row_inv_w_N<32>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 64: return launch_row_inv_w_N<64>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 128: return launch_row_inv_w_N<128>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 192: return launch_row_inv_w_N<192>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 256: return launch_row_inv_w_N<256>(d, tw, t, p, S, lam, rs, pq_out, st);
-        case 512: return launch_row_inv_w_N<512>(d, tw, t, p, S, lam, rs, pq_out, st);
+        case 16: return launch_row_inv_w_N<16>(d, tw, t, p, S, lam, pq, st);
+        case 32: return launch_row_inv_w_N<32>(d, tw, t, p, S, lam, pq, st);
+        case 64: return launch_row_inv_w_N<64>(d, tw, t, p, S, lam, pq, st);
+        case 128: return launch_row_inv_w_N<128>(d, tw, t, p, S, lam, pq, st);
+        case 192: return launch_row_inv_w_N<192>(d, tw, t, p, S, lam, pq, st);
+        case 256: return launch_row_inv_w_N<256>(d, tw, t, p, S, lam, pq, st);
+        case 512: return launch_row_inv_w_N<512>(d, tw, t, p, S, lam, pq, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* p,
-                             const float2* q, const double* rr_in, const double* pq_in,
-                             const RedSlot& rs, double* rr_out, cudaStream_t st) {
+                             const float2* q, const double* rr_in, const Partials& pq,
+                             Partials* rr, cudaStream_t st) {
     const size_t n4 = d.elems() / 2;  // two complex values per float4
-    return launch_pdl(cg_update_kernel, dim3(upd_grid(n4)), dim3(kThreads), 0, st,
+    const int grid = upd_grid(n4);
+    rr->n = grid;
+    return launch_pdl(cg_update_kernel, dim3(grid), dim3(kUpdThreads), 0, st,
                       reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(r),
                       reinterpret_cast<const float4*>(p), reinterpret_cast<const float4*>(q), n4,
-                      rr_in, pq_in, rs.parts, rs.counter, rr_out);
+                      rr_in, (const double*)pq.parts, pq.n, rr->parts);
+}
+
+cudaError_t launch_sum_partials(const Partials& in, double* out, cudaStream_t st) {
+    sum_partials_kernel<<<1, 32, 0, st>>>(in.parts, in.n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const float2* S_old,

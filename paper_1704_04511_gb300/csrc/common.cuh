@@ -181,6 +181,19 @@ RECON_DEV double warp0_sum_array(const double* a, int n) {
     return warp_sum(v);
 }
 
+// Sum of a producer kernel's per-CTA partials (fixed order, warp 0), returned to every thread
+// of the block: the consumer finishes the reduction instead of the producer's last block, which
+// takes the atomic ticket and the serial tail off the critical path. Must be reached by all
+// threads of the block.
+RECON_DEV double sum_partials(const double* parts, int n, double* s_slot) {
+    if (threadIdx.x < 32) {
+        const double v = warp0_sum_array(parts, n);
+        if (threadIdx.x == 0) *s_slot = v;
+    }
+    __syncthreads();
+    return *s_slot;
+}
+
 // ------------------------------------------------------------------------------------------
 // Small DFTs in registers: U[f] = sum_t u[t] e^{s 2 pi i t f / R}, s = -1 forward, +1 inverse.
 // ------------------------------------------------------------------------------------------

@@ -42,17 +42,19 @@ row_fft_kernel(const float2* in, float2* out, int nrows, float scale,
     for (int e = threadIdx.x; e < nr * N; e += blockDim.x) out[base + e] = cscale(res[e], scale);
 }
 
-// Pass A of a CG step: p = r (first) or r + beta p with beta = |r_c|^2 / |r_{c-1}|^2 from the
-// partial sums; p is written back and its row FFT goes to t.
+// Pass A of a CG step: p = r (first) or r + beta p with beta = |r_c|^2 / |r_{c-1}|^2, |r_c|^2
+// summed here from the update pass's per-CTA partials (CTA 0 also stores it); p is written back
+// and its row FFT goes to t.
 template <int N>
 __global__ void __launch_bounds__(kThreads)
 row_fwd_pupdate_kernel(const float2* __restrict__ r, float2* __restrict__ p,
-                       float2* __restrict__ t, int nrows, const double* __restrict__ rr_num,
-                       const double* __restrict__ rr_den, int first,
-                       const float2* __restrict__ tw_g) {
+                       float2* __restrict__ t, int nrows, const double* __restrict__ rr_parts,
+                       int n_rr, const double* __restrict__ rr_prev, double* __restrict__ rr_out,
+                       int first, const float2* __restrict__ tw_g) {
     constexpr int ROWS = rows_per_cta<N>();
     extern __shared__ float2 sm[];
     __shared__ float beta_s;
+    __shared__ double s_rr;
     float2* a = sm;
     float2* b = a + ROWS * N;
     float2* tw = b + ROWS * N;
@@ -60,7 +62,11 @@ row_fwd_pupdate_kernel(const float2* __restrict__ r, float2* __restrict__ p,
     pdl_wait();
     float beta = 0.f;
     if (!first) {
-        if (threadIdx.x == 0) beta_s = (float)(rr_num[0] * rcp_nr(rr_den[0]));
+        const double rr_new = sum_partials(rr_parts, n_rr, &s_rr);
+        if (threadIdx.x == 0) {
+            beta_s = (float)(rr_new * rcp_nr(rr_prev[0]));
+            if (blockIdx.x == 0) rr_out[0] = rr_new;
+        }
         __syncthreads();
         beta = beta_s;
     }
@@ -142,15 +148,15 @@ constexpr int kR256Rows = 4;  // rows per 64-thread CTA, one half-warp per row
 // Pass A of a CG step for 256-point rows (same contract as row_fwd_pupdate_kernel).
 __global__ void __launch_bounds__(64)
 row_fwd_pupdate_256_kernel(const float2* __restrict__ r, float2* __restrict__ p,
-                           float2* __restrict__ t, int nrows, const double* __restrict__ rr_num,
-                           const double* __restrict__ rr_den, int first,
+                           float2* __restrict__ t, int nrows, const double* __restrict__ rr_parts,
+                           int n_rr, const double* __restrict__ rr_prev,
+                           double* __restrict__ rr_out, int first,
                            const float2* __restrict__ tw_g) {
     __shared__ float2 tw2[256];
     __shared__ float2 sx[kR256Rows][16 * 17];
     __shared__ float beta_s;
     fill_tw256(tw2, tw_g);
     pdl_wait();
-    if (!first && threadIdx.x == 0) beta_s = (float)(rr_num[0] * rcp_nr(rr_den[0]));
     const int lr = threadIdx.x / 16, j = threadIdx.x % 16;
     const int row = blockIdx.x * kR256Rows + lr;
     const bool ok = row < nrows;
@@ -166,6 +172,13 @@ row_fwd_pupdate_256_kernel(const float2* __restrict__ r, float2* __restrict__ p,
     } else {
 #pragma unroll
         for (int n1 = 0; n1 < 16; ++n1) u[n1] = make_float2(0.f, 0.f);
+    }
+    if (!first && threadIdx.x < 32) {  // |r|^2 from the update pass's partials, loads in flight
+        const double rr_new = warp0_sum_array(rr_parts, n_rr);
+        if (threadIdx.x == 0) {
+            beta_s = (float)(rr_new * rcp_nr(rr_prev[0]));
+            if (blockIdx.x == 0) rr_out[0] = rr_new;
+        }
     }
     __syncthreads();  // tw2, beta
     if (!first) {
@@ -317,13 +330,13 @@ cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int
 }
 
 cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
-                                   float2* t, const double* rr_num, const double* rr_den,
-                                   int first, cudaStream_t st) {
+                                   float2* t, const Partials& rr, const double* rr_prev,
+                                   double* rr_out, int first, cudaStream_t st) {
     const int nrows = d.T * d.P;
     if (d.Q == 256) {
         const int grid = (nrows + kR256Rows - 1) / kR256Rows;
         return launch_pdl(row_fwd_pupdate_256_kernel, dim3(grid), dim3(64), 0, st, r, p, t, nrows,
-                          rr_num, rr_den, first, tw.twQ);
+                          (const double*)rr.parts, rr.n, rr_prev, rr_out, first, tw.twQ);
     }
     switch (d.Q) {
 #define CASE(N)                                                                              \
@@ -333,7 +346,7 @@ cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const floa
         if (e != cudaSuccess) return e;                                                      \
         const int grid = (nrows + rows_per_cta<N>() - 1) / rows_per_cta<N>();                \
         return launch_pdl(k, dim3(grid), dim3(kThreads), row_smem<N>(), st, r, p, t, nrows,  \
-                          rr_num, rr_den, first, tw.twQ);                                    \
+                          (const double*)rr.parts, rr.n, rr_prev, rr_out, first, tw.twQ);    \
     }
         RECON_FFT_SIZES(CASE)
 #undef CASE

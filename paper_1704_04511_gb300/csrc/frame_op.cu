@@ -6,8 +6,8 @@
 //                      distributed shared memory (DSMEM) for the column transforms and back.
 //                      One pass over r, p and t instead of a row pass plus a strided column pass.
 //   w_combine_kernel:  q = t + lam W p per pixel over all frames (W: the banded frame operator of
-//                      the per-pixel S(r), see cg.cu), written over t; Re <p, q> to a device
-//                      scalar (last-block reduction). All frames of a pixel block are staged in
+//                      the per-pixel S(r), see cg.cu), written over t; per-CTA partials of
+//                      Re <p, q> for the update pass. All frames of a pixel block are staged in
 //                      shared memory first so that every load is in flight at once.
 //
 // Used for P = Q in {32, 64, 128, 192, 256} (two (N/8) x (N+1) complex buffers per CTA fit in
@@ -37,9 +37,9 @@ constexpr int frame_smem_floats2() { return 2 * (N / kCluster) * (N + 1) + 2 * N
 template <int N>
 __global__ void __launch_bounds__(kThreads)
 frame_aha_kernel(const float2* __restrict__ r, float2* __restrict__ p, float2* __restrict__ t,
-                 const uint8_t* __restrict__ mask, const double* __restrict__ rr_num,
-                 const double* __restrict__ rr_den, int first, float scale,
-                 const float2* __restrict__ tw_g) {
+                 const uint8_t* __restrict__ mask, const double* __restrict__ rr_parts, int n_rr,
+                 const double* __restrict__ rr_prev, double* __restrict__ rr_out, int first,
+                 float scale, const float2* __restrict__ tw_g) {
     constexpr int R = N / kCluster;   // rows (and columns) this CTA owns
     constexpr int S = N + 1;          // padded stride of a row / a column in shared memory
     extern __shared__ float2 sm[];
@@ -47,6 +47,7 @@ frame_aha_kernel(const float2* __restrict__ r, float2* __restrict__ p, float2* _
     float2* buf1 = sm + R * S;
     float2* tw = sm + 2 * R * S;
     __shared__ float beta_s;
+    __shared__ double s_rr;
     cg::cluster_group cluster = cg::this_cluster();
     const int j = (int)cluster.block_rank();
     const size_t fbase = (size_t)blockIdx.y * N * N;
@@ -54,7 +55,11 @@ frame_aha_kernel(const float2* __restrict__ r, float2* __restrict__ p, float2* _
     pdl_wait();
     float beta = 0.f;
     if (!first) {
-        if (threadIdx.x == 0) beta_s = (float)(rr_num[0] * rcp_nr(rr_den[0]));
+        const double rr_new = sum_partials(rr_parts, n_rr, &s_rr);
+        if (threadIdx.x == 0) {
+            beta_s = (float)(rr_new * rcp_nr(rr_prev[0]));
+            if (blockIdx.x == 0 && blockIdx.y == 0) rr_out[0] = rr_new;
+        }
         __syncthreads();
         beta = beta_s;
     }
@@ -113,8 +118,7 @@ frame_aha_kernel(const float2* __restrict__ r, float2* __restrict__ p, float2* _
 template <int M>
 __global__ void __launch_bounds__(kPixBlock)
 w_combine_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S, float lam,
-                 int T, size_t npix, double* __restrict__ parts, unsigned int* counter,
-                 double* __restrict__ pq_out) {
+                 int T, size_t npix, double* __restrict__ pq_parts) {
     extern __shared__ float2 sm[];
     float2* sp = sm;                       // [T][kPixBlock]
     float2* sa = sm + (size_t)T * kPixBlock;  // [T][kPixBlock]
@@ -162,13 +166,13 @@ w_combine_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     }
     pdl_trigger();
     const double tot = block_sum_f_t0(acc, red);
-    last_block_sum(tot, parts, counter, pq_out);
+    if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
 template <int N>
 cudaError_t launch_frame_N(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
-                           float2* t, const uint8_t* mask, const double* rr_num,
-                           const double* rr_den, int first, cudaStream_t st) {
+                           float2* t, const uint8_t* mask, const Partials& rr,
+                           const double* rr_prev, double* rr_out, int first, cudaStream_t st) {
     auto kern = frame_aha_kernel<N>;
     const size_t smem = (size_t)frame_smem_floats2<N>() * sizeof(float2);
     if (smem > 48 * 1024) {
@@ -191,7 +195,8 @@ cudaError_t launch_frame_N(const Dims& d, const Twiddles& tw, const float2* r, f
     cfg.numAttrs = 2;
     const float scale = 1.0f / ((float)N * (float)N);
     const float2* twp = tw.twQ;
-    return cudaLaunchKernelEx(&cfg, kern, r, p, t, mask, rr_num, rr_den, first, scale, twp);
+    return cudaLaunchKernelEx(&cfg, kern, r, p, t, mask, (const double*)rr.parts, rr.n, rr_prev,
+                              rr_out, first, scale, twp);
 }
 
 }  // namespace
@@ -205,23 +210,24 @@ bool frame_op_supported(const Dims& d) {
 }
 
 cudaError_t launch_frame_aha(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
-                             float2* t, const uint8_t* mask, const double* rr_num,
-                             const double* rr_den, int first, cudaStream_t st) {
+                             float2* t, const uint8_t* mask, const Partials& rr,
+                             const double* rr_prev, double* rr_out, int first, cudaStream_t st) {
     switch (d.P) {
-        case 32: return launch_frame_N<32>(d, tw, r, p, t, mask, rr_num, rr_den, first, st);
-        case 64: return launch_frame_N<64>(d, tw, r, p, t, mask, rr_num, rr_den, first, st);
-        case 128: return launch_frame_N<128>(d, tw, r, p, t, mask, rr_num, rr_den, first, st);
-        case 192: return launch_frame_N<192>(d, tw, r, p, t, mask, rr_num, rr_den, first, st);
-        case 256: return launch_frame_N<256>(d, tw, r, p, t, mask, rr_num, rr_den, first, st);
+        case 32: return launch_frame_N<32>(d, tw, r, p, t, mask, rr, rr_prev, rr_out, first, st);
+        case 64: return launch_frame_N<64>(d, tw, r, p, t, mask, rr, rr_prev, rr_out, first, st);
+        case 128: return launch_frame_N<128>(d, tw, r, p, t, mask, rr, rr_prev, rr_out, first, st);
+        case 192: return launch_frame_N<192>(d, tw, r, p, t, mask, rr, rr_prev, rr_out, first, st);
+        case 256: return launch_frame_N<256>(d, tw, r, p, t, mask, rr, rr_prev, rr_out, first, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_w_combine(const Dims& d, float2* t, const float2* p, const float2* S, float lam,
-                             const RedSlot& rs, double* pq_out, cudaStream_t st) {
+                             Partials* pq, cudaStream_t st) {
     const size_t npix = d.pixels();
     const int grid = (int)((npix + kPixBlock - 1) / kPixBlock);
     if (grid > max_parts()) return cudaErrorInvalidValue;
+    pq->n = grid;
     const size_t smem = (size_t)2 * d.T * kPixBlock * sizeof(float2);
 #define CASE(MM)                                                                                  \
     case MM: {                                                                                    \
@@ -232,7 +238,7 @@ cudaError_t launch_w_combine(const Dims& d, float2* t, const float2* p, const fl
             if (e != cudaSuccess) return e;                                                       \
         }                                                                                         \
         return launch_pdl(kern, dim3(grid), dim3(kPixBlock), smem, st, t, p, S, lam, d.T, npix,   \
-                          rs.parts, rs.counter, pq_out);                                          \
+                          pq->parts);                                                             \
     }
     switch (d.M) {
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)

@@ -38,6 +38,13 @@ struct RedSlot {
     unsigned int* counter;  // one word
 };
 
+// Per-CTA partial sums of one grid-wide dot product, left by the producing kernel for its
+// consumers to add up (sum_partials: fixed order, so every consumer gets the same value).
+struct Partials {
+    double* parts;  // max_parts() doubles
+    int n;          // partials written (the producer's grid), set by the producer's launcher
+};
+
 // Launch `kern` with programmatic stream serialization (see pdl_wait in common.cuh).
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
@@ -71,23 +78,26 @@ cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int
 // y = unitary forward (inv = 0) or inverse (inv = 1) 2-D DFT of every frame of x (in place ok)
 cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, float2* y, int inv,
                         cudaStream_t st);
-// CG step, pass A: p = r (first) or r + beta p with beta = *rr_num / *rr_den; t = row-FFT(p).
+// CG step, pass A: p = r (first) or r + beta p with beta = |r|^2 / *rr_prev, |r|^2 the sum of
+// the update pass's partials `rr` (also stored to *rr_out); t = row-FFT(p).
 cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
-                                   float2* t, const double* rr_num, const double* rr_den,
-                                   int first, cudaStream_t st);
+                                   float2* t, const Partials& rr, const double* rr_prev,
+                                   double* rr_out, int first, cudaStream_t st);
 // CG step, pass B: t = column-IFFT(mask * column-FFT(t)) / (PQ), in place.
 cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
                             cudaStream_t st);
 
 // ---- cg.cu ----
-// CG step, pass C: q = row-IFFT(t) + lam W p written over t; *pq_out = Re <p, q>.
+// CG step, pass C: q = row-IFFT(t) + lam W p written over t; partials of Re <p, q> to *pq.
 cudaError_t launch_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
-                             const float2* S, float lam, const RedSlot& rs, double* pq_out,
-                             cudaStream_t st);
-// CG step, pass D: alpha = *rr_in / *pq_in; x += alpha p; r -= alpha q; *rr_out = |r|^2.
+                             const float2* S, float lam, Partials* pq, cudaStream_t st);
+// CG step, pass D: alpha = *rr_in / Re <p, q> (sum of `pq`); x += alpha p; r -= alpha q;
+// partials of |r|^2 to *rr.
 cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* p,
-                             const float2* q, const double* rr_in, const double* pq_in,
-                             const RedSlot& rs, double* rr_out, cudaStream_t st);
+                             const float2* q, const double* rr_in, const Partials& pq,
+                             Partials* rr, cudaStream_t st);
+// *out = the sum of the partials `in` (one warp).
+cudaError_t launch_sum_partials(const Partials& in, double* out, cudaStream_t st);
 // Residual carry: r = (first ? 0 : r) + lam W_{S_old - S_new} x (S_old ignored when first);
 // *rr_out = |r|^2.
 cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const float2* S_old,
@@ -137,10 +147,10 @@ cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, 
 bool frame_op_supported(const Dims& d);
 // p = r (first) or r + beta p; t = F^H (mask * F p) frame by frame (one 8-CTA cluster per frame)
 cudaError_t launch_frame_aha(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
-                             float2* t, const uint8_t* mask, const double* rr_num,
-                             const double* rr_den, int first, cudaStream_t st);
-// q = t + lam W_S p written over t; *pq_out = Re <p, q>
+                             float2* t, const uint8_t* mask, const Partials& rr,
+                             const double* rr_prev, double* rr_out, int first, cudaStream_t st);
+// q = t + lam W_S p written over t; partials of Re <p, q> to *pq
 cudaError_t launch_w_combine(const Dims& d, float2* t, const float2* p, const float2* S, float lam,
-                             const RedSlot& rs, double* pq_out, cudaStream_t st);
+                             Partials* pq, cudaStream_t st);
 
 }  // namespace recon

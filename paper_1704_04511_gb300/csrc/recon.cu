@@ -260,7 +260,7 @@ int check_dims(recon_ctx* c, recon_dims dd, const recon_filter* f, Dims* d) {
 struct Work {
     float2 *r, *p, *t, *S0, *S1;
     double2 *G, *lag_part, *lags, *dpart, *dsum, *Z, *eigwork;
-    double *evals, *parts, *rr, *pq, *eps, *lmax;
+    double *evals, *parts, *rparts, *rr, *pq, *eps, *lmax;
     unsigned int* counter;
     int *info, *kerr;
     void *hpd, *lanc;
@@ -311,6 +311,7 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
     GET("dsum", nlag * sizeof(double2), dsum, double2*);
     GET("Z", recon::s_scratch_bytes(d), Z, double2*);
     GET("parts", (size_t)recon::max_parts() * sizeof(double), parts, double*);
+    GET("rparts", (size_t)recon::max_parts() * sizeof(double), rparts, double*);
     GET("counter", 256, counter, unsigned int*);
     GET("rr", (size_t)(n_cg + 1) * sizeof(double), rr, double*);
     GET("pq", (size_t)(n_cg + 1) * sizeof(double), pq, double*);
@@ -416,43 +417,38 @@ int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uin
         ProfScope ps(c, RECON_PROF_RESID);
         RC_CUDA(recon::launch_resid_carry(d, w.r, x, S_old, S_new, lam, first, rs, w.rr, c->stream));
     }
+    // Dot products travel as per-CTA partials: pass C leaves those of Re <p, q> in w.parts for
+    // the update pass; the update pass leaves those of |r|^2 in w.rparts for the next pass A,
+    // which also stores the sum in rr[it] (rr[0] comes from the residual carry).
+    recon::Partials pq{w.parts, 0}, rr{w.rparts, 0};
     const bool fused = c->cluster_fft && recon::frame_op_supported(d);
-    for (int it = 0; fused && it < n_cg; ++it) {
-        {
-            ProfScope ps(c, RECON_PROF_CG_FRAME);
-            RC_CUDA(recon::launch_frame_aha(d, tw, w.r, w.p, w.t, mask, w.rr + it,
-                                            it > 0 ? w.rr + it - 1 : w.rr, it == 0, c->stream));
-        }
-        {
+    for (int it = 0; it < n_cg; ++it) {
+        const double* rr_prev = it > 0 ? w.rr + it - 1 : w.rr;
+        if (fused) {
+            {
+                ProfScope ps(c, RECON_PROF_CG_FRAME);
+                RC_CUDA(recon::launch_frame_aha(d, tw, w.r, w.p, w.t, mask, rr, rr_prev, w.rr + it,
+                                                it == 0, c->stream));
+            }
             ProfScope ps(c, RECON_PROF_CG_WCOMB);
-            RC_CUDA(recon::launch_w_combine(d, w.t, w.p, S_new, lam, rs, w.pq + it, c->stream));
-        }
-        {
-            ProfScope ps(c, RECON_PROF_CG_UPDATE);
-            RC_CUDA(recon::launch_cg_update(d, x, w.r, w.p, w.t, w.rr + it, w.pq + it, rs,
-                                            w.rr + it + 1, c->stream));
-        }
-    }
-    for (int it = 0; !fused && it < n_cg; ++it) {
-        {
-            ProfScope ps(c, RECON_PROF_CG_ROWFWD);
-            RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, w.rr + it,
-                                                  it > 0 ? w.rr + it - 1 : w.rr, it == 0, c->stream));
-        }
-        {
-            ProfScope ps(c, RECON_PROF_CG_COL);
-            RC_CUDA(recon::launch_col_mask(d, tw, w.t, mask, c->stream));
-        }
-        {
+            RC_CUDA(recon::launch_w_combine(d, w.t, w.p, S_new, lam, &pq, c->stream));
+        } else {
+            {
+                ProfScope ps(c, RECON_PROF_CG_ROWFWD);
+                RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, rr, rr_prev, w.rr + it,
+                                                      it == 0, c->stream));
+            }
+            {
+                ProfScope ps(c, RECON_PROF_CG_COL);
+                RC_CUDA(recon::launch_col_mask(d, tw, w.t, mask, c->stream));
+            }
             ProfScope ps(c, RECON_PROF_CG_ROWINVW);
-            RC_CUDA(recon::launch_row_inv_w(d, tw, w.t, w.p, S_new, lam, rs, w.pq + it, c->stream));
+            RC_CUDA(recon::launch_row_inv_w(d, tw, w.t, w.p, S_new, lam, &pq, c->stream));
         }
-        {
-            ProfScope ps(c, RECON_PROF_CG_UPDATE);
-            RC_CUDA(recon::launch_cg_update(d, x, w.r, w.p, w.t, w.rr + it, w.pq + it, rs,
-                                            w.rr + it + 1, c->stream));
-        }
+        ProfScope ps(c, RECON_PROF_CG_UPDATE);
+        RC_CUDA(recon::launch_cg_update(d, x, w.r, w.p, w.t, w.rr + it, pq, &rr, c->stream));
     }
+    if (n_cg > 0) RC_CUDA(recon::launch_sum_partials(rr, w.rr + n_cg, c->stream));
     return RECON_OK;
 }
 
@@ -1043,29 +1039,25 @@ int recon_apply_normal(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_
     Twiddles tw;
     rc = get_twiddles(c, d, &tw);
     if (rc) return rc;
-    void *pp, *parts, *counter, *pq;
+    void *pp, *parts;
     rc = ensure(c, "p", d.elems() * sizeof(float2), &pp);
     if (rc) return rc;
     rc = ensure(c, "parts", (size_t)recon::max_parts() * sizeof(double), &parts);
     if (rc) return rc;
-    rc = ensure(c, "counter", 256, &counter);
-    if (rc) return rc;
-    rc = ensure(c, "pq", 2 * sizeof(double), &pq);
-    if (rc) return rc;
-    RC_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c->stream));
-    const recon::RedSlot rs{(double*)parts, (unsigned int*)counter};
+    recon::Partials pq{(double*)parts, 0};
+    const recon::Partials none{nullptr, 0};
     // the CG operator passes with first = 1 (p = x); y receives (A^H A + lambda W) x
     if (c->cluster_fft && recon::frame_op_supported(d)) {
         RC_CUDA(recon::launch_frame_aha(d, tw, (const float2*)x, (float2*)pp, (float2*)y, masks,
-                                        nullptr, nullptr, 1, c->stream));
+                                        none, nullptr, nullptr, 1, c->stream));
         RC_CUDA(recon::launch_w_combine(d, (float2*)y, (const float2*)pp, (const float2*)S,
-                                        (float)lambda, rs, (double*)pq, c->stream));
+                                        (float)lambda, &pq, c->stream));
     } else {
         RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y,
-                                              nullptr, nullptr, 1, c->stream));
+                                              none, nullptr, nullptr, 1, c->stream));
         RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
         RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
-                                        (float)lambda, rs, (double*)pq, c->stream));
+                                        (float)lambda, &pq, c->stream));
     }
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return RECON_OK;
