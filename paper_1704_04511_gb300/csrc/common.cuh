@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #define RECON_DEV __device__ __forceinline__
+#define RECON_HD __host__ __device__ inline
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization may
 // start while its predecessor is finishing; it must wait before touching the predecessor's

@@ -9,16 +9,16 @@
 // and sweeping every pivot leaves -A^{-1}. Hermitian symmetry holds after every step, so only the
 // lower tiles are kept (tile-major, 1 KB per tile). The kernel is ONE cooperative launch, one grid
 // barrier per pivot step, the lower tiles ping-ponging between two buffers so that a step reads
-// only the previous step's values:
-//   - "diagonal" CTAs own the diagonal tiles; the owner of tile (K+1, K+1) updates it first with
-//     the whole CTA and inverts it (the next pivot, D_{K+1}) while its other warps update the
-//     CTA's remaining diagonal tiles, so the serial pivot chain never waits behind bulk work;
-//   - the other CTAs each own chunks of up to four tiles of one tile row I: the chunk forms
-//     X = A_IK D_K once (split over the CTA's eight warps) and each 64-thread group applies
-//     A_IJ - X A_KJ to its tile.
+// only the previous step's values and any CTA may update any tile:
+//   - CTA 0 carries the serial chain alone: at step K it updates tile (K+1, K+1) and inverts it
+//     (the next pivot, D_{K+1}) with no other FP64 work on its SM;
+//   - the other CTAs own fixed work items (chunks of up to four tiles of one tile row, which
+//     form X = A_IK D_K once and apply A_IJ - X A_KJ per tile, and the diagonal tiles), dealt so
+//     that the FP64 work per SM is even.
 // FP64 on this part issues one warp instruction per ~19 cycles per SM whatever the active lanes,
-// so the products use full warps and the work is spread over every SM. Grid barriers are bounded
-// spin-waits: on timeout the kernel records an error flag and returns.
+// and one warp at most one per ~64 cycles, so the products use full warps spread over every SM
+// and the pivot chain keeps its SM to itself. Grid barriers are bounded spin-waits: on timeout
+// the kernel records an error flag and returns.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -31,7 +31,7 @@ constexpr int kB = 8;                        // tile edge
 constexpr int kTileT = kB * kB;              // elements of a tile = threads of a tile group
 constexpr int kGroups = kThreads / kTileT;   // tile groups per CTA
 constexpr int kChunk = 4;                    // off-diagonal tiles of one row handled per CTA pass
-constexpr int kMaxChunks = 128;              // chunks one off-diagonal CTA may own
+constexpr int kMaxItems = 128;               // work items one CTA may own
 constexpr long long kSpinLimit = 1LL << 26;  // polls (~1 us each at most) before giving up
 
 struct GridBar {
@@ -50,9 +50,9 @@ RECON_DEV int ld_acquire(const int* p) {
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-RECON_DEV unsigned int atom_add_release(unsigned int* p, unsigned int v) {
+RECON_DEV unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
     unsigned int old;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
 
@@ -69,9 +69,11 @@ RECON_DEV bool grid_barrier(GridBar* gb) {
         if (ok) {
             __threadfence();
             const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-            const unsigned int old = atom_add_release(&gb->word, inc);
+            const unsigned int old = atom_add_acq_rel(&gb->word, inc);
+            // the arrival that flips bit 31 is the last one: it need not poll
+            const bool last = (((old + inc) ^ old) & 0x80000000u) != 0u;
             long long it = 0;
-            while (((ld_acquire(&gb->word) ^ old) & 0x80000000u) == 0u) {
+            while (!last && ((ld_acquire(&gb->word) ^ old) & 0x80000000u) == 0u) {
                 if (++it > kSpinLimit) {
                     atomicExch(&gb->err, 1);
                     ok = 0;
@@ -95,32 +97,43 @@ RECON_DEV void group_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kTileT) : "memory");
 }
 
-// Inverse of a Hermitian positive-definite 8 x 8 tile held (full, column-major) in the group's
-// shared memory, by 8 scalar sweeps (which leave -T^{-1}); the negated result goes to `out`.
-// Called by the 64 threads of one tile group.
-RECON_DEV void tile_inverse(double2* T, double2* out, double* s_inv, double2* s_row, int g) {
+// 1 / a for a pivot of a positive-definite matrix: the FP64 approximate reciprocal instruction
+// as the seed, then one cubic Newton-Raphson step r (1 + e + e^2), e = 1 - a r (the error goes
+// from e to e^3). Three dependent FMAs after the seed; no range test (pivots are positive,
+// normal numbers).
+RECON_DEV double rcp_pivot(double a) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+    const double e = fma(-a, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
+// Inverse of a Hermitian positive-definite 8 x 8 tile (full, column-major) by 8 scalar sweeps,
+// which leave -T^{-1}; the negated result goes to `out`. Run by the 64 threads of group 0,
+// ping-ponging between T0 and T1 so that one barrier per pivot suffices. Each sweep is one
+// rank-1 update v = t' - c_i r_j with t' = 0 on the pivot row and column, c = column k with
+// c_k = -1 and r = row k / a_kk with r_k = -1 / a_kk, which gives the row (a_kj / a_kk), the
+// column (a_ik / a_kk) and the pivot (-1 / a_kk) without branches. Every thread forms the
+// reciprocal itself: a warp issues the same FP64 instructions for one lane or for 32.
+RECON_DEV void tile_inverse(double2* T0, double2* T1, double2* out) {
     const int e = threadIdx.x % kTileT, i = e % kB, j = e / kB;
+    double2* a = T0;
+    double2* b = T1;
+#pragma unroll 1
     for (int k = 0; k < kB; ++k) {
-        if (e == 0) *s_inv = rcp_nr(T[k + k * kB].x);  // one reciprocal per pivot
-        group_sync(g);
-        const double inv = *s_inv;
-        if (e < kB) {
-            const double2 t = T[k + e * kB];  // row k, scaled once
-            s_row[e] = make_double2(t.x * inv, t.y * inv);
-        }
-        const double2 tij = T[i + j * kB], tik = T[i + k * kB];
-        group_sync(g);
-        double2 v;
-        if (i == k && j == k) v = make_double2(-inv, 0.0);
-        else if (i == k) v = s_row[j];
-        else if (j == k) v = make_double2(tik.x * inv, tik.y * inv);
-        else v = zfms(tik, s_row[j], tij);
-        T[i + j * kB] = v;
-        group_sync(g);
+        const double inv = rcp_pivot(a[k + k * kB].x);
+        const double2 aij = a[i + j * kB], aik = a[i + k * kB], akj = a[k + j * kB];
+        const double2 t = (i == k || j == k) ? make_double2(0.0, 0.0) : aij;
+        const double2 c = (i == k) ? make_double2(-1.0, 0.0) : aik;
+        const double2 r = (j == k) ? make_double2(-inv, 0.0) : make_double2(akj.x * inv, akj.y * inv);
+        b[i + j * kB] = zfms(c, r, t);
+        group_sync(0);
+        double2* sw = a;
+        a = b;
+        b = sw;
     }
-    const double2 v = T[i + j * kB];
+    const double2 v = a[i + j * kB];
     out[i + j * kB] = make_double2(-v.x, -v.y);
-    group_sync(g);
 }
 
 // Lower tile (I, J), J <= I: offset of its 64 elements, element (i, j) at i + 8 j.
@@ -142,68 +155,156 @@ RECON_DEV void tile_ij(int t, int* I, int* J) {
 }
 
 struct SweepSmem {
-    double2 D[kTileT];              // D_K
-    double2 P[kGroups][kTileT];     // A_IK per group (diagonal CTAs) / per chunk (slot 0)
-    double2 B[kGroups][kTileT];     // A_KJ per group
-    double2 X[kGroups][kTileT];     // X = A_IK D_K per group / per chunk (slot 0)
-    double2 Xp[kGroups][kTileT];    // partial products over quarters of q
-    double s_inv[kGroups];
-    double2 s_row[kGroups][kB];
-    int chunk[kMaxChunks];          // (I << 16) | (J0 << 4) | nj of this CTA's chunks
-    int nchunk;
+    double2 D[kTileT];            // D_K
+    double2 P[kTileT];            // A_IK of the current item
+    double2 B[kGroups][kTileT];   // A_KJ of each group's tile
+    double2 X[kTileT];            // X = A_IK D_K
+    double2 Xp[kGroups][kTileT];  // partial products over quarters of q
+    double2 T1[kTileT];           // second buffer of the pivot inverse
+    int item[kMaxItems];          // (I << 16) | (J0 << 4) | nj of this CTA's work items
+    int nitem;
 };
 
-// One diagonal tile I at step K by the 64-thread group g (not the next pivot).
-RECON_DEV void diag_tile_group(SweepSmem& sm, const double2* Ain, double2* Aout, const double2* DK,
-                               int I, int K, int g) {
-    const int e = threadIdx.x % kTileT, i = e % kB, j = e / kB;
-    if (I == K) {
-        const double2 d = DK[e];
-        Aout[tile_off(K, K) + e] = make_double2(-d.x, -d.y);
+// Work items of the non-pivot CTAs: chunks of up to four tiles (I, J0 .. J0 + nj - 1) of one tile
+// row, J0 + nj <= I, and the diagonal tiles as items (I, I, 1). They are listed largest first
+// (full chunks, then chunks of 3, 2, 1 tiles, then diagonal tiles) and dealt to the CTAs
+// 1 .. grid-1 in a snake order (forward, backward, ...), which balances the FP64 work per SM.
+// Every CTA runs this enumeration and keeps its own items.
+struct ItemDeal {
+    int workers, me, idx, n, cap;
+    int* out;
+};
+
+RECON_HD void deal_item(ItemDeal& d, int code) {
+    const int rnd = d.idx / d.workers, pos = d.idx % d.workers;
+    const int w = (rnd & 1) ? d.workers - 1 - pos : pos;
+    if (w == d.me) {
+        if (d.out && d.n < d.cap) d.out[d.n] = code;
+        ++d.n;
+    }
+    ++d.idx;
+}
+
+// Items of worker `me` (0-based among the CTAs 1 .. grid-1) into out[0 .. cap); returns their
+// count. With me < 0 it returns the largest count of any worker (host capacity check).
+RECON_HD int sweep_items(int nt, int workers, int me, int* out, int cap) {
+    ItemDeal d{workers, me, 0, 0, cap, out};
+    for (int I = 1; I < nt; ++I)
+        for (int J0 = 0; J0 + kChunk <= I; J0 += kChunk) deal_item(d, (I << 16) | (J0 << 4) | kChunk);
+    for (int nj = kChunk - 1; nj >= 1; --nj)
+        for (int I = 1; I < nt; ++I)
+            if (I % kChunk == nj) deal_item(d, (I << 16) | ((I - nj) << 4) | nj);
+    for (int I = 0; I < nt; ++I) deal_item(d, (I << 16) | (I << 4) | 1);
+    return me < 0 ? (d.idx + workers - 1) / workers : d.n;
+}
+
+// One work item at step K by the whole CTA (uniform control flow). Chunk: X = A_IK D_K is formed
+// once (quarters of q on the four groups), then group g updates tile (I, J0 + g):
+//   I == K:  new = D_K A_KJ;   J == K:  new = X;   otherwise  new = A_IJ - X A_KJ.
+// Diagonal tile (I, I): -D_K when I == K, skipped when I == K + 1 (the pivot CTA has it),
+// otherwise new = A_II - X (A_IK)^H.
+RECON_DEV void sweep_item(SweepSmem& sm, int code, int K, int nt, const double2* Ain,
+                          double2* Aout, const double2* DK) {
+    const int tid = threadIdx.x, g = tid / kTileT, e = tid % kTileT;
+    const int i = e % kB, j = e / kB;
+    const int I = code >> 16, J0 = (code >> 4) & 0xfff, nj = code & 15;
+    const bool diag = (J0 == I);
+    if (diag && I == K + 1) return;
+    if (diag && I == K) {
+        if (g == 0) {
+            const double2 d = DK[e];
+            Aout[tile_off(K, K) + e] = make_double2(-d.x, -d.y);
+        }
         return;
     }
-    const double2 own = Ain[tile_off(I, I) + e];
-    sm.P[g][e] = block_elem(Ain, I, K, e);
-    sm.B[g][e] = DK[e];
-    group_sync(g);
+    const int J = J0 + g;
+    const bool mine = g < nj;
+    if (tid < kTileT) sm.D[e] = DK[e];
+    else if (tid < 2 * kTileT && I != K) sm.P[e] = block_elem(Ain, I, K, e);
+    double2 own = make_double2(0.0, 0.0);
+    if (mine) {
+        own = Ain[tile_off(I, J) + e];
+        if (I == K) sm.B[g][e] = own;
+        else if (J != K) sm.B[g][e] = block_elem(Ain, K, J, e);
+    }
+    __syncthreads();
+    if (I == K) {
+        if (mine) {
+            double2 v = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < kB; ++q) v = zfma(sm.D[i + kB * q], sm.B[g][q + kB * j], v);
+            Aout[tile_off(I, J) + e] = v;
+        }
+    } else {
+        double2 x = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 2 * g; q < 2 * g + 2; ++q) x = zfma(sm.P[i + kB * q], sm.D[q + kB * j], x);
+        sm.Xp[g][e] = x;
+        __syncthreads();
+        if (tid < kTileT) sm.X[e] = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
+        __syncthreads();
+        if (mine) {
+            double2 v;
+            if (J == K) {
+                v = sm.X[e];
+            } else {
+                v = own;
+#pragma unroll
+                for (int q = 0; q < kB; ++q) v = zfms(sm.X[i + kB * q], sm.B[g][q + kB * j], v);
+            }
+            Aout[tile_off(I, J) + e] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// The pivot CTA at step K: tile (K+1, K+1) with all eight warps, X = A_{K+1,K} D_K and
+// new = own - X (A_{K+1,K})^H (quarters of q), then its inverse D_{K+1} by group 0. The tile's
+// swept value itself is never read again (step K+1 writes -D_{K+1} there).
+RECON_DEV void sweep_pivot(SweepSmem& sm, int K, const double2* Ain, const double2* DK,
+                           double2* Dnext) {
+    const int tid = threadIdx.x, g = tid / kTileT, e = tid % kTileT;
+    const int i = e % kB, j = e / kB;
+    const int piv = K + 1;
+    if (tid < kTileT) sm.D[e] = DK[e];
+    else if (tid < 2 * kTileT) sm.P[e] = Ain[tile_off(piv, K) + e];
+    const double2 own = Ain[tile_off(piv, piv) + e];
+    __syncthreads();
     double2 x = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int q = 0; q < kB; ++q) x = zfma(sm.P[g][i + kB * q], sm.B[g][q + kB * j], x);
-    sm.X[g][e] = x;
-    group_sync(g);
-    // A_KI = (A_IK)^H:  new = own - X (A_IK)^H
-    double2 v = own;
+    for (int q = 2 * g; q < 2 * g + 2; ++q) x = zfma(sm.P[i + kB * q], sm.D[q + kB * j], x);
+    sm.Xp[g][e] = x;
+    __syncthreads();
+    if (tid < kTileT) sm.X[e] = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
+    __syncthreads();
+    double2 u = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int q = 0; q < kB; ++q) v = zfms(sm.X[g][i + kB * q], zconj(sm.P[g][j + kB * q]), v);
-    Aout[tile_off(I, I) + e] = v;
-    group_sync(g);
+    for (int q = 2 * g; q < 2 * g + 2; ++q) u = zfma(sm.X[i + kB * q], zconj(sm.P[j + kB * q]), u);
+    sm.Xp[g][e] = u;
+    __syncthreads();
+    if (tid < kTileT) {
+        const double2 sum = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
+        sm.X[e] = make_double2(own.x - sum.x, own.y - sum.y);  // the same thread read X[e] above
+        group_sync(0);
+        tile_inverse(sm.X, sm.T1, Dnext);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
-hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt, int ndc,
+hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
                  double2* __restrict__ A0, double2* __restrict__ A1, double2* __restrict__ Dbuf,
                  GridBar* gb) {
     __shared__ SweepSmem sm;
     const int tid = threadIdx.x;
     const int g = tid / kTileT, e = tid % kTileT;
     const int i = e % kB, j = e / kB;
-    const int h = g;  // quarter of the q range in the split products
     const int nlt = nt * (nt + 1) / 2;
     const double eps = eps_p[0];
-    const bool diag_cta = (int)blockIdx.x < ndc;
-    const int noc = (int)gridDim.x - ndc;
 
-    // this CTA's off-diagonal chunks: row I (1..nt-1), columns J0 .. J0 + nj - 1 (J0 < I)
     if (tid == 0) {
-        int n = 0;
-        if (!diag_cta) {
-            int ch = 0;
-            for (int I = 1; I < nt; ++I)
-                for (int J0 = 0; J0 < I; J0 += kChunk, ++ch)
-                    if (ch % noc == (int)blockIdx.x - ndc && n < kMaxChunks)
-                        sm.chunk[n++] = (I << 16) | (J0 << 4) | min(kChunk, I - J0);
-        }
-        sm.nchunk = n;
+        sm.nitem = blockIdx.x == 0 ? 0
+                                   : sweep_items(nt, gridDim.x - 1, blockIdx.x - 1, sm.item, kMaxItems);
+        if (sm.nitem > kMaxItems) sm.nitem = kMaxItems;  // the host refuses such sizes
     }
     // A0 = pad(G + eps I), lower tiles; padding is the identity
     for (int t = blockIdx.x * kGroups + g; t < nlt; t += gridDim.x * kGroups) {
@@ -218,10 +319,10 @@ hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt, in
         A0[tile_off(I, J) + e] = v;
     }
     if (!grid_barrier(gb)) return;
-    if (blockIdx.x == 0 && g == 0) {  // D_0, by the owner of tile (0, 0)
-        sm.X[0][e] = A0[e];
+    if (blockIdx.x == 0 && g == 0) {  // D_0
+        sm.X[e] = A0[e];
         group_sync(0);
-        tile_inverse(sm.X[0], Dbuf, &sm.s_inv[0], sm.s_row[0], 0);
+        tile_inverse(sm.X, sm.T1, Dbuf);
     }
     if (!grid_barrier(gb)) return;
 
@@ -230,99 +331,10 @@ hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt, in
         double2* Aout = (K & 1) ? A0 : A1;
         const double2* DK = Dbuf + (K & 1) * kTileT;
         double2* Dnext = Dbuf + ((K + 1) & 1) * kTileT;
-        if (diag_cta) {
-            const int c = blockIdx.x;
-            const int piv = K + 1;
-            const bool has_piv = piv < nt && piv % ndc == c;
-            if (has_piv) {
-                // next pivot tile (K+1, K+1) with all eight warps: X = A_{K+1,K} D_K (quarters
-                // of q), then new = own - X (A_{K+1,K})^H, then its inverse D_{K+1}
-                if (tid < kTileT) sm.D[e] = DK[e];
-                else if (tid < 2 * kTileT) sm.P[0][e] = Ain[tile_off(piv, K) + e];
-                const double2 own = Ain[tile_off(piv, piv) + e];
-                __syncthreads();
-                double2 x = make_double2(0.0, 0.0);
-#pragma unroll
-                for (int q = 2 * h; q < 2 * h + 2; ++q) x = zfma(sm.P[0][i + kB * q], sm.D[q + kB * j], x);
-                sm.Xp[h][e] = x;
-                __syncthreads();
-                if (tid < kTileT)
-                    sm.X[0][e] = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
-                __syncthreads();
-                double2 u = make_double2(0.0, 0.0);
-#pragma unroll
-                for (int q = 2 * h; q < 2 * h + 2; ++q)
-                    u = zfma(sm.X[0][i + kB * q], zconj(sm.P[0][j + kB * q]), u);
-                sm.Xp[h][e] = u;
-                __syncthreads();
-                if (tid < kTileT) {
-                    const double2 sum = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
-                    const double2 v = make_double2(own.x - sum.x, own.y - sum.y);
-                    Aout[tile_off(piv, piv) + e] = v;
-                    sm.Xp[0][e] = v;  // the same thread read slot (0, e) above
-                }
-                __syncthreads();
-                if (g == 0) {
-                    tile_inverse(sm.Xp[0], Dnext, &sm.s_inv[0], sm.s_row[0], 0);
-                } else {
-                    // the CTA's other diagonal tiles on groups 1..3 meanwhile
-                    int m = 0;
-                    for (int I = c; I < nt; I += ndc) {
-                        if (I == piv) continue;
-                        if (m++ % (kGroups - 1) == g - 1) diag_tile_group(sm, Ain, Aout, DK, I, K, g);
-                    }
-                }
-            } else {
-                int m = 0;
-                for (int I = c; I < nt; I += ndc)
-                    if (m++ % kGroups == g) diag_tile_group(sm, Ain, Aout, DK, I, K, g);
-            }
+        if (blockIdx.x == 0) {
+            if (K + 1 < nt) sweep_pivot(sm, K, Ain, DK, Dnext);
         } else {
-            for (int ci = 0; ci < sm.nchunk; ++ci) {
-                const int code = sm.chunk[ci];
-                const int I = code >> 16, J0 = (code >> 4) & 0xfff, nj = code & 15;
-                const int J = J0 + g;
-                const bool mine = g < nj;
-                if (tid < kTileT) sm.D[e] = DK[e];
-                else if (tid < 2 * kTileT && I != K) sm.P[0][e] = block_elem(Ain, I, K, e);
-                double2 own = make_double2(0.0, 0.0);
-                if (mine) {
-                    own = Ain[tile_off(I, J) + e];
-                    if (I == K) sm.B[g][e] = own;
-                    else if (J != K) sm.B[g][e] = block_elem(Ain, K, J, e);
-                }
-                __syncthreads();
-                if (I == K) {
-                    // row K: new = D_K A_KJ
-                    if (mine) {
-                        double2 v = make_double2(0.0, 0.0);
-#pragma unroll
-                        for (int q = 0; q < kB; ++q) v = zfma(sm.D[i + kB * q], sm.B[g][q + kB * j], v);
-                        Aout[tile_off(I, J) + e] = v;
-                    }
-                } else {
-                    double2 x = make_double2(0.0, 0.0);
-#pragma unroll
-                    for (int q = 2 * h; q < 2 * h + 2; ++q) x = zfma(sm.P[0][i + kB * q], sm.D[q + kB * j], x);
-                    sm.Xp[h][e] = x;
-                    __syncthreads();
-                    if (tid < kTileT)
-                        sm.X[0][e] = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
-                    __syncthreads();
-                    if (mine) {
-                        double2 v;
-                        if (J == K) {
-                            v = sm.X[0][e];  // column K: new = A_IK D_K
-                        } else {
-                            v = own;
-#pragma unroll
-                            for (int q = 0; q < kB; ++q) v = zfms(sm.X[0][i + kB * q], sm.B[g][q + kB * j], v);
-                        }
-                        Aout[tile_off(I, J) + e] = v;
-                    }
-                }
-                __syncthreads();
-            }
+            for (int it = 0; it < sm.nitem; ++it) sweep_item(sm, sm.item[it], K, nt, Ain, Aout, DK);
         }
         if (!grid_barrier(gb)) return;
     }
@@ -551,9 +563,6 @@ int coop_grid(const void* kern, int* grid) {
 
 int tiles_per_side(int s) { return (s + kB - 1) / kB; }
 
-// Diagonal CTAs of the sweep: two diagonal tiles each where the grid allows.
-int sweep_diag_ctas(int nt, int grid) { return max(1, min((nt + 1) / 2, grid / 8)); }
-
 // Cooperative launch (all CTAs co-resident, required by the grid barriers) through
 // cudaLaunchKernelEx so that it can be captured into a CUDA graph.
 template <typename... KArgs, typename... Args>
@@ -589,11 +598,8 @@ cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, voi
     const size_t nlt = (size_t)nt * (nt + 1) / 2;
     int grid = 0;
     if (coop_grid((const void*)hpd_sweep_kernel, &grid) || grid < 2) return cudaErrorInvalidConfiguration;
-    const int ndc = sweep_diag_ctas(nt, grid);
-    // every off-diagonal chunk must fit the per-CTA chunk table
-    long long nch = 0;
-    for (int I = 1; I < nt; ++I) nch += (I + kChunk - 1) / kChunk;
-    if ((nch + (grid - ndc) - 1) / (grid - ndc) > kMaxChunks) return cudaErrorInvalidValue;
+    // every work item must fit the per-CTA item table
+    if (sweep_items(nt, grid - 1, -1, nullptr, 0) > kMaxItems) return cudaErrorInvalidValue;
     unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
     GridBar* gb = reinterpret_cast<GridBar*>(p);
     p += 256;
@@ -604,7 +610,7 @@ cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, voi
     double2* Dbuf = reinterpret_cast<double2*>(p);
     cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;
-    e = launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, nt, ndc, A0, A1, Dbuf, gb);
+    e = launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, nt, A0, A1, Dbuf, gb);
     if (e != cudaSuccess) return e;
     if (err_flag_out) {
         // fold the barrier error into the caller's flag
