@@ -180,19 +180,21 @@ cg_update_kernel(float4* __restrict__ x, float4* __restrict__ r, const float4* _
     __shared__ double s_pq;
     __shared__ float alpha_s;
     pdl_wait();
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float4 xv[kUpdVec], rv[kUpdVec], pv[kUpdVec], qv[kUpdVec];
+    // the first loads go out before alpha is known (they do not depend on it)
+#pragma unroll
+    for (int u = 0; u < kUpdVec; ++u) {
+        const size_t i = i0 + (size_t)u * stride;
+        if (i < n4) { xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i]; }
+    }
     const double pq = sum_partials(pq_parts, n_pq, &s_pq);
     if (threadIdx.x == 0) alpha_s = (float)(rr_in[0] * rcp_nr(pq));
     __syncthreads();
     const float alpha = alpha_s;
     float acc = 0.f, comp = 0.f;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n4; i0 += stride * kUpdVec) {
-        float4 xv[kUpdVec], rv[kUpdVec], pv[kUpdVec], qv[kUpdVec];
-#pragma unroll
-        for (int u = 0; u < kUpdVec; ++u) {
-            const size_t i = i0 + (size_t)u * stride;
-            if (i < n4) { xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i]; }
-        }
+    for (; i0 < n4; i0 += stride * kUpdVec) {
 #pragma unroll
         for (int u = 0; u < kUpdVec; ++u) {
             const size_t i = i0 + (size_t)u * stride;
@@ -212,6 +214,12 @@ cg_update_kernel(float4* __restrict__ x, float4* __restrict__ r, const float4* _
             const float sum = acc + term;
             comp = (sum - acc) - term;
             acc = sum;
+        }
+        const size_t nx = i0 + stride * kUpdVec;
+#pragma unroll
+        for (int u = 0; u < kUpdVec; ++u) {
+            const size_t i = nx + (size_t)u * stride;
+            if (i < n4) { xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i]; }
         }
     }
     pdl_trigger();

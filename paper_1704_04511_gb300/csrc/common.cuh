@@ -128,9 +128,9 @@ RECON_DEV double block_sum_array(const double* a, int n, double* red) {
     return block_sum(v, red);
 }
 
-// Block sum of one float per thread: FP32 shuffle tree inside each warp, FP64 across the warps
-// (fixed order). Only thread 0 holds the result. Keeps the FP64 work to one add per warp (the
-// FP64 pipe is ~60x narrower than FP32 on this part).
+// Block sum of one float per thread: FP32 shuffle tree inside each warp, FP64 shuffle tree over
+// the warps' sums in warp 0 (fixed order). Only thread 0 holds the result. Keeps the FP64 work to
+// a few instructions of one warp (the FP64 pipe is ~60x narrower than FP32 on this part).
 RECON_DEV double block_sum_f_t0(float v, double* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -139,8 +139,10 @@ RECON_DEV double block_sum_f_t0(float v, double* red) {
     if (lane == 0) red[wid] = (double)v;
     __syncthreads();
     double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < nw; ++w) t += red[w];
+    if (wid == 0) {
+        t = lane < nw ? red[lane] : 0.0;
+        t = warp_sum(t);
+    }
     return t;
 }
 

@@ -33,6 +33,7 @@ constexpr int kGroups = kThreads / kTileT;   // tile groups per CTA
 constexpr int kChunk = 4;                    // off-diagonal tiles of one row handled per CTA pass
 constexpr int kMaxItems = 128;               // work items one CTA may own
 constexpr long long kSpinLimit = 1LL << 26;  // polls (~1 us each at most) before giving up
+constexpr int kLanczosMax = 96;              // Lanczos steps (tridiagonal order) at most
 
 struct GridBar {
     unsigned int word;  // bit 31 flips when the last CTA arrives; bits 0-30 count arrivals
@@ -391,7 +392,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
     __shared__ int s_m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = gridDim.x * (kThreads / 32);
-    const int gw = blockIdx.x * (kThreads / 32) + warp;
+    const int gw = warp * gridDim.x + blockIdx.x;  // rows spread over every SM (FP64 unit per SM)
     // deterministic start vector, unnormalised: u_i = 1 + 0.5 sin(i) + i 0.25 i cos(3 i) / s
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
         u[i] = make_double2(1.0 + 0.5 * sin((double)i), 0.25 * cos(3.0 * i) * i / s);
@@ -489,10 +490,22 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
     m = s_m;
     // Largest eigenvalue of the m x m tridiagonal (alpha_k, beta_k) by multisection with Sturm
     // counts (CTA 0): FP32 rounds over the whole block to 1e-4 relative (FP32 counts are exact
-    // for x farther than ~m eps32 |T| from an eigenvalue), then FP64 rounds on
-    // one warp (FP64 divisions are expensive here, so few threads evaluate them).
+    // for x farther than ~m eps32 |T| from an eigenvalue), then FP64 rounds on three warps. The
+    // FP64 count follows the characteristic polynomials p_k = (alpha_k - x) p_{k-1} -
+    // beta_{k-1}^2 p_{k-2} (the number of sign changes of p_0 .. p_m is the number of eigenvalues
+    // below x), rescaled by exact powers of two when the exponent drifts: two dependent FP64
+    // operations per step instead of a reciprocal.
     if (blockIdx.x != 0) return;
     __shared__ int best;
+    __shared__ float sa32[kLanczosMax], sb32[kLanczosMax];
+    __shared__ double sa64[kLanczosMax], sb64[kLanczosMax];
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const double a = ab[2 * k], b2 = k > 0 ? ab[2 * k - 1] * ab[2 * k - 1] : 0.0;
+        sa64[k] = a;
+        sb64[k] = b2;
+        sa32[k] = (float)a;
+        sb32[k] = (float)b2;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double lo = 1e300, hi = -1e300;
@@ -508,7 +521,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
     __syncthreads();
     for (int round = 0; round < 24; ++round) {
         const bool fp32 = (sh_hi - sh_lo) > 1e-4 * fabs(sh_hi);
-        const int nthr = fp32 ? (int)blockDim.x : 32;
+        const int nthr = fp32 ? (int)blockDim.x : 96;
         const double lo = sh_lo, hi = sh_hi;
         int cnt = m;
         if ((int)threadIdx.x < nthr) {
@@ -518,18 +531,27 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
                 const float xf = (float)x;
                 float d = 1.f;
                 for (int k = 0; k < m; ++k) {
-                    const float bb = k > 0 ? (float)(ab[2 * k - 1] * ab[2 * k - 1]) : 0.f;
-                    d = ((float)ab[2 * k] - xf) - (k > 0 ? bb * __frcp_rn(d) : 0.f);
+                    d = (sa32[k] - xf) - (k > 0 ? sb32[k] * __frcp_rn(d) : 0.f);
                     if (d == 0.f) d = -1e-30f;
                     if (d < 0.f) ++cnt;
                 }
             } else {
-                double d = 1.0;
-                for (int k = 0; k < m; ++k) {
-                    const double bb = k > 0 ? ab[2 * k - 1] * ab[2 * k - 1] : 0.0;
-                    d = (ab[2 * k] - x) - (k > 0 ? bb * rcp_nr(d) : 0.0);
-                    if (d == 0.0) d = -1e-300;
-                    if (d < 0.0) ++cnt;
+                double p0 = 1.0, p1 = sa64[0] - x;
+                if (p1 == 0.0) p1 = -1e-300;
+                cnt = p1 < 0.0;
+                for (int k = 1; k < m; ++k) {
+                    double p2 = fma(-sb64[k], p0, (sa64[k] - x) * p1);
+                    if (p2 == 0.0) p2 = p1 < 0.0 ? 1e-300 : -1e-300;  // a zero counts as a change
+                    cnt += (p2 < 0.0) != (p1 < 0.0);
+                    p0 = p1;
+                    p1 = p2;
+                    const int ex = max((int)((__double_as_longlong(p0) >> 52) & 0x7ff),
+                                       (int)((__double_as_longlong(p1) >> 52) & 0x7ff));
+                    if (ex > 1023 + 480 || ex < 1023 - 480) {  // keep the larger one near 1
+                        const double sc = __longlong_as_double((long long)(2046 - ex) << 52);
+                        p0 *= sc;
+                        p1 *= sc;
+                    }
                 }
             }
         }
@@ -589,7 +611,7 @@ size_t hpd_scratch_bytes(const Dims& d) {
 
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {
     return 256 + 2 * (size_t)d.s() * sizeof(double2) + 4 * (size_t)grid_max * sizeof(double) +
-           2 * 96 * sizeof(double) + 1024;
+           2 * kLanczosMax * sizeof(double) + 1024;
 }
 
 cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
@@ -632,7 +654,7 @@ cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, 
     int grid = 0;
     if (coop_grid((const void*)lanczos_kernel, &grid)) return cudaErrorInvalidConfiguration;
     const int s = d.s();
-    int m = s < 96 ? s : 96;
+    int m = s < kLanczosMax ? s : kLanczosMax;
     unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
     GridBar* gb = reinterpret_cast<GridBar*>(p);
     p += 256;
