@@ -32,7 +32,7 @@ constexpr int kTileT = kB * kB;              // elements of a tile = threads of 
 constexpr int kGroups = kThreads / kTileT;   // tile groups per CTA
 constexpr int kChunk = 4;                    // off-diagonal tiles of one row handled per CTA pass
 constexpr int kMaxItems = 128;               // work items one CTA may own
-constexpr long long kSpinLimit = 1LL << 26;  // polls (~1 us each at most) before giving up
+constexpr long long kSpinLimit = 1LL << 24;  // polls (~1 us each at most) before giving up
 constexpr int kLanczosMax = 96;              // Lanczos steps (tridiagonal order) at most
 
 struct GridBar {
