@@ -194,7 +194,7 @@ int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
  * whose device memory is planned when it starts and must not grow, or a program that shares the
  * GPU with other streams and cannot accept the device-wide synchronisation that cudaMalloc and
  * cudaFree can cause. recon_gram_static gives them the same Gram matrix and lags as recon_gram
- * (same kernels) without a context: its scratch (per-block lag partials and twiddle tables)
+ * (same kernels) without a context: its scratch (per-row pruned DFTs and twiddle tables)
  * lives in one fixed device array of RECON_GRAM_STATIC_BYTES inside the library, which every
  * GPU that loads the library holds until the process exits. The paper has no counterpart; this
  * is a deployment aid, not part of the method.
@@ -205,7 +205,7 @@ int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
  *    capture.
  *  - A problem whose scratch exceeds RECON_GRAM_STATIC_BYTES is rejected with RECON_EINVAL and a
  *    message naming the bytes it needs (recon_last_error(NULL)); use recon_gram for it. The
- *    256x256x16 series with a 9x9x3 filter needs about 3.6 MB.
+ *    256x256x16 series with a 9x9x3 filter needs about 0.42 MB.
  *  - Every call uses the same array and it keeps the last call's contents; each call writes
  *    everything it reads first. Calls that overlap on the GPU (other host threads or streams)
  *    race on the array and must be serialised by the caller.

@@ -2,7 +2,7 @@
 // memory, e.g. a scanner-side reconstruction service whose device memory is planned up front and
 // may not grow, or a host program that shares the GPU with other work and cannot afford the
 // device-wide synchronisation that cudaMalloc / cudaFree can cause. Instead of the context's
-// workspace, the per-block lag partials and the twiddle tables live in one file-scope device
+// workspace, the per-row pruned DFTs and the twiddle tables live in one file-scope device
 // array of fixed size, which every GPU that loads the library keeps until the process exits.
 #include <cuda_runtime.h>
 
@@ -93,7 +93,7 @@ extern "C" int recon_gram_static(recon_dims dd, recon_filter f, const void* x, v
     float2* twQ = reinterpret_cast<float2*>(base + part);
     double2* twPd = reinterpret_cast<double2*>(base + part + twq);
     // Every byte the Gram kernels read from the array is written first in this call (twiddles
-    // here, each block's partial by that block), so no clearing is needed.
+    // here, each image row's pruned DFTs by that row's block), so no clearing is needed.
     const int n = d.P > d.Q ? d.P : d.Q;
     static_twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(d.P, d.Q, twQ, twPd);
     e = cudaGetLastError();

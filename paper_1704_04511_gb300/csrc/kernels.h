@@ -111,6 +111,7 @@ int max_parts();  // partial-sum slots a RedSlot must provide
 // ---- gram.cu ----
 // Lags of the Gram matrix (Sec. III-B): per-block partials then deterministic reduction and
 // Hermitian fill of G (column-major s x s complex128).
+size_t gram_smem(const Dims& d);  // shared memory of the Gram row kernel
 size_t gram_scratch_bytes(const Dims& d, int nblocks);
 int gram_blocks(const Dims& d);
 cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, double2* lag_part,

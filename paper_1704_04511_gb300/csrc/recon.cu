@@ -228,10 +228,7 @@ int get_twiddles(recon_ctx* c, const Dims& d, Twiddles* tw) {
     return RECON_OK;
 }
 
-size_t gram_smem_bytes(const Dims& d) {
-    return (size_t)d.npair() * d.L1() * d.L2() * sizeof(double2) +
-           ((size_t)d.T * d.Q + (size_t)d.npair() * d.Q + d.Q) * sizeof(float2) + 2 * d.npair() * sizeof(int);
-}
+size_t gram_smem_bytes(const Dims& d) { return recon::gram_smem(d); }
 
 int check_dims(recon_ctx* c, recon_dims dd, const recon_filter* f, Dims* d) {
     if (dd.P <= 0 || dd.Q <= 0 || dd.T <= 0) return fail(c, RECON_EINVAL, "P, Q, T must be positive");

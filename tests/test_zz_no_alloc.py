@@ -53,10 +53,11 @@ def test_gram_static_matches_gram_on_consecutive_calls():
             assert _rel(G_st, G_ref) < GRAM_TOL
             assert _rel(l_st, l_ref) < GRAM_TOL
         # a problem whose scratch exceeds the fixed array is refused with a clear message
-        x = torch.zeros((8, 32, 32), dtype=torch.complex64, device="cuda")
-        G = torch.zeros((15 * 15 * 6, 15 * 15 * 6), dtype=torch.complex128, device="cuda")
+        # (P rows x 21 pairs x 31 column lags of complex128 = 5.3 MB)
+        x = torch.zeros((8, 512, 32), dtype=torch.complex64, device="cuda")
+        G = torch.zeros((3 * 16 * 6, 3 * 16 * 6), dtype=torch.complex128, device="cuda")
         with pytest.raises(recon.ReconError) as e:
-            recon.recon_gram_static(x, (15, 15, 6), G)
+            recon.recon_gram_static(x, (3, 16, 6), G)
         assert e.value.code == recon.RECON_EINVAL
         assert "RECON_GRAM_STATIC_BYTES" in str(e.value)
     finally:
