@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kChunk = 2;  // eigenvectors per CTA
+constexpr int kMaxL1 = 1024;  // 2 N1 - 1 <= 2 P - 1 < 1024
 
 __global__ void eps_kernel(const double* __restrict__ lmax, double* eps, int first, double frac,
                            double gamma) {
@@ -79,38 +80,49 @@ __global__ void diag_reduce_kernel(const double2* __restrict__ dpart, int nchunk
     if (lane == 0) dsum[o] = v;
 }
 
-// Z[pair][i1][r2] = sum_{d2} d[pair][i1][d2] w_Q^{d2 r2}  (FP64, rounded to FP32 on store)
+// Z[pair][i1][r2] = sum_{d2} d[pair][i1][d2] w_Q^{d2 r2}  (FP64, rounded to FP32 on store);
+// the twiddle index (d2 r2) mod Q advances by r2 per lag (int arithmetic, no division).
 __global__ void __launch_bounds__(kThreads)
 s_stage1_kernel(const double2* __restrict__ dsum, int N1, int N2, int Q,
                 const double2* __restrict__ twQd, float2* __restrict__ Z) {
-    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1;
+    const int L2 = 2 * N2 - 1;
     const int row = blockIdx.x;  // pair * L1 + i1
     const double2* drow = dsum + (size_t)row * L2;
+    const int d2m0 = (Q - (N2 - 1) % Q) % Q;  // (-(N2 - 1)) mod Q
     for (int r2 = threadIdx.x; r2 < Q; r2 += blockDim.x) {
         double2 acc = make_double2(0.0, 0.0);
+        int ti = (d2m0 * r2) % Q;
         for (int i2 = 0; i2 < L2; ++i2) {
-            const int d2 = i2 - (N2 - 1);
-            const int ti = (int)((((long long)d2 % Q + Q) % Q * r2) % Q);
             acc = zfma(drow[i2], twQd[ti], acc);
+            ti += r2;
+            if (ti >= Q) ti -= Q;
         }
         Z[(size_t)row * Q + r2] = make_float2((float)acc.x, (float)acc.y);
     }
 }
 
-// S[pair][r1][r2] = sum_{d1} Z[pair][d1][r2] w_P^{d1 r1}  (FP32)
+// S[pair][r1][r2] = sum_{d1} Z[pair][d1][r2] w_P^{d1 r1}  (FP32): one CTA per image row r1, its
+// L1 twiddles in shared memory, every pair and column.
 __global__ void __launch_bounds__(kThreads)
-s_stage2_kernel(const float2* __restrict__ Z, int N1, int P, int Q,
+s_stage2_kernel(const float2* __restrict__ Z, int N1, int P, int Q, int npair,
                 const float2* __restrict__ twP, float2* __restrict__ S) {
+    __shared__ float2 w1[kMaxL1];
     const int L1 = 2 * N1 - 1;
-    const int r1 = blockIdx.x, pr = blockIdx.y;
-    const float2* zp = Z + (size_t)pr * L1 * Q;
-    for (int r2 = threadIdx.x; r2 < Q; r2 += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f);
+    const int r1 = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int ti = (((P - (N1 - 1) % P) % P) * r1) % P;
         for (int i1 = 0; i1 < L1; ++i1) {
-            const int d1 = i1 - (N1 - 1);
-            const int ti = (int)((((long long)d1 % P + P) % P * r1) % P);
-            acc = cfma(zp[(size_t)i1 * Q + r2], twP[ti], acc);
+            w1[i1] = twP[ti];
+            ti += r1;
+            if (ti >= P) ti -= P;
         }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < npair * Q; e += blockDim.x) {
+        const int pr = e / Q, r2 = e % Q;
+        const float2* zp = Z + (size_t)pr * L1 * Q + r2;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i1 = 0; i1 < L1; ++i1) acc = cfma(zp[(size_t)i1 * Q], w1[i1], acc);
         S[((size_t)pr * P + r1) * Q + r2] = acc;
     }
 }
@@ -157,8 +169,8 @@ cudaError_t launch_weight_S(const Dims& d, const Twiddles& tw, const double2* ds
     s_stage1_kernel<<<d.npair() * d.L1(), kThreads, 0, st>>>(dsum, d.N1, d.N2, d.Q, tw.twQd, Z);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 grid(d.P, d.npair());
-    s_stage2_kernel<<<grid, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, tw.twP, S);
+    if (d.L1() > kMaxL1) return cudaErrorInvalidValue;
+    s_stage2_kernel<<<d.P, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, d.npair(), tw.twP, S);
     return cudaGetLastError();
 }
 
