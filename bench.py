@@ -64,6 +64,11 @@ def alg_bytes(kind: str, w, n_cg: int) -> float:
 
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 dense FP64, nominal (a probe here measured ~1056)
 ALU_KINDS = ("hpd_inverse", "lanczos")
+# DRAM bytes (read + write) per launch from one ncu capture of the launch class's kernel at the
+# benchmark workload (steady state, caches kept; profiles/hpd_sweep_kernel_s243.md gives the
+# command). Only for the kernel versions those captures measured: drop an entry when its
+# kernel changes.
+TRAFFIC_BYTES = {"hpd_inverse": 82944}
 
 
 def alg_flops(kind: str, w) -> float:
@@ -105,7 +110,7 @@ class ClockSampler:
         self.th = None
 
     def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
         if self.gpu_id:
             cmd += ["-i", self.gpu_id]
         try:
@@ -115,6 +120,9 @@ class ClockSampler:
             return
         self.th = threading.Thread(target=self._read, daemon=True)
         self.th.start()
+        t0 = time.time()  # let the first sample arrive before the timed region starts
+        while not self.lines and time.time() - t0 < 2.0:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -247,7 +255,7 @@ def run_reference(args, rank: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -406,7 +414,7 @@ def main():
                 "peak_source": "nominal FP64 rate of the part (no measured FP64 peak provided)",
                 "alg_flops_per_launch": work,
                 "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
-                "traffic": None}
+                "traffic": TRAFFIC_BYTES.get(dom)}
     else:
         work = alg_bytes(dom, w, w.n_cg)
         achieved = work / (dom_ms / dom_n / 1000.0) / 1e9 if dom_n else 0.0
@@ -414,7 +422,7 @@ def main():
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "alg_bytes_per_launch": work,
                 "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
-                "traffic": None}
+                "traffic": TRAFFIC_BYTES.get(dom)}
     # the memory-bound CG passes (per-launch time from the profiled solve)
     cg_roof = {}
     for k in ("cg_frame_aha", "cg_w_combine", "cg_row_fwd", "cg_col_mask", "cg_row_inv_w",
