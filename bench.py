@@ -396,6 +396,20 @@ def main():
     e1.synchronize()
     _, e2e_value = whole_job_rate(e0.elapsed_time(e1), args.steps * B * w.n_irls, dist, dev)
 
+    # ---- T2 maps of the reconstructed series (recon_t2fit), timed alone with events
+    t2_map = torch.empty(tuple(outs[0].shape[1:]), dtype=torch.float32, device=dev)
+    t2_reps = 20
+    for _ in range(3):
+        recon.recon_t2fit(ctx.h, outs[0], w.times_ms, t2_map)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(t2_reps):
+        recon.recon_t2fit(ctx.h, outs[0], w.times_ms, t2_map)
+    e1.record(stream)
+    e1.synchronize()
+    t2_us = 1000.0 * e0.elapsed_time(e1) / t2_reps
+    t2_fg = int(torch.isfinite(t2_map).sum().item())
+
     if rank != 0:
         ctx.close()
         if dist:
@@ -459,6 +473,10 @@ def main():
                 "h2d_bytes_per_step": int(B * (bs[0].numel() * 8 + ms[0].numel())),
                 "d2h_bytes_per_step": int(B * outs[0].numel() * 8)},
         "clocks": clocks,
+        "t2fit": {"us_per_map": round(t2_us, 2), "pixels": int(t2_map.numel()),
+                  "foreground_pixels": t2_fg, "gauss_newton_steps": 20,
+                  "note": "mono-exponential T2 map of one reconstructed series, synchronous call "
+                          "(max |x_0| pass + per-pixel fit), outside the timed region"},
     }
     if args.served > 0:
         line["served"] = run_served(args.served, local_rank)

@@ -214,6 +214,20 @@ int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
 int recon_gram_static(recon_dims d, recon_filter f, const void* x, void* G_out, void* lags_out,
                       void* cuda_stream);
 
+/* Mono-exponential T2 map of a recovered series (Sec. IV-A: the paper fits a mono-exponential
+ * model to every pixel of the reconstructed series for its T2 maps). Over the foreground pixels
+ * |x_0(r)| > fg_frac * max |x_0|: |x_n(r)| ~ A(r) exp(-t_n / T2(r)), log-linear least squares for
+ * the start, then n_gn Gauss-Newton steps on the un-logged residual, 1/T2 >= 1e-4 per ms; FP32.
+ * The foreground test is computed in FP32 with separately rounded operations (reproducible on a
+ * host in FP32).
+ *  - x: device [T][P][Q] complex64 (e.g. recon_solve's output), 2 <= T <= 64.
+ *  - times_ms: HOST array of the T echo times in ms, read during the call.
+ *  - t2_out: device [P][Q] float32, T2 in ms, NaN outside the foreground; amp_out: device
+ *    [P][Q] float32 amplitude A, or NULL.
+ *  - 0 <= fg_frac < 1, 0 <= n_gn <= 1000, else RECON_EINVAL. Synchronous. */
+int recon_t2fit(recon_ctx* c, recon_dims d, const void* x, const double* times_ms, double fg_frac,
+                int n_gn, float* t2_out, float* amp_out);
+
 /* ---- measurement ---- */
 
 /* Launch classes timed by recon_profile (one pair of CUDA events on the context's stream around

@@ -154,4 +154,14 @@ cudaError_t launch_frame_aha(const Dims& d, const Twiddles& tw, const float2* r,
 cudaError_t launch_w_combine(const Dims& d, float2* t, const float2* p, const float2* S, float lam,
                              Partials* pq, cudaStream_t st);
 
+// ---- t2fit.cu ----
+constexpr int kT2MaxT = 64;
+struct T2Times {
+    float t[kT2MaxT];  // echo times in ms (passed to the kernel by value)
+};
+// T2 and amplitude maps of a series: max |x_0| into *amax_scratch (one word, zeroed here), then
+// the per-pixel fit (NaN outside the foreground |x_0| > frac max |x_0|); amp may be null.
+cudaError_t launch_t2fit(const Dims& d, const float2* x, const T2Times& tm, float frac, int n_gn,
+                         unsigned int* amax_scratch, float* t2, float* amp, cudaStream_t st);
+
 }  // namespace recon

@@ -1106,6 +1106,35 @@ int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, 
     return RECON_OK;
 }
 
+int recon_t2fit(recon_ctx* c, recon_dims dd, const void* x, const double* times_ms, double fg_frac,
+                int n_gn, float* t2_out, float* amp_out) {
+    if (!c) return RECON_EINVAL;
+    if (!x || !times_ms || !t2_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (dd.P <= 0 || dd.Q <= 0 || dd.T < 2 || dd.T > recon::kT2MaxT)
+        return fail(c, RECON_EINVAL, "need P, Q > 0 and 2 <= T <= 64");
+    if (!(fg_frac >= 0.0 && fg_frac < 1.0)) return fail(c, RECON_EINVAL, "need 0 <= fg_frac < 1");
+    if (n_gn < 0 || n_gn > 1000) return fail(c, RECON_EINVAL, "need 0 <= n_gn <= 1000");
+    recon::T2Times tm{};
+    for (int n = 0; n < dd.T; ++n) {
+        if (!std::isfinite(times_ms[n])) return fail(c, RECON_EINVAL, "echo times must be finite");
+        tm.t[n] = (float)times_ms[n];
+    }
+    int rc = set_device(c);
+    if (rc) return rc;
+    void* amax = nullptr;
+    rc = ensure(c, "t2amax", 256, &amax);
+    if (rc) return rc;
+    recon::Dims d;
+    d.T = dd.T;
+    d.P = dd.P;
+    d.Q = dd.Q;
+    d.N1 = d.N2 = d.M = 1;
+    RC_CUDA(recon::launch_t2fit(d, (const float2*)x, tm, (float)fg_frac, n_gn, (unsigned int*)amax,
+                                t2_out, amp_out, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
 int recon_set_option(recon_ctx* c, int option, int value) {
     if (!c) return RECON_EINVAL;
     switch (option) {

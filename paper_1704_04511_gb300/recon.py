@@ -38,7 +38,7 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
             "recon_profile_read", "recon_profile_name", "recon_gram_static",
-            "recon_solve_batch", "recon_set_option", "recon_submit", "recon_poll")
+            "recon_solve_batch", "recon_set_option", "recon_submit", "recon_poll", "recon_t2fit")
 
 PROF_KINDS = 15
 
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_submit": (i, [vp, dims, vp, vp, filt, ctypes.POINTER(recon_params), vp,
                                  ctypes.POINTER(i)]),
             "recon_poll": (i, [vp, i, ctypes.POINTER(i)]),
+            "recon_t2fit": (i, [vp, dims, vp, ctypes.POINTER(d), d, i, vp, vp]),
             "recon_solve_batch": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp), filt,
                                       ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
         }
@@ -284,6 +285,15 @@ def recon_cg(ctx, masks, filt, S_old, S_new, lam: float, x, r, n_cg: int):
     _check(ctx, load_library().recon_cg(ctx, _dims(x), _filt(filt), _ptr(masks), _ptr(S_old),
                                         _ptr(S_new), float(lam), _ptr(x), _ptr(r), int(n_cg), hist))
     return list(hist)
+
+
+def recon_t2fit(ctx, x, times_ms, t2_out, amp_out=None, fg_frac: float = 0.1, n_gn: int = 20) -> None:
+    """T2 (ms, NaN outside the foreground) and optionally amplitude maps of a [T, P, Q] series."""
+    if len(times_ms) != x.shape[0]:
+        raise ValueError("need one echo time per frame")
+    t = (ctypes.c_double * len(times_ms))(*[float(v) for v in times_ms])
+    _check(ctx, load_library().recon_t2fit(ctx, _dims(x), _ptr(x), t, float(fg_frac), int(n_gn),
+                                           _ptr(t2_out), _ptr(amp_out)))
 
 
 PROF_ALL = (1 << 15) - 1
