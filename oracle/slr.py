@@ -7,7 +7,9 @@ primitives. Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg
 Conventions (readings of the paper, each stated where it is used):
   * The unknown is the image series x, shape (T, P, Q), complex. Its k-space is x_hat = F x with F
     the unitary 2-D DFT, forward sign e^{-2 pi i}, natural frequency order.
-  * A_n = mask_n * F (single coil, Eq. measurement-ij with C_j = I).
+  * A_n = mask_n * F (single coil, Eq. measurement-ij with C_j = I). With coils (Eq.
+    measurement-ij): b[c, n] = mask_n * F (C_c * x_n) for coil sensitivities C_c (P, Q); the
+    paper's F C_j F^* acting on the k-space x_hat is the multiplication of the image by C_j.
   * Filter support Lambda = N1 x N2 spatial taps x M frame taps, s = N1*N2*M columns. A column of
     the lifted matrix is indexed a = (m*N1 + l1)*N2 + l2.
   * Lifting (Sec. II-B, Eq. annihil-compact, with the hybrid approximation of Sec. III-A): space is
@@ -50,6 +52,16 @@ def A(x: np.ndarray, masks: np.ndarray) -> np.ndarray:
 def AH(b: np.ndarray, masks: np.ndarray) -> np.ndarray:
     """A^H b = F^H (mask * b), frame by frame."""
     return F2H(masks * b)
+
+
+def A_coils(x: np.ndarray, masks: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """b[c, n] = mask_n * F (C_c * x_n) (Eq. measurement-ij): coil-major (Nc, T, P, Q)."""
+    return np.stack([masks * F2(C[c][None] * x) for c in range(C.shape[0])])
+
+
+def AH_coils(b: np.ndarray, masks: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """A^H b = sum_c conj(C_c) * F^H (mask_n * b[c, n])."""
+    return sum(np.conj(C[c])[None] * F2H(masks * b[c]) for c in range(C.shape[0]))
 
 
 # ----------------------------------------------------------------------------------------------
@@ -236,9 +248,12 @@ def penalty_filters(x: np.ndarray, Hh: np.ndarray, N1: int, N2: int, M: int) -> 
 # Least-squares step (Eq. x-update / grad-ls) by conjugate gradients (Algorithm 1, step 2)
 # ----------------------------------------------------------------------------------------------
 
-def normal_op(x: np.ndarray, masks: np.ndarray, S: np.ndarray, lam: float) -> np.ndarray:
-    """(A^H A + lam W) x."""
-    return AH(A(x, masks), masks) + lam * apply_W(x, S)
+def normal_op(x: np.ndarray, masks: np.ndarray, S: np.ndarray, lam: float,
+              coils: np.ndarray | None = None) -> np.ndarray:
+    """(A^H A + lam W) x, single coil or with coil sensitivities `coils` (Nc, P, Q)."""
+    if coils is None:
+        return AH(A(x, masks), masks) + lam * apply_W(x, S)
+    return AH_coils(A_coils(x, masks, coils), masks, coils) + lam * apply_W(x, S)
 
 
 def vdot(u: np.ndarray, v: np.ndarray) -> complex:
@@ -282,17 +297,18 @@ def initial_eps(x0: np.ndarray, N1: int, N2: int, M: int, frac: float = 0.01) ->
 
 def irls(kspace: np.ndarray, masks: np.ndarray, N1: int, N2: int, M: int, lam: float, p: float,
          n_irls: int, n_cg: int, gamma: float = 1.4, eps_frac: float = 0.01,
-         history: list | None = None) -> np.ndarray:
+         history: list | None = None, coils: np.ndarray | None = None) -> np.ndarray:
     """Algorithm 1 with x^(0) = A^H b, eps^(0) = lambda_max / 100, eps <- eps / gamma.
 
     Iteration n uses the weight from x^(n-1) and eps^(n-1), then n_cg CG steps warm-started at
-    x^(n-1). If `history` is a list, (eps, x) after each iteration is appended."""
-    rhs = AH(kspace, masks)
+    x^(n-1). If `history` is a list, (eps, x) after each iteration is appended. With `coils`
+    (Nc, P, Q) the k-space is coil-major (Nc, T, P, Q) and A is the multi-coil operator."""
+    rhs = AH(kspace, masks) if coils is None else AH_coils(kspace, masks, coils)
     x = rhs.copy()
     eps = initial_eps(x, N1, N2, M, eps_frac)
     for _ in range(n_irls):
         S = weight_from_x(x, N1, N2, M, eps, p)
-        x = cg(lambda v: normal_op(v, masks, S, lam), rhs, x, n_cg)
+        x = cg(lambda v: normal_op(v, masks, S, lam, coils), rhs, x, n_cg)
         if history is not None:
             history.append((eps, x.copy()))
         eps = eps / gamma

@@ -16,4 +16,5 @@ from .phantom import (  # noqa: F401
     smooth_field,
     vd_mask,
     served_mix,
+    coil_maps,
 )

@@ -46,6 +46,7 @@ class Workload:
     n_cg: int
     snr_db: float = 30.0
     seed: int = 0
+    n_coils: int = 1           # receiver coils (Eq. measurement-ij); 1 = single channel
 
     @property
     def shape(self):
@@ -72,7 +73,18 @@ def _perf():
         R=8.0, N1=9, N2=9, M=3, lam=1e-3, p=0.0, n_irls=30, n_cg=15)
 
 
-WORKLOADS = {w.name: w for w in (_tiny(), _perf())}
+def _coils():
+    # the paper's in-vivo series (Sec. IV-A): 128 x 128, 12 echoes at 10 .. 120 ms, 12 coils.
+    # lam: with 12 coils at 6x the data term alone is a noisy SENSE-type fit; 0.1 lets IRLS halve
+    # the adjoint's error (the paper picks its weight by an SNR sweep, not reproduced here)
+    return Workload(
+        name="coils_128x128x12", P=128, Q=128, T=12,
+        times_ms=tuple(10.0 * (n + 1) for n in range(12)),
+        n_ellipses=8, t2_ranges=((20.0, 120.0),), frac_range=(1.0, 1.0),
+        R=6.0, N1=9, N2=9, M=3, lam=0.1, p=0.0, n_irls=20, n_cg=10, n_coils=12)
+
+
+WORKLOADS = {w.name: w for w in (_tiny(), _perf(), _coils())}
 
 
 def workload(name: str, **overrides) -> Workload:
@@ -158,21 +170,54 @@ def make_series(w: Workload) -> np.ndarray:
     return x.astype(np.complex128)
 
 
+def coil_maps(n_coils: int, P: int, Q: int, rng: np.random.Generator) -> np.ndarray:
+    """Smooth complex receiver sensitivities (n_coils, P, Q): coils spaced on a circle of radius
+    0.6 P around the image centre, Gaussian magnitude fall-off (sigma 0.4 P, periodic distance),
+    a random constant phase plus a small random linear phase ramp each, normalised so that
+    sum_c |C_c|^2 = 1 at every pixel."""
+    yy, xx = np.meshgrid(np.arange(P, dtype=np.float64), np.arange(Q, dtype=np.float64),
+                         indexing="ij")
+    maps = []
+    for c in range(n_coils):
+        ang = 2.0 * np.pi * c / n_coils
+        cy = P / 2.0 + 0.6 * P * np.sin(ang)
+        cx = Q / 2.0 + 0.6 * Q * np.cos(ang)
+        dy = (yy - cy + P / 2.0) % P - P / 2.0
+        dx = (xx - cx + Q / 2.0) % Q - Q / 2.0
+        mag = np.exp(-(dy * dy + dx * dx) / (2.0 * (0.4 * P) ** 2))
+        ky, kx = rng.uniform(-1.0, 1.0, size=2)
+        ph = rng.uniform(0.0, 2.0 * np.pi) + 2.0 * np.pi * (ky * yy / P + kx * xx / Q)
+        maps.append(mag * np.exp(1j * ph))
+    C = np.stack(maps)
+    return C / np.sqrt((np.abs(C) ** 2).sum(0))[None]
+
+
 def make_problem(w: Workload) -> dict:
     """Seeded problem: x_true (T,P,Q) complex128, masks (T,P,Q) uint8, kspace (T,P,Q) complex128.
 
     kspace = mask * (F x_true + eta); eta is complex Gaussian on the sampled entries, scaled so
-    that 20 log10(||mask * F x_true|| / ||eta||) equals w.snr_db exactly."""
+    that 20 log10(||mask * F x_true|| / ||eta||) equals w.snr_db exactly. With w.n_coils > 1 the
+    k-space is coil-major (Nc, T, P, Q), kspace[c, n] = mask_n * (F (C_c x_n) + eta), and the
+    sensitivities (Nc, P, Q) are returned as "coils" (seed S + 20)."""
     S = w.seed
     x = make_series(w)
     masks = np.stack([vd_mask(w.P, w.Q, w.R, np.random.default_rng(S + 10 + n))
                       for n in range(w.T)])
-    clean = masks * np.fft.fft2(x, norm="ortho")
+    if w.n_coils > 1:
+        coils = coil_maps(w.n_coils, w.P, w.Q, np.random.default_rng(S + 20))
+        clean = np.stack([masks * np.fft.fft2(coils[c][None] * x, norm="ortho")
+                          for c in range(w.n_coils)])
+    else:
+        coils = None
+        clean = masks * np.fft.fft2(x, norm="ortho")
     rng = np.random.default_rng(S + 99)
-    eta = (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)) * masks
+    eta = (rng.standard_normal(clean.shape) + 1j * rng.standard_normal(clean.shape)) * masks
     scale = np.linalg.norm(clean) * 10.0 ** (-w.snr_db / 20.0) / max(np.linalg.norm(eta), 1e-300)
     kspace = clean + scale * eta
-    return {"x_true": x, "masks": masks, "kspace": kspace, "workload": w}
+    out = {"x_true": x, "masks": masks, "kspace": kspace, "workload": w}
+    if coils is not None:
+        out["coils"] = coils
+    return out
 
 
 def served_mix(n_requests: int = 512, rate_hz: float = 20.0, seed: int = 0,
