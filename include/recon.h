@@ -214,6 +214,29 @@ int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
 int recon_gram_static(recon_dims d, recon_filter f, const void* x, void* G_out, void* lags_out,
                       void* cuda_stream);
 
+/* ---- multi-coil measurements (Eq. measurement-ij with receiver sensitivities) ----
+ * b[c][n] = mask_n * F (C_c * x_n) + noise for coils c < n_coils: the paper's S_i F C_j F^* acting
+ * on the k-space of frame i is the multiplication of the image by C_j. A^H b =
+ * sum_c conj(C_c) F^H (mask_n b[c][n]); the normal operator of the least-squares step becomes
+ * sum_c conj(C_c) F^H mask F (C_c x) + lambda W x. Layouts (all device, caller-owned):
+ *  - kspace: coil-major [n_coils][T][P][Q] complex64 (bf16 storage is not offered here);
+ *  - coils: [n_coils][P][Q] complex64 sensitivities (any normalisation; the tests use
+ *    sum_c |C_c|^2 = 1);
+ *  - masks, x, image_out: as for the single-coil calls ([T][P][Q]).
+ * The workspace holds n_coils transform series (8 n_coils T P Q bytes) instead of one, on top of
+ * recon_bytes_needed; serving (recon_submit) is single-coil. */
+#define RECON_MAX_COILS 64
+int recon_solve_coils(recon_ctx* c, recon_dims d, const void* kspace, const uint8_t* masks,
+                      const void* coils, int n_coils, recon_filter f, const recon_params* prm,
+                      void* image_out);
+/* x = A^H b with coils. */
+int recon_adjoint_coils(recon_ctx* c, recon_dims d, const void* kspace, const uint8_t* masks,
+                        const void* coils, int n_coils, void* x_out);
+/* y = (A^H A + lambda W) x with coils; S as for recon_apply_normal. */
+int recon_apply_normal_coils(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
+                             const void* coils, int n_coils, const void* S, double lambda,
+                             const void* x, void* y);
+
 /* Mono-exponential T2 map of a recovered series (Sec. IV-A: the paper fits a mono-exponential
  * model to every pixel of the reconstructed series for its T2 maps). Over the foreground pixels
  * |x_0(r)| > fg_frac * max |x_0|: |x_n(r)| ~ A(r) exp(-t_n / T2(r)), log-linear least squares for

@@ -170,6 +170,85 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
     if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
+// Pass C of a CG step with coils (ADJ = false), or the coil combination of the adjoint
+// (ADJ = true). One CTA per image row r1 holds that row of every frame: for each coil c it
+// inverse-transforms the rows t[c][n][r1] and accumulates conj(C_c) * (...) (Eq.
+// measurement-ij: A^H = sum_c conj(C_c) F^H mask). ADJ: the sum is x[n][r1]. Otherwise lam W p is
+// added from the p rows, q goes over coil 0's plane of t (rows r1, read by this CTA only) and the
+// row's partial Re <p, q> to pq_parts.
+template <int N, int M, bool ADJ>
+__global__ void __launch_bounds__(kThreads)
+coil_row_inv_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ coils,
+                    const float2* __restrict__ S, float lam, int T, int P, int nc,
+                    double* __restrict__ pq_parts, float2* __restrict__ x_out,
+                    const float2* __restrict__ tw_g) {
+    extern __shared__ float2 sm[];
+    __shared__ double red[kThreads / 32];
+    float2* a = sm;
+    float2* b = a + (size_t)T * N;
+    float2* acc = b + (size_t)T * N;
+    float2* pt = acc + (size_t)T * N;
+    float2* tw = pt + (size_t)T * N;
+    const int r1 = blockIdx.x;
+    const size_t npix = (size_t)P * N;
+    const size_t series = (size_t)T * npix;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    pdl_wait();
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        acc[e] = make_float2(0.f, 0.f);
+        if (!ADJ) pt[e] = p[(size_t)(e / N) * npix + (size_t)r1 * N + e % N];
+    }
+    for (int c = 0; c < nc; ++c) {
+        __syncthreads();  // a, b free again
+        for (int e = threadIdx.x; e < T * N; e += blockDim.x)
+            a[e] = t[c * series + (size_t)(e / N) * npix + (size_t)r1 * N + e % N];
+        __syncthreads();
+        float2* res = fft_smem<N, true, false>(a, b, T, N, 1, tw);
+        for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+            const float2 cv = coils[((size_t)c * P + r1) * N + e % N];
+            acc[e] = cfmacj(cv, res[e], acc[e]);
+        }
+    }
+    __syncthreads();
+    if constexpr (ADJ) {
+        pdl_trigger();
+        for (int e = threadIdx.x; e < T * N; e += blockDim.x)
+            x_out[(size_t)(e / N) * npix + (size_t)r1 * N + e % N] = acc[e];
+        return;
+    } else {
+        const int k = T - M + 1;
+        float accd = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
+        for (int c = threadIdx.x; c < N; c += blockDim.x) {
+            float2 s[M][M];
+            load_S<M>(S, npix, (size_t)r1 * N + c, s);
+            for (int n = 0; n < T; ++n) {
+                float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int aa = 0; aa < M; ++aa) {
+                    const int j = n - M + 1 + aa;
+                    if (j < 0 || j >= k) continue;
+#pragma unroll
+                    for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(n + aa - bb) * N + c], w);
+                }
+                float2 q = acc[n * N + c];
+                q.x = fmaf(lam, w.x, q.x);
+                q.y = fmaf(lam, w.y, q.y);
+                acc[n * N + c] = q;
+                const float2 pv = pt[n * N + c];
+                const float term = fmaf(pv.x, q.x, pv.y * q.y) - comp;
+                const float sum = accd + term;
+                comp = (sum - accd) - term;
+                accd = sum;
+            }
+        }
+        const double tot = block_sum_f_t0(accd, red);
+        pdl_trigger();
+        for (int e = threadIdx.x; e < T * N; e += blockDim.x)
+            t[(size_t)(e / N) * npix + (size_t)r1 * N + e % N] = acc[e];
+        if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
+    }
+}
+
 // Pass D: alpha = |r|^2 / Re <p, q> (Re <p, q> summed here from pass C's partials); x += alpha p;
 // r -= alpha q; per-CTA partials of |r_new|^2 for the next pass A.
 __global__ void __launch_bounds__(kUpdThreads, kUpdPerSM)
@@ -232,14 +311,17 @@ __global__ void sum_partials_kernel(const double* __restrict__ parts, int n, dou
     if (threadIdx.x == 0) out[0] = v;
 }
 
-// Residual carry between IRLS iterations: r = (first ? 0 : r) + lam W_{dS} x with
+// Residual carry between IRLS iterations: r = (first ? r0 : r) + lam W_{dS} x with
 // dS = S_old - S_new (or -S_new when first); partial |r|^2. One thread per pixel, all frames.
+// r0 = A^H b - A^H A x0 = x0 - A^H A x0 for x0 = A^H b: zero for one coil and 0/1 masks (A A^H
+// is then a projection), x0 - aha_x when A^H A x0 is supplied (coils).
 template <int M>
 __global__ void __launch_bounds__(kThreads)
 resid_carry_kernel(float2* __restrict__ r, const float2* __restrict__ x,
-                   const float2* __restrict__ S_old, const float2* __restrict__ S_new, float lam,
-                   int first, int T, size_t npix, double* __restrict__ parts,
-                   unsigned int* counter, double* __restrict__ rr_out) {
+                   const float2* __restrict__ aha_x, const float2* __restrict__ S_old,
+                   const float2* __restrict__ S_new, float lam, int first, int T, size_t npix,
+                   double* __restrict__ parts, unsigned int* counter,
+                   double* __restrict__ rr_out) {
     __shared__ double red[kThreads / 32];
     const int k = T - M + 1;
     float acc = 0.f, comp = 0.f;
@@ -269,7 +351,13 @@ resid_carry_kernel(float2* __restrict__ r, const float2* __restrict__ x,
 #pragma unroll
                 for (int b = 0; b < M; ++b) w = cfma(s[a][b], x[(size_t)(n + a - b) * npix + px], w);
             }
-            float2 rv = first ? make_float2(0.f, 0.f) : r[(size_t)n * npix + px];
+            float2 rv = make_float2(0.f, 0.f);
+            if (!first) {
+                rv = r[(size_t)n * npix + px];
+            } else if (aha_x) {  // x0 - A^H A x0 (coils: A A^H is no projection)
+                const float2 xv = x[(size_t)n * npix + px], av = aha_x[(size_t)n * npix + px];
+                rv = make_float2(xv.x - av.x, xv.y - av.y);
+            }
             rv.x = fmaf(lam, w.x, rv.x);
             rv.y = fmaf(lam, w.y, rv.y);
             r[(size_t)n * npix + px] = rv;
@@ -281,6 +369,23 @@ resid_carry_kernel(float2* __restrict__ r, const float2* __restrict__ x,
     }
     const double tot = block_sum_f_t0(acc, red);
     last_block_sum(tot, parts, counter, rr_out);
+}
+
+// max_r | |C(r)|^2 - 1 | of one coil map into *dev (non-negative float bits: atomicMax exact).
+__global__ void __launch_bounds__(kThreads)
+coil_unimodular_kernel(const float2* __restrict__ C, size_t npix, unsigned int* __restrict__ dev) {
+    float m = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = C[i];
+        m = fmaxf(m, fabsf(fmaf(v.x, v.x, v.y * v.y) - 1.f));
+    }
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    if ((threadIdx.x & 31) == 0) atomicMax(dev, __float_as_uint(m));
 }
 
 // y = W_S x (no lambda); parity tests only.
@@ -363,6 +468,52 @@ int upd_grid(size_t n4) {
     return (int)(g < 1 ? 1 : (g < (size_t)kMaxParts ? g : (size_t)kMaxParts));
 }
 
+template <int N, int M, bool ADJ>
+cudaError_t launch_coil_inv_NM(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                               const float2* coils, const float2* S, float lam, double* pq_parts,
+                               float2* x_out, cudaStream_t st) {
+    auto k = coil_row_inv_kernel<N, M, ADJ>;
+    const size_t smem = ((size_t)4 * d.T * N + N) * sizeof(float2);
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_pdl(k, dim3(d.P), dim3(kThreads), smem, st, t, p, coils, S, lam, d.T, d.P, d.nc,
+                      pq_parts, x_out, tw.twQ);
+}
+
+template <int N, bool ADJ>
+cudaError_t launch_coil_inv_N(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                              const float2* coils, const float2* S, float lam, double* pq_parts,
+                              float2* x_out, cudaStream_t st) {
+    if constexpr (ADJ) {
+        return launch_coil_inv_NM<N, 1, true>(d, tw, t, p, coils, S, lam, pq_parts, x_out, st);
+    } else {
+        switch (d.M) {
+#define CASE(MM) \
+    case MM: return launch_coil_inv_NM<N, MM, false>(d, tw, t, p, coils, S, lam, pq_parts, x_out, st);
+            CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
+#undef CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
+}
+
+template <bool ADJ>
+cudaError_t launch_coil_inv(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                            const float2* coils, const float2* S, float lam, double* pq_parts,
+                            float2* x_out, cudaStream_t st) {
+    if (d.P > kMaxParts) return cudaErrorInvalidValue;
+    switch (d.Q) {
+#define CASE(NN) \
+    case NN: return launch_coil_inv_N<NN, ADJ>(d, tw, t, p, coils, S, lam, pq_parts, x_out, st);
+        CASE(16) CASE(32) CASE(64) CASE(128) CASE(192) CASE(256) CASE(512)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 int num_sms() {
@@ -396,6 +547,18 @@ cudaError_t launch_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const
     }
 }
 
+cudaError_t launch_coil_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                                  const float2* coils, const float2* S, float lam, Partials* pq,
+                                  cudaStream_t st) {
+    pq->n = d.P;
+    return launch_coil_inv<false>(d, tw, t, p, coils, S, lam, pq->parts, nullptr, st);
+}
+
+cudaError_t launch_coil_combine(const Dims& d, const Twiddles& tw, float2* t, const float2* coils,
+                                float2* x, cudaStream_t st) {
+    return launch_coil_inv<true>(d, tw, t, nullptr, coils, nullptr, 0.f, nullptr, x, st);
+}
+
 cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* p,
                              const float2* q, const double* rr_in, const Partials& pq,
                              Partials* rr, cudaStream_t st) {
@@ -415,12 +578,12 @@ cudaError_t launch_sum_partials(const Partials& in, double* out, cudaStream_t st
 
 cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const float2* S_old,
                                const float2* S_new, float lam, int first, const RedSlot& rs,
-                               double* rr_out, cudaStream_t st) {
+                               double* rr_out, cudaStream_t st, const float2* aha_x) {
     const int g = pix_grid(d.pixels());
 #define CASE(MM)                                                                              \
     case MM:                                                                                  \
-        resid_carry_kernel<MM><<<g, kThreads, 0, st>>>(r, x, S_old, S_new, lam, first, d.T,   \
-                                                       d.pixels(), rs.parts, rs.counter,      \
+        resid_carry_kernel<MM><<<g, kThreads, 0, st>>>(r, x, aha_x, S_old, S_new, lam, first, \
+                                                       d.T, d.pixels(), rs.parts, rs.counter, \
                                                        rr_out);                               \
         break;
     switch (d.M) {
@@ -428,6 +591,14 @@ cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const 
         default: return cudaErrorInvalidValue;
     }
 #undef CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coil_unimodular(const Dims& d, const float2* coils, unsigned int* dev,
+                                   cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(dev, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    coil_unimodular_kernel<<<pix_grid(d.pixels()), kThreads, 0, st>>>(coils, d.pixels(), dev);
     return cudaGetLastError();
 }
 

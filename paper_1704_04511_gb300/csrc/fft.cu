@@ -89,11 +89,69 @@ row_fwd_pupdate_kernel(const float2* __restrict__ r, float2* __restrict__ p,
     for (int e = threadIdx.x; e < nr * N; e += blockDim.x) t[base + e] = res[e];
 }
 
+// Pass A of a CG step with coils (Eq. measurement-ij): p = r (first) or r + beta p as in
+// row_fwd_pupdate_kernel, then for every coil c the row FFT of C_c * p goes to the coil-major
+// transform buffer t[c][n] (rows of the T x P row space; coil maps [nc][P][Q]).
+template <int N>
+__global__ void __launch_bounds__(kThreads)
+coil_row_fwd_kernel(const float2* __restrict__ r, float2* __restrict__ p, float2* __restrict__ t,
+                    const float2* __restrict__ coils, int nrows, int P, int nc,
+                    const double* __restrict__ rr_parts, int n_rr,
+                    const double* __restrict__ rr_prev, double* __restrict__ rr_out, int first,
+                    const float2* __restrict__ tw_g) {
+    constexpr int ROWS = rows_per_cta<N>();
+    extern __shared__ float2 sm[];
+    __shared__ float beta_s;
+    __shared__ double s_rr;
+    float2* a = sm;
+    float2* b = a + ROWS * N;
+    float2* pk = b + ROWS * N;
+    float2* tw = pk + ROWS * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+    pdl_wait();
+    float beta = 0.f;
+    if (!first) {
+        const double rr_new = sum_partials(rr_parts, n_rr, &s_rr);
+        if (threadIdx.x == 0) {
+            beta_s = (float)(rr_new * rcp_nr(rr_prev[0]));
+            if (blockIdx.x == 0) rr_out[0] = rr_new;
+        }
+        __syncthreads();
+        beta = beta_s;
+    }
+    const int row0 = blockIdx.x * ROWS;
+    const int nr = min(ROWS, nrows - row0);
+    const size_t base = (size_t)row0 * N;
+    const size_t series = (size_t)nrows * N;  // one coil's T x P x Q block
+    for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
+        float2 v = r[base + e];
+        if (!first) {
+            const float2 pv = p[base + e];
+            v.x = fmaf(beta, pv.x, v.x);
+            v.y = fmaf(beta, pv.y, v.y);
+        }
+        p[base + e] = v;
+        pk[e] = v;
+    }
+    for (int c = 0; c < nc; ++c) {
+        __syncthreads();  // pk written / a, b free again
+        for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
+            const int row = row0 + e / N;
+            const float2 cv = coils[((size_t)c * P + row % P) * N + e % N];
+            a[e] = cmul(cv, pk[e]);
+        }
+        __syncthreads();
+        float2* res = fft_smem<N, false, false>(a, b, nr, N, 1, tw);
+        if (c == nc - 1) pdl_trigger();
+        for (int e = threadIdx.x; e < nr * N; e += blockDim.x) t[c * series + base + e] = res[e];
+    }
+}
+
 // Column pass over a P x 8 tile (frame blockIdx.y, columns 8*blockIdx.x ..).
 template <int N, int MODE>
 __global__ void __launch_bounds__(kThreads)
 col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
-           int Q, float scale, const float2* __restrict__ tw_g) {
+           int Q, int mask_frames, float scale, const float2* __restrict__ tw_g) {
     constexpr int C = kColTile;
     extern __shared__ float2 sm[];
     float2* a = sm;
@@ -103,9 +161,12 @@ col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
     pdl_wait();
     const int c0 = blockIdx.x * C;
     const size_t fbase = (size_t)blockIdx.y * N * Q;
+    // coil-major series: frame blockIdx.y is coil blockIdx.y / T of frame blockIdx.y % T
+    const size_t mbase = (size_t)(blockIdx.y % mask_frames) * N * Q;
     for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
         const int i = e / C, c = e % C;
         const size_t g = fbase + (size_t)i * Q + c0 + c;
+        const size_t gm = mbase + (size_t)i * Q + c0 + c;
         float2 v;
         if constexpr (MODE == COL_ADJ_BF16) {
             const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162*>(in_)[g];
@@ -114,7 +175,7 @@ col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
             v = reinterpret_cast<const float2*>(in_)[g];
         }
         if constexpr (MODE == COL_ADJ_C64 || MODE == COL_ADJ_BF16) {
-            v = mask[g] ? cscale(v, scale) : make_float2(0.f, 0.f);
+            v = mask[gm] ? cscale(v, scale) : make_float2(0.f, 0.f);
         }
         a[e] = v;
     }
@@ -128,7 +189,7 @@ col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
         float2* f = fft_smem<N, false, true>(a, b, C, 1, C, tw);
         for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
             const int i = e / C, c = e % C;
-            const uint8_t m = mask[fbase + (size_t)i * Q + c0 + c];
+            const uint8_t m = mask[mbase + (size_t)i * Q + c0 + c];
             f[e] = m ? cscale(f[e], scale) : make_float2(0.f, 0.f);
         }
         __syncthreads();
@@ -206,8 +267,8 @@ row_fwd_pupdate_256_kernel(const float2* __restrict__ r, float2* __restrict__ p,
 // 1/(PQ) scale, inverse DFT, all in registers; two exchanges through shared memory, laid out as
 // c + 8 (17 a + b) so that both the writes and the reads are conflict-free.
 __global__ void __launch_bounds__(128)
-col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, float scale,
-                    const float2* __restrict__ tw_g) {
+col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, int mask_frames,
+                    float scale, const float2* __restrict__ tw_g) {
     __shared__ float2 tw2[256];
     __shared__ float2 buf[8 * 17 * 16];
     fill_tw256(tw2, tw_g);
@@ -215,12 +276,13 @@ col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, float sc
     const int c = threadIdx.x % 8, j = threadIdx.x / 8;
     const int col = blockIdx.x * 8 + c;
     const size_t fbase = (size_t)blockIdx.y * 256 * Q;
+    const size_t mbase = (size_t)(blockIdx.y % mask_frames) * 256 * Q;  // coil-major series
     float2 u[16];
 #pragma unroll
     for (int n1 = 0; n1 < 16; ++n1) u[n1] = t[fbase + (size_t)(16 * n1 + j) * Q + col];
     uint8_t mk[16];
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) mk[k2] = mask[fbase + (size_t)(j + 16 * k2) * Q + col];
+    for (int k2 = 0; k2 < 16; ++k2) mk[k2] = mask[mbase + (size_t)(j + 16 * k2) * Q + col];
     __syncthreads();  // tw2
     dft16<false>(u);
     twiddle256<false>(u, tw2, j);
@@ -280,9 +342,10 @@ cudaError_t row_fft(int n, const float2* in, float2* out, int nrows, float scale
     }
 }
 
+// `T` transforms (frames), the mask of frame f being mask frame f % mask_frames.
 template <int MODE>
-cudaError_t col_pass(int n, int Q, int T, const void* in, float2* out, const uint8_t* mask,
-                     float scale, const float2* tw, cudaStream_t st) {
+cudaError_t col_pass(int n, int Q, int T, int mask_frames, const void* in, float2* out,
+                     const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
     switch (n) {
 #define CASE(N)                                                                          \
     case N: {                                                                            \
@@ -291,7 +354,7 @@ cudaError_t col_pass(int n, int Q, int T, const void* in, float2* out, const uin
         if (e != cudaSuccess) return e;                                                  \
         dim3 grid(Q / kColTile, T);                                                      \
         return launch_pdl(k, grid, dim3(kThreads), col_smem<N>(), st, in, out, mask, Q,  \
-                          scale, tw);                                                    \
+                          mask_frames, scale, tw);                                       \
     }
         RECON_FFT_SIZES(CASE)
 #undef CASE
@@ -316,15 +379,15 @@ cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, floa
     cudaError_t e = inv ? row_fft<true>(d.Q, x, y, d.T * d.P, sq, tw.twQ, st)
                         : row_fft<false>(d.Q, x, y, d.T * d.P, sq, tw.twQ, st);
     if (e != cudaSuccess) return e;
-    return inv ? col_pass<COL_INV>(d.P, d.Q, d.T, y, y, nullptr, sp, tw.twP, st)
-               : col_pass<COL_FWD>(d.P, d.Q, d.T, y, y, nullptr, sp, tw.twP, st);
+    return inv ? col_pass<COL_INV>(d.P, d.Q, d.T, d.T, y, y, nullptr, sp, tw.twP, st)
+               : col_pass<COL_FWD>(d.P, d.Q, d.T, d.T, y, y, nullptr, sp, tw.twP, st);
 }
 
 cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int b_bf16,
                            const uint8_t* mask, float2* t, float2* x, cudaStream_t st) {
     const float sc = 1.0f / sqrtf((float)d.P * (float)d.Q);
-    cudaError_t e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, d.Q, d.T, b, t, mask, sc, tw.twP, st)
-                           : col_pass<COL_ADJ_C64>(d.P, d.Q, d.T, b, t, mask, sc, tw.twP, st);
+    cudaError_t e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st)
+                           : col_pass<COL_ADJ_C64>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st);
     if (e != cudaSuccess) return e;
     return row_fft<true>(d.Q, t, x, d.T * d.P, 1.0f, tw.twQ, st);
 }
@@ -354,13 +417,42 @@ cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const floa
     }
 }
 
+cudaError_t launch_coil_row_fwd(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
+                                float2* t, const float2* coils, const Partials& rr,
+                                const double* rr_prev, double* rr_out, int first, cudaStream_t st) {
+    const int nrows = d.T * d.P;
+    switch (d.Q) {
+#define CASE(N)                                                                              \
+    case N: {                                                                                \
+        auto k = coil_row_fwd_kernel<N>;                                                     \
+        const size_t smem = (size_t)(3 * rows_per_cta<N>() * N + N) * sizeof(float2);       \
+        cudaError_t e = set_smem(k, smem);                                                   \
+        if (e != cudaSuccess) return e;                                                      \
+        const int grid = (nrows + rows_per_cta<N>() - 1) / rows_per_cta<N>();                \
+        return launch_pdl(k, dim3(grid), dim3(kThreads), smem, st, r, p, t, coils, nrows,    \
+                          d.P, d.nc, (const double*)rr.parts, rr.n, rr_prev, rr_out, first,  \
+                          tw.twQ);                                                           \
+    }
+        RECON_FFT_SIZES(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_adjoint_coils_cols(const Dims& d, const Twiddles& tw, const void* b,
+                                      const uint8_t* mask, float2* t, cudaStream_t st) {
+    const float sc = 1.0f / sqrtf((float)d.P * (float)d.Q);
+    return col_pass<COL_ADJ_C64>(d.P, d.Q, d.T * d.nc, d.T, b, t, mask, sc, tw.twP, st);
+}
+
 cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
                             cudaStream_t st) {
     const float sc = 1.0f / ((float)d.P * (float)d.Q);
+    const int frames = d.T * d.nc;  // coil-major: the mask of frame f is mask frame f % T
     if (d.P == 256)
-        return launch_pdl(col_mask_256_kernel, dim3(d.Q / kColTile, d.T), dim3(128), 0, st, t, mask,
-                          d.Q, sc, tw.twP);
-    return col_pass<COL_MASK_OP>(d.P, d.Q, d.T, t, t, mask, sc, tw.twP, st);
+        return launch_pdl(col_mask_256_kernel, dim3(d.Q / kColTile, frames), dim3(128), 0, st, t,
+                          mask, d.Q, d.T, sc, tw.twP);
+    return col_pass<COL_MASK_OP>(d.P, d.Q, frames, d.T, t, t, mask, sc, tw.twP, st);
 }
 
 }  // namespace recon

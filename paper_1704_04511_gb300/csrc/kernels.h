@@ -14,6 +14,7 @@ namespace recon {
 struct Dims {
     int T, P, Q;
     int N1, N2, M;
+    int nc = 1;  // receiver coils (Eq. measurement-ij); the transform buffer holds nc series
     int k() const { return T - M + 1; }
     int npair() const { return M * (M + 1) / 2; }
     int L1() const { return 2 * N1 - 1; }
@@ -98,11 +99,11 @@ cudaError_t launch_cg_update(const Dims& d, float2* x, float2* r, const float2* 
                              Partials* rr, cudaStream_t st);
 // *out = the sum of the partials `in` (one warp).
 cudaError_t launch_sum_partials(const Partials& in, double* out, cudaStream_t st);
-// Residual carry: r = (first ? 0 : r) + lam W_{S_old - S_new} x (S_old ignored when first);
-// *rr_out = |r|^2.
+// Residual carry: r = (first ? r0 : r) + lam W_{S_old - S_new} x (S_old ignored when first),
+// r0 = 0 or, when aha_x = A^H A x is given, x - aha_x; *rr_out = |r|^2.
 cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const float2* S_old,
                                const float2* S_new, float lam, int first, const RedSlot& rs,
-                               double* rr_out, cudaStream_t st);
+                               double* rr_out, cudaStream_t st, const float2* aha_x = nullptr);
 // y = W_S x alone (tests)
 cudaError_t launch_apply_w(const Dims& d, const float2* x, const float2* S, float2* y,
                            cudaStream_t st);
@@ -153,6 +154,27 @@ cudaError_t launch_frame_aha(const Dims& d, const Twiddles& tw, const float2* r,
 // q = t + lam W_S p written over t; partials of Re <p, q> to *pq
 cudaError_t launch_w_combine(const Dims& d, float2* t, const float2* p, const float2* S, float lam,
                              Partials* pq, cudaStream_t st);
+
+// ---- coils (Eq. measurement-ij with receiver sensitivities C_c; d.nc coils, coil-major) ----
+// Pass A: p = r (first) or r + beta p (as launch_row_fwd_pupdate); t[c] = row-FFT(C_c * p).
+cudaError_t launch_coil_row_fwd(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
+                                float2* t, const float2* coils, const Partials& rr,
+                                const double* rr_prev, double* rr_out, int first, cudaStream_t st);
+// Pass C: q = sum_c conj(C_c) row-IFFT(t[c]) + lam W p over coil 0's plane of t; partials of
+// Re <p, q> to *pq.
+cudaError_t launch_coil_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
+                                  const float2* coils, const float2* S, float lam, Partials* pq,
+                                  cudaStream_t st);
+// Adjoint: t[c][n] = column-IFFT(mask_n * b[c][n]) / sqrt(PQ), then
+// x = sum_c conj(C_c) row-IFFT(t[c]).
+cudaError_t launch_adjoint_coils_cols(const Dims& d, const Twiddles& tw, const void* b,
+                                      const uint8_t* mask, float2* t, cudaStream_t st);
+cudaError_t launch_coil_combine(const Dims& d, const Twiddles& tw, float2* t, const float2* coils,
+                                float2* x, cudaStream_t st);
+
+// *dev = max | |C|^2 - 1 | of the first coil map (float bits; zeroed here).
+cudaError_t launch_coil_unimodular(const Dims& d, const float2* coils, unsigned int* dev,
+                                   cudaStream_t st);
 
 // ---- t2fit.cu ----
 constexpr int kT2MaxT = 64;

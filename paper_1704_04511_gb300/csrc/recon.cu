@@ -64,7 +64,8 @@ struct recon_ctx {
     struct GraphKey {
         int T, P, Q, N1, N2, M, irls, cg, bf16, method;
         double lambda, p, gamma, eps0_frac;
-        const void *kspace, *masks, *out;
+        const void *kspace, *masks, *out, *coils;
+        int nc, coil_proj;
         unsigned long ws_gen;
     };
     GraphKey gkey = {};
@@ -298,7 +299,7 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
     if (vectors) {
         GET("r", vec, r, float2*);
         GET("p", vec, p, float2*);
-        GET("t", vec, t, float2*);
+        GET("t", vec * (size_t)d.nc, t, float2*);  // one series per coil
         GET("S0", sbytes, S0, float2*);
         GET("S1", sbytes, S1, float2*);
     }
@@ -408,17 +409,33 @@ int check_status(recon_ctx* c, Work& w, int n_iter) {
 
 // Residual carry + n_cg CG steps on x (in place).
 int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uint8_t* mask,
-             const float2* S_old, const float2* S_new, float lam, float2* x, int first, int n_cg) {
+             const float2* S_old, const float2* S_new, float lam, float2* x, int first, int n_cg,
+             const float2* coils = nullptr, bool coil_proj = false) {
     const recon::RedSlot rs{w.parts, w.counter};
     {
         ProfScope ps(c, RECON_PROF_RESID);
-        RC_CUDA(recon::launch_resid_carry(d, w.r, x, S_old, S_new, lam, first, rs, w.rr, c->stream));
+        const float2* aha_x = nullptr;
+        if (first && coils && !coil_proj) {
+            // with coils A A^H is no projection: the first residual needs A^H A x0 (in coil 0's
+            // plane of t, from the operator passes with lambda = 0). One coil of unit modulus
+            // keeps the projection, and the exact identity avoids the FP32 cancellation.
+            const recon::Partials none{nullptr, 0};
+            recon::Partials scratch{w.rparts, 0};
+            RC_CUDA(recon::launch_coil_row_fwd(d, tw, x, w.p, w.t, coils, none, nullptr, nullptr, 1,
+                                               c->stream));
+            RC_CUDA(recon::launch_col_mask(d, tw, w.t, mask, c->stream));
+            RC_CUDA(recon::launch_coil_row_inv_w(d, tw, w.t, w.p, coils, S_new, 0.f, &scratch,
+                                                 c->stream));
+            aha_x = w.t;
+        }
+        RC_CUDA(recon::launch_resid_carry(d, w.r, x, S_old, S_new, lam, first, rs, w.rr, c->stream,
+                                          aha_x));
     }
     // Dot products travel as per-CTA partials: pass C leaves those of Re <p, q> in w.parts for
     // the update pass; the update pass leaves those of |r|^2 in w.rparts for the next pass A,
     // which also stores the sum in rr[it] (rr[0] comes from the residual carry).
     recon::Partials pq{w.parts, 0}, rr{w.rparts, 0};
-    const bool fused = c->cluster_fft && recon::frame_op_supported(d);
+    const bool fused = c->cluster_fft && recon::frame_op_supported(d) && !coils;
     for (int it = 0; it < n_cg; ++it) {
         const double* rr_prev = it > 0 ? w.rr + it - 1 : w.rr;
         if (fused) {
@@ -432,15 +449,23 @@ int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uin
         } else {
             {
                 ProfScope ps(c, RECON_PROF_CG_ROWFWD);
-                RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, rr, rr_prev, w.rr + it,
-                                                      it == 0, c->stream));
+                if (coils)
+                    RC_CUDA(recon::launch_coil_row_fwd(d, tw, w.r, w.p, w.t, coils, rr, rr_prev,
+                                                       w.rr + it, it == 0, c->stream));
+                else
+                    RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, rr, rr_prev,
+                                                          w.rr + it, it == 0, c->stream));
             }
             {
                 ProfScope ps(c, RECON_PROF_CG_COL);
                 RC_CUDA(recon::launch_col_mask(d, tw, w.t, mask, c->stream));
             }
             ProfScope ps(c, RECON_PROF_CG_ROWINVW);
-            RC_CUDA(recon::launch_row_inv_w(d, tw, w.t, w.p, S_new, lam, &pq, c->stream));
+            if (coils)
+                RC_CUDA(recon::launch_coil_row_inv_w(d, tw, w.t, w.p, coils, S_new, lam, &pq,
+                                                     c->stream));
+            else
+                RC_CUDA(recon::launch_row_inv_w(d, tw, w.t, w.p, S_new, lam, &pq, c->stream));
         }
         ProfScope ps(c, RECON_PROF_CG_UPDATE);
         RC_CUDA(recon::launch_cg_update(d, x, w.r, w.p, w.t, w.rr + it, pq, &rr, c->stream));
@@ -524,6 +549,8 @@ struct Solve {
     const void* kspace;
     const uint8_t* masks;
     const recon_params* prm;
+    const float2* coils = nullptr;  // [nc][P][Q] for the multi-coil operator
+    bool coil_proj = false;         // one coil with |C| = 1: A A^H is a projection
 };
 
 // Twiddles, eigensolver handle and workspace of one solve on the active slot (no stream work).
@@ -549,6 +576,12 @@ int solve_begin(recon_ctx* c, Solve* sv) {
     int rc = reset_status(c, sv->w);
     if (rc) return rc;
     ProfScope ps(c, RECON_PROF_ADJOINT);
+    if (sv->coils) {
+        RC_CUDA(recon::launch_adjoint_coils_cols(sv->d, sv->tw, sv->kspace, sv->masks, sv->w.t,
+                                                 c->stream));
+        RC_CUDA(recon::launch_coil_combine(sv->d, sv->tw, sv->w.t, sv->coils, sv->x, c->stream));
+        return RECON_OK;
+    }
     RC_CUDA(recon::launch_adjoint(sv->d, sv->tw, sv->kspace, sv->prm->kspace_bf16, sv->masks,
                                   sv->w.t, sv->x, c->stream));
     return RECON_OK;
@@ -569,7 +602,7 @@ int solve_iter(recon_ctx* c, Solve& sv, int n) {
                          0.0, S_new, n);
     if (rc) return rc;
     return cg_block(c, d, sv.tw, w, sv.masks, S_old, S_new, (float)sv.prm->lambda, sv.x, n == 0,
-                    sv.prm->cg);
+                    sv.prm->cg, sv.coils, sv.coil_proj);
 }
 
 // Enqueue a whole solve on the active slot's stream: as one replay of a captured CUDA graph
@@ -590,6 +623,7 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     k.irls = prm->irls; k.cg = prm->cg; k.bf16 = prm->kspace_bf16; k.method = prm->weight_method;
     k.lambda = prm->lambda; k.p = prm->p; k.gamma = prm->gamma; k.eps0_frac = prm->eps0_frac;
     k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
+    k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
     if (!c->gexec || std::memcmp(&k, &c->gkey, sizeof(k)) != 0) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -773,6 +807,106 @@ int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* 
     if (rc) return rc;
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return solve_check(c, sv);
+}
+
+int recon_solve_coils(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* masks,
+                      const void* coils, int n_coils, recon_filter f, const recon_params* prm,
+                      void* image_out) {
+    if (!c) return RECON_EINVAL;
+    if (!kspace || !masks || !coils || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (n_coils < 1 || n_coils > RECON_MAX_COILS)
+        return fail(c, RECON_EINVAL, "need 1 <= n_coils <= RECON_MAX_COILS");
+    if (prm->kspace_bf16) return fail(c, RECON_EINVAL, "multi-coil k-space must be complex64");
+    Dims d;
+    int rc = check_params(c, dd, f, prm, &d);
+    if (rc) return rc;
+    d.nc = n_coils;
+    rc = set_device(c);
+    if (rc) return rc;
+    rc = select_slot(c, 0);
+    if (rc) return rc;
+    Solve sv;
+    rc = solve_prepare(c, d, kspace, masks, prm, image_out, &sv);
+    if (rc) return rc;
+    sv.coils = reinterpret_cast<const float2*>(coils);
+    if (n_coils == 1) {  // unit modulus (to FP32 rounding) keeps A A^H a projection
+        void* dev = nullptr;
+        rc = ensure(c, "coildev", 256, &dev);
+        if (rc) return rc;
+        RC_CUDA(recon::launch_coil_unimodular(d, sv.coils, (unsigned int*)dev, c->stream));
+        unsigned int bits = 0;
+        RC_CUDA(cudaMemcpyAsync(&bits, dev, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+        RC_CUDA(cudaStreamSynchronize(c->stream));
+        float m;
+        std::memcpy(&m, &bits, sizeof(m));
+        sv.coil_proj = m <= 1e-6f;
+    }
+    rc = solve_enqueue_all(c, sv);
+    if (rc) return rc;
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return solve_check(c, sv);
+}
+
+int recon_adjoint_coils(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* masks,
+                        const void* coils, int n_coils, void* x_out) {
+    if (!c) return RECON_EINVAL;
+    if (!kspace || !masks || !coils || !x_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (n_coils < 1 || n_coils > RECON_MAX_COILS)
+        return fail(c, RECON_EINVAL, "need 1 <= n_coils <= RECON_MAX_COILS");
+    Dims d;
+    int rc = check_dims(c, dd, nullptr, &d);
+    if (rc) return rc;
+    d.nc = n_coils;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    void* t;
+    rc = ensure(c, "t", d.elems() * (size_t)d.nc * sizeof(float2), &t);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_adjoint_coils_cols(d, tw, kspace, masks, (float2*)t, c->stream));
+    RC_CUDA(recon::launch_coil_combine(d, tw, (float2*)t, (const float2*)coils, (float2*)x_out,
+                                       c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int recon_apply_normal_coils(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks,
+                             const void* coils, int n_coils, const void* S, double lambda,
+                             const void* x, void* y) {
+    if (!c) return RECON_EINVAL;
+    if (!masks || !coils || !S || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
+    if (n_coils < 1 || n_coils > RECON_MAX_COILS)
+        return fail(c, RECON_EINVAL, "need 1 <= n_coils <= RECON_MAX_COILS");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    d.nc = n_coils;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    void *pp, *t, *parts;
+    rc = ensure(c, "p", d.elems() * sizeof(float2), &pp);
+    if (rc) return rc;
+    rc = ensure(c, "t", d.elems() * (size_t)d.nc * sizeof(float2), &t);
+    if (rc) return rc;
+    rc = ensure(c, "parts", (size_t)recon::max_parts() * sizeof(double), &parts);
+    if (rc) return rc;
+    recon::Partials pq{(double*)parts, 0};
+    const recon::Partials none{nullptr, 0};
+    // the coil passes with first = 1 (p = x); q lands in coil 0's plane of t
+    RC_CUDA(recon::launch_coil_row_fwd(d, tw, (const float2*)x, (float2*)pp, (float2*)t,
+                                       (const float2*)coils, none, nullptr, nullptr, 1, c->stream));
+    RC_CUDA(recon::launch_col_mask(d, tw, (float2*)t, masks, c->stream));
+    RC_CUDA(recon::launch_coil_row_inv_w(d, tw, (float2*)t, (const float2*)pp, (const float2*)coils,
+                                         (const float2*)S, (float)lambda, &pq, c->stream));
+    RC_CUDA(cudaMemcpyAsync(y, t, d.elems() * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
 }
 
 int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* kspace,

@@ -38,7 +38,8 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
             "recon_profile_read", "recon_profile_name", "recon_gram_static",
-            "recon_solve_batch", "recon_set_option", "recon_submit", "recon_poll", "recon_t2fit")
+            "recon_solve_batch", "recon_set_option", "recon_submit", "recon_poll", "recon_t2fit",
+            "recon_solve_coils", "recon_adjoint_coils", "recon_apply_normal_coils")
 
 PROF_KINDS = 15
 
@@ -102,6 +103,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(i)]),
             "recon_poll": (i, [vp, i, ctypes.POINTER(i)]),
             "recon_t2fit": (i, [vp, dims, vp, ctypes.POINTER(d), d, i, vp, vp]),
+            "recon_solve_coils": (i, [vp, dims, vp, vp, vp, i, filt, ctypes.POINTER(recon_params),
+                                      vp]),
+            "recon_adjoint_coils": (i, [vp, dims, vp, vp, vp, i, vp]),
+            "recon_apply_normal_coils": (i, [vp, dims, filt, vp, vp, i, vp, d, vp, vp]),
             "recon_solve_batch": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp), filt,
                                       ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
         }
@@ -178,6 +183,29 @@ def recon_solve(ctx, kspace, masks, filt, lam: float, p: float, irls: int, cg: i
                        weight_method=int(weight_method))
     _check(ctx, load_library().recon_solve(ctx, _dims(masks), _ptr(kspace), _ptr(masks),
                                            _filt(filt), ctypes.byref(prm), _ptr(image_out)))
+
+
+def recon_solve_coils(ctx, kspace, masks, coils, filt, lam: float, p: float, irls: int, cg: int,
+                      image_out, gamma: float = 1.4, eps0_frac: float = 0.01,
+                      weight_method: int = RECON_WEIGHT_AUTO) -> None:
+    """Multi-coil solve: kspace [Nc, T, P, Q] complex64, coils [Nc, P, Q] complex64."""
+    prm = recon_params(irls=int(irls), cg=int(cg), lambda_=float(lam), p=float(p),
+                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=0,
+                       weight_method=int(weight_method))
+    _check(ctx, load_library().recon_solve_coils(ctx, _dims(masks), _ptr(kspace), _ptr(masks),
+                                                 _ptr(coils), int(coils.shape[0]), _filt(filt),
+                                                 ctypes.byref(prm), _ptr(image_out)))
+
+
+def recon_adjoint_coils(ctx, kspace, masks, coils, x_out) -> None:
+    _check(ctx, load_library().recon_adjoint_coils(ctx, _dims(masks), _ptr(kspace), _ptr(masks),
+                                                   _ptr(coils), int(coils.shape[0]), _ptr(x_out)))
+
+
+def recon_apply_normal_coils(ctx, masks, coils, filt, S, lam: float, x, y) -> None:
+    _check(ctx, load_library().recon_apply_normal_coils(ctx, _dims(x), _filt(filt), _ptr(masks),
+                                                        _ptr(coils), int(coils.shape[0]), _ptr(S),
+                                                        float(lam), _ptr(x), _ptr(y)))
 
 
 def recon_solve_batch(ctx, kspaces, masks_list, filt, lam: float, p: float, irls: int, cg: int,
