@@ -27,6 +27,7 @@ sys.path.insert(0, ROOT)
 METRIC = "IRLS iterations/s, 256x256x16 series, 9x9x3 filter, 15 CG steps per iteration"
 UNIT = "IRLS iter/s"
 WORKLOAD = "perf_256x256x16"
+COIL_WORKLOAD = "coils_128x128x12"
 
 # kernels launched per profiled scope (eig is the cuSOLVER library call and is not counted;
 # diag_sums is one kernel on the p = 0 path, two after the eigendecomposition)
@@ -193,6 +194,46 @@ def cpu_oracle_rate(w, prob, budget_s: float = 12.0, max_iters: int = 6):
     return n / dt, n, dt, cores
 
 
+def run_coils(steps: int, device: int) -> dict:
+    """The multi-coil workload (128x128x12, 12 coils): whole solves, device-resident inputs,
+    timed with CUDA events."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1704_04511_gb300 import recon
+    w = synth.workload(COIL_WORKLOAD)
+    prob = synth.make_problem(w)
+    dev = torch.device("cuda", device)
+    b = torch.from_numpy(prob["kspace"].astype(np.complex64)).to(dev)
+    m = torch.from_numpy(prob["masks"]).to(dev)
+    C = torch.from_numpy(prob["coils"].astype(np.complex64)).to(dev)
+    out = torch.empty(tuple(m.shape), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = recon.Context(device, cuda_stream=stream.cuda_stream)
+    try:
+        def solve():
+            recon.recon_solve_coils(ctx.h, b, m, C, (w.N1, w.N2, w.M), w.lam, w.p, w.n_irls,
+                                    w.n_cg, out)
+        for _ in range(2):
+            solve()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    finally:
+        ctx.close()
+    return {"workload": COIL_WORKLOAD, "n_coils": w.n_coils, "irls": w.n_irls, "cg": w.n_cg,
+            "filter": [w.N1, w.N2, w.M], "ms_per_solve": round(ms, 3),
+            "irls_iters_per_s": round(1000.0 * w.n_irls / ms, 1),
+            "note": "recon_solve_coils on device-resident k-space (12 coil series), one solve at "
+                    "a time; the k-space of every coil stays in HBM/L2 between steps"}
+
+
 def run_served(n_requests: int, device: int) -> dict:
     """Continuous batching over the served mix: n requests, Poisson arrivals at 20/s, sizes
     {64, 128, 192, 256}^2, 8-24 frames, filters 5-9 x 2-3, 30 IRLS x 15 CG each."""
@@ -262,6 +303,8 @@ def main():
     ap.add_argument("--irls", type=int, default=None, help="override IRLS iterations (testing)")
     ap.add_argument("--batch", type=int, default=4,
                     help="independent problems solved concurrently per step (1 = single solve)")
+    ap.add_argument("--coil-steps", type=int, default=3,
+                    help="solves of the 12-coil 128x128x12 workload to time (0 = skip)")
     ap.add_argument("--served", type=int, default=48,
                     help="requests of the served mix (Poisson 20/s, mixed sizes) to serve after "
                          "the timed steps, reported as p50/p99 latency; 0 = skip, 512 = full mix")
@@ -480,6 +523,8 @@ def main():
     }
     if args.served > 0:
         line["served"] = run_served(args.served, local_rank)
+    if args.coil_steps > 0:
+        line["coils"] = run_coils(args.coil_steps, local_rank)
     if not args.no_cpu_baseline:
         rate, n, dt, cores = cpu_oracle_rate(w, prob)
         line["cpu_baseline"] = {
