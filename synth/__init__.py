@@ -17,4 +17,6 @@ from .phantom import (  # noqa: F401
     vd_mask,
     served_mix,
     coil_maps,
+    make_problem3,
+    vd_mask3,
 )

@@ -47,6 +47,8 @@ class Workload:
     snr_db: float = 30.0
     seed: int = 0
     n_coils: int = 1           # receiver coils (Eq. measurement-ij); 1 = single channel
+    depth: int = 1             # slices of a 3-D volume (1 = 2-D images)
+    N3: int = 1                # filter taps along the depth
 
     @property
     def shape(self):
@@ -84,7 +86,17 @@ def _coils():
         R=6.0, N1=9, N2=9, M=3, lam=0.1, p=0.0, n_irls=20, n_cg=10, n_coils=12)
 
 
-WORKLOADS = {w.name: w for w in (_tiny(), _perf(), _coils())}
+def _vol():
+    # 3-D volumes: 128 x 128 x 64 slices, 12 frames, one exponential, 6x 3-D variable-density
+    # sampling, filter 7 x 7 x 3 spatial taps x 2 frame taps (s = 294)
+    return Workload(
+        name="vol_128x128x64x12", P=128, Q=128, T=12, depth=64, N3=3,
+        times_ms=tuple(10.0 * (n + 1) for n in range(12)),
+        n_ellipses=12, t2_ranges=((20.0, 120.0),), frac_range=(1.0, 1.0),
+        R=6.0, N1=7, N2=7, M=2, lam=1e-3, p=0.0, n_irls=25, n_cg=15)
+
+
+WORKLOADS = {w.name: w for w in (_tiny(), _perf(), _coils(), _vol())}
 
 
 def workload(name: str, **overrides) -> Workload:
@@ -192,13 +204,101 @@ def coil_maps(n_coils: int, P: int, Q: int, rng: np.random.Generator) -> np.ndar
     return C / np.sqrt((np.abs(C) ** 2).sum(0))[None]
 
 
+def ellipsoid_phantom(D: int, P: int, Q: int, n: int, rng: np.random.Generator) -> np.ndarray:
+    """Additive sum of n random filled ellipsoids (centres in the central 60 % of each axis,
+    semi-axes 3-12 px scaled with the grid per axis, a random rotation about the depth axis,
+    intensity U[0.2, 1]); shape (D, P, Q)."""
+    sp, sd = min(P, Q) / 32.0, D / 32.0
+    zz, yy, xx = np.meshgrid(np.arange(D, dtype=np.float64), np.arange(P, dtype=np.float64),
+                             np.arange(Q, dtype=np.float64), indexing="ij")
+    vol = np.zeros((D, P, Q), dtype=np.float64)
+    for _ in range(n):
+        cz = rng.uniform(0.2 * D, 0.8 * D)
+        cy = rng.uniform(0.2 * P, 0.8 * P)
+        cx = rng.uniform(0.2 * Q, 0.8 * Q)
+        a = rng.uniform(3.0, 12.0) * sp
+        b = rng.uniform(3.0, 12.0) * sp
+        c = rng.uniform(3.0, 12.0) * sd
+        th = rng.uniform(0.0, math.pi)
+        amp = rng.uniform(0.2, 1.0)
+        dz, dy, dx = zz - cz, yy - cy, xx - cx
+        u = (dx * math.cos(th) + dy * math.sin(th)) / a
+        v = (-dx * math.sin(th) + dy * math.cos(th)) / b
+        wv = dz / c
+        vol += amp * ((u * u + v * v + wv * wv) <= 1.0)
+    return vol
+
+
+def smooth_field3(D: int, P: int, Q: int, sigma: float, sigma_d: float, lo: float, hi: float,
+                  rng: np.random.Generator) -> np.ndarray:
+    """White N(0,1) noise blurred by a periodic Gaussian (sigma px in-plane, sigma_d px in
+    depth), min-max mapped onto [lo, hi]; shape (D, P, Q)."""
+    w = rng.standard_normal((D, P, Q))
+    f0 = np.fft.fftfreq(D)[:, None, None]
+    f1 = np.fft.fftfreq(P)[None, :, None]
+    f2 = np.fft.fftfreq(Q)[None, None, :]
+    g = np.exp(-2.0 * math.pi ** 2 * (sigma_d ** 2 * f0 * f0 + sigma ** 2 * (f1 * f1 + f2 * f2)))
+    s = np.real(np.fft.ifftn(np.fft.fftn(w) * g))
+    s = (s - s.min()) / max(s.max() - s.min(), 1e-300)
+    return lo + (hi - lo) * s
+
+
+def vd_mask3(D: int, P: int, Q: int, R: float, rng: np.random.Generator) -> np.ndarray:
+    """3-D variable-density Cartesian mask with exactly D*P*Q/R samples: a c x c x cd block around
+    DC fully sampled (c = max(4, P//32), cd = max(2, D//32)), the rest drawn without replacement
+    with probability proportional to 1 / (1 + (|k| / (P/8))^2), |k| the centred frequency radius
+    with the depth frequencies scaled by P / D."""
+    n_target = int(round(D * P * Q / R))
+    k0 = np.fft.fftfreq(D) * D
+    k1 = np.fft.fftfreq(P) * P
+    k2 = np.fft.fftfreq(Q) * Q
+    K0, K1, K2 = np.meshgrid(k0, k1, k2, indexing="ij")
+    c, cd = max(4, P // 32), max(2, D // 32)
+    centre = ((K1 >= -c // 2) & (K1 < c - c // 2) & (K2 >= -c // 2) & (K2 < c - c // 2) &
+              (K0 >= -cd // 2) & (K0 < cd - cd // 2))
+    mask = centre.copy()
+    need = n_target - int(mask.sum())
+    if need > 0:
+        rad = np.sqrt(K1 * K1 + K2 * K2 + (K0 * P / D) ** 2)
+        wgt = 1.0 / (1.0 + (rad / (P / 8.0)) ** 2)
+        wgt[mask] = 0.0
+        flat = wgt.ravel() / wgt.sum()
+        pick = rng.choice(D * P * Q, size=need, replace=False, p=flat)
+        mask.ravel()[pick] = True
+    return mask.astype(np.uint8)
+
+
+def make_problem3(w: Workload) -> dict:
+    """Seeded 3-D problem: x_true (T, D, P, Q) complex128 = rho exp(-t / T2) on random ellipsoids
+    with a T2 field smooth in 3-D (sigma 3 P / 32 px in-plane, 3 D / 32 px in depth); masks
+    (T, D, P, Q) uint8 (seed S + 10 + n); kspace = mask * (F3 x_true + eta) at w.snr_db
+    (noise seed S + 99), F3 the unitary 3-D DFT."""
+    S, D = w.seed, w.depth
+    rho = ellipsoid_phantom(D, w.P, w.Q, w.n_ellipses, np.random.default_rng(S + 1))
+    lo, hi = w.t2_ranges[0]
+    t2 = smooth_field3(D, w.P, w.Q, 3.0 * w.P / 32.0, 3.0 * D / 32.0, lo, hi,
+                       np.random.default_rng(S + 2))
+    t = np.asarray(w.times_ms, dtype=np.float64)[:, None, None, None]
+    x = (rho[None] * np.exp(-t / t2[None])).astype(np.complex128)
+    masks = np.stack([vd_mask3(D, w.P, w.Q, w.R, np.random.default_rng(S + 10 + n))
+                      for n in range(w.T)])
+    clean = masks * np.fft.fftn(x, axes=(1, 2, 3), norm="ortho")
+    rng = np.random.default_rng(S + 99)
+    eta = (rng.standard_normal(clean.shape) + 1j * rng.standard_normal(clean.shape)) * masks
+    scale = np.linalg.norm(clean) * 10.0 ** (-w.snr_db / 20.0) / max(np.linalg.norm(eta), 1e-300)
+    return {"x_true": x, "masks": masks, "kspace": clean + scale * eta, "workload": w}
+
+
 def make_problem(w: Workload) -> dict:
     """Seeded problem: x_true (T,P,Q) complex128, masks (T,P,Q) uint8, kspace (T,P,Q) complex128.
 
     kspace = mask * (F x_true + eta); eta is complex Gaussian on the sampled entries, scaled so
     that 20 log10(||mask * F x_true|| / ||eta||) equals w.snr_db exactly. With w.n_coils > 1 the
     k-space is coil-major (Nc, T, P, Q), kspace[c, n] = mask_n * (F (C_c x_n) + eta), and the
-    sensitivities (Nc, P, Q) are returned as "coils" (seed S + 20)."""
+    sensitivities (Nc, P, Q) are returned as "coils" (seed S + 20). Volumes (w.depth > 1) come
+    from make_problem3."""
+    if w.depth > 1:
+        return make_problem3(w)
     S = w.seed
     x = make_series(w)
     masks = np.stack([vd_mask(w.P, w.Q, w.R, np.random.default_rng(S + 10 + n))
