@@ -28,6 +28,7 @@ METRIC = "IRLS iterations/s, 256x256x16 series, 9x9x3 filter, 15 CG steps per it
 UNIT = "IRLS iter/s"
 WORKLOAD = "perf_256x256x16"
 COIL_WORKLOAD = "coils_128x128x12"
+VOL_WORKLOAD = "vol_128x128x64x12"
 
 # kernels launched per profiled scope (eig is the cuSOLVER library call and is not counted;
 # diag_sums is one kernel on the p = 0 path, two after the eigendecomposition)
@@ -38,9 +39,12 @@ KERNELS_PER_SCOPE = {"adjoint": 2, "gram": 2, "eps": 1, "diag_sums": 1, "weight_
 
 
 def alg_bytes(kind: str, w, n_cg: int) -> float:
-    """Algorithmic bytes per launch (complex64 elements E = T*P*Q, pixels N = P*Q)."""
-    E = w.T * w.P * w.Q
-    N = w.P * w.Q
+    """Algorithmic bytes per launch (complex64 elements E = T*P*Q, pixels N = P*Q; volumes:
+    E = T*D*P*Q, N = D*P*Q). For volumes the column class holds three launches (column DFT,
+    masked depth pass, column IDFT); its algorithmic bytes stay those of the operation."""
+    D = getattr(w, "depth", 1)
+    E = w.T * w.P * w.Q * D
+    N = w.P * w.Q * D
     npair = w.M * (w.M + 1) // 2
     if kind == "cg_row_fwd":      # read r (+ p), write p and t
         return (24.0 * E + 32.0 * E * (n_cg - 1)) / n_cg
@@ -234,6 +238,75 @@ def run_coils(steps: int, device: int) -> dict:
                     "a time; the k-space of every coil stays in HBM/L2 between steps"}
 
 
+def run_vol(steps: int, device: int) -> dict:
+    """The volume workload (128x128x64 voxels x 12 frames, 7x7x3x2 filter, 25 IRLS x 15 CG):
+    whole solves through recon_solve3 on device-resident k-space (working set ~0.6 GB, beyond
+    L2, so every CG pass streams from HBM), one profiled solve for the per-class device times."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1704_04511_gb300 import recon
+    w = synth.workload(VOL_WORKLOAD)
+    prob = synth.make_problem(w)
+    dev = torch.device("cuda", device)
+    b = torch.from_numpy(prob["kspace"].astype(np.complex64)).to(dev)
+    m = torch.from_numpy(prob["masks"]).to(dev)
+    out = torch.empty(tuple(m.shape), dtype=torch.complex64, device=dev)
+    filt = (w.N1, w.N2, w.N3, w.M)
+    stream = torch.cuda.current_stream(dev)
+    ctx = recon.Context(device, cuda_stream=stream.cuda_stream)
+    try:
+        def solve():
+            recon.recon_solve3(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+        solve()
+        torch.cuda.synchronize(dev)
+        recon.recon_profile(ctx.h, recon.PROF_ALL)
+        solve()
+        torch.cuda.synchronize(dev)
+        prof = {recon.recon_profile_name(k): recon.recon_profile_read(ctx.h, k)
+                for k in range(recon.PROF_KINDS)}
+        recon.recon_profile(ctx.h, 0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        need = recon.recon_bytes_needed3(tuple(m.shape), filt)
+    finally:
+        ctx.close()
+    peak, peak_src = load_peaks()
+    tot = sum(v[0] for v in prof.values())
+    classes = {}
+    for k, (ms_k, n_k) in prof.items():
+        if not n_k:
+            continue
+        ent = {"ms_per_solve": round(ms_k, 3), "launches": n_k,
+               "share": round(ms_k / tot, 4) if tot else None,
+               "avg_launch_us": round(1000.0 * ms_k / n_k, 2)}
+        ab = alg_bytes(k, w, w.n_cg)
+        if ab:
+            gbs = ab / (ms_k / n_k / 1000.0) / 1e9
+            ent.update({"alg_bytes_per_launch": ab, "achieved_GBs": round(gbs, 1),
+                        "frac_of_hbm": round(gbs / peak, 4)})
+        classes[k] = ent
+    T, D, P, Q = m.shape
+    s = w.N1 * w.N2 * w.N3 * w.M
+    rows_lifted = (w.T - w.M + 1) * D * P * Q
+    return {"workload": VOL_WORKLOAD, "T": T, "D": D, "P": P, "Q": Q, "filter": list(filt),
+            "irls": w.n_irls, "cg": w.n_cg, "ms_per_solve": round(ms, 2),
+            "irls_iters_per_s": round(1000.0 * w.n_irls / ms, 2),
+            "voxel_frame_cg_steps_per_s": round(T * D * P * Q * w.n_irls * w.n_cg / (ms / 1000.0), 1),
+            "hbm_peak_GBs": peak, "hbm_peak_source": peak_src, "classes": classes,
+            "footprint": {"workspace_bytes": int(need),
+                          "lifted_matrix_bytes_complex64": int(rows_lifted * s * 8),
+                          "gram_bytes_complex128": int(s * s * 16)},
+            "note": "recon_solve3, device-resident k-space, solves back to back (CUDA events); "
+                    "per-class times from one profiled solve before the timed ones"}
+
+
 def run_served(n_requests: int, device: int) -> dict:
     """Continuous batching over the served mix: n requests, Poisson arrivals at 20/s, sizes
     {64, 128, 192, 256}^2, 8-24 frames, filters 5-9 x 2-3, 30 IRLS x 15 CG each."""
@@ -305,6 +378,8 @@ def main():
                     help="independent problems solved concurrently per step (1 = single solve)")
     ap.add_argument("--coil-steps", type=int, default=3,
                     help="solves of the 12-coil 128x128x12 workload to time (0 = skip)")
+    ap.add_argument("--vol-steps", type=int, default=2,
+                    help="solves of the 128x128x64x12 volume workload to time (0 = skip)")
     ap.add_argument("--served", type=int, default=48,
                     help="requests of the served mix (Poisson 20/s, mixed sizes) to serve after "
                          "the timed steps, reported as p50/p99 latency; 0 = skip, 512 = full mix")
@@ -525,6 +600,8 @@ def main():
         line["served"] = run_served(args.served, local_rank)
     if args.coil_steps > 0:
         line["coils"] = run_coils(args.coil_steps, local_rank)
+    if args.vol_steps > 0:
+        line["vol"] = run_vol(args.vol_steps, local_rank)
     if not args.no_cpu_baseline:
         rate, n, dt, cores = cpu_oracle_rate(w, prob)
         line["cpu_baseline"] = {

@@ -251,6 +251,50 @@ int recon_apply_normal_coils(recon_ctx* c, recon_dims d, recon_filter f, const u
 int recon_t2fit(recon_ctx* c, recon_dims d, const void* x, const double* times_ms, double fg_frac,
                 int n_gn, float* t2_out, float* amp_out);
 
+/* ---- image volumes ----
+ * The method on series of 3-D volumes: the signal model of Sec. II-B holds per voxel, and the
+ * lifting of Sec. III-A gains a third spatial axis, circular like the other two. The paper
+ * builds the lifting for P x Q frames (a 3-D k-t dataset, Sec. II-C) and motivates its FFT
+ * approximations by larger multidimensional problems (Sec. I); these calls carry the same
+ * formulas along one more spatial axis. Conventions as above, except:
+ *  - series, k-space and masks are [T][R][P][Q] (Q fastest): T volumes of R slices of P x Q;
+ *  - F is the unitary 3-D DFT of each volume (sign e^{-2 pi i}, natural order); A = mask * F;
+ *  - the filter has N1 x N2 x N3 spatial taps (rows, columns, depth) x M frame taps,
+ *    s = N1 N2 N3 M, column index ((m N3 + l3) N1 + l1) N2 + l2;
+ *  - lags and summed diagonals are npair x (2N3-1) x (2N1-1) x (2N2-1) complex128 (lag (d3, d1,
+ *    d2) at offset (N3-1, N1-1, N2-1)), with the extra factor e^{-2 pi i d3 r3 / R};
+ *  - S is npair x R x P x Q complex64;
+ *  - R = 1 or R in {16, 32, 64, 128, 192, 256, 512}; 1 <= N3 <= R. With R = N3 = 1 every call
+ *    computes what its 2-D counterpart does.
+ * Single coil; no batched or serving form. */
+typedef struct {
+    int P, Q, R, T; /* volume R x P x Q (Q fastest), T frames */
+} recon_dims3;
+
+typedef struct {
+    int N1, N2, N3, M; /* N1 x N2 x N3 spatial taps (rows, columns, depth), M frame taps */
+} recon_filter3;
+
+size_t recon_bytes_needed3(recon_dims3 d, recon_filter3 f, int kspace_bf16);
+/* Algorithm 1 on volumes (as recon_solve). */
+int recon_solve3(recon_ctx* c, recon_dims3 d, const void* kspace, const uint8_t* masks,
+                 recon_filter3 f, const recon_params* prm, void* image_out);
+/* x = A^H b = F^H (mask * b), 3-D. */
+int recon_adjoint3(recon_ctx* c, recon_dims3 d, const void* kspace, int kspace_bf16,
+                   const uint8_t* masks, void* x_out);
+/* y = F x or F^H x (unitary 3-D DFT per volume); y may equal x. */
+int recon_fft3(recon_ctx* c, recon_dims3 d, const void* x, void* y, int inverse);
+/* Gram matrix and lags of the 3-D lifting (as recon_gram). */
+int recon_gram3(recon_ctx* c, recon_dims3 d, recon_filter3 f, const void* x, void* G_out,
+                void* lags_out);
+/* Weight step (as recon_weight), S_out npair x R x P x Q. */
+int recon_weight3(recon_ctx* c, recon_dims3 d, recon_filter3 f, const void* G_in, double eps_in,
+                  double p, int method, void* S_out, void* dsum_out, void* evals_out,
+                  double* eps_out);
+/* y = (A^H A + lambda W_S) x on volumes (W_S per voxel, as recon_apply_normal). */
+int recon_apply_normal3(recon_ctx* c, recon_dims3 d, recon_filter3 f, const uint8_t* masks,
+                        const void* S, double lambda, const void* x, void* y);
+
 /* ---- measurement ---- */
 
 /* Launch classes timed by recon_profile (one pair of CUDA events on the context's stream around

@@ -51,10 +51,13 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     float2* b = a + (size_t)T * N;
     float2* pt = b + (size_t)T * N;
     float2* tw = pt + (size_t)T * N;
-    const int r1 = blockIdx.x;
     const size_t npix = (size_t)P * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
     pdl_wait();
+    const int k = T - M + 1;
+    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
+    for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
+    __syncthreads();  // the previous row's results are stored
     for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
         const int n = e / N, c = e % N;
         const size_t g = (size_t)n * npix + (size_t)r1 * N + c;
@@ -63,8 +66,6 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     }
     __syncthreads();
     float2* res = fft_smem<N, true, false>(a, b, T, N, 1, tw);
-    const int k = T - M + 1;
-    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         float2 s[M][M];
         load_S<M>(S, npix, (size_t)r1 * N + c, s);
@@ -88,12 +89,14 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
             acc = sum;
         }
     }
-    const double tot = block_sum_f_t0(acc, red);
-    pdl_trigger();
+    __syncthreads();  // every column of q written
+    if (r1 + (int)gridDim.x >= P) pdl_trigger();
     for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
         const int n = e / N, c = e % N;
         t[(size_t)n * npix + (size_t)r1 * N + c] = res[e];
     }
+    }
+    const double tot = block_sum_f_t0(acc, red);
     if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
@@ -116,8 +119,11 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
     pdl_wait();
     const int n = threadIdx.x / 16, j = threadIdx.x % 16;
     const bool live = n < T;  // the block is padded to whole warps (an odd T leaves a half-warp)
-    const int r1 = blockIdx.x;
     const size_t npix = (size_t)P * N;
+    const int k = T - M + 1;
+    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
+    for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
+    __syncthreads();  // the previous row's results are stored
     const size_t g0 = (size_t)n * npix + (size_t)r1 * N + j;
     float2 u[16];
 #pragma unroll
@@ -136,8 +142,6 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
         for (int k2 = 0; k2 < 16; ++k2) res[n * N + j + 16 * k2] = u[k2];
     }
     __syncthreads();
-    const int k = T - M + 1;
-    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         float2 s[M][M];
         load_S<M>(S, npix, (size_t)r1 * N + c, s);
@@ -161,12 +165,14 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
             acc = sum;
         }
     }
-    const double tot = block_sum_f_t0(acc, red);
-    pdl_trigger();
+    __syncthreads();  // every column of q written
+    if (r1 + (int)gridDim.x >= P) pdl_trigger();
     for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
         const int nn = e / N, c = e % N;
         t[(size_t)nn * npix + (size_t)r1 * N + c] = res[e];
     }
+    }
+    const double tot = block_sum_f_t0(acc, red);
     if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
@@ -412,10 +418,24 @@ apply_w_kernel(const float2* __restrict__ x, const float2* __restrict__ S, float
     }
 }
 
+// Grid of a row kernel: one CTA per row while the rows fit one resident wave, else one wave
+// (the CTAs then loop over rows), so that the pass leaves at most a wave of partials.
+template <typename K>
+cudaError_t row_grid(K kern, int threads, size_t smem, int rows, int* grid) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    long long wave = (long long)(per_sm < 1 ? 1 : per_sm) * num_sms();
+    if (wave > kMaxParts) wave = kMaxParts;
+    *grid = rows < wave ? rows : (int)wave;
+    return cudaSuccess;
+}
+
 template <int N, int M>
 cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
                                 const float2* S, float lam, Partials* pq, cudaStream_t st) {
-    pq->n = d.P;
+    const int rows = d.rows();
+    int grid = 0;
     if constexpr (N == 256) {
         const int tpad = (d.T + 1) / 2 * 2;
         const size_t smem256 = ((size_t)d.T * N + (size_t)tpad * 16 * 17) * sizeof(float2);
@@ -426,7 +446,10 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
                                                      (int)smem256);
                 if (e != cudaSuccess) return e;
             }
-            return launch_pdl(k, dim3(d.P), dim3(tpad * 16), smem256, st, t, p, S, lam, d.T, d.P,
+            cudaError_t e = row_grid(k, tpad * 16, smem256, rows, &grid);
+            if (e != cudaSuccess) return e;
+            pq->n = grid;
+            return launch_pdl(k, dim3(grid), dim3(tpad * 16), smem256, st, t, p, S, lam, d.T, rows,
                               pq->parts, tw.twQ);
         }
     }
@@ -436,7 +459,10 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    return launch_pdl(k, dim3(d.P), dim3(kThreads), smem, st, t, p, S, lam, d.T, d.P, pq->parts,
+    cudaError_t e = row_grid(k, kThreads, smem, rows, &grid);
+    if (e != cudaSuccess) return e;
+    pq->n = grid;
+    return launch_pdl(k, dim3(grid), dim3(kThreads), smem, st, t, p, S, lam, d.T, rows, pq->parts,
                       tw.twQ);
 }
 
@@ -534,7 +560,6 @@ int max_parts() { return kMaxParts; }
 
 cudaError_t launch_row_inv_w(const Dims& d, const Twiddles& tw, float2* t, const float2* p,
                              const float2* S, float lam, Partials* pq, cudaStream_t st) {
-    if (d.P > kMaxParts) return cudaErrorInvalidValue;
     switch (d.Q) {
         case 16: return launch_row_inv_w_N<16>(d, tw, t, p, S, lam, pq, st);
         case 32: return launch_row_inv_w_N<32>(d, tw, t, p, S, lam, pq, st);

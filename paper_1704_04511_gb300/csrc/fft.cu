@@ -373,29 +373,48 @@ bool fft_size_supported(int n) {
     }
 }
 
+// Volumes (R > 1): the depth transforms reuse the column kernel with the depth as the transform
+// axis and the P * Q voxels of a depth slice as its "columns" (stride P * Q between depth
+// samples); the length-P column passes then run over the T * R slices.
 cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, float2* y, int inv,
                         cudaStream_t st) {
     const float sq = 1.0f / sqrtf((float)d.Q), sp = 1.0f / sqrtf((float)d.P);
-    cudaError_t e = inv ? row_fft<true>(d.Q, x, y, d.T * d.P, sq, tw.twQ, st)
-                        : row_fft<false>(d.Q, x, y, d.T * d.P, sq, tw.twQ, st);
+    const int slices = d.T * d.R;
+    cudaError_t e = inv ? row_fft<true>(d.Q, x, y, slices * d.P, sq, tw.twQ, st)
+                        : row_fft<false>(d.Q, x, y, slices * d.P, sq, tw.twQ, st);
     if (e != cudaSuccess) return e;
-    return inv ? col_pass<COL_INV>(d.P, d.Q, d.T, d.T, y, y, nullptr, sp, tw.twP, st)
-               : col_pass<COL_FWD>(d.P, d.Q, d.T, d.T, y, y, nullptr, sp, tw.twP, st);
+    e = inv ? col_pass<COL_INV>(d.P, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st)
+            : col_pass<COL_FWD>(d.P, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st);
+    if (e != cudaSuccess || d.R == 1) return e;
+    const float sr = 1.0f / sqrtf((float)d.R);
+    const int pq = d.P * d.Q;
+    return inv ? col_pass<COL_INV>(d.R, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st)
+               : col_pass<COL_FWD>(d.R, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st);
 }
 
 cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int b_bf16,
                            const uint8_t* mask, float2* t, float2* x, cudaStream_t st) {
-    const float sc = 1.0f / sqrtf((float)d.P * (float)d.Q);
-    cudaError_t e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st)
-                           : col_pass<COL_ADJ_C64>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st);
+    const float sc = 1.0f / sqrtf((float)d.P * (float)d.Q * (float)d.R);
+    cudaError_t e;
+    if (d.R > 1) {
+        // masked depth IDFT (with the whole 1/sqrt(PQR)), then the column IDFT of every slice
+        const int pq = d.P * d.Q, slices = d.T * d.R;
+        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.R, pq, d.T, d.T, b, t, mask, sc, tw.twR, st)
+                   : col_pass<COL_ADJ_C64>(d.R, pq, d.T, d.T, b, t, mask, sc, tw.twR, st);
+        if (e != cudaSuccess) return e;
+        e = col_pass<COL_INV>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+    } else {
+        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st)
+                   : col_pass<COL_ADJ_C64>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st);
+    }
     if (e != cudaSuccess) return e;
-    return row_fft<true>(d.Q, t, x, d.T * d.P, 1.0f, tw.twQ, st);
+    return row_fft<true>(d.Q, t, x, d.T * d.rows(), 1.0f, tw.twQ, st);
 }
 
 cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
                                    float2* t, const Partials& rr, const double* rr_prev,
                                    double* rr_out, int first, cudaStream_t st) {
-    const int nrows = d.T * d.P;
+    const int nrows = d.T * d.rows();
     if (d.Q == 256) {
         const int grid = (nrows + kR256Rows - 1) / kR256Rows;
         return launch_pdl(row_fwd_pupdate_256_kernel, dim3(grid), dim3(64), 0, st, r, p, t, nrows,
@@ -447,6 +466,17 @@ cudaError_t launch_adjoint_coils_cols(const Dims& d, const Twiddles& tw, const v
 
 cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
                             cudaStream_t st) {
+    if (d.R > 1) {
+        // volumes: column DFT of every slice, depth DFT + mask + depth IDFT (with the 1/(PQR)
+        // of the two unnormalised transforms), column IDFT of every slice
+        const int pq = d.P * d.Q, slices = d.T * d.R;
+        const float sc3 = 1.0f / ((float)d.P * (float)d.Q * (float)d.R);
+        cudaError_t e = col_pass<COL_FWD>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+        if (e != cudaSuccess) return e;
+        e = col_pass<COL_MASK_OP>(d.R, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
+        if (e != cudaSuccess) return e;
+        return col_pass<COL_INV>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+    }
     const float sc = 1.0f / ((float)d.P * (float)d.Q);
     const int frames = d.T * d.nc;  // coil-major: the mask of frame f is mask frame f % T
     if (d.P == 256)

@@ -12,6 +12,11 @@
 //   gram_fill_kernel: one warp per lag: the length-P direction sum_r1 Y[pair][d2][r1] w_P^(d1 r1)
 //                     in FP64 (fixed order, deterministic), then the lag scattered over the
 //                     (l, l') pairs it fills in G (column-major s x s complex128, both triangles).
+// Volumes (depth R, N3 depth taps; lag_ab[d] also carries w_R^(d3 r3)): the row kernel runs over
+// the R * P rows unchanged, then the length-P and length-R directions are separated:
+//   gram_depth_kernel: Z[pair][d2][d1][r3] = sum_r1 Y[pair][d2][r3 P + r1] w_P^(d1 r1)  (FP64);
+//   gram_fill3_kernel: one warp per 3-D lag: sum_r3 Z[..][r3] w_R^(d3 r3) (FP64), scattered over
+//                      the tap pairs of G with column index ((m N3 + l3) N1 + l1) N2 + l2.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -117,22 +122,83 @@ __global__ void gram_fill_kernel(const double2* __restrict__ Y, int P, int N1, i
     }
 }
 
+// One warp per (pair, d2, d1, r3): the length-P direction of depth slice r3 (FP64, lanes over r1
+// in a fixed order, then a fixed shuffle tree).
+__global__ void gram_depth_kernel(const double2* __restrict__ Y, int P, int R, int N1, int N2,
+                                  int npair, const double2* __restrict__ twPd,
+                                  double2* __restrict__ Z) {
+    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1;
+    const long long nout = (long long)npair * L2 * L1 * R;
+    const long long o = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (o >= nout) return;
+    const int r3 = (int)(o % R);
+    const long long q = o / R;  // (pair * L2 + i2) * L1 + i1
+    const int i1 = (int)(q % L1);
+    const long long pi2 = q / L1;  // pair * L2 + i2
+    const int d1m = ((i1 - (N1 - 1)) % P + P) % P;
+    const double2* yrow = Y + (size_t)pi2 * R * P + (size_t)r3 * P;
+    double2 v = make_double2(0.0, 0.0);
+    for (int r1 = lane; r1 < P; r1 += 32) v = zfma(yrow[r1], twPd[(d1m * r1) % P], v);
+    v.x = warp_sum(v.x);
+    v.y = warp_sum(v.y);
+    if (lane == 0) Z[o] = v;
+}
+
+// One warp per 3-D lag (pair, d3, d1, d2): the length-R direction in FP64, then the lag
+// scattered over the tap pairs (l, l') with l - l' = d that it fills in G.
+__global__ void gram_fill3_kernel(const double2* __restrict__ Z, int R, int N1, int N2, int N3,
+                                  int M, const double2* __restrict__ twRd,
+                                  double2* __restrict__ lags, double2* __restrict__ G) {
+    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1, L3 = 2 * N3 - 1, npair = M * (M + 1) / 2;
+    const int nlag = npair * L3 * L1 * L2;
+    const int s = N1 * N2 * N3 * M;
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (o >= nlag) return;
+    const int i2 = o % L2, i1 = (o / L2) % L1, i3 = (o / (L2 * L1)) % L3, pr = o / (L2 * L1 * L3);
+    const int d1 = i1 - (N1 - 1), d2 = i2 - (N2 - 1), d3 = i3 - (N3 - 1);
+    const int d3m = (d3 % R + R) % R;
+    const double2* zrow = Z + (((size_t)pr * L2 + i2) * L1 + i1) * R;
+    double2 v = make_double2(0.0, 0.0);
+    for (int r3 = lane; r3 < R; r3 += 32) v = zfma(zrow[r3], twRd[(d3m * r3) % R], v);
+    v.x = warp_sum(v.x);
+    v.y = warp_sum(v.y);
+    if (lags && lane == 0) lags[o] = v;
+    int a = 0, e = pr;
+    while (e >= M - a) { e -= M - a; ++a; }
+    const int b = a + e;
+    const int lo1 = max(0, -d1), hi1 = min(N1, N1 - d1);
+    const int lo2 = max(0, -d2), hi2 = min(N2, N2 - d2);
+    const int lo3 = max(0, -d3), hi3 = min(N3, N3 - d3);
+    const int n1 = hi1 - lo1, n2 = hi2 - lo2, cnt = (hi3 - lo3) * n1 * n2;
+    for (int t = lane; t < cnt; t += 32) {
+        const int lp2 = lo2 + t % n2, lp1 = lo1 + (t / n2) % n1, lp3 = lo3 + t / (n2 * n1);
+        const size_t i = (((size_t)a * N3 + lp3 + d3) * N1 + lp1 + d1) * N2 + lp2 + d2;
+        const size_t j = (((size_t)b * N3 + lp3) * N1 + lp1) * N2 + lp2;
+        G[i + j * s] = v;
+        if (a != b) G[j + i * s] = zconj(v);
+    }
+}
+
 }  // namespace
 
 size_t gram_smem(const Dims& d) {
     return ((size_t)d.T * d.Q + (size_t)d.npair() * d.Q + d.Q) * sizeof(float2);
 }
 
-// One CTA per image row; the scratch holds the row DFTs Y[pair][d2][r1] (complex128).
-int gram_blocks(const Dims& d) { return d.P; }
+// One CTA per image row; the scratch holds the row DFTs Y[pair][d2][row] (complex128) and, for
+// volumes, the depth-slice sums Z[pair][d2][d1][r3] after them.
+int gram_blocks(const Dims& d) { return d.rows(); }
 
 size_t gram_scratch_bytes(const Dims& d, int nblocks) {
-    return (size_t)nblocks * d.npair() * d.L2() * sizeof(double2);
+    size_t b = (size_t)nblocks * d.npair() * d.L2() * sizeof(double2);
+    if (d.R > 1) b += (size_t)d.npair() * d.L2() * d.L1() * d.R * sizeof(double2);
+    return b;
 }
 
 cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, double2* lag_part,
                         int nblocks, double2* lags, double2* G, cudaStream_t st) {
-    if (nblocks != d.P) return cudaErrorInvalidValue;
+    if (nblocks != d.rows()) return cudaErrorInvalidValue;
     const size_t smem = gram_smem(d);
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
 #define CASE(MM)                                                                                 \
@@ -141,7 +207,7 @@ cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, doub
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem);                                         \
         if (e != cudaSuccess) return e;                                                          \
-        k<<<d.P, kThreads, smem, st>>>(x, d.T, d.P, d.Q, d.N2, tw.twQ, lag_part);                \
+        k<<<d.rows(), kThreads, smem, st>>>(x, d.T, d.rows(), d.Q, d.N2, tw.twQ, lag_part);      \
         break;                                                                                   \
     }
     switch (d.M) {
@@ -151,6 +217,18 @@ cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, doub
 #undef CASE
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (d.R > 1) {
+        double2* Z = lag_part + (size_t)nblocks * d.npair() * d.L2();
+        const long long nz = (long long)d.npair() * d.L2() * d.L1() * d.R;
+        gram_depth_kernel<<<(unsigned)((nz + 7) / 8), 256, 0, st>>>(lag_part, d.P, d.R, d.N1, d.N2,
+                                                                    d.npair(), tw.twPd, Z);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int nlag3 = (int)d.nlag();
+        gram_fill3_kernel<<<(nlag3 + 7) / 8, 256, 0, st>>>(Z, d.R, d.N1, d.N2, d.N3, d.M, tw.twRd,
+                                                           lags, G);
+        return cudaGetLastError();
+    }
     const int nlag = d.npair() * d.L1() * d.L2();
     gram_fill_kernel<<<(nlag + 7) / 8, 256, 0, st>>>(lag_part, d.P, d.N1, d.N2, d.M, tw.twPd, lags, G);
     return cudaGetLastError();

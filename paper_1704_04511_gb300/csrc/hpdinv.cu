@@ -352,28 +352,31 @@ hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
     }
 }
 
-// d_ab[delta] = sum_{l - l' = delta} H[(l', b), (l, a)] from H (s x s column-major).
-__global__ void hdiag_kernel(const double2* __restrict__ H, int N1, int N2, int M,
+// d_ab[delta] = sum_{l - l' = delta} H[(l', b), (l, a)] from H (s x s column-major); taps
+// l = (l3, l1, l2) at column index ((m N3 + l3) N1 + l1) N2 + l2, output [pair][d3][d1][d2].
+__global__ void hdiag_kernel(const double2* __restrict__ H, int N1, int N2, int N3, int M,
                              double2* __restrict__ dsum) {
-    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1;
+    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1, L3 = 2 * N3 - 1;
     const int npair = M * (M + 1) / 2;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= npair * L1 * L2) return;
-    const int pr = warp / (L1 * L2), rem = warp % (L1 * L2);
-    const int d1 = rem / L2 - (N1 - 1), d2 = rem % L2 - (N2 - 1);
+    if (warp >= npair * L3 * L1 * L2) return;
+    const int pr = warp / (L3 * L1 * L2), rem = warp % (L3 * L1 * L2);
+    const int d3 = rem / (L1 * L2) - (N3 - 1);
+    const int d1 = (rem / L2) % L1 - (N1 - 1), d2 = rem % L2 - (N2 - 1);
     int a = 0, e = pr;
     while (e >= M - a) { e -= M - a; ++a; }
     const int b = a + e;
-    const int s = N1 * N2 * M;
+    const int s = N1 * N2 * N3 * M;
     const int lo1 = max(0, -d1), hi1 = min(N1, N1 - d1);
     const int lo2 = max(0, -d2), hi2 = min(N2, N2 - d2);
-    const int n2 = hi2 - lo2;
-    const int cnt = (hi1 - lo1) * n2;
+    const int lo3 = max(0, -d3), hi3 = min(N3, N3 - d3);
+    const int n1 = hi1 - lo1, n2 = hi2 - lo2;
+    const int cnt = (hi3 - lo3) * n1 * n2;
     double2 acc = make_double2(0.0, 0.0);
     for (int t = lane; t < cnt; t += 32) {
-        const int lp1 = lo1 + t / n2, lp2 = lo2 + t % n2;
-        const size_t rowi = ((size_t)b * N1 + lp1) * N2 + lp2;
-        const size_t coli = ((size_t)a * N1 + lp1 + d1) * N2 + lp2 + d2;
+        const int lp2 = lo2 + t % n2, lp1 = lo1 + (t / n2) % n1, lp3 = lo3 + t / (n2 * n1);
+        const size_t rowi = (((size_t)b * N3 + lp3) * N1 + lp1) * N2 + lp2;
+        const size_t coli = (((size_t)a * N3 + lp3 + d3) * N1 + lp1 + d1) * N2 + lp2 + d2;
         acc = zadd(acc, H[rowi + coli * s]);
     }
     acc.x = warp_sum(acc.x);
@@ -642,10 +645,10 @@ cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, voi
 }
 
 cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStream_t st) {
-    const int nout = d.npair() * d.L1() * d.L2();
+    const int nout = (int)d.nlag();
     const int warps_per_block = 8;
     hdiag_kernel<<<(nout + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
-        H, d.N1, d.N2, d.M, dsum);
+        H, d.N1, d.N2, d.N3, d.M, dsum);
     return cudaGetLastError();
 }
 

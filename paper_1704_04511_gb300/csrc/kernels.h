@@ -10,26 +10,35 @@
 
 namespace recon {
 
-// Geometry of one problem: image series [T][P][Q] complex64, filter N1 x N2 x M taps.
+// Geometry of one problem: image series [T][P][Q] complex64 (or volumes [T][R][P][Q] when
+// R > 1), filter N1 x N2 (x N3) x M taps. A volume is laid out as R * P image rows of length Q,
+// so the row passes, the pixel-wise W and the CG vectors see rows() = R * P rows.
 struct Dims {
     int T, P, Q;
     int N1, N2, M;
     int nc = 1;  // receiver coils (Eq. measurement-ij); the transform buffer holds nc series
+    int R = 1;   // depth of a volume (third spatial axis, circular like the other two)
+    int N3 = 1;  // filter taps along the depth
     int k() const { return T - M + 1; }
     int npair() const { return M * (M + 1) / 2; }
     int L1() const { return 2 * N1 - 1; }
     int L2() const { return 2 * N2 - 1; }
-    int s() const { return N1 * N2 * M; }
-    size_t pixels() const { return (size_t)P * Q; }
-    size_t elems() const { return (size_t)T * P * Q; }
+    int L3() const { return 2 * N3 - 1; }
+    int s() const { return N1 * N2 * N3 * M; }
+    int rows() const { return R * P; }
+    size_t nlag() const { return (size_t)npair() * L1() * L2() * L3(); }
+    size_t pixels() const { return (size_t)R * P * Q; }
+    size_t elems() const { return (size_t)T * R * P * Q; }
 };
 
-// Twiddle tables e^{-2 pi i j / n}, j < n, for the two grid lengths (device memory).
+// Twiddle tables e^{-2 pi i j / n}, j < n, for the grid lengths (device memory).
 struct Twiddles {
     const float2* twP;   // length P, FP32
     const float2* twQ;   // length Q, FP32
     const double2* twPd; // length P, FP64
     const double2* twQd; // length Q, FP64
+    const float2* twR = nullptr;   // length R (volumes), FP32
+    const double2* twRd = nullptr; // length R (volumes), FP64
 };
 
 // Grid-wide deterministic reduction slot: one partial per block, finished by the last block.

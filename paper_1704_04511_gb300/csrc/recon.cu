@@ -62,7 +62,7 @@ struct recon_ctx {
     // stream / bufs / solver above always hold the ACTIVE slot's; the others are parked here.
     unsigned long ws_gen = 0;          // bumped when the active slot's workspace moves
     struct GraphKey {
-        int T, P, Q, N1, N2, M, irls, cg, bf16, method;
+        int T, P, Q, N1, N2, M, irls, cg, bf16, method, R, N3;
         double lambda, p, gamma, eps0_frac;
         const void *kspace, *masks, *out, *coils;
         int nc, coil_proj;
@@ -226,33 +226,60 @@ int get_twiddles(recon_ctx* c, const Dims& d, Twiddles* tw) {
     tw->twQ = tq.f;
     tw->twPd = tp.d;
     tw->twQd = tq.d;
+    if (d.R > 1) {
+        TwTable tr;
+        rc = twiddles(c, d.R, &tr);
+        if (rc) return rc;
+        tw->twR = tr.f;
+        tw->twRd = tr.d;
+    }
     return RECON_OK;
 }
 
 size_t gram_smem_bytes(const Dims& d) { return recon::gram_smem(d); }
 
-int check_dims(recon_ctx* c, recon_dims dd, const recon_filter* f, Dims* d) {
-    if (dd.P <= 0 || dd.Q <= 0 || dd.T <= 0) return fail(c, RECON_EINVAL, "P, Q, T must be positive");
-    if (!recon::fft_size_supported(dd.P) || !recon::fft_size_supported(dd.Q))
+// Geometry checks shared by the image-series (R = 1) and volume entry points; f = NULL for calls
+// without a filter.
+int check_geometry(recon_ctx* c, int T, int R, int P, int Q, const recon_filter3* f, Dims* d) {
+    if (P <= 0 || Q <= 0 || T <= 0 || R <= 0)
+        return fail(c, RECON_EINVAL, "P, Q, R, T must be positive");
+    if (!recon::fft_size_supported(P) || !recon::fft_size_supported(Q))
         return fail(c, RECON_EINVAL, "P and Q must be one of 16, 32, 64, 128, 192, 256, 512");
-    d->T = dd.T;
-    d->P = dd.P;
-    d->Q = dd.Q;
-    d->N1 = d->N2 = d->M = 1;
+    if (R > 1 && !recon::fft_size_supported(R))
+        return fail(c, RECON_EINVAL, "R must be 1 or one of 16, 32, 64, 128, 192, 256, 512");
+    *d = Dims{};
+    d->T = T;
+    d->P = P;
+    d->Q = Q;
+    d->R = R;
+    d->N1 = d->N2 = d->N3 = d->M = 1;
     if (f) {
-        if (f->M < 1 || f->M > recon::w_max_M() || f->M > dd.T)
+        if (f->M < 1 || f->M > recon::w_max_M() || f->M > T)
             return fail(c, RECON_EINVAL, "need 1 <= M <= min(6, T)");
-        if (f->N1 < 1 || f->N1 > dd.P || f->N2 < 1 || f->N2 > dd.Q)
+        if (f->N1 < 1 || f->N1 > P || f->N2 < 1 || f->N2 > Q)
             return fail(c, RECON_EINVAL, "need 1 <= N1 <= P and 1 <= N2 <= Q");
+        if (f->N3 < 1 || f->N3 > R) return fail(c, RECON_EINVAL, "need 1 <= N3 <= R");
         d->N1 = f->N1;
         d->N2 = f->N2;
+        d->N3 = f->N3;
         d->M = f->M;
         if (gram_smem_bytes(*d) > 220 * 1024)
             return fail(c, RECON_EINVAL, "filter / frame count too large for the Gram kernel");
     }
-    if ((long long)dd.T * dd.Q > recon::w_max_frames_times_q())
+    if ((long long)T * Q > recon::w_max_frames_times_q())
         return fail(c, RECON_EINVAL, "T * Q too large for the fused row pass");
+    if ((long long)T * R * P > (1LL << 30)) return fail(c, RECON_EINVAL, "problem too large");
     return RECON_OK;
+}
+
+int check_dims(recon_ctx* c, recon_dims dd, const recon_filter* f, Dims* d) {
+    if (!f) return check_geometry(c, dd.T, 1, dd.P, dd.Q, nullptr, d);
+    const recon_filter3 f3{f->N1, f->N2, 1, f->M};
+    return check_geometry(c, dd.T, 1, dd.P, dd.Q, &f3, d);
+}
+
+int check_dims3(recon_ctx* c, recon_dims3 dd, const recon_filter3* f, Dims* d) {
+    return check_geometry(c, dd.T, dd.R, dd.P, dd.Q, f, d);
 }
 
 struct Work {
@@ -288,7 +315,7 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
     const size_t vec = d.elems() * sizeof(float2);
     const size_t sbytes = (size_t)d.npair() * d.pixels() * sizeof(float2);
     const int s = d.s();
-    const size_t nlag = (size_t)d.npair() * d.L1() * d.L2();
+    const size_t nlag = d.nlag();
     const int ni = n_iter < 1 ? 1 : n_iter;
     w->gblocks = recon::gram_blocks(d);
     w->use_eig = use_eig;
@@ -525,9 +552,7 @@ int ensure_solver(recon_ctx* c) {
     return RECON_OK;
 }
 
-int check_params(recon_ctx* c, recon_dims dd, recon_filter f, const recon_params* prm, Dims* d) {
-    int rc = check_dims(c, dd, &f, d);
-    if (rc) return rc;
+int check_prm(recon_ctx* c, const recon_params* prm) {
     if (prm->irls < 0 || prm->cg < 1) return fail(c, RECON_EINVAL, "need irls >= 0, cg >= 1");
     if (!(prm->lambda > 0.0) || !std::isfinite(prm->lambda))
         return fail(c, RECON_EINVAL, "lambda must be positive and finite");
@@ -538,6 +563,11 @@ int check_params(recon_ctx* c, recon_dims dd, recon_filter f, const recon_params
     if (prm->weight_method != RECON_WEIGHT_AUTO && prm->weight_method != RECON_WEIGHT_EIG)
         return fail(c, RECON_EINVAL, "unknown weight method");
     return RECON_OK;
+}
+
+int check_params(recon_ctx* c, recon_dims dd, recon_filter f, const recon_params* prm, Dims* d) {
+    int rc = check_dims(c, dd, &f, d);
+    return rc ? rc : check_prm(c, prm);
 }
 
 // One solve in flight on the active slot's stream.
@@ -620,6 +650,7 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     recon_ctx::GraphKey k;
     std::memset(&k, 0, sizeof(k));
     k.T = sv.d.T; k.P = sv.d.P; k.Q = sv.d.Q; k.N1 = sv.d.N1; k.N2 = sv.d.N2; k.M = sv.d.M;
+    k.R = sv.d.R; k.N3 = sv.d.N3;
     k.irls = prm->irls; k.cg = prm->cg; k.bf16 = prm->kspace_bf16; k.method = prm->weight_method;
     k.lambda = prm->lambda; k.p = prm->p; k.gamma = prm->gamma; k.eps0_frac = prm->eps0_frac;
     k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
@@ -695,6 +726,156 @@ void release_idle(recon_ctx* c) {
         sl.bufs.clear();
         ++sl.ws_gen;
     }
+}
+
+}  // namespace
+
+namespace {
+
+size_t bytes_needed(const Dims& d) {
+    if (d.T <= 0 || d.P <= 0 || d.Q <= 0 || d.R <= 0 || d.M <= 0 || d.N1 <= 0 || d.N2 <= 0 ||
+        d.N3 <= 0)
+        return 0;
+    const size_t vec = d.elems() * sizeof(float2);
+    const size_t s = d.s();
+    const size_t nlag = d.nlag();
+    size_t b = 3 * vec + 2 * (size_t)d.npair() * d.pixels() * sizeof(float2);
+    b += s * s * sizeof(double2) * 3 + s * sizeof(double);  // G + eigensolver work (estimate)
+    b += recon::gram_scratch_bytes(d, recon::gram_blocks(d)) + recon::diag_scratch_bytes(d) +
+         2 * nlag * sizeof(double2) + recon::s_scratch_bytes(d);
+    b += (size_t)(recon::max_parts() + 512) * sizeof(double);
+    return b;
+}
+
+int solve_impl(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* masks,
+               const recon_params* prm, void* image_out) {
+    int rc = set_device(c);
+    if (rc) return rc;
+    rc = select_slot(c, 0);
+    if (rc) return rc;
+    Solve sv;
+    rc = solve_prepare(c, d, kspace, masks, prm, image_out, &sv);
+    if (rc) return rc;
+    rc = solve_enqueue_all(c, sv);
+    if (rc) return rc;
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return solve_check(c, sv);
+}
+
+int adjoint_impl(recon_ctx* c, const Dims& d, const void* kspace, int kspace_bf16,
+                 const uint8_t* masks, void* x_out) {
+    int rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    void* t;
+    rc = ensure(c, "t", d.elems() * sizeof(float2), &t);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_adjoint(d, tw, kspace, kspace_bf16, masks, (float2*)t, (float2*)x_out,
+                                  c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int fft_impl(recon_ctx* c, const Dims& d, const void* x, void* y, int inverse) {
+    int rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_fft2(d, tw, (const float2*)x, (float2*)y, inverse, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int gram_impl(recon_ctx* c, const Dims& d, const void* x, void* G_out, void* lags_out) {
+    int rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    void* lp;
+    const int nb = recon::gram_blocks(d);
+    rc = ensure(c, "lag_part", recon::gram_scratch_bytes(d, nb), &lp);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_gram(d, tw, (const float2*)x, (double2*)lp, nb, (double2*)lags_out,
+                               (double2*)G_out, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int weight_impl(recon_ctx* c, const Dims& d, const void* G_in, double eps_in, double p,
+                int method, void* S_out, void* dsum_out, void* evals_out, double* eps_out) {
+    int rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    Work w;
+    rc = get_work(c, d, 1, 1, false, wants_eig(p, method), &w);
+    if (rc) return rc;
+    rc = reset_status(c, w);
+    if (rc) return rc;
+    const size_t gbytes = (size_t)d.s() * d.s() * sizeof(double2);
+    RC_CUDA(cudaMemcpyAsync(w.G, G_in, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+    const bool set = eps_in >= 0.0;
+    rc = weight_step(c, d, tw, w, p, 1, set ? 0.0 : -eps_in, 1.0, set, eps_in, (float2*)S_out, 0);
+    if (rc) return rc;
+    if (dsum_out)
+        RC_CUDA(cudaMemcpyAsync(dsum_out, w.dsum, d.nlag() * sizeof(double2),
+                                cudaMemcpyDeviceToDevice, c->stream));
+    if (evals_out)
+        RC_CUDA(cudaMemcpyAsync(evals_out, w.evals, (size_t)d.s() * sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    rc = check_status(c, w, 1);
+    if (rc) return rc;
+    if (eps_out) RC_CUDA(cudaMemcpy(eps_out, w.eps, sizeof(double), cudaMemcpyDeviceToHost));
+    return RECON_OK;
+}
+
+int weight_args(recon_ctx* c, const void* G_in, double eps_in, double p, int method,
+                const void* S_out, const void* evals_out) {
+    if (!G_in || !S_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (method != RECON_WEIGHT_AUTO && method != RECON_WEIGHT_EIG)
+        return fail(c, RECON_EINVAL, "unknown weight method");
+    if (evals_out && !wants_eig(p, method))
+        return fail(c, RECON_EINVAL, "eigenvalues are only formed by RECON_WEIGHT_EIG or p > 0");
+    if (!std::isfinite(eps_in) || !(p >= 0.0 && p <= 1.0)) return fail(c, RECON_EINVAL, "bad eps or p");
+    return RECON_OK;
+}
+
+int apply_normal_impl(recon_ctx* c, const Dims& d, const uint8_t* masks, const void* S,
+                      double lambda, const void* x, void* y) {
+    int rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    Twiddles tw;
+    rc = get_twiddles(c, d, &tw);
+    if (rc) return rc;
+    void *pp, *parts;
+    rc = ensure(c, "p", d.elems() * sizeof(float2), &pp);
+    if (rc) return rc;
+    rc = ensure(c, "parts", (size_t)recon::max_parts() * sizeof(double), &parts);
+    if (rc) return rc;
+    recon::Partials pq{(double*)parts, 0};
+    const recon::Partials none{nullptr, 0};
+    // the CG operator passes with first = 1 (p = x); y receives (A^H A + lambda W) x
+    if (c->cluster_fft && recon::frame_op_supported(d)) {
+        RC_CUDA(recon::launch_frame_aha(d, tw, (const float2*)x, (float2*)pp, (float2*)y, masks,
+                                        none, nullptr, nullptr, 1, c->stream));
+        RC_CUDA(recon::launch_w_combine(d, (float2*)y, (const float2*)pp, (const float2*)S,
+                                        (float)lambda, &pq, c->stream));
+    } else {
+        RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y,
+                                              none, nullptr, nullptr, 1, c->stream));
+        RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
+        RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
+                                        (float)lambda, &pq, c->stream));
+    }
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
 }
 
 }  // namespace
@@ -777,16 +958,15 @@ const char* recon_last_error(const recon_ctx* c) {
 size_t recon_bytes_needed(recon_dims dd, recon_filter f, int kspace_bf16) {
     (void)kspace_bf16;  // k-space stays in the caller's buffer
     Dims d{dd.T, dd.P, dd.Q, f.N1, f.N2, f.M};
-    if (d.T <= 0 || d.P <= 0 || d.Q <= 0 || d.M <= 0 || d.N1 <= 0 || d.N2 <= 0) return 0;
-    const size_t vec = d.elems() * sizeof(float2);
-    const size_t s = d.s();
-    const size_t nlag = (size_t)d.npair() * d.L1() * d.L2();
-    size_t b = 3 * vec + 2 * (size_t)d.npair() * d.pixels() * sizeof(float2);
-    b += s * s * sizeof(double2) * 3 + s * sizeof(double);  // G + eigensolver work (estimate)
-    b += recon::gram_scratch_bytes(d, recon::gram_blocks(d)) + recon::diag_scratch_bytes(d) +
-         2 * nlag * sizeof(double2) + recon::s_scratch_bytes(d);
-    b += (size_t)(recon::max_parts() + 512) * sizeof(double);
-    return b;
+    return bytes_needed(d);
+}
+
+size_t recon_bytes_needed3(recon_dims3 dd, recon_filter3 f, int kspace_bf16) {
+    (void)kspace_bf16;
+    Dims d{dd.T, dd.P, dd.Q, f.N1, f.N2, f.M};
+    d.R = dd.R;
+    d.N3 = f.N3;
+    return bytes_needed(d);
 }
 
 int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* masks,
@@ -796,17 +976,18 @@ int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* 
     Dims d;
     int rc = check_params(c, dd, f, prm, &d);
     if (rc) return rc;
-    rc = set_device(c);
+    return solve_impl(c, d, kspace, masks, prm, image_out);
+}
+
+int recon_solve3(recon_ctx* c, recon_dims3 dd, const void* kspace, const uint8_t* masks,
+                 recon_filter3 f, const recon_params* prm, void* image_out) {
+    if (!c) return RECON_EINVAL;
+    if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims3(c, dd, &f, &d);
+    if (!rc) rc = check_prm(c, prm);
     if (rc) return rc;
-    rc = select_slot(c, 0);
-    if (rc) return rc;
-    Solve sv;
-    rc = solve_prepare(c, d, kspace, masks, prm, image_out, &sv);
-    if (rc) return rc;
-    rc = solve_enqueue_all(c, sv);
-    if (rc) return rc;
-    RC_CUDA(cudaStreamSynchronize(c->stream));
-    return solve_check(c, sv);
+    return solve_impl(c, d, kspace, masks, prm, image_out);
 }
 
 int recon_solve_coils(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* masks,
@@ -1063,19 +1244,16 @@ int recon_adjoint(recon_ctx* c, recon_dims dd, const void* kspace, int kspace_bf
     if (!kspace || !masks || !x_out) return fail(c, RECON_EINVAL, "null pointer");
     Dims d;
     int rc = check_dims(c, dd, nullptr, &d);
-    if (rc) return rc;
-    rc = set_device(c);
-    if (rc) return rc;
-    Twiddles tw;
-    rc = get_twiddles(c, d, &tw);
-    if (rc) return rc;
-    void* t;
-    rc = ensure(c, "t", d.elems() * sizeof(float2), &t);
-    if (rc) return rc;
-    RC_CUDA(recon::launch_adjoint(d, tw, kspace, kspace_bf16, masks, (float2*)t, (float2*)x_out,
-                                  c->stream));
-    RC_CUDA(cudaStreamSynchronize(c->stream));
-    return RECON_OK;
+    return rc ? rc : adjoint_impl(c, d, kspace, kspace_bf16, masks, x_out);
+}
+
+int recon_adjoint3(recon_ctx* c, recon_dims3 dd, const void* kspace, int kspace_bf16,
+                   const uint8_t* masks, void* x_out) {
+    if (!c) return RECON_EINVAL;
+    if (!kspace || !masks || !x_out) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims3(c, dd, nullptr, &d);
+    return rc ? rc : adjoint_impl(c, d, kspace, kspace_bf16, masks, x_out);
 }
 
 int recon_fft2(recon_ctx* c, recon_dims dd, const void* x, void* y, int inverse) {
@@ -1083,15 +1261,15 @@ int recon_fft2(recon_ctx* c, recon_dims dd, const void* x, void* y, int inverse)
     if (!x || !y) return fail(c, RECON_EINVAL, "null pointer");
     Dims d;
     int rc = check_dims(c, dd, nullptr, &d);
-    if (rc) return rc;
-    rc = set_device(c);
-    if (rc) return rc;
-    Twiddles tw;
-    rc = get_twiddles(c, d, &tw);
-    if (rc) return rc;
-    RC_CUDA(recon::launch_fft2(d, tw, (const float2*)x, (float2*)y, inverse, c->stream));
-    RC_CUDA(cudaStreamSynchronize(c->stream));
-    return RECON_OK;
+    return rc ? rc : fft_impl(c, d, x, y, inverse);
+}
+
+int recon_fft3(recon_ctx* c, recon_dims3 dd, const void* x, void* y, int inverse) {
+    if (!c) return RECON_EINVAL;
+    if (!x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims3(c, dd, nullptr, &d);
+    return rc ? rc : fft_impl(c, d, x, y, inverse);
 }
 
 int recon_gram(recon_ctx* c, recon_dims dd, recon_filter f, const void* x, void* G_out,
@@ -1100,61 +1278,38 @@ int recon_gram(recon_ctx* c, recon_dims dd, recon_filter f, const void* x, void*
     if (!x || !G_out) return fail(c, RECON_EINVAL, "null pointer");
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
-    if (rc) return rc;
-    rc = set_device(c);
-    if (rc) return rc;
-    Twiddles tw;
-    rc = get_twiddles(c, d, &tw);
-    if (rc) return rc;
-    void* lp;
-    const int nb = recon::gram_blocks(d);
-    rc = ensure(c, "lag_part", recon::gram_scratch_bytes(d, nb), &lp);
-    if (rc) return rc;
-    RC_CUDA(recon::launch_gram(d, tw, (const float2*)x, (double2*)lp, nb, (double2*)lags_out,
-                               (double2*)G_out, c->stream));
-    RC_CUDA(cudaStreamSynchronize(c->stream));
-    return RECON_OK;
+    return rc ? rc : gram_impl(c, d, x, G_out, lags_out);
+}
+
+int recon_gram3(recon_ctx* c, recon_dims3 dd, recon_filter3 f, const void* x, void* G_out,
+                void* lags_out) {
+    if (!c) return RECON_EINVAL;
+    if (!x || !G_out) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims3(c, dd, &f, &d);
+    return rc ? rc : gram_impl(c, d, x, G_out, lags_out);
 }
 
 int recon_weight(recon_ctx* c, recon_dims dd, recon_filter f, const void* G_in, double eps_in,
                  double p, int method, void* S_out, void* dsum_out, void* evals_out,
                  double* eps_out) {
     if (!c) return RECON_EINVAL;
-    if (!G_in || !S_out) return fail(c, RECON_EINVAL, "null pointer");
-    if (method != RECON_WEIGHT_AUTO && method != RECON_WEIGHT_EIG)
-        return fail(c, RECON_EINVAL, "unknown weight method");
-    if (evals_out && !wants_eig(p, method))
-        return fail(c, RECON_EINVAL, "eigenvalues are only formed by RECON_WEIGHT_EIG or p > 0");
-    if (!std::isfinite(eps_in) || !(p >= 0.0 && p <= 1.0)) return fail(c, RECON_EINVAL, "bad eps or p");
+    int rc = weight_args(c, G_in, eps_in, p, method, S_out, evals_out);
+    if (rc) return rc;
     Dims d;
-    int rc = check_dims(c, dd, &f, &d);
+    rc = check_dims(c, dd, &f, &d);
+    return rc ? rc : weight_impl(c, d, G_in, eps_in, p, method, S_out, dsum_out, evals_out, eps_out);
+}
+
+int recon_weight3(recon_ctx* c, recon_dims3 dd, recon_filter3 f, const void* G_in, double eps_in,
+                  double p, int method, void* S_out, void* dsum_out, void* evals_out,
+                  double* eps_out) {
+    if (!c) return RECON_EINVAL;
+    int rc = weight_args(c, G_in, eps_in, p, method, S_out, evals_out);
     if (rc) return rc;
-    rc = set_device(c);
-    if (rc) return rc;
-    Twiddles tw;
-    rc = get_twiddles(c, d, &tw);
-    if (rc) return rc;
-    Work w;
-    rc = get_work(c, d, 1, 1, false, wants_eig(p, method), &w);
-    if (rc) return rc;
-    rc = reset_status(c, w);
-    if (rc) return rc;
-    const size_t gbytes = (size_t)d.s() * d.s() * sizeof(double2);
-    RC_CUDA(cudaMemcpyAsync(w.G, G_in, gbytes, cudaMemcpyDeviceToDevice, c->stream));
-    const bool set = eps_in >= 0.0;
-    rc = weight_step(c, d, tw, w, p, 1, set ? 0.0 : -eps_in, 1.0, set, eps_in, (float2*)S_out, 0);
-    if (rc) return rc;
-    if (dsum_out)
-        RC_CUDA(cudaMemcpyAsync(dsum_out, w.dsum, (size_t)d.npair() * d.L1() * d.L2() * sizeof(double2),
-                                cudaMemcpyDeviceToDevice, c->stream));
-    if (evals_out)
-        RC_CUDA(cudaMemcpyAsync(evals_out, w.evals, (size_t)d.s() * sizeof(double),
-                                cudaMemcpyDeviceToDevice, c->stream));
-    RC_CUDA(cudaStreamSynchronize(c->stream));
-    rc = check_status(c, w, 1);
-    if (rc) return rc;
-    if (eps_out) RC_CUDA(cudaMemcpy(eps_out, w.eps, sizeof(double), cudaMemcpyDeviceToHost));
-    return RECON_OK;
+    Dims d;
+    rc = check_dims3(c, dd, &f, &d);
+    return rc ? rc : weight_impl(c, d, G_in, eps_in, p, method, S_out, dsum_out, evals_out, eps_out);
 }
 
 int recon_apply_normal(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks,
@@ -1164,34 +1319,17 @@ int recon_apply_normal(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_
     if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
-    if (rc) return rc;
-    rc = set_device(c);
-    if (rc) return rc;
-    Twiddles tw;
-    rc = get_twiddles(c, d, &tw);
-    if (rc) return rc;
-    void *pp, *parts;
-    rc = ensure(c, "p", d.elems() * sizeof(float2), &pp);
-    if (rc) return rc;
-    rc = ensure(c, "parts", (size_t)recon::max_parts() * sizeof(double), &parts);
-    if (rc) return rc;
-    recon::Partials pq{(double*)parts, 0};
-    const recon::Partials none{nullptr, 0};
-    // the CG operator passes with first = 1 (p = x); y receives (A^H A + lambda W) x
-    if (c->cluster_fft && recon::frame_op_supported(d)) {
-        RC_CUDA(recon::launch_frame_aha(d, tw, (const float2*)x, (float2*)pp, (float2*)y, masks,
-                                        none, nullptr, nullptr, 1, c->stream));
-        RC_CUDA(recon::launch_w_combine(d, (float2*)y, (const float2*)pp, (const float2*)S,
-                                        (float)lambda, &pq, c->stream));
-    } else {
-        RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y,
-                                              none, nullptr, nullptr, 1, c->stream));
-        RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
-        RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
-                                        (float)lambda, &pq, c->stream));
-    }
-    RC_CUDA(cudaStreamSynchronize(c->stream));
-    return RECON_OK;
+    return rc ? rc : apply_normal_impl(c, d, masks, S, lambda, x, y);
+}
+
+int recon_apply_normal3(recon_ctx* c, recon_dims3 dd, recon_filter3 f, const uint8_t* masks,
+                        const void* S, double lambda, const void* x, void* y) {
+    if (!c) return RECON_EINVAL;
+    if (!masks || !S || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
+    Dims d;
+    int rc = check_dims3(c, dd, &f, &d);
+    return rc ? rc : apply_normal_impl(c, d, masks, S, lambda, x, y);
 }
 
 int recon_apply_w(recon_ctx* c, recon_dims dd, recon_filter f, const void* S, const void* x,

@@ -7,6 +7,9 @@
 //   d_ab[delta] = sum_i sum_{l'} V[(l', b), i] conj(V[(l' + delta, a), i]),
 // in FP64, in chunks of eigenvectors (one CTA per chunk and pair), then reduced in a fixed
 // order. S is a pruned 2-D DFT evaluated separably: FP64 along Q, FP32 along P.
+// Volumes (depth R, N3 depth taps): d carries a third lag d3 (layout [pair][d3][d1][d2]) and S a
+// third factor e^{-2 pi i d3 r3 / R}: the Q and P stages run over the pair x d3 planes, then an
+// FP32 depth stage forms S[pair][r3][r1][r2].
 #include "common.cuh"
 #include "kernels.h"
 
@@ -28,12 +31,12 @@ __global__ void eps_kernel(const double* __restrict__ lmax, double* eps, int fir
 
 __global__ void __launch_bounds__(kThreads)
 diag_part_kernel(const double2* __restrict__ U, const double* __restrict__ evals,
-                 const double* __restrict__ eps_p, double p, int N1, int N2, int M,
+                 const double* __restrict__ eps_p, double p, int N1, int N2, int N3, int M,
                  double2* __restrict__ dpart) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double2* V = reinterpret_cast<double2*>(smraw);  // [kChunk][s]
-    const int s = N1 * N2 * M;
-    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1;
+    const int s = N1 * N2 * N3 * M;
+    const int L1 = 2 * N1 - 1, L2 = 2 * N2 - 1, L3 = 2 * N3 - 1;
     const int i0 = blockIdx.x * kChunk;
     const int nc = min(kChunk, s - i0);
     const int pr = blockIdx.y;
@@ -50,19 +53,21 @@ diag_part_kernel(const double2* __restrict__ U, const double* __restrict__ evals
         V[t] = make_double2(u.x * sf, u.y * sf);
     }
     __syncthreads();
-    const int nlag = L1 * L2;
+    const int nlag = L3 * L1 * L2;
     double2* out = dpart + ((size_t)blockIdx.x * gridDim.y + pr) * nlag;
     for (int o = threadIdx.x; o < nlag; o += blockDim.x) {
-        const int d1 = o / L2 - (N1 - 1), d2 = o % L2 - (N2 - 1);
+        const int d2 = o % L2 - (N2 - 1), d1 = (o / L2) % L1 - (N1 - 1), d3 = o / (L2 * L1) - (N3 - 1);
         double2 acc = make_double2(0.0, 0.0);
         for (int c = 0; c < nc; ++c) {
             const double2* v = V + (size_t)c * s;
-            for (int lp1 = max(0, -d1); lp1 < min(N1, N1 - d1); ++lp1)
-                for (int lp2 = max(0, -d2); lp2 < min(N2, N2 - d2); ++lp2) {
-                    const double2 vb = v[((size_t)b * N1 + lp1) * N2 + lp2];
-                    const double2 va = v[((size_t)a * N1 + lp1 + d1) * N2 + lp2 + d2];
-                    acc = zfmacj2(vb, va, acc);
-                }
+            for (int lp3 = max(0, -d3); lp3 < min(N3, N3 - d3); ++lp3)
+                for (int lp1 = max(0, -d1); lp1 < min(N1, N1 - d1); ++lp1)
+                    for (int lp2 = max(0, -d2); lp2 < min(N2, N2 - d2); ++lp2) {
+                        const double2 vb = v[(((size_t)b * N3 + lp3) * N1 + lp1) * N2 + lp2];
+                        const double2 va =
+                            v[(((size_t)a * N3 + lp3 + d3) * N1 + lp1 + d1) * N2 + lp2 + d2];
+                        acc = zfmacj2(vb, va, acc);
+                    }
         }
         out[o] = acc;
     }
@@ -127,7 +132,36 @@ s_stage2_kernel(const float2* __restrict__ Z, int N1, int P, int Q, int npair,
     }
 }
 
+// S[pair][r3][px] = sum_{d3} Z2[pair][d3][px] w_R^{d3 r3} (FP32): one thread per voxel of depth
+// slice r3 (blockIdx.y = pair * R + r3), the L3 twiddles in shared memory.
+__global__ void __launch_bounds__(kThreads)
+s_stage3_kernel(const float2* __restrict__ Z2, int N3, int R, size_t npx,
+                const float2* __restrict__ twR, float2* __restrict__ S) {
+    __shared__ float2 w3[kMaxL1];
+    const int L3 = 2 * N3 - 1;
+    const int pr = blockIdx.y / R, r3 = blockIdx.y % R;
+    if (threadIdx.x == 0) {
+        int ti = (((R - (N3 - 1) % R) % R) * r3) % R;
+        for (int i3 = 0; i3 < L3; ++i3) {
+            w3[i3] = twR[ti];
+            ti += r3;
+            if (ti >= R) ti -= R;
+        }
+    }
+    __syncthreads();
+    const float2* zp = Z2 + (size_t)pr * L3 * npx;
+    float2* out = S + ((size_t)pr * R + r3) * npx;
+    for (size_t px = (size_t)blockIdx.x * blockDim.x + threadIdx.x; px < npx;
+         px += (size_t)gridDim.x * blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i3 = 0; i3 < L3; ++i3) acc = cfma(zp[(size_t)i3 * npx + px], w3[i3], acc);
+        out[px] = acc;
+    }
+}
+
 int nchunks(const Dims& d) { return (d.s() + kChunk - 1) / kChunk; }
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
@@ -138,7 +172,7 @@ cudaError_t launch_eps(const double* lmax, double* eps, int first, double frac, 
 }
 
 size_t diag_scratch_bytes(const Dims& d) {
-    return (size_t)nchunks(d) * d.npair() * d.L1() * d.L2() * sizeof(double2);
+    return (size_t)nchunks(d) * d.nlag() * sizeof(double2);
 }
 
 cudaError_t launch_diag_sums(const Dims& d, const double2* U, const double* evals,
@@ -151,26 +185,41 @@ cudaError_t launch_diag_sums(const Dims& d, const double2* U, const double* eval
         if (e != cudaSuccess) return e;
     }
     dim3 grid(nchunks(d), d.npair());
-    diag_part_kernel<<<grid, kThreads, smem, st>>>(U, evals, eps, p, d.N1, d.N2, d.M, dpart);
+    diag_part_kernel<<<grid, kThreads, smem, st>>>(U, evals, eps, p, d.N1, d.N2, d.N3, d.M, dpart);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int nout = d.npair() * d.L1() * d.L2();
+    const int nout = (int)d.nlag();
     diag_reduce_kernel<<<(nout + 7) / 8, 256, 0, st>>>(dpart, nchunks(d), nout, dsum);
     return cudaGetLastError();
 }
 
 size_t s_scratch_bytes(const Dims& d) {
-    return (size_t)d.npair() * d.L1() * d.Q * sizeof(float2);
+    size_t b = align256((size_t)d.npair() * d.L3() * d.L1() * d.Q * sizeof(float2));
+    if (d.R > 1) b += (size_t)d.npair() * d.L3() * d.P * d.Q * sizeof(float2);
+    return b;
 }
 
 cudaError_t launch_weight_S(const Dims& d, const Twiddles& tw, const double2* dsum, double2* Z_,
                             float2* S, cudaStream_t st) {
     float2* Z = reinterpret_cast<float2*>(Z_);
-    s_stage1_kernel<<<d.npair() * d.L1(), kThreads, 0, st>>>(dsum, d.N1, d.N2, d.Q, tw.twQd, Z);
+    const int planes = d.npair() * d.L3();  // (pair, d3) planes of the summed diagonals
+    s_stage1_kernel<<<planes * d.L1(), kThreads, 0, st>>>(dsum, d.N1, d.N2, d.Q, tw.twQd, Z);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (d.L1() > kMaxL1) return cudaErrorInvalidValue;
-    s_stage2_kernel<<<d.P, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, d.npair(), tw.twP, S);
+    if (d.L1() > kMaxL1 || d.L3() > kMaxL1) return cudaErrorInvalidValue;
+    if (d.R == 1) {
+        s_stage2_kernel<<<d.P, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, d.npair(), tw.twP, S);
+        return cudaGetLastError();
+    }
+    float2* Z2 = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Z) +
+                                           align256((size_t)planes * d.L1() * d.Q * sizeof(float2)));
+    s_stage2_kernel<<<d.P, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, planes, tw.twP, Z2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t npx = (size_t)d.P * d.Q;
+    const int gx = (int)((npx + kThreads - 1) / kThreads);
+    s_stage3_kernel<<<dim3(gx < 64 ? gx : 64, d.npair() * d.R), kThreads, 0, st>>>(
+        Z2, d.N3, d.R, npx, tw.twR, S);
     return cudaGetLastError();
 }
 

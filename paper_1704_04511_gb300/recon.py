@@ -10,6 +10,8 @@ Tensor conventions: image series / k-space are torch.complex64 tensors of shape 
 torch.complex128 (s, s) stored column-major, i.e. the C array G[i + j*s] is tensor element
 [j, i] of a row-major (s, s) tensor (use .T to read it as G[i, j]); S is complex64
 (npair, P, Q); lags and summed diagonals are complex128 (npair, 2N1-1, 2N2-1).
+Volumes (the *3 calls): series, k-space and masks (T, R, P, Q); filters (N1, N2, N3, M); S
+(npair, R, P, Q); lags and summed diagonals (npair, 2N3-1, 2N1-1, 2N2-1).
 """
 
 from __future__ import annotations
@@ -39,7 +41,9 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
             "recon_profile_read", "recon_profile_name", "recon_gram_static",
             "recon_solve_batch", "recon_set_option", "recon_submit", "recon_poll", "recon_t2fit",
-            "recon_solve_coils", "recon_adjoint_coils", "recon_apply_normal_coils")
+            "recon_solve_coils", "recon_adjoint_coils", "recon_apply_normal_coils",
+            "recon_bytes_needed3", "recon_solve3", "recon_adjoint3", "recon_fft3", "recon_gram3",
+            "recon_weight3", "recon_apply_normal3")
 
 PROF_KINDS = 15
 
@@ -56,6 +60,15 @@ class recon_dims(ctypes.Structure):
 
 class recon_filter(ctypes.Structure):
     _fields_ = [("N1", ctypes.c_int), ("N2", ctypes.c_int), ("M", ctypes.c_int)]
+
+
+class recon_dims3(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int), ("Q", ctypes.c_int), ("R", ctypes.c_int), ("T", ctypes.c_int)]
+
+
+class recon_filter3(ctypes.Structure):
+    _fields_ = [("N1", ctypes.c_int), ("N2", ctypes.c_int), ("N3", ctypes.c_int),
+                ("M", ctypes.c_int)]
 
 
 class recon_params(ctypes.Structure):
@@ -81,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib = ctypes.CDLL(path)
         vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
         dims, filt = recon_dims, recon_filter
+        dims3, filt3 = recon_dims3, recon_filter3
         sig = {
             "recon_create": (i, [ctypes.POINTER(vp), i, sz, vp]),
             "recon_destroy": (None, [vp]),
@@ -109,6 +123,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_apply_normal_coils": (i, [vp, dims, filt, vp, vp, i, vp, d, vp, vp]),
             "recon_solve_batch": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp), filt,
                                       ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
+            "recon_bytes_needed3": (sz, [dims3, filt3, i]),
+            "recon_solve3": (i, [vp, dims3, vp, vp, filt3, ctypes.POINTER(recon_params), vp]),
+            "recon_adjoint3": (i, [vp, dims3, vp, i, vp, vp]),
+            "recon_fft3": (i, [vp, dims3, vp, vp, i]),
+            "recon_gram3": (i, [vp, dims3, filt3, vp, vp, vp]),
+            "recon_weight3": (i, [vp, dims3, filt3, vp, d, d, i, vp, vp, vp, ctypes.POINTER(d)]),
+            "recon_apply_normal3": (i, [vp, dims3, filt3, vp, vp, d, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -322,6 +343,68 @@ def recon_t2fit(ctx, x, times_ms, t2_out, amp_out=None, fg_frac: float = 0.1, n_
     t = (ctypes.c_double * len(times_ms))(*[float(v) for v in times_ms])
     _check(ctx, load_library().recon_t2fit(ctx, _dims(x), _ptr(x), t, float(fg_frac), int(n_gn),
                                            _ptr(t2_out), _ptr(amp_out)))
+
+
+# ---- volumes (T, R, P, Q) ----
+
+def _dims3(x) -> recon_dims3:
+    T, R, P, Q = x.shape[:4]
+    return recon_dims3(P=int(P), Q=int(Q), R=int(R), T=int(T))
+
+
+def _filt3(f) -> recon_filter3:
+    N1, N2, N3, M = f
+    return recon_filter3(N1=int(N1), N2=int(N2), N3=int(N3), M=int(M))
+
+
+def recon_bytes_needed3(shape, filt, kspace_bf16: bool = False) -> int:
+    T, R, P, Q = shape
+    return int(load_library().recon_bytes_needed3(recon_dims3(P=P, Q=Q, R=R, T=T), _filt3(filt),
+                                                   int(kspace_bf16)))
+
+
+def recon_solve3(ctx, kspace, masks, filt, lam: float, p: float, irls: int, cg: int,
+                 image_out, gamma: float = 1.4, eps0_frac: float = 0.01,
+                 weight_method: int = RECON_WEIGHT_AUTO) -> None:
+    import torch
+    bf16 = kspace.dtype == torch.bfloat16
+    prm = recon_params(irls=int(irls), cg=int(cg), lambda_=float(lam), p=float(p),
+                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=int(bf16),
+                       weight_method=int(weight_method))
+    _check(ctx, load_library().recon_solve3(ctx, _dims3(masks), _ptr(kspace), _ptr(masks),
+                                            _filt3(filt), ctypes.byref(prm), _ptr(image_out)))
+
+
+def recon_adjoint3(ctx, kspace, masks, x_out) -> None:
+    import torch
+    bf16 = kspace.dtype == torch.bfloat16
+    _check(ctx, load_library().recon_adjoint3(ctx, _dims3(masks), _ptr(kspace), int(bf16),
+                                              _ptr(masks), _ptr(x_out)))
+
+
+def recon_fft3(ctx, x, y, inverse: bool = False) -> None:
+    _check(ctx, load_library().recon_fft3(ctx, _dims3(x), _ptr(x), _ptr(y), int(inverse)))
+
+
+def recon_gram3(ctx, x, filt, G_out, lags_out=None) -> None:
+    _check(ctx, load_library().recon_gram3(ctx, _dims3(x), _filt3(filt), _ptr(x), _ptr(G_out),
+                                           _ptr(lags_out)))
+
+
+def recon_weight3(ctx, shape, filt, G_in, eps_in: float, p: float, S_out, dsum_out=None,
+                  evals_out=None, method: int = RECON_WEIGHT_AUTO) -> float:
+    T, R, P, Q = shape
+    eps_used = ctypes.c_double(0.0)
+    _check(ctx, load_library().recon_weight3(ctx, recon_dims3(P=P, Q=Q, R=R, T=T), _filt3(filt),
+                                             _ptr(G_in), float(eps_in), float(p), int(method),
+                                             _ptr(S_out), _ptr(dsum_out), _ptr(evals_out),
+                                             ctypes.byref(eps_used)))
+    return eps_used.value
+
+
+def recon_apply_normal3(ctx, masks, filt, S, lam: float, x, y) -> None:
+    _check(ctx, load_library().recon_apply_normal3(ctx, _dims3(x), _filt3(filt), _ptr(masks),
+                                                   _ptr(S), float(lam), _ptr(x), _ptr(y)))
 
 
 PROF_ALL = (1 << 15) - 1
