@@ -295,6 +295,51 @@ int recon_weight3(recon_ctx* c, recon_dims3 d, recon_filter3 f, const void* G_in
 int recon_apply_normal3(recon_ctx* c, recon_dims3 d, recon_filter3 f, const uint8_t* masks,
                         const void* S, double lambda, const void* x, void* y);
 
+/* ---- comparison methods (Sec. IV) ----
+ * The methods the paper compares against, on the same forward model and parameters as
+ * recon_solve, for reproducing its qualitative comparison on synthetic data:
+ *  RECON_VARIANT_PROPOSED   the method of recon_solve;
+ *  RECON_VARIANT_GIRAF      the lifting circular along the frames as well (the GIRAF
+ *                           approximation, Sec. III-A): T windows, window j taking frames
+ *                           (j + M - 1 - m) mod T; Gram, weight and W otherwise as proposed;
+ *  RECON_VARIANT_HLR_VOXEL  the pixel-wise Toeplitz prior (Sec. II-D, Eq. MORASA-objective):
+ *                           per pixel r the k x M matrix T_r[j][m] = x_{j+M-1-m}(r) (image
+ *                           domain), its Gram G_r and weight H_r = (G_r + eps_r I)^(p/2-1) (FP64
+ *                           Jacobi eigendecomposition per pixel), eps_r^(0) = eps0_frac *
+ *                           lambda_max(G_r(x0)), eps_r <- eps_r / gamma; W uses S(r) = H_r^T.
+ *                           The filter must have N1 = N2 = 1;
+ *  RECON_VARIANT_DIRECT     IRLS without the FFT approximations (Sec. IV-A): the exact multi-fold
+ *                           Toeplitz matrix, valid in space and time, (T-M+1)(P-N1+1)(Q-N2+1) x s,
+ *                           formed explicitly (complex128 for its Gram, a library Hermitian
+ *                           rank-k product; complex64 for the CG, a library GEMM per step); the
+ *                           workspace holds (T-M+1)(P-N1+1)(Q-N2+1) s 16 bytes for it. */
+#define RECON_VARIANT_PROPOSED 0
+#define RECON_VARIANT_GIRAF 1
+#define RECON_VARIANT_HLR_VOXEL 2
+#define RECON_VARIANT_DIRECT 3
+/* Algorithm 1 with the chosen variant (arguments as recon_solve). */
+int recon_solve_variant(recon_ctx* c, recon_dims d, const void* kspace, const uint8_t* masks,
+                        recon_filter f, const recon_params* prm, int variant, void* image_out);
+/* Gram of the variant's lifting of F x: PROPOSED / GIRAF / DIRECT: s x s complex128 column-major;
+ * HLR_VOXEL: the per-pixel Grams G_r, [P][Q][M][M] complex128 (row-major M x M). */
+int recon_gram_variant(recon_ctx* c, recon_dims d, recon_filter f, int variant, const void* x,
+                       void* G_out);
+/* HLR-Voxel weight of x: per pixel G_r, its FP64 eigendecomposition, H_r with eps[r] (device
+ * [P][Q] doubles, > 0) and S(r) = H_r^T into S_out (npair x P x Q complex64, the pair layout of
+ * recon_weight); lmax_out (device [P][Q] doubles, may be NULL) receives lambda_max(G_r). */
+int recon_voxel_weight(recon_ctx* c, recon_dims d, int M, const void* x, const double* eps,
+                       double p, void* S_out, double* lmax_out);
+/* IRLS-direct weight: H = (G + eps I)^(p/2-1) as a full s x s complex128 column-major matrix
+ * (eps as in recon_weight; the FP64 sweep inverse for p = 0 with RECON_WEIGHT_AUTO, else the
+ * eigendecomposition). */
+int recon_weight_direct(recon_ctx* c, recon_dims d, recon_filter f, const void* G_in,
+                        double eps_in, double p, int method, void* H_out, double* eps_out);
+/* y = (A^H A + lambda W) x of the variant: W is S (npair x P x Q complex64) for PROPOSED, GIRAF and
+ * HLR_VOXEL, and H (s x s complex128 column-major) for DIRECT, where W x = F^H T^*(T(F x) H). */
+int recon_apply_normal_variant(recon_ctx* c, recon_dims d, recon_filter f, int variant,
+                               const uint8_t* masks, const void* W, double lambda, const void* x,
+                               void* y);
+
 /* ---- measurement ---- */
 
 /* Launch classes timed by recon_profile (one pair of CUDA events on the context's stream around

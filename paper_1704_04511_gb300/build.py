@@ -1,7 +1,8 @@
 """Build the in-tree CUDA library `librecon.so` (sm_103a) with nvcc.
 
 Each .cu file under csrc/ is compiled in parallel into _build/, then linked against cuSOLVER
-(the FP64 eigensolver) into paper_1704_04511_gb300/lib/librecon.so. Usage:
+(the FP64 eigensolver) and cuBLAS (the library GEMMs of the IRLS-direct comparison variant)
+into paper_1704_04511_gb300/lib/librecon.so. Usage:
     python -m paper_1704_04511_gb300.build [--force]
 """
 
@@ -21,7 +22,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "librecon.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fft.cu", "cg.cu", "gram.cu", "weight.cu", "hpdinv.cu", "frame_op.cu", "t2fit.cu", "recon.cu",
-           "gram_static.cu"]
+           "gram_static.cu", "variants.cu"]
 HEADERS = ["common.cuh", "kernels.h", "regfft.cuh"]
 
 
@@ -73,7 +74,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if force or jobs or _stale(LIB, objs):
         libdir = _cuda_libdir(nvcc)
         cmd = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + [
-            "-L" + libdir, "-lcusolver", "-Xlinker", "-rpath," + libdir]
+            "-L" + libdir, "-lcusolver", "-lcublas", "-Xlinker", "-rpath," + libdir]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + res.stderr)

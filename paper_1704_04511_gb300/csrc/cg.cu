@@ -43,7 +43,7 @@ RECON_DEV void load_S(const float2* __restrict__ S, size_t npix, size_t px, floa
 template <int N, int M>
 __global__ void __launch_bounds__(kThreads)
 row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
-                 float lam, int T, int P, double* __restrict__ pq_parts,
+                 float lam, int T, int P, int circ, double* __restrict__ pq_parts,
                  const float2* __restrict__ tw_g) {
     extern __shared__ float2 sm[];
     __shared__ double red[kThreads / 32];
@@ -54,7 +54,7 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     const size_t npix = (size_t)P * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
     pdl_wait();
-    const int k = T - M + 1;
+    const int k = circ ? T : T - M + 1;
     float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
     for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
     __syncthreads();  // the previous row's results are stored
@@ -74,9 +74,10 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
 #pragma unroll
             for (int aa = 0; aa < M; ++aa) {
                 const int j = n - M + 1 + aa;
-                if (j < 0 || j >= k) continue;
+                if (!circ && (j < 0 || j >= k)) continue;  // circ: every window
 #pragma unroll
-                for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(n + aa - bb) * N + c], w);
+                for (int bb = 0; bb < M; ++bb)
+                    w = cfma(s[aa][bb], pt[wrap_frame(n + aa - bb, T) * N + c], w);
             }
             float2 q = res[n * N + c];
             q.x = fmaf(lam, w.x, q.x);
@@ -107,7 +108,7 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
 template <int M>
 __global__ void __launch_bounds__(1024)
 row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
-                     float lam, int T, int P, double* __restrict__ pq_parts,
+                     float lam, int T, int P, int circ, double* __restrict__ pq_parts,
                      const float2* __restrict__ tw_g) {
     constexpr int N = 256;
     extern __shared__ float2 sm[];
@@ -120,7 +121,7 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
     const int n = threadIdx.x / 16, j = threadIdx.x % 16;
     const bool live = n < T;  // the block is padded to whole warps (an odd T leaves a half-warp)
     const size_t npix = (size_t)P * N;
-    const int k = T - M + 1;
+    const int k = circ ? T : T - M + 1;
     float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
     for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
     __syncthreads();  // the previous row's results are stored
@@ -150,9 +151,10 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
 #pragma unroll
             for (int aa = 0; aa < M; ++aa) {
                 const int jw = nn - M + 1 + aa;
-                if (jw < 0 || jw >= k) continue;
+                if (!circ && (jw < 0 || jw >= k)) continue;  // circ: every window
 #pragma unroll
-                for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(nn + aa - bb) * N + c], w);
+                for (int bb = 0; bb < M; ++bb)
+                    w = cfma(s[aa][bb], pt[wrap_frame(nn + aa - bb, T) * N + c], w);
             }
             float2 q = res[nn * N + c];
             q.x = fmaf(lam, w.x, q.x);
@@ -234,7 +236,8 @@ coil_row_inv_kernel(float2* t, const float2* __restrict__ p, const float2* __res
                     const int j = n - M + 1 + aa;
                     if (j < 0 || j >= k) continue;
 #pragma unroll
-                    for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(n + aa - bb) * N + c], w);
+                    for (int bb = 0; bb < M; ++bb)
+                    w = cfma(s[aa][bb], pt[wrap_frame(n + aa - bb, T) * N + c], w);
                 }
                 float2 q = acc[n * N + c];
                 q.x = fmaf(lam, w.x, q.x);
@@ -325,11 +328,12 @@ template <int M>
 __global__ void __launch_bounds__(kThreads)
 resid_carry_kernel(float2* __restrict__ r, const float2* __restrict__ x,
                    const float2* __restrict__ aha_x, const float2* __restrict__ S_old,
-                   const float2* __restrict__ S_new, float lam, int first, int T, size_t npix,
+                   const float2* __restrict__ S_new, float lam, int first, int T, int circ,
+                   size_t npix,
                    double* __restrict__ parts, unsigned int* counter,
                    double* __restrict__ rr_out) {
     __shared__ double red[kThreads / 32];
-    const int k = T - M + 1;
+    const int k = circ ? T : T - M + 1;
     float acc = 0.f, comp = 0.f;
     for (size_t px = (size_t)blockIdx.x * blockDim.x + threadIdx.x; px < npix;
          px += (size_t)gridDim.x * blockDim.x) {
@@ -353,9 +357,10 @@ resid_carry_kernel(float2* __restrict__ r, const float2* __restrict__ x,
 #pragma unroll
             for (int a = 0; a < M; ++a) {
                 const int j = n - M + 1 + a;
-                if (j < 0 || j >= k) continue;
+                if (!circ && (j < 0 || j >= k)) continue;  // circ: every window
 #pragma unroll
-                for (int b = 0; b < M; ++b) w = cfma(s[a][b], x[(size_t)(n + a - b) * npix + px], w);
+                for (int b = 0; b < M; ++b)
+                    w = cfma(s[a][b], x[(size_t)wrap_frame(n + a - b, T) * npix + px], w);
             }
             float2 rv = make_float2(0.f, 0.f);
             if (!first) {
@@ -398,8 +403,8 @@ coil_unimodular_kernel(const float2* __restrict__ C, size_t npix, unsigned int* 
 template <int M>
 __global__ void __launch_bounds__(kThreads)
 apply_w_kernel(const float2* __restrict__ x, const float2* __restrict__ S, float2* __restrict__ y,
-               int T, size_t npix) {
-    const int k = T - M + 1;
+               int T, int circ, size_t npix) {
+    const int k = circ ? T : T - M + 1;
     for (size_t px = (size_t)blockIdx.x * blockDim.x + threadIdx.x; px < npix;
          px += (size_t)gridDim.x * blockDim.x) {
         float2 s[M][M];
@@ -409,9 +414,10 @@ apply_w_kernel(const float2* __restrict__ x, const float2* __restrict__ S, float
 #pragma unroll
             for (int a = 0; a < M; ++a) {
                 const int j = n - M + 1 + a;
-                if (j < 0 || j >= k) continue;
+                if (!circ && (j < 0 || j >= k)) continue;  // circ: every window
 #pragma unroll
-                for (int b = 0; b < M; ++b) w = cfma(s[a][b], x[(size_t)(n + a - b) * npix + px], w);
+                for (int b = 0; b < M; ++b)
+                    w = cfma(s[a][b], x[(size_t)wrap_frame(n + a - b, T) * npix + px], w);
             }
             y[(size_t)n * npix + px] = w;
         }
@@ -450,7 +456,7 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
             if (e != cudaSuccess) return e;
             pq->n = grid;
             return launch_pdl(k, dim3(grid), dim3(tpad * 16), smem256, st, t, p, S, lam, d.T, rows,
-                              pq->parts, tw.twQ);
+                              d.circ, pq->parts, tw.twQ);
         }
     }
     auto k = row_inv_w_kernel<N, M>;
@@ -462,8 +468,8 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
     cudaError_t e = row_grid(k, kThreads, smem, rows, &grid);
     if (e != cudaSuccess) return e;
     pq->n = grid;
-    return launch_pdl(k, dim3(grid), dim3(kThreads), smem, st, t, p, S, lam, d.T, rows, pq->parts,
-                      tw.twQ);
+    return launch_pdl(k, dim3(grid), dim3(kThreads), smem, st, t, p, S, lam, d.T, rows, d.circ,
+                      pq->parts, tw.twQ);
 }
 
 template <int N>
@@ -608,7 +614,8 @@ cudaError_t launch_resid_carry(const Dims& d, float2* r, const float2* x, const 
 #define CASE(MM)                                                                              \
     case MM:                                                                                  \
         resid_carry_kernel<MM><<<g, kThreads, 0, st>>>(r, x, aha_x, S_old, S_new, lam, first, \
-                                                       d.T, d.pixels(), rs.parts, rs.counter, \
+                                                       d.T, d.circ, d.pixels(), rs.parts,     \
+                                                       rs.counter,                            \
                                                        rr_out);                               \
         break;
     switch (d.M) {
@@ -631,7 +638,7 @@ cudaError_t launch_apply_w(const Dims& d, const float2* x, const float2* S, floa
                            cudaStream_t st) {
     const int g = pix_grid(d.pixels());
 #define CASE(MM)                                                                        \
-    case MM: apply_w_kernel<MM><<<g, kThreads, 0, st>>>(x, S, y, d.T, d.pixels()); break;
+    case MM: apply_w_kernel<MM><<<g, kThreads, 0, st>>>(x, S, y, d.T, d.circ, d.pixels()); break;
     switch (d.M) {
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
         default: return cudaErrorInvalidValue;

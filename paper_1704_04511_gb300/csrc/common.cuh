@@ -15,6 +15,13 @@
 RECON_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 RECON_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Frame index of the banded W / the pair products, wrapped into [0, T) for the fully circulant
+// (time-circular) lifting; for the valid lifting every index already lies in [0, T).
+RECON_DEV int wrap_frame(int f, int T) {
+    f += f < 0 ? T : 0;
+    return f >= T ? f - T : f;
+}
+
 // ------------------------------------------------------------------------------------------
 // complex helpers (float2 / double2 hold (re, im))
 // ------------------------------------------------------------------------------------------

@@ -202,7 +202,7 @@ cudaError_t launch_frame_N(const Dims& d, const Twiddles& tw, const float2* r, f
 }  // namespace
 
 bool frame_op_supported(const Dims& d) {
-    if (d.P != d.Q || d.R != 1 || d.nc != 1) return false;
+    if (d.P != d.Q || d.R != 1 || d.nc != 1 || d.circ) return false;
     switch (d.P) {
         case 32: case 64: case 128: case 192: case 256: return true;
         default: return false;

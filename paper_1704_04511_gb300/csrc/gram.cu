@@ -29,11 +29,12 @@ constexpr int kWarps = kThreads / 32;
 
 template <int M>
 __global__ void __launch_bounds__(kThreads)
-gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2,
+gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int circ,
                  const float2* __restrict__ twQ, double2* __restrict__ Y) {
     constexpr int NP = M * (M + 1) / 2;
     extern __shared__ float2 sm[];
-    const int k = T - M + 1, L2 = 2 * N2 - 1;
+    // circ: T windows with frame indices taken mod T (the fully circulant lifting)
+    const int k = circ ? T : T - M + 1, L2 = 2 * N2 - 1;
     float2* xs = sm;                         // [T][Q] row r1 of every frame
     float2* qp = xs + (size_t)T * Q;         // [NP][Q] pair products
     float2* tw = qp + (size_t)NP * Q;        // [Q]
@@ -52,7 +53,7 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2,
 #pragma unroll
         for (int m = 1; m < M; ++m) w[m] = xs[(M - 1 - m) * Q + c];
         for (int j = 0; j < k; ++j) {
-            w[0] = xs[(j + M - 1) * Q + c];
+            w[0] = xs[wrap_frame(j + M - 1, T) * Q + c];
             int e = 0;
 #pragma unroll
             for (int a = 0; a < M; ++a)
@@ -207,7 +208,8 @@ cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, doub
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem);                                         \
         if (e != cudaSuccess) return e;                                                          \
-        k<<<d.rows(), kThreads, smem, st>>>(x, d.T, d.rows(), d.Q, d.N2, tw.twQ, lag_part);      \
+        k<<<d.rows(), kThreads, smem, st>>>(x, d.T, d.rows(), d.Q, d.N2, d.circ, tw.twQ,       \
+                                            lag_part);                                           \
         break;                                                                                   \
     }
     switch (d.M) {

@@ -19,7 +19,8 @@ struct Dims {
     int nc = 1;  // receiver coils (Eq. measurement-ij); the transform buffer holds nc series
     int R = 1;   // depth of a volume (third spatial axis, circular like the other two)
     int N3 = 1;  // filter taps along the depth
-    int k() const { return T - M + 1; }
+    int circ = 0;  // 1: lifting circular in time as well (the fully circulant GIRAF form)
+    int k() const { return circ ? T : T - M + 1; }
     int npair() const { return M * (M + 1) / 2; }
     int L1() const { return 2 * N1 - 1; }
     int L2() const { return 2 * N2 - 1; }
@@ -194,5 +195,33 @@ struct T2Times {
 // the per-pixel fit (NaN outside the foreground |x_0| > frac max |x_0|); amp may be null.
 cudaError_t launch_t2fit(const Dims& d, const float2* x, const T2Times& tm, float frac, int n_gn,
                          unsigned int* amax_scratch, float* t2, float* amp, cudaStream_t st);
+
+// ---- variants.cu (comparison methods of Sec. IV) ----
+// HLR-Voxel weight per pixel (S = H_r^T into [pair][P][Q]); eps_mode 0: eps_in[px], 1: eps0 =
+// frac * lambda_max(G_r) into eps_state, 2: eps_state /= gamma. G_out / lmax_out may be null.
+cudaError_t launch_voxel_weight(const Dims& d, const float2* x, double p, const double* eps_in,
+                                double* eps_state, int eps_mode, double frac, double gamma,
+                                float2* S, double2* G_out, double* lmax_out, cudaStream_t st);
+// IRLS-direct: rows of the exact (valid) lifting, (T-M+1)(P-N1+1)(Q-N2+1)
+size_t direct_rows(const Dims& d);
+// Tm (rows x s, column-major) of x_hat; complex128 when fp64, else complex64
+cudaError_t launch_direct_lift(const Dims& d, const float2* xh, void* Tm, int fp64, cudaStream_t st);
+// z = mask * yh (mask may be null: no data term) + lam T^*(Y)
+cudaError_t launch_direct_unlift(const Dims& d, const float2* Y, const float2* yh,
+                                 const uint8_t* mask, float lam, float2* z, cudaStream_t st);
+cudaError_t launch_herm_fill(double2* G, int s, cudaStream_t st);
+cudaError_t launch_form_H(const double2* U, const double* evals, const double* eps, double p,
+                          int s, double2* H, cudaStream_t st);
+cudaError_t launch_h_delta(const double2* H_new, const double2* H_old, float2* delta, float2* h32,
+                           size_t n, cudaStream_t st);
+cudaError_t launch_dcg_dot(const float2* a, const float2* b, size_t n, const RedSlot& rs,
+                           double* out, cudaStream_t st);
+cudaError_t launch_dcg_resid(float2* r, const float2* w, int first, size_t n, const RedSlot& rs,
+                             double* rr_out, cudaStream_t st);
+cudaError_t launch_dcg_update(float2* x, float2* r, const float2* p, const float2* q, size_t n,
+                              const double* rr, const double* pq, const RedSlot& rs,
+                              double* rr_out, cudaStream_t st);
+cudaError_t launch_dcg_pupdate(float2* p, const float2* r, size_t n, const double* rr_new,
+                               const double* rr_old, int first, cudaStream_t st);
 
 }  // namespace recon

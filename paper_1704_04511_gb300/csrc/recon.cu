@@ -13,6 +13,7 @@
 // which equals A^H b - (A^H A + lam W^(n+1)) x^(n) in exact arithmetic but avoids forming it by
 // cancellation in FP32 (the two terms agree to ~1e-5 relative near convergence).
 #include <cuda_runtime.h>
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <cmath>
@@ -55,6 +56,7 @@ struct recon_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cusolverDnHandle_t solver = nullptr;
+    cublasHandle_t blas = nullptr;  // library GEMMs of the IRLS-direct variant (slot 0 stream)
     std::string err;
     std::map<int, TwTable> tw;
     std::map<std::string, Buf> bufs;
@@ -65,7 +67,7 @@ struct recon_ctx {
         int T, P, Q, N1, N2, M, irls, cg, bf16, method, R, N3;
         double lambda, p, gamma, eps0_frac;
         const void *kspace, *masks, *out, *coils;
-        int nc, coil_proj;
+        int nc, coil_proj, circ, variant;
         unsigned long ws_gen;
     };
     GraphKey gkey = {};
@@ -581,6 +583,8 @@ struct Solve {
     const recon_params* prm;
     const float2* coils = nullptr;  // [nc][P][Q] for the multi-coil operator
     bool coil_proj = false;         // one coil with |C| = 1: A A^H is a projection
+    int variant = RECON_VARIANT_PROPOSED;  // HLR-Voxel: per-pixel weights instead of the Gram
+    double* veps = nullptr;         // HLR-Voxel: per-pixel eps state [R P Q]
 };
 
 // Twiddles, eigensolver handle and workspace of one solve on the active slot (no stream work).
@@ -599,6 +603,15 @@ int solve_prepare(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t
         if (rc) return rc;
     }
     return get_work(c, d, prm->cg, prm->irls, true, eig, &sv->w);
+}
+
+// HLR-Voxel: the per-pixel eps state of a solve (after solve_prepare).
+int prepare_voxel(recon_ctx* c, Solve* sv) {
+    sv->variant = RECON_VARIANT_HLR_VOXEL;
+    void* ptr = nullptr;
+    int rc = ensure(c, "veps", sv->d.pixels() * sizeof(double), &ptr);
+    sv->veps = reinterpret_cast<double*>(ptr);
+    return rc;
 }
 
 // Status reset and x0 = A^H b (Algorithm 1 initialisation). Enqueues only.
@@ -624,13 +637,22 @@ int solve_iter(recon_ctx* c, Solve& sv, int n) {
     float2* S[2] = {w.S0, w.S1};
     float2* S_new = S[n & 1];
     const float2* S_old = n == 0 ? nullptr : S[(n + 1) & 1];
-    {
-        ProfScope ps(c, RECON_PROF_GRAM);
-        RC_CUDA(recon::launch_gram(d, sv.tw, sv.x, w.lag_part, w.gblocks, nullptr, w.G, c->stream));
+    if (sv.variant == RECON_VARIANT_HLR_VOXEL) {
+        // one M x M Gram, eigendecomposition and weight per pixel; eps_r^(0) from lambda_max
+        ProfScope ps(c, RECON_PROF_S);
+        RC_CUDA(recon::launch_voxel_weight(d, sv.x, sv.prm->p, nullptr, sv.veps, n == 0 ? 1 : 2,
+                                           sv.prm->eps0_frac, sv.prm->gamma, S_new, nullptr,
+                                           nullptr, c->stream));
+    } else {
+        {
+            ProfScope ps(c, RECON_PROF_GRAM);
+            RC_CUDA(recon::launch_gram(d, sv.tw, sv.x, w.lag_part, w.gblocks, nullptr, w.G,
+                                       c->stream));
+        }
+        int rc = weight_step(c, d, sv.tw, w, sv.prm->p, n == 0, sv.prm->eps0_frac, sv.prm->gamma,
+                             0, 0.0, S_new, n);
+        if (rc) return rc;
     }
-    int rc = weight_step(c, d, sv.tw, w, sv.prm->p, n == 0, sv.prm->eps0_frac, sv.prm->gamma, 0,
-                         0.0, S_new, n);
-    if (rc) return rc;
     return cg_block(c, d, sv.tw, w, sv.masks, S_old, S_new, (float)sv.prm->lambda, sv.x, n == 0,
                     sv.prm->cg, sv.coils, sv.coil_proj);
 }
@@ -655,6 +677,7 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     k.lambda = prm->lambda; k.p = prm->p; k.gamma = prm->gamma; k.eps0_frac = prm->eps0_frac;
     k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
     k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
+    k.circ = sv.d.circ; k.variant = sv.variant;
     if (!c->gexec || std::memcmp(&k, &c->gkey, sizeof(k)) != 0) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -748,7 +771,7 @@ size_t bytes_needed(const Dims& d) {
 }
 
 int solve_impl(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* masks,
-               const recon_params* prm, void* image_out) {
+               const recon_params* prm, void* image_out, int variant = RECON_VARIANT_PROPOSED) {
     int rc = set_device(c);
     if (rc) return rc;
     rc = select_slot(c, 0);
@@ -756,10 +779,187 @@ int solve_impl(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* m
     Solve sv;
     rc = solve_prepare(c, d, kspace, masks, prm, image_out, &sv);
     if (rc) return rc;
+    if (variant == RECON_VARIANT_HLR_VOXEL) {
+        rc = prepare_voxel(c, &sv);
+        if (rc) return rc;
+    }
     rc = solve_enqueue_all(c, sv);
     if (rc) return rc;
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return solve_check(c, sv);
+}
+
+// ---- IRLS-direct (Sec. IV-A): the exact valid lifting, explicit, with library GEMMs ----
+
+int ensure_blas(recon_ctx* c) {
+    if (!c->blas && cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) {
+        c->blas = nullptr;
+        return fail(c, RECON_ECUDA, "cublasCreate failed");
+    }
+    if (cublasSetStream(c->blas, c->stream) != CUBLAS_STATUS_SUCCESS)
+        return fail(c, RECON_ECUDA, "cublasSetStream failed");
+    return RECON_OK;
+}
+
+#define RC_BLAS(call)                                                          \
+    do {                                                                       \
+        if ((call) != CUBLAS_STATUS_SUCCESS) return fail(c, RECON_ECUDA, #call); \
+    } while (0)
+
+// Buffers of the direct variant (slot 0).
+struct DirectWork {
+    float2 *yh, *z, *h32, *hd32;
+    double2 *H, *Hold;
+    void* lift;  // rows x s complex128 for the Gram, or two rows x s complex64 (lifting, product)
+};
+
+int get_direct_work(recon_ctx* c, const Dims& d, DirectWork* dw) {
+    void* ptr;
+    int rc;
+    const size_t vec = d.elems() * sizeof(float2);
+    const size_t ss = (size_t)d.s() * d.s();
+#define GETD(name, bytes, field, type)    \
+    rc = ensure(c, name, (bytes), &ptr); \
+    if (rc) return rc;                   \
+    dw->field = reinterpret_cast<type>(ptr);
+    GETD("d_yh", vec, yh, float2*);
+    GETD("d_z", vec, z, float2*);
+    GETD("d_h32", ss * sizeof(float2), h32, float2*);
+    GETD("d_hd32", ss * sizeof(float2), hd32, float2*);
+    GETD("d_H", ss * sizeof(double2), H, double2*);
+    GETD("d_Hold", ss * sizeof(double2), Hold, double2*);
+    GETD("d_lift", recon::direct_rows(d) * d.s() * sizeof(double2), lift, void*);
+#undef GETD
+    return RECON_OK;
+}
+
+// G = T^H T of the exact lifting of F x (lower triangle by the library rank-k product, then the
+// upper triangle filled).
+int direct_gram(recon_ctx* c, const Dims& d, const Twiddles& tw, DirectWork& dw, const float2* x,
+                double2* G) {
+    const int s = d.s();
+    const long long m = (long long)recon::direct_rows(d);
+    RC_CUDA(recon::launch_fft2(d, tw, x, dw.yh, 0, c->stream));
+    RC_CUDA(recon::launch_direct_lift(d, dw.yh, dw.lift, 1, c->stream));
+    const double one = 1.0, zero = 0.0;
+    RC_BLAS(cublasZherk(c->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, s, (int)m, &one,
+                        reinterpret_cast<const cuDoubleComplex*>(dw.lift), (int)m, &zero,
+                        reinterpret_cast<cuDoubleComplex*>(G), s));
+    RC_CUDA(recon::launch_herm_fill(G, s, c->stream));
+    return RECON_OK;
+}
+
+// out = F^H( mask * F v + lam T^*(T(F v) h) ), h complex64 s x s; mask = NULL drops the data term.
+int direct_op(recon_ctx* c, const Dims& d, const Twiddles& tw, DirectWork& dw, const float2* v,
+              const float2* h, const uint8_t* mask, float lam, float2* out) {
+    const int s = d.s();
+    const long long m = (long long)recon::direct_rows(d);
+    float2* Tm = reinterpret_cast<float2*>(dw.lift);
+    float2* Y = Tm + (size_t)m * s;
+    RC_CUDA(recon::launch_fft2(d, tw, v, dw.yh, 0, c->stream));
+    RC_CUDA(recon::launch_direct_lift(d, dw.yh, Tm, 0, c->stream));
+    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+    RC_BLAS(cublasCgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)m, s, s, &one,
+                        reinterpret_cast<const cuComplex*>(Tm), (int)m,
+                        reinterpret_cast<const cuComplex*>(h), s, &zero,
+                        reinterpret_cast<cuComplex*>(Y), (int)m));
+    RC_CUDA(recon::launch_direct_unlift(d, Y, dw.yh, mask, lam, dw.z, c->stream));
+    RC_CUDA(recon::launch_fft2(d, tw, dw.z, out, 1, c->stream));
+    return RECON_OK;
+}
+
+// H = (G + eps I)^(p/2-1) into dw.H from G (consumed). eps: the Sec. III-C schedule (first:
+// eps0_frac * lambda_max, else eps / gamma) unless eps_set.
+int direct_weight(recon_ctx* c, const Dims& d, Work& w, DirectWork& dw, double p, int first,
+                  double frac, double gamma, int eps_set, double eps_value, int it) {
+    const int s = d.s();
+    const size_t gbytes = (size_t)s * s * sizeof(double2);
+    if (eps_set)
+        RC_CUDA(cudaMemcpyAsync(w.eps, &eps_value, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (w.use_eig) {
+        int rc = run_eig(c, s, w, w.info + it);
+        if (rc) return rc;
+        if (!eps_set) RC_CUDA(recon::launch_eps(w.evals + s - 1, w.eps, first, frac, gamma, c->stream));
+        RC_CUDA(recon::launch_form_H(w.G, w.evals, w.eps, p, s, dw.H, c->stream));
+    } else {
+        if (!eps_set) {
+            if (first)
+                RC_CUDA(recon::launch_lanczos_lmax(d, w.G, w.lanc, w.lmax, w.kerr + 2 * it + 1, c->stream));
+            RC_CUDA(recon::launch_eps(w.lmax, w.eps, first, frac, gamma, c->stream));
+        }
+        RC_CUDA(recon::launch_hpd_inverse(d, w.G, w.eps, w.hpd, w.kerr + 2 * it, c->stream));
+        RC_CUDA(cudaMemcpyAsync(dw.H, w.G, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return RECON_OK;
+}
+
+int direct_prepare(recon_ctx* c, const Dims& d, const recon_params* prm, int n_cg, Twiddles* tw,
+                   Work* w, DirectWork* dw) {
+    int rc = set_device(c);
+    if (rc) return rc;
+    rc = get_twiddles(c, d, tw);
+    if (rc) return rc;
+    rc = ensure_blas(c);
+    if (rc) return rc;
+    const bool eig = prm ? wants_eig(prm->p, prm->weight_method) : false;
+    if (eig) {
+        rc = ensure_solver(c);
+        if (rc) return rc;
+    }
+    rc = get_work(c, d, n_cg, prm ? prm->irls : 1, true, eig, w);
+    if (rc) return rc;
+    return get_direct_work(c, d, dw);
+}
+
+// Algorithm 1 with the exact lifting: x0 = A^H b; per iteration the Gram, the weight H, the
+// carried residual r += lam W_{H_old - H_new} x (r0 = -lam W x0), n_cg plain CG steps.
+int solve_direct(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* masks,
+                 const recon_params* prm, void* image_out) {
+    Twiddles tw;
+    Work w;
+    DirectWork dw;
+    int rc = direct_prepare(c, d, prm, prm->cg, &tw, &w, &dw);
+    if (rc) return rc;
+    rc = reset_status(c, w);
+    if (rc) return rc;
+    float2* x = reinterpret_cast<float2*>(image_out);
+    const size_t n = d.elems();
+    const size_t ss = (size_t)d.s() * d.s();
+    const float lam = (float)prm->lambda;
+    const recon::RedSlot rs{w.parts, w.counter};
+    RC_CUDA(recon::launch_adjoint(d, tw, kspace, prm->kspace_bf16, masks, w.t, x, c->stream));
+    for (int it = 0; it < prm->irls; ++it) {
+        rc = direct_gram(c, d, tw, dw, x, w.G);
+        if (rc) return rc;
+        rc = direct_weight(c, d, w, dw, prm->p, it == 0, prm->eps0_frac, prm->gamma, 0, 0.0, it);
+        if (rc) return rc;
+        RC_CUDA(recon::launch_h_delta(dw.H, it == 0 ? nullptr : dw.Hold, dw.hd32, dw.h32, ss,
+                                      c->stream));
+        RC_CUDA(cudaMemcpyAsync(dw.Hold, dw.H, ss * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                c->stream));
+        // residual carry: r = (first ? 0 : r) + lam W_{H_old - H_new} x
+        rc = direct_op(c, d, tw, dw, x, dw.hd32, nullptr, lam, w.t);
+        if (rc) return rc;
+        RC_CUDA(recon::launch_dcg_resid(w.r, w.t, it == 0, n, rs, w.rr, c->stream));
+        for (int k = 0; k < prm->cg; ++k) {
+            RC_CUDA(recon::launch_dcg_pupdate(w.p, w.r, n, w.rr + k, k > 0 ? w.rr + k - 1 : w.rr,
+                                              k == 0, c->stream));
+            rc = direct_op(c, d, tw, dw, w.p, dw.h32, masks, lam, w.t);
+            if (rc) return rc;
+            RC_CUDA(recon::launch_dcg_dot(w.p, w.t, n, rs, w.pq + k, c->stream));
+            RC_CUDA(recon::launch_dcg_update(x, w.r, w.p, w.t, n, w.rr + k, w.pq + k, rs,
+                                             w.rr + k + 1, c->stream));
+        }
+    }
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    rc = check_status(c, w, prm->irls);
+    if (rc) return rc;
+    if (prm->irls > 0) {
+        double rr = 0.0;
+        RC_CUDA(cudaMemcpy(&rr, w.rr + prm->cg, sizeof(double), cudaMemcpyDeviceToHost));
+        if (!std::isfinite(rr)) return fail(c, RECON_ENUMERIC, "non-finite residual in the iteration");
+    }
+    return RECON_OK;
 }
 
 int adjoint_impl(recon_ctx* c, const Dims& d, const void* kspace, int kspace_bf16,
@@ -878,6 +1078,14 @@ int apply_normal_impl(recon_ctx* c, const Dims& d, const uint8_t* masks, const v
     return RECON_OK;
 }
 
+int check_variant(recon_ctx* c, int variant, const recon_filter& f) {
+    if (variant < RECON_VARIANT_PROPOSED || variant > RECON_VARIANT_DIRECT)
+        return fail(c, RECON_EINVAL, "unknown variant");
+    if (variant == RECON_VARIANT_HLR_VOXEL && (f.N1 != 1 || f.N2 != 1))
+        return fail(c, RECON_EINVAL, "HLR-Voxel has no spatial taps: need N1 = N2 = 1");
+    return RECON_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -946,6 +1154,7 @@ void recon_destroy(recon_ctx* c) {
     }
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->solver) cusolverDnDestroy(c->solver);
+    if (c->blas) cublasDestroy(c->blas);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -1330,6 +1539,133 @@ int recon_apply_normal3(recon_ctx* c, recon_dims3 dd, recon_filter3 f, const uin
     Dims d;
     int rc = check_dims3(c, dd, &f, &d);
     return rc ? rc : apply_normal_impl(c, d, masks, S, lambda, x, y);
+}
+
+// ---- comparison methods (Sec. IV) ----
+
+int recon_solve_variant(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* masks,
+                        recon_filter f, const recon_params* prm, int variant, void* image_out) {
+    if (!c) return RECON_EINVAL;
+    if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_params(c, dd, f, prm, &d);
+    if (!rc) rc = check_variant(c, variant, f);
+    if (rc) return rc;
+    if (variant == RECON_VARIANT_DIRECT) return solve_direct(c, d, kspace, masks, prm, image_out);
+    d.circ = variant == RECON_VARIANT_GIRAF;
+    return solve_impl(c, d, kspace, masks, prm, image_out, variant);
+}
+
+int recon_gram_variant(recon_ctx* c, recon_dims dd, recon_filter f, int variant, const void* x,
+                       void* G_out) {
+    if (!c) return RECON_EINVAL;
+    if (!x || !G_out) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (!rc) rc = check_variant(c, variant, f);
+    if (rc) return rc;
+    if (variant == RECON_VARIANT_PROPOSED || variant == RECON_VARIANT_GIRAF) {
+        d.circ = variant == RECON_VARIANT_GIRAF;
+        return gram_impl(c, d, x, G_out, nullptr);
+    }
+    rc = set_device(c);
+    if (rc) return rc;
+    if (variant == RECON_VARIANT_HLR_VOXEL) {
+        void *S, *st;
+        rc = ensure(c, "vS", (size_t)d.npair() * d.pixels() * sizeof(float2), &S);
+        if (!rc) rc = ensure(c, "veps_g", d.pixels() * sizeof(double), &st);
+        if (rc) return rc;
+        RC_CUDA(recon::launch_voxel_weight(d, (const float2*)x, 0.0, nullptr, (double*)st, 1, 1.0,
+                                           1.0, (float2*)S, (double2*)G_out, nullptr, c->stream));
+        RC_CUDA(cudaStreamSynchronize(c->stream));
+        return RECON_OK;
+    }
+    Twiddles tw;
+    Work w;
+    DirectWork dw;
+    rc = direct_prepare(c, d, nullptr, 1, &tw, &w, &dw);
+    if (rc) return rc;
+    rc = direct_gram(c, d, tw, dw, (const float2*)x, (double2*)G_out);
+    if (rc) return rc;
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int recon_voxel_weight(recon_ctx* c, recon_dims dd, int M, const void* x, const double* eps,
+                       double p, void* S_out, double* lmax_out) {
+    if (!c) return RECON_EINVAL;
+    if (!x || !eps || !S_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (!(p >= 0.0 && p <= 1.0)) return fail(c, RECON_EINVAL, "need 0 <= p <= 1");
+    Dims d;
+    const recon_filter f{1, 1, M};
+    int rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    rc = set_device(c);
+    if (rc) return rc;
+    RC_CUDA(recon::launch_voxel_weight(d, (const float2*)x, p, eps, nullptr, 0, 0.0, 1.0,
+                                       (float2*)S_out, nullptr, lmax_out, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+int recon_weight_direct(recon_ctx* c, recon_dims dd, recon_filter f, const void* G_in,
+                        double eps_in, double p, int method, void* H_out, double* eps_out) {
+    if (!c) return RECON_EINVAL;
+    int rc = weight_args(c, G_in, eps_in, p, method, H_out, nullptr);
+    if (rc) return rc;
+    Dims d;
+    rc = check_dims(c, dd, &f, &d);
+    if (rc) return rc;
+    recon_params prm{};
+    prm.irls = 1;
+    prm.cg = 1;
+    prm.p = p;
+    prm.weight_method = method;
+    Twiddles tw;
+    Work w;
+    DirectWork dw;
+    rc = direct_prepare(c, d, &prm, 1, &tw, &w, &dw);
+    if (rc) return rc;
+    rc = reset_status(c, w);
+    if (rc) return rc;
+    const size_t gbytes = (size_t)d.s() * d.s() * sizeof(double2);
+    RC_CUDA(cudaMemcpyAsync(w.G, G_in, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+    const bool set = eps_in >= 0.0;
+    rc = direct_weight(c, d, w, dw, p, 1, set ? 0.0 : -eps_in, 1.0, set, eps_in, 0);
+    if (rc) return rc;
+    RC_CUDA(cudaMemcpyAsync(H_out, dw.H, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    rc = check_status(c, w, 1);
+    if (rc) return rc;
+    if (eps_out) RC_CUDA(cudaMemcpy(eps_out, w.eps, sizeof(double), cudaMemcpyDeviceToHost));
+    return RECON_OK;
+}
+
+int recon_apply_normal_variant(recon_ctx* c, recon_dims dd, recon_filter f, int variant,
+                               const uint8_t* masks, const void* W, double lambda, const void* x,
+                               void* y) {
+    if (!c) return RECON_EINVAL;
+    if (!masks || !W || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
+    Dims d;
+    int rc = check_dims(c, dd, &f, &d);
+    if (!rc) rc = check_variant(c, variant, f);
+    if (rc) return rc;
+    if (variant != RECON_VARIANT_DIRECT) {
+        d.circ = variant == RECON_VARIANT_GIRAF;
+        return apply_normal_impl(c, d, masks, W, lambda, x, y);
+    }
+    Twiddles tw;
+    Work w;
+    DirectWork dw;
+    rc = direct_prepare(c, d, nullptr, 1, &tw, &w, &dw);
+    if (rc) return rc;
+    const size_t ss = (size_t)d.s() * d.s();
+    RC_CUDA(recon::launch_h_delta((const double2*)W, nullptr, dw.hd32, dw.h32, ss, c->stream));
+    rc = direct_op(c, d, tw, dw, (const float2*)x, dw.h32, masks, (float)lambda, (float2*)y);
+    if (rc) return rc;
+    RC_CUDA(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
 }
 
 int recon_apply_w(recon_ctx* c, recon_dims dd, recon_filter f, const void* S, const void* x,

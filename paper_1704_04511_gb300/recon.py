@@ -31,6 +31,10 @@ RECON_ETIMEOUT = -5
 RECON_EBUSY = -6
 RECON_WEIGHT_AUTO = 0
 RECON_WEIGHT_EIG = 1
+RECON_VARIANT_PROPOSED = 0
+RECON_VARIANT_GIRAF = 1
+RECON_VARIANT_HLR_VOXEL = 2
+RECON_VARIANT_DIRECT = 3
 
 _ERR_NAMES = {RECON_EINVAL: "RECON_EINVAL", RECON_ENOMEM: "RECON_ENOMEM",
               RECON_ECUDA: "RECON_ECUDA", RECON_ENUMERIC: "RECON_ENUMERIC",
@@ -43,7 +47,8 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_solve_batch", "recon_set_option", "recon_submit", "recon_poll", "recon_t2fit",
             "recon_solve_coils", "recon_adjoint_coils", "recon_apply_normal_coils",
             "recon_bytes_needed3", "recon_solve3", "recon_adjoint3", "recon_fft3", "recon_gram3",
-            "recon_weight3", "recon_apply_normal3")
+            "recon_weight3", "recon_apply_normal3", "recon_solve_variant", "recon_gram_variant",
+            "recon_voxel_weight", "recon_weight_direct", "recon_apply_normal_variant")
 
 PROF_KINDS = 15
 
@@ -130,6 +135,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_gram3": (i, [vp, dims3, filt3, vp, vp, vp]),
             "recon_weight3": (i, [vp, dims3, filt3, vp, d, d, i, vp, vp, vp, ctypes.POINTER(d)]),
             "recon_apply_normal3": (i, [vp, dims3, filt3, vp, vp, d, vp, vp]),
+            "recon_solve_variant": (i, [vp, dims, vp, vp, filt, ctypes.POINTER(recon_params), i,
+                                        vp]),
+            "recon_gram_variant": (i, [vp, dims, filt, i, vp, vp]),
+            "recon_voxel_weight": (i, [vp, dims, i, vp, vp, d, vp, vp]),
+            "recon_weight_direct": (i, [vp, dims, filt, vp, d, d, i, vp, ctypes.POINTER(d)]),
+            "recon_apply_normal_variant": (i, [vp, dims, filt, i, vp, vp, d, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -343,6 +354,49 @@ def recon_t2fit(ctx, x, times_ms, t2_out, amp_out=None, fg_frac: float = 0.1, n_
     t = (ctypes.c_double * len(times_ms))(*[float(v) for v in times_ms])
     _check(ctx, load_library().recon_t2fit(ctx, _dims(x), _ptr(x), t, float(fg_frac), int(n_gn),
                                            _ptr(t2_out), _ptr(amp_out)))
+
+
+# ---- comparison methods (RECON_VARIANT_*) ----
+
+def recon_solve_variant(ctx, kspace, masks, filt, lam: float, p: float, irls: int, cg: int,
+                        image_out, variant: int, gamma: float = 1.4, eps0_frac: float = 0.01,
+                        weight_method: int = RECON_WEIGHT_AUTO) -> None:
+    import torch
+    bf16 = kspace.dtype == torch.bfloat16
+    prm = recon_params(irls=int(irls), cg=int(cg), lambda_=float(lam), p=float(p),
+                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=int(bf16),
+                       weight_method=int(weight_method))
+    _check(ctx, load_library().recon_solve_variant(ctx, _dims(masks), _ptr(kspace), _ptr(masks),
+                                                   _filt(filt), ctypes.byref(prm), int(variant),
+                                                   _ptr(image_out)))
+
+
+def recon_gram_variant(ctx, x, filt, variant: int, G_out) -> None:
+    _check(ctx, load_library().recon_gram_variant(ctx, _dims(x), _filt(filt), int(variant),
+                                                  _ptr(x), _ptr(G_out)))
+
+
+def recon_voxel_weight(ctx, x, M: int, eps, p: float, S_out, lmax_out=None) -> None:
+    """HLR-Voxel weight: eps (P, Q) float64 CUDA tensor, S_out (npair, P, Q) complex64."""
+    _check(ctx, load_library().recon_voxel_weight(ctx, _dims(x), int(M), _ptr(x), _ptr(eps),
+                                                  float(p), _ptr(S_out), _ptr(lmax_out)))
+
+
+def recon_weight_direct(ctx, shape, filt, G_in, eps_in: float, p: float, H_out,
+                        method: int = RECON_WEIGHT_AUTO) -> float:
+    T, P, Q = shape
+    eps_used = ctypes.c_double(0.0)
+    _check(ctx, load_library().recon_weight_direct(ctx, recon_dims(P=P, Q=Q, T=T), _filt(filt),
+                                                   _ptr(G_in), float(eps_in), float(p),
+                                                   int(method), _ptr(H_out),
+                                                   ctypes.byref(eps_used)))
+    return eps_used.value
+
+
+def recon_apply_normal_variant(ctx, masks, filt, variant: int, W, lam: float, x, y) -> None:
+    _check(ctx, load_library().recon_apply_normal_variant(ctx, _dims(x), _filt(filt), int(variant),
+                                                          _ptr(masks), _ptr(W), float(lam),
+                                                          _ptr(x), _ptr(y)))
 
 
 # ---- volumes (T, R, P, Q) ----
