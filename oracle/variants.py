@@ -16,7 +16,12 @@ x_hat = F x unitary, A = mask * F):
   * IRLS-direct (Sec. IV-A: Eq. x-update and Eq. weight-update solved without the FFT
     approximations): the exact multi-fold Toeplitz matrix, valid linear convolution in all three
     dimensions (rows Gamma:Lambda of Sec. II-B; slr.lift_linear), its Gram G = T^H T, the weight
-    H, and the penalty gradient F^H T^*(T(F x) H) with T^* the adjoint of the lifting.
+    H, and the penalty gradient F^H C^H T^*(T(C F x) H) with T^* the adjoint of the lifting. The
+    exact lifting is not shift invariant, so it is taken on the centred k-space C F x (C =
+    fftshift, DC at (P/2, Q/2)): the grid Gamma of Sec. II-B holds the Fourier samples around
+    k = 0, and its boundaries, where the circulant approximation is justified by the decay of
+    the coefficients, are the highest frequencies. (For the circulant liftings the centring
+    changes nothing.)
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may use it.
 """
@@ -194,16 +199,23 @@ def unlift_direct(Y: np.ndarray, T: int, P: int, Q: int, N1: int, N2: int, M: in
     return z
 
 
+def centred_kspace(x: np.ndarray) -> np.ndarray:
+    """C F x: the unitary 2-D DFT of every frame with DC moved to (P/2, Q/2)."""
+    return np.fft.fftshift(slr.F2(x), axes=(-2, -1))
+
+
 def gram_direct(x: np.ndarray, N1: int, N2: int, M: int) -> np.ndarray:
-    Tm = lift_direct(slr.F2(x), N1, N2, M)
+    Tm = lift_direct(centred_kspace(x), N1, N2, M)
     return Tm.conj().T @ Tm
 
 
 def apply_W_direct(x: np.ndarray, H: np.ndarray, N1: int, N2: int, M: int) -> np.ndarray:
-    """Gradient of Tr(H T(F x)^H T(F x)) with respect to conj(x): F^H T^*(T(F x) H)."""
+    """Gradient of Tr(H T(C F x)^H T(C F x)) with respect to conj(x):
+    F^H C^H T^*(T(C F x) H)."""
     T, P, Q = x.shape
-    Tm = lift_direct(slr.F2(x), N1, N2, M)
-    return slr.F2H(unlift_direct(Tm @ H, T, P, Q, N1, N2, M))
+    Tm = lift_direct(centred_kspace(x), N1, N2, M)
+    z = unlift_direct(Tm @ H, T, P, Q, N1, N2, M)
+    return slr.F2H(np.fft.ifftshift(z, axes=(-2, -1)))
 
 
 def normal_op_direct(x, masks, H, lam, N1, N2, M):

@@ -15,6 +15,7 @@ from .phantom import (  # noqa: F401
     ellipse_phantom,
     smooth_field,
     vd_mask,
+    uniform_mask,
     served_mix,
     coil_maps,
     make_problem3,

@@ -49,6 +49,7 @@ class Workload:
     n_coils: int = 1           # receiver coils (Eq. measurement-ij); 1 = single channel
     depth: int = 1             # slices of a 3-D volume (1 = 2-D images)
     N3: int = 1                # filter taps along the depth
+    mask: str = "vd"           # "vd": variable density (vd_mask); "uniform": uniform_mask
 
     @property
     def shape(self):
@@ -96,7 +97,17 @@ def _vol():
         R=6.0, N1=7, N2=7, M=2, lam=1e-3, p=0.0, n_irls=25, n_cg=15)
 
 
-WORKLOADS = {w.name: w for w in (_tiny(), _perf(), _coils(), _vol())}
+def _cmp():
+    # the paper's comparison of the approximations (Sec. IV-A, Fig. 2 / Fig. 3): a single-channel
+    # 128 x 128 series of 12 echoes at 10 .. 120 ms from 30 % uniform random Fourier samples
+    return Workload(
+        name="cmp_128x128x12", P=128, Q=128, T=12,
+        times_ms=tuple(10.0 * (n + 1) for n in range(12)),
+        n_ellipses=8, t2_ranges=((20.0, 120.0),), frac_range=(1.0, 1.0),
+        R=1.0 / 0.3, N1=9, N2=9, M=3, lam=1e-3, p=0.0, n_irls=20, n_cg=10, mask="uniform")
+
+
+WORKLOADS = {w.name: w for w in (_tiny(), _perf(), _coils(), _vol(), _cmp())}
 
 
 def workload(name: str, **overrides) -> Workload:
@@ -160,6 +171,17 @@ def vd_mask(P: int, Q: int, R: float, rng: np.random.Generator) -> np.ndarray:
         pick = rng.choice(P * Q, size=need, replace=False, p=flat)
         mask.ravel()[pick] = True
     return mask.astype(np.uint8)
+
+
+def uniform_mask(P: int, Q: int, R: float, rng: np.random.Generator) -> np.ndarray:
+    """Uniform random Cartesian point mask with round(P*Q/R) samples: the DC sample plus
+    draws without replacement, every other position equally likely."""
+    n_target = int(round(P * Q / R))
+    mask = np.zeros(P * Q, dtype=bool)
+    mask[0] = True
+    pick = rng.choice(np.arange(1, P * Q), size=n_target - 1, replace=False)
+    mask[pick] = True
+    return mask.reshape(P, Q).astype(np.uint8)
 
 
 def make_series(w: Workload) -> np.ndarray:
@@ -301,7 +323,8 @@ def make_problem(w: Workload) -> dict:
         return make_problem3(w)
     S = w.seed
     x = make_series(w)
-    masks = np.stack([vd_mask(w.P, w.Q, w.R, np.random.default_rng(S + 10 + n))
+    draw = uniform_mask if w.mask == "uniform" else vd_mask
+    masks = np.stack([draw(w.P, w.Q, w.R, np.random.default_rng(S + 10 + n))
                       for n in range(w.T)])
     if w.n_coils > 1:
         coils = coil_maps(w.n_coils, w.P, w.Q, np.random.default_rng(S + 20))

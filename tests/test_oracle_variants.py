@@ -144,7 +144,7 @@ def test_direct_sum_of_squares_identity_and_planted_transpose(p):
     G = V.gram_direct(xw, N1, N2, M)
     eps = 0.05 * np.linalg.eigvalsh(G)[-1]
     H, _ = slr.weight_H(G, eps, p)
-    Tm = V.lift_direct(slr.F2(x), N1, N2, M)
+    Tm = V.lift_direct(V.centred_kspace(x), N1, N2, M)
     pen = sum(float(np.sum(np.abs(Tm @ h.conj()) ** 2)) for h in slr.filters_from_H(G, eps, p))
     quad = np.vdot(x, V.apply_W_direct(x, H, N1, N2, M))
     assert abs(quad.real - pen) <= 1e-10 * pen and abs(quad.imag) <= 1e-10 * pen
@@ -162,6 +162,17 @@ def test_direct_equals_proposed_for_a_one_pixel_filter():
     H, _ = slr.weight_H(G, 0.1 * np.linalg.eigvalsh(G)[-1], 0.0)
     S = slr.weight_S(slr.diag_sums(H, 1, 1, M), P, Q)
     assert np.allclose(V.apply_W_direct(x, H, 1, 1, M), slr.apply_W(x, S), atol=1e-10)
+
+
+def test_direct_lifting_is_taken_on_the_centred_kspace():
+    """The exact Gram equals T^H T of the valid lifting of fftshift(F x), and differs from that
+    of the natural-order k-space (the valid lifting is not shift invariant)."""
+    x = _crandn(np.random.default_rng(12), 4, 8, 6)
+    Tc = V.lift_direct(np.fft.fftshift(np.fft.fft2(x, norm="ortho"), axes=(1, 2)), 3, 2, 2)
+    G = V.gram_direct(x, 3, 2, 2)
+    assert np.allclose(G, Tc.conj().T @ Tc, atol=1e-12)
+    Tn = V.lift_direct(slr.F2(x), 3, 2, 2)
+    assert not np.allclose(G, Tn.conj().T @ Tn, atol=1e-3)
 
 
 def test_direct_cg_reaches_the_dense_solution():
@@ -195,3 +206,16 @@ def test_direct_matches_proposed_and_giraf_breaks_down():
     print(f"\nNRMSE proposed {e_prop:.4f} direct {e_dir:.4f} GIRAF {e_gir:.4f} adjoint {e_adj:.4f}")
     assert abs(e_dir - e_prop) < 0.15 * e_prop
     assert e_gir > 1.2 * e_prop
+
+
+def test_uniform_mask_generator():
+    """The comparison workload's sampling: exactly round(PQ/R) samples, DC included, seeded, no
+    preference for low frequencies (compare the inner and outer halves of the k-space radius)."""
+    m1 = synth.uniform_mask(128, 128, 1 / 0.3, np.random.default_rng(5))
+    m2 = synth.uniform_mask(128, 128, 1 / 0.3, np.random.default_rng(5))
+    assert np.array_equal(m1, m2)
+    assert int(m1.sum()) == round(128 * 128 * 0.3) and m1[0, 0] == 1
+    k = np.fft.fftfreq(128) * 128
+    rad = np.hypot(*np.meshgrid(k, k, indexing="ij"))
+    inner = rad < np.median(rad)
+    assert abs(m1[inner].mean() - m1[~inner].mean()) < 0.03
