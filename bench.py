@@ -29,6 +29,7 @@ UNIT = "IRLS iter/s"
 WORKLOAD = "perf_256x256x16"
 COIL_WORKLOAD = "coils_128x128x12"
 VOL_WORKLOAD = "vol_128x128x64x12"
+CMP_WORKLOAD = "cmp_128x128x12"
 
 # kernels launched per profiled scope (eig is the cuSOLVER library call and is not counted;
 # diag_sums is one kernel on the p = 0 path, two after the eigendecomposition)
@@ -307,6 +308,56 @@ def run_vol(steps: int, device: int) -> dict:
                     "per-class times from one profiled solve before the timed ones"}
 
 
+def run_variants(steps: int, device: int) -> dict:
+    """The comparison methods of Sec. IV on the 128x128x12 series from 30 % uniform random samples
+    (9x9x3 filter, 20 IRLS x 10 CG; HLR-Voxel: 1x1x3): ms per solve (CUDA events, after one
+    untimed solve) and NRMSE of each reconstruction against the ground truth."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1704_04511_gb300 import recon
+    w = synth.workload(CMP_WORKLOAD)
+    prob = synth.make_problem(w)
+    dev = torch.device("cuda", device)
+    b = torch.from_numpy(prob["kspace"].astype(np.complex64)).to(dev)
+    m = torch.from_numpy(prob["masks"]).to(dev)
+    out = torch.empty(tuple(m.shape), dtype=torch.complex64, device=dev)
+    xt = prob["x_true"]
+    stream = torch.cuda.current_stream(dev)
+    ctx = recon.Context(device, cuda_stream=stream.cuda_stream)
+    res = {}
+    try:
+        for name, variant, filt in (("proposed", recon.RECON_VARIANT_PROPOSED, (w.N1, w.N2, w.M)),
+                                    ("giraf", recon.RECON_VARIANT_GIRAF, (w.N1, w.N2, w.M)),
+                                    ("hlr_voxel", recon.RECON_VARIANT_HLR_VOXEL, (1, 1, w.M)),
+                                    ("direct", recon.RECON_VARIANT_DIRECT, (w.N1, w.N2, w.M))):
+            def solve():
+                recon.recon_solve_variant(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out,
+                                          variant)
+            solve()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                solve()
+            e1.record(stream)
+            e1.synchronize()
+            x = out.cpu().numpy().astype(np.complex128)
+            res[name] = {"ms_per_solve": round(e0.elapsed_time(e1) / steps, 2),
+                         "nrmse": round(float(np.linalg.norm(x - xt) / np.linalg.norm(xt)), 5),
+                         "filter": list(filt)}
+    finally:
+        ctx.close()
+    x0 = np.fft.ifft2(prob["masks"] * prob["kspace"], norm="ortho")
+    return {"workload": CMP_WORKLOAD, "irls": w.n_irls, "cg": w.n_cg, "lambda": w.lam,
+            "sampling": "30 % uniform random per frame", "methods": res,
+            "nrmse_adjoint": round(float(np.linalg.norm(x0 - xt) / np.linalg.norm(xt)), 5),
+            "direct_over_proposed_time": round(res["direct"]["ms_per_solve"] /
+                                               res["proposed"]["ms_per_solve"], 1),
+            "note": "recon_solve_variant, one problem at a time, device-resident k-space"}
+
+
 def run_served(n_requests: int, device: int) -> dict:
     """Continuous batching over the served mix: n requests, Poisson arrivals at 20/s, sizes
     {64, 128, 192, 256}^2, 8-24 frames, filters 5-9 x 2-3, 30 IRLS x 15 CG each."""
@@ -378,6 +429,9 @@ def main():
                     help="independent problems solved concurrently per step (1 = single solve)")
     ap.add_argument("--coil-steps", type=int, default=3,
                     help="solves of the 12-coil 128x128x12 workload to time (0 = skip)")
+    ap.add_argument("--variant-steps", type=int, default=1,
+                    help="solves per comparison method on the 128x128x12 30 %% uniform series "
+                         "(0 = skip)")
     ap.add_argument("--vol-steps", type=int, default=2,
                     help="solves of the 128x128x64x12 volume workload to time (0 = skip)")
     ap.add_argument("--served", type=int, default=48,
@@ -602,6 +656,8 @@ def main():
         line["coils"] = run_coils(args.coil_steps, local_rank)
     if args.vol_steps > 0:
         line["vol"] = run_vol(args.vol_steps, local_rank)
+    if args.variant_steps > 0:
+        line["variants"] = run_variants(args.variant_steps, local_rank)
     if not args.no_cpu_baseline:
         rate, n, dt, cores = cpu_oracle_rate(w, prob)
         line["cpu_baseline"] = {

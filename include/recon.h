@@ -310,7 +310,9 @@ int recon_apply_normal3(recon_ctx* c, recon_dims3 d, recon_filter3 f, const uint
  *                           The filter must have N1 = N2 = 1;
  *  RECON_VARIANT_DIRECT     IRLS without the FFT approximations (Sec. IV-A): the exact multi-fold
  *                           Toeplitz matrix, valid in space and time, (T-M+1)(P-N1+1)(Q-N2+1) x s,
- *                           formed explicitly (complex128 for its Gram, a library Hermitian
+ *                           of the centred k-space C F x (C moves DC to (P/2, Q/2); the valid
+ *                           lifting is not shift invariant and the grid of Sec. II-B is centred
+ *                           on k = 0), formed explicitly (complex128 for its Gram, a library Hermitian
  *                           rank-k product; complex64 for the CG, a library GEMM per step); the
  *                           workspace holds (T-M+1)(P-N1+1)(Q-N2+1) s 16 bytes for it. */
 #define RECON_VARIANT_PROPOSED 0
@@ -335,7 +337,8 @@ int recon_voxel_weight(recon_ctx* c, recon_dims d, int M, const void* x, const d
 int recon_weight_direct(recon_ctx* c, recon_dims d, recon_filter f, const void* G_in,
                         double eps_in, double p, int method, void* H_out, double* eps_out);
 /* y = (A^H A + lambda W) x of the variant: W is S (npair x P x Q complex64) for PROPOSED, GIRAF and
- * HLR_VOXEL, and H (s x s complex128 column-major) for DIRECT, where W x = F^H T^*(T(F x) H). */
+ * HLR_VOXEL, and H (s x s complex128 column-major) for DIRECT, where
+ * W x = F^H C^H T^*(T(C F x) H). */
 int recon_apply_normal_variant(recon_ctx* c, recon_dims d, recon_filter f, int variant,
                                const uint8_t* masks, const void* W, double lambda, const void* x,
                                void* y);

@@ -8,10 +8,13 @@
 // Re <x, W x> = sum_r Tr(H_r G_r)); the CG then runs on the proposed path's kernels.
 //
 // IRLS-direct (Sec. IV-A: Eq. x-update and Eq. weight-update without the FFT approximations):
-// the exact multi-fold Toeplitz matrix, valid in all three dimensions, is formed explicitly
-// (direct_lift_kernel), its Gram is a library Hermitian rank-k product, and the penalty gradient
-// F^H T^*(T(F p) H) is a library GEMM between the lifting and its adjoint (direct_unlift_kernel,
-// a gather: each element of T(F p) H goes back to the k-space sample it was copied from).
+// the exact multi-fold Toeplitz matrix, valid in all three dimensions, of the centred k-space
+// (DC at (P/2, Q/2): the valid lifting is not shift invariant and the grid of Sec. II-B is
+// centred on k = 0) is formed explicitly (direct_lift_kernel), its Gram is a library Hermitian
+// rank-k product, and the penalty gradient F^H C^H T^*(T(C F p) H) is a library GEMM between the
+// lifting and its adjoint (direct_unlift_kernel, a gather: each element of T(C F p) H goes back
+// to the k-space sample it was copied from). The centring C is folded into the index maps
+// (P and Q are even, so it is the half-grid shift both ways).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -155,7 +158,8 @@ voxel_weight_kernel(const float2* __restrict__ x, int T, size_t npix, double p,
 }
 
 // Tm[col * m + row] with row = (j nr1 + c1) nr2 + c2, col = (mm N1 + l1) N2 + l2:
-// x_hat[j + M - 1 - mm][c1 + N1 - 1 - l1][c2 + N2 - 1 - l2] (grid.y = column).
+// centred x_hat[j + M - 1 - mm][c1 + N1 - 1 - l1][c2 + N2 - 1 - l2] (grid.y = column); centred
+// index u is natural index (u + P/2) mod P.
 template <typename TOut>
 __global__ void __launch_bounds__(kThreads)
 direct_lift_kernel(const float2* __restrict__ xh, int T, int P, int Q, int N1, int N2, int M,
@@ -169,7 +173,8 @@ direct_lift_kernel(const float2* __restrict__ xh, int T, int P, int Q, int N1, i
         const int c2 = (int)(row % nr2);
         const int c1 = (int)((row / nr2) % nr1);
         const int j = (int)(row / ((size_t)nr2 * nr1));
-        const float2 v = xh[((size_t)(j + M - 1 - mm) * P + c1 + N1 - 1 - l1) * Q + c2 + N2 - 1 - l2];
+        const int k1 = (c1 + N1 - 1 - l1 + P / 2) % P, k2 = (c2 + N2 - 1 - l2 + Q / 2) % Q;
+        const float2 v = xh[((size_t)(j + M - 1 - mm) * P + k1) * Q + k2];
         if constexpr (sizeof(TOut) == sizeof(double2)) {
             Tm[(size_t)col * m + row] = make_double2(v.x, v.y);
         } else {
@@ -179,7 +184,7 @@ direct_lift_kernel(const float2* __restrict__ xh, int T, int P, int Q, int N1, i
 }
 
 // z[n][k1][k2] = (mask ? mask * yh : 0) + lam * sum of Y over the lifted entries copied from
-// x_hat[n][k1][k2] (the adjoint of direct_lift_kernel, as a gather).
+// x_hat[n][k1][k2] (the adjoint of direct_lift_kernel, as a gather; natural order in and out).
 __global__ void __launch_bounds__(kThreads)
 direct_unlift_kernel(const float2* __restrict__ Y, int T, int P, int Q, int N1, int N2, int M,
                      const float2* __restrict__ yh, const uint8_t* __restrict__ mask, float lam,
@@ -190,15 +195,16 @@ direct_unlift_kernel(const float2* __restrict__ Y, int T, int P, int Q, int N1, 
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_el;
          i += (size_t)gridDim.x * blockDim.x) {
         const int k2 = (int)(i % Q), k1 = (int)((i / Q) % P), n = (int)(i / ((size_t)Q * P));
+        const int u1 = (k1 + P / 2) % P, u2 = (k2 + Q / 2) % Q;  // centred position
         float2 acc = make_float2(0.f, 0.f);
         for (int mm = 0; mm < M; ++mm) {
             const int j = n - (M - 1 - mm);
             if (j < 0 || j >= k) continue;
             for (int l1 = 0; l1 < N1; ++l1) {
-                const int c1 = k1 - (N1 - 1 - l1);
+                const int c1 = u1 - (N1 - 1 - l1);
                 if (c1 < 0 || c1 >= nr1) continue;
                 for (int l2 = 0; l2 < N2; ++l2) {
-                    const int c2 = k2 - (N2 - 1 - l2);
+                    const int c2 = u2 - (N2 - 1 - l2);
                     if (c2 < 0 || c2 >= nr2) continue;
                     const size_t row = ((size_t)j * nr1 + c1) * nr2 + c2;
                     const size_t col = ((size_t)mm * N1 + l1) * N2 + l2;
