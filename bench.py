@@ -432,6 +432,8 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=1,
                     help="solves per comparison method on the 128x128x12 30 %% uniform series "
                          "(0 = skip)")
+    ap.add_argument("--only-vol", action="store_true",
+                    help="time only the volume workload and print {\"vol\": ...} (profiling)")
     ap.add_argument("--vol-steps", type=int, default=2,
                     help="solves of the 128x128x64x12 volume workload to time (0 = skip)")
     ap.add_argument("--served", type=int, default=48,
@@ -445,6 +447,11 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.only_vol:
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"vol": run_vol(max(args.vol_steps, 1), local_rank)}), flush=True)
         return
 
     import numpy as np

@@ -22,8 +22,6 @@ constexpr int kUpdVec = 2;       // float4 per thread per iteration in the updat
 constexpr int kUpdThreads = 512;
 constexpr int kUpdPerSM = 2;     // update CTAs per SM (few partials for the next pass to add)
 
-RECON_DEV int pair_index(int a, int b, int M) { return a * (2 * M - a + 1) / 2 + (b - a); }
-
 // Load S(r) (full M x M from the stored upper triangle) into registers.
 template <int M>
 RECON_DEV void load_S(const float2* __restrict__ S, size_t npix, size_t px, float2 (&s)[M][M]) {
@@ -40,10 +38,10 @@ RECON_DEV void load_S(const float2* __restrict__ S, size_t npix, size_t px, floa
 // Pass C of a CG step. One CTA per image row r1 holds that row of every frame: it inverse-
 // transforms the k-space rows of t (giving A^H A p; the 1/(PQ) scale was applied with the mask),
 // adds lam W p from the p rows, writes q over t and emits the partial Re <p, q> of its row.
-template <int N, int M>
+template <int N, int M, bool CIRC>
 __global__ void __launch_bounds__(kThreads)
 row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
-                 float lam, int T, int P, int circ, double* __restrict__ pq_parts,
+                 float lam, int T, int P, double* __restrict__ pq_parts,
                  const float2* __restrict__ tw_g) {
     extern __shared__ float2 sm[];
     __shared__ double red[kThreads / 32];
@@ -54,7 +52,7 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     const size_t npix = (size_t)P * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
     pdl_wait();
-    const int k = circ ? T : T - M + 1;
+    const int k = CIRC ? T : T - M + 1;
     float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
     for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
     __syncthreads();  // the previous row's results are stored
@@ -74,10 +72,10 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
 #pragma unroll
             for (int aa = 0; aa < M; ++aa) {
                 const int j = n - M + 1 + aa;
-                if (!circ && (j < 0 || j >= k)) continue;  // circ: every window
+                if (!CIRC && (j < 0 || j >= k)) continue;  // CIRC: every window
 #pragma unroll
                 for (int bb = 0; bb < M; ++bb)
-                    w = cfma(s[aa][bb], pt[wrap_frame(n + aa - bb, T) * N + c], w);
+                    w = cfma(s[aa][bb], pt[(CIRC ? wrap_frame(n + aa - bb, T) : n + aa - bb) * N + c], w);
             }
             float2 q = res[n * N + c];
             q.x = fmaf(lam, w.x, q.x);
@@ -108,7 +106,7 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
 template <int M>
 __global__ void __launch_bounds__(1024)
 row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
-                     float lam, int T, int P, int circ, double* __restrict__ pq_parts,
+                     float lam, int T, int P, double* __restrict__ pq_parts,
                      const float2* __restrict__ tw_g) {
     constexpr int N = 256;
     extern __shared__ float2 sm[];
@@ -121,7 +119,7 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
     const int n = threadIdx.x / 16, j = threadIdx.x % 16;
     const bool live = n < T;  // the block is padded to whole warps (an odd T leaves a half-warp)
     const size_t npix = (size_t)P * N;
-    const int k = circ ? T : T - M + 1;
+    const int k = T - M + 1;
     float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
     for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
     __syncthreads();  // the previous row's results are stored
@@ -151,10 +149,10 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
 #pragma unroll
             for (int aa = 0; aa < M; ++aa) {
                 const int jw = nn - M + 1 + aa;
-                if (!circ && (jw < 0 || jw >= k)) continue;  // circ: every window
+                if (jw < 0 || jw >= k) continue;
 #pragma unroll
                 for (int bb = 0; bb < M; ++bb)
-                    w = cfma(s[aa][bb], pt[wrap_frame(nn + aa - bb, T) * N + c], w);
+                    w = cfma(s[aa][bb], pt[(nn + aa - bb) * N + c], w);
             }
             float2 q = res[nn * N + c];
             q.x = fmaf(lam, w.x, q.x);
@@ -442,7 +440,7 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
                                 const float2* S, float lam, Partials* pq, cudaStream_t st) {
     const int rows = d.rows();
     int grid = 0;
-    if constexpr (N == 256) {
+    if (N == 256 && !d.circ) {  // the register kernel serves the valid (non-circular) lifting
         const int tpad = (d.T + 1) / 2 * 2;
         const size_t smem256 = ((size_t)d.T * N + (size_t)tpad * 16 * 17) * sizeof(float2);
         if (tpad * 16 <= 1024 && smem256 <= 200 * 1024) {
@@ -456,10 +454,10 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
             if (e != cudaSuccess) return e;
             pq->n = grid;
             return launch_pdl(k, dim3(grid), dim3(tpad * 16), smem256, st, t, p, S, lam, d.T, rows,
-                              d.circ, pq->parts, tw.twQ);
+                              pq->parts, tw.twQ);
         }
     }
-    auto k = row_inv_w_kernel<N, M>;
+    auto k = d.circ ? row_inv_w_kernel<N, M, true> : row_inv_w_kernel<N, M, false>;
     const size_t smem = ((size_t)3 * d.T * N + N) * sizeof(float2);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -468,7 +466,7 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
     cudaError_t e = row_grid(k, kThreads, smem, rows, &grid);
     if (e != cudaSuccess) return e;
     pq->n = grid;
-    return launch_pdl(k, dim3(grid), dim3(kThreads), smem, st, t, p, S, lam, d.T, rows, d.circ,
+    return launch_pdl(k, dim3(grid), dim3(kThreads), smem, st, t, p, S, lam, d.T, rows,
                       pq->parts, tw.twQ);
 }
 

@@ -21,6 +21,11 @@ constexpr int kColTile = 8;
 template <int N>
 __host__ __device__ constexpr int rows_per_cta() { return N >= 1024 ? 1 : 1024 / N; }
 
+// Columns per CTA of the wide column tile used by the volume passes (about 4096 elements per
+// CTA: 256-byte row segments and 16 elements per thread for the shorter transforms).
+template <int N>
+__host__ __device__ constexpr int wide_cols() { return N <= 128 ? 32 : (N <= 256 ? 16 : 8); }
+
 enum ColMode { COL_FWD = 0, COL_INV = 1, COL_MASK_OP = 2, COL_ADJ_C64 = 3, COL_ADJ_BF16 = 4 };
 
 template <int N, bool INV>
@@ -147,12 +152,11 @@ coil_row_fwd_kernel(const float2* __restrict__ r, float2* __restrict__ p, float2
     }
 }
 
-// Column pass over a P x 8 tile (frame blockIdx.y, columns 8*blockIdx.x ..).
-template <int N, int MODE>
+// Column pass over an N x C tile (frame blockIdx.y, columns C*blockIdx.x ..).
+template <int N, int MODE, int C>
 __global__ void __launch_bounds__(kThreads)
 col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
            int Q, int mask_frames, float scale, const float2* __restrict__ tw_g) {
-    constexpr int C = kColTile;
     extern __shared__ float2 sm[];
     float2* a = sm;
     float2* b = a + N * C;
@@ -310,8 +314,8 @@ col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, int mask
 
 template <int N>
 size_t row_smem() { return (size_t)(2 * rows_per_cta<N>() * N + N) * sizeof(float2); }
-template <int N>
-size_t col_smem() { return (size_t)(2 * N * kColTile + N) * sizeof(float2); }
+template <int N, int C>
+size_t col_smem() { return (size_t)(2 * N * C + N) * sizeof(float2); }
 
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
@@ -342,19 +346,30 @@ cudaError_t row_fft(int n, const float2* in, float2* out, int nrows, float scale
     }
 }
 
-// `T` transforms (frames), the mask of frame f being mask frame f % mask_frames.
-template <int MODE>
+template <int N, int MODE, int C>
+cudaError_t col_launch(int Q, int T, int mask_frames, const void* in, float2* out,
+                       const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
+    auto k = col_kernel<N, MODE, C>;
+    cudaError_t e = set_smem(k, col_smem<N, C>());
+    if (e != cudaSuccess) return e;
+    dim3 grid(Q / C, T);
+    return launch_pdl(k, grid, dim3(kThreads), col_smem<N, C>(), st, in, out, mask, Q, mask_frames,
+                      scale, tw);
+}
+
+// `T` transforms (frames), the mask of frame f being mask frame f % mask_frames. WIDE: tiles of
+// wide_cols<n>() columns when Q allows (the volume passes), else 8.
+template <int MODE, bool WIDE = false>
 cudaError_t col_pass(int n, int Q, int T, int mask_frames, const void* in, float2* out,
                      const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
     switch (n) {
-#define CASE(N)                                                                          \
-    case N: {                                                                            \
-        auto k = col_kernel<N, MODE>;                                                    \
-        cudaError_t e = set_smem(k, col_smem<N>());                                      \
-        if (e != cudaSuccess) return e;                                                  \
-        dim3 grid(Q / kColTile, T);                                                      \
-        return launch_pdl(k, grid, dim3(kThreads), col_smem<N>(), st, in, out, mask, Q,  \
-                          mask_frames, scale, tw);                                       \
+#define CASE(N)                                                                           \
+    case N: {                                                                             \
+        if (WIDE && Q % wide_cols<N>() == 0)                                              \
+            return col_launch<N, MODE, wide_cols<N>()>(Q, T, mask_frames, in, out, mask,  \
+                                                       scale, tw, st);                    \
+        return col_launch<N, MODE, kColTile>(Q, T, mask_frames, in, out, mask, scale, tw, \
+                                             st);                                         \
     }
         RECON_FFT_SIZES(CASE)
 #undef CASE
@@ -388,8 +403,8 @@ cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, floa
     if (e != cudaSuccess || d.R == 1) return e;
     const float sr = 1.0f / sqrtf((float)d.R);
     const int pq = d.P * d.Q;
-    return inv ? col_pass<COL_INV>(d.R, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st)
-               : col_pass<COL_FWD>(d.R, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st);
+    return inv ? col_pass<COL_INV, true>(d.R, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st)
+               : col_pass<COL_FWD, true>(d.R, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st);
 }
 
 cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int b_bf16,
@@ -399,10 +414,10 @@ cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int
     if (d.R > 1) {
         // masked depth IDFT (with the whole 1/sqrt(PQR)), then the column IDFT of every slice
         const int pq = d.P * d.Q, slices = d.T * d.R;
-        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.R, pq, d.T, d.T, b, t, mask, sc, tw.twR, st)
-                   : col_pass<COL_ADJ_C64>(d.R, pq, d.T, d.T, b, t, mask, sc, tw.twR, st);
+        e = b_bf16 ? col_pass<COL_ADJ_BF16, true>(d.R, pq, d.T, d.T, b, t, mask, sc, tw.twR, st)
+                   : col_pass<COL_ADJ_C64, true>(d.R, pq, d.T, d.T, b, t, mask, sc, tw.twR, st);
         if (e != cudaSuccess) return e;
-        e = col_pass<COL_INV>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+        e = col_pass<COL_INV, true>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
     } else {
         e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st)
                    : col_pass<COL_ADJ_C64>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st);
@@ -471,11 +486,12 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
         // of the two unnormalised transforms), column IDFT of every slice
         const int pq = d.P * d.Q, slices = d.T * d.R;
         const float sc3 = 1.0f / ((float)d.P * (float)d.Q * (float)d.R);
-        cudaError_t e = col_pass<COL_FWD>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+        cudaError_t e =
+            col_pass<COL_FWD, true>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
         if (e != cudaSuccess) return e;
-        e = col_pass<COL_MASK_OP>(d.R, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
+        e = col_pass<COL_MASK_OP, true>(d.R, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
         if (e != cudaSuccess) return e;
-        return col_pass<COL_INV>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+        return col_pass<COL_INV, true>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
     }
     const float sc = 1.0f / ((float)d.P * (float)d.Q);
     const int frames = d.T * d.nc;  // coil-major: the mask of frame f is mask frame f % T
