@@ -21,10 +21,11 @@ constexpr int kColTile = 8;
 template <int N>
 __host__ __device__ constexpr int rows_per_cta() { return N >= 1024 ? 1 : 1024 / N; }
 
-// Columns per CTA of the wide column tile used by the volume passes (about 4096 elements per
-// CTA: 256-byte row segments and 16 elements per thread for the shorter transforms).
+// Columns per CTA of the wide column tile used by the volume passes: about 2048 elements per
+// CTA (8 per thread, 33 KB of shared memory, six CTAs per SM), at least 8 and at most 32 columns
+// (64- to 256-byte row segments).
 template <int N>
-__host__ __device__ constexpr int wide_cols() { return N <= 128 ? 32 : (N <= 256 ? 16 : 8); }
+__host__ __device__ constexpr int wide_cols() { return N <= 64 ? 32 : (N <= 128 ? 16 : 8); }
 
 enum ColMode { COL_FWD = 0, COL_INV = 1, COL_MASK_OP = 2, COL_ADJ_C64 = 3, COL_ADJ_BF16 = 4 };
 
