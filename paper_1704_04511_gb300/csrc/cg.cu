@@ -176,6 +176,85 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
     if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
+// Pass C for 128-point rows: as row_inv_w_256_kernel with 8 threads per frame (row_dft128), the
+// block padded to a multiple of four frames (whole warps). Shared memory: p rows [T][128], then
+// the exchange buffers [T'][kX128] which afterwards hold the transformed rows [T][128].
+template <int M>
+__global__ void __launch_bounds__(1024)
+row_inv_w_128_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
+                     float lam, int T, int P, double* __restrict__ pq_parts,
+                     const float2* __restrict__ tw_g) {
+    constexpr int N = 128;
+    extern __shared__ float2 sm[];
+    __shared__ float2 tw8[128];
+    __shared__ double red[32];
+    float2* pt = sm;
+    float2* res = sm + (size_t)T * N;
+    fill_tw128(tw8, tw_g);
+    pdl_wait();
+    const int n = threadIdx.x / 8, j = threadIdx.x % 8;
+    const bool live = n < T;
+    const size_t npix = (size_t)P * N;
+    const int k = T - M + 1;
+    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
+    for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
+    __syncthreads();  // the previous row's results are stored
+    const size_t g0 = (size_t)n * npix + (size_t)r1 * N + j;
+    float2 u[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        u[n1] = make_float2(0.f, 0.f);
+        if (live) {
+            u[n1] = t[g0 + 8 * n1];
+            pt[n * N + 8 * n1 + j] = p[g0 + 8 * n1];
+        }
+    }
+    __syncthreads();  // tw8
+    float2 a[8], b[8];
+    row_dft128<true>(u, a, b, res + n * kX128, tw8, j);
+    __syncthreads();  // every exchange buffer read
+    if (live) {
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) {
+            res[n * N + 2 * j + 16 * k2] = a[k2];
+            res[n * N + 2 * j + 1 + 16 * k2] = b[k2];
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        float2 s[M][M];
+        load_S<M>(S, npix, (size_t)r1 * N + c, s);
+        for (int nn = 0; nn < T; ++nn) {
+            float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int aa = 0; aa < M; ++aa) {
+                const int jw = nn - M + 1 + aa;
+                if (jw < 0 || jw >= k) continue;
+#pragma unroll
+                for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(nn + aa - bb) * N + c], w);
+            }
+            float2 q = res[nn * N + c];
+            q.x = fmaf(lam, w.x, q.x);
+            q.y = fmaf(lam, w.y, q.y);
+            res[nn * N + c] = q;
+            const float2 pv = pt[nn * N + c];
+            const float term = fmaf(pv.x, q.x, pv.y * q.y) - comp;
+            const float sum = acc + term;
+            comp = (sum - acc) - term;
+            acc = sum;
+        }
+    }
+    __syncthreads();  // every column of q written
+    if (r1 + (int)gridDim.x >= P) pdl_trigger();
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int nn = e / N, c = e % N;
+        t[(size_t)nn * npix + (size_t)r1 * N + c] = res[e];
+    }
+    }
+    const double tot = block_sum_f_t0(acc, red);
+    if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
+}
+
 // Pass C of a CG step with coils (ADJ = false), or the coil combination of the adjoint
 // (ADJ = true). One CTA per image row r1 holds that row of every frame: for each coil c it
 // inverse-transforms the rows t[c][n][r1] and accumulates conj(C_c) * (...) (Eq.
@@ -440,6 +519,23 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
                                 const float2* S, float lam, Partials* pq, cudaStream_t st) {
     const int rows = d.rows();
     int grid = 0;
+    if (N == 128 && !d.circ) {  // register transforms for the valid (non-circular) lifting
+        const int tpad = (d.T + 3) / 4 * 4;
+        const size_t smem128 = ((size_t)d.T * N + (size_t)tpad * kX128) * sizeof(float2);
+        if (tpad * 8 <= 1024 && smem128 <= 200 * 1024) {
+            auto k = row_inv_w_128_kernel<M>;
+            if (smem128 > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem128);
+                if (e != cudaSuccess) return e;
+            }
+            cudaError_t e = row_grid(k, tpad * 8, smem128, rows, &grid);
+            if (e != cudaSuccess) return e;
+            pq->n = grid;
+            return launch_pdl(k, dim3(grid), dim3(tpad * 8), smem128, st, t, p, S, lam, d.T, rows,
+                              pq->parts, tw.twQ);
+        }
+    }
     if (N == 256 && !d.circ) {  // the register kernel serves the valid (non-circular) lifting
         const int tpad = (d.T + 1) / 2 * 2;
         const size_t smem256 = ((size_t)d.T * N + (size_t)tpad * 16 * 17) * sizeof(float2);

@@ -267,6 +267,70 @@ row_fwd_pupdate_256_kernel(const float2* __restrict__ r, float2* __restrict__ p,
     }
 }
 
+// Pass A of a CG step for 128-point rows (same contract as row_fwd_pupdate_kernel): 8 rows per
+// 64-thread CTA, 8 lanes per row (row_dft128 in regfft.cuh).
+constexpr int kR128Rows = 8;
+
+__global__ void __launch_bounds__(64)
+row_fwd_pupdate_128_kernel(const float2* __restrict__ r, float2* __restrict__ p,
+                           float2* __restrict__ t, int nrows, const double* __restrict__ rr_parts,
+                           int n_rr, const double* __restrict__ rr_prev,
+                           double* __restrict__ rr_out, int first,
+                           const float2* __restrict__ tw_g) {
+    __shared__ float2 tw8[128];
+    __shared__ float2 sx[kR128Rows][kX128];
+    __shared__ float beta_s;
+    fill_tw128(tw8, tw_g);
+    pdl_wait();
+    const int lr = threadIdx.x / 8, j = threadIdx.x % 8;
+    const int row = blockIdx.x * kR128Rows + lr;
+    const bool ok = row < nrows;
+    const size_t base = (size_t)row * 128 + j;
+    float2 u[16], pv[16];
+    if (ok) {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) u[n1] = r[base + 8 * n1];
+        if (!first) {
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) pv[n1] = p[base + 8 * n1];
+        }
+    } else {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) u[n1] = make_float2(0.f, 0.f);
+    }
+    if (!first && threadIdx.x < 32) {  // |r|^2 from the update pass's partials, loads in flight
+        const double rr_new = warp0_sum_array(rr_parts, n_rr);
+        if (threadIdx.x == 0) {
+            beta_s = (float)(rr_new * rcp_nr(rr_prev[0]));
+            if (blockIdx.x == 0) rr_out[0] = rr_new;
+        }
+    }
+    __syncthreads();  // tw8, beta
+    if (!first) {
+        const float beta = beta_s;
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) {
+            u[n1].x = fmaf(beta, pv[n1].x, u[n1].x);
+            u[n1].y = fmaf(beta, pv[n1].y, u[n1].y);
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) p[base + 8 * n1] = u[n1];
+    }
+    float2 a[8], b[8];
+    row_dft128<false>(u, a, b, sx[lr], tw8, j);
+    pdl_trigger();
+    if (ok) {
+        float2* out = t + (size_t)row * 128 + 2 * j;
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) {
+            out[16 * k2] = a[k2];
+            out[16 * k2 + 1] = b[k2];
+        }
+    }
+}
+
 // Column pass with the sampling mask for 256-point columns: 8 adjacent columns of one frame per
 // 128-thread CTA, thread (c, j) holding rows j + 16 n1 of column c. Forward DFT, mask and the
 // 1/(PQ) scale, inverse DFT, all in registers; two exchanges through shared memory, laid out as
@@ -434,6 +498,11 @@ cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const floa
     if (d.Q == 256) {
         const int grid = (nrows + kR256Rows - 1) / kR256Rows;
         return launch_pdl(row_fwd_pupdate_256_kernel, dim3(grid), dim3(64), 0, st, r, p, t, nrows,
+                          (const double*)rr.parts, rr.n, rr_prev, rr_out, first, tw.twQ);
+    }
+    if (d.Q == 128) {
+        const int grid = (nrows + kR128Rows - 1) / kR128Rows;
+        return launch_pdl(row_fwd_pupdate_128_kernel, dim3(grid), dim3(64), 0, st, r, p, t, nrows,
                           (const double*)rr.parts, rr.n, rr_prev, rr_out, first, tw.twQ);
     }
     switch (d.Q) {

@@ -1,4 +1,5 @@
-// Length-256 DFTs held in registers, 16 threads per sequence (256 = 16 x 16, Cooley-Tukey):
+// Length-256 (and, at the end, length-128) DFTs held in registers, 16 threads per sequence
+// (256 = 16 x 16, Cooley-Tukey):
 //   X[k1 + 16 k2] = sum_n2 w16^(n2 k2) w256^(n2 k1) sum_n1 x[16 n1 + n2] w16^(n1 k1),
 // with w_N = e^{-2 pi i / N} (forward) or its conjugate (inverse). Thread n2 loads the 16
 // elements x[16 n1 + n2] (consecutive threads read consecutive elements), runs a 16-point DFT in
@@ -117,6 +118,41 @@ RECON_DEV void row_dft256(float2 (&u)[16], float2* sx, const float2* tw2, int j)
     for (int n2 = 0; n2 < 16; ++n2) u[n2] = sx[j * 17 + n2];
     __syncwarp();
     dft16<INV>(u);
+}
+
+// ---- length 128 = 16 x 8, 8 threads per sequence ----
+//   X[k1 + 16 k2] = sum_j w8^(j k2) w128^(j k1) sum_n1 x[8 n1 + j] w16^(n1 k1).
+// Lane j loads x[8 n1 + j] (n1 < 16), runs the 16-point DFT and the twiddles, writes its 16
+// values to the row's exchange buffer (16 x 9, row k1), and reads back rows 2j and 2j + 1 for
+// two 8-point DFTs: it then holds X[2j + 16 k2] in a[k2] and X[2j + 1 + 16 k2] in b[k2].
+constexpr int kX128 = 152;  // float2 per exchange buffer (16 x 9 + 8: alternate 16-bank offset)
+
+// tw8[k1 * 8 + j] = w128^(j k1) (forward sign) from the length-128 table; 128 entries.
+RECON_DEV void fill_tw128(float2* tw8, const float2* __restrict__ tw_g) {
+    for (int e = threadIdx.x; e < 128; e += blockDim.x) tw8[e] = tw_g[(e / 8) * (e % 8)];
+}
+
+template <bool INV>
+RECON_DEV void row_dft128(float2 (&u)[16], float2 (&a)[8], float2 (&b)[8], float2* sx,
+                          const float2* tw8, int j) {
+    dft16<INV>(u);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+        float2 w = tw8[k1 * 8 + j];
+        if (INV) w.y = -w.y;
+        u[k1] = cmul(u[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) sx[k1 * 9 + j] = u[k1];
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        a[jj] = sx[(2 * j) * 9 + jj];
+        b[jj] = sx[(2 * j + 1) * 9 + jj];
+    }
+    __syncwarp();
+    SmallDFT<8, INV>::run(a);
+    SmallDFT<8, INV>::run(b);
 }
 
 }  // namespace recon
