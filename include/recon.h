@@ -133,9 +133,15 @@ int recon_poll(recon_ctx* c, int ticket, int* done);
  *   runs each frame's 2-D transform, mask and inverse in one kernel on an 8-CTA cluster
  *   (distributed shared memory), followed by a pixel-parallel W pass; off = the row / column
  *   passes used for every other shape. */
+/* RECON_OPT_AUTOTUNE: on the first solve of each shape (P, Q, T, R, coils) the context times the
+ *   column passes of the CG operator with tiles of 8, 16 and 32 columns (CUDA events on its own
+ *   stream, a few milliseconds at most) and keeps the fastest; off = the built-in widths. The
+ *   width changes launch shapes only: results are bitwise the same either way. */
 #define RECON_OPT_GRAPHS 1      /* default on  */
 #define RECON_OPT_CLUSTER_FFT 2 /* default off */
+#define RECON_OPT_AUTOTUNE 3    /* default on  */
 int recon_set_option(recon_ctx* c, int option, int value);
+
 
 /* ---- stage entry points (the same kernels recon_solve runs; used for parity checks) ---- */
 
@@ -342,6 +348,14 @@ int recon_weight_direct(recon_ctx* c, recon_dims d, recon_filter f, const void* 
 int recon_apply_normal_variant(recon_ctx* c, recon_dims d, recon_filter f, int variant,
                                const uint8_t* masks, const void* W, double lambda, const void* x,
                                void* y);
+
+/* ---- autotuner (RECON_OPT_AUTOTUNE) ----
+ * Autotuner cache file: reads the choices stored in `path` (lines "P Q T R coils colC depthC"; a
+ * missing file is an empty cache) into the context and appends every new choice to it. NULL
+ * stops appending. RECON_EINVAL on a malformed entry. */
+int recon_tile_cache(recon_ctx* c, const char* path);
+/* The tile widths the context uses for a shape (R = 1 for image series; 0 = not tuned yet). */
+int recon_tile_choice(recon_ctx* c, recon_dims3 d, int n_coils, int* colC, int* depthC);
 
 /* ---- measurement ---- */
 

@@ -21,11 +21,13 @@ constexpr int kColTile = 8;
 template <int N>
 __host__ __device__ constexpr int rows_per_cta() { return N >= 1024 ? 1 : 1024 / N; }
 
-// Columns per CTA of the wide column tile used by the volume passes: about 2048 elements per
-// CTA (8 per thread, 33 KB of shared memory, six CTAs per SM), at least 8 and at most 32 columns
-// (64- to 256-byte row segments).
-template <int N>
-__host__ __device__ constexpr int wide_cols() { return N <= 64 ? 32 : (N <= 128 ? 16 : 8); }
+// Columns per CTA of the column passes: 8, 16 or 32 (64- to 256-byte row segments). The default
+// for the volume passes is about 2048 elements per CTA (8 per thread, 33 KB of shared memory,
+// six CTAs per SM); the image-series passes default to 8. The autotuner of recon.cu may choose
+// another width per shape: the width changes the launch shape, not the arithmetic of any column.
+int wide_cols(int n) { return n <= 64 ? 32 : (n <= 128 ? 16 : 8); }
+template <int N, int C>
+constexpr bool col_tile_ok() { return (size_t)(2 * N * C + N) * sizeof(float2) <= 100 * 1024; }
 
 enum ColMode { COL_FWD = 0, COL_INV = 1, COL_MASK_OP = 2, COL_ADJ_C64 = 3, COL_ADJ_BF16 = 4 };
 
@@ -422,20 +424,29 @@ cudaError_t col_launch(int Q, int T, int mask_frames, const void* in, float2* ou
                       scale, tw);
 }
 
-// `T` transforms (frames), the mask of frame f being mask frame f % mask_frames. WIDE: tiles of
-// wide_cols<n>() columns when Q allows (the volume passes), else 8.
-template <int MODE, bool WIDE = false>
-cudaError_t col_pass(int n, int Q, int T, int mask_frames, const void* in, float2* out,
+template <int N, int MODE>
+cudaError_t col_launch_c(int C, int Q, int T, int mask_frames, const void* in, float2* out,
+                         const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
+    if constexpr (col_tile_ok<N, 32>()) {
+        if (C >= 32 && Q % 32 == 0)
+            return col_launch<N, MODE, 32>(Q, T, mask_frames, in, out, mask, scale, tw, st);
+    }
+    if constexpr (col_tile_ok<N, 16>()) {
+        if (C >= 16 && Q % 16 == 0)
+            return col_launch<N, MODE, 16>(Q, T, mask_frames, in, out, mask, scale, tw, st);
+    }
+    return col_launch<N, MODE, kColTile>(Q, T, mask_frames, in, out, mask, scale, tw, st);
+}
+
+// `T` transforms (frames), the mask of frame f being mask frame f % mask_frames; tiles of C
+// columns (rounded down to what Q and the shared memory allow; 8 at least).
+template <int MODE>
+cudaError_t col_pass(int n, int C, int Q, int T, int mask_frames, const void* in, float2* out,
                      const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
     switch (n) {
-#define CASE(N)                                                                           \
-    case N: {                                                                             \
-        if (WIDE && Q % wide_cols<N>() == 0)                                              \
-            return col_launch<N, MODE, wide_cols<N>()>(Q, T, mask_frames, in, out, mask,  \
-                                                       scale, tw, st);                    \
-        return col_launch<N, MODE, kColTile>(Q, T, mask_frames, in, out, mask, scale, tw, \
-                                             st);                                         \
-    }
+#define CASE(N)                                                                              \
+    case N:                                                                                  \
+        return col_launch_c<N, MODE>(C, Q, T, mask_frames, in, out, mask, scale, tw, st);
         RECON_FFT_SIZES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
@@ -456,20 +467,31 @@ bool fft_size_supported(int n) {
 // Volumes (R > 1): the depth transforms reuse the column kernel with the depth as the transform
 // axis and the P * Q voxels of a depth slice as its "columns" (stride P * Q between depth
 // samples); the length-P column passes then run over the T * R slices.
+// Column tile for the length-P passes (depth = false) or the depth passes of a volume: the
+// width the caller chose in Dims (autotuner), else 8 for image series and the wide default for
+// volumes.
+int col_tile_for(const Dims& d, bool depth) {
+    const int chosen = depth ? d.depthC : d.colC;
+    if (chosen > 0) return chosen;
+    if (d.R == 1) return kColTile;
+    return wide_cols(depth ? d.R : d.P);
+}
+
 cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, float2* y, int inv,
                         cudaStream_t st) {
     const float sq = 1.0f / sqrtf((float)d.Q), sp = 1.0f / sqrtf((float)d.P);
     const int slices = d.T * d.R;
+    const int cP = col_tile_for(d, false), cR = col_tile_for(d, true);
     cudaError_t e = inv ? row_fft<true>(d.Q, x, y, slices * d.P, sq, tw.twQ, st)
                         : row_fft<false>(d.Q, x, y, slices * d.P, sq, tw.twQ, st);
     if (e != cudaSuccess) return e;
-    e = inv ? col_pass<COL_INV>(d.P, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st)
-            : col_pass<COL_FWD>(d.P, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st);
+    e = inv ? col_pass<COL_INV>(d.P, cP, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st)
+            : col_pass<COL_FWD>(d.P, cP, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st);
     if (e != cudaSuccess || d.R == 1) return e;
     const float sr = 1.0f / sqrtf((float)d.R);
     const int pq = d.P * d.Q;
-    return inv ? col_pass<COL_INV, true>(d.R, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st)
-               : col_pass<COL_FWD, true>(d.R, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st);
+    return inv ? col_pass<COL_INV>(d.R, cR, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st)
+               : col_pass<COL_FWD>(d.R, cR, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st);
 }
 
 cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int b_bf16,
@@ -479,13 +501,15 @@ cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int
     if (d.R > 1) {
         // masked depth IDFT (with the whole 1/sqrt(PQR)), then the column IDFT of every slice
         const int pq = d.P * d.Q, slices = d.T * d.R;
-        e = b_bf16 ? col_pass<COL_ADJ_BF16, true>(d.R, pq, d.T, d.T, b, t, mask, sc, tw.twR, st)
-                   : col_pass<COL_ADJ_C64, true>(d.R, pq, d.T, d.T, b, t, mask, sc, tw.twR, st);
+        const int cP = col_tile_for(d, false), cR = col_tile_for(d, true);
+        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.R, cR, pq, d.T, d.T, b, t, mask, sc, tw.twR, st)
+                   : col_pass<COL_ADJ_C64>(d.R, cR, pq, d.T, d.T, b, t, mask, sc, tw.twR, st);
         if (e != cudaSuccess) return e;
-        e = col_pass<COL_INV, true>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+        e = col_pass<COL_INV>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
     } else {
-        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st)
-                   : col_pass<COL_ADJ_C64>(d.P, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st);
+        const int cP = col_tile_for(d, false);
+        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, cP, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st)
+                   : col_pass<COL_ADJ_C64>(d.P, cP, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st);
     }
     if (e != cudaSuccess) return e;
     return row_fft<true>(d.Q, t, x, d.T * d.rows(), 1.0f, tw.twQ, st);
@@ -546,7 +570,8 @@ cudaError_t launch_coil_row_fwd(const Dims& d, const Twiddles& tw, const float2*
 cudaError_t launch_adjoint_coils_cols(const Dims& d, const Twiddles& tw, const void* b,
                                       const uint8_t* mask, float2* t, cudaStream_t st) {
     const float sc = 1.0f / sqrtf((float)d.P * (float)d.Q);
-    return col_pass<COL_ADJ_C64>(d.P, d.Q, d.T * d.nc, d.T, b, t, mask, sc, tw.twP, st);
+    return col_pass<COL_ADJ_C64>(d.P, col_tile_for(d, false), d.Q, d.T * d.nc, d.T, b, t, mask,
+                                 sc, tw.twP, st);
 }
 
 cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
@@ -556,19 +581,21 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
         // of the two unnormalised transforms), column IDFT of every slice
         const int pq = d.P * d.Q, slices = d.T * d.R;
         const float sc3 = 1.0f / ((float)d.P * (float)d.Q * (float)d.R);
+        const int cP = col_tile_for(d, false), cR = col_tile_for(d, true);
         cudaError_t e =
-            col_pass<COL_FWD, true>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+            col_pass<COL_FWD>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
         if (e != cudaSuccess) return e;
-        e = col_pass<COL_MASK_OP, true>(d.R, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
+        e = col_pass<COL_MASK_OP>(d.R, cR, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
         if (e != cudaSuccess) return e;
-        return col_pass<COL_INV, true>(d.P, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+        return col_pass<COL_INV>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
     }
     const float sc = 1.0f / ((float)d.P * (float)d.Q);
     const int frames = d.T * d.nc;  // coil-major: the mask of frame f is mask frame f % T
     if (d.P == 256)
         return launch_pdl(col_mask_256_kernel, dim3(d.Q / kColTile, frames), dim3(128), 0, st, t,
                           mask, d.Q, d.T, sc, tw.twP);
-    return col_pass<COL_MASK_OP>(d.P, d.Q, frames, d.T, t, t, mask, sc, tw.twP, st);
+    return col_pass<COL_MASK_OP>(d.P, col_tile_for(d, false), d.Q, frames, d.T, t, t, mask, sc,
+                                 tw.twP, st);
 }
 
 }  // namespace recon

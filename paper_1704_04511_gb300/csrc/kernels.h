@@ -20,6 +20,7 @@ struct Dims {
     int R = 1;   // depth of a volume (third spatial axis, circular like the other two)
     int N3 = 1;  // filter taps along the depth
     int circ = 0;  // 1: lifting circular in time as well (the fully circulant GIRAF form)
+    int colC = 0, depthC = 0;  // column tiles of the column / depth passes (0 = default)
     int k() const { return circ ? T : T - M + 1; }
     int npair() const { return M * (M + 1) / 2; }
     int L1() const { return 2 * N1 - 1; }
@@ -77,6 +78,8 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 int num_sms();
 
 bool fft_size_supported(int n);
+// Column tile the length-P (depth = false) or depth passes of `d` use (fft.cu).
+int col_tile_for(const Dims& d, bool depth);
 // Message returned by recon_last_error(NULL) (calls that have no context).
 void set_context_free_error(const std::string& msg);
 int w_max_M();

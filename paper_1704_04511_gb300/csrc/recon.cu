@@ -19,7 +19,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <map>
+#include <sstream>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -67,13 +70,17 @@ struct recon_ctx {
         int T, P, Q, N1, N2, M, irls, cg, bf16, method, R, N3;
         double lambda, p, gamma, eps0_frac;
         const void *kspace, *masks, *out, *coils;
-        int nc, coil_proj, circ, variant;
+        int nc, coil_proj, circ, variant, colC, depthC;
         unsigned long ws_gen;
     };
     GraphKey gkey = {};
     cudaGraphExec_t gexec = nullptr;   // the active slot's captured solve
     bool graphs = true;
     bool cluster_fft = false;          // square frames: cluster 2-D transform kernel (opt-in)
+    // autotuner: column tile widths per problem shape (P, Q, T, R, coils), timed on first use
+    bool autotune = true;
+    std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tiles;
+    std::string tile_cache;            // file the tuned choices are appended to (may be empty)
     struct Slot {
         cudaStream_t stream = nullptr;
         bool own_stream = false;
@@ -587,6 +594,79 @@ struct Solve {
     double* veps = nullptr;         // HLR-Voxel: per-pixel eps state [R P Q]
 };
 
+// Autotuner of the column passes: on the first solve of a shape (P, Q, T, R, coils) the context
+// times the column stage of the CG operator (launch_col_mask, one warm-up and three timed
+// launches per candidate, CUDA events on the solve's stream) for tile widths of 8, 16 and 32
+// columns -- first for the length-P passes, then, for volumes, for the depth passes -- and keeps
+// the fastest. The width changes only the launch shape: every column is transformed by the same
+// arithmetic, so results do not depend on the choice. Choices are cached per context and, when a
+// cache file is set (recon_tile_cache), appended to it and read back by later contexts.
+int autotune_tiles(recon_ctx* c, Dims* d, const Twiddles& tw, float2* t, const uint8_t* mask) {
+    const auto key = std::make_tuple(d->P, d->Q, d->T, d->R, d->nc);
+    auto it = c->tiles.find(key);
+    if (it != c->tiles.end()) {
+        d->colC = it->second.first;
+        d->depthC = it->second.second;
+        return RECON_OK;
+    }
+    if (!c->autotune) return RECON_OK;
+    cudaEvent_t e0, e1;
+    RC_CUDA(cudaEventCreate(&e0));
+    RC_CUDA(cudaEventCreate(&e1));
+    auto time_it = [&](Dims& dd, float* ms) -> cudaError_t {
+        cudaError_t e = recon::launch_col_mask(dd, tw, t, mask, c->stream);
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = recon::launch_col_mask(dd, tw, t, mask, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        return e;
+    };
+    cudaError_t err = cudaSuccess;
+    const int cand[3] = {8, 16, 32};
+    Dims dd = *d;
+    // the length-P passes (the 256-row image-series pass is a register kernel without tiles)
+    if (!(d->R == 1 && d->P == 256)) {
+        float best = 1e30f;
+        int bestC = recon::col_tile_for(*d, false);
+        for (int C : cand) {
+            if (d->Q % C) continue;
+            dd.colC = C;
+            float ms = 0.f;
+            err = time_it(dd, &ms);
+            if (err != cudaSuccess) break;
+            if (ms < best) { best = ms; bestC = C; }
+        }
+        dd.colC = bestC;
+    }
+    if (err == cudaSuccess && d->R > 1) {
+        float best = 1e30f;
+        int bestC = recon::col_tile_for(*d, true);
+        for (int C : cand) {
+            if ((d->P * d->Q) % C) continue;
+            dd.depthC = C;
+            float ms = 0.f;
+            err = time_it(dd, &ms);
+            if (err != cudaSuccess) break;
+            if (ms < best) { best = ms; bestC = C; }
+        }
+        dd.depthC = bestC;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(c, err, "autotuner");
+    d->colC = dd.colC;
+    d->depthC = dd.depthC;
+    c->tiles[key] = {d->colC, d->depthC};
+    if (!c->tile_cache.empty()) {
+        std::ofstream f(c->tile_cache, std::ios::app);
+        if (f) f << d->P << ' ' << d->Q << ' ' << d->T << ' ' << d->R << ' ' << d->nc << ' '
+                 << d->colC << ' ' << d->depthC << '\n';
+    }
+    return RECON_OK;
+}
+
 // Twiddles, eigensolver handle and workspace of one solve on the active slot (no stream work).
 int solve_prepare(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* masks,
                   const recon_params* prm, void* image_out, Solve* sv) {
@@ -602,7 +682,9 @@ int solve_prepare(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t
         rc = ensure_solver(c);
         if (rc) return rc;
     }
-    return get_work(c, d, prm->cg, prm->irls, true, eig, &sv->w);
+    rc = get_work(c, d, prm->cg, prm->irls, true, eig, &sv->w);
+    if (rc) return rc;
+    return autotune_tiles(c, &sv->d, sv->tw, sv->w.t, masks);
 }
 
 // HLR-Voxel: the per-pixel eps state of a solve (after solve_prepare).
@@ -677,7 +759,7 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     k.lambda = prm->lambda; k.p = prm->p; k.gamma = prm->gamma; k.eps0_frac = prm->eps0_frac;
     k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
     k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
-    k.circ = sv.d.circ; k.variant = sv.variant;
+    k.circ = sv.d.circ; k.variant = sv.variant; k.colC = sv.d.colC; k.depthC = sv.d.depthC;
     if (!c->gexec || std::memcmp(&k, &c->gkey, sizeof(k)) != 0) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -1748,8 +1830,41 @@ int recon_set_option(recon_ctx* c, int option, int value) {
     switch (option) {
         case RECON_OPT_GRAPHS: c->graphs = value != 0; return RECON_OK;
         case RECON_OPT_CLUSTER_FFT: c->cluster_fft = value != 0; return RECON_OK;
+        case RECON_OPT_AUTOTUNE: c->autotune = value != 0; return RECON_OK;
         default: return fail(c, RECON_EINVAL, "unknown option");
     }
+}
+
+int recon_tile_cache(recon_ctx* c, const char* path) {
+    if (!c) return RECON_EINVAL;
+    if (!path) {
+        c->tile_cache.clear();
+        return RECON_OK;
+    }
+    std::ifstream f(path);
+    std::string line;
+    auto width_ok = [](int v) { return v == 0 || v == 8 || v == 16 || v == 32; };
+    while (f && std::getline(f, line)) {
+        std::istringstream ls(line);
+        int P, Q, T, R, nc, colC, depthC;
+        if (!(ls >> P >> Q >> T >> R >> nc >> colC >> depthC) || !width_ok(colC) || !width_ok(depthC))
+            return fail(c, RECON_EINVAL, "tile cache: malformed entry in " + std::string(path));
+        c->tiles[std::make_tuple(P, Q, T, R, nc)] = {colC, depthC};
+    }
+    c->tile_cache = path;
+    return RECON_OK;
+}
+
+int recon_tile_choice(recon_ctx* c, recon_dims3 dd, int n_coils, int* colC, int* depthC) {
+    if (!c || !colC || !depthC) return RECON_EINVAL;
+    auto it = c->tiles.find(std::make_tuple(dd.P, dd.Q, dd.T, dd.R, n_coils));
+    if (it == c->tiles.end()) {
+        *colC = *depthC = 0;
+        return RECON_OK;
+    }
+    *colC = it->second.first;
+    *depthC = it->second.second;
+    return RECON_OK;
 }
 
 int recon_profile(recon_ctx* c, unsigned int kind_mask) {

@@ -48,7 +48,8 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_solve_coils", "recon_adjoint_coils", "recon_apply_normal_coils",
             "recon_bytes_needed3", "recon_solve3", "recon_adjoint3", "recon_fft3", "recon_gram3",
             "recon_weight3", "recon_apply_normal3", "recon_solve_variant", "recon_gram_variant",
-            "recon_voxel_weight", "recon_weight_direct", "recon_apply_normal_variant")
+            "recon_voxel_weight", "recon_weight_direct", "recon_apply_normal_variant",
+            "recon_tile_cache", "recon_tile_choice")
 
 PROF_KINDS = 15
 
@@ -141,6 +142,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_voxel_weight": (i, [vp, dims, i, vp, vp, d, vp, vp]),
             "recon_weight_direct": (i, [vp, dims, filt, vp, d, d, i, vp, ctypes.POINTER(d)]),
             "recon_apply_normal_variant": (i, [vp, dims, filt, i, vp, vp, d, vp, vp]),
+            "recon_tile_cache": (i, [vp, ctypes.c_char_p]),
+            "recon_tile_choice": (i, [vp, dims3, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -262,6 +265,25 @@ def recon_solve_batch(ctx, kspaces, masks_list, filt, lam: float, p: float, irls
 
 RECON_OPT_GRAPHS = 1
 RECON_OPT_CLUSTER_FFT = 2
+RECON_OPT_AUTOTUNE = 3
+
+
+def recon_tile_cache(ctx, path) -> None:
+    """Read tuned column-tile choices from `path` and append new ones to it (None: stop)."""
+    _check(ctx, load_library().recon_tile_cache(ctx, None if path is None else str(path).encode()))
+
+
+def recon_tile_choice(ctx, shape, n_coils: int = 1):
+    """(colC, depthC) the context uses for shape (T, P, Q) or (T, R, P, Q); 0 = not tuned."""
+    if len(shape) == 3:
+        T, P, Q = shape
+        R = 1
+    else:
+        T, R, P, Q = shape
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(ctx, load_library().recon_tile_choice(ctx, recon_dims3(P=P, Q=Q, R=R, T=T), int(n_coils),
+                                                 ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def recon_set_option(ctx, option: int, value: int) -> None:
