@@ -276,6 +276,7 @@ def run_vol(steps: int, device: int) -> dict:
         e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
         need = recon.recon_bytes_needed3(tuple(m.shape), filt)
+        tiles = recon.recon_tile_choice(ctx.h, tuple(m.shape))
     finally:
         ctx.close()
     peak, peak_src = load_peaks()
@@ -301,6 +302,7 @@ def run_vol(steps: int, device: int) -> dict:
             "irls_iters_per_s": round(1000.0 * w.n_irls / ms, 2),
             "voxel_frame_cg_steps_per_s": round(T * D * P * Q * w.n_irls * w.n_cg / (ms / 1000.0), 1),
             "hbm_peak_GBs": peak, "hbm_peak_source": peak_src, "classes": classes,
+            "column_tiles": {"length_P": tiles[0], "depth": tiles[1]},
             "footprint": {"workspace_bytes": int(need),
                           "lifted_matrix_bytes_complex64": int(rows_lifted * s * 8),
                           "gram_bytes_complex128": int(s * s * 16)},

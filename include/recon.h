@@ -140,6 +140,13 @@ int recon_poll(recon_ctx* c, int ticket, int* done);
 #define RECON_OPT_GRAPHS 1      /* default on  */
 #define RECON_OPT_CLUSTER_FFT 2 /* default off */
 #define RECON_OPT_AUTOTUNE 3    /* default on  */
+/* RECON_OPT_THREE_PASS: 256 x 256 single-coil series run each CG step in three passes -- the
+ *   step's scalar <p, (A^H A + lambda W) p> is assembled from partials of ||A p||^2 (column pass)
+ *   and <p, W p> (row pass), so the last pass applies alpha and updates x and r itself, and q is
+ *   never stored (17 % fewer bytes per step); off = the four-pass step (row, column, row + W,
+ *   update), which measures faster on one GB300 while the series fits in L2. Same CG in exact
+ *   arithmetic; rounding differs at the FP32 level. */
+#define RECON_OPT_THREE_PASS 4  /* default off */
 int recon_set_option(recon_ctx* c, int option, int value);
 
 

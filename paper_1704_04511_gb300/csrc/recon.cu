@@ -70,7 +70,7 @@ struct recon_ctx {
         int T, P, Q, N1, N2, M, irls, cg, bf16, method, R, N3;
         double lambda, p, gamma, eps0_frac;
         const void *kspace, *masks, *out, *coils;
-        int nc, coil_proj, circ, variant, colC, depthC;
+        int nc, coil_proj, circ, variant, colC, depthC, three_pass;
         unsigned long ws_gen;
     };
     GraphKey gkey = {};
@@ -79,6 +79,7 @@ struct recon_ctx {
     bool cluster_fft = false;          // square frames: cluster 2-D transform kernel (opt-in)
     // autotuner: column tile widths per problem shape (P, Q, T, R, coils), timed on first use
     bool autotune = true;
+    bool three_pass = false;           // 256 x 256 series: three-pass CG step (RECON_OPT_THREE_PASS)
     std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tiles;
     std::string tile_cache;            // file the tuned choices are appended to (may be empty)
     struct Slot {
@@ -294,7 +295,7 @@ int check_dims3(recon_ctx* c, recon_dims3 dd, const recon_filter3* f, Dims* d) {
 struct Work {
     float2 *r, *p, *t, *S0, *S1;
     double2 *G, *lag_part, *lags, *dpart, *dsum, *Z, *eigwork;
-    double *evals, *parts, *rparts, *rr, *pq, *eps, *lmax;
+    double *evals, *parts, *rparts, *mparts, *rr, *pq, *eps, *lmax;
     unsigned int* counter;
     int *info, *kerr;
     void *hpd, *lanc;
@@ -346,6 +347,7 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
     GET("Z", recon::s_scratch_bytes(d), Z, double2*);
     GET("parts", (size_t)recon::max_parts() * sizeof(double), parts, double*);
     GET("rparts", (size_t)recon::max_parts() * sizeof(double), rparts, double*);
+    GET("mparts", (size_t)recon::max_parts() * sizeof(double), mparts, double*);
     GET("counter", 256, counter, unsigned int*);
     GET("rr", (size_t)(n_cg + 1) * sizeof(double), rr, double*);
     GET("pq", (size_t)(n_cg + 1) * sizeof(double), pq, double*);
@@ -471,6 +473,28 @@ int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uin
     // the update pass; the update pass leaves those of |r|^2 in w.rparts for the next pass A,
     // which also stores the sum in rr[it] (rr[0] comes from the residual carry).
     recon::Partials pq{w.parts, 0}, rr{w.rparts, 0};
+    if (!coils && c->three_pass && recon::fused3_supported(d)) {
+        // three passes per step: <p, q> from the quadratic forms' partials of passes A3 and B3,
+        // so that pass C3 applies alpha and no separate update pass is needed
+        recon::Partials pw{w.parts, 0}, mp{w.mparts, 0};
+        for (int it = 0; it < n_cg; ++it) {
+            const double* rr_prev = it > 0 ? w.rr + it - 1 : w.rr;
+            {
+                ProfScope ps(c, RECON_PROF_CG_ROWFWD);
+                RC_CUDA(recon::launch_row_fwd_w(d, tw, w.r, w.p, w.t, S_new, rr, rr_prev, w.rr + it,
+                                                it == 0, &pw, c->stream));
+            }
+            {
+                ProfScope ps(c, RECON_PROF_CG_COL);
+                RC_CUDA(recon::launch_col_mask_parts(d, tw, w.t, mask, &mp, c->stream));
+            }
+            ProfScope ps(c, RECON_PROF_CG_ROWINVW);
+            RC_CUDA(recon::launch_row_inv_w_upd(d, tw, w.t, w.p, S_new, lam, x, w.r, pw, mp,
+                                                w.rr + it, w.pq + it, &rr, c->stream));
+        }
+        if (n_cg > 0) RC_CUDA(recon::launch_sum_partials(rr, w.rr + n_cg, c->stream));
+        return RECON_OK;
+    }
     const bool fused = c->cluster_fft && recon::frame_op_supported(d) && !coils;
     for (int it = 0; it < n_cg; ++it) {
         const double* rr_prev = it > 0 ? w.rr + it - 1 : w.rr;
@@ -760,6 +784,7 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
     k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
     k.circ = sv.d.circ; k.variant = sv.variant; k.colC = sv.d.colC; k.depthC = sv.d.depthC;
+    k.three_pass = c->three_pass;
     if (!c->gexec || std::memcmp(&k, &c->gkey, sizeof(k)) != 0) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -1831,6 +1856,7 @@ int recon_set_option(recon_ctx* c, int option, int value) {
         case RECON_OPT_GRAPHS: c->graphs = value != 0; return RECON_OK;
         case RECON_OPT_CLUSTER_FFT: c->cluster_fft = value != 0; return RECON_OK;
         case RECON_OPT_AUTOTUNE: c->autotune = value != 0; return RECON_OK;
+        case RECON_OPT_THREE_PASS: c->three_pass = value != 0; return RECON_OK;
         default: return fail(c, RECON_EINVAL, "unknown option");
     }
 }

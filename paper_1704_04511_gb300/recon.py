@@ -266,6 +266,7 @@ def recon_solve_batch(ctx, kspaces, masks_list, filt, lam: float, p: float, irls
 RECON_OPT_GRAPHS = 1
 RECON_OPT_CLUSTER_FFT = 2
 RECON_OPT_AUTOTUNE = 3
+RECON_OPT_THREE_PASS = 4
 
 
 def recon_tile_cache(ctx, path) -> None:

@@ -256,3 +256,19 @@ def test_volume_errors(R):
     with pytest.raises(recon.ReconError) as e:
         recon.recon_fft3(ctx.h, bad, bad)
     assert e.value.code == recon.RECON_EINVAL
+
+
+def test_solve3_bf16_kspace(R):
+    """Volumes with k-space stored as bfloat16 pairs (FP32 transforms and CG, FP64 weight): the
+    oracle gets the same bfloat16-rounded k-space, so the gate measures the solver."""
+    recon, ctx = R
+    w, prob = _small()
+    bt = torch.view_as_real(torch.from_numpy(c64(prob["kspace"]))).to(torch.bfloat16).contiguous()
+    b_rounded = torch.view_as_complex(bt.float()).numpy().astype(np.complex128)
+    masks = prob["masks"]
+    out = torch.empty(masks.shape, dtype=torch.complex64, device="cuda")
+    recon.recon_solve3(ctx.h, bt.cuda(), to_dev(masks), _filt(w), w.lam, w.p, w.n_irls, w.n_cg, out)
+    x_ref = slr3.irls3(b_rounded, masks, w.N1, w.N2, w.N3, w.M, w.lam, w.p, w.n_irls, w.n_cg)
+    err = rel(out.cpu().numpy(), x_ref)
+    print(f"\n[solve3 bf16 k-space] {err:.2e}; NRMSE {rel(out.cpu().numpy(), prob['x_true']):.5f}")
+    assert err < 1e-4

@@ -389,3 +389,24 @@ def test_errors(R):
         assert e.value.code == recon.RECON_ENOMEM
     finally:
         small.close()
+
+
+def test_three_pass_step_matches_four_pass_step(R):
+    """The three-pass CG step (scalar from the quadratic forms' partials, update inside the last
+    pass) against the four-pass step on the 256x256x16 series: same CG, FP32 rounding apart."""
+    recon, ctx = R
+    w, prob = _problem("perf_256x256x16", n_irls=3, n_cg=8)
+    b = to_dev(c64(prob["kspace"]))
+    m = to_dev(prob["masks"])
+    outs = []
+    for three in (1, 0):
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_THREE_PASS, three)
+        out = torch.empty(prob["masks"].shape, dtype=torch.complex64, device="cuda")
+        recon.recon_solve(ctx.h, b, m, (w.N1, w.N2, w.M), w.lam, w.p, w.n_irls, w.n_cg, out)
+        outs.append(out.cpu().numpy())
+    x_ref = slr.irls(c64(prob["kspace"]).astype(np.complex128), prob["masks"], w.N1, w.N2, w.M,
+                     w.lam, w.p, w.n_irls, w.n_cg)
+    err = rel(outs[0], outs[1])
+    print(f"\n[three-pass vs four-pass 256x256x16, 3 x 8] {err:.2e}; three-pass vs oracle "
+          f"{rel(outs[0], x_ref):.2e}")
+    assert err < 1e-5 and rel(outs[0], x_ref) < 1e-4
