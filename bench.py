@@ -542,8 +542,12 @@ def main():
     sampler = ClockSampler(gpu_id) if rank == 0 else None
 
     # ---- timed region: K steps of B concurrent solves; only the dominant launch class is
-    # bracketed by events inside it; L2 flushed before each step (outside the events)
+    # bracketed by events inside it (event nodes of the captured solve graphs, read after the
+    # region: the last step's launches); L2 flushed before each step (outside the events). One
+    # untimed step first captures the graphs with those event nodes.
     recon.recon_profile(ctx.h, 1 << dom_kind)
+    step()
+    torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)

@@ -44,6 +44,19 @@ struct TwTable {
     double2* d = nullptr;
 };
 
+// Timing events captured into a solve's CUDA graph (event-record nodes): the launch class and
+// the event pair of every timed launch, and how many replays have run / been read.
+struct GraphProf {
+    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> ev;
+    unsigned long replays = 0, collected = 0;
+    ~GraphProf() {
+        for (auto& t : ev) {
+            cudaEventDestroy(std::get<1>(t));
+            cudaEventDestroy(std::get<2>(t));
+        }
+    }
+};
+
 thread_local std::string g_create_error;
 
 }  // namespace
@@ -71,10 +84,13 @@ struct recon_ctx {
         double lambda, p, gamma, eps0_frac;
         const void *kspace, *masks, *out, *coils;
         int nc, coil_proj, circ, variant, colC, depthC, three_pass;
+        unsigned int prof;
         unsigned long ws_gen;
     };
     GraphKey gkey = {};
     cudaGraphExec_t gexec = nullptr;   // the active slot's captured solve
+    GraphProf* gprof = nullptr;        // its timing events (launch classes timed when captured)
+    GraphProf* capturing = nullptr;    // set while a solve with timed classes is being captured
     bool graphs = true;
     bool cluster_fft = false;          // square frames: cluster 2-D transform kernel (opt-in)
     // autotuner: column tile widths per problem shape (P, Q, T, R, coils), timed on first use
@@ -90,6 +106,7 @@ struct recon_ctx {
         unsigned long ws_gen = 0;
         GraphKey gkey = {};
         cudaGraphExec_t gexec = nullptr;
+        GraphProf* gprof = nullptr;
     };
     std::vector<Slot> slots;  // slots[i] valid while i != active
     int active = 0;
@@ -122,14 +139,27 @@ int cuda_fail(recon_ctx* c, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);       \
     } while (0)
 
-// Bracket one launch of `kind` with two events when profiling is on.
+// Bracket one launch of `kind` with two events when profiling is on. While a solve is being
+// captured into a CUDA graph the events become event-record nodes of the graph (read after each
+// replay by prof_collect); otherwise they come from the context's pool.
 struct ProfScope {
     recon_ctx* c;
     int kind;
     size_t i0 = 0;
     bool on = false;
+    cudaEvent_t g0 = nullptr, g1 = nullptr;
     ProfScope(recon_ctx* c_, int kind_) : c(c_), kind(kind_) {
         if (!(c->prof & (1u << kind))) return;
+        if (c->capturing) {
+            if (cudaEventCreate(&g0) != cudaSuccess) return;
+            if (cudaEventCreate(&g1) != cudaSuccess) {
+                cudaEventDestroy(g0);
+                return;
+            }
+            cudaEventRecordWithFlags(g0, c->stream, cudaEventRecordExternal);
+            on = true;
+            return;
+        }
         if (c->ev_used + 2 > c->ev_pool.size()) {
             for (int k = 0; k < 256; ++k) {
                 cudaEvent_t e;
@@ -144,13 +174,34 @@ struct ProfScope {
     }
     ~ProfScope() {
         if (!on) return;
+        if (g0) {
+            cudaEventRecordWithFlags(g1, c->stream, cudaEventRecordExternal);
+            c->capturing->ev.emplace_back(kind, g0, g1);
+            return;
+        }
         cudaEventRecord(c->ev_pool[i0 + 1], c->stream);
         c->prof_pending.push_back({kind, i0});
     }
 };
 
-// Fold the recorded event pairs into the per-kind totals (synchronises on the events).
+void collect_graph(recon_ctx* c, GraphProf* gp) {
+    if (!gp || gp->replays == gp->collected) return;
+    for (auto& t : gp->ev) {  // the most recent replay's launches
+        float ms = 0.f;
+        cudaEventSynchronize(std::get<2>(t));
+        if (cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)) == cudaSuccess) {
+            c->prof_ms[std::get<0>(t)] += ms;
+            c->prof_n[std::get<0>(t)] += 1;
+        }
+    }
+    gp->collected = gp->replays;
+}
+
+// Fold the recorded event pairs into the per-kind totals (synchronises on the events); for solves
+// replayed from a graph, the launches of the latest replay not yet read.
 void prof_collect(recon_ctx* c) {
+    collect_graph(c, c->gprof);
+    for (auto& sl : c->slots) collect_graph(c, sl.gprof);
     for (auto& pk : c->prof_pending) {
         float ms = 0.f;
         cudaEventSynchronize(c->ev_pool[pk.second + 1]);
@@ -555,6 +606,7 @@ int select_slot(recon_ctx* c, int i) {
     park.ws_gen = c->ws_gen;
     park.gkey = c->gkey;
     park.gexec = c->gexec;
+    park.gprof = c->gprof;
     auto& next = c->slots[i];
     if (!next.stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&next.stream, cudaStreamNonBlocking);
@@ -571,6 +623,7 @@ int select_slot(recon_ctx* c, int i) {
     c->ws_gen = next.ws_gen;
     c->gkey = next.gkey;
     c->gexec = next.gexec;
+    c->gprof = next.gprof;
     next = recon_ctx::Slot{};
     c->active = i;
     return RECON_OK;
@@ -769,7 +822,7 @@ int solve_iter(recon_ctx* c, Solve& sv, int n) {
 // library path is used, or while launch classes are being timed.
 int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     const recon_params* prm = sv.prm;
-    const bool direct = !c->graphs || c->prof || wants_eig(prm->p, prm->weight_method);
+    const bool direct = !c->graphs || wants_eig(prm->p, prm->weight_method);
     if (direct) {
         int rc = solve_begin(c, &sv);
         for (int n = 0; n < prm->irls && !rc; ++n) rc = solve_iter(c, sv, n);
@@ -785,16 +838,21 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
     k.circ = sv.d.circ; k.variant = sv.variant; k.colC = sv.d.colC; k.depthC = sv.d.depthC;
     k.three_pass = c->three_pass;
+    k.prof = c->prof;
     if (!c->gexec || std::memcmp(&k, &c->gkey, sizeof(k)) != 0) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }
+        delete c->gprof;
+        c->gprof = c->prof ? new GraphProf() : nullptr;
+        c->capturing = c->gprof;
         RC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
         int rc = solve_begin(c, &sv);
         for (int n = 0; n < prm->irls && !rc; ++n) rc = solve_iter(c, sv, n);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+        c->capturing = nullptr;
         if (rc) {
             if (g) cudaGraphDestroy(g);
             return rc;
@@ -809,6 +867,7 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
         c->gkey = k;
     }
     RC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    if (c->gprof) ++c->gprof->replays;
     return RECON_OK;
 }
 
@@ -1242,6 +1301,7 @@ void recon_destroy(recon_ctx* c) {
     for (auto& sl : c->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
+        delete sl.gprof;
         for (auto& kv : sl.bufs)
             if (kv.second.ptr) cudaFree(kv.second.ptr);
         if (sl.solver) cusolverDnDestroy(sl.solver);
@@ -1260,6 +1320,7 @@ void recon_destroy(recon_ctx* c) {
         delete pd;
     }
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    delete c->gprof;
     if (c->solver) cusolverDnDestroy(c->solver);
     if (c->blas) cublasDestroy(c->blas);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1434,7 +1495,7 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
     std::vector<Solve> sv(n);
     rc = RECON_OK;
     cudaError_t e = cudaEventRecord(start, c->stream);
-    const bool direct = !c->graphs || c->prof || wants_eig(prm->p, prm->weight_method);
+    const bool direct = !c->graphs || wants_eig(prm->p, prm->weight_method);
     for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
         rc = select_slot(c, i);
         if (!rc) e = cudaStreamWaitEvent(c->stream, start, 0);
@@ -1895,7 +1956,7 @@ int recon_tile_choice(recon_ctx* c, recon_dims3 dd, int n_coils, int* colC, int*
 
 int recon_profile(recon_ctx* c, unsigned int kind_mask) {
     if (!c) return RECON_EINVAL;
-    prof_collect(c);
+    prof_collect(c);  // drop what was recorded so far (the totals are reset below)
     for (int k = 0; k < RECON_PROF_KINDS; ++k) {
         c->prof_ms[k] = 0.0;
         c->prof_n[k] = 0;
