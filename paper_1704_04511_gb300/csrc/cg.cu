@@ -370,8 +370,9 @@ row_inv_w_upd_256_kernel(const float2* __restrict__ t, const float2* __restrict_
 }
 
 // Pass C for 128-point rows: as row_inv_w_256_kernel with 8 threads per frame (row_dft128), the
-// block padded to a multiple of four frames (whole warps). Shared memory: p rows [T][128], then
-// the exchange buffers [T'][kX128] which afterwards hold the transformed rows [T][128].
+// block padded to a multiple of four frames (whole warps) and to at least 16 frames (128 threads,
+// one column each in the W phase). Shared memory: p rows [T][128], then the exchange buffers
+// [T'][kX128] which afterwards hold the transformed rows [T][128].
 template <int M>
 __global__ void __launch_bounds__(1024)
 row_inv_w_128_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
@@ -713,7 +714,8 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
     const int rows = d.rows();
     int grid = 0;
     if (N == 128 && !d.circ) {  // register transforms for the valid (non-circular) lifting
-        const int tpad = (d.T + 3) / 4 * 4;
+        // whole warps, and at least 128 threads so that the W phase has one column per thread
+        const int tpad = d.T <= 16 ? 16 : (d.T + 3) / 4 * 4;
         const size_t smem128 = ((size_t)d.T * N + (size_t)tpad * kX128) * sizeof(float2);
         if (tpad * 8 <= 1024 && smem128 <= 200 * 1024) {
             auto k = row_inv_w_128_kernel<M>;
