@@ -199,6 +199,21 @@ def cpu_oracle_rate(w, prob, budget_s: float = 12.0, max_iters: int = 6):
     return n / dt, n, dt, cores
 
 
+def cpu_oracle_one_thread(budget_s: float = 6.0):
+    """The same oracle sample with one BLAS / OpenMP thread, in a child process (the thread count
+    is fixed when NumPy loads); None if the child fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench, synth; w = synth.workload(bench.WORKLOAD); "
+            "p = synth.make_problem(w); r = bench.cpu_oracle_rate(w, p, budget_s=%r, max_iters=3); "
+            "print(json.dumps(r[0]))" % budget_s)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                             text=True, timeout=300)
+        return float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    except Exception:
+        return None
+
+
 def run_coils(steps: int, device: int) -> dict:
     """The multi-coil workload (128x128x12, 12 coils): whole solves, device-resident inputs,
     timed with CUDA events."""
@@ -677,6 +692,9 @@ def main():
             "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} IRLS iterations of {WORKLOAD} (Gram + eigh + weight + {w.n_cg} CG) "
                       f"in {dt:.1f} s, FP64 NumPy; numpy.fft single-threaded, eigh on BLAS threads"}
+        one = cpu_oracle_one_thread()
+        if one is not None:
+            line["cpu_baseline"]["value_1_thread"] = one
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
