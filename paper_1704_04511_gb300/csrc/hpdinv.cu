@@ -110,24 +110,29 @@ RECON_DEV double rcp_pivot(double a) {
 }
 
 // Inverse of a Hermitian positive-definite 8 x 8 tile (full, column-major) by 8 scalar sweeps,
-// which leave -T^{-1}; the negated result goes to `out`. Run by the 64 threads of group 0,
-// ping-ponging between T0 and T1 so that one barrier per pivot suffices. Each sweep is one
-// rank-1 update v = t' - c_i r_j with t' = 0 on the pivot row and column, c = column k with
-// c_k = -1 and r = row k / a_kk with r_k = -1 / a_kk, which gives the row (a_kj / a_kk), the
-// column (a_ik / a_kk) and the pivot (-1 / a_kk) without branches. Every thread forms the
-// reciprocal itself: a warp issues the same FP64 instructions for one lane or for 32.
+// which leave -T^{-1}; the negated result goes to `out`. Run by the 64 threads of group 0, one
+// element each, ping-ponging between T0 and T1 so that one barrier per pivot suffices. Each sweep
+// is one rank-1 update v = t' - c_i r_j with t' = 0 on the pivot row and column, c = column k
+// with c_k = -1 and r = row k / a_kk with r_k = -1 / a_kk, which gives the row (a_kj / a_kk), the
+// column (a_ik / a_kk) and the pivot (-1 / a_kk) without branches. It is evaluated as
+// v = t' - (c_i rr_j) / a_kk with rr = row k (rr_k = -1): the complex product c_i rr_j is formed
+// while the reciprocal is being computed, so that one FMA per component follows it on the
+// dependent chain. Every thread forms the reciprocal itself: a warp issues the same FP64
+// instructions for one lane or for 32.
 RECON_DEV void tile_inverse(double2* T0, double2* T1, double2* out) {
     const int e = threadIdx.x % kTileT, i = e % kB, j = e / kB;
     double2* a = T0;
     double2* b = T1;
 #pragma unroll 1
     for (int k = 0; k < kB; ++k) {
-        const double inv = rcp_pivot(a[k + k * kB].x);
+        const double akk = a[k + k * kB].x;
         const double2 aij = a[i + j * kB], aik = a[i + k * kB], akj = a[k + j * kB];
         const double2 t = (i == k || j == k) ? make_double2(0.0, 0.0) : aij;
         const double2 c = (i == k) ? make_double2(-1.0, 0.0) : aik;
-        const double2 r = (j == k) ? make_double2(-inv, 0.0) : make_double2(akj.x * inv, akj.y * inv);
-        b[i + j * kB] = zfms(c, r, t);
+        const double2 rr = (j == k) ? make_double2(-1.0, 0.0) : akj;
+        const double2 ca = zmul(c, rr);
+        const double inv = rcp_pivot(akk);
+        b[i + j * kB] = make_double2(fma(-ca.x, inv, t.x), fma(-ca.y, inv, t.y));
         group_sync(0);
         double2* sw = a;
         a = b;
