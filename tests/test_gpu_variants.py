@@ -242,3 +242,24 @@ def test_variant_errors(R):
     with pytest.raises(recon.ReconError) as e:
         recon.recon_solve_variant(ctx.h, b, masks, (3, 3, 2), w.lam, w.p, 1, 1, out, 7)
     assert e.value.code == recon.RECON_EINVAL
+
+
+@pytest.mark.parametrize("variant", ["giraf", "hlr_voxel", "direct"])
+def test_variant_solves_p05(R, variant):
+    """Schatten p = 0.5 (the eigendecomposition path of every variant's weight)."""
+    recon, ctx = R
+    w, prob = _tiny(n_irls=4, n_cg=6, p=0.5)
+    b = c64(prob["kspace"]).astype(np.complex128)
+    m = prob["masks"]
+    filt = (w.N1, w.N2, w.M)
+    if variant == "giraf":
+        code, f, x_ref = recon.RECON_VARIANT_GIRAF, filt, V.irls_giraf(b, m, *filt, w.lam, w.p, 4, 6)
+    elif variant == "direct":
+        code, f, x_ref = recon.RECON_VARIANT_DIRECT, filt, V.irls_direct(b, m, *filt, w.lam, w.p, 4, 6)
+    else:
+        code, f = recon.RECON_VARIANT_HLR_VOXEL, (1, 1, 3)
+        x_ref = V.irls_hlr_voxel(b, m, 3, w.lam, w.p, 4, 6)
+    x_gpu = _solve(recon, ctx, w, prob, code, f)
+    err = rel(x_gpu, x_ref)
+    print(f"\n[{variant} p=0.5, 4 x 6] {err:.2e}")
+    assert err < (5e-4 if variant == "hlr_voxel" else 1e-4)
