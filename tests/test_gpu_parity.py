@@ -410,3 +410,26 @@ def test_three_pass_step_matches_four_pass_step(R):
     print(f"\n[three-pass vs four-pass 256x256x16, 3 x 8] {err:.2e}; three-pass vs oracle "
           f"{rel(outs[0], x_ref):.2e}")
     assert err < 1e-5 and rel(outs[0], x_ref) < 1e-4
+
+
+SIZE_CASES = [("192x192x6", dict(P=192, Q=192, T=6, N1=5, N2=5, M=2)),
+              ("512x512x4", dict(P=512, Q=512, T=4, N1=3, N2=3, M=2)),
+              ("16x512x5", dict(P=16, Q=512, T=5, N1=3, N2=7, M=3)),
+              ("512x16x3-M3", dict(P=512, Q=16, T=3, N1=7, N2=3, M=3))]
+
+
+@pytest.mark.parametrize("case", SIZE_CASES, ids=[c[0] for c in SIZE_CASES])
+def test_solve_parity_sizes(R, case):
+    """The largest and the radix-3 transform lengths, very unequal sides and M = T (one window):
+    a short solve against the oracle."""
+    recon, ctx = R
+    kw = dict(case[1], times_ms=tuple(5.0 + 6.0 * n for n in range(case[1]["T"])), n_irls=2, n_cg=3)
+    w, prob = _problem("tiny_32x32x8", **kw)
+    out = torch.empty(prob["masks"].shape, dtype=torch.complex64, device="cuda")
+    recon.recon_solve(ctx.h, to_dev(c64(prob["kspace"])), to_dev(prob["masks"]), (w.N1, w.N2, w.M),
+                      w.lam, w.p, w.n_irls, w.n_cg, out)
+    x_ref = slr.irls(c64(prob["kspace"]).astype(np.complex128), prob["masks"], w.N1, w.N2, w.M,
+                     w.lam, w.p, w.n_irls, w.n_cg)
+    err = rel(out.cpu().numpy(), x_ref)
+    print(f"\n[solve {case[0]} 2 x 3] {err:.2e}")
+    assert err < 1e-4
