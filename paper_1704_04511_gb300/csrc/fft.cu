@@ -397,6 +397,106 @@ col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, int mask
     }
 }
 
+// ---- register-transform column passes of the volume column stage ----
+// 128-point columns (the length-P passes, slices of a volume): 16 columns per 128-thread CTA, 8
+// lanes per column in different warps; lane j loads x[8 n1 + j] (n1 < 16), runs the 16-point
+// DFT and the twiddles w128^(j k1), and after one exchange through shared memory (layout
+// [k1][j][column], conflict-free) runs two 8-point DFTs for k1 = 2j and 2j + 1: it then holds
+// X[k1 + 16 k2]. Unnormalised, forward or inverse, in place (each CTA owns its columns).
+template <bool INV>
+__global__ void __launch_bounds__(128)
+col128_kernel(float2* t, int Q, const float2* __restrict__ tw_g) {
+    constexpr int C = 16;
+    __shared__ float2 tw8[128];
+    __shared__ float2 buf[16 * 8 * C];
+    fill_tw128(tw8, tw_g);
+    pdl_wait();
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int col = blockIdx.x * C + c;
+    const size_t fbase = (size_t)blockIdx.y * 128 * Q;
+    float2 u[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) u[n1] = t[fbase + (size_t)(8 * n1 + j) * Q + col];
+    __syncthreads();  // tw8
+    dft16<INV>(u);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+        float2 w = tw8[k1 * 8 + j];
+        if (INV) w.y = -w.y;
+        u[k1] = cmul(u[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) buf[(k1 * 8 + j) * C + c] = u[k1];
+    __syncthreads();
+    float2 a[8], b[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        a[jj] = buf[((2 * j) * 8 + jj) * C + c];
+        b[jj] = buf[((2 * j + 1) * 8 + jj) * C + c];
+    }
+    SmallDFT<8, INV>::run(a);
+    SmallDFT<8, INV>::run(b);
+    pdl_trigger();
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        t[fbase + (size_t)(2 * j + 16 * k2) * Q + col] = a[k2];
+        t[fbase + (size_t)(2 * j + 1 + 16 * k2) * Q + col] = b[k2];
+    }
+}
+
+// 64-point depth pass with the mask (volumes of depth 64): 32 columns per 256-thread CTA, 8
+// lanes per column; lane j loads x[8 n1 + j], and after the 8-point DFT, the twiddles w64^(j k1)
+// and one exchange it holds X[j + 8 k2]; it applies the mask and the 1/(PQR) scale, then runs the
+// inverse in the mirrored order (8-point IDFT over k2, twiddles w64^(-n2 j), exchange, 8-point
+// IDFT) and ends holding y[j + 8 n1] -- the elements it loaded.
+__global__ void __launch_bounds__(256)
+col_mask_64_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, float scale,
+                   const float2* __restrict__ tw_g) {
+    constexpr int C = 32;
+    __shared__ float2 tw8[64];
+    __shared__ float2 buf[8 * 8 * C];
+    for (int e = threadIdx.x; e < 64; e += blockDim.x) tw8[e] = tw_g[(e / 8) * (e % 8)];
+    pdl_wait();
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int col = blockIdx.x * C + c;
+    const size_t fbase = (size_t)blockIdx.y * 64 * Q;
+    float2 u[8];
+    uint8_t mk[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) u[n1] = t[fbase + (size_t)(8 * n1 + j) * Q + col];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) mk[k2] = mask[fbase + (size_t)(j + 8 * k2) * Q + col];
+    __syncthreads();  // tw8
+    SmallDFT<8, false>::run(u);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) u[k1] = cmul(u[k1], tw8[k1 * 8 + j]);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) buf[(k1 * 8 + j) * C + c] = u[k1];
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) u[jj] = buf[(j * 8 + jj) * C + c];
+    SmallDFT<8, false>::run(u);  // u[k2] = X[j + 8 k2]
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) u[k2] = mk[k2] ? cscale(u[k2], scale) : make_float2(0.f, 0.f);
+    SmallDFT<8, true>::run(u);   // u[n2] = sum_k2 Y[j + 8 k2] w8^(-k2 n2)
+#pragma unroll
+    for (int n2 = 1; n2 < 8; ++n2) {
+        float2 w = tw8[n2 * 8 + j];
+        w.y = -w.y;
+        u[n2] = cmul(u[n2], w);
+    }
+    __syncthreads();  // the first exchange is read
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) buf[(n2 * 8 + j) * C + c] = u[n2];
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) u[jj] = buf[(j * 8 + jj) * C + c];
+    SmallDFT<8, true>::run(u);   // u[n1] = y[j + 8 n1]
+    pdl_trigger();
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) t[fbase + (size_t)(j + 8 * n1) * Q + col] = u[n1];
+}
+
 template <int N>
 size_t row_smem() { return (size_t)(2 * rows_per_cta<N>() * N + N) * sizeof(float2); }
 template <int N, int C>
@@ -600,12 +700,21 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
         const int pq = d.P * d.Q, slices = d.T * d.R;
         const float sc3 = 1.0f / ((float)d.P * (float)d.Q * (float)d.R);
         const int cP = col_tile_for(d, false), cR = col_tile_for(d, true);
+        const bool reg128 = d.P == 128 && d.Q % 16 == 0;  // register transforms where they exist
+        const bool reg64 = d.R == 64 && pq % 32 == 0;
         cudaError_t e =
-            col_pass<COL_FWD>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+            reg128 ? launch_pdl(col128_kernel<false>, dim3(d.Q / 16, slices), dim3(128), 0, st, t,
+                                d.Q, tw.twP)
+                   : col_pass<COL_FWD>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
         if (e != cudaSuccess) return e;
-        e = col_pass<COL_MASK_OP>(d.R, cR, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
+        e = reg64 ? launch_pdl(col_mask_64_kernel, dim3(pq / 32, d.T), dim3(256), 0, st, t, mask, pq,
+                               sc3, tw.twR)
+                  : col_pass<COL_MASK_OP>(d.R, cR, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
         if (e != cudaSuccess) return e;
-        return col_pass<COL_INV>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+        return reg128 ? launch_pdl(col128_kernel<true>, dim3(d.Q / 16, slices), dim3(128), 0, st, t,
+                                   d.Q, tw.twP)
+                      : col_pass<COL_INV>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP,
+                                          st);
     }
     const float sc = 1.0f / ((float)d.P * (float)d.Q);
     const int frames = d.T * d.nc;  // coil-major: the mask of frame f is mask frame f % T
