@@ -444,6 +444,77 @@ col128_kernel(float2* t, int Q, const float2* __restrict__ tw_g) {
     }
 }
 
+// 128-point column pass with the mask (image series of 128 rows, any coil count): the forward
+// transform of col128_kernel, the mask and the 1/(PQ) scale on X[k1 + 16 k2] (k1 = 2j, 2j + 1),
+// then the inverse in the mirrored order -- two 8-point IDFTs over k2, twiddles w128^(-n2 k1),
+// an exchange, a 16-point IDFT over k1 -- so that lane j ends holding y[j + 8 n1], the elements
+// it loaded. Frame blockIdx.y uses mask frame blockIdx.y % mask_frames (coil-major series).
+__global__ void __launch_bounds__(128)
+col_mask_128_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, int mask_frames,
+                    float scale, const float2* __restrict__ tw_g) {
+    constexpr int C = 16;
+    __shared__ float2 tw8[128];
+    __shared__ float2 buf[16 * 8 * C];
+    fill_tw128(tw8, tw_g);
+    pdl_wait();
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int col = blockIdx.x * C + c;
+    const size_t fbase = (size_t)blockIdx.y * 128 * Q;
+    const size_t mbase = (size_t)(blockIdx.y % mask_frames) * 128 * Q;
+    float2 u[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) u[n1] = t[fbase + (size_t)(8 * n1 + j) * Q + col];
+    uint8_t ma[8], mb[8];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        ma[k2] = mask[mbase + (size_t)(2 * j + 16 * k2) * Q + col];
+        mb[k2] = mask[mbase + (size_t)(2 * j + 1 + 16 * k2) * Q + col];
+    }
+    __syncthreads();  // tw8
+    dft16<false>(u);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) u[k1] = cmul(u[k1], tw8[k1 * 8 + j]);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) buf[(k1 * 8 + j) * C + c] = u[k1];
+    __syncthreads();
+    float2 a[8], b[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        a[jj] = buf[((2 * j) * 8 + jj) * C + c];
+        b[jj] = buf[((2 * j + 1) * 8 + jj) * C + c];
+    }
+    SmallDFT<8, false>::run(a);  // a[k2] = X[2j + 16 k2], b[k2] = X[2j + 1 + 16 k2]
+    SmallDFT<8, false>::run(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        a[k2] = ma[k2] ? cscale(a[k2], scale) : make_float2(0.f, 0.f);
+        b[k2] = mb[k2] ? cscale(b[k2], scale) : make_float2(0.f, 0.f);
+    }
+    SmallDFT<8, true>::run(a);   // a[n2] = sum_k2 Y[2j + 16 k2] w8^(-k2 n2)
+    SmallDFT<8, true>::run(b);
+#pragma unroll
+    for (int n2 = 1; n2 < 8; ++n2) {  // w128^(-n2 k1) for k1 = 2j and 2j + 1
+        float2 wa = tw8[(2 * j) * 8 + n2], wb = tw8[(2 * j + 1) * 8 + n2];
+        wa.y = -wa.y;
+        wb.y = -wb.y;
+        a[n2] = cmul(a[n2], wa);
+        b[n2] = cmul(b[n2], wb);
+    }
+    __syncthreads();  // the first exchange is read
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) {
+        buf[((2 * j) * 8 + n2) * C + c] = a[n2];
+        buf[((2 * j + 1) * 8 + n2) * C + c] = b[n2];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) u[k1] = buf[(k1 * 8 + j) * C + c];
+    dft16<true>(u);  // u[n1] = y[j + 8 n1]
+    pdl_trigger();
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) t[fbase + (size_t)(8 * n1 + j) * Q + col] = u[n1];
+}
+
 // 64-point depth pass with the mask (volumes of depth 64): 32 columns per 256-thread CTA, 8
 // lanes per column; lane j loads x[8 n1 + j], and after the 8-point DFT, the twiddles w64^(j k1)
 // and one exchange it holds X[j + 8 k2]; it applies the mask and the 1/(PQR) scale, then runs the
@@ -595,6 +666,12 @@ int col_tile_for(const Dims& d, bool depth) {
     return wide_cols(depth ? d.R : d.P);
 }
 
+bool col_register(const Dims& d, bool depth) {
+    if (depth) return d.R == 64 && (d.P * d.Q) % 32 == 0;
+    if (d.R == 1 && d.P == 256) return true;
+    return d.P == 128 && d.Q % 16 == 0;
+}
+
 cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, float2* y, int inv,
                         cudaStream_t st) {
     const float sq = 1.0f / sqrtf((float)d.Q), sp = 1.0f / sqrtf((float)d.P);
@@ -700,8 +777,8 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
         const int pq = d.P * d.Q, slices = d.T * d.R;
         const float sc3 = 1.0f / ((float)d.P * (float)d.Q * (float)d.R);
         const int cP = col_tile_for(d, false), cR = col_tile_for(d, true);
-        const bool reg128 = d.P == 128 && d.Q % 16 == 0;  // register transforms where they exist
-        const bool reg64 = d.R == 64 && pq % 32 == 0;
+        const bool reg128 = col_register(d, false);  // register transforms where they exist
+        const bool reg64 = col_register(d, true);
         cudaError_t e =
             reg128 ? launch_pdl(col128_kernel<false>, dim3(d.Q / 16, slices), dim3(128), 0, st, t,
                                 d.Q, tw.twP)
@@ -721,6 +798,9 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
     if (d.P == 256)
         return launch_pdl(col_mask_256_kernel<false>, dim3(d.Q / kColTile, frames), dim3(128), 0,
                           st, t, mask, d.Q, d.T, sc, tw.twP, (double*)nullptr);
+    if (col_register(d, false))
+        return launch_pdl(col_mask_128_kernel, dim3(d.Q / 16, frames), dim3(128), 0, st, t, mask,
+                          d.Q, d.T, sc, tw.twP);
     return col_pass<COL_MASK_OP>(d.P, col_tile_for(d, false), d.Q, frames, d.T, t, t, mask, sc,
                                  tw.twP, st);
 }

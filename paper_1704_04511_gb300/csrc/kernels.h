@@ -80,6 +80,8 @@ int num_sms();
 bool fft_size_supported(int n);
 // Column tile the length-P (depth = false) or depth passes of `d` use (fft.cu).
 int col_tile_for(const Dims& d, bool depth);
+// True where the column stage of the CG operator runs register transforms without tiles.
+bool col_register(const Dims& d, bool depth);
 // Message returned by recon_last_error(NULL) (calls that have no context).
 void set_context_free_error(const std::string& msg);
 int w_max_M();

@@ -703,8 +703,8 @@ int autotune_tiles(recon_ctx* c, Dims* d, const Twiddles& tw, float2* t, const u
     cudaError_t err = cudaSuccess;
     const int cand[3] = {8, 16, 32};
     Dims dd = *d;
-    // the length-P passes (the 256-row image-series pass is a register kernel without tiles)
-    if (!(d->R == 1 && d->P == 256)) {
+    // the length-P passes (those in register transforms have no tiles to choose)
+    if (!recon::col_register(*d, false)) {
         float best = 1e30f;
         int bestC = recon::col_tile_for(*d, false);
         for (int C : cand) {
@@ -717,7 +717,7 @@ int autotune_tiles(recon_ctx* c, Dims* d, const Twiddles& tw, float2* t, const u
         }
         dd.colC = bestC;
     }
-    if (err == cudaSuccess && d->R > 1) {
+    if (err == cudaSuccess && d->R > 1 && !recon::col_register(*d, true)) {
         float best = 1e30f;
         int bestC = recon::col_tile_for(*d, true);
         for (int C : cand) {

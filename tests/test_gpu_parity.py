@@ -192,7 +192,9 @@ def _times(T):
 OP_CASES = [("tiny", "tiny_32x32x8", {}), ("perf", "perf_256x256x16", {}),
             ("perf-T5", "perf_256x256x16", {"T": 5, "times_ms": _times(5)}),
             ("rows256-cols64", "perf_256x256x16", {"P": 64, "T": 6, "times_ms": _times(6)}),
-            ("rows128-cols256", "perf_256x256x16", {"Q": 128, "T": 7, "times_ms": _times(7)})]
+            ("rows128-cols256", "perf_256x256x16", {"Q": 128, "T": 7, "times_ms": _times(7)}),
+            ("rows128-cols128", "perf_256x256x16", {"P": 128, "Q": 128, "T": 5, "times_ms": _times(5)}),
+            ("rows128-cols64", "perf_256x256x16", {"P": 128, "Q": 64, "T": 4, "times_ms": _times(4)})]
 
 
 @pytest.mark.parametrize("case", OP_CASES, ids=[c[0] for c in OP_CASES])
