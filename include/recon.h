@@ -21,7 +21,9 @@
  *    linear convolution over frames (the hybrid approximation of Sec. III-A), k = T - M + 1.
  *  - Every data pointer is a DEVICE pointer on the context's device unless stated otherwise,
  *    owned by the caller, and must stay valid until the call returns. Calls are synchronous:
- *    they return after the device work finished (results readable).
+ *    they return after the device work finished (results readable). Image, k-space, mask,
+ *    coil, S and G arrays start on a 16-byte boundary (every cudaMalloc / PyTorch allocation
+ *    does; a view starting at an odd complex64 element does not): RECON_EINVAL otherwise.
  *  - Supported sizes: P, Q in {16, 32, 64, 128, 192, 256, 512}; 1 <= M <= 6, M <= T;
  *    1 <= N1 <= P, 1 <= N2 <= Q; T * Q <= 8738 (fused row/W pass).
  *  - Return value: RECON_OK (0) or a negative RECON_E* code; recon_last_error() describes it.

@@ -35,6 +35,48 @@ RECON_DEV void load_S(const float2* __restrict__ S, size_t npix, size_t px, floa
         }
 }
 
+// Diagonal sums of the per-pixel block: c[M - 1 + d] = sum_{a - b = d} s[a][b], d = -(M-1) ..
+// M-1. A frame n whose M windows n - M + 1 + a all exist (every frame of the circular lifting)
+// has (W x)_n = sum_d c[M - 1 + d] x_{n+d}: 2M - 1 products instead of M^2. s is Hermitian, so
+// c[M - 1 - d] = conj(c[M - 1 + d]).
+template <int M>
+RECON_DEV void s_diagonals(const float2 (&s)[M][M], float2 (&c)[2 * M - 1]) {
+#pragma unroll
+    for (int d = 0; d < M; ++d) {
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = d; a < M; ++a) v = cadd(v, s[a][a - d]);
+        c[M - 1 + d] = v;
+        if (d > 0) c[M - 1 - d] = cconj(v);
+    }
+}
+
+// (W x)_n at one pixel, from the frame values xs[f * stride] (0 <= f < T), the block s and its
+// diagonal sums c: the diagonal form where all M windows of frame n exist (for 3 <= M <= 5,
+// where it saves products and the block and its sums fit the registers; the circular lifting
+// always), else the window sum.
+template <int M, bool CIRC>
+RECON_DEV float2 w_frame(const float2 (&s)[M][M], const float2 (&c)[2 * M - 1],
+                         const float2* xs, int stride, int n, int T, int k) {
+    float2 w = make_float2(0.f, 0.f);
+    if (CIRC || (M >= 3 && M <= 5 && n >= M - 1 && n < k)) {
+#pragma unroll
+        for (int d = 0; d < 2 * M - 1; ++d) {
+            const int f = n + d - (M - 1);
+            w = cfma(c[d], xs[(CIRC ? wrap_frame(f, T) : f) * stride], w);
+        }
+        return w;
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        const int j = n - M + 1 + a;
+        if (j < 0 || j >= k) continue;
+#pragma unroll
+        for (int b = 0; b < M; ++b) w = cfma(s[a][b], xs[(n + a - b) * stride], w);
+    }
+    return w;
+}
+
 // Pass C of a CG step. One CTA per image row r1 holds that row of every frame: it inverse-
 // transforms the k-space rows of t (giving A^H A p; the 1/(PQ) scale was applied with the mask),
 // adds lam W p from the p rows, writes q over t and emits the partial Re <p, q> of its row.
@@ -67,16 +109,10 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         float2 s[M][M];
         load_S<M>(S, npix, (size_t)r1 * N + c, s);
+        float2 cs[2 * M - 1];
+        s_diagonals<M>(s, cs);
         for (int n = 0; n < T; ++n) {
-            float2 w = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int aa = 0; aa < M; ++aa) {
-                const int j = n - M + 1 + aa;
-                if (!CIRC && (j < 0 || j >= k)) continue;  // CIRC: every window
-#pragma unroll
-                for (int bb = 0; bb < M; ++bb)
-                    w = cfma(s[aa][bb], pt[(CIRC ? wrap_frame(n + aa - bb, T) : n + aa - bb) * N + c], w);
-            }
+            const float2 w = w_frame<M, CIRC>(s, cs, pt + c, N, n, T, k);
             float2 q = res[n * N + c];
             q.x = fmaf(lam, w.x, q.x);
             q.y = fmaf(lam, w.y, q.y);
@@ -99,10 +135,13 @@ row_inv_w_kernel(float2* t, const float2* __restrict__ p, const float2* __restri
     if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
-// Pass C for 256-point rows: one CTA per image row r1 with 16 threads per frame (T * 16 threads);
-// the inverse row transforms run in registers (regfft.cuh), the rest as in row_inv_w_kernel.
-// Shared memory: p rows [T][256], then the exchange buffers [T'][16 x 17] (T' = T rounded up to
-// even: the block has whole warps) which afterwards hold the transformed rows [T][256].
+// Pass C for 256-point rows: one CTA per image row r1 with 16 threads per frame; the inverse row
+// transforms run in registers (regfft.cuh), the rest as in row_inv_w_kernel. The block is padded
+// to a multiple of 16 frames (256 threads), at least 32: warps without a frame skip the
+// transform, and the W phase gives each column blockDim / 256 threads, each with a contiguous
+// range of frames. Shared memory: p rows [T][256], then the exchange buffers [T'][16 x 17] (T' = T
+// rounded up to even, the frames of the warps that transform) which afterwards hold the
+// transformed rows [T][256].
 template <int M>
 __global__ void __launch_bounds__(1024)
 row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
@@ -117,7 +156,8 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
     fill_tw256(tw2, tw_g);
     pdl_wait();
     const int n = threadIdx.x / 16, j = threadIdx.x % 16;
-    const bool live = n < T;  // the block is padded to whole warps (an odd T leaves a half-warp)
+    const bool live = n < T;                            // the block is padded (see the launch)
+    const bool warp_live = (threadIdx.x / 32) * 2 < T;  // a warp holds frames 2w and 2w + 1
     const size_t npix = (size_t)P * N;
     const int k = T - M + 1;
     float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
@@ -134,26 +174,22 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
         }
     }
     __syncthreads();  // tw2
-    row_dft256<true>(u, res + n * (16 * 17), tw2, j);
+    if (warp_live) row_dft256<true>(u, res + n * (16 * 17), tw2, j);  // warp-uniform
     __syncthreads();  // every exchange buffer read
     if (live) {
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) res[n * N + j + 16 * k2] = u[k2];
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    {   // W phase: column c, frames [f0, f1) of this thread's group (blockDim.x = ng N)
+        const int c = threadIdx.x % N, ng = blockDim.x / N, g = threadIdx.x / N;
+        const int f0 = g * T / ng, f1 = (g + 1) * T / ng;
         float2 s[M][M];
         load_S<M>(S, npix, (size_t)r1 * N + c, s);
-        for (int nn = 0; nn < T; ++nn) {
-            float2 w = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int aa = 0; aa < M; ++aa) {
-                const int jw = nn - M + 1 + aa;
-                if (jw < 0 || jw >= k) continue;
-#pragma unroll
-                for (int bb = 0; bb < M; ++bb)
-                    w = cfma(s[aa][bb], pt[(nn + aa - bb) * N + c], w);
-            }
+        float2 cs[2 * M - 1];
+        s_diagonals<M>(s, cs);
+        for (int nn = f0; nn < f1; ++nn) {
+            const float2 w = w_frame<M, false>(s, cs, pt + c, N, nn, T, k);
             float2 q = res[nn * N + c];
             q.x = fmaf(lam, w.x, q.x);
             q.y = fmaf(lam, w.y, q.y);
@@ -252,15 +288,10 @@ row_fwd_w_256_kernel(const float2* __restrict__ r, float2* __restrict__ p, float
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         float2 s[M][M];
         load_S<M>(S, npix, (size_t)r1 * N + c, s);
+        float2 cs[2 * M - 1];
+        s_diagonals<M>(s, cs);
         for (int nn = 0; nn < T; ++nn) {
-            float2 w = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int aa = 0; aa < M; ++aa) {
-                const int jw = nn - M + 1 + aa;
-                if (jw < 0 || jw >= k) continue;
-#pragma unroll
-                for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(nn + aa - bb) * N + c], w);
-            }
+            const float2 w = w_frame<M, false>(s, cs, pt + c, N, nn, T, k);
             const float2 pv = pt[nn * N + c];
             const float term = fmaf(pv.x, w.x, pv.y * w.y) - comp;
             const float sum = acc + term;
@@ -336,15 +367,10 @@ row_inv_w_upd_256_kernel(const float2* __restrict__ t, const float2* __restrict_
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         float2 s[M][M];
         load_S<M>(S, npix, (size_t)r1 * N + c, s);
+        float2 cs[2 * M - 1];
+        s_diagonals<M>(s, cs);
         for (int nn = 0; nn < T; ++nn) {
-            float2 w = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int aa = 0; aa < M; ++aa) {
-                const int jw = nn - M + 1 + aa;
-                if (jw < 0 || jw >= k) continue;
-#pragma unroll
-                for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(nn + aa - bb) * N + c], w);
-            }
+            const float2 w = w_frame<M, false>(s, cs, pt + c, N, nn, T, k);
             float2 q = res[nn * N + c];
             q.x = fmaf(lam, w.x, q.x);
             q.y = fmaf(lam, w.y, q.y);
@@ -370,43 +396,68 @@ row_inv_w_upd_256_kernel(const float2* __restrict__ t, const float2* __restrict_
 }
 
 // Pass C for 128-point rows: as row_inv_w_256_kernel with 8 threads per frame (row_dft128), the
-// block padded to a multiple of four frames (whole warps) and to at least 16 frames (128 threads,
-// one column each in the W phase). Shared memory: p rows [T][128], then the exchange buffers
-// [T'][kX128] which afterwards hold the transformed rows [T][128].
+// block padded to a multiple of 16 frames (128 threads), at most 64; warps
+// without a frame skip the transform, and the W phase gives each column blockDim / 128 threads,
+// each with a contiguous range of frames. A CTA usually owns several rows (volumes have
+// R P rows), so the inputs of its next row are staged into shared memory by asynchronous copies
+// while the current one is processed: the p rows (double-buffered) as the row starts, the t rows
+// once the current ones are in registers, the S row once the current one has been used. Shared
+// memory: p rows [2][T][128], t rows [T][128], S row [npair][128], then the exchange buffers
+// [T4][kX128] (T4 = T rounded up to whole warps) which afterwards hold the transformed rows.
 template <int M>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(512)
 row_inv_w_128_kernel(float2* t, const float2* __restrict__ p, const float2* __restrict__ S,
                      float lam, int T, int P, double* __restrict__ pq_parts,
                      const float2* __restrict__ tw_g) {
     constexpr int N = 128;
-    extern __shared__ float2 sm[];
+    constexpr int NP = M * (M + 1) / 2;
+    extern __shared__ __align__(16) float2 sm[];
     __shared__ float2 tw8[128];
     __shared__ double red[32];
-    float2* pt = sm;
-    float2* res = sm + (size_t)T * N;
+    const int TN = T * N;
+    float2* pst = sm;             // [2][T][N]
+    float2* tst = sm + 2 * TN;    // [T][N]
+    float2* sst = tst + TN;       // [NP][N]
+    float2* res = sst + NP * N;   // [T4][kX128]
     fill_tw128(tw8, tw_g);
     pdl_wait();
     const int n = threadIdx.x / 8, j = threadIdx.x % 8;
     const bool live = n < T;
+    const bool warp_live = (threadIdx.x / 32) * 4 < T;  // a warp holds frames 4w .. 4w + 3
     const size_t npix = (size_t)P * N;
     const int k = T - M + 1;
-    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
-    for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
-    __syncthreads();  // the previous row's results are stored
-    const size_t g0 = (size_t)n * npix + (size_t)r1 * N + j;
-    float2 u[16];
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) {
-        u[n1] = make_float2(0.f, 0.f);
-        if (live) {
-            u[n1] = t[g0 + 8 * n1];
-            pt[n * N + 8 * n1 + j] = p[g0 + 8 * n1];
+    // 16-byte copies of `rows` rows of N values, row f from src + f * stride, to dst + f * N
+    auto stage = [&](float2* dst, const float2* src, size_t stride, int rows) {
+        for (int e = threadIdx.x; e < rows * (N / 2); e += blockDim.x) {
+            const int f = e / (N / 2), c2 = 2 * (e % (N / 2));
+            cp_async16(dst + f * N + c2, src + f * stride + c2);
         }
+        cp_async_commit();
+    };
+    float acc = 0.f, comp = 0.f;  // Kahan-compensated per-thread partial of Re <p, q>
+    int buf = 0;
+    if ((int)blockIdx.x < P) {
+        const size_t r0 = (size_t)blockIdx.x * N;
+        stage(pst, p + r0, npix, T);
+        stage(tst, t + r0, npix, T);
+        stage(sst, S + r0, npix, NP);
     }
-    __syncthreads();  // tw8
+    for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x, buf ^= 1) {
+    const int nxt = r1 + gridDim.x;
+    const size_t rn = (size_t)nxt * N;
+    cp_async_wait<0>();
+    __syncthreads();  // this row's copies landed (every thread's); tw8; the previous row stored
+    // the other p buffer was last read before the previous row's final barrier
+    if (nxt < P) stage(pst + (buf ^ 1) * TN, p + rn, npix, T);
     float2 a[8], b[8];
-    row_dft128<true>(u, a, b, res + n * kX128, tw8, j);
-    __syncthreads();  // every exchange buffer read
+    if (warp_live) {  // warp-uniform
+        float2 u[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) u[n1] = live ? tst[n * N + 8 * n1 + j] : make_float2(0.f, 0.f);
+        row_dft128<true>(u, a, b, res + n * kX128, tw8, j);
+    }
+    __syncthreads();  // every exchange buffer read; every t row in registers
+    if (nxt < P) stage(tst, t + rn, npix, T);
     if (live) {
 #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) {
@@ -415,18 +466,23 @@ row_inv_w_128_kernel(float2* t, const float2* __restrict__ p, const float2* __re
         }
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < N; c += blockDim.x) {
-        float2 s[M][M];
-        load_S<M>(S, npix, (size_t)r1 * N + c, s);
-        for (int nn = 0; nn < T; ++nn) {
-            float2 w = make_float2(0.f, 0.f);
+    const float2* pt = pst + buf * TN;
+    {   // W phase: column c, frames [f0, f1) of this thread's group (blockDim.x = ng N)
+        const int c = threadIdx.x % N, ng = blockDim.x / N, g = threadIdx.x / N;
+        const int f0 = g * T / ng, f1 = (g + 1) * T / ng;
+        float2 s[M][M];  // S(r) from the staged row, pair (a <= b) at a(2M-a+1)/2 + (b-a)
 #pragma unroll
-            for (int aa = 0; aa < M; ++aa) {
-                const int jw = nn - M + 1 + aa;
-                if (jw < 0 || jw >= k) continue;
+        for (int aa = 0; aa < M; ++aa)
 #pragma unroll
-                for (int bb = 0; bb < M; ++bb) w = cfma(s[aa][bb], pt[(nn + aa - bb) * N + c], w);
+            for (int bb = aa; bb < M; ++bb) {
+                const float2 v = sst[(aa * (2 * M - aa + 1) / 2 + (bb - aa)) * N + c];
+                s[aa][bb] = v;
+                s[bb][aa] = cconj(v);
             }
+        float2 cs[2 * M - 1];
+        s_diagonals<M>(s, cs);
+        for (int nn = f0; nn < f1; ++nn) {
+            const float2 w = w_frame<M, false>(s, cs, pt + c, N, nn, T, k);
             float2 q = res[nn * N + c];
             q.x = fmaf(lam, w.x, q.x);
             q.y = fmaf(lam, w.y, q.y);
@@ -438,11 +494,13 @@ row_inv_w_128_kernel(float2* t, const float2* __restrict__ p, const float2* __re
             acc = sum;
         }
     }
-    __syncthreads();  // every column of q written
-    if (r1 + (int)gridDim.x >= P) pdl_trigger();
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+    __syncthreads();  // every column of q written; the S row used
+    if (nxt < P) stage(sst, S + rn, npix, NP);
+    else pdl_trigger();
+    float2* trow = t + (size_t)r1 * N;
+    for (int e = threadIdx.x; e < TN; e += blockDim.x) {
         const int nn = e / N, c = e % N;
-        t[(size_t)nn * npix + (size_t)r1 * N + c] = res[e];
+        trow[nn * npix + c] = res[e];
     }
     }
     const double tot = block_sum_f_t0(acc, red);
@@ -715,9 +773,13 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
     int grid = 0;
     if (N == 128 && !d.circ) {  // register transforms for the valid (non-circular) lifting
         // whole warps, and at least 128 threads so that the W phase has one column per thread
-        const int tpad = d.T <= 16 ? 16 : (d.T + 3) / 4 * 4;
-        const size_t smem128 = ((size_t)d.T * N + (size_t)tpad * kX128) * sizeof(float2);
-        if (tpad * 8 <= 1024 && smem128 <= 200 * 1024) {
+        // 8 threads per frame, whole multiples of 128 threads (the W phase splits the frames of
+        // a column over blockDim / 128 threads); 128 threads measure faster than 256 for T <= 16
+        const int tpad = (d.T + 15) / 16 * 16;
+        const int t4 = (d.T + 3) / 4 * 4;  // frames of the warps that transform
+        const size_t smem128 =
+            ((size_t)3 * d.T * N + (size_t)d.M * (d.M + 1) / 2 * N + (size_t)t4 * kX128) * sizeof(float2);
+        if (tpad * 8 <= 512 && smem128 <= 200 * 1024) {
             auto k = row_inv_w_128_kernel<M>;
             if (smem128 > 48 * 1024) {
                 cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -732,8 +794,9 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
         }
     }
     if (N == 256 && !d.circ) {  // the register kernel serves the valid (non-circular) lifting
-        const int tpad = (d.T + 1) / 2 * 2;
-        const size_t smem256 = ((size_t)d.T * N + (size_t)tpad * 16 * 17) * sizeof(float2);
+        const int t2 = (d.T + 1) / 2 * 2;                          // frames that transform
+        const int tpad = d.T <= 32 ? 32 : (d.T + 15) / 16 * 16;   // frames of the block
+        const size_t smem256 = ((size_t)d.T * N + (size_t)t2 * 16 * 17) * sizeof(float2);
         if (tpad * 16 <= 1024 && smem256 <= 200 * 1024) {
             auto k = row_inv_w_256_kernel<M>;
             if (smem256 > 48 * 1024) {

@@ -15,6 +15,20 @@
 RECON_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 RECON_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, cached in L2 only). Both addresses must
+// be 16-byte aligned. A thread's copies are grouped by commit; wait<N> returns once at most the N
+// most recent groups of this thread are still in flight (the copies always complete), after which
+// a barrier makes the landed data visible to the other threads of the CTA.
+RECON_DEV void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned int d = static_cast<unsigned int>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+RECON_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+RECON_DEV void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Frame index of the banded W / the pair products, wrapped into [0, T) for the fully circulant
 // (time-circular) lifting; for the valid lifting every index already lies in [0, T).
 RECON_DEV int wrap_frame(int f, int T) {

@@ -19,7 +19,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <fstream>
+#include <initializer_list>
 #include <map>
 #include <sstream>
 #include <tuple>
@@ -127,6 +129,15 @@ namespace {
 int fail(recon_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg;
     return code;
+}
+
+// Device arrays handed to the library start on a 16-byte boundary: the vector passes move two
+// complex64 values per access and the row passes stage rows with 16-byte asynchronous copies.
+constexpr const char* kAlignMsg = "device arrays must be 16-byte aligned";
+bool misaligned(std::initializer_list<const void*> ptrs) {
+    for (const void* p : ptrs)
+        if (reinterpret_cast<uintptr_t>(p) & 15u) return true;
+    return false;
 }
 
 int cuda_fail(recon_ctx* c, cudaError_t e, const char* where) {
@@ -1204,6 +1215,7 @@ int weight_impl(recon_ctx* c, const Dims& d, const void* G_in, double eps_in, do
 int weight_args(recon_ctx* c, const void* G_in, double eps_in, double p, int method,
                 const void* S_out, const void* evals_out) {
     if (!G_in || !S_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({G_in, S_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (method != RECON_WEIGHT_AUTO && method != RECON_WEIGHT_EIG)
         return fail(c, RECON_EINVAL, "unknown weight method");
     if (evals_out && !wants_eig(p, method))
@@ -1350,6 +1362,7 @@ int recon_solve(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* 
                 recon_filter f, const recon_params* prm, void* image_out) {
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({kspace, masks, image_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_params(c, dd, f, prm, &d);
     if (rc) return rc;
@@ -1360,6 +1373,7 @@ int recon_solve3(recon_ctx* c, recon_dims3 dd, const void* kspace, const uint8_t
                  recon_filter3 f, const recon_params* prm, void* image_out) {
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({kspace, masks, image_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_dims3(c, dd, &f, &d);
     if (!rc) rc = check_prm(c, prm);
@@ -1372,6 +1386,7 @@ int recon_solve_coils(recon_ctx* c, recon_dims dd, const void* kspace, const uin
                       void* image_out) {
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !coils || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({kspace, masks, coils, image_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (n_coils < 1 || n_coils > RECON_MAX_COILS)
         return fail(c, RECON_EINVAL, "need 1 <= n_coils <= RECON_MAX_COILS");
     if (prm->kspace_bf16) return fail(c, RECON_EINVAL, "multi-coil k-space must be complex64");
@@ -1409,6 +1424,7 @@ int recon_adjoint_coils(recon_ctx* c, recon_dims dd, const void* kspace, const u
                         const void* coils, int n_coils, void* x_out) {
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !coils || !x_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({kspace, masks, coils, x_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (n_coils < 1 || n_coils > RECON_MAX_COILS)
         return fail(c, RECON_EINVAL, "need 1 <= n_coils <= RECON_MAX_COILS");
     Dims d;
@@ -1435,6 +1451,7 @@ int recon_apply_normal_coils(recon_ctx* c, recon_dims dd, recon_filter f, const 
                              const void* x, void* y) {
     if (!c) return RECON_EINVAL;
     if (!masks || !coils || !S || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({masks, coils, S, x, y})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
     if (n_coils < 1 || n_coils > RECON_MAX_COILS)
         return fail(c, RECON_EINVAL, "need 1 <= n_coils <= RECON_MAX_COILS");
@@ -1473,8 +1490,10 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
     if (!c) return RECON_EINVAL;
     if (n < 1 || n > RECON_MAX_BATCH) return fail(c, RECON_EINVAL, "need 1 <= n <= RECON_MAX_BATCH");
     if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
         if (!kspace[i] || !masks[i] || !image_out[i]) return fail(c, RECON_EINVAL, "null pointer");
+        if (misaligned({kspace[i], masks[i], image_out[i]})) return fail(c, RECON_EINVAL, kAlignMsg);
+    }
     Dims d;
     int rc = check_params(c, dd, f, prm, &d);
     if (rc) return rc;
@@ -1533,6 +1552,7 @@ int recon_submit(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t*
                  recon_filter f, const recon_params* prm, void* image_out, int* ticket) {
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !prm || !image_out || !ticket) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({kspace, masks, image_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_params(c, dd, f, prm, &d);
     if (rc) return rc;
@@ -1619,6 +1639,7 @@ int recon_adjoint(recon_ctx* c, recon_dims dd, const void* kspace, int kspace_bf
                   const uint8_t* masks, void* x_out) {
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !x_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({kspace, masks, x_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_dims(c, dd, nullptr, &d);
     return rc ? rc : adjoint_impl(c, d, kspace, kspace_bf16, masks, x_out);
@@ -1628,6 +1649,7 @@ int recon_adjoint3(recon_ctx* c, recon_dims3 dd, const void* kspace, int kspace_
                    const uint8_t* masks, void* x_out) {
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !x_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({kspace, masks, x_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_dims3(c, dd, nullptr, &d);
     return rc ? rc : adjoint_impl(c, d, kspace, kspace_bf16, masks, x_out);
@@ -1636,6 +1658,7 @@ int recon_adjoint3(recon_ctx* c, recon_dims3 dd, const void* kspace, int kspace_
 int recon_fft2(recon_ctx* c, recon_dims dd, const void* x, void* y, int inverse) {
     if (!c) return RECON_EINVAL;
     if (!x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({x, y})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_dims(c, dd, nullptr, &d);
     return rc ? rc : fft_impl(c, d, x, y, inverse);
@@ -1644,6 +1667,7 @@ int recon_fft2(recon_ctx* c, recon_dims dd, const void* x, void* y, int inverse)
 int recon_fft3(recon_ctx* c, recon_dims3 dd, const void* x, void* y, int inverse) {
     if (!c) return RECON_EINVAL;
     if (!x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({x, y})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_dims3(c, dd, nullptr, &d);
     return rc ? rc : fft_impl(c, d, x, y, inverse);
@@ -1653,6 +1677,7 @@ int recon_gram(recon_ctx* c, recon_dims dd, recon_filter f, const void* x, void*
                void* lags_out) {
     if (!c) return RECON_EINVAL;
     if (!x || !G_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({x, G_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
     return rc ? rc : gram_impl(c, d, x, G_out, lags_out);
@@ -1662,6 +1687,7 @@ int recon_gram3(recon_ctx* c, recon_dims3 dd, recon_filter3 f, const void* x, vo
                 void* lags_out) {
     if (!c) return RECON_EINVAL;
     if (!x || !G_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({x, G_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_dims3(c, dd, &f, &d);
     return rc ? rc : gram_impl(c, d, x, G_out, lags_out);
@@ -1693,6 +1719,7 @@ int recon_apply_normal(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_
                        const void* S, double lambda, const void* x, void* y) {
     if (!c) return RECON_EINVAL;
     if (!masks || !S || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({masks, S, x, y})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
@@ -1703,6 +1730,7 @@ int recon_apply_normal3(recon_ctx* c, recon_dims3 dd, recon_filter3 f, const uin
                         const void* S, double lambda, const void* x, void* y) {
     if (!c) return RECON_EINVAL;
     if (!masks || !S || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({masks, S, x, y})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
     Dims d;
     int rc = check_dims3(c, dd, &f, &d);
@@ -1715,6 +1743,7 @@ int recon_solve_variant(recon_ctx* c, recon_dims dd, const void* kspace, const u
                         recon_filter f, const recon_params* prm, int variant, void* image_out) {
     if (!c) return RECON_EINVAL;
     if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({kspace, masks, image_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_params(c, dd, f, prm, &d);
     if (!rc) rc = check_variant(c, variant, f);
@@ -1728,6 +1757,7 @@ int recon_gram_variant(recon_ctx* c, recon_dims dd, recon_filter f, int variant,
                        void* G_out) {
     if (!c) return RECON_EINVAL;
     if (!x || !G_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({x, G_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
     if (!rc) rc = check_variant(c, variant, f);
@@ -1763,6 +1793,7 @@ int recon_voxel_weight(recon_ctx* c, recon_dims dd, int M, const void* x, const 
                        double p, void* S_out, double* lmax_out) {
     if (!c) return RECON_EINVAL;
     if (!x || !eps || !S_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({x, S_out})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (!(p >= 0.0 && p <= 1.0)) return fail(c, RECON_EINVAL, "need 0 <= p <= 1");
     Dims d;
     const recon_filter f{1, 1, M};
@@ -1814,6 +1845,7 @@ int recon_apply_normal_variant(recon_ctx* c, recon_dims dd, recon_filter f, int 
                                void* y) {
     if (!c) return RECON_EINVAL;
     if (!masks || !W || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({masks, W, x, y})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
@@ -1840,6 +1872,7 @@ int recon_apply_w(recon_ctx* c, recon_dims dd, recon_filter f, const void* S, co
                   void* y) {
     if (!c) return RECON_EINVAL;
     if (!S || !x || !y) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({S, x, y})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (x == y) return fail(c, RECON_EINVAL, "y must not alias x");
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
@@ -1855,6 +1888,7 @@ int recon_cg(recon_ctx* c, recon_dims dd, recon_filter f, const uint8_t* masks, 
              const void* S_new, double lambda, void* x, void* r, int n_cg, double* rr_hist) {
     if (!c) return RECON_EINVAL;
     if (!masks || !S_new || !x || !r) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({masks, S_new, x, r})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (n_cg < 0) return fail(c, RECON_EINVAL, "n_cg must be >= 0");
     Dims d;
     int rc = check_dims(c, dd, &f, &d);
@@ -1886,6 +1920,7 @@ int recon_t2fit(recon_ctx* c, recon_dims dd, const void* x, const double* times_
                 int n_gn, float* t2_out, float* amp_out) {
     if (!c) return RECON_EINVAL;
     if (!x || !times_ms || !t2_out) return fail(c, RECON_EINVAL, "null pointer");
+    if (misaligned({x})) return fail(c, RECON_EINVAL, kAlignMsg);
     if (dd.P <= 0 || dd.Q <= 0 || dd.T < 2 || dd.T > recon::kT2MaxT)
         return fail(c, RECON_EINVAL, "need P, Q > 0 and 2 <= T <= 64");
     if (!(fg_frac >= 0.0 && fg_frac < 1.0)) return fail(c, RECON_EINVAL, "need 0 <= fg_frac < 1");

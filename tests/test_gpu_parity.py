@@ -194,7 +194,14 @@ OP_CASES = [("tiny", "tiny_32x32x8", {}), ("perf", "perf_256x256x16", {}),
             ("rows256-cols64", "perf_256x256x16", {"P": 64, "T": 6, "times_ms": _times(6)}),
             ("rows128-cols256", "perf_256x256x16", {"Q": 128, "T": 7, "times_ms": _times(7)}),
             ("rows128-cols128", "perf_256x256x16", {"P": 128, "Q": 128, "T": 5, "times_ms": _times(5)}),
-            ("rows128-cols64", "perf_256x256x16", {"P": 128, "Q": 64, "T": 4, "times_ms": _times(4)})]
+            ("rows128-cols64", "perf_256x256x16", {"P": 128, "Q": 64, "T": 4, "times_ms": _times(4)}),
+            # frame taps M = 4 and 5: W by the diagonal sums of S(r) in the interior frames
+            ("rows256-M5", "perf_256x256x16", {"P": 32, "T": 12, "M": 5, "N1": 5, "N2": 5,
+                                               "times_ms": _times(12)}),
+            ("rows128-M4", "perf_256x256x16", {"P": 32, "Q": 128, "T": 8, "M": 4, "N1": 5,
+                                               "N2": 5, "times_ms": _times(8)}),
+            ("rows64-M4", "perf_256x256x16", {"P": 16, "Q": 64, "T": 7, "M": 4, "N1": 3,
+                                              "N2": 5, "times_ms": _times(7)})]
 
 
 @pytest.mark.parametrize("case", OP_CASES, ids=[c[0] for c in OP_CASES])
@@ -384,6 +391,16 @@ def test_errors(R):
     m = torch.ones((2, 16, 16), dtype=torch.uint8, device="cuda")
     with pytest.raises(recon.ReconError):
         recon.recon_solve(ctx.h, x, m, (2, 2, 1), -1.0, 0.0, 1, 1, x.clone())   # lambda <= 0
+    # device arrays must start on a 16-byte boundary: a view from an odd complex64 element
+    flat = torch.zeros(2 * 16 * 16 + 1, dtype=torch.complex64, device="cuda")
+    odd = flat[1:].view(2, 16, 16)
+    assert odd.data_ptr() % 16 == 8
+    with pytest.raises(recon.ReconError) as e:
+        recon.recon_solve(ctx.h, x, m, (2, 2, 1), 1e-3, 0.0, 1, 1, odd)
+    assert e.value.code == recon.RECON_EINVAL
+    with pytest.raises(recon.ReconError) as e:
+        recon.recon_fft2(ctx.h, odd, x.clone())
+    assert e.value.code == recon.RECON_EINVAL
     small = recon.Context(0, mem_budget_bytes=1024)
     try:
         with pytest.raises(recon.ReconError) as e:
