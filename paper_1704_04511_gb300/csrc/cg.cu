@@ -396,9 +396,8 @@ row_inv_w_upd_256_kernel(const float2* __restrict__ t, const float2* __restrict_
 }
 
 // Pass C for 128-point rows: as row_inv_w_256_kernel with 8 threads per frame (row_dft128), the
-// block padded to a multiple of 16 frames (128 threads), at most 64; warps
-// without a frame skip the transform, and the W phase gives each column blockDim / 128 threads,
-// each with a contiguous range of frames. A CTA usually owns several rows (volumes have
+// block padded to at least 16 frames (128 threads, one column each in the W phase) and at most
+// 64; warps without a frame skip the transform. A CTA usually owns several rows (volumes have
 // R P rows), so the inputs of its next row are staged into shared memory by asynchronous copies
 // while the current one is processed: the p rows (double-buffered) as the row starts, the t rows
 // once the current ones are in registers, the S row once the current one has been used. Shared
@@ -467,9 +466,7 @@ row_inv_w_128_kernel(float2* t, const float2* __restrict__ p, const float2* __re
     }
     __syncthreads();
     const float2* pt = pst + buf * TN;
-    {   // W phase: column c, frames [f0, f1) of this thread's group (blockDim.x = ng N)
-        const int c = threadIdx.x % N, ng = blockDim.x / N, g = threadIdx.x / N;
-        const int f0 = g * T / ng, f1 = (g + 1) * T / ng;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
         float2 s[M][M];  // S(r) from the staged row, pair (a <= b) at a(2M-a+1)/2 + (b-a)
 #pragma unroll
         for (int aa = 0; aa < M; ++aa)
@@ -481,7 +478,7 @@ row_inv_w_128_kernel(float2* t, const float2* __restrict__ p, const float2* __re
             }
         float2 cs[2 * M - 1];
         s_diagonals<M>(s, cs);
-        for (int nn = f0; nn < f1; ++nn) {
+        for (int nn = 0; nn < T; ++nn) {
             const float2 w = w_frame<M, false>(s, cs, pt + c, N, nn, T, k);
             float2 q = res[nn * N + c];
             q.x = fmaf(lam, w.x, q.x);
@@ -773,9 +770,7 @@ cudaError_t launch_row_inv_w_NM(const Dims& d, const Twiddles& tw, float2* t, co
     int grid = 0;
     if (N == 128 && !d.circ) {  // register transforms for the valid (non-circular) lifting
         // whole warps, and at least 128 threads so that the W phase has one column per thread
-        // 8 threads per frame, whole multiples of 128 threads (the W phase splits the frames of
-        // a column over blockDim / 128 threads); 128 threads measure faster than 256 for T <= 16
-        const int tpad = (d.T + 15) / 16 * 16;
+        const int tpad = d.T <= 16 ? 16 : (d.T + 3) / 4 * 4;
         const int t4 = (d.T + 3) / 4 * 4;  // frames of the warps that transform
         const size_t smem128 =
             ((size_t)3 * d.T * N + (size_t)d.M * (d.M + 1) / 2 * N + (size_t)t4 * kX128) * sizeof(float2);
