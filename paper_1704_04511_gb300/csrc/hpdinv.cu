@@ -19,6 +19,8 @@
 // and one warp at most one per ~64 cycles, so the products use full warps spread over every SM
 // and the pivot chain keeps its SM to itself. Grid barriers are bounded spin-waits: on timeout
 // the kernel records an error flag and returns.
+#include <cstddef>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -43,6 +45,7 @@ struct GridBar {
     int err;
     unsigned int pad[2];
 };
+static_assert(sizeof(GridBar) <= kCoopBarrierBytes, "grid barrier exceeds its scratch header");
 
 RECON_DEV unsigned int ld_acquire(const unsigned int* p) {
     unsigned int v;
@@ -62,7 +65,10 @@ RECON_DEV unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
 
 // Barrier over gridDim.x co-resident CTAs (cooperative launch) with one atomic per CTA: CTA 0 adds
 // 2^31 - (gridDim.x - 1) and every other CTA adds 1, so bit 31 of the word flips exactly when the
-// last CTA arrives and the low bits return to zero. Thread 0 of each CTA then polls the word with
+// last CTA arrives and the low bits return to zero. The barrier only looks at the flip, so a
+// launch that completed every barrier leaves a valid starting state for the next one: the word
+// is zeroed once when its scratch is allocated and again by the host after a reported failure,
+// not before every launch. Thread 0 of each CTA then polls the word with
 // acquire loads. Returns false (and sets gb->err) if the wait exceeded kSpinLimit polls; after a
 // failure every later call returns false at once so the kernel can unwind.
 RECON_DEV bool grid_barrier(GridBar* gb) {
@@ -94,6 +100,12 @@ RECON_DEV bool grid_barrier(GridBar* gb) {
     }
     __syncthreads();
     return ok_s != 0;
+}
+
+// Status of a cooperative launch for the host: thread 0 of CTA 0 writes 0 when the kernel
+// completed, 1 when a barrier gave up (every CTA then fails its next barrier and returns).
+RECON_DEV void report(int* err_out, int v) {
+    if (err_out && blockIdx.x == 0 && threadIdx.x == 0) *err_out = v;
 }
 
 // Synchronise the 64 threads of tile group g (named barrier g + 1; 0 is __syncthreads).
@@ -302,7 +314,7 @@ RECON_DEV void sweep_pivot(SweepSmem& sm, int K, const double2* Ain, const doubl
 __global__ void __launch_bounds__(kThreads, 2)
 hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
                  double2* __restrict__ A0, double2* __restrict__ A1, double2* __restrict__ Dbuf,
-                 GridBar* gb) {
+                 GridBar* gb, int* err_out) {
     __shared__ SweepSmem sm;
     const int tid = threadIdx.x;
     const int g = tid / kTileT, e = tid % kTileT;
@@ -327,13 +339,13 @@ hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
         }
         A0[tile_off(I, J) + e] = v;
     }
-    if (!grid_barrier(gb)) return;
+    if (!grid_barrier(gb)) return report(err_out, 1);
     if (blockIdx.x == 0 && g == 0) {  // D_0
         sm.X[e] = A0[e];
         group_sync(0);
         tile_inverse(sm.X, sm.T1, Dbuf);
     }
-    if (!grid_barrier(gb)) return;
+    if (!grid_barrier(gb)) return report(err_out, 1);
 
     for (int K = 0; K < nt; ++K) {
         const double2* Ain = (K & 1) ? A1 : A0;
@@ -345,7 +357,7 @@ hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
         } else {
             for (int it = 0; it < sm.nitem; ++it) sweep_item(sm, sm.item[it], K, nt, Ain, Aout, DK);
         }
-        if (!grid_barrier(gb)) return;
+        if (!grid_barrier(gb)) return report(err_out, 1);
     }
     // H = -A (s x s, full, column-major) written over G
     const double2* Af = (nt & 1) ? A1 : A0;
@@ -358,6 +370,7 @@ hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
                                    : zconj(Af[tile_off(J, I) + c % kB + kB * (r % kB)]);
         G[idx] = make_double2(-v.x, -v.y);
     }
+    report(err_out, 0);
 }
 
 // d_ab[delta] = sum_{l - l' = delta} H[(l', b), (l, a)] from H (s x s column-major); taps
@@ -396,7 +409,7 @@ __global__ void hdiag_kernel(const double2* __restrict__ H, int N1, int N2, int 
 __global__ void __launch_bounds__(kThreads)
 lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict__ u,
                double2* __restrict__ vprev, double* __restrict__ part, double* __restrict__ ab,
-               double* __restrict__ lmax_out, GridBar* gb) {
+               double* __restrict__ lmax_out, GridBar* gb, int* err_out) {
     __shared__ double red[kThreads / 32];
     __shared__ double s_beta, s_ib, s_alpha;
     __shared__ double sh_lo, sh_hi;
@@ -409,7 +422,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
         u[i] = make_double2(1.0 + 0.5 * sin((double)i), 0.25 * cos(3.0 * i) * i / s);
         vprev[i] = make_double2(0.0, 0.0);
     }
-    if (!grid_barrier(gb)) return;
+    if (!grid_barrier(gb)) return report(err_out, 1);
     if (warp == 0) {
         double acc = 0.0;
         for (int i = lane; i < s; i += 32) acc += u[i].x * u[i].x + u[i].y * u[i].y;
@@ -454,7 +467,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
             for (int w = 0; w < kThreads / 32; ++w) t += red[w];
             pa[blockIdx.x] = t;
         }
-        if (!grid_barrier(gb)) return;
+        if (!grid_barrier(gb)) return report(err_out, 1);
         if (warp == 0) {
             const double al = warp0_sum_array(pa, gridDim.x);
             if (lane == 0) s_alpha = al;
@@ -481,7 +494,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
             for (int w = 0; w < kThreads / 32; ++w) t += red[w];
             pb[blockIdx.x] = t;
         }
-        if (!grid_barrier(gb)) return;
+        if (!grid_barrier(gb)) return report(err_out, 1);
         if (warp == 0) {
             const double b2 = warp0_sum_array(pb, gridDim.x);
             if (lane == 0) {
@@ -582,6 +595,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
         if (sh_hi - sh_lo <= 2e-16 * fabs(sh_hi)) break;
     }
     if (threadIdx.x == 0) lmax_out[0] = 0.5 * (sh_lo + sh_hi);
+    report(err_out, 0);
 }
 
 int coop_grid(const void* kern, int* grid) {
@@ -614,14 +628,19 @@ cudaError_t launch_coop(void (*kern)(KArgs...), int grid, cudaStream_t st, Args.
 
 }  // namespace
 
+cudaError_t set_barrier_error(void* scratch, cudaStream_t st) {
+    return cudaMemsetAsync(reinterpret_cast<unsigned char*>(scratch) + offsetof(GridBar, err), 1,
+                           sizeof(int), st);
+}
+
 size_t hpd_scratch_bytes(const Dims& d) {
     const size_t nt = (size_t)tiles_per_side(d.s());
     const size_t nlt = nt * (nt + 1) / 2;
-    return 256 + 2 * nlt * kTileT * sizeof(double2) + 2 * kTileT * sizeof(double2) + 1024;
+    return kCoopBarrierBytes + 2 * nlt * kTileT * sizeof(double2) + 2 * kTileT * sizeof(double2) + 1024;
 }
 
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {
-    return 256 + 2 * (size_t)d.s() * sizeof(double2) + 4 * (size_t)grid_max * sizeof(double) +
+    return kCoopBarrierBytes + 2 * (size_t)d.s() * sizeof(double2) + 4 * (size_t)grid_max * sizeof(double) +
            2 * kLanczosMax * sizeof(double) + 1024;
 }
 
@@ -635,21 +654,13 @@ cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, voi
     if (sweep_items(nt, grid - 1, -1, nullptr, 0) > kMaxItems) return cudaErrorInvalidValue;
     unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
     GridBar* gb = reinterpret_cast<GridBar*>(p);
-    p += 256;
+    p += kCoopBarrierBytes;
     double2* A0 = reinterpret_cast<double2*>(p);
     p += nlt * kTileT * sizeof(double2);
     double2* A1 = reinterpret_cast<double2*>(p);
     p += nlt * kTileT * sizeof(double2);
     double2* Dbuf = reinterpret_cast<double2*>(p);
-    cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
-    if (e != cudaSuccess) return e;
-    e = launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, nt, A0, A1, Dbuf, gb);
-    if (e != cudaSuccess) return e;
-    if (err_flag_out) {
-        // fold the barrier error into the caller's flag
-        e = cudaMemcpyAsync(err_flag_out, &gb->err, sizeof(int), cudaMemcpyDeviceToDevice, st);
-    }
-    return e;
+    return launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, nt, A0, A1, Dbuf, gb, err_flag_out);
 }
 
 cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStream_t st) {
@@ -668,7 +679,7 @@ cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, 
     int m = s < kLanczosMax ? s : kLanczosMax;
     unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
     GridBar* gb = reinterpret_cast<GridBar*>(p);
-    p += 256;
+    p += kCoopBarrierBytes;
     double2* u = reinterpret_cast<double2*>(p);
     p += (size_t)s * sizeof(double2);
     double2* vprev = reinterpret_cast<double2*>(p);
@@ -676,12 +687,7 @@ cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, 
     double* part = reinterpret_cast<double*>(p);
     p += 4 * (size_t)grid * sizeof(double);
     double* ab = reinterpret_cast<double*>(p);
-    cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
-    if (e != cudaSuccess) return e;
-    e = launch_coop(lanczos_kernel, grid, st, G, s, m, u, vprev, part, ab, lmax, gb);
-    if (e != cudaSuccess) return e;
-    if (err_flag_out) e = cudaMemcpyAsync(err_flag_out, &gb->err, sizeof(int), cudaMemcpyDeviceToDevice, st);
-    return e;
+    return launch_coop(lanczos_kernel, grid, st, G, s, m, u, vprev, part, ab, lmax, gb, err_flag_out);
 }
 
 }  // namespace recon

@@ -148,6 +148,13 @@ cudaError_t launch_weight_S(const Dims& d, const Twiddles& tw, const double2* ds
                             float2* S, cudaStream_t st);
 
 // ---- hpdinv.cu (p = 0: H = (G + eps I)^-1 by a blocked Hermitian sweep, FP64) ----
+// The first kCoopBarrierBytes of the sweep and Lanczos scratch hold the grid barrier of their
+// cooperative launch. A launch that completed leaves it ready for the next one; zero it when the
+// scratch is allocated and after a launch reported a barrier failure (err_flag_out = 1).
+constexpr size_t kCoopBarrierBytes = 256;
+// Sets the error word of the grid barrier at the head of `scratch` (stream-ordered memset; host-side
+// fault injection for tests).
+cudaError_t set_barrier_error(void* scratch, cudaStream_t st);
 size_t hpd_scratch_bytes(const Dims& d);
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max);
 // G (s x s, column-major, Hermitian) is replaced by H = (G + eps I)^-1. *err_flag_out receives

@@ -98,6 +98,7 @@ struct recon_ctx {
     // autotuner: column tile widths per problem shape (P, Q, T, R, coils), timed on first use
     bool autotune = true;
     bool three_pass = false;           // 256 x 256 series: three-pass CG step (RECON_OPT_THREE_PASS)
+    bool inject_barrier_fault = false; // next solve: sweep barrier starts failed (RECON_OPT_INJECT_BARRIER_FAULT)
     std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tiles;
     std::string tile_cache;            // file the tuned choices are appended to (may be empty)
     struct Slot {
@@ -360,7 +361,7 @@ struct Work {
     double *evals, *parts, *rparts, *mparts, *rr, *pq, *eps, *lmax;
     unsigned int* counter;
     int *info, *kerr;
-    void *hpd, *lanc;
+    void *hpd = nullptr, *lanc = nullptr;
     int lwork;
     int gblocks;
     int n_status;
@@ -427,8 +428,13 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
         int dev = 0, sms = 0;
         RC_CUDA(cudaGetDevice(&dev));
         RC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        // the grid barriers of the cooperative kernels start zeroed (see kCoopBarrierBytes)
+        unsigned long gen0 = c->ws_gen;
         GET("hpd", recon::hpd_scratch_bytes(d), hpd, void*);
+        if (c->ws_gen != gen0) RC_CUDA(cudaMemsetAsync(w->hpd, 0, recon::kCoopBarrierBytes, c->stream));
+        gen0 = c->ws_gen;
         GET("lanc", recon::lanczos_scratch_bytes(d, sms), lanc, void*);
+        if (c->ws_gen != gen0) RC_CUDA(cudaMemsetAsync(w->lanc, 0, recon::kCoopBarrierBytes, c->stream));
     }
 #undef GET
     w->n_status = ni;
@@ -501,7 +507,13 @@ int check_status(recon_ctx* c, Work& w, int n_iter) {
     RC_CUDA(cudaMemcpy(info.data(), w.info, n_iter * sizeof(int), cudaMemcpyDeviceToHost));
     RC_CUDA(cudaMemcpy(kerr.data(), w.kerr, 2 * (size_t)n_iter * sizeof(int), cudaMemcpyDeviceToHost));
     for (int e : kerr)
-        if (e != 0) return fail(c, RECON_ETIMEOUT, "a bounded device-wide barrier timed out");
+        if (e != 0) {
+            // re-arm the grid barriers for the next solve (a failed launch leaves them set)
+            if (w.hpd) RC_CUDA(cudaMemset(w.hpd, 0, recon::kCoopBarrierBytes));
+            if (w.lanc) RC_CUDA(cudaMemset(w.lanc, 0, recon::kCoopBarrierBytes));
+            RC_CUDA(cudaDeviceSynchronize());
+            return fail(c, RECON_ETIMEOUT, "a bounded device-wide barrier timed out");
+        }
     for (int e : info)
         if (e != 0) return fail(c, RECON_ENUMERIC, "eigensolver failed (info != 0)");
     return RECON_OK;
@@ -772,6 +784,12 @@ int solve_prepare(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t
     }
     rc = get_work(c, d, prm->cg, prm->irls, true, eig, &sv->w);
     if (rc) return rc;
+    if (c->inject_barrier_fault && sv->w.hpd) {
+        // host-side fault injection: the sweep's barrier error word set, as a peer that gave up
+        // would leave it; the sweeps then return at their first barrier and report it
+        c->inject_barrier_fault = false;
+        RC_CUDA(recon::set_barrier_error(sv->w.hpd, c->stream));
+    }
     return autotune_tiles(c, &sv->d, sv->tw, sv->w.t, masks);
 }
 
@@ -1953,6 +1971,7 @@ int recon_set_option(recon_ctx* c, int option, int value) {
         case RECON_OPT_CLUSTER_FFT: c->cluster_fft = value != 0; return RECON_OK;
         case RECON_OPT_AUTOTUNE: c->autotune = value != 0; return RECON_OK;
         case RECON_OPT_THREE_PASS: c->three_pass = value != 0; return RECON_OK;
+        case RECON_OPT_INJECT_BARRIER_FAULT: c->inject_barrier_fault = value != 0; return RECON_OK;
         default: return fail(c, RECON_EINVAL, "unknown option");
     }
 }

@@ -431,6 +431,28 @@ def test_three_pass_step_matches_four_pass_step(R):
     assert err < 1e-5 and rel(outs[0], x_ref) < 1e-4
 
 
+def test_barrier_fault_injection(R):
+    """Failure detection without a device fault: the FP64 sweep's grid-barrier error word is set
+    from the host before a solve (as a CTA whose bounded wait gave up would leave it). Every sweep
+    of that solve returns at its first barrier and reports it, the solve returns RECON_ETIMEOUT,
+    the barrier is re-armed, and the next solve matches a clean one bitwise."""
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8", n_irls=3, n_cg=4)
+    b = to_dev(c64(prob["kspace"]))
+    m = to_dev(prob["masks"])
+    filt = (w.N1, w.N2, w.M)
+    ref = torch.empty(prob["masks"].shape, dtype=torch.complex64, device="cuda")
+    recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, ref)
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_INJECT_BARRIER_FAULT, 1)
+    out = torch.empty_like(ref)
+    with pytest.raises(recon.ReconError) as e:
+        recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+    assert e.value.code == recon.RECON_ETIMEOUT
+    again = torch.empty_like(ref)
+    recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, again)
+    assert torch.equal(again.cpu(), ref.cpu())
+
+
 SIZE_CASES = [("192x192x6", dict(P=192, Q=192, T=6, N1=5, N2=5, M=2)),
               ("512x512x4", dict(P=512, Q=512, T=4, N1=3, N2=3, M=2)),
               ("16x512x5", dict(P=16, Q=512, T=5, N1=3, N2=7, M=3)),
