@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -65,6 +66,9 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 extern "C" int recon_gram_static(recon_dims dd, recon_filter f, const void* x, void* G_out,
                                  void* lags_out, void* cuda_stream) {
     if (!x || !G_out) return static_fail(RECON_EINVAL, "null pointer");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(G_out) |
+         reinterpret_cast<uintptr_t>(lags_out)) & 15u)
+        return static_fail(RECON_EINVAL, "device arrays must be 16-byte aligned");
     if (dd.P <= 0 || dd.Q <= 0 || dd.T <= 0 || !recon::fft_size_supported(dd.P) ||
         !recon::fft_size_supported(dd.Q))
         return static_fail(RECON_EINVAL, "P and Q must be one of 16, 32, 64, 128, 192, 256, 512");
