@@ -201,7 +201,10 @@ OP_CASES = [("tiny", "tiny_32x32x8", {}), ("perf", "perf_256x256x16", {}),
             ("rows128-M4", "perf_256x256x16", {"P": 32, "Q": 128, "T": 8, "M": 4, "N1": 5,
                                                "N2": 5, "times_ms": _times(8)}),
             ("rows64-M4", "perf_256x256x16", {"P": 16, "Q": 64, "T": 7, "M": 4, "N1": 3,
-                                              "N2": 5, "times_ms": _times(7)})]
+                                              "N2": 5, "times_ms": _times(7)}),
+            # 128-point rows with more than 16 frames (block of 20 frames, 160 threads)
+            ("rows128-T20", "perf_256x256x16", {"P": 32, "Q": 128, "T": 20, "N1": 5, "N2": 5,
+                                                "times_ms": _times(20)})]
 
 
 @pytest.mark.parametrize("case", OP_CASES, ids=[c[0] for c in OP_CASES])
@@ -354,6 +357,16 @@ def test_solve_irls0_is_adjoint(R):
     w, prob = _problem("tiny_32x32x8")
     x_gpu = _solve_gpu(recon, ctx, w, prob, irls=0)
     assert rel(x_gpu, slr.AH(prob["kspace"], prob["masks"])) < 2e-6
+
+
+def test_solve_cg0_refused(R):
+    """Degenerate CG count: a solve needs at least one CG step per IRLS iteration (with none, x
+    would stay at A^H b); cg = 0 is refused before any launch."""
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8")
+    with pytest.raises(recon.ReconError) as e:
+        _solve_gpu(recon, ctx, w, prob, irls=3, cg=0)
+    assert e.value.code == recon.RECON_EINVAL
 
 
 def test_solve_deterministic(R):
