@@ -157,8 +157,9 @@ constexpr size_t kCoopBarrierBytes = 256;
 cudaError_t set_barrier_error(void* scratch, cudaStream_t st);
 size_t hpd_scratch_bytes(const Dims& d);
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max);
-// G (s x s, column-major, Hermitian) is replaced by H = (G + eps I)^-1. *err_flag_out receives
-// 1 if a grid barrier timed out.
+// G (s x s, column-major, Hermitian) is replaced by H = (G + eps I)^-1. The kernel writes
+// *err_flag_out itself (device int, may be NULL): 0 when it completed, 1 when a grid barrier
+// gave up. The same holds for launch_lanczos_lmax.
 cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
                                int* err_flag_out, cudaStream_t st);
 // d_ab[delta] (summed diagonals) from an explicit H
