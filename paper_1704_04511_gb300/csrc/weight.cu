@@ -127,7 +127,15 @@ s_stage2_kernel(const float2* __restrict__ Z, int N1, int P, int Q, int npair,
         const int pr = e / Q, r2 = e % Q;
         const float2* zp = Z + (size_t)pr * L1 * Q + r2;
         float2 acc = make_float2(0.f, 0.f);
-        for (int i1 = 0; i1 < L1; ++i1) acc = cfma(zp[(size_t)i1 * Q], w1[i1], acc);
+        int i1 = 0;
+        for (; i1 + 8 <= L1; i1 += 8) {  // eight loads in flight, then the products in order
+            float2 z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) z[u] = zp[(size_t)(i1 + u) * Q];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc = cfma(z[u], w1[i1 + u], acc);
+        }
+        for (; i1 < L1; ++i1) acc = cfma(zp[(size_t)i1 * Q], w1[i1], acc);
         S[((size_t)pr * P + r1) * Q + r2] = acc;
     }
 }
@@ -154,7 +162,15 @@ s_stage3_kernel(const float2* __restrict__ Z2, int N3, int R, size_t npx,
     for (size_t px = (size_t)blockIdx.x * blockDim.x + threadIdx.x; px < npx;
          px += (size_t)gridDim.x * blockDim.x) {
         float2 acc = make_float2(0.f, 0.f);
-        for (int i3 = 0; i3 < L3; ++i3) acc = cfma(zp[(size_t)i3 * npx + px], w3[i3], acc);
+        int i3 = 0;
+        for (; i3 + 4 <= L3; i3 += 4) {  // four loads in flight, then the products in order
+            float2 z[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) z[u] = zp[(size_t)(i3 + u) * npx + px];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc = cfma(z[u], w3[i3 + u], acc);
+        }
+        for (; i3 < L3; ++i3) acc = cfma(zp[(size_t)i3 * npx + px], w3[i3], acc);
         out[px] = acc;
     }
 }
