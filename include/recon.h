@@ -149,9 +149,9 @@ int recon_poll(recon_ctx* c, int ticket, int* done);
  *   update), which measures faster on one GB300 while the series fits in L2. Same CG in exact
  *   arithmetic; rounding differs at the FP32 level. */
 #define RECON_OPT_THREE_PASS 4  /* default off */
-/* RECON_OPT_INJECT_BARRIER_FAULT (testing): the next solve on this context starts with the error
- *   word of its FP64 sweep's grid barrier set from the host, as a CTA whose bounded wait gave up
- *   would leave it; every sweep of that solve returns at its first barrier and reports it, the
+/* RECON_OPT_INJECT_BARRIER_FAULT (testing): the next solve on this context that forms its weight
+ *   by the FP64 sweep (p = 0, RECON_WEIGHT_AUTO) starts with the error word of the sweep's grid
+ *   barrier set from the host, as a CTA whose bounded wait gave up would leave it; every sweep of that solve returns at its first barrier and reports it, the
  *   solve returns RECON_ETIMEOUT and re-arms the barrier, and the following solve runs normally.
  *   One-shot (cleared when used). No kernel waits, traps or faults for it. */
 #define RECON_OPT_INJECT_BARRIER_FAULT 5
