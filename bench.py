@@ -74,7 +74,7 @@ ALU_KINDS = ("hpd_inverse", "lanczos")
 # benchmark workload (steady state, caches kept; profiles/hpd_sweep_kernel_s243.md gives the
 # command). Only for the kernel versions those captures measured: drop an entry when its
 # kernel changes.
-TRAFFIC_BYTES = {"hpd_inverse": 475947}
+TRAFFIC_BYTES = {"hpd_inverse": 462123}
 
 
 def alg_flops(kind: str, w) -> float:
