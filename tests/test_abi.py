@@ -58,3 +58,30 @@ def test_null_context_is_rejected(lib):
     from paper_1704_04511_gb300 import recon
     assert lib.recon_solve(None, recon.recon_dims(32, 32, 8), None, None,
                            recon.recon_filter(5, 5, 2), None, None) == recon.RECON_EINVAL
+
+
+def test_binding_constants_match_header(lib):
+    """Every integer #define the binding mirrors has the header's value."""
+    from paper_1704_04511_gb300 import recon
+    src = open(os.path.join(ROOT, "include", "recon.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in
+               re.finditer(r"#define (RECON_[A-Z0-9_]+) \(?(-?\d+)\)?", src)}
+    mirrored = [n for n in dir(recon) if n.startswith("RECON_") and isinstance(getattr(recon, n), int)]
+    assert "RECON_OPT_INJECT_BARRIER_FAULT" in mirrored and "RECON_ETIMEOUT" in mirrored
+    for n in mirrored:
+        if n in defines:
+            assert getattr(recon, n) == defines[n], n
+    assert recon.PROF_KINDS == defines["RECON_PROF_KINDS"]
+
+
+def test_static_gram_checks_pointers_first(lib):
+    """recon_gram_static refuses null or misaligned device pointers with RECON_EINVAL before it
+    touches the device (the values are never dereferenced)."""
+    import ctypes
+    from paper_1704_04511_gb300 import recon
+    d, f = recon.recon_dims(32, 32, 8), recon.recon_filter(5, 5, 2)
+    assert lib.recon_gram_static(d, f, None, ctypes.c_void_p(4096), None, None) == recon.RECON_EINVAL
+    assert lib.recon_gram_static(d, f, ctypes.c_void_p(4096 + 8), ctypes.c_void_p(8192), None,
+                                 None) == recon.RECON_EINVAL
+    assert lib.recon_gram_static(d, f, ctypes.c_void_p(4096), ctypes.c_void_p(8192),
+                                 ctypes.c_void_p(16384 + 4), None) == recon.RECON_EINVAL
