@@ -137,3 +137,24 @@ def test_full_sampling_small_lambda_returns_adjoint(rng):
     b = _crandn(rng, T, P, Q)
     x = slr.irls(b, masks, 3, 3, 2, lam=1e-12, p=0.0, n_irls=2, n_cg=3)
     assert np.linalg.norm(x - slr.F2H(b)) <= 1e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("M,T", [(2, 6), (3, 16), (4, 9), (5, 12)])
+def test_banded_W_diagonal_sum_form(M, T):
+    """The CG kernels evaluate W x (Eq. grad-ls) per frame n whose M windows all exist
+    (M - 1 <= n < k) as sum_d c_d x_{n+d}, c_d = sum_{a-b=d} S_ab(r) (2M - 1 products instead of
+    M^2). Pinned here against the window sum of the oracle on random Hermitian S(r)."""
+    rng = np.random.default_rng(100 + 10 * M + T)
+    P, Q = 4, 6
+    A = rng.standard_normal((M, M, P, Q)) + 1j * rng.standard_normal((M, M, P, Q))
+    S = A + np.conj(np.transpose(A, (1, 0, 2, 3)))           # Hermitian per pixel
+    x = rng.standard_normal((T, P, Q)) + 1j * rng.standard_normal((T, P, Q))
+    ref = slr.apply_W(x, S)
+    k = T - M + 1
+    c = {d: sum(S[a, a - d] for a in range(M) if 0 <= a - d < M) for d in range(-(M - 1), M)}
+    for n in range(M - 1, k):
+        wn = sum(c[d] * x[n + d] for d in range(-(M - 1), M))
+        assert np.max(np.abs(wn - ref[n])) <= 1e-12 * np.max(np.abs(ref[n]))
+    # the diagonal sums are Hermitian-conjugate pairs
+    for d in range(1, M):
+        assert np.allclose(c[-d], np.conj(c[d]), rtol=0, atol=1e-13)
