@@ -158,3 +158,42 @@ def test_banded_W_diagonal_sum_form(M, T):
     # the diagonal sums are Hermitian-conjugate pairs
     for d in range(1, M):
         assert np.allclose(c[-d], np.conj(c[d]), rtol=0, atol=1e-13)
+
+
+def _lanczos_top(G, m):
+    """Largest Ritz value after m steps of plain Lanczos (no reorthogonalisation) from the start
+    vector the GPU kernel uses, u_i = 1 + 0.5 sin(i) + i 0.25 i cos(3 i) / s."""
+    s = G.shape[0]
+    i = np.arange(s)
+    u = (1.0 + 0.5 * np.sin(i)) + 1j * (0.25 * np.cos(3.0 * i) * i / s)
+    beta, vprev, al, be = np.linalg.norm(u), np.zeros(s, complex), [], []
+    for _ in range(min(m, s)):
+        v = u / beta
+        w = G @ v
+        a = float(np.real(np.vdot(v, w)))
+        u = w - a * v - beta * vprev
+        vprev, beta = v, np.linalg.norm(u)
+        al.append(a)
+        be.append(beta)
+        if beta <= 1e-300 * abs(a) + 1e-300:
+            break
+    Tm = np.diag(al) + np.diag(be[:-1], 1) + np.diag(be[:-1], -1)
+    return np.linalg.eigvalsh(Tm)[-1]
+
+
+@pytest.mark.parametrize("case", ["tiny_32x32x8", "perf_256x256x16", "random"])
+def test_lanczos_step_cap_converges(case):
+    """The p = 0 weight takes eps0 = lambda_max(G(x0)) / 100 from at most 64 Lanczos steps.
+    Pinned: lambda_max of the workloads' Grams (and of a random series' Gram, whose top gap is
+    only ~0.2 %) is reached to rounding within that cap."""
+    import synth
+    if case == "random":
+        rng = np.random.default_rng(3)
+        x = rng.standard_normal((16, 64, 64)) + 1j * rng.standard_normal((16, 64, 64))
+        G = slr.gram_fft(x, 9, 9, 3)
+    else:
+        w = synth.workload(case)
+        prob = synth.make_problem(w)
+        G = slr.gram_fft(slr.AH(prob["kspace"], prob["masks"]), w.N1, w.N2, w.M)
+    lam = np.linalg.eigvalsh(G)[-1]
+    assert abs(_lanczos_top(G, 64) - lam) <= 1e-12 * lam
