@@ -155,6 +155,14 @@ int recon_poll(recon_ctx* c, int ticket, int* done);
  *   solve returns RECON_ETIMEOUT and re-arms the barrier, and the following solve runs normally.
  *   One-shot (cleared when used). No kernel waits, traps or faults for it. */
 #define RECON_OPT_INJECT_BARRIER_FAULT 5
+/* RECON_OPT_TEST_WITHHOLD_ARRIVAL (testing): in the next solve on this context that forms its
+ *   weight by the FP64 sweep (p = 0, RECON_WEIGHT_AUTO), CTA 1 of every Lanczos and sweep launch
+ *   leaves at its first grid barrier without arriving, as a lost CTA would, and the bounded waits
+ *   of the other CTAs give up after 4096 polls (about a millisecond) instead of the default limit
+ *   of seconds. The waits run out for real: the kernels record the failure and return, the solve
+ *   returns RECON_ETIMEOUT and re-arms the barriers, and the following solve runs normally. That
+ *   solve is issued as direct launches (no graph). One-shot (cleared when used). */
+#define RECON_OPT_TEST_WITHHOLD_ARRIVAL 6
 int recon_set_option(recon_ctx* c, int option, int value);
 
 
@@ -221,16 +229,22 @@ int recon_cg(recon_ctx* c, recon_dims d, recon_filter f, const uint8_t* masks,
  * is a deployment aid, not part of the method.
  *  - Arguments as for recon_gram, plus cuda_stream (a cudaStream_t; NULL = the default stream);
  *    x, G_out, lags_out are device pointers on the current device. The call is synchronous.
- *  - The first call on each device (with that device current) looks up the array's device
- *    address (cudaGetSymbolAddress) and caches it; make that first call before any stream
- *    capture.
+ *  - The first call on each device is a warm-up. With the device current it looks up the array's
+ *    device address (cudaGetSymbolAddress) and caches it for that device's context. Under CUDA's
+ *    lazy module loading (the default since CUDA 12.2) this first call is also what loads the
+ *    library's Gram code on that device and commits the RECON_GRAM_STATIC_BYTES array, which can
+ *    allocate device memory and synchronise the device. Make it once at start-up, before any
+ *    stream capture; only the calls after it allocate nothing. After a device reset
+ *    (cudaDeviceReset, a new primary context) the next call is a first call again: the cached
+ *    address belongs to the old context and is looked up anew.
  *  - A problem whose scratch exceeds RECON_GRAM_STATIC_BYTES is rejected with RECON_EINVAL and a
  *    message naming the bytes it needs (recon_last_error(NULL)); use recon_gram for it. The
  *    256x256x16 series with a 9x9x3 filter needs about 0.42 MB.
  *  - Every call uses the same array and it keeps the last call's contents; each call writes
  *    everything it reads first. Calls that overlap on the GPU (other host threads or streams)
  *    race on the array and must be serialised by the caller.
- *  - Allocates no device memory (no cudaMalloc / cudaFree or allocating library call). */
+ *  - After the warm-up call, allocates no device memory (no cudaMalloc / cudaFree or allocating
+ *    library call). */
 #define RECON_GRAM_STATIC_BYTES (4u * 1024u * 1024u)
 int recon_gram_static(recon_dims d, recon_filter f, const void* x, void* G_out, void* lags_out,
                       void* cuda_stream);

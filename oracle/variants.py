@@ -10,9 +10,9 @@ x_hat = F x unitary, A = mask * F):
     Everything else is the proposed method's arithmetic.
   * HLR-Voxel (Sec. II-D, Eq. MORASA-objective; Sec. IV-B names it): one k x M Toeplitz matrix of
     the temporal signal per pixel, T_r[j, m] = x_{j+M-1-m}(r), image domain, no spatial coupling;
-    IRLS with one M x M Gram G_r = T_r^H T_r and one weight H_r = (G_r + eps_r I)^(p/2-1) per
-    pixel. eps_r^(0) = eps0_frac * lambda_max(G_r(x0)), eps_r <- eps_r / gamma (the Sec. III-C
-    schedule applied to every pixel's matrix).
+    IRLS with one M x M Gram G_r = T_r^H T_r and one weight H_r = (G_r + eps I)^(p/2-1) per
+    pixel. The penalty sum_r ||T_r||_p is one objective smoothed by one eps, scheduled as in
+    Sec. III-C: eps^(0) = eps0_frac * max_r lambda_max(G_r(x0)), eps <- eps / gamma.
   * IRLS-direct (Sec. IV-A: Eq. x-update and Eq. weight-update solved without the FFT
     approximations): the exact multi-fold Toeplitz matrix, valid linear convolution in all three
     dimensions (rows Gamma:Lambda of Sec. II-B; slr.lift_linear), its Gram G = T^H T, the weight
@@ -130,10 +130,11 @@ def voxel_grams(x: np.ndarray, M: int) -> np.ndarray:
     return np.moveaxis(slr.pair_products(x, M), (0, 1), (2, 3))
 
 
-def voxel_weights(Gv: np.ndarray, eps: np.ndarray, p: float) -> np.ndarray:
-    """H_r = U diag((lambda + eps_r)^(p/2-1)) U^H per pixel (batched eigh). eps: (P, Q)."""
+def voxel_weights(Gv: np.ndarray, eps, p: float) -> np.ndarray:
+    """H_r = U diag((lambda + eps_r)^(p/2-1)) U^H per pixel (batched eigh). eps: one value for
+    every pixel, or (P, Q)."""
     lam, U = np.linalg.eigh(Gv)
-    alpha = (lam + eps[..., None]) ** (p / 2.0 - 1.0)
+    alpha = (lam + np.asarray(eps, dtype=np.float64)[..., None]) ** (p / 2.0 - 1.0)
     return np.einsum("...im,...m,...jm->...ij", U, alpha, U.conj())
 
 
@@ -155,13 +156,14 @@ def voxel_penalty(x: np.ndarray, Hv: np.ndarray, M: int) -> float:
     return tot
 
 
-def voxel_initial_eps(x0: np.ndarray, M: int, frac: float = 0.01) -> np.ndarray:
-    return frac * np.linalg.eigvalsh(voxel_grams(x0, M))[..., -1]
+def voxel_initial_eps(x0: np.ndarray, M: int, frac: float = 0.01) -> float:
+    """eps^(0) = frac * the largest lambda_max(G_r(x0)) over the pixels (Sec. III-C)."""
+    return frac * float(np.max(np.linalg.eigvalsh(voxel_grams(x0, M))[..., -1]))
 
 
 def irls_hlr_voxel(kspace, masks, M, lam, p, n_irls, n_cg, gamma=1.4, eps_frac=0.01):
-    """IRLS on sum_r ||T_r||_p: x0 = A^H b, per-pixel eps schedule, n_cg CG steps per iteration
-    on (A^H A + lam W) with W built from S(r) = H_r^T."""
+    """IRLS on sum_r ||T_r||_p: x0 = A^H b, one eps for the whole penalty (Sec. III-C schedule),
+    n_cg CG steps per iteration on (A^H A + lam W) with W built from S(r) = H_r^T."""
     rhs = slr.AH(kspace, masks)
     x = rhs.copy()
     eps = voxel_initial_eps(x, M, eps_frac)

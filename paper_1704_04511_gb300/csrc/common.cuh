@@ -67,6 +67,21 @@ RECON_DEV float2 cfmacj(float2 a, float2 b, float2 acc) {
     return acc;
 }
 
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly in round-to-nearest; the explicit
+// rounding intrinsics keep the compiler from contracting or reassociating it.
+RECON_DEV void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// Compensated accumulation: hi + lo += v, the rounding error of every addition to hi kept in lo.
+RECON_DEV void comp_add(float& hi, float& lo, float v) {
+    float s, e;
+    two_sum(hi, v, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
 RECON_DEV double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 RECON_DEV double2 zmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));

@@ -8,7 +8,10 @@
 // lags around zero are used, so they are evaluated directly as a pruned separable DFT:
 //   gram_rows_kernel: one CTA per image row r1: the pair products of the row (a sliding window
 //                     over the frames, all pairs per column in registers) and their pruned
-//                     length-Q DFT Y[pair][d2][r1] (FP32, warp-tree sums);
+//                     length-Q DFT Y[pair][d2][r1] (FP32 products with compensated sums: each
+//                     accumulation carries the rounding errors of its additions in a second
+//                     float, through the window sums, the DFT terms and the warp tree, and the
+//                     pair becomes one FP64 value);
 //   gram_fill_kernel: one warp per lag: the length-P direction sum_r1 Y[pair][d2][r1] w_P^(d1 r1)
 //                     in FP64 (fixed order, deterministic), then the lag scattered over the
 //                     (l, l') pairs it fills in G (column-major s x s complex128, both triangles).
@@ -27,7 +30,10 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-template <int M>
+// kLo = false (only where the low parts do not fit in shared memory: M = 6 with 512-point rows
+// and more than 12 frames): each window sum is rounded once to FP32 (hi + lo) before the DFT,
+// whose terms and tree stay compensated.
+template <int M, bool kLo>
 __global__ void __launch_bounds__(kThreads)
 gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int circ,
                  const float2* __restrict__ twQ, double2* __restrict__ Y) {
@@ -36,8 +42,9 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int 
     // circ: T windows with frame indices taken mod T (the fully circulant lifting)
     const int k = circ ? T : T - M + 1, L2 = 2 * N2 - 1;
     float2* xs = sm;                         // [T][Q] row r1 of every frame
-    float2* qp = xs + (size_t)T * Q;         // [NP][Q] pair products
-    float2* tw = qp + (size_t)NP * Q;        // [Q]
+    float2* qp = xs + (size_t)T * Q;         // [NP][Q] pair products (compensated sum, high part)
+    float2* ql = qp + (size_t)NP * Q;        // [NP][Q] their low parts (kLo)
+    float2* tw = ql + (kLo ? (size_t)NP * Q : 0);  // [Q]
     const int r1 = blockIdx.x;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) tw[i] = twQ[i];
     for (int e = threadIdx.x; e < T * Q; e += blockDim.x) {
@@ -47,9 +54,9 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int 
     __syncthreads();
     // q_ab(c) = sum_j conj(x_{j+M-1-a}(c)) x_{j+M-1-b}(c): window w[m] = x_{j+M-1-m}(c)
     for (int c = threadIdx.x; c < Q; c += blockDim.x) {
-        float2 w[M], acc[NP];
+        float2 w[M], acc[NP], lo[NP];
 #pragma unroll
-        for (int e = 0; e < NP; ++e) acc[e] = make_float2(0.f, 0.f);
+        for (int e = 0; e < NP; ++e) acc[e] = lo[e] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 1; m < M; ++m) w[m] = xs[(M - 1 - m) * Q + c];
         for (int j = 0; j < k; ++j) {
@@ -58,32 +65,65 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int 
 #pragma unroll
             for (int a = 0; a < M; ++a)
 #pragma unroll
-                for (int b = a; b < M; ++b, ++e) acc[e] = cfmacj(w[a], w[b], acc[e]);
+                for (int b = a; b < M; ++b, ++e) {
+                    const float2 t = cmulcj(w[a], w[b]);
+                    comp_add(acc[e].x, lo[e].x, t.x);
+                    comp_add(acc[e].y, lo[e].y, t.y);
+                }
 #pragma unroll
             for (int m = M - 1; m > 0; --m) w[m] = w[m - 1];
         }
 #pragma unroll
-        for (int e = 0; e < NP; ++e) qp[e * Q + c] = acc[e];
+        for (int e = 0; e < NP; ++e) {
+            if (kLo) {
+                qp[e * Q + c] = acc[e];
+                ql[e * Q + c] = lo[e];
+            } else {
+                qp[e * Q + c] = make_float2(__fadd_rn(acc[e].x, lo[e].x), __fadd_rn(acc[e].y, lo[e].y));
+            }
+        }
     }
     __syncthreads();
-    // Y[pair][d2] = sum_c q[pair][c] w_Q^(d2 c); one warp per output, lanes stride c
+    // Y[pair][d2] = sum_c q[pair][c] w_Q^(d2 c); one warp per output, lanes stride c, each term
+    // (hi + lo) w added to a compensated (hi, lo) pair, then a TwoSum shuffle tree
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nout = NP * L2;
     for (int o = warp; o < nout; o += kWarps) {
         const int pr = o / L2, i2 = o % L2;
         const int d2m = (i2 - (N2 - 1) + Q) % Q;
         const float2* qrow = qp + (size_t)pr * Q;
+        const float2* qlow = ql + (size_t)pr * Q;
         int idx = (d2m * lane) % Q;
         const int step = (d2m * 32) % Q;
-        float2 y = make_float2(0.f, 0.f);
+        float2 y = make_float2(0.f, 0.f), yl = make_float2(0.f, 0.f);
         for (int c = lane; c < Q; c += 32) {
-            y = cfma(qrow[c], tw[idx], y);
+            const float2 wt = tw[idx];
+            const float2 t = cmul(qrow[c], wt);
+            comp_add(y.x, yl.x, t.x);
+            comp_add(y.y, yl.y, t.y);
+            if (kLo) {
+                const float2 tl = cmul(qlow[c], wt);
+                yl.x = __fadd_rn(yl.x, tl.x);
+                yl.y = __fadd_rn(yl.y, tl.y);
+            }
             idx += step;
             if (idx >= Q) idx -= Q;
         }
-        y.x = warp_sum(y.x);
-        y.y = warp_sum(y.y);
-        if (lane == 0) Y[(size_t)o * P + r1] = make_double2((double)y.x, (double)y.y);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float hx = __shfl_xor_sync(0xffffffffu, y.x, off);
+            const float lx = __shfl_xor_sync(0xffffffffu, yl.x, off);
+            const float hy = __shfl_xor_sync(0xffffffffu, y.y, off);
+            const float ly = __shfl_xor_sync(0xffffffffu, yl.y, off);
+            float sx, ex, sy, ey;
+            two_sum(y.x, hx, sx, ex);
+            two_sum(y.y, hy, sy, ey);
+            y = make_float2(sx, sy);
+            yl.x = __fadd_rn(__fadd_rn(yl.x, lx), ex);
+            yl.y = __fadd_rn(__fadd_rn(yl.y, ly), ey);
+        }
+        if (lane == 0)
+            Y[(size_t)o * P + r1] = make_double2((double)y.x + (double)yl.x, (double)y.y + (double)yl.y);
     }
 }
 
@@ -181,10 +221,17 @@ __global__ void gram_fill3_kernel(const double2* __restrict__ Z, int R, int N1, 
     }
 }
 
+constexpr size_t kGramSmemMax = 220 * 1024;
+
+size_t gram_smem_lo(const Dims& d, bool lo) {
+    return ((size_t)d.T * d.Q + (lo ? 2 : 1) * (size_t)d.npair() * d.Q + d.Q) * sizeof(float2);
+}
+
 }  // namespace
 
 size_t gram_smem(const Dims& d) {
-    return ((size_t)d.T * d.Q + (size_t)d.npair() * d.Q + d.Q) * sizeof(float2);
+    const size_t with_lo = gram_smem_lo(d, true);
+    return with_lo <= kGramSmemMax ? with_lo : gram_smem_lo(d, false);
 }
 
 // One CTA per image row; the scratch holds the row DFTs Y[pair][d2][row] (complex128) and, for
@@ -201,10 +248,11 @@ cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, doub
                         int nblocks, double2* lags, double2* G, cudaStream_t st) {
     if (nblocks != d.rows()) return cudaErrorInvalidValue;
     const size_t smem = gram_smem(d);
-    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem > kGramSmemMax) return cudaErrorInvalidValue;
+    const bool lo = smem == gram_smem_lo(d, true);
 #define CASE(MM)                                                                                 \
     case MM: {                                                                                   \
-        auto k = gram_rows_kernel<MM>;                                                           \
+        auto k = lo ? gram_rows_kernel<MM, true> : gram_rows_kernel<MM, false>;                  \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem);                                         \
         if (e != cudaSuccess) return e;                                                          \

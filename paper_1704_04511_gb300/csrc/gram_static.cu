@@ -24,21 +24,56 @@ static __device__ __align__(256) unsigned char g_gram_scratch[RECON_GRAM_STATIC_
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx_id[kMaxDevices] = {0};
 
 int static_fail(int code, const std::string& msg) {
     recon::set_context_free_error(msg);  // read back with recon_last_error(NULL)
     return code;
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Identity of the calling thread's current context (a driver context id, unique for the life of
+// the process), 0 when there is none yet or the driver does not offer the query. The two driver
+// calls are reached through the runtime's entry-point lookup, so the library does not link the
+// driver library itself.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    }
+    if (!get_current || !get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device, looked up once per device and
+// context: a device reset gives the device a new primary context, whose array lives elsewhere.
+// Without a context id (no current context yet, or no driver query) it is looked up every call.
 int scratch_on_device(int dev, unsigned char** out) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!g_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_gram_scratch);
         if (e != cudaSuccess)
             return static_fail(RECON_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_addr[dev] = p;
+        // the lookup creates the context when the thread had none: read its id now
+        g_ctx_id[dev] = id != 0 ? id : current_context_id();
     }
     *out = reinterpret_cast<unsigned char*>(g_addr[dev]);
     return RECON_OK;

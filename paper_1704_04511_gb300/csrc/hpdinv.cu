@@ -69,22 +69,26 @@ RECON_DEV unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
 // launch that completed every barrier leaves a valid starting state for the next one: the word
 // is zeroed once when its scratch is allocated and again by the host after a reported failure,
 // not before every launch. Thread 0 of each CTA then polls the word with
-// acquire loads. Returns false (and sets gb->err) if the wait exceeded kSpinLimit polls; after a
-// failure every later call returns false at once so the kernel can unwind.
-RECON_DEV bool grid_barrier(GridBar* gb) {
+// acquire loads. Returns false (and sets gb->err) if the wait exceeded `polls` polls; after a
+// failure every later call returns false at once so the kernel can unwind. Test hook: the CTA
+// numbered `fault.withhold` (> 0) returns false at once without arriving, as a CTA that was lost
+// would, so that the others' waits run out.
+RECON_DEV bool grid_barrier(GridBar* gb, const CoopFault& fault) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = (ld_acquire(&gb->err) == 0);
+        if (ok && fault.withhold > 0 && (int)blockIdx.x == fault.withhold) ok = 0;
         if (ok) {
             __threadfence();
             const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
             const unsigned int old = atom_add_acq_rel(&gb->word, inc);
             // the arrival that flips bit 31 is the last one: it need not poll
             const bool last = (((old + inc) ^ old) & 0x80000000u) != 0u;
+            const long long limit = fault.polls > 0 ? fault.polls : kSpinLimit;
             long long it = 0;
             while (!last && ((ld_acquire(&gb->word) ^ old) & 0x80000000u) == 0u) {
-                if (++it > kSpinLimit) {
+                if (++it > limit) {
                     atomicExch(&gb->err, 1);
                     ok = 0;
                     break;
@@ -314,7 +318,7 @@ RECON_DEV void sweep_pivot(SweepSmem& sm, int K, const double2* Ain, const doubl
 __global__ void __launch_bounds__(kThreads, 2)
 hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
                  double2* __restrict__ A0, double2* __restrict__ A1, double2* __restrict__ Dbuf,
-                 GridBar* gb, int* err_out) {
+                 GridBar* gb, int* err_out, CoopFault fault) {
     __shared__ SweepSmem sm;
     const int tid = threadIdx.x;
     const int g = tid / kTileT, e = tid % kTileT;
@@ -339,13 +343,13 @@ hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
         }
         A0[tile_off(I, J) + e] = v;
     }
-    if (!grid_barrier(gb)) return report(err_out, 1);
+    if (!grid_barrier(gb, fault)) return report(err_out, 1);
     if (blockIdx.x == 0 && g == 0) {  // D_0
         sm.X[e] = A0[e];
         group_sync(0);
         tile_inverse(sm.X, sm.T1, Dbuf);
     }
-    if (!grid_barrier(gb)) return report(err_out, 1);
+    if (!grid_barrier(gb, fault)) return report(err_out, 1);
 
     for (int K = 0; K < nt; ++K) {
         const double2* Ain = (K & 1) ? A1 : A0;
@@ -357,7 +361,7 @@ hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
         } else {
             for (int it = 0; it < sm.nitem; ++it) sweep_item(sm, sm.item[it], K, nt, Ain, Aout, DK);
         }
-        if (!grid_barrier(gb)) return report(err_out, 1);
+        if (!grid_barrier(gb, fault)) return report(err_out, 1);
     }
     // H = -A (s x s, full, column-major) written over G
     const double2* Af = (nt & 1) ? A1 : A0;
@@ -409,7 +413,7 @@ __global__ void hdiag_kernel(const double2* __restrict__ H, int N1, int N2, int 
 __global__ void __launch_bounds__(kThreads)
 lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict__ u,
                double2* __restrict__ vprev, double* __restrict__ part, double* __restrict__ ab,
-               double* __restrict__ lmax_out, GridBar* gb, int* err_out) {
+               double* __restrict__ lmax_out, GridBar* gb, int* err_out, CoopFault fault) {
     __shared__ double red[kThreads / 32];
     __shared__ double s_beta, s_ib, s_alpha;
     __shared__ double sh_lo, sh_hi;
@@ -422,7 +426,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
         u[i] = make_double2(1.0 + 0.5 * sin((double)i), 0.25 * cos(3.0 * i) * i / s);
         vprev[i] = make_double2(0.0, 0.0);
     }
-    if (!grid_barrier(gb)) return report(err_out, 1);
+    if (!grid_barrier(gb, fault)) return report(err_out, 1);
     if (warp == 0) {
         double acc = 0.0;
         for (int i = lane; i < s; i += 32) acc += u[i].x * u[i].x + u[i].y * u[i].y;
@@ -467,7 +471,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
             for (int w = 0; w < kThreads / 32; ++w) t += red[w];
             pa[blockIdx.x] = t;
         }
-        if (!grid_barrier(gb)) return report(err_out, 1);
+        if (!grid_barrier(gb, fault)) return report(err_out, 1);
         if (warp == 0) {
             const double al = warp0_sum_array(pa, gridDim.x);
             if (lane == 0) s_alpha = al;
@@ -494,7 +498,7 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
             for (int w = 0; w < kThreads / 32; ++w) t += red[w];
             pb[blockIdx.x] = t;
         }
-        if (!grid_barrier(gb)) return report(err_out, 1);
+        if (!grid_barrier(gb, fault)) return report(err_out, 1);
         if (warp == 0) {
             const double b2 = warp0_sum_array(pb, gridDim.x);
             if (lane == 0) {
@@ -645,7 +649,7 @@ size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {
 }
 
 cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
-                               int* err_flag_out, cudaStream_t st) {
+                               int* err_flag_out, cudaStream_t st, CoopFault fault) {
     const int s = d.s(), nt = tiles_per_side(s);
     const size_t nlt = (size_t)nt * (nt + 1) / 2;
     int grid = 0;
@@ -660,7 +664,8 @@ cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, voi
     double2* A1 = reinterpret_cast<double2*>(p);
     p += nlt * kTileT * sizeof(double2);
     double2* Dbuf = reinterpret_cast<double2*>(p);
-    return launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, nt, A0, A1, Dbuf, gb, err_flag_out);
+    return launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, nt, A0, A1, Dbuf, gb, err_flag_out,
+                       fault);
 }
 
 cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStream_t st) {
@@ -672,7 +677,7 @@ cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStr
 }
 
 cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, double* lmax,
-                                int* err_flag_out, cudaStream_t st) {
+                                int* err_flag_out, cudaStream_t st, CoopFault fault) {
     int grid = 0;
     if (coop_grid((const void*)lanczos_kernel, &grid)) return cudaErrorInvalidConfiguration;
     const int s = d.s();
@@ -687,7 +692,8 @@ cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, 
     double* part = reinterpret_cast<double*>(p);
     p += 4 * (size_t)grid * sizeof(double);
     double* ab = reinterpret_cast<double*>(p);
-    return launch_coop(lanczos_kernel, grid, st, G, s, m, u, vprev, part, ab, lmax, gb, err_flag_out);
+    return launch_coop(lanczos_kernel, grid, st, G, s, m, u, vprev, part, ab, lmax, gb, err_flag_out,
+                       fault);
 }
 
 }  // namespace recon

@@ -155,18 +155,26 @@ constexpr size_t kCoopBarrierBytes = 256;
 // Sets the error word of the grid barrier at the head of `scratch` (stream-ordered memset; host-side
 // fault injection for tests).
 cudaError_t set_barrier_error(void* scratch, cudaStream_t st);
+// Test hook of the cooperative weight kernels (host-directed failure, no fault): CTA `withhold`
+// (> 0; 0 = none) leaves at its first grid barrier without arriving, and every wait gives up after
+// `polls` polls (0 = the default limit of seconds), so that the others' bounded waits run out,
+// the launch reports 1 and returns.
+struct CoopFault {
+    int withhold = 0;
+    long long polls = 0;
+};
 size_t hpd_scratch_bytes(const Dims& d);
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max);
 // G (s x s, column-major, Hermitian) is replaced by H = (G + eps I)^-1. The kernel writes
 // *err_flag_out itself (device int, may be NULL): 0 when it completed, 1 when a grid barrier
 // gave up. The same holds for launch_lanczos_lmax.
 cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
-                               int* err_flag_out, cudaStream_t st);
+                               int* err_flag_out, cudaStream_t st, CoopFault fault = {});
 // d_ab[delta] (summed diagonals) from an explicit H
 cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStream_t st);
 // *lmax = largest eigenvalue of G (Lanczos, FP64)
 cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, double* lmax,
-                                int* err_flag_out, cudaStream_t st);
+                                int* err_flag_out, cudaStream_t st, CoopFault fault = {});
 
 // ---- frame_op.cu (square frames: cluster 2-D transform per frame + pixel-parallel W) ----
 bool frame_op_supported(const Dims& d);
@@ -228,11 +236,12 @@ cudaError_t launch_row_inv_w_upd(const Dims& d, const Twiddles& tw, const float2
                                  double* pq_out, Partials* rr, cudaStream_t st);
 
 // ---- variants.cu (comparison methods of Sec. IV) ----
-// HLR-Voxel weight per pixel (S = H_r^T into [pair][P][Q]); eps_mode 0: eps_in[px], 1: eps0 =
-// frac * lambda_max(G_r) into eps_state, 2: eps_state /= gamma. G_out / lmax_out may be null.
+// HLR-Voxel weight per pixel (S = H_r^T into [pair][P][Q]); eps_mode 0: eps_r = eps_in[px];
+// 1: no weight, the largest lambda_max(G_r) over the pixels into *lmax_max (atomic max of the
+// FP64 bits; zero it first); 2: eps_r = eps_in[0] for every pixel. G_out / lmax_out may be null.
 cudaError_t launch_voxel_weight(const Dims& d, const float2* x, double p, const double* eps_in,
-                                double* eps_state, int eps_mode, double frac, double gamma,
-                                float2* S, double2* G_out, double* lmax_out, cudaStream_t st);
+                                double* lmax_max, int eps_mode, float2* S, double2* G_out,
+                                double* lmax_out, cudaStream_t st);
 // IRLS-direct: rows of the exact (valid) lifting, (T-M+1)(P-N1+1)(Q-N2+1)
 size_t direct_rows(const Dims& d);
 // Tm (rows x s, column-major) of x_hat; complex128 when fp64, else complex64

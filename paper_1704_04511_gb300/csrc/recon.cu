@@ -99,6 +99,7 @@ struct recon_ctx {
     bool autotune = true;
     bool three_pass = false;           // 256 x 256 series: three-pass CG step (RECON_OPT_THREE_PASS)
     bool inject_barrier_fault = false; // next solve: sweep barrier starts failed (RECON_OPT_INJECT_BARRIER_FAULT)
+    bool withhold_arrival = false;     // next solve: one CTA withholds its barrier arrival (RECON_OPT_TEST_WITHHOLD_ARRIVAL)
     std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tiles;
     std::string tile_cache;            // file the tuned choices are appended to (may be empty)
     struct Slot {
@@ -366,6 +367,7 @@ struct Work {
     int gblocks;
     int n_status;
     bool use_eig;
+    recon::CoopFault fault;  // test hook of the cooperative weight kernels (default: none)
 };
 
 int eig_lwork(recon_ctx* c, int s, double2* G, double* evals, int* lwork) {
@@ -481,14 +483,15 @@ int weight_step(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, double
         if (!eps_mode_set) {
             if (eps_first) {
                 ProfScope ps(c, RECON_PROF_LANCZOS);
-                RC_CUDA(recon::launch_lanczos_lmax(d, w.G, w.lanc, w.lmax, w.kerr + 2 * it + 1, c->stream));
+                RC_CUDA(recon::launch_lanczos_lmax(d, w.G, w.lanc, w.lmax, w.kerr + 2 * it + 1, c->stream,
+                                                   w.fault));
             }
             ProfScope ps(c, RECON_PROF_EPS);
             RC_CUDA(recon::launch_eps(w.lmax, w.eps, eps_first, eps_frac, gamma, c->stream));
         }
         {
             ProfScope ps(c, RECON_PROF_INV);
-            RC_CUDA(recon::launch_hpd_inverse(d, w.G, w.eps, w.hpd, w.kerr + 2 * it, c->stream));
+            RC_CUDA(recon::launch_hpd_inverse(d, w.G, w.eps, w.hpd, w.kerr + 2 * it, c->stream, w.fault));
         }
         ProfScope ps(c, RECON_PROF_DIAG);
         RC_CUDA(recon::launch_hdiag(d, w.G, w.dsum, c->stream));
@@ -691,7 +694,6 @@ struct Solve {
     const float2* coils = nullptr;  // [nc][P][Q] for the multi-coil operator
     bool coil_proj = false;         // one coil with |C| = 1: A A^H is a projection
     int variant = RECON_VARIANT_PROPOSED;  // HLR-Voxel: per-pixel weights instead of the Gram
-    double* veps = nullptr;         // HLR-Voxel: per-pixel eps state [R P Q]
 };
 
 // Autotuner of the column passes: on the first solve of a shape (P, Q, T, R, coils) the context
@@ -790,16 +792,21 @@ int solve_prepare(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t
         c->inject_barrier_fault = false;
         RC_CUDA(recon::set_barrier_error(sv->w.hpd, c->stream));
     }
+    if (c->withhold_arrival && sv->w.hpd) {
+        // host-directed lost peer: CTA 1 of the Lanczos and sweep launches of this solve leaves
+        // at its first grid barrier without arriving; the others' waits give up after 4096 polls
+        c->withhold_arrival = false;
+        sv->w.fault.withhold = 1;
+        sv->w.fault.polls = 4096;
+    }
     return autotune_tiles(c, &sv->d, sv->tw, sv->w.t, masks);
 }
 
-// HLR-Voxel: the per-pixel eps state of a solve (after solve_prepare).
+// HLR-Voxel: per-pixel weights instead of the Gram (after solve_prepare).
 int prepare_voxel(recon_ctx* c, Solve* sv) {
+    (void)c;
     sv->variant = RECON_VARIANT_HLR_VOXEL;
-    void* ptr = nullptr;
-    int rc = ensure(c, "veps", sv->d.pixels() * sizeof(double), &ptr);
-    sv->veps = reinterpret_cast<double*>(ptr);
-    return rc;
+    return RECON_OK;
 }
 
 // Status reset and x0 = A^H b (Algorithm 1 initialisation). Enqueues only.
@@ -826,10 +833,17 @@ int solve_iter(recon_ctx* c, Solve& sv, int n) {
     float2* S_new = S[n & 1];
     const float2* S_old = n == 0 ? nullptr : S[(n + 1) & 1];
     if (sv.variant == RECON_VARIANT_HLR_VOXEL) {
-        // one M x M Gram, eigendecomposition and weight per pixel; eps_r^(0) from lambda_max
+        // one M x M Gram, eigendecomposition and weight per pixel with one eps for the whole
+        // penalty: eps0 = eps0_frac * (largest lambda_max(G_r(x0)) over the pixels), then
+        // eps <- eps / gamma (Sec. III-C)
         ProfScope ps(c, RECON_PROF_S);
-        RC_CUDA(recon::launch_voxel_weight(d, sv.x, sv.prm->p, nullptr, sv.veps, n == 0 ? 1 : 2,
-                                           sv.prm->eps0_frac, sv.prm->gamma, S_new, nullptr,
+        if (n == 0) {
+            RC_CUDA(cudaMemsetAsync(w.lmax, 0, sizeof(double), c->stream));
+            RC_CUDA(recon::launch_voxel_weight(d, sv.x, sv.prm->p, nullptr, w.lmax, 1, nullptr,
+                                               nullptr, nullptr, c->stream));
+        }
+        RC_CUDA(recon::launch_eps(w.lmax, w.eps, n == 0, sv.prm->eps0_frac, sv.prm->gamma, c->stream));
+        RC_CUDA(recon::launch_voxel_weight(d, sv.x, sv.prm->p, w.eps, nullptr, 2, S_new, nullptr,
                                            nullptr, c->stream));
     } else {
         {
@@ -851,7 +865,7 @@ int solve_iter(recon_ctx* c, Solve& sv, int n) {
 // library path is used, or while launch classes are being timed.
 int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     const recon_params* prm = sv.prm;
-    const bool direct = !c->graphs || wants_eig(prm->p, prm->weight_method);
+    const bool direct = !c->graphs || wants_eig(prm->p, prm->weight_method) || sv.w.fault.withhold;
     if (direct) {
         int rc = solve_begin(c, &sv);
         for (int n = 0; n < prm->irls && !rc; ++n) rc = solve_iter(c, sv, n);
@@ -1079,7 +1093,8 @@ int direct_weight(recon_ctx* c, const Dims& d, Work& w, DirectWork& dw, double p
     } else {
         if (!eps_set) {
             if (first)
-                RC_CUDA(recon::launch_lanczos_lmax(d, w.G, w.lanc, w.lmax, w.kerr + 2 * it + 1, c->stream));
+                RC_CUDA(recon::launch_lanczos_lmax(d, w.G, w.lanc, w.lmax, w.kerr + 2 * it + 1, c->stream,
+                                                   w.fault));
             RC_CUDA(recon::launch_eps(w.lmax, w.eps, first, frac, gamma, c->stream));
         }
         RC_CUDA(recon::launch_hpd_inverse(d, w.G, w.eps, w.hpd, w.kerr + 2 * it, c->stream));
@@ -1787,12 +1802,12 @@ int recon_gram_variant(recon_ctx* c, recon_dims dd, recon_filter f, int variant,
     rc = set_device(c);
     if (rc) return rc;
     if (variant == RECON_VARIANT_HLR_VOXEL) {
-        void *S, *st;
-        rc = ensure(c, "vS", (size_t)d.npair() * d.pixels() * sizeof(float2), &S);
-        if (!rc) rc = ensure(c, "veps_g", d.pixels() * sizeof(double), &st);
+        void* st;
+        rc = ensure(c, "veps_g", sizeof(double), &st);
         if (rc) return rc;
-        RC_CUDA(recon::launch_voxel_weight(d, (const float2*)x, 0.0, nullptr, (double*)st, 1, 1.0,
-                                           1.0, (float2*)S, (double2*)G_out, nullptr, c->stream));
+        RC_CUDA(cudaMemsetAsync(st, 0, sizeof(double), c->stream));
+        RC_CUDA(recon::launch_voxel_weight(d, (const float2*)x, 0.0, nullptr, (double*)st, 1,
+                                           nullptr, (double2*)G_out, nullptr, c->stream));
         RC_CUDA(cudaStreamSynchronize(c->stream));
         return RECON_OK;
     }
@@ -1819,8 +1834,8 @@ int recon_voxel_weight(recon_ctx* c, recon_dims dd, int M, const void* x, const 
     if (rc) return rc;
     rc = set_device(c);
     if (rc) return rc;
-    RC_CUDA(recon::launch_voxel_weight(d, (const float2*)x, p, eps, nullptr, 0, 0.0, 1.0,
-                                       (float2*)S_out, nullptr, lmax_out, c->stream));
+    RC_CUDA(recon::launch_voxel_weight(d, (const float2*)x, p, eps, nullptr, 0, (float2*)S_out,
+                                       nullptr, lmax_out, c->stream));
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return RECON_OK;
 }
@@ -1972,6 +1987,7 @@ int recon_set_option(recon_ctx* c, int option, int value) {
         case RECON_OPT_AUTOTUNE: c->autotune = value != 0; return RECON_OK;
         case RECON_OPT_THREE_PASS: c->three_pass = value != 0; return RECON_OK;
         case RECON_OPT_INJECT_BARRIER_FAULT: c->inject_barrier_fault = value != 0; return RECON_OK;
+        case RECON_OPT_TEST_WITHHOLD_ARRIVAL: c->withhold_arrival = value != 0; return RECON_OK;
         default: return fail(c, RECON_EINVAL, "unknown option");
     }
 }

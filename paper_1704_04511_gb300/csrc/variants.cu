@@ -4,8 +4,11 @@
 // HLR-Voxel (Sec. II-D, Eq. MORASA-objective): one k x M Toeplitz matrix of the temporal signal
 // per pixel, T_r[j][m] = x_{j+M-1-m}(r). voxel_weight_kernel forms, per pixel and in FP64, the
 // Gram G_r = T_r^H T_r, its eigendecomposition by cyclic complex Jacobi rotations, the weight
-// H_r = U diag((lambda + eps_r)^(p/2-1)) U^H and the banded-W matrix S(r) = H_r^T (so that
-// Re <x, W x> = sum_r Tr(H_r G_r)); the CG then runs on the proposed path's kernels.
+// H_r = U diag((lambda + eps)^(p/2-1)) U^H and the banded-W matrix S(r) = H_r^T (so that
+// Re <x, W x> = sum_r Tr(H_r G_r)); the CG then runs on the proposed path's kernels. The penalty
+// sum_r ||T_r||_p is one objective with one smoothing eps, scheduled as in Sec. III-C from the
+// largest lambda_max(G_r(x0)) over the pixels (a first launch reduces it, the weight launch
+// reads the one eps).
 //
 // IRLS-direct (Sec. IV-A: Eq. x-update and Eq. weight-update without the FFT approximations):
 // the exact multi-fold Toeplitz matrix, valid in all three dimensions, of the centred k-space
@@ -26,15 +29,16 @@ constexpr int kThreads = 256;
 constexpr int kVoxThreads = 128;
 constexpr int kJacobiSweeps = 16;
 
-// Per-pixel HLR-Voxel weight. eps_mode: 0 = eps_r from eps_in; 1 = eps_r = frac * lambda_max
-// (stored to eps_state); 2 = eps_r = eps_state / gamma (stored back). G_out (may be null):
+// Per-pixel HLR-Voxel weight. eps_mode: 0 = eps_r = eps_in[px] (one eps per pixel); 1 = no
+// weight: the largest lambda_max(G_r) over the pixels goes to *lmax_max (FP64 bits, atomic max;
+// zero it first); 2 = eps_r = eps_in[0] (one eps for every pixel). G_out (may be null):
 // [npix][M][M] complex128 row-major; lmax_out (may be null): [npix].
 template <int M>
 __global__ void __launch_bounds__(kVoxThreads)
 voxel_weight_kernel(const float2* __restrict__ x, int T, size_t npix, double p,
-                    const double* __restrict__ eps_in, double* __restrict__ eps_state,
-                    int eps_mode, double frac, double gamma, float2* __restrict__ S,
-                    double2* __restrict__ G_out, double* __restrict__ lmax_out) {
+                    const double* __restrict__ eps_in, unsigned long long* __restrict__ lmax_max,
+                    int eps_mode, float2* __restrict__ S, double2* __restrict__ G_out,
+                    double* __restrict__ lmax_out) {
     const int k = T - M + 1;
     for (size_t px = (size_t)blockIdx.x * blockDim.x + threadIdx.x; px < npix;
          px += (size_t)gridDim.x * blockDim.x) {
@@ -123,16 +127,13 @@ voxel_weight_kernel(const float2* __restrict__ x, int T, size_t npix, double p,
 #pragma unroll
         for (int a = 1; a < M; ++a) lmax = fmax(lmax, A[a][a].x);
         if (lmax_out) lmax_out[px] = lmax;
-        double eps;
-        if (eps_mode == 0) {
-            eps = eps_in[px];
-        } else if (eps_mode == 1) {
-            eps = frac * lmax;
-            eps_state[px] = eps;
-        } else {
-            eps = eps_state[px] / gamma;
-            eps_state[px] = eps;
+        if (eps_mode == 1) {
+            // lambda_max >= 0 (PSD Gram): the bit patterns of non-negative doubles order as the
+            // values do
+            atomicMax(lmax_max, (unsigned long long)__double_as_longlong(fmax(lmax, 0.0)));
+            continue;
         }
+        const double eps = eps_mode == 0 ? eps_in[px] : eps_in[0];
         double alpha[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
@@ -374,17 +375,17 @@ size_t direct_rows(const Dims& d) {
 }
 
 cudaError_t launch_voxel_weight(const Dims& d, const float2* x, double p, const double* eps_in,
-                                double* eps_state, int eps_mode, double frac, double gamma,
-                                float2* S, double2* G_out, double* lmax_out, cudaStream_t st) {
+                                double* lmax_max, int eps_mode, float2* S, double2* G_out,
+                                double* lmax_out, cudaStream_t st) {
     const size_t npix = d.pixels();
     const int g = grid_for(npix * 2, 4 * num_sms() * 4);
     const int grid = (int)((npix + kVoxThreads - 1) / kVoxThreads) < g
                          ? (int)((npix + kVoxThreads - 1) / kVoxThreads) : g;
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(lmax_max);
 #define CASE(MM)                                                                               \
     case MM:                                                                                   \
-        voxel_weight_kernel<MM><<<grid, kVoxThreads, 0, st>>>(x, d.T, npix, p, eps_in,          \
-                                                              eps_state, eps_mode, frac, gamma, \
-                                                              S, G_out, lmax_out);             \
+        voxel_weight_kernel<MM><<<grid, kVoxThreads, 0, st>>>(x, d.T, npix, p, eps_in, mx,      \
+                                                              eps_mode, S, G_out, lmax_out);   \
         break;
     switch (d.M) {
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)

@@ -22,6 +22,28 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def maxrel(a, b):
+    """max |a - b| / max |b| (element-wise, complex magnitude)."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+# Per-element companion of the relative-Frobenius gates: max |a - b| <= PEAK_FACTOR * tol *
+# max |b|. An error confined to a few elements (one tail column, one boundary frame, one ragged
+# tile) is diluted in the norm of the whole array; relative to the array's peak it is not.
+PEAK_FACTOR = 10.0
+
+
+def assert_close(a, b, tol, what=""):
+    """The relative-Frobenius gate ||a - b|| / ||b|| < tol and the per-element bound
+    max |a - b| < PEAK_FACTOR * tol * max |b|."""
+    e, m = rel(a, b), maxrel(a, b)
+    assert e < tol, f"{what} relative error {e:.3e} >= {tol:.1e}"
+    assert m < PEAK_FACTOR * tol, f"{what} peak-relative element error {m:.3e} >= {PEAK_FACTOR * tol:.1e}"
+    return e, m
+
+
 def crandn(rng, *shape):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 

@@ -18,7 +18,7 @@ import pytest
 import synth
 from oracle import slr, t2fit
 
-from gpu_util import c64, crandn, lags_pairs, pairs_from_full, rel, to_dev
+from gpu_util import assert_close, c64, crandn, lags_pairs, maxrel, pairs_from_full, rel, to_dev
 
 torch = pytest.importorskip("torch")
 
@@ -49,13 +49,13 @@ def test_fft2_parity(R, T, P, Q):
     xd = to_dev(x)
     y = torch.empty_like(xd)
     recon.recon_fft2(ctx.h, xd, y, inverse=False)
-    assert rel(y.cpu().numpy(), slr.F2(x.astype(np.complex128))) < 2e-6
+    assert_close(y.cpu().numpy(), slr.F2(x.astype(np.complex128)), 2e-6)
     recon.recon_fft2(ctx.h, xd, y, inverse=True)
-    assert rel(y.cpu().numpy(), slr.F2H(x.astype(np.complex128))) < 2e-6
+    assert_close(y.cpu().numpy(), slr.F2H(x.astype(np.complex128)), 2e-6)
     # in place
     z = xd.clone()
     recon.recon_fft2(ctx.h, z, z, inverse=False)
-    assert rel(z.cpu().numpy(), slr.F2(x.astype(np.complex128))) < 2e-6
+    assert_close(z.cpu().numpy(), slr.F2(x.astype(np.complex128)), 2e-6)
 
 
 @pytest.mark.parametrize("bf16", [False, True])
@@ -73,7 +73,7 @@ def test_adjoint_parity(R, bf16):
         bd = to_dev(b)
     x = torch.empty(masks.shape, dtype=torch.complex64, device="cuda")
     recon.recon_adjoint(ctx.h, bd, to_dev(masks), x)
-    assert rel(x.cpu().numpy(), slr.AH(b_ref, masks)) < 2e-6
+    assert_close(x.cpu().numpy(), slr.AH(b_ref, masks), 2e-6)
 
 
 GRAM_CASES = [
@@ -83,6 +83,9 @@ GRAM_CASES = [
     ("tikhonov", 6, 32, 16, 1, 1, 1),
     ("M=T", 3, 16, 32, 2, 2, 3),
     ("perf", 16, 256, 256, 9, 9, 3),
+    # M = 6 with 512-point rows and 17 frames: the window sums' low parts do not fit in shared
+    # memory next to the rows, so each is rounded once before the compensated DFT
+    ("rows512-M6-T17", 17, 16, 512, 3, 3, 6),
 ]
 
 
@@ -101,8 +104,8 @@ def test_gram_parity(R, case):
     G_ref = slr.gram_fft(xr, N1, N2, M)
     G_gpu = G.cpu().numpy().T              # column-major storage
     print(f"\n[gram {case[0]}] relative Frobenius error vs FP64 = {rel(G_gpu, G_ref):.3e}")
-    assert rel(G_gpu, G_ref) < 1e-5
-    assert rel(lags.cpu().numpy(), lags_pairs(slr.gram_lags(xr, N1, N2, M))) < 1e-5
+    assert_close(G_gpu, G_ref, 1e-5)
+    assert_close(lags.cpu().numpy(), lags_pairs(slr.gram_lags(xr, N1, N2, M)), 1e-5)
 
 
 def test_gram_matches_brute_force_lifting(R):
@@ -114,7 +117,7 @@ def test_gram_matches_brute_force_lifting(R):
     s = N1 * N2 * M
     G = torch.empty((s, s), dtype=torch.complex128, device="cuda")
     recon.recon_gram(ctx.h, to_dev(x), (N1, N2, M), G, None)
-    assert rel(G.cpu().numpy().T, slr.gram_brute(x.astype(np.complex128), N1, N2, M)) < 1e-5
+    assert_close(G.cpu().numpy().T, slr.gram_brute(x.astype(np.complex128), N1, N2, M), 1e-5)
 
 
 WEIGHT_CASES = [("tiny-p0", 8, 32, 32, 5, 5, 2, 0.0), ("p0.7", 6, 16, 32, 3, 4, 3, 0.7),
@@ -147,15 +150,15 @@ def test_weight_parity(R, case, method):
         assert np.allclose(ev.cpu().numpy(), lam, rtol=0, atol=1e-11 * lam[-1])
     H, _ = slr.weight_H(G, eps, p)
     d_ref = slr.diag_sums(H, N1, N2, M)
-    assert rel(dsum.cpu().numpy(), lags_pairs(d_ref)) < 1e-8
+    assert_close(dsum.cpu().numpy(), lags_pairs(d_ref), 1e-8)
     S_ref = pairs_from_full(slr.weight_S(d_ref, P, Q))
-    assert rel(S.cpu().numpy(), S_ref) < 2e-6
+    assert_close(S.cpu().numpy(), S_ref, 2e-6)
     # explicit eps
     eps2 = recon.recon_weight(ctx.h, (T, P, Q), (N1, N2, M), Gd, 0.5 * eps, p, S, dsum, None,
                               method=meth)
     assert eps2 == 0.5 * eps
     H2, _ = slr.weight_H(G, 0.5 * eps, p)
-    assert rel(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H2, N1, N2, M))) < 1e-8
+    assert_close(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H2, N1, N2, M)), 1e-8)
 
 
 def test_weight_inverse_small_eps(R):
@@ -173,7 +176,7 @@ def test_weight_inverse_small_eps(R):
     recon.recon_weight(ctx.h, (T, P, Q), (N1, N2, M), to_dev(np.ascontiguousarray(G.T)), eps, 0.0,
                        S, dsum, None)
     H, _ = slr.weight_H(G, eps, 0.0)
-    assert rel(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H, N1, N2, M))) < 1e-9
+    assert_close(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H, N1, N2, M)), 1e-9)
 
 
 def _oracle_S(x, N1, N2, M, eps_frac=0.01, p=0.0):
@@ -223,9 +226,9 @@ def test_normal_operator_parity(R, case):
     y = torch.empty_like(to_dev(v))
     lam = 10.0 * w.lam
     recon.recon_apply_normal(ctx.h, md, (w.N1, w.N2, w.M), Sd, lam, to_dev(v), y)
-    assert rel(y.cpu().numpy(), slr.normal_op(vr, masks, S_full, lam)) < 1e-5
+    assert_close(y.cpu().numpy(), slr.normal_op(vr, masks, S_full, lam), 1e-5, "normal operator")
     recon.recon_apply_w(ctx.h, (w.N1, w.N2, w.M), Sd, to_dev(v), y)
-    assert rel(y.cpu().numpy(), slr.apply_W(vr, S_full)) < 1e-5
+    assert_close(y.cpu().numpy(), slr.apply_W(vr, S_full), 1e-5, "W")
 
 
 @pytest.mark.parametrize("name", ["tiny_32x32x8", "perf_256x256x16"])
@@ -283,7 +286,7 @@ def test_cg_block_parity(R):
     md = to_dev(masks)
     hist = recon.recon_cg(ctx.h, md, (w.N1, w.N2, w.M), None, Sd1, w.lam, xd, rd, w.n_cg)
     x_ref, r_ref, h_ref = _oracle_cg_block(x0r, None, masks, None, S1, w.lam, w.n_cg)
-    assert rel(xd.cpu().numpy(), x_ref) < 1e-5
+    assert_close(xd.cpu().numpy(), x_ref, 1e-5)
     assert np.allclose(hist, h_ref, rtol=1e-3)
     # second block: residual carried with a new weight
     x1 = xd.cpu().numpy().astype(np.complex128)
@@ -292,7 +295,7 @@ def test_cg_block_parity(R):
     r1 = rd.cpu().numpy().astype(np.complex128)
     recon.recon_cg(ctx.h, md, (w.N1, w.N2, w.M), Sd1, Sd2, w.lam, xd, rd, w.n_cg)
     x_ref2, _, _ = _oracle_cg_block(x1, r1, masks, S1, S2, w.lam, w.n_cg)
-    assert rel(xd.cpu().numpy(), x_ref2) < 1e-5
+    assert_close(xd.cpu().numpy(), x_ref2, 1e-5)
 
 
 def _solve_gpu(recon, ctx, w, prob, irls=None, cg=None, method=0):
@@ -312,9 +315,9 @@ def _check_solve(x_gpu, x_ref, prob, w, tag=""):
     t2_gpu = t2fit.fit_t2(x_gpu, w.times_ms, fg)
     t2_err = t2fit.t2_rel_l2(t2_ref, t2_gpu)
     print(f"\n[{w.name} irls={w.n_irls} cg={w.n_cg} p={w.p}{tag}] |x_gpu - x_oracle| / |x_oracle| = "
-          f"{rel(x_gpu, x_ref):.3e}; NRMSE gpu {nrmse_gpu:.6f} oracle {nrmse_ref:.6f}; "
-          f"T2 map rel. L2 {t2_err:.3e}")
-    assert rel(x_gpu, x_ref) < 1e-4
+          f"{rel(x_gpu, x_ref):.3e} (peak-relative element {maxrel(x_gpu, x_ref):.3e}); NRMSE gpu "
+          f"{nrmse_gpu:.6f} oracle {nrmse_ref:.6f}; T2 map rel. L2 {t2_err:.3e}")
+    assert_close(x_gpu, x_ref, 1e-4, "image")
     assert abs(nrmse_gpu - nrmse_ref) < 1e-4
     assert t2_err < 5e-3
 
@@ -356,7 +359,7 @@ def test_solve_irls0_is_adjoint(R):
     recon, ctx = R
     w, prob = _problem("tiny_32x32x8")
     x_gpu = _solve_gpu(recon, ctx, w, prob, irls=0)
-    assert rel(x_gpu, slr.AH(prob["kspace"], prob["masks"])) < 2e-6
+    assert_close(x_gpu, slr.AH(prob["kspace"], prob["masks"]), 2e-6)
 
 
 def test_solve_cg0_refused(R):
@@ -464,6 +467,57 @@ def test_barrier_fault_injection(R):
     again = torch.empty_like(ref)
     recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, again)
     assert torch.equal(again.cpu(), ref.cpu())
+
+
+def test_bounded_wait_runs_out(R):
+    """Failure detection with the bounded wait really running out (host-directed, no device
+    fault): CTA 1 of the Lanczos and sweep launches leaves at its first grid barrier without
+    arriving, the other CTAs' waits give up after 4096 polls, the kernels report it, the solve
+    returns RECON_ETIMEOUT within seconds, and the next solve matches a clean one bitwise -- on
+    the graph path and on direct launches."""
+    import time
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8", n_irls=3, n_cg=4)
+    b = to_dev(c64(prob["kspace"]))
+    m = to_dev(prob["masks"])
+    filt = (w.N1, w.N2, w.M)
+    for graphs in (1, 0):
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_GRAPHS, graphs)
+        ref = torch.empty(prob["masks"].shape, dtype=torch.complex64, device="cuda")
+        recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, ref)
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_TEST_WITHHOLD_ARRIVAL, 1)
+        out = torch.empty_like(ref)
+        t0 = time.perf_counter()
+        with pytest.raises(recon.ReconError) as e:
+            recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+        dt = time.perf_counter() - t0
+        assert e.value.code == recon.RECON_ETIMEOUT
+        assert dt < 5.0, dt
+        again = torch.empty_like(ref)
+        recon.recon_solve(ctx.h, b, m, filt, w.lam, w.p, w.n_irls, w.n_cg, again)
+        assert torch.equal(again.cpu(), ref.cpu())
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_GRAPHS, 1)
+
+
+def test_nonfinite_kspace_reports_enumeric(R):
+    """A NaN in the k-space (a sampled entry) propagates through x0, the Gram, the weight and the
+    CG; the solve reports RECON_ENUMERIC instead of a result, and the context stays usable."""
+    recon, ctx = R
+    w, prob = _problem("tiny_32x32x8", n_irls=2, n_cg=3)
+    k = c64(prob["kspace"]).copy()
+    t, r1, r2 = np.argwhere(prob["masks"] != 0)[5]
+    k[t, r1, r2] = np.nan
+    m = to_dev(prob["masks"])
+    filt = (w.N1, w.N2, w.M)
+    out = torch.empty(prob["masks"].shape, dtype=torch.complex64, device="cuda")
+    with pytest.raises(recon.ReconError) as e:
+        recon.recon_solve(ctx.h, to_dev(k), m, filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+    assert e.value.code == recon.RECON_ENUMERIC
+    recon.recon_solve(ctx.h, to_dev(c64(prob["kspace"])), m, filt, w.lam, w.p, w.n_irls, w.n_cg,
+                      out)
+    x_ref = slr.irls(c64(prob["kspace"]).astype(np.complex128), prob["masks"], w.N1, w.N2, w.M,
+                     w.lam, w.p, w.n_irls, w.n_cg)
+    assert_close(out.cpu().numpy(), x_ref, 1e-4)
 
 
 SIZE_CASES = [("192x192x6", dict(P=192, Q=192, T=6, N1=5, N2=5, M=2)),

@@ -98,6 +98,21 @@ def test_voxel_sum_of_squares_identity_and_planted_transpose(p):
     assert abs(np.vdot(x, slr.apply_W(x, S_bad)).real - pen) > 1e-6 * pen
 
 
+def test_voxel_initial_eps_is_one_value_from_the_largest_pixel_singular_value():
+    """eps^(0) of HLR-Voxel is one number for the whole penalty: eps0_frac times the largest
+    lambda_max(G_r) over the pixels, i.e. the square of the largest singular value of any
+    pixel's explicit k x M Toeplitz matrix (Sec. III-C schedule)."""
+    rng = np.random.default_rng(11)
+    T, P, Q, M = 7, 3, 5, 3
+    x = _crandn(rng, T, P, Q)
+    x[:, 1, 2] *= 4.0                      # one bright pixel sets the value
+    smax = max(np.linalg.svd(V.voxel_toeplitz(x, M, (r1, r2)), compute_uv=False)[0]
+               for r1 in range(P) for r2 in range(Q))
+    eps = V.voxel_initial_eps(x, M, 0.01)
+    assert np.ndim(eps) == 0
+    assert abs(eps - 0.01 * smax ** 2) <= 1e-12 * eps
+
+
 def test_voxel_weight_closed_form_p0():
     rng = np.random.default_rng(6)
     Gv = np.stack([_hermitian_pd(rng, 3) for _ in range(6)]).reshape(2, 3, 3, 3)

@@ -4,8 +4,10 @@ A reconstruction service with a device-memory plan fixed at start-up, or a progr
 GPU that must avoid the device-wide synchronisation of cudaMalloc / cudaFree, cannot use the
 context's growing workspace; recon_gram_static keeps its scratch in a fixed array inside the
 library instead. Through the C ABI, two calls in a row (different problems, then the first one
-again) must each reproduce the allocating entry point's G and lags within the Gram tolerance of
-the parity tests (1e-5 relative Frobenius). Runs alone in a fresh process or after the others.
+again, that one on a non-blocking stream) must each reproduce the allocating entry point's G and
+lags within the Gram tolerance of the parity tests (1e-5 relative Frobenius), and once the first
+calls have loaded the code and committed the array, further calls must leave the device's free
+memory unchanged. Runs alone in a fresh process or after the others.
 """
 
 import numpy as np
@@ -22,7 +24,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def _gram_both(recon, ctx, x, filt):
+def _gram_both(recon, ctx, x, filt, stream=None):
     N1, N2, M = filt
     s, npair = N1 * N2 * M, M * (M + 1) // 2
     shape_l = (npair, 2 * N1 - 1, 2 * N2 - 1)
@@ -31,7 +33,9 @@ def _gram_both(recon, ctx, x, filt):
     G_st = torch.full((s, s), float("nan"), dtype=torch.complex128, device="cuda")
     l_st = torch.full(shape_l, float("nan"), dtype=torch.complex128, device="cuda")
     recon.recon_gram(ctx.h, x, filt, G_ref, l_ref)
-    recon.recon_gram_static(x, filt, G_st, l_st)
+    torch.cuda.synchronize()
+    recon.recon_gram_static(x, filt, G_st, l_st,
+                            cuda_stream=stream.cuda_stream if stream is not None else None)
     return (G_st.cpu().numpy(), G_ref.cpu().numpy(), l_st.cpu().numpy(), l_ref.cpu().numpy())
 
 
@@ -47,11 +51,27 @@ def test_gram_static_matches_gram_on_consecutive_calls():
         for (T, P, Q), filt in cases:
             x = (rng.standard_normal((T, P, Q)) + 1j * rng.standard_normal((T, P, Q))).astype(np.complex64)
             xs.append((torch.from_numpy(x).cuda(), filt))
-        for x, filt in xs + xs[:1]:
-            G_st, G_ref, l_st, l_ref = _gram_both(recon, ctx, x, filt)
+        # two calls in a row (different problems), then the first one again on a non-blocking
+        # stream of its own
+        side = torch.cuda.Stream(priority=0)
+        for i, (x, filt) in enumerate(xs + xs[:1]):
+            G_st, G_ref, l_st, l_ref = _gram_both(recon, ctx, x, filt, side if i == 2 else None)
             assert np.isfinite(G_st).all() and np.isfinite(l_st).all()
             assert _rel(G_st, G_ref) < GRAM_TOL
             assert _rel(l_st, l_ref) < GRAM_TOL
+        # after the warm-up calls above, calls allocate nothing: free device memory is the same
+        # before and after two further calls (outputs allocated beforehand)
+        outs = []
+        for x, (N1, N2, M) in xs:
+            s = N1 * N2 * M
+            outs.append((x, (N1, N2, M), torch.empty((s, s), dtype=torch.complex128, device="cuda")))
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        for x, filt, G in outs:
+            recon.recon_gram_static(x, filt, G)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0, free1)
         # a problem whose scratch exceeds the fixed array is refused with a clear message
         # (P rows x 21 pairs x 31 column lags of complex128 = 5.3 MB)
         x = torch.zeros((8, 512, 32), dtype=torch.complex64, device="cuda")
