@@ -25,7 +25,7 @@
  *    coil, S and G arrays start on a 16-byte boundary (every cudaMalloc / PyTorch allocation
  *    does; a view starting at an odd complex64 element does not): RECON_EINVAL otherwise.
  *  - Supported sizes: P, Q in {16, 32, 64, 128, 192, 256, 512}; 1 <= M <= 6, M <= T;
- *    1 <= N1 <= P, 1 <= N2 <= Q; T * Q <= 8738 (fused row/W pass).
+ *    1 <= N1 <= P, 1 <= N2 <= Q; T * Q <= 8533 (fused row/W pass).
  *  - Return value: RECON_OK (0) or a negative RECON_E* code; recon_last_error() describes it.
  *    A failed call never reports partial output as valid.
  */
@@ -163,6 +163,15 @@ int recon_poll(recon_ctx* c, int ticket, int* done);
  *   returns RECON_ETIMEOUT and re-arms the barriers, and the following solve runs normally. That
  *   solve is issued as direct launches (no graph). One-shot (cleared when used). */
 #define RECON_OPT_TEST_WITHHOLD_ARRIVAL 6
+/* RECON_OPT_BATCH_GROUP (value g, 0 <= g <= RECON_MAX_BATCH; default 0): how recon_solve_batch runs
+ *   the FP64 weight of its solves on the sweep path (p = 0, RECON_WEIGHT_AUTO, graphs on).
+ *   0: every solve has its own graph and stream, its weight launches its own (independent slots).
+ *   g >= 1: the whole batch is one CUDA graph; every IRLS iteration the solves of each group of g
+ *   consecutive slots join for ONE Lanczos (first iteration), one eps and ONE sweep launch that
+ *   serve all of them (one grid barrier per pivot step for the group), then continue on their
+ *   own streams; with several groups the groups' weight launches take turns, so each overlaps
+ *   the other groups' CG. Results are bitwise identical to solving each problem alone. */
+#define RECON_OPT_BATCH_GROUP 7
 int recon_set_option(recon_ctx* c, int option, int value);
 
 
@@ -180,12 +189,14 @@ int recon_fft2(recon_ctx* c, recon_dims d, const void* x, void* y, int inverse);
  * Eq. P-ij-modified): G_out, s x s complex128 column-major (both triangles written);
  * lags_out (may be NULL): npair x (2N1-1) x (2N2-1) complex128, pair (a <= b) at index
  * a(2M-a+1)/2 + (b-a), lag (d1, d2) at offset (N1-1, N2-1):
- * lag_ab[d] = sum_r sum_{j<k} conj(x_{j+M-1-a}(r)) x_{j+M-1-b}(r) e^{-2 pi i (d1 r1/P + d2 r2/Q)}. */
+ * lag_ab[d] = sum_r sum_{j<k} conj(x_{j+M-1-a}(r)) x_{j+M-1-b}(r) e^{-2 pi i (d1 r1/P + d2 r2/Q)}.
+ * G is exactly Hermitian: lag_aa[-d] is written as conj(lag_aa[d]) and lag_aa[0] is real. */
 int recon_gram(recon_ctx* c, recon_dims d, recon_filter f, const void* x, void* G_out,
                void* lags_out);
 
 /* Weight step (Sec. III-B, Eq. weight-update) on G_in (s x s complex128, column-major,
- * Hermitian positive semi-definite; not modified), all in FP64:
+ * Hermitian positive semi-definite; not modified; the inverse and the eigendecomposition read its
+ * lower triangle, the diagonal as real), all in FP64:
  * H = (G + eps I)^(p/2-1) -- by the eigendecomposition H = U diag((lambda+eps)^(p/2-1)) U^H, or
  * for p = 0 with method RECON_WEIGHT_AUTO by the Hermitian sweep inverse (G + eps I)^-1 --,
  * then the summed diagonals d_ab[delta] = sum_{l-l'=delta} H[(l',b),(l,a)] and the per-pixel

@@ -141,15 +141,23 @@ __global__ void gram_fill_kernel(const double2* __restrict__ Y, int P, int N1, i
     const int i1 = rem / L2, i2 = rem % L2;
     const int d1 = i1 - (N1 - 1), d2 = i2 - (N2 - 1);
     const int d1m = (d1 + P) % P;
+    int a = 0, e = pr;
+    while (e >= M - a) { e -= M - a; ++a; }
+    const int b = a + e;
+    // a frame with itself: lag_aa[-d] = conj(lag_aa[d]) exactly, so the warp of the lag in the
+    // non-negative half (d1 > 0, or d1 = 0 and d2 >= 0) writes both and G is exactly Hermitian
+    const bool self = a == b;
+    if (self && (d1 < 0 || (d1 == 0 && d2 < 0))) return;
     const double2* yrow = Y + ((size_t)pr * L2 + i2) * P;
     double2 v = make_double2(0.0, 0.0);
     for (int r1 = lane; r1 < P; r1 += 32) v = zfma(yrow[r1], twPd[(d1m * r1) % P], v);
     v.x = warp_sum(v.x);
     v.y = warp_sum(v.y);
-    if (lags && lane == 0) lags[o] = v;
-    int a = 0, e = pr;
-    while (e >= M - a) { e -= M - a; ++a; }
-    const int b = a + e;
+    if (self && d1 == 0 && d2 == 0) v.y = 0.0;  // sum of |x|^2
+    if (lags && lane == 0) {
+        lags[o] = v;
+        if (self) lags[(size_t)pr * L1 * L2 + (size_t)(L1 - 1 - i1) * L2 + (L2 - 1 - i2)] = zconj(v);
+    }
     const int lo1 = max(0, -d1), hi1 = min(N1, N1 - d1);
     const int lo2 = max(0, -d2), hi2 = min(N2, N2 - d2);
     const int n2 = hi2 - lo2, cnt = (hi1 - lo1) * n2;
@@ -159,7 +167,7 @@ __global__ void gram_fill_kernel(const double2* __restrict__ Y, int P, int N1, i
         const size_t i = ((size_t)a * N1 + l1) * N2 + l2;
         const size_t j = ((size_t)b * N1 + lp1) * N2 + lp2;
         G[i + j * s] = v;
-        if (a != b) G[j + i * s] = zconj(v);
+        if (i != j) G[j + i * s] = zconj(v);
     }
 }
 
@@ -199,15 +207,24 @@ __global__ void gram_fill3_kernel(const double2* __restrict__ Z, int R, int N1, 
     const int i2 = o % L2, i1 = (o / L2) % L1, i3 = (o / (L2 * L1)) % L3, pr = o / (L2 * L1 * L3);
     const int d1 = i1 - (N1 - 1), d2 = i2 - (N2 - 1), d3 = i3 - (N3 - 1);
     const int d3m = (d3 % R + R) % R;
+    int a = 0, e = pr;
+    while (e >= M - a) { e -= M - a; ++a; }
+    const int b = a + e;
+    // a frame with itself: only the non-negative half of the lags (d3 > 0, or d3 = 0 and
+    // (d1, d2) non-negative as in 2-D) is summed; it writes the mirrored lag as its conjugate
+    const bool self = a == b;
+    if (self && (d3 < 0 || (d3 == 0 && (d1 < 0 || (d1 == 0 && d2 < 0))))) return;
     const double2* zrow = Z + (((size_t)pr * L2 + i2) * L1 + i1) * R;
     double2 v = make_double2(0.0, 0.0);
     for (int r3 = lane; r3 < R; r3 += 32) v = zfma(zrow[r3], twRd[(d3m * r3) % R], v);
     v.x = warp_sum(v.x);
     v.y = warp_sum(v.y);
-    if (lags && lane == 0) lags[o] = v;
-    int a = 0, e = pr;
-    while (e >= M - a) { e -= M - a; ++a; }
-    const int b = a + e;
+    if (self && d3 == 0 && d1 == 0 && d2 == 0) v.y = 0.0;
+    if (lags && lane == 0) {
+        lags[o] = v;
+        if (self)
+            lags[(((size_t)pr * L3 + (L3 - 1 - i3)) * L1 + (L1 - 1 - i1)) * L2 + (L2 - 1 - i2)] = zconj(v);
+    }
     const int lo1 = max(0, -d1), hi1 = min(N1, N1 - d1);
     const int lo2 = max(0, -d2), hi2 = min(N2, N2 - d2);
     const int lo3 = max(0, -d3), hi3 = min(N3, N3 - d3);
@@ -217,7 +234,7 @@ __global__ void gram_fill3_kernel(const double2* __restrict__ Z, int R, int N1, 
         const size_t i = (((size_t)a * N3 + lp3 + d3) * N1 + lp1 + d1) * N2 + lp2 + d2;
         const size_t j = (((size_t)b * N3 + lp3) * N1 + lp1) * N2 + lp2;
         G[i + j * s] = v;
-        if (a != b) G[j + i * s] = zconj(v);
+        if (i != j) G[j + i * s] = zconj(v);
     }
 }
 

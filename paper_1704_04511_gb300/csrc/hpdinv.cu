@@ -106,24 +106,24 @@ RECON_DEV bool grid_barrier(GridBar* gb, const CoopFault& fault) {
     return ok_s != 0;
 }
 
-// Status of a cooperative launch for the host: thread 0 of CTA 0 writes 0 when the kernel
-// completed, 1 when a barrier gave up (every CTA then fails its next barrier and returns).
-RECON_DEV void report(int* err_out, int v) {
-    if (err_out && blockIdx.x == 0 && threadIdx.x == 0) *err_out = v;
-}
 
 // Synchronise the 64 threads of tile group g (named barrier g + 1; 0 is __syncthreads).
 RECON_DEV void group_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kTileT) : "memory");
 }
 
-// 1 / a for a pivot of a positive-definite matrix: the FP64 approximate reciprocal instruction
-// as the seed, then one cubic Newton-Raphson step r (1 + e + e^2), e = 1 - a r (the error goes
-// from e to e^3). Three dependent FMAs after the seed; no range test (pivots are positive,
-// normal numbers).
+// 1 / a for a pivot of a positive-definite matrix: the correctly rounded FP32 reciprocal as the
+// seed (relative error <= 2^-24), then one cubic Newton-Raphson step r (1 + e + e^2),
+// e = 1 - a r, which takes the error from e to e^3 <= 2^-72, below FP64 rounding. Three
+// dependent FP64 FMAs after the seed. Outside the FP32 exponent range the division is used (the
+// branch is uniform: every thread of the tile computes the same pivot). A coarser seed is not
+// enough: each pivot's relative error reaches the inverse amplified by about the square of the
+// condition number, which the weights of late IRLS iterations (eps down to ~1e-6 lambda_max)
+// make large.
 RECON_DEV double rcp_pivot(double a) {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+    const double aa = fabs(a);
+    if (!(aa > 1e-30 && aa < 1e30)) return 1.0 / a;
+    const double r = (double)__frcp_rn((float)a);
     const double e = fma(-a, r, 1.0);
     return fma(r, fma(e, e, e), r);
 }
@@ -157,8 +157,15 @@ RECON_DEV void tile_inverse(double2* T0, double2* T1, double2* out) {
         a = b;
         b = sw;
     }
-    const double2 v = a[i + j * kB];
-    out[i + j * kB] = make_double2(-v.x, -v.y);
+    // The Hermitian part of the result: the tile (a Schur complement updated in floating point)
+    // and its computed inverse are Hermitian only up to rounding, while the sweep keeps the lower
+    // tiles alone and reads an upper block as the conjugate transpose of the lower one. An inverse
+    // that is not exactly Hermitian would make the two halves disagree by its anti-Hermitian part
+    // times the block, an inconsistency that late pivots (inverses of nearly singular Schur
+    // complements) amplify step after step; its Hermitian part keeps them consistent and is as
+    // accurate.
+    const double2 v = a[i + j * kB], w = a[j + i * kB];
+    out[i + j * kB] = make_double2(-0.5 * (v.x + w.x), -0.5 * (v.y - w.y));
 }
 
 // Lower tile (I, J), J <= I: offset of its 64 elements, element (i, j) at i + 8 j.
@@ -179,6 +186,33 @@ RECON_DEV void tile_ij(int t, int* I, int* J) {
     *J = t - r * (r + 1) / 2;
 }
 
+// One matrix of a batched sweep launch (passed by value in the kernel parameters).
+struct SweepMat {
+    double2* G;            // s x s column-major; H = (G + eps I)^-1 written over it
+    const double* eps;     // device scalar
+    double2 *A0, *A1;      // lower tiles, ping-pong
+    double2* Dbuf;         // two pivot inverses
+    int* err_out;          // status word (may be null)
+    int s, nt;
+};
+struct SweepBatch {
+    int n, nt_max;
+    SweepMat m[kMaxHpdBatch];
+};
+
+// Status of the launch for the host, per matrix (thread 0 of CTA 0): 0 when the kernel completed,
+// 1 when a barrier gave up (every CTA then fails its next barrier and returns).
+RECON_DEV void report_batch(const SweepBatch& bt, int v) {
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int b = 0; b < bt.n; ++b)
+            if (bt.m[b].err_out) *bt.m[b].err_out = v;
+}
+
+// Failure status of a batched Lanczos launch (thread 0 of CTA 0, every matrix); on success each
+// matrix's CTA writes 0 after its multisection.
+struct LancBatch;
+RECON_DEV void report_lanc(const LancBatch& bt, int v);
+
 struct SweepSmem {
     double2 D[kTileT];            // D_K
     double2 P[kTileT];            // A_IK of the current item
@@ -191,10 +225,11 @@ struct SweepSmem {
 };
 
 // Work items of the non-pivot CTAs: chunks of up to four tiles (I, J0 .. J0 + nj - 1) of one tile
-// row, J0 + nj <= I, and the diagonal tiles as items (I, I, 1). They are listed largest first
-// (full chunks, then chunks of 3, 2, 1 tiles, then diagonal tiles) and dealt to the CTAs
-// 1 .. grid-1 in a snake order (forward, backward, ...), which balances the FP64 work per SM.
-// Every CTA runs this enumeration and keeps its own items.
+// row, J0 + nj <= I, and the diagonal tiles as items (I, I, 1), for every matrix b of the launch.
+// They are listed largest first (full chunks of every matrix, then chunks of 3, 2, 1 tiles, then
+// diagonal tiles) and dealt to the worker CTAs in a snake order (forward, backward, ...), which
+// balances the FP64 work per SM. Every CTA runs this enumeration and keeps its own items.
+// Item code: (b << 26) | (I << 16) | (J0 << 4) | nj.
 struct ItemDeal {
     int workers, me, idx, n, cap;
     int* out;
@@ -210,16 +245,22 @@ RECON_HD void deal_item(ItemDeal& d, int code) {
     ++d.idx;
 }
 
-// Items of worker `me` (0-based among the CTAs 1 .. grid-1) into out[0 .. cap); returns their
-// count. With me < 0 it returns the largest count of any worker (host capacity check).
-RECON_HD int sweep_items(int nt, int workers, int me, int* out, int cap) {
+RECON_HD int item_code(int b, int I, int J0, int nj) { return (b << 26) | (I << 16) | (J0 << 4) | nj; }
+
+// Items of worker `me` (0-based among the worker CTAs) into out[0 .. cap); returns their count.
+// nts[b]: tile rows of matrix b. With me < 0 it returns the largest count of any worker (host
+// capacity check).
+RECON_HD int sweep_items(const int* nts, int nmat, int workers, int me, int* out, int cap) {
     ItemDeal d{workers, me, 0, 0, cap, out};
-    for (int I = 1; I < nt; ++I)
-        for (int J0 = 0; J0 + kChunk <= I; J0 += kChunk) deal_item(d, (I << 16) | (J0 << 4) | kChunk);
+    for (int b = 0; b < nmat; ++b)
+        for (int I = 1; I < nts[b]; ++I)
+            for (int J0 = 0; J0 + kChunk <= I; J0 += kChunk) deal_item(d, item_code(b, I, J0, kChunk));
     for (int nj = kChunk - 1; nj >= 1; --nj)
-        for (int I = 1; I < nt; ++I)
-            if (I % kChunk == nj) deal_item(d, (I << 16) | ((I - nj) << 4) | nj);
-    for (int I = 0; I < nt; ++I) deal_item(d, (I << 16) | (I << 4) | 1);
+        for (int b = 0; b < nmat; ++b)
+            for (int I = 1; I < nts[b]; ++I)
+                if (I % kChunk == nj) deal_item(d, item_code(b, I, I - nj, nj));
+    for (int b = 0; b < nmat; ++b)
+        for (int I = 0; I < nts[b]; ++I) deal_item(d, item_code(b, I, I, 1));
     return me < 0 ? (d.idx + workers - 1) / workers : d.n;
 }
 
@@ -232,7 +273,7 @@ RECON_DEV void sweep_item(SweepSmem& sm, int code, int K, int nt, const double2*
                           double2* Aout, const double2* DK) {
     const int tid = threadIdx.x, g = tid / kTileT, e = tid % kTileT;
     const int i = e % kB, j = e / kB;
-    const int I = code >> 16, J0 = (code >> 4) & 0xfff, nj = code & 15;
+    const int I = (code >> 16) & 0x3ff, J0 = (code >> 4) & 0xfff, nj = code & 15;
     const bool diag = (J0 == I);
     if (diag && I == K + 1) return;
     if (diag && I == K) {
@@ -315,66 +356,89 @@ RECON_DEV void sweep_pivot(SweepSmem& sm, int K, const double2* Ain, const doubl
     }
 }
 
+// One cooperative launch sweeps every matrix of the batch: one grid barrier per pivot step serves
+// all of them (the largest tile count sets the number of steps; a matrix with fewer tiles is done
+// earlier and its CTAs skip its later steps). CTA b (< n) carries matrix b's pivot chain, the
+// other CTAs share the work items of all matrices. Every tile is computed by the same arithmetic
+// as in a launch of its matrix alone, so the results do not depend on the batch.
 __global__ void __launch_bounds__(kThreads, 2)
-hpd_sweep_kernel(double2* G, int s, const double* __restrict__ eps_p, int nt,
-                 double2* __restrict__ A0, double2* __restrict__ A1, double2* __restrict__ Dbuf,
-                 GridBar* gb, int* err_out, CoopFault fault) {
+hpd_sweep_kernel(SweepBatch bt, GridBar* gb, CoopFault fault) {
     __shared__ SweepSmem sm;
     const int tid = threadIdx.x;
     const int g = tid / kTileT, e = tid % kTileT;
     const int i = e % kB, j = e / kB;
-    const int nlt = nt * (nt + 1) / 2;
-    const double eps = eps_p[0];
+    const int n = bt.n;
 
     if (tid == 0) {
-        sm.nitem = blockIdx.x == 0 ? 0
-                                   : sweep_items(nt, gridDim.x - 1, blockIdx.x - 1, sm.item, kMaxItems);
+        int nts[kMaxHpdBatch];
+        for (int b = 0; b < n; ++b) nts[b] = bt.m[b].nt;
+        sm.nitem = (int)blockIdx.x < n
+                       ? 0 : sweep_items(nts, n, gridDim.x - n, blockIdx.x - n, sm.item, kMaxItems);
         if (sm.nitem > kMaxItems) sm.nitem = kMaxItems;  // the host refuses such sizes
     }
-    // A0 = pad(G + eps I), lower tiles; padding is the identity
-    for (int t = blockIdx.x * kGroups + g; t < nlt; t += gridDim.x * kGroups) {
-        int I, J;
-        tile_ij(t, &I, &J);
-        const int r = I * kB + i, c = J * kB + j;
-        double2 v = make_double2(r == c ? 1.0 : 0.0, 0.0);
-        if (r < s && c < s) {
-            v = G[r + (size_t)c * s];
-            if (r == c) v.x += eps;
+    // A0 = pad(G + eps I), lower tiles; padding is the identity. Only the lower triangle of G is
+    // read (the upper half of a diagonal tile is taken as the conjugate of the lower, the
+    // diagonal as real), as the FP64 eigensolver reads it: the sweep assumes an exactly Hermitian
+    // matrix, and a G whose halves differ by rounding would make its pivots' inverses disagree
+    // with the mirrored off-diagonal tiles by far more than rounding at large condition numbers.
+    for (int b = 0; b < n; ++b) {
+        const SweepMat& mt = bt.m[b];
+        const int nlt = mt.nt * (mt.nt + 1) / 2, s = mt.s;
+        const double eps = mt.eps[0];
+        for (int t = blockIdx.x * kGroups + g; t < nlt; t += gridDim.x * kGroups) {
+            int I, J;
+            tile_ij(t, &I, &J);
+            const int r = I * kB + i, c = J * kB + j;
+            double2 v = make_double2(r == c ? 1.0 : 0.0, 0.0);
+            if (r < s && c < s) {
+                v = r >= c ? mt.G[r + (size_t)c * s] : zconj(mt.G[c + (size_t)r * s]);
+                if (r == c) v = make_double2(v.x + eps, 0.0);
+            }
+            mt.A0[tile_off(I, J) + e] = v;
         }
-        A0[tile_off(I, J) + e] = v;
     }
-    if (!grid_barrier(gb, fault)) return report(err_out, 1);
-    if (blockIdx.x == 0 && g == 0) {  // D_0
-        sm.X[e] = A0[e];
+    if (!grid_barrier(gb, fault)) return report_batch(bt, 1);
+    if ((int)blockIdx.x < n && g == 0) {  // D_0 of matrix blockIdx.x
+        const SweepMat& mt = bt.m[blockIdx.x];
+        sm.X[e] = mt.A0[e];
         group_sync(0);
-        tile_inverse(sm.X, sm.T1, Dbuf);
+        tile_inverse(sm.X, sm.T1, mt.Dbuf);
     }
-    if (!grid_barrier(gb, fault)) return report(err_out, 1);
+    if (!grid_barrier(gb, fault)) return report_batch(bt, 1);
 
-    for (int K = 0; K < nt; ++K) {
-        const double2* Ain = (K & 1) ? A1 : A0;
-        double2* Aout = (K & 1) ? A0 : A1;
-        const double2* DK = Dbuf + (K & 1) * kTileT;
-        double2* Dnext = Dbuf + ((K + 1) & 1) * kTileT;
-        if (blockIdx.x == 0) {
-            if (K + 1 < nt) sweep_pivot(sm, K, Ain, DK, Dnext);
+    for (int K = 0; K < bt.nt_max; ++K) {
+        if ((int)blockIdx.x < n) {
+            const SweepMat& mt = bt.m[blockIdx.x];
+            if (K + 1 < mt.nt)
+                sweep_pivot(sm, K, (K & 1) ? mt.A1 : mt.A0, mt.Dbuf + (K & 1) * kTileT,
+                            mt.Dbuf + ((K + 1) & 1) * kTileT);
         } else {
-            for (int it = 0; it < sm.nitem; ++it) sweep_item(sm, sm.item[it], K, nt, Ain, Aout, DK);
+            for (int it = 0; it < sm.nitem; ++it) {
+                const int code = sm.item[it];
+                const SweepMat& mt = bt.m[code >> 26];
+                if (K < mt.nt)
+                    sweep_item(sm, code, K, mt.nt, (K & 1) ? mt.A1 : mt.A0, (K & 1) ? mt.A0 : mt.A1,
+                               mt.Dbuf + (K & 1) * kTileT);
+            }
         }
-        if (!grid_barrier(gb, fault)) return report(err_out, 1);
+        if (!grid_barrier(gb, fault)) return report_batch(bt, 1);
     }
     // H = -A (s x s, full, column-major) written over G
-    const double2* Af = (nt & 1) ? A1 : A0;
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + tid;
     const size_t gstride = (size_t)gridDim.x * blockDim.x;
-    for (size_t idx = gtid; idx < (size_t)s * s; idx += gstride) {
-        const int r = (int)(idx % s), c = (int)(idx / s);
-        const int I = r / kB, J = c / kB;
-        const double2 v = (I >= J) ? Af[tile_off(I, J) + r % kB + kB * (c % kB)]
-                                   : zconj(Af[tile_off(J, I) + c % kB + kB * (r % kB)]);
-        G[idx] = make_double2(-v.x, -v.y);
+    for (int b = 0; b < n; ++b) {
+        const SweepMat& mt = bt.m[b];
+        const int s = mt.s;
+        const double2* Af = (mt.nt & 1) ? mt.A1 : mt.A0;
+        for (size_t idx = gtid; idx < (size_t)s * s; idx += gstride) {
+            // from the lower triangle (within a diagonal tile too): H exactly Hermitian
+            const int r = (int)(idx % s), c = (int)(idx / s);
+            const double2 v = (r >= c) ? Af[tile_off(r / kB, c / kB) + r % kB + kB * (c % kB)]
+                                       : zconj(Af[tile_off(c / kB, r / kB) + c % kB + kB * (r % kB)]);
+            mt.G[idx] = make_double2(-v.x, r == c ? 0.0 : -v.y);
+        }
     }
-    report(err_out, 0);
+    report_batch(bt, 0);
 }
 
 // d_ab[delta] = sum_{l - l' = delta} H[(l', b), (l, a)] from H (s x s column-major); taps
@@ -410,120 +474,168 @@ __global__ void hdiag_kernel(const double2* __restrict__ H, int N1, int N2, int 
 }
 
 // ---- Lanczos estimate of lambda_max(G), FP64, m steps, then multisection on the tridiagonal.
+// One matrix of a batched Lanczos launch (by value in the kernel parameters).
+struct LancMat {
+    const double2* G;      // s x s column-major, Hermitian
+    double2 *u, *vprev, *y;  // Lanczos vectors and the current G v (s each)
+    double* part;          // 4 x grid partial sums (alpha, beta; ping-pong)
+    double* ab;            // alpha_k, beta_k
+    double* lmax_out;      // device scalar
+    int* err_out;          // status word (may be null)
+    int s, m;              // order, steps (<= kLanczosMax)
+};
+struct LancBatch {
+    int n, m_max;
+    LancMat mt[kMaxHpdBatch];
+};
+
+RECON_DEV void report_lanc(const LancBatch& bt, int v) {
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int b = 0; b < bt.n; ++b)
+            if (bt.mt[b].err_out) *bt.mt[b].err_out = v;
+}
+
+// Several matrices per launch, two grid barriers per step for all of them. Row i of matrix b goes
+// to global warp i mod (warps of the grid), as in a launch of that matrix alone, and every sum is
+// taken in the same order, so each matrix's lambda_max is bitwise the one its own launch gives.
 __global__ void __launch_bounds__(kThreads)
-lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict__ u,
-               double2* __restrict__ vprev, double* __restrict__ part, double* __restrict__ ab,
-               double* __restrict__ lmax_out, GridBar* gb, int* err_out, CoopFault fault) {
-    __shared__ double red[kThreads / 32];
-    __shared__ double s_beta, s_ib, s_alpha;
-    __shared__ double sh_lo, sh_hi;
-    __shared__ int s_m;
+lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
+    __shared__ double red[kMaxHpdBatch][kThreads / 32];
+    __shared__ double s_beta[kMaxHpdBatch], s_ib[kMaxHpdBatch], s_alpha[kMaxHpdBatch];
+    __shared__ int s_m[kMaxHpdBatch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = gridDim.x * (kThreads / 32);
     const int gw = warp * gridDim.x + blockIdx.x;  // rows spread over every SM (FP64 unit per SM)
+    const int n = bt.n;
     // deterministic start vector, unnormalised: u_i = 1 + 0.5 sin(i) + i 0.25 i cos(3 i) / s
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
-        u[i] = make_double2(1.0 + 0.5 * sin((double)i), 0.25 * cos(3.0 * i) * i / s);
-        vprev[i] = make_double2(0.0, 0.0);
+    for (int b = 0; b < n; ++b) {
+        const LancMat& L = bt.mt[b];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.s; i += gridDim.x * blockDim.x) {
+            L.u[i] = make_double2(1.0 + 0.5 * sin((double)i), 0.25 * cos(3.0 * i) * i / L.s);
+            L.vprev[i] = make_double2(0.0, 0.0);
+        }
     }
-    if (!grid_barrier(gb, fault)) return report(err_out, 1);
-    if (warp == 0) {
+    if (!grid_barrier(gb, fault)) return report_lanc(bt, 1);
+    for (int b = warp; b < n; b += kThreads / 32) {
+        const LancMat& L = bt.mt[b];
         double acc = 0.0;
-        for (int i = lane; i < s; i += 32) acc += u[i].x * u[i].x + u[i].y * u[i].y;
+        for (int i = lane; i < L.s; i += 32) acc += L.u[i].x * L.u[i].x + L.u[i].y * L.u[i].y;
         acc = warp_sum(acc);
         if (lane == 0) {
-            s_beta = sqrt(acc);
-            s_ib = rcp_nr(s_beta);
-            s_m = m;
+            s_beta[b] = sqrt(acc);
+            s_ib[b] = rcp_nr(s_beta[b]);
+            s_m[b] = L.m;
         }
     }
     __syncthreads();
-    for (int k = 0; k < m; ++k) {
+    for (int k = 0; k < bt.m_max; ++k) {
         // v_k = u / beta_{k-1};  w = G v_k - alpha_k v_k - beta_{k-1} v_{k-1};  beta_k = |w|
-        const double beta = s_beta, ib = s_ib;
-        double* pa = part + (size_t)(k & 1) * 2 * gridDim.x;   // alpha partials (ping-pong)
-        double* pb = pa + gridDim.x;                            // beta partials
-        double ap = 0.0;
-        double2 yrow[4];
-        int nrow = 0;
-        for (int i = gw; i < s && nrow < 4; i += nw, ++nrow) {
-            // row i of the Hermitian G is the conjugate of column i (contiguous)
-            double2 acc = make_double2(0.0, 0.0);
-            const double2* gcol = G + (size_t)i * s;
-            for (int j = lane; j < s; j += 32) {
-                const double2 g = gcol[j], uj = u[j];
-                acc.x = fma(g.x, uj.x, acc.x);
-                acc.x = fma(g.y, uj.y, acc.x);
-                acc.y = fma(g.x, uj.y, acc.y);
-                acc.y = fma(-g.y, uj.x, acc.y);
+        bool any = false;
+        for (int b = 0; b < n; ++b) {
+            const LancMat& L = bt.mt[b];
+            const bool act = k < s_m[b];
+            any = any || act;
+            double ap = 0.0;
+            if (act) {
+                const double ib = s_ib[b];
+                int nrow = 0;
+                for (int i = gw; i < L.s && nrow < 4; i += nw, ++nrow) {
+                    // row i of the Hermitian G is the conjugate of column i (contiguous)
+                    double2 acc = make_double2(0.0, 0.0);
+                    const double2* gcol = L.G + (size_t)i * L.s;
+                    for (int j = lane; j < L.s; j += 32) {
+                        const double2 g = gcol[j], uj = L.u[j];
+                        acc.x = fma(g.x, uj.x, acc.x);
+                        acc.x = fma(g.y, uj.y, acc.x);
+                        acc.y = fma(g.x, uj.y, acc.y);
+                        acc.y = fma(-g.y, uj.x, acc.y);
+                    }
+                    acc.x = warp_sum(acc.x) * ib;
+                    acc.y = warp_sum(acc.y) * ib;
+                    if (lane == 0) L.y[i] = acc;
+                    const double2 vi = make_double2(L.u[i].x * ib, L.u[i].y * ib);
+                    ap += vi.x * acc.x + vi.y * acc.y;
+                }
             }
-            acc.x = warp_sum(acc.x) * ib;
-            acc.y = warp_sum(acc.y) * ib;
-            yrow[nrow] = acc;
-            const double2 vi = make_double2(u[i].x * ib, u[i].y * ib);
-            ap += vi.x * acc.x + vi.y * acc.y;
+            if (lane == 0) red[b][warp] = ap;
         }
+        if (!any) break;
         __syncthreads();
-        if (lane == 0) red[warp] = ap;
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if ((int)threadIdx.x < n && k < s_m[threadIdx.x]) {
+            const int b = threadIdx.x;
             double t = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) t += red[w];
-            pa[blockIdx.x] = t;
+            for (int w = 0; w < kThreads / 32; ++w) t += red[b][w];
+            bt.mt[b].part[(size_t)(k & 1) * 2 * gridDim.x + blockIdx.x] = t;
         }
-        if (!grid_barrier(gb, fault)) return report(err_out, 1);
-        if (warp == 0) {
-            const double al = warp0_sum_array(pa, gridDim.x);
-            if (lane == 0) s_alpha = al;
+        if (!grid_barrier(gb, fault)) return report_lanc(bt, 1);
+        for (int b = warp; b < n; b += kThreads / 32) {
+            if (k >= s_m[b]) continue;
+            const double* pa = bt.mt[b].part + (size_t)(k & 1) * 2 * gridDim.x;
+            double v = 0.0;
+            for (int c = lane; c < (int)gridDim.x; c += 32) v += pa[c];
+            v = warp_sum(v);
+            if (lane == 0) s_alpha[b] = v;
         }
         __syncthreads();
-        const double alpha = s_alpha;
-        double bp = 0.0;
-        nrow = 0;
-        for (int i = gw; i < s && nrow < 4; i += nw, ++nrow) {
-            if (lane == 0) {
-                const double2 vi = make_double2(u[i].x * ib, u[i].y * ib);
-                const double2 vp = vprev[i];
-                const double2 un = make_double2(yrow[nrow].x - alpha * vi.x - beta * vp.x,
-                                                yrow[nrow].y - alpha * vi.y - beta * vp.y);
-                bp += un.x * un.x + un.y * un.y;
-                vprev[i] = vi;
-                u[i] = un;
+        for (int b = 0; b < n; ++b) {
+            const LancMat& L = bt.mt[b];
+            double bp = 0.0;
+            if (k < s_m[b] && lane == 0) {
+                const double alpha = s_alpha[b], beta = s_beta[b], ib = s_ib[b];
+                int nrow = 0;
+                for (int i = gw; i < L.s && nrow < 4; i += nw, ++nrow) {
+                    const double2 vi = make_double2(L.u[i].x * ib, L.u[i].y * ib);
+                    const double2 vp = L.vprev[i], yi = L.y[i];
+                    const double2 un = make_double2(yi.x - alpha * vi.x - beta * vp.x,
+                                                    yi.y - alpha * vi.y - beta * vp.y);
+                    bp += un.x * un.x + un.y * un.y;
+                    L.vprev[i] = vi;
+                    L.u[i] = un;
+                }
             }
+            if (lane == 0) red[b][warp] = bp;
         }
-        if (lane == 0) red[warp] = bp;
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if ((int)threadIdx.x < n && k < s_m[threadIdx.x]) {
+            const int b = threadIdx.x;
             double t = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) t += red[w];
-            pb[blockIdx.x] = t;
+            for (int w = 0; w < kThreads / 32; ++w) t += red[b][w];
+            bt.mt[b].part[(size_t)(k & 1) * 2 * gridDim.x + gridDim.x + blockIdx.x] = t;
         }
-        if (!grid_barrier(gb, fault)) return report(err_out, 1);
-        if (warp == 0) {
-            const double b2 = warp0_sum_array(pb, gridDim.x);
+        if (!grid_barrier(gb, fault)) return report_lanc(bt, 1);
+        for (int b = warp; b < n; b += kThreads / 32) {
+            if (k >= s_m[b]) continue;
+            const double* pb = bt.mt[b].part + (size_t)(k & 1) * 2 * gridDim.x + gridDim.x;
+            double v = 0.0;
+            for (int c = lane; c < (int)gridDim.x; c += 32) v += pb[c];
+            const double b2 = warp_sum(v);
             if (lane == 0) {
                 const double bnew = sqrt(b2);
-                if (blockIdx.x == 0) {
-                    ab[2 * k] = alpha;
-                    ab[2 * k + 1] = bnew;
+                if ((int)blockIdx.x == b) {  // the CTA that reads them for the multisection
+                    bt.mt[b].ab[2 * k] = s_alpha[b];
+                    bt.mt[b].ab[2 * k + 1] = bnew;
                 }
-                s_beta = bnew;
-                s_ib = rcp_nr(bnew);
-                if (!(bnew > 1e-300 * fabs(alpha) + 1e-300)) s_m = k + 1;
+                const double al = s_alpha[b];
+                s_beta[b] = bnew;
+                s_ib[b] = rcp_nr(bnew);
+                if (!(bnew > 1e-300 * fabs(al) + 1e-300)) s_m[b] = k + 1;
             }
         }
         __syncthreads();
-        if (s_m == k + 1) break;
     }
-    m = s_m;
+    // matrix b's tridiagonal on CTA b
+    if ((int)blockIdx.x >= n) return;
+    const LancMat& L = bt.mt[blockIdx.x];
+    const double* ab = L.ab;
+    const int m = s_m[blockIdx.x];
+    __shared__ double sh_lo, sh_hi;
     // Largest eigenvalue of the m x m tridiagonal (alpha_k, beta_k) by multisection with Sturm
-    // counts (CTA 0): FP32 rounds over the whole block to 1e-4 relative (FP32 counts are exact
+    // counts (one CTA per matrix): FP32 rounds over the whole block to 1e-4 relative (FP32 counts are exact
     // for x farther than ~m eps32 |T| from an eigenvalue), then FP64 rounds on three warps. The
     // FP64 count follows the characteristic polynomials p_k = (alpha_k - x) p_{k-1} -
     // beta_{k-1}^2 p_{k-2} (the number of sign changes of p_0 .. p_m is the number of eigenvalues
     // below x), rescaled by exact powers of two when the exponent drifts: two dependent FP64
     // operations per step instead of a reciprocal.
-    if (blockIdx.x != 0) return;
     __shared__ int best;
     __shared__ float sa32[kLanczosMax], sb32[kLanczosMax];
     __shared__ double sa64[kLanczosMax], sb64[kLanczosMax];
@@ -598,9 +710,12 @@ lanczos_kernel(const double2* __restrict__ G, int s, int m, double2* __restrict_
         __syncthreads();
         if (sh_hi - sh_lo <= 2e-16 * fabs(sh_hi)) break;
     }
-    if (threadIdx.x == 0) lmax_out[0] = 0.5 * (sh_lo + sh_hi);
-    report(err_out, 0);
+    if (threadIdx.x == 0) {
+        L.lmax_out[0] = 0.5 * (sh_lo + sh_hi);
+        if (L.err_out) *L.err_out = 0;
+    }
 }
+
 
 int coop_grid(const void* kern, int* grid) {
     int dev = 0, sms = 0, per = 0;
@@ -644,28 +759,49 @@ size_t hpd_scratch_bytes(const Dims& d) {
 }
 
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {
-    return kCoopBarrierBytes + 2 * (size_t)d.s() * sizeof(double2) + 4 * (size_t)grid_max * sizeof(double) +
+    return kCoopBarrierBytes + 3 * (size_t)d.s() * sizeof(double2) + 4 * (size_t)grid_max * sizeof(double) +
            2 * kLanczosMax * sizeof(double) + 1024;
+}
+
+cudaError_t launch_hpd_inverse_batch(const HpdJob* jobs, int n, void* barrier_scratch,
+                                     cudaStream_t st, CoopFault fault) {
+    if (n < 1 || n > kMaxHpdBatch || !barrier_scratch) return cudaErrorInvalidValue;
+    int grid = 0;
+    if (coop_grid((const void*)hpd_sweep_kernel, &grid) || grid < n + 1)
+        return cudaErrorInvalidConfiguration;
+    SweepBatch bt = {};
+    bt.n = n;
+    int nts[kMaxHpdBatch];
+    for (int b = 0; b < n; ++b) {
+        const int s = jobs[b].s, nt = tiles_per_side(s);
+        if (s < 1 || nt >= 1024 || !jobs[b].G || !jobs[b].eps || !jobs[b].scratch)
+            return cudaErrorInvalidValue;
+        const size_t nlt = (size_t)nt * (nt + 1) / 2;
+        unsigned char* p = reinterpret_cast<unsigned char*>(jobs[b].scratch) + kCoopBarrierBytes;
+        SweepMat& mt = bt.m[b];
+        mt.G = jobs[b].G;
+        mt.eps = jobs[b].eps;
+        mt.A0 = reinterpret_cast<double2*>(p);
+        p += nlt * kTileT * sizeof(double2);
+        mt.A1 = reinterpret_cast<double2*>(p);
+        p += nlt * kTileT * sizeof(double2);
+        mt.Dbuf = reinterpret_cast<double2*>(p);
+        mt.err_out = jobs[b].err_out;
+        mt.s = s;
+        mt.nt = nt;
+        nts[b] = nt;
+        if (nt > bt.nt_max) bt.nt_max = nt;
+    }
+    // every work item must fit the per-CTA item table
+    if (sweep_items(nts, n, grid - n, -1, nullptr, 0) > kMaxItems) return cudaErrorInvalidValue;
+    GridBar* gb = reinterpret_cast<GridBar*>(barrier_scratch);
+    return launch_coop(hpd_sweep_kernel, grid, st, bt, gb, fault);
 }
 
 cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
                                int* err_flag_out, cudaStream_t st, CoopFault fault) {
-    const int s = d.s(), nt = tiles_per_side(s);
-    const size_t nlt = (size_t)nt * (nt + 1) / 2;
-    int grid = 0;
-    if (coop_grid((const void*)hpd_sweep_kernel, &grid) || grid < 2) return cudaErrorInvalidConfiguration;
-    // every work item must fit the per-CTA item table
-    if (sweep_items(nt, grid - 1, -1, nullptr, 0) > kMaxItems) return cudaErrorInvalidValue;
-    unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
-    GridBar* gb = reinterpret_cast<GridBar*>(p);
-    p += kCoopBarrierBytes;
-    double2* A0 = reinterpret_cast<double2*>(p);
-    p += nlt * kTileT * sizeof(double2);
-    double2* A1 = reinterpret_cast<double2*>(p);
-    p += nlt * kTileT * sizeof(double2);
-    double2* Dbuf = reinterpret_cast<double2*>(p);
-    return launch_coop(hpd_sweep_kernel, grid, st, G, s, eps, nt, A0, A1, Dbuf, gb, err_flag_out,
-                       fault);
+    const HpdJob job{G, eps, scratch, err_flag_out, d.s()};
+    return launch_hpd_inverse_batch(&job, 1, scratch, st, fault);
 }
 
 cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStream_t st) {
@@ -676,24 +812,45 @@ cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStr
     return cudaGetLastError();
 }
 
+cudaError_t launch_lanczos_batch(const LanczosJob* jobs, int n, void* barrier_scratch,
+                                 cudaStream_t st, CoopFault fault) {
+    if (n < 1 || n > kMaxHpdBatch || !barrier_scratch) return cudaErrorInvalidValue;
+    int grid = 0;
+    if (coop_grid((const void*)lanczos_kernel, &grid) || grid < n) return cudaErrorInvalidConfiguration;
+    const int nw = grid * (kThreads / 32);
+    LancBatch bt = {};
+    bt.n = n;
+    for (int b = 0; b < n; ++b) {
+        const int s = jobs[b].s;
+        // each warp holds at most four rows of a matrix
+        if (s < 1 || s > 4 * nw || !jobs[b].G || !jobs[b].scratch || !jobs[b].lmax)
+            return cudaErrorInvalidValue;
+        unsigned char* p = reinterpret_cast<unsigned char*>(jobs[b].scratch) + kCoopBarrierBytes;
+        LancMat& L = bt.mt[b];
+        L.G = jobs[b].G;
+        L.u = reinterpret_cast<double2*>(p);
+        p += (size_t)s * sizeof(double2);
+        L.vprev = reinterpret_cast<double2*>(p);
+        p += (size_t)s * sizeof(double2);
+        L.y = reinterpret_cast<double2*>(p);
+        p += (size_t)s * sizeof(double2);
+        L.part = reinterpret_cast<double*>(p);
+        p += 4 * (size_t)grid * sizeof(double);
+        L.ab = reinterpret_cast<double*>(p);
+        L.lmax_out = jobs[b].lmax;
+        L.err_out = jobs[b].err_out;
+        L.s = s;
+        L.m = s < kLanczosMax ? s : kLanczosMax;
+        if (L.m > bt.m_max) bt.m_max = L.m;
+    }
+    GridBar* gb = reinterpret_cast<GridBar*>(barrier_scratch);
+    return launch_coop(lanczos_kernel, grid, st, bt, gb, fault);
+}
+
 cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, double* lmax,
                                 int* err_flag_out, cudaStream_t st, CoopFault fault) {
-    int grid = 0;
-    if (coop_grid((const void*)lanczos_kernel, &grid)) return cudaErrorInvalidConfiguration;
-    const int s = d.s();
-    int m = s < kLanczosMax ? s : kLanczosMax;
-    unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
-    GridBar* gb = reinterpret_cast<GridBar*>(p);
-    p += kCoopBarrierBytes;
-    double2* u = reinterpret_cast<double2*>(p);
-    p += (size_t)s * sizeof(double2);
-    double2* vprev = reinterpret_cast<double2*>(p);
-    p += (size_t)s * sizeof(double2);
-    double* part = reinterpret_cast<double*>(p);
-    p += 4 * (size_t)grid * sizeof(double);
-    double* ab = reinterpret_cast<double*>(p);
-    return launch_coop(lanczos_kernel, grid, st, G, s, m, u, vprev, part, ab, lmax, gb, err_flag_out,
-                       fault);
+    const LanczosJob job{G, scratch, lmax, err_flag_out, d.s()};
+    return launch_lanczos_batch(&job, 1, scratch, st, fault);
 }
 
 }  // namespace recon

@@ -10,6 +10,9 @@
 
 namespace recon {
 
+// Most matrices (solves) one batched weight launch serves.
+constexpr int kMaxHpdBatch = 16;
+
 // Geometry of one problem: image series [T][P][Q] complex64 (or volumes [T][R][P][Q] when
 // R > 1), filter N1 x N2 (x N3) x M taps. A volume is laid out as R * P image rows of length Q,
 // so the row passes, the pixel-wise W and the CG vectors see rows() = R * P rows.
@@ -137,6 +140,9 @@ cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, doub
 // eps update: first -> eps = frac * lambda_max (read from *lmax), else eps /= gamma
 cudaError_t launch_eps(const double* lmax, double* eps, int first, double frac, double gamma,
                        cudaStream_t st);
+// The same for n solves in one launch (n <= kMaxHpdBatch).
+cudaError_t launch_eps_batch(const double* const* lmax, double* const* eps, int n, int first,
+                             double frac, double gamma, cudaStream_t st);
 // Summed diagonals of H = U diag((lambda + eps)^(p/2-1)) U^H: d[pair][L1][L2] (complex128)
 size_t diag_scratch_bytes(const Dims& d);
 cudaError_t launch_diag_sums(const Dims& d, const double2* U, const double* evals,
@@ -170,11 +176,36 @@ size_t lanczos_scratch_bytes(const Dims& d, int grid_max);
 // gave up. The same holds for launch_lanczos_lmax.
 cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
                                int* err_flag_out, cudaStream_t st, CoopFault fault = {});
+// Several matrices in one cooperative launch (one grid barrier per pivot step serves all): job b
+// inverts its G (s_b x s_b) with its own eps, scratch (hpd_scratch_bytes of its s) and status
+// word. barrier_scratch: the scratch whose barrier header the launch uses (launches sharing it
+// must be stream-ordered). Results are bitwise those of launching each matrix alone.
+struct HpdJob {
+    double2* G;
+    const double* eps;
+    void* scratch;
+    int* err_out;
+    int s;
+};
+cudaError_t launch_hpd_inverse_batch(const HpdJob* jobs, int n, void* barrier_scratch,
+                                     cudaStream_t st, CoopFault fault = {});
 // d_ab[delta] (summed diagonals) from an explicit H
 cudaError_t launch_hdiag(const Dims& d, const double2* H, double2* dsum, cudaStream_t st);
 // *lmax = largest eigenvalue of G (Lanczos, FP64)
 cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, double* lmax,
                                 int* err_flag_out, cudaStream_t st, CoopFault fault = {});
+// Several matrices in one cooperative launch (two grid barriers per step serve all): job b writes
+// lambda_max of its G (s_b x s_b) to its *lmax, using its scratch (lanczos_scratch_bytes of its
+// s). Bitwise the value of launching the matrix alone.
+struct LanczosJob {
+    const double2* G;
+    void* scratch;
+    double* lmax;
+    int* err_out;
+    int s;
+};
+cudaError_t launch_lanczos_batch(const LanczosJob* jobs, int n, void* barrier_scratch,
+                                 cudaStream_t st, CoopFault fault = {});
 
 // ---- frame_op.cu (square frames: cluster 2-D transform per frame + pixel-parallel W) ----
 bool frame_op_supported(const Dims& d);

@@ -16,6 +16,7 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -100,6 +101,12 @@ struct recon_ctx {
     bool three_pass = false;           // 256 x 256 series: three-pass CG step (RECON_OPT_THREE_PASS)
     bool inject_barrier_fault = false; // next solve: sweep barrier starts failed (RECON_OPT_INJECT_BARRIER_FAULT)
     bool withhold_arrival = false;     // next solve: one CTA withholds its barrier arrival (RECON_OPT_TEST_WITHHOLD_ARRIVAL)
+    // lockstep batches (RECON_OPT_BATCH_GROUP): one graph over every slot of recon_solve_batch
+    int batch_group = 0;               // solves per shared weight launch; 0 = independent slots
+    cudaGraphExec_t batch_gexec = nullptr;
+    GraphProf* batch_gprof = nullptr;
+    std::vector<unsigned char> batch_key;
+    std::vector<cudaEvent_t> batch_ev;  // fork / join events of the capture
     std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tiles;
     std::string tile_cache;            // file the tuned choices are appended to (may be empty)
     struct Slot {
@@ -215,6 +222,7 @@ void collect_graph(recon_ctx* c, GraphProf* gp) {
 void prof_collect(recon_ctx* c) {
     collect_graph(c, c->gprof);
     for (auto& sl : c->slots) collect_graph(c, sl.gprof);
+    collect_graph(c, c->batch_gprof);
     for (auto& pk : c->prof_pending) {
         float ms = 0.f;
         cudaEventSynchronize(c->ev_pool[pk.second + 1]);
@@ -859,6 +867,23 @@ int solve_iter(recon_ctx* c, Solve& sv, int n) {
                     sv.prm->cg, sv.coils, sv.coil_proj);
 }
 
+// The key of a solve's graph (shapes, parameters, buffers, workspace generation, options).
+recon_ctx::GraphKey graph_key(recon_ctx* c, const Solve& sv) {
+    const recon_params* prm = sv.prm;
+    recon_ctx::GraphKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.T = sv.d.T; k.P = sv.d.P; k.Q = sv.d.Q; k.N1 = sv.d.N1; k.N2 = sv.d.N2; k.M = sv.d.M;
+    k.R = sv.d.R; k.N3 = sv.d.N3;
+    k.irls = prm->irls; k.cg = prm->cg; k.bf16 = prm->kspace_bf16; k.method = prm->weight_method;
+    k.lambda = prm->lambda; k.p = prm->p; k.gamma = prm->gamma; k.eps0_frac = prm->eps0_frac;
+    k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
+    k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
+    k.circ = sv.d.circ; k.variant = sv.variant; k.colC = sv.d.colC; k.depthC = sv.d.depthC;
+    k.three_pass = c->three_pass;
+    k.prof = c->prof;
+    return k;
+}
+
 // Enqueue a whole solve on the active slot's stream: as one replay of a captured CUDA graph
 // (captured on first use, cached per slot and keyed by shapes, parameters, buffers and the
 // workspace generation), or as direct launches when graphs are off, when the eigensolver
@@ -871,17 +896,7 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
         for (int n = 0; n < prm->irls && !rc; ++n) rc = solve_iter(c, sv, n);
         return rc;
     }
-    recon_ctx::GraphKey k;
-    std::memset(&k, 0, sizeof(k));
-    k.T = sv.d.T; k.P = sv.d.P; k.Q = sv.d.Q; k.N1 = sv.d.N1; k.N2 = sv.d.N2; k.M = sv.d.M;
-    k.R = sv.d.R; k.N3 = sv.d.N3;
-    k.irls = prm->irls; k.cg = prm->cg; k.bf16 = prm->kspace_bf16; k.method = prm->weight_method;
-    k.lambda = prm->lambda; k.p = prm->p; k.gamma = prm->gamma; k.eps0_frac = prm->eps0_frac;
-    k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
-    k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
-    k.circ = sv.d.circ; k.variant = sv.variant; k.colC = sv.d.colC; k.depthC = sv.d.depthC;
-    k.three_pass = c->three_pass;
-    k.prof = c->prof;
+    const recon_ctx::GraphKey k = graph_key(c, sv);
     if (!c->gexec || std::memcmp(&k, &c->gkey, sizeof(k)) != 0) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -911,6 +926,173 @@ int solve_enqueue_all(recon_ctx* c, Solve& sv) {
     }
     RC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
     if (c->gprof) ++c->gprof->replays;
+    return RECON_OK;
+}
+
+// ---- lockstep batches: the weight steps of a group of solves share their launches ----
+
+// Gram of x^(n-1) into the solve's G (active slot's stream).
+int iter_gram(recon_ctx* c, Solve& sv) {
+    ProfScope ps(c, RECON_PROF_GRAM);
+    RC_CUDA(recon::launch_gram(sv.d, sv.tw, sv.x, sv.w.lag_part, sv.w.gblocks, nullptr, sv.w.G,
+                               c->stream));
+    return RECON_OK;
+}
+
+// The FP64 weight of a group of solves (p = 0 sweep path) in shared launches on the active
+// stream: at n = 0 one Lanczos launch for every lambda_max, then one eps launch and one sweep
+// launch for all. The group leader's scratch holds the barriers of the shared launches.
+int group_weight(recon_ctx* c, Solve* grp, int cnt, int n) {
+    if (n == 0) {
+        recon::LanczosJob jobs[recon::kMaxHpdBatch];
+        for (int b = 0; b < cnt; ++b)
+            jobs[b] = {grp[b].w.G, grp[b].w.lanc, grp[b].w.lmax, grp[b].w.kerr + 2 * n + 1, grp[b].d.s()};
+        ProfScope ps(c, RECON_PROF_LANCZOS);
+        RC_CUDA(recon::launch_lanczos_batch(jobs, cnt, grp[0].w.lanc, c->stream, grp[0].w.fault));
+    }
+    {
+        const double* lmax[recon::kMaxHpdBatch];
+        double* eps[recon::kMaxHpdBatch];
+        for (int b = 0; b < cnt; ++b) {
+            lmax[b] = grp[b].w.lmax;
+            eps[b] = grp[b].w.eps;
+        }
+        ProfScope ps(c, RECON_PROF_EPS);
+        RC_CUDA(recon::launch_eps_batch(lmax, eps, cnt, n == 0, grp[0].prm->eps0_frac,
+                                        grp[0].prm->gamma, c->stream));
+    }
+    recon::HpdJob jobs[recon::kMaxHpdBatch];
+    for (int b = 0; b < cnt; ++b)
+        jobs[b] = {grp[b].w.G, grp[b].w.eps, grp[b].w.hpd, grp[b].w.kerr + 2 * n, grp[b].d.s()};
+    ProfScope ps(c, RECON_PROF_INV);
+    RC_CUDA(recon::launch_hpd_inverse_batch(jobs, cnt, grp[0].w.hpd, c->stream, grp[0].w.fault));
+    return RECON_OK;
+}
+
+// After the weight: summed diagonals of H, S(r), residual carry and the CG steps (active slot).
+int iter_post_weight(recon_ctx* c, Solve& sv, int n) {
+    Work& w = sv.w;
+    float2* S[2] = {w.S0, w.S1};
+    float2* S_new = S[n & 1];
+    const float2* S_old = n == 0 ? nullptr : S[(n + 1) & 1];
+    {
+        ProfScope ps(c, RECON_PROF_DIAG);
+        RC_CUDA(recon::launch_hdiag(sv.d, w.G, w.dsum, c->stream));
+    }
+    {
+        ProfScope ps(c, RECON_PROF_S);
+        RC_CUDA(recon::launch_weight_S(sv.d, sv.tw, w.dsum, w.Z, S_new, c->stream));
+    }
+    return cg_block(c, sv.d, sv.tw, w, sv.masks, S_old, S_new, (float)sv.prm->lambda, sv.x, n == 0,
+                    sv.prm->cg);
+}
+
+// Capture body of a lockstep batch (slot 0 active and capturing): every solve runs on its own
+// slot stream; per IRLS iteration the solves' Grams join on their group leader's stream for the
+// shared weight launches, then fork back for the summed diagonals, S(r) and CG. With several
+// groups the weight launches take turns (each waits for the previous group's), so that the FP64
+// launches of one group overlap the other groups' CG instead of each other.
+int batch_capture(recon_ctx* c, std::vector<Solve>& sv, int group) {
+    const int n = (int)sv.size();
+    const int ngroups = (n + group - 1) / group;
+    cudaEvent_t ev_start = c->batch_ev[0], ev_tok = c->batch_ev[1];
+    auto ev = [&](int i) { return c->batch_ev[2 + i]; };
+    RC_CUDA(cudaEventRecord(ev_start, c->stream));
+    int rc = RECON_OK;
+    for (int i = 1; i < n && !rc; ++i) {
+        rc = select_slot(c, i);
+        if (!rc) RC_CUDA(cudaStreamWaitEvent(c->stream, ev_start, 0));
+    }
+    for (int i = 0; i < n && !rc; ++i) {
+        rc = select_slot(c, i);
+        if (!rc) rc = solve_begin(c, &sv[i]);
+    }
+    bool tok = false;
+    for (int it = 0; it < sv[0].prm->irls && !rc; ++it) {
+        for (int i = 0; i < n && !rc; ++i) {
+            rc = select_slot(c, i);
+            if (!rc) rc = iter_gram(c, sv[i]);
+            if (!rc) RC_CUDA(cudaEventRecord(ev(i), c->stream));
+        }
+        for (int g0 = 0; g0 < n && !rc; g0 += group) {
+            const int cnt = std::min(group, n - g0);
+            rc = select_slot(c, g0);
+            for (int i = g0 + 1; i < g0 + cnt && !rc; ++i)
+                RC_CUDA(cudaStreamWaitEvent(c->stream, ev(i), 0));
+            if (!rc && tok) RC_CUDA(cudaStreamWaitEvent(c->stream, ev_tok, 0));
+            if (!rc) rc = group_weight(c, &sv[g0], cnt, it);
+            if (!rc) RC_CUDA(cudaEventRecord(ev(g0), c->stream));
+            if (!rc && ngroups > 1) {
+                RC_CUDA(cudaEventRecord(ev_tok, c->stream));
+                tok = true;
+            }
+            for (int i = g0; i < g0 + cnt && !rc; ++i) {
+                rc = select_slot(c, i);
+                if (!rc && i != g0) RC_CUDA(cudaStreamWaitEvent(c->stream, ev(g0), 0));
+                if (!rc) rc = iter_post_weight(c, sv[i], it);
+            }
+        }
+    }
+    for (int i = 1; i < n && !rc; ++i) {
+        rc = select_slot(c, i);
+        if (!rc) RC_CUDA(cudaEventRecord(ev(i), c->stream));
+        if (!rc) rc = select_slot(c, 0);
+        if (!rc) RC_CUDA(cudaStreamWaitEvent(c->stream, ev(i), 0));
+    }
+    return rc;
+}
+
+// Enqueue a lockstep batch on slot 0's stream as one replay of its captured graph (captured on
+// first use, cached while every solve's key, the group size and the slots' workspaces stay).
+int batch_enqueue_lockstep(recon_ctx* c, std::vector<Solve>& sv, int group) {
+    const int n = (int)sv.size();
+    std::vector<unsigned char> key(sizeof(int) * 2);
+    std::memcpy(key.data(), &n, sizeof(int));
+    std::memcpy(key.data() + sizeof(int), &group, sizeof(int));
+    for (int i = 0; i < n; ++i) {
+        int rc = select_slot(c, i);
+        if (rc) return rc;
+        const recon_ctx::GraphKey k = graph_key(c, sv[i]);
+        const unsigned char* kb = reinterpret_cast<const unsigned char*>(&k);
+        key.insert(key.end(), kb, kb + sizeof(k));
+    }
+    int rc = select_slot(c, 0);
+    if (rc) return rc;
+    if (!c->batch_gexec || key != c->batch_key) {
+        if (c->batch_gexec) {
+            cudaGraphExecDestroy(c->batch_gexec);
+            c->batch_gexec = nullptr;
+        }
+        while ((int)c->batch_ev.size() < RECON_MAX_BATCH + 2) {
+            cudaEvent_t e;
+            RC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            c->batch_ev.push_back(e);
+        }
+        delete c->batch_gprof;
+        c->batch_gprof = c->prof ? new GraphProf() : nullptr;
+        c->capturing = c->batch_gprof;
+        RC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        rc = batch_capture(c, sv, group);
+        const int rc0 = select_slot(c, 0);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+        c->capturing = nullptr;
+        if (!rc) rc = rc0;
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return cuda_fail(c, ec, "cudaStreamEndCapture");
+        const cudaError_t ei = cudaGraphInstantiate(&c->batch_gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->batch_gexec = nullptr;
+            return cuda_fail(c, ei, "cudaGraphInstantiate");
+        }
+        c->batch_key = key;
+    }
+    RC_CUDA(cudaGraphLaunch(c->batch_gexec, c->stream));
+    if (c->batch_gprof) ++c->batch_gprof->replays;
     return RECON_OK;
 }
 
@@ -1366,6 +1548,9 @@ void recon_destroy(recon_ctx* c) {
     }
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     delete c->gprof;
+    if (c->batch_gexec) cudaGraphExecDestroy(c->batch_gexec);
+    delete c->batch_gprof;
+    for (cudaEvent_t e : c->batch_ev) cudaEventDestroy(e);
     if (c->solver) cusolverDnDestroy(c->solver);
     if (c->blas) cublasDestroy(c->blas);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1548,12 +1733,26 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
     rc = RECON_OK;
     cudaError_t e = cudaEventRecord(start, c->stream);
     const bool direct = !c->graphs || wants_eig(prm->p, prm->weight_method);
+    // lockstep: one graph over all slots, the weight steps of each group of solves in shared
+    // launches (p = 0 sweep path, more than one solve, no test hook pending)
+    const bool lockstep = !direct && c->batch_group > 0 && n > 1 && !c->withhold_arrival &&
+                          !c->inject_barrier_fault;
     for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
         rc = select_slot(c, i);
         if (!rc) e = cudaStreamWaitEvent(c->stream, start, 0);
         if (!rc && e == cudaSuccess) rc = solve_prepare(c, d, kspace[i], masks[i], prm, image_out[i], &sv[i]);
-        if (!rc && e == cudaSuccess && !direct) rc = solve_enqueue_all(c, sv[i]);
+        if (!rc && e == cudaSuccess && !direct && !lockstep) rc = solve_enqueue_all(c, sv[i]);
         if (!rc && e == cudaSuccess && direct) rc = solve_begin(c, &sv[i]);
+        // the set-up work of the slot (workspace clears, tuning) precedes the lockstep graph
+        if (!rc && e == cudaSuccess && lockstep && i > 0) {
+            e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(done[i], c->stream);
+        }
+    }
+    if (lockstep && !rc && e == cudaSuccess) {
+        rc = select_slot(c, 0);
+        for (int i = 1; i < n && !rc && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->stream, done[i], 0);
+        if (!rc && e == cudaSuccess) rc = batch_enqueue_lockstep(c, sv, c->batch_group);
     }
     // direct launches: iterations interleaved over the slots so that every stream has work
     // queued early
@@ -1562,14 +1761,15 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
             rc = select_slot(c, i);
             if (!rc) rc = solve_iter(c, sv[i], it);
         }
-    for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
+    for (int i = 0; i < n && !rc && e == cudaSuccess && !lockstep; ++i) {
         rc = select_slot(c, i);
         if (!rc) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
         if (!rc && e == cudaSuccess) e = cudaEventRecord(done[i], c->stream);
     }
     if (!rc && e == cudaSuccess) {
         rc = select_slot(c, 0);
-        for (int i = 1; i < n && !rc && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->stream, done[i], 0);
+        for (int i = 1; i < n && !rc && e == cudaSuccess && !lockstep; ++i)
+            e = cudaStreamWaitEvent(c->stream, done[i], 0);
         if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
     for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
@@ -1988,6 +2188,10 @@ int recon_set_option(recon_ctx* c, int option, int value) {
         case RECON_OPT_THREE_PASS: c->three_pass = value != 0; return RECON_OK;
         case RECON_OPT_INJECT_BARRIER_FAULT: c->inject_barrier_fault = value != 0; return RECON_OK;
         case RECON_OPT_TEST_WITHHOLD_ARRIVAL: c->withhold_arrival = value != 0; return RECON_OK;
+        case RECON_OPT_BATCH_GROUP:
+            if (value < 0 || value > RECON_MAX_BATCH) return fail(c, RECON_EINVAL, "need 0 <= group <= RECON_MAX_BATCH");
+            c->batch_group = value;
+            return RECON_OK;
         default: return fail(c, RECON_EINVAL, "unknown option");
     }
 }

@@ -29,6 +29,20 @@ __global__ void eps_kernel(const double* __restrict__ lmax, double* eps, int fir
     }
 }
 
+// The eps schedule of several solves in one launch (thread b: solve b).
+struct EpsBatch {
+    const double* lmax[kMaxHpdBatch];
+    double* eps[kMaxHpdBatch];
+    int n;
+};
+__global__ void eps_batch_kernel(EpsBatch bt, int first, double frac, double gamma) {
+    const int b = threadIdx.x;
+    if (blockIdx.x == 0 && b < bt.n) {
+        if (first) bt.eps[b][0] = frac * bt.lmax[b][0];
+        else bt.eps[b][0] = bt.eps[b][0] / gamma;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads)
 diag_part_kernel(const double2* __restrict__ U, const double* __restrict__ evals,
                  const double* __restrict__ eps_p, double p, int N1, int N2, int N3, int M,
@@ -184,6 +198,19 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 cudaError_t launch_eps(const double* lmax, double* eps, int first, double frac, double gamma,
                        cudaStream_t st) {
     eps_kernel<<<1, 32, 0, st>>>(lmax, eps, first, frac, gamma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eps_batch(const double* const* lmax, double* const* eps, int n, int first,
+                             double frac, double gamma, cudaStream_t st) {
+    if (n < 1 || n > kMaxHpdBatch) return cudaErrorInvalidValue;
+    EpsBatch bt = {};
+    bt.n = n;
+    for (int b = 0; b < n; ++b) {
+        bt.lmax[b] = lmax[b];
+        bt.eps[b] = eps[b];
+    }
+    eps_batch_kernel<<<1, 32, 0, st>>>(bt, first, frac, gamma);
     return cudaGetLastError();
 }
 

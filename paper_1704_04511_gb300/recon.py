@@ -269,6 +269,7 @@ RECON_OPT_AUTOTUNE = 3
 RECON_OPT_THREE_PASS = 4
 RECON_OPT_INJECT_BARRIER_FAULT = 5
 RECON_OPT_TEST_WITHHOLD_ARRIVAL = 6
+RECON_OPT_BATCH_GROUP = 7
 
 
 def recon_tile_cache(ctx, path) -> None:

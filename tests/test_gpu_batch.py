@@ -51,6 +51,57 @@ def test_batch_equals_solo(R, p, method):
     assert not np.array_equal(solo[0], solo[1])
 
 
+@pytest.mark.parametrize("group", [1, 2, 3, 4])
+def test_lockstep_batch_equals_solo(R, group):
+    """Lockstep batches (RECON_OPT_BATCH_GROUP): the Lanczos, eps and sweep launches of each group
+    serve all of its solves at once (group 2 over three solves leaves a ragged group of one;
+    group 1 gives three groups whose weight launches take turns). Every result is bitwise the
+    solo one, also on a second replay of the captured batch graph."""
+    recon, ctx = R
+    w = synth.workload("tiny_32x32x8", n_irls=5)
+    ks, ms = _inputs(w, [0, 1, 2])
+    filt = (w.N1, w.N2, w.M)
+    solo = []
+    for k, m in zip(ks, ms):
+        out = torch.empty(tuple(m.shape), dtype=torch.complex64, device="cuda")
+        recon.recon_solve(ctx.h, k, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+        solo.append(out.cpu().numpy())
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, group)
+    try:
+        outs = [torch.full(tuple(m.shape), float("nan"), dtype=torch.complex64, device="cuda")
+                for m in ms]
+        for _ in range(2):
+            recon.recon_solve_batch(ctx.h, ks, ms, filt, w.lam, w.p, w.n_irls, w.n_cg, outs)
+            for a, b in zip(outs, solo):
+                assert np.array_equal(a.cpu().numpy(), b)
+            for o in outs:
+                o.fill_(float("nan"))
+    finally:
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, 0)
+
+
+def test_lockstep_batch_perf_size(R):
+    """Four 256x256x16 solves (s = 243) in one group: one sweep launch per IRLS iteration for
+    the four, results bitwise the solo ones."""
+    recon, ctx = R
+    w = synth.workload("perf_256x256x16", n_irls=3)
+    ks, ms = _inputs(w, [0, 5, 6, 7])
+    filt = (w.N1, w.N2, w.M)
+    solo = []
+    for k, m in zip(ks, ms):
+        out = torch.empty(tuple(m.shape), dtype=torch.complex64, device="cuda")
+        recon.recon_solve(ctx.h, k, m, filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+        solo.append(out.cpu().numpy())
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, 4)
+    try:
+        outs = [torch.empty(tuple(ms[0].shape), dtype=torch.complex64, device="cuda") for _ in ms]
+        recon.recon_solve_batch(ctx.h, ks, ms, filt, w.lam, w.p, w.n_irls, w.n_cg, outs)
+        for a, b in zip(outs, solo):
+            assert np.array_equal(a.cpu().numpy(), b)
+    finally:
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, 0)
+
+
 def test_batch_perf_size_two_slots(R):
     recon, ctx = R
     w = synth.workload("perf_256x256x16", n_irls=2)

@@ -83,9 +83,9 @@ GRAM_CASES = [
     ("tikhonov", 6, 32, 16, 1, 1, 1),
     ("M=T", 3, 16, 32, 2, 2, 3),
     ("perf", 16, 256, 256, 9, 9, 3),
-    # M = 6 with 512-point rows and 17 frames: the window sums' low parts do not fit in shared
+    # M = 6 with 512-point rows and 16 frames: the window sums' low parts do not fit in shared
     # memory next to the rows, so each is rounded once before the compensated DFT
-    ("rows512-M6-T17", 17, 16, 512, 3, 3, 6),
+    ("rows512-M6-T16", 16, 16, 512, 3, 3, 6),
 ]
 
 
@@ -104,6 +104,8 @@ def test_gram_parity(R, case):
     G_ref = slr.gram_fft(xr, N1, N2, M)
     G_gpu = G.cpu().numpy().T              # column-major storage
     print(f"\n[gram {case[0]}] relative Frobenius error vs FP64 = {rel(G_gpu, G_ref):.3e}")
+    # exactly Hermitian: every lag of a frame with itself is written with its mirror
+    assert np.array_equal(G_gpu, G_gpu.conj().T)
     assert_close(G_gpu, G_ref, 1e-5)
     assert_close(lags.cpu().numpy(), lags_pairs(slr.gram_lags(xr, N1, N2, M)), 1e-5)
 
@@ -161,22 +163,97 @@ def test_weight_parity(R, case, method):
     assert_close(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H2, N1, N2, M)), 1e-8)
 
 
-def test_weight_inverse_small_eps(R):
-    """The sweep inverse at the last IRLS iteration's eps (condition number ~2e6)."""
+@pytest.mark.parametrize("n", [0, 15, 29])
+def test_weight_inverse_ill_conditioned(R, n):
+    """The FP64 sweep inverse at the eps of IRLS iteration n (eps = 0.01 lambda_max / 1.4^n) on a
+    Hermitian G whose eigenvalues fall over eight decades, as the Grams of late, nearly low-rank
+    iterates do: condition numbers of G + eps I up to ~2e6. An FP64 inverse loses about
+    kappa * 1e-17 here (an FP64 emulation of the sweep on the CPU: 2e-11 at kappa 1.7e6); the
+    gate allows 1e-14 kappa, far below what a reciprocal accurate to only ~1e-13 gives (errors
+    growing like kappa^2, the whole weight lost at kappa ~1e5)."""
     recon, ctx = R
     T, P, Q, N1, N2, M = 16, 64, 64, 9, 9, 3
+    s = N1 * N2 * M
     rng = np.random.default_rng(5)
-    x = crandn(rng, T, P, Q)
-    G = slr.gram_fft(x, N1, N2, M)
+    U, _ = np.linalg.qr(crandn(rng, s, s))
+    G = (U * (1e5 * np.logspace(0, -8, s))) @ U.conj().T
+    G = (G + G.conj().T) / 2
     lam = np.linalg.eigvalsh(G)
-    eps = 0.01 * lam[-1] / 1.4 ** 29
+    eps = 0.01 * lam[-1] / 1.4 ** n
+    kappa = (lam[-1] + eps) / (lam[0] + eps)
+    tol = 1e-14 * kappa + 1e-12
     npair = M * (M + 1) // 2
+    Gd = to_dev(np.ascontiguousarray(G.T))
     S = torch.empty((npair, P, Q), dtype=torch.complex64, device="cuda")
     dsum = torch.empty((npair, 2 * N1 - 1, 2 * N2 - 1), dtype=torch.complex128, device="cuda")
-    recon.recon_weight(ctx.h, (T, P, Q), (N1, N2, M), to_dev(np.ascontiguousarray(G.T)), eps, 0.0,
-                       S, dsum, None)
+    recon.recon_weight(ctx.h, (T, P, Q), (N1, N2, M), Gd, eps, 0.0, S, dsum, None)
     H, _ = slr.weight_H(G, eps, 0.0)
-    assert_close(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H, N1, N2, M)), 1e-9)
+    e_d, _ = assert_close(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H, N1, N2, M)), tol, "d")
+    Hg = torch.empty((s, s), dtype=torch.complex128, device="cuda")
+    recon.recon_weight_direct(ctx.h, (T, P, Q), (N1, N2, M), Gd, eps, 0.0, Hg)
+    e_h, _ = assert_close(Hg.cpu().numpy().T, H, tol, "H")
+    print(f"\n[sweep inverse kappa {kappa:.2e}] H {e_h:.2e} d {e_d:.2e} (gate {tol:.1e})")
+
+
+@pytest.mark.parametrize("n", [20, 28])
+def test_weight_inverse_late_iteration_gram(R, n):
+    """The sweep inverse on the Gram of a nearly converged iterate (a request of the served mix,
+    64x64x18 with a 9x9x3 filter, after 20 IRLS iterations on the GPU) at the eps of iteration n:
+    condition numbers 6e4..1e6 on a Gram whose Schur complements become nearly singular in the
+    lifting's own structure. Such Grams are what exposes a sweep whose halves drift apart (an
+    inverse error of 3e-7 at kappa 6e4 and 1e-5 at 6e5 in an FP64 emulation on the CPU, against
+    5e-12 and 3e-11 for an exactly Hermitian sweep); the gate is 1e-14 kappa."""
+    recon, ctx = R
+    _, w = synth.served_mix(512, rate_hz=20.0, seed=0)[235]
+    prob = synth.make_problem(w)
+    N1, N2, M = w.N1, w.N2, w.M
+    T, P, Q = prob["masks"].shape
+    s, npair = N1 * N2 * M, M * (M + 1) // 2
+    x = torch.empty((T, P, Q), dtype=torch.complex64, device="cuda")
+    recon.recon_solve(ctx.h, to_dev(c64(prob["kspace"])), to_dev(prob["masks"]), (N1, N2, M),
+                      w.lam, w.p, 20, w.n_cg, x)
+    Gd = torch.empty((s, s), dtype=torch.complex128, device="cuda")
+    recon.recon_gram(ctx.h, x, (N1, N2, M), Gd)
+    G = Gd.cpu().numpy().T
+    lam = np.linalg.eigvalsh(G)
+    eps = 0.01 * lam[-1] / 1.4 ** n
+    kappa = (lam[-1] + eps) / (lam[0] + eps)
+    tol = 1e-14 * kappa + 1e-12
+    H, _ = slr.weight_H(G, eps, 0.0)
+    S = torch.empty((npair, P, Q), dtype=torch.complex64, device="cuda")
+    dsum = torch.empty((npair, 2 * N1 - 1, 2 * N2 - 1), dtype=torch.complex128, device="cuda")
+    recon.recon_weight(ctx.h, (T, P, Q), (N1, N2, M), Gd, eps, 0.0, S, dsum, None)
+    e_d, _ = assert_close(dsum.cpu().numpy(), lags_pairs(slr.diag_sums(H, N1, N2, M)), tol, "d")
+    Hg = torch.empty((s, s), dtype=torch.complex128, device="cuda")
+    recon.recon_weight_direct(ctx.h, (T, P, Q), (N1, N2, M), Gd, eps, 0.0, Hg)
+    H_gpu = Hg.cpu().numpy().T
+    assert np.array_equal(H_gpu, H_gpu.conj().T)
+    e_h, _ = assert_close(H_gpu, H, tol, "H")
+    print(f"\n[late-iteration Gram, eps of iteration {n}, kappa {kappa:.2e}] H {e_h:.2e} d {e_d:.2e}")
+
+
+def test_weight_reads_the_lower_triangle(R):
+    """The FP64 sweep inverse reads only the lower triangle of G (the diagonal as real), as the
+    eigensolver does: a G whose strict upper triangle holds garbage gives bitwise the weight of
+    the Hermitian G."""
+    recon, ctx = R
+    T, P, Q, N1, N2, M = 8, 32, 32, 5, 5, 2
+    rng = np.random.default_rng(21)
+    G = slr.gram_fft(crandn(rng, T, P, Q), N1, N2, M)
+    s = N1 * N2 * M
+    bad = G.copy()
+    iu = np.triu_indices(s, 1)
+    bad[iu] = crandn(rng, len(iu[0]))
+    bad[np.diag_indices(s)] += 1j * rng.standard_normal(s)
+    npair = M * (M + 1) // 2
+    outs = []
+    for g in (G, bad):
+        S = torch.empty((npair, P, Q), dtype=torch.complex64, device="cuda")
+        dsum = torch.empty((npair, 2 * N1 - 1, 2 * N2 - 1), dtype=torch.complex128, device="cuda")
+        recon.recon_weight(ctx.h, (T, P, Q), (N1, N2, M), to_dev(np.ascontiguousarray(g.T)),
+                           1e-3 * np.abs(G).max(), 0.0, S, dsum, None)
+        outs.append(dsum.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
 
 
 def _oracle_S(x, N1, N2, M, eps_frac=0.01, p=0.0):
@@ -385,6 +462,21 @@ def test_solve_parity_perf(R):
     """256x256x16, 9x9x3 filter, 30 IRLS x 15 CG: the workload the benchmark times."""
     recon, ctx = R
     w, prob = _problem("perf_256x256x16")
+    x_gpu = _solve_gpu(recon, ctx, w, prob)
+    x_ref = slr.irls(prob["kspace"].astype(np.complex64).astype(np.complex128), prob["masks"],
+                     w.N1, w.N2, w.M, w.lam, w.p, w.n_irls, w.n_cg)
+    _check_solve(x_gpu, x_ref, prob, w)
+
+
+@pytest.mark.slow
+def test_solve_parity_served_request_late_iterations(R):
+    """A request of the served mix (64x64x18, 9x9x3 filter, ~10x undersampling, two exponentials,
+    30 IRLS x 15 CG): its late iterations drive G + eps I to condition numbers near 1e6, where
+    the weight must stay an FP64-accurate inverse for the iteration to stay on the oracle's
+    trajectory."""
+    recon, ctx = R
+    _, w = synth.served_mix(512, rate_hz=20.0, seed=0)[235]
+    prob = synth.make_problem(w)
     x_gpu = _solve_gpu(recon, ctx, w, prob)
     x_ref = slr.irls(prob["kspace"].astype(np.complex64).astype(np.complex128), prob["masks"],
                      w.N1, w.N2, w.M, w.lam, w.p, w.n_irls, w.n_cg)
