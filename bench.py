@@ -402,6 +402,51 @@ def run_served(n_requests: int, device: int) -> dict:
     return stats
 
 
+def run_p07(steps: int, device: int) -> dict:
+    """The 256x256x16 workload at the paper's own operating point p = 0.7 (Sec. IV): the weight
+    (G + eps I)^(0.35 - 1) needs the eigenvalues, so every IRLS iteration runs the FP64
+    eigendecomposition (library zheevd) instead of the sweep inverse. Whole solves on
+    device-resident k-space; per-class times from one profiled solve."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1704_04511_gb300 import recon
+    w = synth.workload(WORKLOAD, p=0.7)
+    prob = synth.make_problem(w)
+    dev = torch.device("cuda", device)
+    b = torch.from_numpy(prob["kspace"].astype(np.complex64)).to(dev)
+    m = torch.from_numpy(prob["masks"]).to(dev)
+    out = torch.empty(tuple(m.shape), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = recon.Context(device, cuda_stream=stream.cuda_stream)
+    try:
+        def solve():
+            recon.recon_solve(ctx.h, b, m, (w.N1, w.N2, w.M), w.lam, w.p, w.n_irls, w.n_cg, out)
+        solve()
+        torch.cuda.synchronize(dev)
+        recon.recon_profile(ctx.h, recon.PROF_ALL)
+        solve()
+        torch.cuda.synchronize(dev)
+        eig_ms, eig_n = recon.recon_profile_read(ctx.h, 2)
+        recon.recon_profile(ctx.h, 0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    finally:
+        ctx.close()
+    return {"workload": WORKLOAD, "p": w.p, "irls": w.n_irls, "cg": w.n_cg,
+            "ms_per_solve": round(ms, 2), "irls_iters_per_s": round(1000.0 * w.n_irls / ms, 1),
+            "eig_ms_per_solve": round(eig_ms, 2), "eig_calls": eig_n,
+            "eig_share": round(eig_ms / ms, 3) if ms else None,
+            "note": "p > 0 needs the eigenvalues: FP64 eigendecomposition per IRLS iteration "
+                    "(cuSOLVER zheevd, s = 243), direct launches (no graph)"}
+
+
 def run_reference(args, rank: int):
     import synth
     if rank != 0:
@@ -451,6 +496,10 @@ def main():
                     help="time only the volume workload and print {\"vol\": ...} (profiling)")
     ap.add_argument("--vol-steps", type=int, default=2,
                     help="solves of the 128x128x64x12 volume workload to time (0 = skip)")
+    ap.add_argument("--p07-steps", type=int, default=1,
+                    help="solves of the 256x256x16 workload at p = 0.7 to time (0 = skip)")
+    ap.add_argument("--batch-modes", type=int, default=3,
+                    help="steps timed per lockstep group size (RECON_OPT_BATCH_GROUP), 0 = skip")
     ap.add_argument("--served", type=int, default=512,
                     help="requests of the served mix (Poisson 20/s, mixed sizes) to serve after "
                          "the timed steps, reported as p50/p99 latency; 0 = skip, 512 = full mix")
@@ -596,6 +645,37 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
+    # ---- lockstep batches (RECON_OPT_BATCH_GROUP): the same B solves as one graph whose groups
+    # share their FP64 weight launches; IRLS iterations/s per group size (same conditions as the
+    # timed steps) and the shared sweep launch timed inside the step (event nodes of the graph)
+    lockstep = None
+    if B > 1 and args.batch_modes > 0:
+        lockstep = {"groups": {}}
+        inv_kind = [recon.recon_profile_name(k) for k in range(recon.PROF_KINDS)].index("hpd_inverse")
+        for g in sorted({1, 2, B}):
+            recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, g)
+            recon.recon_profile(ctx.h, 1 << inv_kind)
+            step()
+            torch.cuda.synchronize(dev)
+            g_ms = timed(step, args.batch_modes)
+            inv_ms, inv_n = recon.recon_profile_read(ctx.h, inv_kind)
+            recon.recon_profile(ctx.h, 0)
+            per_launch_us = 1000.0 * inv_ms / inv_n if inv_n else None
+            mats = min(g, B)
+            ent = {"irls_iters_per_s": round(args.batch_modes * B * w.n_irls / (g_ms / 1000.0), 1),
+                   "sweep_launches_per_step": inv_n, "matrices_per_sweep_launch": mats}
+            if per_launch_us:
+                gfl = mats * alg_flops("hpd_inverse", w) / (per_launch_us * 1e-6) / 1e9
+                ent.update({"sweep_us_per_launch": round(per_launch_us, 1),
+                            "sweep_us_per_matrix": round(per_launch_us / mats, 1),
+                            "sweep_GFLOPs": round(gfl, 1),
+                            "sweep_frac_of_fp64_nominal": round(gfl / FP64_NOMINAL_GFLOPS, 4)})
+            lockstep["groups"][str(g)] = ent
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, 0)
+        lockstep["note"] = ("recon_solve_batch with RECON_OPT_BATCH_GROUP = g: per IRLS iteration "
+                            "one Lanczos / eps / sweep launch per group of g solves; the headline "
+                            "value runs the independent slots (g = 0), measured faster")
+
     # ---- T2 maps of the reconstructed series (recon_t2fit), timed alone with events
     t2_map = torch.empty(tuple(outs[0].shape[1:]), dtype=torch.float32, device=dev)
     t2_reps = 20
@@ -676,6 +756,7 @@ def main():
                         "like the device-timed ones (L2 flushed before it, outside its events) "
                         "plus its host-device copies"},
         "clocks": clocks,
+        "lockstep_batch": lockstep,
         "t2fit": {"us_per_map": round(t2_us, 2), "pixels": int(t2_map.numel()),
                   "foreground_pixels": t2_fg, "gauss_newton_steps": 20,
                   "note": "mono-exponential T2 map of one reconstructed series, synchronous call "
@@ -687,6 +768,8 @@ def main():
         line["coils"] = run_coils(args.coil_steps, local_rank)
     if args.vol_steps > 0:
         line["vol"] = run_vol(args.vol_steps, local_rank)
+    if args.p07_steps > 0:
+        line["p07"] = run_p07(args.p07_steps, local_rank)
     if args.variant_steps > 0:
         line["variants"] = run_variants(args.variant_steps, local_rank)
     if not args.no_cpu_baseline:

@@ -172,6 +172,18 @@ int recon_poll(recon_ctx* c, int ticket, int* done);
  *   own streams; with several groups the groups' weight launches take turns, so each overlaps
  *   the other groups' CG. Results are bitwise identical to solving each problem alone. */
 #define RECON_OPT_BATCH_GROUP 7
+/* RECON_OPT_AUTOTUNE_FFT (default off): with RECON_OPT_AUTOTUNE on, the autotuner also picks the
+ *   radix schedule of the column passes' Stockham transforms (lengths other than the register
+ *   transforms' 128 and 256): schedule 0 takes radix 8 whenever the remaining length allows
+ *   (fewest passes), schedule 1 takes radix 4 before 8 (more passes, fewer registers per
+ *   butterfly). Each (tile width, schedule) pair is timed on the first solve of a shape. Unlike
+ *   the tile width, the schedule changes the order of the FP32 operations, so results move at
+ *   the FP32 rounding level with the choice (each schedule is parity-tested against the FP64
+ *   reference); a cache file (recon_tile_cache) makes the choice reproducible.
+ * RECON_OPT_FFT_SCHEDULE (testing; default -1): -1 uses the tuned (or default) schedule, 0 or 1
+ *   forces that schedule on the column passes of the CG operator. */
+#define RECON_OPT_AUTOTUNE_FFT 8
+#define RECON_OPT_FFT_SCHEDULE 9
 int recon_set_option(recon_ctx* c, int option, int value);
 
 
@@ -390,12 +402,16 @@ int recon_apply_normal_variant(recon_ctx* c, recon_dims d, recon_filter f, int v
                                void* y);
 
 /* ---- autotuner (RECON_OPT_AUTOTUNE) ----
- * Autotuner cache file: reads the choices stored in `path` (lines "P Q T R coils colC depthC"; a
- * missing file is an empty cache) into the context and appends every new choice to it. NULL
- * stops appending. RECON_EINVAL on a malformed entry. */
+ * Autotuner cache file: reads the choices stored in `path` (lines "P Q T R coils colC depthC
+ * [colS depthS]"; a missing file is an empty cache) into the context and appends every new
+ * choice to it. NULL stops appending. RECON_EINVAL on a malformed entry. */
 int recon_tile_cache(recon_ctx* c, const char* path);
 /* The tile widths the context uses for a shape (R = 1 for image series; 0 = not tuned yet). */
 int recon_tile_choice(recon_ctx* c, recon_dims3 d, int n_coils, int* colC, int* depthC);
+/* The radix schedules (0 or 1) of the length-P and depth column passes the context uses for a
+ * shape; -1 = not tuned yet. Cache lines carry them as two more fields ("... colC depthC colS
+ * depthS"); lines without them mean schedule 0. */
+int recon_fft_schedule_choice(recon_ctx* c, recon_dims3 d, int n_coils, int* colS, int* depthS);
 
 /* ---- measurement ---- */
 

@@ -304,12 +304,20 @@ struct SmallDFT<8, INV> {
     }
 };
 
-__host__ __device__ constexpr int fft_radix_at(int n, int p) {
-    return ((n / p) % 8 == 0) ? 8 : ((n / p) % 4 == 0) ? 4 : ((n / p) % 3 == 0) ? 3 : 2;
+// Radix schedules of the Stockham passes: the radix of the pass at span p for length n.
+// Schedule 0: radix 8 whenever the remaining length allows it, then 4, 3, 2 (fewest passes).
+// Schedule 1: radix 4 before 8 (more passes over shared memory, fewer registers and fewer bank
+// conflicts per butterfly). Both are exact factorisations of the same DFT; results differ only
+// in FP32 rounding.
+__host__ __device__ constexpr int fft_radix_at(int n, int p, int sched = 0) {
+    return sched == 1
+               ? (((n / p) % 4 == 0) ? 4 : ((n / p) % 8 == 0) ? 8 : ((n / p) % 3 == 0) ? 3 : 2)
+               : (((n / p) % 8 == 0) ? 8 : ((n / p) % 4 == 0) ? 4 : ((n / p) % 3 == 0) ? 3 : 2);
 }
-__host__ __device__ constexpr int fft_num_stages(int n, int p = 1) {
-    return p >= n ? 0 : 1 + fft_num_stages(n, p * fft_radix_at(n, p));
+__host__ __device__ constexpr int fft_num_stages(int n, int p = 1, int sched = 0) {
+    return p >= n ? 0 : 1 + fft_num_stages(n, p * fft_radix_at(n, p, sched), sched);
 }
+
 
 // One Stockham autosort pass (radix R, span p) over `nseq` independent length-N sequences.
 // Element e of sequence s lives at buf[s * ss + e * es]. `tw` holds e^{-2 pi i j / N}, j < N,
@@ -348,14 +356,14 @@ RECON_DEV void stockham_pass(const float2* __restrict__ src, float2* __restrict_
 
 // Full length-N FFT of nseq sequences, ping-ponging between a and b (both in shared memory).
 // Returns the buffer that holds the result. Ends with __syncthreads().
-template <int N, bool INV, bool SEQ_FAST, int P = 1>
+template <int N, bool INV, bool SEQ_FAST, int P = 1, int SCHED = 0>
 RECON_DEV float2* fft_smem(float2* a, float2* b, int nseq, int ss, int es, const float2* tw) {
     if constexpr (P >= N) {
         return a;
     } else {
-        constexpr int R = fft_radix_at(N, P);
+        constexpr int R = fft_radix_at(N, P, SCHED);
         stockham_pass<N, R, INV, SEQ_FAST>(a, b, P, nseq, ss, es, tw);
         __syncthreads();
-        return fft_smem<N, INV, SEQ_FAST, P * R>(b, a, nseq, ss, es, tw);
+        return fft_smem<N, INV, SEQ_FAST, P * R, SCHED>(b, a, nseq, ss, es, tw);
     }
 }

@@ -155,8 +155,9 @@ coil_row_fwd_kernel(const float2* __restrict__ r, float2* __restrict__ p, float2
     }
 }
 
-// Column pass over an N x C tile (frame blockIdx.y, columns C*blockIdx.x ..).
-template <int N, int MODE, int C>
+// Column pass over an N x C tile (frame blockIdx.y, columns C*blockIdx.x ..), Stockham passes
+// in radix schedule S (fft_radix_at).
+template <int N, int MODE, int C, int S>
 __global__ void __launch_bounds__(kThreads)
 col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
            int Q, int mask_frames, float scale, const float2* __restrict__ tw_g) {
@@ -189,18 +190,18 @@ col_kernel(const void* in_, float2* out, const uint8_t* __restrict__ mask,
     __syncthreads();
     float2* res;
     if constexpr (MODE == COL_FWD) {
-        res = fft_smem<N, false, true>(a, b, C, 1, C, tw);
+        res = fft_smem<N, false, true, 1, S>(a, b, C, 1, C, tw);
     } else if constexpr (MODE == COL_INV || MODE == COL_ADJ_C64 || MODE == COL_ADJ_BF16) {
-        res = fft_smem<N, true, true>(a, b, C, 1, C, tw);
+        res = fft_smem<N, true, true, 1, S>(a, b, C, 1, C, tw);
     } else {  // COL_MASK_OP
-        float2* f = fft_smem<N, false, true>(a, b, C, 1, C, tw);
+        float2* f = fft_smem<N, false, true, 1, S>(a, b, C, 1, C, tw);
         for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
             const int i = e / C, c = e % C;
             const uint8_t m = mask[mbase + (size_t)i * Q + c0 + c];
             f[e] = m ? cscale(f[e], scale) : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        res = fft_smem<N, true, true>(f, f == a ? b : a, C, 1, C, tw);
+        res = fft_smem<N, true, true, 1, S>(f, f == a ? b : a, C, 1, C, tw);
     }
     pdl_trigger();
     const float osc = (MODE == COL_FWD || MODE == COL_INV) ? scale : 1.f;
@@ -602,10 +603,10 @@ cudaError_t row_fft(int n, const float2* in, float2* out, int nrows, float scale
     }
 }
 
-template <int N, int MODE, int C>
+template <int N, int MODE, int C, int S>
 cudaError_t col_launch(int Q, int T, int mask_frames, const void* in, float2* out,
                        const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
-    auto k = col_kernel<N, MODE, C>;
+    auto k = col_kernel<N, MODE, C, S>;
     cudaError_t e = set_smem(k, col_smem<N, C>());
     if (e != cudaSuccess) return e;
     dim3 grid(Q / C, T);
@@ -613,29 +614,42 @@ cudaError_t col_launch(int Q, int T, int mask_frames, const void* in, float2* ou
                       scale, tw);
 }
 
-template <int N, int MODE>
-cudaError_t col_launch_c(int C, int Q, int T, int mask_frames, const void* in, float2* out,
-                         const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
+// Tile width C (rounded down to what Q and the shared memory allow; 8 at least) and radix
+// schedule S (the adjoint's one-off passes keep schedule 0).
+template <int N, int MODE, int S>
+cudaError_t col_launch_cs(int C, int Q, int T, int mask_frames, const void* in, float2* out,
+                          const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
     if constexpr (col_tile_ok<N, 32>()) {
         if (C >= 32 && Q % 32 == 0)
-            return col_launch<N, MODE, 32>(Q, T, mask_frames, in, out, mask, scale, tw, st);
+            return col_launch<N, MODE, 32, S>(Q, T, mask_frames, in, out, mask, scale, tw, st);
     }
     if constexpr (col_tile_ok<N, 16>()) {
         if (C >= 16 && Q % 16 == 0)
-            return col_launch<N, MODE, 16>(Q, T, mask_frames, in, out, mask, scale, tw, st);
+            return col_launch<N, MODE, 16, S>(Q, T, mask_frames, in, out, mask, scale, tw, st);
     }
-    return col_launch<N, MODE, kColTile>(Q, T, mask_frames, in, out, mask, scale, tw, st);
+    return col_launch<N, MODE, kColTile, S>(Q, T, mask_frames, in, out, mask, scale, tw, st);
+}
+
+template <int N, int MODE>
+cudaError_t col_launch_c(int C, int S, int Q, int T, int mask_frames, const void* in, float2* out,
+                         const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
+    if constexpr (MODE == COL_FWD || MODE == COL_INV || MODE == COL_MASK_OP) {
+        if (S == 1)
+            return col_launch_cs<N, MODE, 1>(C, Q, T, mask_frames, in, out, mask, scale, tw, st);
+    }
+    return col_launch_cs<N, MODE, 0>(C, Q, T, mask_frames, in, out, mask, scale, tw, st);
 }
 
 // `T` transforms (frames), the mask of frame f being mask frame f % mask_frames; tiles of C
-// columns (rounded down to what Q and the shared memory allow; 8 at least).
+// columns, radix schedule S.
 template <int MODE>
-cudaError_t col_pass(int n, int C, int Q, int T, int mask_frames, const void* in, float2* out,
-                     const uint8_t* mask, float scale, const float2* tw, cudaStream_t st) {
+cudaError_t col_pass(int n, int C, int S, int Q, int T, int mask_frames, const void* in,
+                     float2* out, const uint8_t* mask, float scale, const float2* tw,
+                     cudaStream_t st) {
     switch (n) {
 #define CASE(N)                                                                              \
     case N:                                                                                  \
-        return col_launch_c<N, MODE>(C, Q, T, mask_frames, in, out, mask, scale, tw, st);
+        return col_launch_c<N, MODE>(C, S, Q, T, mask_frames, in, out, mask, scale, tw, st);
         RECON_FFT_SIZES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
@@ -659,6 +673,8 @@ bool fft_size_supported(int n) {
 // Column tile for the length-P passes (depth = false) or the depth passes of a volume: the
 // width the caller chose in Dims (autotuner), else 8 for image series and the wide default for
 // volumes.
+int col_sched_for(const Dims& d, bool depth) { return depth ? d.depthS : d.colS; }
+
 int col_tile_for(const Dims& d, bool depth) {
     const int chosen = depth ? d.depthC : d.colC;
     if (chosen > 0) return chosen;
@@ -680,13 +696,13 @@ cudaError_t launch_fft2(const Dims& d, const Twiddles& tw, const float2* x, floa
     cudaError_t e = inv ? row_fft<true>(d.Q, x, y, slices * d.P, sq, tw.twQ, st)
                         : row_fft<false>(d.Q, x, y, slices * d.P, sq, tw.twQ, st);
     if (e != cudaSuccess) return e;
-    e = inv ? col_pass<COL_INV>(d.P, cP, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st)
-            : col_pass<COL_FWD>(d.P, cP, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st);
+    e = inv ? col_pass<COL_INV>(d.P, cP, 0, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st)
+            : col_pass<COL_FWD>(d.P, cP, 0, d.Q, slices, slices, y, y, nullptr, sp, tw.twP, st);
     if (e != cudaSuccess || d.R == 1) return e;
     const float sr = 1.0f / sqrtf((float)d.R);
     const int pq = d.P * d.Q;
-    return inv ? col_pass<COL_INV>(d.R, cR, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st)
-               : col_pass<COL_FWD>(d.R, cR, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st);
+    return inv ? col_pass<COL_INV>(d.R, cR, 0, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st)
+               : col_pass<COL_FWD>(d.R, cR, 0, pq, d.T, d.T, y, y, nullptr, sr, tw.twR, st);
 }
 
 cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int b_bf16,
@@ -697,14 +713,14 @@ cudaError_t launch_adjoint(const Dims& d, const Twiddles& tw, const void* b, int
         // masked depth IDFT (with the whole 1/sqrt(PQR)), then the column IDFT of every slice
         const int pq = d.P * d.Q, slices = d.T * d.R;
         const int cP = col_tile_for(d, false), cR = col_tile_for(d, true);
-        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.R, cR, pq, d.T, d.T, b, t, mask, sc, tw.twR, st)
-                   : col_pass<COL_ADJ_C64>(d.R, cR, pq, d.T, d.T, b, t, mask, sc, tw.twR, st);
+        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.R, cR, 0, pq, d.T, d.T, b, t, mask, sc, tw.twR, st)
+                   : col_pass<COL_ADJ_C64>(d.R, cR, 0, pq, d.T, d.T, b, t, mask, sc, tw.twR, st);
         if (e != cudaSuccess) return e;
-        e = col_pass<COL_INV>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+        e = col_pass<COL_INV>(d.P, cP, 0, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
     } else {
         const int cP = col_tile_for(d, false);
-        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, cP, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st)
-                   : col_pass<COL_ADJ_C64>(d.P, cP, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st);
+        e = b_bf16 ? col_pass<COL_ADJ_BF16>(d.P, cP, 0, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st)
+                   : col_pass<COL_ADJ_C64>(d.P, cP, 0, d.Q, d.T, d.T, b, t, mask, sc, tw.twP, st);
     }
     if (e != cudaSuccess) return e;
     return row_fft<true>(d.Q, t, x, d.T * d.rows(), 1.0f, tw.twQ, st);
@@ -765,7 +781,7 @@ cudaError_t launch_coil_row_fwd(const Dims& d, const Twiddles& tw, const float2*
 cudaError_t launch_adjoint_coils_cols(const Dims& d, const Twiddles& tw, const void* b,
                                       const uint8_t* mask, float2* t, cudaStream_t st) {
     const float sc = 1.0f / sqrtf((float)d.P * (float)d.Q);
-    return col_pass<COL_ADJ_C64>(d.P, col_tile_for(d, false), d.Q, d.T * d.nc, d.T, b, t, mask,
+    return col_pass<COL_ADJ_C64>(d.P, col_tile_for(d, false), 0, d.Q, d.T * d.nc, d.T, b, t, mask,
                                  sc, tw.twP, st);
 }
 
@@ -782,16 +798,16 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
         cudaError_t e =
             reg128 ? launch_pdl(col128_kernel<false>, dim3(d.Q / 16, slices), dim3(128), 0, st, t,
                                 d.Q, tw.twP)
-                   : col_pass<COL_FWD>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
+                   : col_pass<COL_FWD>(d.P, cP, d.colS, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP, st);
         if (e != cudaSuccess) return e;
         e = reg64 ? launch_pdl(col_mask_64_kernel, dim3(pq / 32, d.T), dim3(256), 0, st, t, mask, pq,
                                sc3, tw.twR)
-                  : col_pass<COL_MASK_OP>(d.R, cR, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
+                  : col_pass<COL_MASK_OP>(d.R, cR, d.depthS, pq, d.T, d.T, t, t, mask, sc3, tw.twR, st);
         if (e != cudaSuccess) return e;
         return reg128 ? launch_pdl(col128_kernel<true>, dim3(d.Q / 16, slices), dim3(128), 0, st, t,
                                    d.Q, tw.twP)
-                      : col_pass<COL_INV>(d.P, cP, d.Q, slices, slices, t, t, nullptr, 1.0f, tw.twP,
-                                          st);
+                      : col_pass<COL_INV>(d.P, cP, d.colS, d.Q, slices, slices, t, t, nullptr, 1.0f,
+                                          tw.twP, st);
     }
     const float sc = 1.0f / ((float)d.P * (float)d.Q);
     const int frames = d.T * d.nc;  // coil-major: the mask of frame f is mask frame f % T
@@ -801,8 +817,8 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
     if (col_register(d, false))
         return launch_pdl(col_mask_128_kernel, dim3(d.Q / 16, frames), dim3(128), 0, st, t, mask,
                           d.Q, d.T, sc, tw.twP);
-    return col_pass<COL_MASK_OP>(d.P, col_tile_for(d, false), d.Q, frames, d.T, t, t, mask, sc,
-                                 tw.twP, st);
+    return col_pass<COL_MASK_OP>(d.P, col_tile_for(d, false), d.colS, d.Q, frames, d.T, t, t, mask,
+                                 sc, tw.twP, st);
 }
 
 bool col_mask_parts_supported(const Dims& d) {

@@ -27,15 +27,19 @@ namespace recon {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+// Threads of the row kernel: 512 (its DFT outputs spread over 16 warps) while the window sums of
+// all pairs fit in the registers that leaves; 256 for M >= 5 (15 or 21 compensated pairs).
+__host__ __device__ constexpr int row_threads(int M) { return M >= 5 ? 256 : 512; }
 
 // kLo = false (only where the low parts do not fit in shared memory: M = 6 with 512-point rows
 // and more than 12 frames): each window sum is rounded once to FP32 (hi + lo) before the DFT,
-// whose terms and tree stay compensated.
+// whose terms and tree stay compensated. tab: the twiddles of every output lag d2 are laid out
+// contiguously in c ([L2][Q], built once per CTA), so that the lanes of a warp read consecutive
+// entries; otherwise lane c reads w^(d2 c mod Q) from the length-Q table (bank conflicts for
+// even d2). The same values either way.
 template <int M, bool kLo>
-__global__ void __launch_bounds__(kThreads)
-gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int circ,
+__global__ void __launch_bounds__(row_threads(M))
+gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int circ, int tab,
                  const float2* __restrict__ twQ, double2* __restrict__ Y) {
     constexpr int NP = M * (M + 1) / 2;
     extern __shared__ float2 sm[];
@@ -45,8 +49,16 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int 
     float2* qp = xs + (size_t)T * Q;         // [NP][Q] pair products (compensated sum, high part)
     float2* ql = qp + (size_t)NP * Q;        // [NP][Q] their low parts (kLo)
     float2* tw = ql + (kLo ? (size_t)NP * Q : 0);  // [Q]
+    float2* dtab = tw + Q;                   // [L2][Q] (tab)
     const int r1 = blockIdx.x;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) tw[i] = twQ[i];
+    if (tab) {
+        for (int e = threadIdx.x; e < L2 * Q; e += blockDim.x) {
+            const int i2 = e / Q, c = e % Q;
+            const int d2m = (i2 - (N2 - 1) + Q) % Q;
+            dtab[e] = twQ[(int)(((long long)d2m * c) % Q)];
+        }
+    }
     for (int e = threadIdx.x; e < T * Q; e += blockDim.x) {
         const int n = e / Q, c = e % Q;
         xs[e] = x[((size_t)n * P + r1) * Q + c];
@@ -88,16 +100,17 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int 
     // (hi + lo) w added to a compensated (hi, lo) pair, then a TwoSum shuffle tree
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nout = NP * L2;
-    for (int o = warp; o < nout; o += kWarps) {
+    for (int o = warp; o < nout; o += row_threads(M) / 32) {
         const int pr = o / L2, i2 = o % L2;
         const int d2m = (i2 - (N2 - 1) + Q) % Q;
         const float2* qrow = qp + (size_t)pr * Q;
         const float2* qlow = ql + (size_t)pr * Q;
+        const float2* trow = dtab + (size_t)i2 * Q;
         int idx = (d2m * lane) % Q;
         const int step = (d2m * 32) % Q;
         float2 y = make_float2(0.f, 0.f), yl = make_float2(0.f, 0.f);
         for (int c = lane; c < Q; c += 32) {
-            const float2 wt = tw[idx];
+            const float2 wt = tab ? trow[c] : tw[idx];
             const float2 t = cmul(qrow[c], wt);
             comp_add(y.x, yl.x, t.x);
             comp_add(y.y, yl.y, t.y);
@@ -240,15 +253,24 @@ __global__ void gram_fill3_kernel(const double2* __restrict__ Z, int R, int N1, 
 
 constexpr size_t kGramSmemMax = 220 * 1024;
 
-size_t gram_smem_lo(const Dims& d, bool lo) {
-    return ((size_t)d.T * d.Q + (lo ? 2 : 1) * (size_t)d.npair() * d.Q + d.Q) * sizeof(float2);
+size_t gram_smem_cfg(const Dims& d, bool lo, bool tab) {
+    return ((size_t)d.T * d.Q + (lo ? 2 : 1) * (size_t)d.npair() * d.Q + d.Q +
+            (tab ? (size_t)d.L2() * d.Q : 0)) * sizeof(float2);
+}
+
+// The shared-memory layout of the row kernel: the low parts first (accuracy), then the twiddle
+// rows (speed), each where it fits.
+void gram_cfg(const Dims& d, bool* lo, bool* tab) {
+    *lo = gram_smem_cfg(d, true, false) <= kGramSmemMax;
+    *tab = gram_smem_cfg(d, *lo, true) <= kGramSmemMax;
 }
 
 }  // namespace
 
 size_t gram_smem(const Dims& d) {
-    const size_t with_lo = gram_smem_lo(d, true);
-    return with_lo <= kGramSmemMax ? with_lo : gram_smem_lo(d, false);
+    bool lo, tab;
+    gram_cfg(d, &lo, &tab);
+    return gram_smem_cfg(d, lo, tab);
 }
 
 // One CTA per image row; the scratch holds the row DFTs Y[pair][d2][row] (complex128) and, for
@@ -266,15 +288,16 @@ cudaError_t launch_gram(const Dims& d, const Twiddles& tw, const float2* x, doub
     if (nblocks != d.rows()) return cudaErrorInvalidValue;
     const size_t smem = gram_smem(d);
     if (smem > kGramSmemMax) return cudaErrorInvalidValue;
-    const bool lo = smem == gram_smem_lo(d, true);
+    bool lo, tab;
+    gram_cfg(d, &lo, &tab);
 #define CASE(MM)                                                                                 \
     case MM: {                                                                                   \
         auto k = lo ? gram_rows_kernel<MM, true> : gram_rows_kernel<MM, false>;                  \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem);                                         \
         if (e != cudaSuccess) return e;                                                          \
-        k<<<d.rows(), kThreads, smem, st>>>(x, d.T, d.rows(), d.Q, d.N2, d.circ, tw.twQ,       \
-                                            lag_part);                                           \
+        k<<<d.rows(), row_threads(MM), smem, st>>>(x, d.T, d.rows(), d.Q, d.N2, d.circ, (int)tab,\
+                                               tw.twQ, lag_part);                                \
         break;                                                                                   \
     }
     switch (d.M) {

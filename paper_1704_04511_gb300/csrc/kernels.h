@@ -24,6 +24,7 @@ struct Dims {
     int N3 = 1;  // filter taps along the depth
     int circ = 0;  // 1: lifting circular in time as well (the fully circulant GIRAF form)
     int colC = 0, depthC = 0;  // column tiles of the column / depth passes (0 = default)
+    int colS = 0, depthS = 0;  // radix schedules of their Stockham passes (fft_radix_at)
     int k() const { return circ ? T : T - M + 1; }
     int npair() const { return M * (M + 1) / 2; }
     int L1() const { return 2 * N1 - 1; }
@@ -83,6 +84,9 @@ int num_sms();
 bool fft_size_supported(int n);
 // Column tile the length-P (depth = false) or depth passes of `d` use (fft.cu).
 int col_tile_for(const Dims& d, bool depth);
+// Radix schedule of those passes' Stockham transforms (0 or 1, see fft_radix_at).
+int col_sched_for(const Dims& d, bool depth);
+constexpr int kFftSchedules = 2;
 // True where the column stage of the CG operator runs register transforms without tiles.
 bool col_register(const Dims& d, bool depth);
 // Message returned by recon_last_error(NULL) (calls that have no context).

@@ -86,7 +86,7 @@ struct recon_ctx {
         int T, P, Q, N1, N2, M, irls, cg, bf16, method, R, N3;
         double lambda, p, gamma, eps0_frac;
         const void *kspace, *masks, *out, *coils;
-        int nc, coil_proj, circ, variant, colC, depthC, three_pass;
+        int nc, coil_proj, circ, variant, colC, depthC, colS, depthS, three_pass;
         unsigned int prof;
         unsigned long ws_gen;
     };
@@ -107,7 +107,12 @@ struct recon_ctx {
     GraphProf* batch_gprof = nullptr;
     std::vector<unsigned char> batch_key;
     std::vector<cudaEvent_t> batch_ev;  // fork / join events of the capture
-    std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tiles;
+    bool autotune_fft = false;         // the autotuner also picks the radix schedule (RECON_OPT_AUTOTUNE_FFT)
+    int fft_sched = -1;                // forced radix schedule of the column passes (-1 = tuned / 0)
+    struct TileChoice {
+        int colC = 0, depthC = 0, colS = 0, depthS = 0;
+    };
+    std::map<std::tuple<int, int, int, int, int>, TileChoice> tiles;
     std::string tile_cache;            // file the tuned choices are appended to (may be empty)
     struct Slot {
         cudaStream_t stream = nullptr;
@@ -713,13 +718,22 @@ struct Solve {
 // cache file is set (recon_tile_cache), appended to it and read back by later contexts.
 int autotune_tiles(recon_ctx* c, Dims* d, const Twiddles& tw, float2* t, const uint8_t* mask) {
     const auto key = std::make_tuple(d->P, d->Q, d->T, d->R, d->nc);
+    auto apply_forced = [&]() {
+        if (c->fft_sched >= 0) d->colS = d->depthS = c->fft_sched;
+    };
     auto it = c->tiles.find(key);
     if (it != c->tiles.end()) {
-        d->colC = it->second.first;
-        d->depthC = it->second.second;
+        d->colC = it->second.colC;
+        d->depthC = it->second.depthC;
+        d->colS = it->second.colS;
+        d->depthS = it->second.depthS;
+        apply_forced();
         return RECON_OK;
     }
-    if (!c->autotune) return RECON_OK;
+    if (!c->autotune) {
+        apply_forced();
+        return RECON_OK;
+    }
     cudaEvent_t e0, e1;
     RC_CUDA(cudaEventCreate(&e0));
     RC_CUDA(cudaEventCreate(&e1));
@@ -735,45 +749,56 @@ int autotune_tiles(recon_ctx* c, Dims* d, const Twiddles& tw, float2* t, const u
     };
     cudaError_t err = cudaSuccess;
     const int cand[3] = {8, 16, 32};
+    // radix schedules tried (the Stockham passes' factorisation order), when asked for
+    const int nsched = c->autotune_fft ? recon::kFftSchedules : 1;
     Dims dd = *d;
-    // the length-P passes (those in register transforms have no tiles to choose)
+    // the length-P passes (those in register transforms have no tiles or schedules to choose)
     if (!recon::col_register(*d, false)) {
         float best = 1e30f;
-        int bestC = recon::col_tile_for(*d, false);
-        for (int C : cand) {
-            if (d->Q % C) continue;
-            dd.colC = C;
-            float ms = 0.f;
-            err = time_it(dd, &ms);
-            if (err != cudaSuccess) break;
-            if (ms < best) { best = ms; bestC = C; }
-        }
+        int bestC = recon::col_tile_for(*d, false), bestS = 0;
+        for (int S = 0; S < nsched && err == cudaSuccess; ++S)
+            for (int C : cand) {
+                if (d->Q % C) continue;
+                dd.colC = C;
+                dd.colS = S;
+                float ms = 0.f;
+                err = time_it(dd, &ms);
+                if (err != cudaSuccess) break;
+                if (ms < best) { best = ms; bestC = C; bestS = S; }
+            }
         dd.colC = bestC;
+        dd.colS = bestS;
     }
     if (err == cudaSuccess && d->R > 1 && !recon::col_register(*d, true)) {
         float best = 1e30f;
-        int bestC = recon::col_tile_for(*d, true);
-        for (int C : cand) {
-            if ((d->P * d->Q) % C) continue;
-            dd.depthC = C;
-            float ms = 0.f;
-            err = time_it(dd, &ms);
-            if (err != cudaSuccess) break;
-            if (ms < best) { best = ms; bestC = C; }
-        }
+        int bestC = recon::col_tile_for(*d, true), bestS = 0;
+        for (int S = 0; S < nsched && err == cudaSuccess; ++S)
+            for (int C : cand) {
+                if ((d->P * d->Q) % C) continue;
+                dd.depthC = C;
+                dd.depthS = S;
+                float ms = 0.f;
+                err = time_it(dd, &ms);
+                if (err != cudaSuccess) break;
+                if (ms < best) { best = ms; bestC = C; bestS = S; }
+            }
         dd.depthC = bestC;
+        dd.depthS = bestS;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(c, err, "autotuner");
     d->colC = dd.colC;
     d->depthC = dd.depthC;
-    c->tiles[key] = {d->colC, d->depthC};
+    d->colS = dd.colS;
+    d->depthS = dd.depthS;
+    c->tiles[key] = {d->colC, d->depthC, d->colS, d->depthS};
     if (!c->tile_cache.empty()) {
         std::ofstream f(c->tile_cache, std::ios::app);
         if (f) f << d->P << ' ' << d->Q << ' ' << d->T << ' ' << d->R << ' ' << d->nc << ' '
-                 << d->colC << ' ' << d->depthC << '\n';
+                 << d->colC << ' ' << d->depthC << ' ' << d->colS << ' ' << d->depthS << '\n';
     }
+    apply_forced();
     return RECON_OK;
 }
 
@@ -879,6 +904,7 @@ recon_ctx::GraphKey graph_key(recon_ctx* c, const Solve& sv) {
     k.kspace = sv.kspace; k.masks = sv.masks; k.out = sv.x; k.ws_gen = c->ws_gen;
     k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
     k.circ = sv.d.circ; k.variant = sv.variant; k.colC = sv.d.colC; k.depthC = sv.d.depthC;
+    k.colS = sv.d.colS; k.depthS = sv.d.depthS;
     k.three_pass = c->three_pass;
     k.prof = c->prof;
     return k;
@@ -1439,8 +1465,10 @@ int weight_args(recon_ctx* c, const void* G_in, double eps_in, double p, int met
     return RECON_OK;
 }
 
-int apply_normal_impl(recon_ctx* c, const Dims& d, const uint8_t* masks, const void* S,
+int apply_normal_impl(recon_ctx* c, const Dims& d0, const uint8_t* masks, const void* S,
                       double lambda, const void* x, void* y) {
+    Dims d = d0;
+    if (c->fft_sched >= 0) d.colS = d.depthS = c->fft_sched;  // forced radix schedule (tests)
     int rc;
     rc = set_device(c);
     if (rc) return rc;
@@ -2188,6 +2216,12 @@ int recon_set_option(recon_ctx* c, int option, int value) {
         case RECON_OPT_THREE_PASS: c->three_pass = value != 0; return RECON_OK;
         case RECON_OPT_INJECT_BARRIER_FAULT: c->inject_barrier_fault = value != 0; return RECON_OK;
         case RECON_OPT_TEST_WITHHOLD_ARRIVAL: c->withhold_arrival = value != 0; return RECON_OK;
+        case RECON_OPT_AUTOTUNE_FFT: c->autotune_fft = value != 0; return RECON_OK;
+        case RECON_OPT_FFT_SCHEDULE:
+            if (value < -1 || value >= recon::kFftSchedules)
+                return fail(c, RECON_EINVAL, "radix schedule must be -1 (tuned), 0 or 1");
+            c->fft_sched = value;
+            return RECON_OK;
         case RECON_OPT_BATCH_GROUP:
             if (value < 0 || value > RECON_MAX_BATCH) return fail(c, RECON_EINVAL, "need 0 <= group <= RECON_MAX_BATCH");
             c->batch_group = value;
@@ -2205,12 +2239,18 @@ int recon_tile_cache(recon_ctx* c, const char* path) {
     std::ifstream f(path);
     std::string line;
     auto width_ok = [](int v) { return v == 0 || v == 8 || v == 16 || v == 32; };
+    auto sched_ok = [](int v) { return v >= 0 && v < recon::kFftSchedules; };
     while (f && std::getline(f, line)) {
         std::istringstream ls(line);
-        int P, Q, T, R, nc, colC, depthC;
+        int P, Q, T, R, nc, colC, depthC, colS = 0, depthS = 0;
         if (!(ls >> P >> Q >> T >> R >> nc >> colC >> depthC) || !width_ok(colC) || !width_ok(depthC))
             return fail(c, RECON_EINVAL, "tile cache: malformed entry in " + std::string(path));
-        c->tiles[std::make_tuple(P, Q, T, R, nc)] = {colC, depthC};
+        // the radix schedules (two more fields) are optional: entries without them use schedule 0
+        if (ls >> colS) {
+            if (!(ls >> depthS) || !sched_ok(colS) || !sched_ok(depthS))
+                return fail(c, RECON_EINVAL, "tile cache: malformed entry in " + std::string(path));
+        }
+        c->tiles[std::make_tuple(P, Q, T, R, nc)] = {colC, depthC, colS, depthS};
     }
     c->tile_cache = path;
     return RECON_OK;
@@ -2223,8 +2263,20 @@ int recon_tile_choice(recon_ctx* c, recon_dims3 dd, int n_coils, int* colC, int*
         *colC = *depthC = 0;
         return RECON_OK;
     }
-    *colC = it->second.first;
-    *depthC = it->second.second;
+    *colC = it->second.colC;
+    *depthC = it->second.depthC;
+    return RECON_OK;
+}
+
+int recon_fft_schedule_choice(recon_ctx* c, recon_dims3 dd, int n_coils, int* colS, int* depthS) {
+    if (!c || !colS || !depthS) return RECON_EINVAL;
+    auto it = c->tiles.find(std::make_tuple(dd.P, dd.Q, dd.T, dd.R, n_coils));
+    if (it == c->tiles.end()) {
+        *colS = *depthS = -1;
+        return RECON_OK;
+    }
+    *colS = it->second.colS;
+    *depthS = it->second.depthS;
     return RECON_OK;
 }
 

@@ -49,7 +49,7 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_bytes_needed3", "recon_solve3", "recon_adjoint3", "recon_fft3", "recon_gram3",
             "recon_weight3", "recon_apply_normal3", "recon_solve_variant", "recon_gram_variant",
             "recon_voxel_weight", "recon_weight_direct", "recon_apply_normal_variant",
-            "recon_tile_cache", "recon_tile_choice")
+            "recon_tile_cache", "recon_tile_choice", "recon_fft_schedule_choice")
 
 PROF_KINDS = 15
 
@@ -144,6 +144,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_apply_normal_variant": (i, [vp, dims, filt, i, vp, vp, d, vp, vp]),
             "recon_tile_cache": (i, [vp, ctypes.c_char_p]),
             "recon_tile_choice": (i, [vp, dims3, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+            "recon_fft_schedule_choice": (i, [vp, dims3, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -270,6 +271,8 @@ RECON_OPT_THREE_PASS = 4
 RECON_OPT_INJECT_BARRIER_FAULT = 5
 RECON_OPT_TEST_WITHHOLD_ARRIVAL = 6
 RECON_OPT_BATCH_GROUP = 7
+RECON_OPT_AUTOTUNE_FFT = 8
+RECON_OPT_FFT_SCHEDULE = 9
 
 
 def recon_tile_cache(ctx, path) -> None:
@@ -287,6 +290,21 @@ def recon_tile_choice(ctx, shape, n_coils: int = 1):
     a, b = ctypes.c_int(0), ctypes.c_int(0)
     _check(ctx, load_library().recon_tile_choice(ctx, recon_dims3(P=P, Q=Q, R=R, T=T), int(n_coils),
                                                  ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def recon_fft_schedule_choice(ctx, shape, n_coils: int = 1):
+    """(colS, depthS) radix schedules the context uses for shape (T, P, Q) or (T, R, P, Q);
+    -1 = not tuned."""
+    if len(shape) == 3:
+        T, P, Q = shape
+        R = 1
+    else:
+        T, R, P, Q = shape
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(ctx, load_library().recon_fft_schedule_choice(ctx, recon_dims3(P=P, Q=Q, R=R, T=T),
+                                                         int(n_coils), ctypes.byref(a),
+                                                         ctypes.byref(b)))
     return a.value, b.value
 
 
