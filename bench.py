@@ -74,7 +74,7 @@ ALU_KINDS = ("hpd_inverse", "lanczos")
 # benchmark workload (steady state, caches kept; profiles/hpd_sweep_kernel_s243.md gives the
 # command). Only for the kernel versions those captures measured: drop an entry when its
 # kernel changes.
-TRAFFIC_BYTES = {"hpd_inverse": 462123}
+TRAFFIC_BYTES = {"hpd_inverse": 552704}
 
 
 def alg_flops(kind: str, w) -> float:
@@ -447,6 +447,63 @@ def run_p07(steps: int, device: int) -> dict:
                     "(cuSOLVER zheevd, s = 243), direct launches (no graph)"}
 
 
+def run_many(n: int, steps: int, device: int) -> dict:
+    """recon_solve_many on the first n requests of the served mix (uneven grids, frame counts and
+    filters, shared parameters): aggregate IRLS iterations/s of the independent slots and of
+    lockstep groups whose sweep launches mix the requests' matrices, and the shared sweep's
+    per-launch time."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1704_04511_gb300 import recon
+    mix = synth.served_mix(n, rate_hz=20.0, seed=0)
+    dev = torch.device("cuda", device)
+    ks, ms, outs, filts = [], [], [], []
+    for _, w in mix:
+        pr = synth.make_problem(w)
+        ks.append(torch.from_numpy(np.ascontiguousarray(pr["kspace"], dtype=np.complex64)).to(dev))
+        ms.append(torch.from_numpy(pr["masks"]).to(dev))
+        outs.append(torch.empty(tuple(ms[-1].shape), dtype=torch.complex64, device=dev))
+        filts.append((w.N1, w.N2, w.M))
+    w0 = mix[0][1]
+    stream = torch.cuda.current_stream(dev)
+    ctx = recon.Context(device, cuda_stream=stream.cuda_stream)
+    inv_kind = [recon.recon_profile_name(k) for k in range(recon.PROF_KINDS)].index("hpd_inverse")
+    res = {}
+    try:
+        def solve():
+            recon.recon_solve_many(ctx.h, ks, ms, filts, w0.lam, w0.p, w0.n_irls, w0.n_cg, outs)
+        for g in (0, 4, n):
+            recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, g)
+            solve()
+            torch.cuda.synchronize(dev)
+            recon.recon_profile(ctx.h, 1 << inv_kind)
+            solve()
+            torch.cuda.synchronize(dev)
+            inv_ms, inv_n = recon.recon_profile_read(ctx.h, inv_kind)
+            recon.recon_profile(ctx.h, 0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                solve()
+            e1.record(stream)
+            e1.synchronize()
+            ms_step = e0.elapsed_time(e1) / steps
+            res[str(g)] = {"ms_per_batch": round(ms_step, 2),
+                           "irls_iters_per_s": round(n * w0.n_irls / (ms_step / 1000.0), 1),
+                           "sweep_launches": inv_n,
+                           "sweep_us_per_launch": round(1000.0 * inv_ms / inv_n, 1) if inv_n else None}
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, 0)
+    finally:
+        ctx.close()
+    return {"requests": n, "shapes": [list(m.shape) for m in ms], "filters": filts,
+            "groups": res,
+            "note": "recon_solve_many over the first requests of the served mix; group 0 = "
+                    "independent slots, g > 0 = lockstep groups of g sharing one sweep launch of "
+                    "matrices of different sizes per IRLS iteration"}
+
+
 def run_reference(args, rank: int):
     import synth
     if rank != 0:
@@ -496,6 +553,8 @@ def main():
                     help="time only the volume workload and print {\"vol\": ...} (profiling)")
     ap.add_argument("--vol-steps", type=int, default=2,
                     help="solves of the 128x128x64x12 volume workload to time (0 = skip)")
+    ap.add_argument("--many", type=int, default=8,
+                    help="served-mix requests solved as one uneven batch (recon_solve_many), 0 = skip")
     ap.add_argument("--p07-steps", type=int, default=1,
                     help="solves of the 256x256x16 workload at p = 0.7 to time (0 = skip)")
     ap.add_argument("--batch-modes", type=int, default=3,
@@ -770,6 +829,8 @@ def main():
         line["vol"] = run_vol(args.vol_steps, local_rank)
     if args.p07_steps > 0:
         line["p07"] = run_p07(args.p07_steps, local_rank)
+    if args.many > 0:
+        line["uneven_batch"] = run_many(args.many, 2, local_rank)
     if args.variant_steps > 0:
         line["variants"] = run_variants(args.variant_steps, local_rank)
     if not args.no_cpu_baseline:

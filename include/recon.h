@@ -109,6 +109,18 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims d, const void* const* kspa
                       const uint8_t* const* masks, recon_filter f, const recon_params* prm,
                       void* const* image_out);
 
+/* Batched reconstruction of uneven problems: problem i has its own dims d[i] and filter f[i]
+ * (grid, frame count and filter support may all differ; the parameters prm are shared), slot i
+ * reading kspace[i], masks[i] and writing image_out[i]. Run as recon_solve_batch runs its slots:
+ * independent slots by default; with RECON_OPT_BATCH_GROUP = g the whole batch is one CUDA graph
+ * and every g consecutive slots share one Lanczos, one eps and one FP64 sweep launch per IRLS
+ * iteration, each matrix of its own size s_i = N1 N2 M (the sweep runs as many pivot steps as
+ * the largest needs). Results are bitwise identical to solving each problem alone.
+ * 1 <= n <= RECON_MAX_BATCH; synchronous. */
+int recon_solve_many(recon_ctx* c, int n, const recon_dims* d, const recon_filter* f,
+                     const void* const* kspace, const uint8_t* const* masks,
+                     const recon_params* prm, void* const* image_out);
+
 /* ---- serving: asynchronous requests (continuous batching) ----
  * recon_submit queues one reconstruction (arguments as recon_solve; buffers must stay valid
  * until the request completes) on a free request slot -- its own stream and workspace -- and

@@ -52,18 +52,18 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int 
     float2* dtab = tw + Q;                   // [L2][Q] (tab)
     const int r1 = blockIdx.x;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) tw[i] = twQ[i];
-    if (tab) {
-        for (int e = threadIdx.x; e < L2 * Q; e += blockDim.x) {
-            const int i2 = e / Q, c = e % Q;
-            const int d2m = (i2 - (N2 - 1) + Q) % Q;
-            dtab[e] = twQ[(int)(((long long)d2m * c) % Q)];
-        }
-    }
     for (int e = threadIdx.x; e < T * Q; e += blockDim.x) {
         const int n = e / Q, c = e % Q;
         xs[e] = x[((size_t)n * P + r1) * Q + c];
     }
     __syncthreads();
+    if (tab) {  // from the shared copy of the table (no further global loads)
+        for (int e = threadIdx.x; e < L2 * Q; e += blockDim.x) {
+            const int i2 = e / Q, c = e % Q;
+            const int d2m = (i2 - (N2 - 1) + Q) % Q;
+            dtab[e] = tw[(int)(((long long)d2m * c) % Q)];
+        }
+    }
     // q_ab(c) = sum_j conj(x_{j+M-1-a}(c)) x_{j+M-1-b}(c): window w[m] = x_{j+M-1-m}(c)
     for (int c = threadIdx.x; c < Q; c += blockDim.x) {
         float2 w[M], acc[NP], lo[NP];

@@ -1730,20 +1730,15 @@ int recon_apply_normal_coils(recon_ctx* c, recon_dims dd, recon_filter f, const 
     return RECON_OK;
 }
 
-int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* kspace,
-                      const uint8_t* const* masks, recon_filter f, const recon_params* prm,
-                      void* const* image_out) {
-    if (!c) return RECON_EINVAL;
-    if (n < 1 || n > RECON_MAX_BATCH) return fail(c, RECON_EINVAL, "need 1 <= n <= RECON_MAX_BATCH");
-    if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
-    for (int i = 0; i < n; ++i) {
-        if (!kspace[i] || !masks[i] || !image_out[i]) return fail(c, RECON_EINVAL, "null pointer");
-        if (misaligned({kspace[i], masks[i], image_out[i]})) return fail(c, RECON_EINVAL, kAlignMsg);
-    }
-    Dims d;
-    int rc = check_params(c, dd, f, prm, &d);
-    if (rc) return rc;
-    rc = set_device(c);
+namespace {
+
+// n solves with their own geometry (dims[i]) and shared parameters: independent slots (each its
+// own stream, workspace and graph), or lockstep groups sharing their weight launches
+// (RECON_OPT_BATCH_GROUP), or direct launches (graphs off / eigensolver path). Arguments checked
+// by the callers.
+int solve_many_impl(recon_ctx* c, int n, const Dims* dims, const void* const* kspace,
+                    const uint8_t* const* masks, const recon_params* prm, void* const* image_out) {
+    int rc = set_device(c);
     if (rc) return rc;
     rc = select_slot(c, 0);
     if (rc) return rc;
@@ -1768,7 +1763,7 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
     for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
         rc = select_slot(c, i);
         if (!rc) e = cudaStreamWaitEvent(c->stream, start, 0);
-        if (!rc && e == cudaSuccess) rc = solve_prepare(c, d, kspace[i], masks[i], prm, image_out[i], &sv[i]);
+        if (!rc && e == cudaSuccess) rc = solve_prepare(c, dims[i], kspace[i], masks[i], prm, image_out[i], &sv[i]);
         if (!rc && e == cudaSuccess && !direct && !lockstep) rc = solve_enqueue_all(c, sv[i]);
         if (!rc && e == cudaSuccess && direct) rc = solve_begin(c, &sv[i]);
         // the set-up work of the slot (workspace clears, tuning) precedes the lockstep graph
@@ -1805,8 +1800,49 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
         if (!rc) rc = solve_check(c, sv[i]);
     }
     cleanup();
-    if (e != cudaSuccess) return cuda_fail(c, e, "recon_solve_batch");
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched solve");
     return rc;
+}
+
+int check_many_ptrs(recon_ctx* c, int n, const void* const* kspace, const uint8_t* const* masks,
+                    const recon_params* prm, void* const* image_out) {
+    if (n < 1 || n > RECON_MAX_BATCH) return fail(c, RECON_EINVAL, "need 1 <= n <= RECON_MAX_BATCH");
+    if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    for (int i = 0; i < n; ++i) {
+        if (!kspace[i] || !masks[i] || !image_out[i]) return fail(c, RECON_EINVAL, "null pointer");
+        if (misaligned({kspace[i], masks[i], image_out[i]})) return fail(c, RECON_EINVAL, kAlignMsg);
+    }
+    return RECON_OK;
+}
+
+}  // namespace
+
+int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* kspace,
+                      const uint8_t* const* masks, recon_filter f, const recon_params* prm,
+                      void* const* image_out) {
+    if (!c) return RECON_EINVAL;
+    int rc = check_many_ptrs(c, n, kspace, masks, prm, image_out);
+    if (rc) return rc;
+    Dims d;
+    rc = check_params(c, dd, f, prm, &d);
+    if (rc) return rc;
+    std::vector<Dims> dims(n, d);
+    return solve_many_impl(c, n, dims.data(), kspace, masks, prm, image_out);
+}
+
+int recon_solve_many(recon_ctx* c, int n, const recon_dims* dd, const recon_filter* f,
+                     const void* const* kspace, const uint8_t* const* masks,
+                     const recon_params* prm, void* const* image_out) {
+    if (!c) return RECON_EINVAL;
+    int rc = check_many_ptrs(c, n, kspace, masks, prm, image_out);
+    if (rc) return rc;
+    if (!dd || !f) return fail(c, RECON_EINVAL, "null pointer");
+    std::vector<Dims> dims(n);
+    for (int i = 0; i < n; ++i) {
+        rc = check_params(c, dd[i], f[i], prm, &dims[i]);
+        if (rc) return rc;
+    }
+    return solve_many_impl(c, n, dims.data(), kspace, masks, prm, image_out);
 }
 
 int recon_submit(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t* masks,

@@ -102,6 +102,42 @@ def test_lockstep_batch_perf_size(R):
         recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, 0)
 
 
+UNEVEN = [(32, 8, (5, 5, 2)), (64, 12, (9, 9, 3)), (16, 6, (3, 3, 1)), (32, 10, (7, 5, 3)),
+          (64, 8, (5, 7, 2))]
+
+
+@pytest.mark.parametrize("group", [0, 2, 5])
+def test_uneven_batch_equals_solo(R, group):
+    """recon_solve_many: five problems of different grids, frame counts and filters (s = 50,
+    243, 9, 105 and 70). Independent slots (group 0), and lockstep groups whose shared sweep and
+    Lanczos launches mix matrices of different sizes; every result bitwise the solo one."""
+    recon, ctx = R
+    ks, ms, filts, solo = [], [], [], []
+    for i, (P, T, filt) in enumerate(UNEVEN):
+        w = synth.workload("tiny_32x32x8", P=P, Q=P, T=T, N1=filt[0], N2=filt[1], M=filt[2],
+                           n_irls=4, n_cg=5, times_ms=tuple(5.0 + 4.0 * n for n in range(T)),
+                           seed=40 + i)
+        prob = synth.make_problem(w)
+        ks.append(torch.from_numpy(np.ascontiguousarray(prob["kspace"], dtype=np.complex64)).cuda())
+        ms.append(torch.from_numpy(prob["masks"]).cuda())
+        filts.append(filt)
+        out = torch.empty((T, P, P), dtype=torch.complex64, device="cuda")
+        recon.recon_solve(ctx.h, ks[-1], ms[-1], filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+        solo.append(out.cpu().numpy())
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, group)
+    try:
+        outs = [torch.full(tuple(m.shape), float("nan"), dtype=torch.complex64, device="cuda")
+                for m in ms]
+        for _ in range(2):  # capture, then replay of the batch graph
+            recon.recon_solve_many(ctx.h, ks, ms, filts, w.lam, w.p, w.n_irls, w.n_cg, outs)
+            for a, b in zip(outs, solo):
+                assert np.array_equal(a.cpu().numpy(), b)
+            for o in outs:
+                o.fill_(float("nan"))
+    finally:
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, 0)
+
+
 def test_batch_perf_size_two_slots(R):
     recon, ctx = R
     w = synth.workload("perf_256x256x16", n_irls=2)
