@@ -71,10 +71,10 @@ def alg_bytes(kind: str, w, n_cg: int) -> float:
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 dense FP64, nominal (a probe here measured ~1056)
 ALU_KINDS = ("hpd_inverse", "lanczos")
 # DRAM bytes (read + write) per launch from one ncu capture of the launch class's kernel at the
-# benchmark workload (steady state, caches kept; profiles/hpd_sweep_kernel_s243.md gives the
-# command). Only for the kernel versions those captures measured: drop an entry when its
-# kernel changes.
-TRAFFIC_BYTES = {"hpd_inverse": 552704}
+# benchmark workload (the first sweep of the bench's first solve; profiles/hpd_sweep_kernel_s243.md
+# gives the command). Only for the kernel versions those captures measured: drop an entry when
+# its kernel changes.
+TRAFFIC_BYTES = {"hpd_inverse": 553216}
 
 
 def alg_flops(kind: str, w) -> float:
