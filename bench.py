@@ -35,8 +35,7 @@ CMP_WORKLOAD = "cmp_128x128x12"
 # diag_sums is one kernel on the p = 0 path, two after the eigendecomposition)
 KERNELS_PER_SCOPE = {"adjoint": 2, "gram": 2, "eps": 1, "diag_sums": 1, "weight_S": 2,
                      "resid_carry": 1, "cg_row_fwd": 1, "cg_col_mask": 1, "cg_row_inv_w": 1,
-                     "cg_update": 1, "lanczos": 1, "hpd_inverse": 1, "cg_frame_aha": 1,
-                     "cg_w_combine": 1}
+                     "cg_update": 1, "lanczos": 1, "hpd_inverse": 1}
 
 
 def alg_bytes(kind: str, w, n_cg: int) -> float:
@@ -55,10 +54,6 @@ def alg_bytes(kind: str, w, n_cg: int) -> float:
         return 24.0 * E + 8.0 * npair * N
     if kind == "cg_update":       # read x, r, p, q; write x, r
         return 48.0 * E
-    if kind == "cg_frame_aha":    # read r (+ p), mask; write p, t
-        return (25.0 * E + 33.0 * E * (n_cg - 1)) / n_cg
-    if kind == "cg_w_combine":    # read t, p, S; write q
-        return 24.0 * E + 8.0 * npair * N
     if kind == "resid_carry":     # read x, r, S_old, S_new; write r (first: no r, S_old)
         return 24.0 * E + 16.0 * npair * N
     if kind == "gram":            # read x
@@ -778,7 +773,7 @@ def main():
                 "traffic": TRAFFIC_BYTES.get(dom)}
     # the memory-bound CG passes (per-launch time from the profiled solve)
     cg_roof = {}
-    for k in ("cg_frame_aha", "cg_w_combine", "cg_row_fwd", "cg_col_mask", "cg_row_inv_w",
+    for k in ("cg_row_fwd", "cg_col_mask", "cg_row_inv_w",
               "cg_update"):
         ms_k, n_k = prof1.get(k, (0.0, 0))
         if n_k:

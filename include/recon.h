@@ -137,30 +137,19 @@ int recon_submit(recon_ctx* c, recon_dims d, const void* kspace, const uint8_t* 
  * error recon_solve would have returned). */
 int recon_poll(recon_ctx* c, int ticket, int* done);
 
-/* Context options (value 0 = off, 1 = on; results are the same either way up to floating-point
- * rounding of the operator, see the parity tests):
+/* Context options (value 0 = off, 1 = on unless stated):
  * RECON_OPT_GRAPHS: recon_solve and recon_solve_batch capture a whole solve (every launch of
  *   Algorithm 1) into a CUDA graph on first use and replay it while the shapes, parameters,
  *   buffer pointers and workspace stay the same (one graph per slot). Not used for the
  *   eigensolver-library path or while launch classes are timed.
- * RECON_OPT_CLUSTER_FFT: for square frames (P = Q in {32, 64, 128, 192, 256}) the CG operator
- *   runs each frame's 2-D transform, mask and inverse in one kernel on an 8-CTA cluster
- *   (distributed shared memory), followed by a pixel-parallel W pass; off = the row / column
- *   passes used for every other shape. */
-/* RECON_OPT_AUTOTUNE: on the first solve of each shape (P, Q, T, R, coils) the context times the
+ * RECON_OPT_AUTOTUNE: on the first solve of each shape (P, Q, T, R, coils) the context times the
  *   column passes of the CG operator with tiles of 8, 16 and 32 columns (CUDA events on its own
  *   stream, a few milliseconds at most) and keeps the fastest; off = the built-in widths. The
- *   width changes launch shapes only: results are bitwise the same either way. */
+ *   width changes launch shapes only: results are bitwise the same either way.
+ * Option numbers 2 and 4 are retired (a cluster operator for square frames and a three-pass CG
+ *   step, both measured slower than the four-pass step): setting them gives RECON_EINVAL. */
 #define RECON_OPT_GRAPHS 1      /* default on  */
-#define RECON_OPT_CLUSTER_FFT 2 /* default off */
 #define RECON_OPT_AUTOTUNE 3    /* default on  */
-/* RECON_OPT_THREE_PASS: 256 x 256 single-coil series run each CG step in three passes -- the
- *   step's scalar <p, (A^H A + lambda W) p> is assembled from partials of ||A p||^2 (column pass)
- *   and <p, W p> (row pass), so the last pass applies alpha and updates x and r itself, and q is
- *   never stored (17 % fewer bytes per step); off = the four-pass step (row, column, row + W,
- *   update), which measures faster on one GB300 while the series fits in L2. Same CG in exact
- *   arithmetic; rounding differs at the FP32 level. */
-#define RECON_OPT_THREE_PASS 4  /* default off */
 /* RECON_OPT_INJECT_BARRIER_FAULT (testing): the next solve on this context that forms its weight
  *   by the FP64 sweep (p = 0, RECON_WEIGHT_AUTO) starts with the error word of the sweep's grid
  *   barrier set from the host, as a CTA whose bounded wait gave up would leave it; every sweep of that solve returns at its first barrier and reports it, the
@@ -442,9 +431,7 @@ int recon_fft_schedule_choice(recon_ctx* c, recon_dims3 d, int n_coils, int* col
 #define RECON_PROF_CG_UPDATE 10   /* CG pass D: x, r update + |r|^2 partials               */
 #define RECON_PROF_LANCZOS 11     /* lambda_max of G for eps0 (p = 0 path)                 */
 #define RECON_PROF_INV 12         /* FP64 sweep inverse (G + eps I)^-1 (p = 0 path)        */
-#define RECON_PROF_CG_FRAME 13    /* CG, square frames: p update + cluster F^H M F per frame */
-#define RECON_PROF_CG_WCOMB 14    /* CG, square frames: q = t + lambda W p, <p, q>          */
-#define RECON_PROF_KINDS 15
+#define RECON_PROF_KINDS 13
 
 #define RECON_PROF_ALL ((1u << RECON_PROF_KINDS) - 1u)
 

@@ -21,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "librecon.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fft.cu", "cg.cu", "gram.cu", "weight.cu", "hpdinv.cu", "frame_op.cu", "t2fit.cu", "recon.cu",
+SOURCES = ["fft.cu", "cg.cu", "gram.cu", "weight.cu", "hpdinv.cu", "t2fit.cu", "recon.cu",
            "gram_static.cu", "variants.cu"]
 HEADERS = ["common.cuh", "kernels.h", "regfft.cuh"]
 

@@ -212,189 +212,6 @@ row_inv_w_256_kernel(float2* t, const float2* __restrict__ p, const float2* __re
     if (threadIdx.x == 0) pq_parts[blockIdx.x] = tot;
 }
 
-// ---- three-pass CG step for 256 x 256 image series ----
-// The step's one global scalar, <p, (A^H A + lam W) p> = ||A p||^2 + lam <p, W p>, is assembled
-// from partials left by the first two passes, so that the third pass can apply alpha at once:
-//   A3: p = r + beta p; t = row-DFT(p); partials of <p, W p> (W p from p rows of all frames);
-//   B3: column DFT, mask, column IDFT (col_mask_256_kernel) and partials of sum_sampled |X|^2
-//       (X the unnormalised 2-D DFT: ||A p||^2 = sum / (PQ));
-//   C3: q = row-IDFT(t) + lam W p per pixel, alpha = |r|^2 / <p, q> from those partials,
-//       x += alpha p, r -= alpha q, partials of |r|^2; q itself is never stored.
-// Same CG iterates as the four-pass step in exact arithmetic (Hestenes-Stiefel CG; <p, q> is
-// evaluated through the two quadratic forms instead of the product with the stored q).
-
-// Pass A3: one CTA per image row r1 holds that row of every frame (T' x 16 threads, T' = T rounded
-// up to even). Shared memory: p rows [T][256] then the exchange buffers [T'][16 x 17].
-template <int M>
-__global__ void __launch_bounds__(1024)
-row_fwd_w_256_kernel(const float2* __restrict__ r, float2* __restrict__ p, float2* __restrict__ t,
-                     const float2* __restrict__ S, int T, int P, const double* __restrict__ rr_parts,
-                     int n_rr, const double* __restrict__ rr_prev, double* __restrict__ rr_out,
-                     int first, double* __restrict__ pw_parts, const float2* __restrict__ tw_g) {
-    constexpr int N = 256;
-    extern __shared__ float2 sm[];
-    __shared__ float2 tw2[256];
-    __shared__ double red[32];
-    __shared__ float beta_s;
-    float2* pt = sm;
-    float2* ex = sm + (size_t)T * N;
-    fill_tw256(tw2, tw_g);
-    pdl_wait();
-    if (threadIdx.x < 32) {  // beta = |r|^2 / |r_prev|^2 from the previous pass C3's partials
-        float beta = 0.f;
-        if (!first) {
-            const double rr_new = warp0_sum_array(rr_parts, n_rr);
-            beta = (float)(rr_new * rcp_nr(rr_prev[0]));
-            if (threadIdx.x == 0 && blockIdx.x == 0) rr_out[0] = rr_new;
-        }
-        if (threadIdx.x == 0) beta_s = beta;
-    }
-    __syncthreads();
-    const float beta = beta_s;
-    const int n = threadIdx.x / 16, j = threadIdx.x % 16;
-    const bool live = n < T;
-    const size_t npix = (size_t)P * N;
-    const int k = T - M + 1;
-    float acc = 0.f, comp = 0.f;  // Kahan-compensated partial of <p, W p>
-    for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
-    __syncthreads();  // the previous row's p rows are consumed
-    const size_t g0 = (size_t)n * npix + (size_t)r1 * N + j;
-    float2 u[16];
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) u[n1] = make_float2(0.f, 0.f);
-    if (live) {
-#pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) u[n1] = r[g0 + 16 * n1];
-        if (!first) {
-#pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1) {
-                const float2 pv = p[g0 + 16 * n1];
-                u[n1].x = fmaf(beta, pv.x, u[n1].x);
-                u[n1].y = fmaf(beta, pv.y, u[n1].y);
-            }
-        }
-#pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) {
-            p[g0 + 16 * n1] = u[n1];
-            pt[n * N + 16 * n1 + j] = u[n1];
-        }
-    }
-    row_dft256<false>(u, ex + n * (16 * 17), tw2, j);
-    if (live) {
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) t[g0 + 16 * k2] = u[k2];
-    }
-    __syncthreads();  // p rows of every frame in shared memory
-    for (int c = threadIdx.x; c < N; c += blockDim.x) {
-        float2 s[M][M];
-        load_S<M>(S, npix, (size_t)r1 * N + c, s);
-        float2 cs[2 * M - 1];
-        s_diagonals<M>(s, cs);
-        for (int nn = 0; nn < T; ++nn) {
-            const float2 w = w_frame<M, false>(s, cs, pt + c, N, nn, T, k);
-            const float2 pv = pt[nn * N + c];
-            const float term = fmaf(pv.x, w.x, pv.y * w.y) - comp;
-            const float sum = acc + term;
-            comp = (sum - acc) - term;
-            acc = sum;
-        }
-    }
-    }
-    pdl_trigger();
-    const double tot = block_sum_f_t0(acc, red);
-    if (threadIdx.x == 0) pw_parts[blockIdx.x] = tot;
-}
-
-// Pass C3 (layout as row_inv_w_256_kernel): alpha from the partials of A3 and B3, then
-// x += alpha p, r -= alpha q per element, partials of |r|^2 to rr_parts.
-template <int M>
-__global__ void __launch_bounds__(1024)
-row_inv_w_upd_256_kernel(const float2* __restrict__ t, const float2* __restrict__ p,
-                         const float2* __restrict__ S, float lam, int T, int P,
-                         float2* __restrict__ x, float2* __restrict__ r,
-                         const double* __restrict__ pw_parts, int n_pw,
-                         const double* __restrict__ m_parts, int n_m, double inv_pq_grid,
-                         const double* __restrict__ rr_cur, double* __restrict__ pq_out,
-                         double* __restrict__ rr_parts, const float2* __restrict__ tw_g) {
-    constexpr int N = 256;
-    extern __shared__ float2 sm[];
-    __shared__ float2 tw2[256];
-    __shared__ double red[32];
-    __shared__ float alpha_s;
-    float2* pt = sm;
-    float2* res = sm + (size_t)T * N;
-    fill_tw256(tw2, tw_g);
-    pdl_wait();
-    const int n = threadIdx.x / 16, j = threadIdx.x % 16;
-    const bool live = n < T;
-    const size_t npix = (size_t)P * N;
-    const int k = T - M + 1;
-    float acc = 0.f, comp = 0.f;  // Kahan-compensated partial of |r_new|^2
-    bool have_alpha = false;
-    float alpha = 0.f;
-    for (int r1 = blockIdx.x; r1 < P; r1 += gridDim.x) {
-    __syncthreads();  // the previous row's results are consumed
-    const size_t g0 = (size_t)n * npix + (size_t)r1 * N + j;
-    float2 u[16];
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) {
-        u[n1] = make_float2(0.f, 0.f);
-        if (live) {
-            u[n1] = t[g0 + 16 * n1];
-            pt[n * N + 16 * n1 + j] = p[g0 + 16 * n1];
-        }
-    }
-    if (!have_alpha && threadIdx.x < 32) {  // loads in flight: <p, q> = ||A p||^2 + lam <p, W p>
-        const double pq = warp0_sum_array(m_parts, n_m) * inv_pq_grid +
-                          (double)lam * warp0_sum_array(pw_parts, n_pw);
-        if (threadIdx.x == 0) {
-            alpha_s = (float)(rr_cur[0] * rcp_nr(pq));
-            if (blockIdx.x == 0) pq_out[0] = pq;
-        }
-    }
-    __syncthreads();  // tw2, alpha
-    if (!have_alpha) {
-        alpha = alpha_s;
-        have_alpha = true;
-    }
-    row_dft256<true>(u, res + n * (16 * 17), tw2, j);
-    __syncthreads();  // every exchange buffer read
-    if (live) {
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) res[n * N + j + 16 * k2] = u[k2];
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < N; c += blockDim.x) {
-        float2 s[M][M];
-        load_S<M>(S, npix, (size_t)r1 * N + c, s);
-        float2 cs[2 * M - 1];
-        s_diagonals<M>(s, cs);
-        for (int nn = 0; nn < T; ++nn) {
-            const float2 w = w_frame<M, false>(s, cs, pt + c, N, nn, T, k);
-            float2 q = res[nn * N + c];
-            q.x = fmaf(lam, w.x, q.x);
-            q.y = fmaf(lam, w.y, q.y);
-            const size_t g = (size_t)nn * npix + (size_t)r1 * N + c;
-            const float2 pv = pt[nn * N + c];
-            float2 xv = x[g], rv = r[g];
-            xv.x = fmaf(alpha, pv.x, xv.x);
-            xv.y = fmaf(alpha, pv.y, xv.y);
-            rv.x = fmaf(-alpha, q.x, rv.x);
-            rv.y = fmaf(-alpha, q.y, rv.y);
-            x[g] = xv;
-            r[g] = rv;
-            const float term = fmaf(rv.x, rv.x, rv.y * rv.y) - comp;
-            const float sum = acc + term;
-            comp = (sum - acc) - term;
-            acc = sum;
-        }
-    }
-    }
-    pdl_trigger();
-    const double tot = block_sum_f_t0(acc, red);
-    if (threadIdx.x == 0) rr_parts[blockIdx.x] = tot;
-}
-
 // Pass C for 128-point rows: as row_inv_w_256_kernel with 8 threads per frame (row_dft128), the
 // block padded to at least 16 frames (128 threads, one column each in the W phase) and at most
 // 64; warps without a frame skip the transform. A CTA usually owns several rows (volumes have
@@ -992,75 +809,6 @@ cudaError_t launch_apply_w(const Dims& d, const float2* x, const float2* S, floa
     }
 #undef CASE
     return cudaGetLastError();
-}
-
-bool fused3_supported(const Dims& d) {
-    return d.P == 256 && d.Q == 256 && d.R == 1 && d.nc == 1 && !d.circ && d.M >= 1 &&
-           d.M <= kMaxM && d.T <= 64 && col_mask_parts_supported(d);
-}
-
-namespace {
-
-size_t fused3_smem(const Dims& d) {
-    const int tpad = (d.T + 1) / 2 * 2;
-    return ((size_t)d.T * 256 + (size_t)tpad * 16 * 17) * sizeof(float2);
-}
-
-template <typename K>
-cudaError_t fused3_setup(K k, const Dims& d, int* threads, int* grid) {
-    const size_t smem = fused3_smem(d);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    *threads = (d.T + 1) / 2 * 2 * 16;
-    return row_grid(k, *threads, smem, d.P, grid);
-}
-
-}  // namespace
-
-cudaError_t launch_row_fwd_w(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
-                             float2* t, const float2* S, const Partials& rr, const double* rr_prev,
-                             double* rr_out, int first, Partials* pw, cudaStream_t st) {
-    if (!fused3_supported(d)) return cudaErrorInvalidValue;
-#define CASE(MM)                                                                                 \
-    case MM: {                                                                                   \
-        auto k = row_fwd_w_256_kernel<MM>;                                                       \
-        int threads = 0, grid = 0;                                                               \
-        cudaError_t e = fused3_setup(k, d, &threads, &grid);                                     \
-        if (e != cudaSuccess) return e;                                                          \
-        pw->n = grid;                                                                            \
-        return launch_pdl(k, dim3(grid), dim3(threads), fused3_smem(d), st, r, p, t, S, d.T,      \
-                          d.P, (const double*)rr.parts, rr.n, rr_prev, rr_out, first, pw->parts,  \
-                          tw.twQ);                                                               \
-    }
-    switch (d.M) {
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
-        default: return cudaErrorInvalidValue;
-    }
-#undef CASE
-}
-
-cudaError_t launch_row_inv_w_upd(const Dims& d, const Twiddles& tw, const float2* t,
-                                 const float2* p, const float2* S, float lam, float2* x, float2* r,
-                                 const Partials& pw, const Partials& mp, const double* rr_cur,
-                                 double* pq_out, Partials* rr, cudaStream_t st) {
-    if (!fused3_supported(d)) return cudaErrorInvalidValue;
-    const double inv_pq = 1.0 / ((double)d.P * (double)d.Q);
-#define CASE(MM)                                                                                  \
-    case MM: {                                                                                    \
-        auto k = row_inv_w_upd_256_kernel<MM>;                                                    \
-        int threads = 0, grid = 0;                                                                \
-        cudaError_t e = fused3_setup(k, d, &threads, &grid);                                      \
-        if (e != cudaSuccess) return e;                                                           \
-        rr->n = grid;                                                                             \
-        return launch_pdl(k, dim3(grid), dim3(threads), fused3_smem(d), st, t, p, S, lam, d.T,     \
-                          d.P, x, r, (const double*)pw.parts, pw.n, (const double*)mp.parts, mp.n, \
-                          inv_pq, rr_cur, pq_out, rr->parts, tw.twQ);                              \
-    }
-    switch (d.M) {
-        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
-        default: return cudaErrorInvalidValue;
-    }
-#undef CASE
 }
 
 }  // namespace recon

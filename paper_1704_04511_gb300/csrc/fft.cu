@@ -338,15 +338,11 @@ row_fwd_pupdate_128_kernel(const float2* __restrict__ r, float2* __restrict__ p,
 // 128-thread CTA, thread (c, j) holding rows j + 16 n1 of column c. Forward DFT, mask and the
 // 1/(PQ) scale, inverse DFT, all in registers; two exchanges through shared memory, laid out as
 // c + 8 (17 a + b) so that both the writes and the reads are conflict-free.
-// PARTS: also the CTA's partial of sum |X|^2 over the sampled entries (X the unnormalised 2-D DFT
-// of the frame), i.e. PQ ||A p||^2 summed over its columns, into m_parts (one per CTA).
-template <bool PARTS>
 __global__ void __launch_bounds__(128)
 col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, int mask_frames,
-                    float scale, const float2* __restrict__ tw_g, double* __restrict__ m_parts) {
+                    float scale, const float2* __restrict__ tw_g) {
     __shared__ float2 tw2[256];
     __shared__ float2 buf[8 * 17 * 16];
-    __shared__ double red[4];
     fill_tw256(tw2, tw_g);
     pdl_wait();
     const int c = threadIdx.x % 8, j = threadIdx.x / 8;
@@ -368,16 +364,6 @@ col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, int mask
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) u[n2] = buf[c + 8 * (17 * j + n2)];
     dft16<false>(u);  // u[k2] = X[j + 16 k2]
-    float acc = 0.f, comp = 0.f;
-    if constexpr (PARTS) {
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-            const float term = (mk[k2] ? fmaf(u[k2].x, u[k2].x, u[k2].y * u[k2].y) : 0.f) - comp;
-            const float sum = acc + term;
-            comp = (sum - acc) - term;
-            acc = sum;
-        }
-    }
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) u[k2] = mk[k2] ? cscale(u[k2], scale) : make_float2(0.f, 0.f);
     dft16<true>(u);  // u[n1] = sum_k2 X[j + 16 k2] w16^(-k2 n1)
@@ -392,10 +378,6 @@ col_mask_256_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, int mask
     pdl_trigger();
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) t[fbase + (size_t)(j + 16 * n2) * Q + col] = u[n2];
-    if constexpr (PARTS) {
-        const double tot = block_sum_f_t0(acc, red);
-        if (threadIdx.x == 0) m_parts[blockIdx.y * gridDim.x + blockIdx.x] = tot;
-    }
 }
 
 // ---- register-transform column passes of the volume column stage ----
@@ -812,28 +794,13 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
     const float sc = 1.0f / ((float)d.P * (float)d.Q);
     const int frames = d.T * d.nc;  // coil-major: the mask of frame f is mask frame f % T
     if (d.P == 256)
-        return launch_pdl(col_mask_256_kernel<false>, dim3(d.Q / kColTile, frames), dim3(128), 0,
-                          st, t, mask, d.Q, d.T, sc, tw.twP, (double*)nullptr);
+        return launch_pdl(col_mask_256_kernel, dim3(d.Q / kColTile, frames), dim3(128), 0, st, t,
+                          mask, d.Q, d.T, sc, tw.twP);
     if (col_register(d, false))
         return launch_pdl(col_mask_128_kernel, dim3(d.Q / 16, frames), dim3(128), 0, st, t, mask,
                           d.Q, d.T, sc, tw.twP);
     return col_pass<COL_MASK_OP>(d.P, col_tile_for(d, false), d.colS, d.Q, frames, d.T, t, t, mask,
                                  sc, tw.twP, st);
-}
-
-bool col_mask_parts_supported(const Dims& d) {
-    return d.P == 256 && d.R == 1 && d.nc == 1;
-}
-
-cudaError_t launch_col_mask_parts(const Dims& d, const Twiddles& tw, float2* t, const uint8_t* mask,
-                                  Partials* mp, cudaStream_t st) {
-    if (!col_mask_parts_supported(d)) return cudaErrorInvalidValue;
-    const float sc = 1.0f / ((float)d.P * (float)d.Q);
-    const dim3 grid(d.Q / kColTile, d.T);
-    mp->n = (int)(grid.x * grid.y);
-    if (mp->n > max_parts()) return cudaErrorInvalidValue;
-    return launch_pdl(col_mask_256_kernel<true>, grid, dim3(128), 0, st, t, mask, d.Q, d.T, sc,
-                      tw.twP, mp->parts);
 }
 
 }  // namespace recon

@@ -211,16 +211,6 @@ struct LanczosJob {
 cudaError_t launch_lanczos_batch(const LanczosJob* jobs, int n, void* barrier_scratch,
                                  cudaStream_t st, CoopFault fault = {});
 
-// ---- frame_op.cu (square frames: cluster 2-D transform per frame + pixel-parallel W) ----
-bool frame_op_supported(const Dims& d);
-// p = r (first) or r + beta p; t = F^H (mask * F p) frame by frame (one 8-CTA cluster per frame)
-cudaError_t launch_frame_aha(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
-                             float2* t, const uint8_t* mask, const Partials& rr,
-                             const double* rr_prev, double* rr_out, int first, cudaStream_t st);
-// q = t + lam W_S p written over t; partials of Re <p, q> to *pq
-cudaError_t launch_w_combine(const Dims& d, float2* t, const float2* p, const float2* S, float lam,
-                             Partials* pq, cudaStream_t st);
-
 // ---- coils (Eq. measurement-ij with receiver sensitivities C_c; d.nc coils, coil-major) ----
 // Pass A: p = r (first) or r + beta p (as launch_row_fwd_pupdate); t[c] = row-FFT(C_c * p).
 cudaError_t launch_coil_row_fwd(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
@@ -251,24 +241,6 @@ struct T2Times {
 // the per-pixel fit (NaN outside the foreground |x_0| > frac max |x_0|); amp may be null.
 cudaError_t launch_t2fit(const Dims& d, const float2* x, const T2Times& tm, float frac, int n_gn,
                          unsigned int* amax_scratch, float* t2, float* amp, cudaStream_t st);
-
-// ---- three-pass CG step (256 x 256 image series, one coil, valid lifting) ----
-bool col_mask_parts_supported(const Dims& d);
-bool fused3_supported(const Dims& d);
-// Pass A3: p = r (first) or r + beta p (beta from the partials `rr` of the previous pass C3, its
-// numerator stored to *rr_out); t = row-DFT(p); partials of <p, W p> to *pw.
-cudaError_t launch_row_fwd_w(const Dims& d, const Twiddles& tw, const float2* r, float2* p,
-                             float2* t, const float2* S, const Partials& rr, const double* rr_prev,
-                             double* rr_out, int first, Partials* pw, cudaStream_t st);
-// Pass B3: the column pass of launch_col_mask plus partials of sum over sampled |X|^2 to *mp.
-cudaError_t launch_col_mask_parts(const Dims& d, const Twiddles& tw, float2* t,
-                                  const uint8_t* mask, Partials* mp, cudaStream_t st);
-// Pass C3: q = row-IDFT(t) + lam W p; alpha = *rr_cur / (sum(mp) / (PQ) + lam sum(pw)) (also
-// stored to *pq_out); x += alpha p; r -= alpha q; partials of |r|^2 to *rr.
-cudaError_t launch_row_inv_w_upd(const Dims& d, const Twiddles& tw, const float2* t,
-                                 const float2* p, const float2* S, float lam, float2* x, float2* r,
-                                 const Partials& pw, const Partials& mp, const double* rr_cur,
-                                 double* pq_out, Partials* rr, cudaStream_t st);
 
 // ---- variants.cu (comparison methods of Sec. IV) ----
 // HLR-Voxel weight per pixel (S = H_r^T into [pair][P][Q]); eps_mode 0: eps_r = eps_in[px];

@@ -86,7 +86,7 @@ struct recon_ctx {
         int T, P, Q, N1, N2, M, irls, cg, bf16, method, R, N3;
         double lambda, p, gamma, eps0_frac;
         const void *kspace, *masks, *out, *coils;
-        int nc, coil_proj, circ, variant, colC, depthC, colS, depthS, three_pass;
+        int nc, coil_proj, circ, variant, colC, depthC, colS, depthS;
         unsigned int prof;
         unsigned long ws_gen;
     };
@@ -95,10 +95,8 @@ struct recon_ctx {
     GraphProf* gprof = nullptr;        // its timing events (launch classes timed when captured)
     GraphProf* capturing = nullptr;    // set while a solve with timed classes is being captured
     bool graphs = true;
-    bool cluster_fft = false;          // square frames: cluster 2-D transform kernel (opt-in)
     // autotuner: column tile widths per problem shape (P, Q, T, R, coils), timed on first use
     bool autotune = true;
-    bool three_pass = false;           // 256 x 256 series: three-pass CG step (RECON_OPT_THREE_PASS)
     bool inject_barrier_fault = false; // next solve: sweep barrier starts failed (RECON_OPT_INJECT_BARRIER_FAULT)
     bool withhold_arrival = false;     // next solve: one CTA withholds its barrier arrival (RECON_OPT_TEST_WITHHOLD_ARRIVAL)
     // lockstep batches (RECON_OPT_BATCH_GROUP): one graph over every slot of recon_solve_batch
@@ -372,7 +370,7 @@ int check_dims3(recon_ctx* c, recon_dims3 dd, const recon_filter3* f, Dims* d) {
 struct Work {
     float2 *r, *p, *t, *S0, *S1;
     double2 *G, *lag_part, *lags, *dpart, *dsum, *Z, *eigwork;
-    double *evals, *parts, *rparts, *mparts, *rr, *pq, *eps, *lmax;
+    double *evals, *parts, *rparts, *rr, *pq, *eps, *lmax;
     unsigned int* counter;
     int *info, *kerr;
     void *hpd = nullptr, *lanc = nullptr;
@@ -425,7 +423,6 @@ int get_work(recon_ctx* c, const Dims& d, int n_cg, int n_iter, bool vectors, bo
     GET("Z", recon::s_scratch_bytes(d), Z, double2*);
     GET("parts", (size_t)recon::max_parts() * sizeof(double), parts, double*);
     GET("rparts", (size_t)recon::max_parts() * sizeof(double), rparts, double*);
-    GET("mparts", (size_t)recon::max_parts() * sizeof(double), mparts, double*);
     GET("counter", 256, counter, unsigned int*);
     GET("rr", (size_t)(n_cg + 1) * sizeof(double), rr, double*);
     GET("pq", (size_t)(n_cg + 1) * sizeof(double), pq, double*);
@@ -563,53 +560,22 @@ int cg_block(recon_ctx* c, const Dims& d, const Twiddles& tw, Work& w, const uin
     // the update pass; the update pass leaves those of |r|^2 in w.rparts for the next pass A,
     // which also stores the sum in rr[it] (rr[0] comes from the residual carry).
     recon::Partials pq{w.parts, 0}, rr{w.rparts, 0};
-    if (!coils && c->three_pass && recon::fused3_supported(d)) {
-        // three passes per step: <p, q> from the quadratic forms' partials of passes A3 and B3,
-        // so that pass C3 applies alpha and no separate update pass is needed
-        recon::Partials pw{w.parts, 0}, mp{w.mparts, 0};
-        for (int it = 0; it < n_cg; ++it) {
-            const double* rr_prev = it > 0 ? w.rr + it - 1 : w.rr;
-            {
-                ProfScope ps(c, RECON_PROF_CG_ROWFWD);
-                RC_CUDA(recon::launch_row_fwd_w(d, tw, w.r, w.p, w.t, S_new, rr, rr_prev, w.rr + it,
-                                                it == 0, &pw, c->stream));
-            }
-            {
-                ProfScope ps(c, RECON_PROF_CG_COL);
-                RC_CUDA(recon::launch_col_mask_parts(d, tw, w.t, mask, &mp, c->stream));
-            }
-            ProfScope ps(c, RECON_PROF_CG_ROWINVW);
-            RC_CUDA(recon::launch_row_inv_w_upd(d, tw, w.t, w.p, S_new, lam, x, w.r, pw, mp,
-                                                w.rr + it, w.pq + it, &rr, c->stream));
-        }
-        if (n_cg > 0) RC_CUDA(recon::launch_sum_partials(rr, w.rr + n_cg, c->stream));
-        return RECON_OK;
-    }
-    const bool fused = c->cluster_fft && recon::frame_op_supported(d) && !coils;
     for (int it = 0; it < n_cg; ++it) {
         const double* rr_prev = it > 0 ? w.rr + it - 1 : w.rr;
-        if (fused) {
-            {
-                ProfScope ps(c, RECON_PROF_CG_FRAME);
-                RC_CUDA(recon::launch_frame_aha(d, tw, w.r, w.p, w.t, mask, rr, rr_prev, w.rr + it,
-                                                it == 0, c->stream));
-            }
-            ProfScope ps(c, RECON_PROF_CG_WCOMB);
-            RC_CUDA(recon::launch_w_combine(d, w.t, w.p, S_new, lam, &pq, c->stream));
-        } else {
-            {
-                ProfScope ps(c, RECON_PROF_CG_ROWFWD);
-                if (coils)
-                    RC_CUDA(recon::launch_coil_row_fwd(d, tw, w.r, w.p, w.t, coils, rr, rr_prev,
-                                                       w.rr + it, it == 0, c->stream));
-                else
-                    RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, rr, rr_prev,
-                                                          w.rr + it, it == 0, c->stream));
-            }
-            {
-                ProfScope ps(c, RECON_PROF_CG_COL);
-                RC_CUDA(recon::launch_col_mask(d, tw, w.t, mask, c->stream));
-            }
+        {
+            ProfScope ps(c, RECON_PROF_CG_ROWFWD);
+            if (coils)
+                RC_CUDA(recon::launch_coil_row_fwd(d, tw, w.r, w.p, w.t, coils, rr, rr_prev,
+                                                   w.rr + it, it == 0, c->stream));
+            else
+                RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, w.r, w.p, w.t, rr, rr_prev,
+                                                      w.rr + it, it == 0, c->stream));
+        }
+        {
+            ProfScope ps(c, RECON_PROF_CG_COL);
+            RC_CUDA(recon::launch_col_mask(d, tw, w.t, mask, c->stream));
+        }
+        {
             ProfScope ps(c, RECON_PROF_CG_ROWINVW);
             if (coils)
                 RC_CUDA(recon::launch_coil_row_inv_w(d, tw, w.t, w.p, coils, S_new, lam, &pq,
@@ -905,7 +871,6 @@ recon_ctx::GraphKey graph_key(recon_ctx* c, const Solve& sv) {
     k.coils = sv.coils; k.nc = sv.d.nc; k.coil_proj = sv.coil_proj;
     k.circ = sv.d.circ; k.variant = sv.variant; k.colC = sv.d.colC; k.depthC = sv.d.depthC;
     k.colS = sv.d.colS; k.depthS = sv.d.depthS;
-    k.three_pass = c->three_pass;
     k.prof = c->prof;
     return k;
 }
@@ -1483,18 +1448,11 @@ int apply_normal_impl(recon_ctx* c, const Dims& d0, const uint8_t* masks, const 
     recon::Partials pq{(double*)parts, 0};
     const recon::Partials none{nullptr, 0};
     // the CG operator passes with first = 1 (p = x); y receives (A^H A + lambda W) x
-    if (c->cluster_fft && recon::frame_op_supported(d)) {
-        RC_CUDA(recon::launch_frame_aha(d, tw, (const float2*)x, (float2*)pp, (float2*)y, masks,
-                                        none, nullptr, nullptr, 1, c->stream));
-        RC_CUDA(recon::launch_w_combine(d, (float2*)y, (const float2*)pp, (const float2*)S,
-                                        (float)lambda, &pq, c->stream));
-    } else {
-        RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y,
-                                              none, nullptr, nullptr, 1, c->stream));
-        RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
-        RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
-                                        (float)lambda, &pq, c->stream));
-    }
+    RC_CUDA(recon::launch_row_fwd_pupdate(d, tw, (const float2*)x, (float2*)pp, (float2*)y, none,
+                                          nullptr, nullptr, 1, c->stream));
+    RC_CUDA(recon::launch_col_mask(d, tw, (float2*)y, masks, c->stream));
+    RC_CUDA(recon::launch_row_inv_w(d, tw, (float2*)y, (const float2*)pp, (const float2*)S,
+                                    (float)lambda, &pq, c->stream));
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return RECON_OK;
 }
@@ -2247,9 +2205,7 @@ int recon_set_option(recon_ctx* c, int option, int value) {
     if (!c) return RECON_EINVAL;
     switch (option) {
         case RECON_OPT_GRAPHS: c->graphs = value != 0; return RECON_OK;
-        case RECON_OPT_CLUSTER_FFT: c->cluster_fft = value != 0; return RECON_OK;
         case RECON_OPT_AUTOTUNE: c->autotune = value != 0; return RECON_OK;
-        case RECON_OPT_THREE_PASS: c->three_pass = value != 0; return RECON_OK;
         case RECON_OPT_INJECT_BARRIER_FAULT: c->inject_barrier_fault = value != 0; return RECON_OK;
         case RECON_OPT_TEST_WITHHOLD_ARRIVAL: c->withhold_arrival = value != 0; return RECON_OK;
         case RECON_OPT_AUTOTUNE_FFT: c->autotune_fft = value != 0; return RECON_OK;
@@ -2340,8 +2296,7 @@ int recon_profile_read(recon_ctx* c, int kind, double* total_ms, long long* laun
 const char* recon_profile_name(int kind) {
     static const char* names[RECON_PROF_KINDS] = {
         "adjoint", "gram", "eig", "eps", "diag_sums", "weight_S", "resid_carry",
-        "cg_row_fwd", "cg_col_mask", "cg_row_inv_w", "cg_update", "lanczos", "hpd_inverse",
-        "cg_frame_aha", "cg_w_combine"};
+        "cg_row_fwd", "cg_col_mask", "cg_row_inv_w", "cg_update", "lanczos", "hpd_inverse"};
     return (kind >= 0 && kind < RECON_PROF_KINDS) ? names[kind] : "";
 }
 

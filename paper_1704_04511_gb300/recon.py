@@ -51,7 +51,7 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_voxel_weight", "recon_weight_direct", "recon_apply_normal_variant",
             "recon_tile_cache", "recon_tile_choice", "recon_fft_schedule_choice")
 
-PROF_KINDS = 15
+PROF_KINDS = 13
 
 
 class ReconError(RuntimeError):
@@ -290,9 +290,7 @@ def recon_solve_many(ctx, kspaces, masks_list, filts, lam: float, p: float, irls
 
 
 RECON_OPT_GRAPHS = 1
-RECON_OPT_CLUSTER_FFT = 2
 RECON_OPT_AUTOTUNE = 3
-RECON_OPT_THREE_PASS = 4
 RECON_OPT_INJECT_BARRIER_FAULT = 5
 RECON_OPT_TEST_WITHHOLD_ARRIVAL = 6
 RECON_OPT_BATCH_GROUP = 7
