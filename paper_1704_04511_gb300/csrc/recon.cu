@@ -1152,6 +1152,14 @@ size_t bytes_needed(const Dims& d) {
     return b;
 }
 
+// A solve that fails part-way through being enqueued may have work queued on the active slot's
+// stream that still writes the caller's buffers: wait for it before the error is returned (the
+// error stays the one reported).
+int drain_on_fail(recon_ctx* c, int rc) {
+    if (rc) cudaStreamSynchronize(c->stream);
+    return rc;
+}
+
 int solve_impl(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* masks,
                const recon_params* prm, void* image_out, int variant = RECON_VARIANT_PROPOSED) {
     int rc = set_device(c);
@@ -1160,13 +1168,13 @@ int solve_impl(recon_ctx* c, const Dims& d, const void* kspace, const uint8_t* m
     if (rc) return rc;
     Solve sv;
     rc = solve_prepare(c, d, kspace, masks, prm, image_out, &sv);
-    if (rc) return rc;
+    if (rc) return drain_on_fail(c, rc);
     if (variant == RECON_VARIANT_HLR_VOXEL) {
         rc = prepare_voxel(c, &sv);
-        if (rc) return rc;
+        if (rc) return drain_on_fail(c, rc);
     }
     rc = solve_enqueue_all(c, sv);
-    if (rc) return rc;
+    if (rc) return drain_on_fail(c, rc);
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return solve_check(c, sv);
 }
@@ -1604,7 +1612,7 @@ int recon_solve_coils(recon_ctx* c, recon_dims dd, const void* kspace, const uin
     if (rc) return rc;
     Solve sv;
     rc = solve_prepare(c, d, kspace, masks, prm, image_out, &sv);
-    if (rc) return rc;
+    if (rc) return drain_on_fail(c, rc);
     sv.coils = reinterpret_cast<const float2*>(coils);
     if (n_coils == 1) {  // unit modulus (to FP32 rounding) keeps A A^H a projection
         void* dev = nullptr;
@@ -1619,7 +1627,7 @@ int recon_solve_coils(recon_ctx* c, recon_dims dd, const void* kspace, const uin
         sv.coil_proj = m <= 1e-6f;
     }
     rc = solve_enqueue_all(c, sv);
-    if (rc) return rc;
+    if (rc) return drain_on_fail(c, rc);
     RC_CUDA(cudaStreamSynchronize(c->stream));
     return solve_check(c, sv);
 }
@@ -1757,6 +1765,9 @@ int solve_many_impl(recon_ctx* c, int n, const Dims* dims, const void* const* ks
         rc = select_slot(c, i);
         if (!rc) rc = solve_check(c, sv[i]);
     }
+    if (rc || e != cudaSuccess)  // nothing queued for the caller's buffers outlives the call
+        for (int i = 0; i < n && i < (int)c->slots.size(); ++i)
+            if (select_slot(c, i) == RECON_OK) cudaStreamSynchronize(c->stream);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(c, e, "batched solve");
     return rc;
@@ -1860,6 +1871,7 @@ int recon_submit(recon_ctx* c, recon_dims dd, const void* kspace, const uint8_t*
         cudaError_t e = cudaEventRecord(pd->done, c->stream);
         if (e != cudaSuccess) rc = cuda_fail(c, e, "cudaEventRecord");
     }
+    drain_on_fail(c, rc);  // a request that failed part-way leaves nothing running
     const int rc0 = select_slot(c, 0);
     if (rc) {
         if (rc == RECON_ENOMEM) c->err += " (request not admitted)";

@@ -183,3 +183,28 @@ def test_graph_replay_matches_direct_launches(R):
     third = run(torch.empty(shape, dtype=torch.complex64, device="cuda"))   # re-capture
     for got in (first, second, third):
         assert np.array_equal(got, direct)
+
+
+def test_batch_over_budget_fails_cleanly(R):
+    """A batch whose later slots do not fit the context's memory budget: the call reports
+    RECON_ENOMEM after the first slots' work was queued, waits for that work before returning,
+    and the context then solves as before (bitwise the result of a fresh context)."""
+    recon, ctx = R
+    w = synth.workload("tiny_32x32x8", n_irls=3)
+    ks, ms = _inputs(w, [0, 1, 2, 3])
+    filt = (w.N1, w.N2, w.M)
+    need = recon.recon_bytes_needed(tuple(ms[0].shape), filt)
+    ref = torch.empty(tuple(ms[0].shape), dtype=torch.complex64, device="cuda")
+    recon.recon_solve(ctx.h, ks[0], ms[0], filt, w.lam, w.p, w.n_irls, w.n_cg, ref)
+    small = recon.Context(0, mem_budget_bytes=int(2.5 * need))
+    try:
+        outs = [torch.empty(tuple(m.shape), dtype=torch.complex64, device="cuda") for m in ms]
+        with pytest.raises(recon.ReconError) as e:
+            recon.recon_solve_batch(small.h, ks, ms, filt, w.lam, w.p, w.n_irls, w.n_cg, outs)
+        assert e.value.code == recon.RECON_ENOMEM
+        torch.cuda.synchronize()
+        out = torch.empty_like(ref)
+        recon.recon_solve(small.h, ks[0], ms[0], filt, w.lam, w.p, w.n_irls, w.n_cg, out)
+        assert np.array_equal(out.cpu().numpy(), ref.cpu().numpy())
+    finally:
+        small.close()
