@@ -222,10 +222,13 @@ struct SweepSmem {
 };
 
 // Work items of the non-pivot CTAs: chunks of up to four tiles (I, J0 .. J0 + nj - 1) of one tile
-// row, J0 + nj <= I, and the diagonal tiles as items (I, I, 1), for every matrix b of the launch.
-// They are listed largest first (full chunks of every matrix, then chunks of 3, 2, 1 tiles, then
-// diagonal tiles) and dealt to the worker CTAs in a snake order (forward, backward, ...), which
-// balances the FP64 work per SM. Every CTA runs this enumeration and keeps its own items.
+// row, J0 + nj <= I + 1, for every matrix b of the launch: full chunks of four off-diagonal tiles,
+// then the rest of each row together with its diagonal tile (which shares the row's X = A_IK D_K),
+// then the diagonal tiles of the rows that have no rest (I a multiple of four) alone. Listed
+// largest first and dealt to the worker CTAs in a snake order (forward, backward, ...), which
+// balances the FP64 work per SM; at s = 243 that makes 136 items for 151 workers, one pass each
+// (with every diagonal tile an item of its own, 159 items left 8 CTAs two passes per step). Every
+// CTA runs this enumeration and keeps its own items.
 // Item code: (b << 26) | (I << 16) | (J0 << 4) | nj.
 struct ItemDeal {
     int workers, me, idx, n, cap;
@@ -255,23 +258,23 @@ RECON_HD int sweep_items(const int* nts, int nmat, int workers, int me, int* out
     for (int nj = kChunk - 1; nj >= 1; --nj)
         for (int b = 0; b < nmat; ++b)
             for (int I = 1; I < nts[b]; ++I)
-                if (I % kChunk == nj) deal_item(d, item_code(b, I, I - nj, nj));
+                if (I % kChunk == nj) deal_item(d, item_code(b, I, I - nj, nj + 1));
     for (int b = 0; b < nmat; ++b)
-        for (int I = 0; I < nts[b]; ++I) deal_item(d, item_code(b, I, I, 1));
+        for (int I = 0; I < nts[b]; I += kChunk) deal_item(d, item_code(b, I, I, 1));
     return me < 0 ? (d.idx + workers - 1) / workers : d.n;
 }
 
 // One work item at step K by the whole CTA (uniform control flow). Chunk: X = A_IK D_K is formed
 // once (quarters of q on the four groups), then group g updates tile (I, J0 + g):
 //   I == K:  new = D_K A_KJ;   J == K:  new = X;   otherwise  new = A_IJ - X A_KJ.
-// Diagonal tile (I, I): -D_K when I == K, skipped when I == K + 1 (the pivot CTA has it),
-// otherwise new = A_II - X (A_IK)^H.
+// Diagonal tile (I, I) (the last tile of its row's item): -D_K when I == K, skipped when
+// I == K + 1 (the pivot CTA has it), otherwise new = A_II - X A_KI with A_KI = (A_IK)^H.
 RECON_DEV void sweep_item(SweepSmem& sm, int code, int K, int nt, const double2* Ain,
                           double2* Aout, const double2* DK) {
     const int tid = threadIdx.x, g = tid / kTileT, e = tid % kTileT;
     const int i = e % kB, j = e / kB;
     const int I = (code >> 16) & 0x3ff, J0 = (code >> 4) & 0xfff, nj = code & 15;
-    const bool diag = (J0 == I);
+    const bool diag = (J0 == I);  // the diagonal tile alone
     if (diag && I == K + 1) return;
     if (diag && I == K) {
         if (g == 0) {
@@ -281,7 +284,8 @@ RECON_DEV void sweep_item(SweepSmem& sm, int code, int K, int nt, const double2*
         return;
     }
     const int J = J0 + g;
-    const bool mine = g < nj;
+    const bool dtile = (J == I);  // the row's diagonal tile at the end of a chunk
+    const bool mine = g < nj && !(dtile && I == K + 1);
     if (tid < kTileT) sm.D[e] = DK[e];
     else if (tid < 2 * kTileT && I != K) sm.P[e] = block_elem(Ain, I, K, e);
     double2 own = make_double2(0.0, 0.0);
@@ -294,8 +298,12 @@ RECON_DEV void sweep_item(SweepSmem& sm, int code, int K, int nt, const double2*
     if (I == K) {
         if (mine) {
             double2 v = make_double2(0.0, 0.0);
+            if (dtile) {
+                v = make_double2(-sm.D[e].x, -sm.D[e].y);
+            } else {
 #pragma unroll
-            for (int q = 0; q < kB; ++q) v = zfma(sm.D[i + kB * q], sm.B[g][q + kB * j], v);
+                for (int q = 0; q < kB; ++q) v = zfma(sm.D[i + kB * q], sm.B[g][q + kB * j], v);
+            }
             Aout[tile_off(I, J) + e] = v;
         }
     } else {
