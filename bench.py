@@ -69,7 +69,7 @@ ALU_KINDS = ("hpd_inverse", "lanczos")
 # benchmark workload (the first sweep of the bench's first solve; profiles/hpd_sweep_kernel_s243.md
 # gives the command). Only for the kernel versions those captures measured: drop an entry when
 # its kernel changes.
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {"hpd_inverse": 551680}
 
 
 def alg_flops(kind: str, w) -> float:
