@@ -124,7 +124,10 @@ def test_gram_matches_brute_force_lifting(R):
 
 WEIGHT_CASES = [("tiny-p0", 8, 32, 32, 5, 5, 2, 0.0), ("p0.7", 6, 16, 32, 3, 4, 3, 0.7),
                 ("perf-p0", 16, 256, 256, 9, 9, 3, 0.0), ("M1", 4, 16, 16, 4, 4, 1, 0.5),
-                ("odd-s", 5, 16, 16, 3, 5, 2, 0.0)]
+                ("odd-s", 5, 16, 16, 3, 5, 2, 0.0),
+                # the sweep's item shapes: one tile (s = 8), and nine tile rows (s = 72: rows 4
+                # and 8 end in a diagonal tile of their own, row 8 has two full chunks)
+                ("one-tile", 4, 16, 16, 2, 2, 2, 0.0), ("nine-rows", 6, 32, 32, 6, 6, 2, 0.0)]
 
 
 @pytest.mark.parametrize("method", ["auto", "eig"])
