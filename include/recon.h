@@ -109,6 +109,19 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims d, const void* const* kspa
                       const uint8_t* const* masks, recon_filter f, const recon_params* prm,
                       void* const* image_out);
 
+/* recon_solve_batch with the problems in host memory: kspace[i], masks[i] and image_out[i] are
+ * host pointers (same layouts and types as recon_solve_batch). Slot i copies its k-space and
+ * masks into device buffers of its own workspace on its own stream, solves, and copies its image
+ * back, so that the copies of one slot overlap the other slots' solves: with page-locked host
+ * memory (cudaHostAlloc, or a pinned torch tensor) the copies run asynchronously; pageable memory
+ * works but its copies do not overlap. Each slot's workspace grows by (8 or 4) T P Q + T P Q +
+ * 8 T P Q bytes (k-space, masks, image) on top of recon_bytes_needed. Results are bitwise those of
+ * recon_solve_batch on the same inputs. The call returns when every image_out[i] holds its
+ * result; on an error nothing queued is still running. 1 <= n <= RECON_MAX_BATCH. */
+int recon_solve_batch_host(recon_ctx* c, int n, recon_dims d, const void* const* kspace,
+                           const uint8_t* const* masks, recon_filter f, const recon_params* prm,
+                           void* const* image_out);
+
 /* Batched reconstruction of uneven problems: problem i has its own dims d[i] and filter f[i]
  * (grid, frame count and filter support may all differ; the parameters prm are shared), slot i
  * reading kspace[i], masks[i] and writing image_out[i]. Run as recon_solve_batch runs its slots:

@@ -1702,12 +1702,18 @@ namespace {
 // own stream, workspace and graph), or lockstep groups sharing their weight launches
 // (RECON_OPT_BATCH_GROUP), or direct launches (graphs off / eigensolver path). Arguments checked
 // by the callers.
+// host_io: kspace, masks and image_out are host pointers; slot i copies its inputs into device
+// buffers of its own workspace on its own stream before its solve and its image back after it,
+// so that one slot's copies overlap the other slots' work (one cudaMemcpyAsync per buffer).
 int solve_many_impl(recon_ctx* c, int n, const Dims* dims, const void* const* kspace,
-                    const uint8_t* const* masks, const recon_params* prm, void* const* image_out) {
+                    const uint8_t* const* masks, const recon_params* prm, void* const* image_out,
+                    bool host_io = false) {
     int rc = set_device(c);
     if (rc) return rc;
     rc = select_slot(c, 0);
     if (rc) return rc;
+    std::vector<void*> out_dev(n, nullptr);
+    auto image_bytes = [&](int i) { return dims[i].elems() * sizeof(float2); };
     // slot streams start after the work already queued on the context's stream
     cudaEvent_t start = nullptr;
     RC_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
@@ -1729,7 +1735,24 @@ int solve_many_impl(recon_ctx* c, int n, const Dims* dims, const void* const* ks
     for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
         rc = select_slot(c, i);
         if (!rc) e = cudaStreamWaitEvent(c->stream, start, 0);
-        if (!rc && e == cudaSuccess) rc = solve_prepare(c, dims[i], kspace[i], masks[i], prm, image_out[i], &sv[i]);
+        const void* kd = kspace[i];
+        const uint8_t* md = masks[i];
+        void* od = image_out[i];
+        if (host_io && !rc && e == cudaSuccess) {
+            const size_t ne = dims[i].elems();
+            const size_t kb = ne * (prm->kspace_bf16 ? 4 : 8);
+            void *kdev = nullptr, *mdev = nullptr;
+            rc = ensure(c, "io_kspace", kb, &kdev);
+            if (!rc) rc = ensure(c, "io_masks", ne, &mdev);
+            if (!rc) rc = ensure(c, "io_image", image_bytes(i), &out_dev[i]);
+            if (!rc) e = cudaMemcpyAsync(kdev, kspace[i], kb, cudaMemcpyHostToDevice, c->stream);
+            if (!rc && e == cudaSuccess)
+                e = cudaMemcpyAsync(mdev, masks[i], ne, cudaMemcpyHostToDevice, c->stream);
+            kd = kdev;
+            md = reinterpret_cast<const uint8_t*>(mdev);
+            od = out_dev[i];
+        }
+        if (!rc && e == cudaSuccess) rc = solve_prepare(c, dims[i], kd, md, prm, od, &sv[i]);
         if (!rc && e == cudaSuccess && !direct && !lockstep) rc = solve_enqueue_all(c, sv[i]);
         if (!rc && e == cudaSuccess && direct) rc = solve_begin(c, &sv[i]);
         // the set-up work of the slot (workspace clears, tuning) precedes the lockstep graph
@@ -1742,6 +1765,9 @@ int solve_many_impl(recon_ctx* c, int n, const Dims* dims, const void* const* ks
         rc = select_slot(c, 0);
         for (int i = 1; i < n && !rc && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->stream, done[i], 0);
         if (!rc && e == cudaSuccess) rc = batch_enqueue_lockstep(c, sv, c->batch_group);
+        for (int i = 0; host_io && i < n && !rc && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(image_out[i], out_dev[i], image_bytes(i), cudaMemcpyDeviceToHost,
+                                c->stream);
     }
     // direct launches: iterations interleaved over the slots so that every stream has work
     // queued early
@@ -1752,7 +1778,10 @@ int solve_many_impl(recon_ctx* c, int n, const Dims* dims, const void* const* ks
         }
     for (int i = 0; i < n && !rc && e == cudaSuccess && !lockstep; ++i) {
         rc = select_slot(c, i);
-        if (!rc) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+        if (!rc && host_io)
+            e = cudaMemcpyAsync(image_out[i], out_dev[i], image_bytes(i), cudaMemcpyDeviceToHost,
+                                c->stream);
+        if (!rc && e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
         if (!rc && e == cudaSuccess) e = cudaEventRecord(done[i], c->stream);
     }
     if (!rc && e == cudaSuccess) {
@@ -1797,6 +1826,21 @@ int recon_solve_batch(recon_ctx* c, int n, recon_dims dd, const void* const* ksp
     if (rc) return rc;
     std::vector<Dims> dims(n, d);
     return solve_many_impl(c, n, dims.data(), kspace, masks, prm, image_out);
+}
+
+int recon_solve_batch_host(recon_ctx* c, int n, recon_dims dd, const void* const* kspace,
+                           const uint8_t* const* masks, recon_filter f, const recon_params* prm,
+                           void* const* image_out) {
+    if (!c) return RECON_EINVAL;
+    if (n < 1 || n > RECON_MAX_BATCH) return fail(c, RECON_EINVAL, "need 1 <= n <= RECON_MAX_BATCH");
+    if (!kspace || !masks || !prm || !image_out) return fail(c, RECON_EINVAL, "null pointer");
+    for (int i = 0; i < n; ++i)
+        if (!kspace[i] || !masks[i] || !image_out[i]) return fail(c, RECON_EINVAL, "null pointer");
+    Dims d;
+    int rc = check_params(c, dd, f, prm, &d);
+    if (rc) return rc;
+    std::vector<Dims> dims(n, d);
+    return solve_many_impl(c, n, dims.data(), kspace, masks, prm, image_out, true);
 }
 
 int recon_solve_many(recon_ctx* c, int n, const recon_dims* dd, const recon_filter* f,

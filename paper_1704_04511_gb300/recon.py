@@ -44,7 +44,7 @@ EXPORTED = ("recon_create", "recon_destroy", "recon_last_error", "recon_bytes_ne
             "recon_solve", "recon_adjoint", "recon_fft2", "recon_gram", "recon_weight",
             "recon_apply_normal", "recon_apply_w", "recon_cg", "recon_profile",
             "recon_profile_read", "recon_profile_name", "recon_gram_static",
-            "recon_solve_batch", "recon_solve_many", "recon_set_option", "recon_submit", "recon_poll", "recon_t2fit",
+            "recon_solve_batch", "recon_solve_batch_host", "recon_solve_many", "recon_set_option", "recon_submit", "recon_poll", "recon_t2fit",
             "recon_solve_coils", "recon_adjoint_coils", "recon_apply_normal_coils",
             "recon_bytes_needed3", "recon_solve3", "recon_adjoint3", "recon_fft3", "recon_gram3",
             "recon_weight3", "recon_apply_normal3", "recon_solve_variant", "recon_gram_variant",
@@ -129,6 +129,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "recon_apply_normal_coils": (i, [vp, dims, filt, vp, vp, i, vp, d, vp, vp]),
             "recon_solve_batch": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp), filt,
                                       ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
+            "recon_solve_batch_host": (i, [vp, i, dims, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           filt, ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
             "recon_solve_many": (i, [vp, i, ctypes.POINTER(dims), ctypes.POINTER(filt),
                                      ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(recon_params), ctypes.POINTER(vp)]),
@@ -265,6 +267,35 @@ def recon_solve_batch(ctx, kspaces, masks_list, filt, lam: float, p: float, irls
     op = arr(*[_ptr(t) for t in image_outs])
     _check(ctx, load_library().recon_solve_batch(ctx, int(n), _dims(masks_list[0]), kp, mp,
                                                  _filt(filt), ctypes.byref(prm), op))
+
+
+def _host_ptr(t):
+    if t.is_cuda:
+        raise ValueError("expected a host (CPU) tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def recon_solve_batch_host(ctx, kspaces, masks_list, filt, lam: float, p: float, irls: int,
+                           cg: int, image_outs, gamma: float = 1.4, eps0_frac: float = 0.01,
+                           weight_method: int = RECON_WEIGHT_AUTO) -> None:
+    """recon_solve_batch on host tensors (pin them for overlapped copies); image_outs are host
+    tensors that hold the results when the call returns."""
+    import torch
+    n = len(kspaces)
+    if not (len(masks_list) == n == len(image_outs)):
+        raise ValueError("kspaces, masks_list and image_outs must have the same length")
+    bf16 = kspaces[0].dtype == torch.bfloat16
+    prm = recon_params(irls=int(irls), cg=int(cg), lambda_=float(lam), p=float(p),
+                       gamma=float(gamma), eps0_frac=float(eps0_frac), kspace_bf16=int(bf16),
+                       weight_method=int(weight_method))
+    arr = ctypes.c_void_p * n
+    kp = arr(*[_host_ptr(t) for t in kspaces])
+    mp = arr(*[_host_ptr(t) for t in masks_list])
+    op = arr(*[_host_ptr(t) for t in image_outs])
+    _check(ctx, load_library().recon_solve_batch_host(ctx, int(n), _dims(masks_list[0]), kp, mp,
+                                                      _filt(filt), ctypes.byref(prm), op))
 
 
 def recon_solve_many(ctx, kspaces, masks_list, filts, lam: float, p: float, irls: int, cg: int,

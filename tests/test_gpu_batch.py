@@ -208,3 +208,36 @@ def test_batch_over_budget_fails_cleanly(R):
         assert np.array_equal(out.cpu().numpy(), ref.cpu().numpy())
     finally:
         small.close()
+
+
+@pytest.mark.parametrize("pinned,group", [(True, 0), (False, 0), (True, 2)])
+def test_host_batch_equals_device_batch(R, pinned, group):
+    """recon_solve_batch_host (k-space, masks and images in host memory, copied per slot on the
+    slot's own stream) gives bitwise the images of recon_solve_batch on device copies of the same
+    inputs: page-locked and pageable host memory, independent slots and a lockstep group."""
+    recon, ctx = R
+    w = synth.workload("tiny_32x32x8", n_irls=4)
+    ks, ms = _inputs(w, [0, 1, 2])
+    filt = (w.N1, w.N2, w.M)
+    shape = tuple(ms[0].shape)
+    ref = [torch.empty(shape, dtype=torch.complex64, device="cuda") for _ in ms]
+    recon.recon_solve_batch(ctx.h, ks, ms, filt, w.lam, w.p, w.n_irls, w.n_cg, ref)
+    hk = [k.cpu() for k in ks]
+    hm = [m.cpu() for m in ms]
+    ho = [torch.full(shape, float("nan"), dtype=torch.complex64) for _ in ms]
+    if pinned:
+        hk = [t.pin_memory() for t in hk]
+        hm = [t.pin_memory() for t in hm]
+        ho = [t.pin_memory() for t in ho]
+    recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, group)
+    try:
+        for _ in range(2):  # the second call replays the slots' graphs
+            recon.recon_solve_batch_host(ctx.h, hk, hm, filt, w.lam, w.p, w.n_irls, w.n_cg, ho)
+            for a, b in zip(ho, ref):
+                assert np.array_equal(a.numpy(), b.cpu().numpy())
+            for o in ho:
+                o.fill_(float("nan"))
+    finally:
+        recon.recon_set_option(ctx.h, recon.RECON_OPT_BATCH_GROUP, 0)
+    with pytest.raises(ValueError):
+        recon.recon_solve_batch_host(ctx.h, ks, ms, filt, w.lam, w.p, w.n_irls, w.n_cg, ho)
