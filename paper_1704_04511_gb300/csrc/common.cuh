@@ -212,8 +212,32 @@ RECON_DEV void last_block_sum(double partial, double* parts, unsigned int* count
     }
 }
 
+// Lane-strided sum of a[lane], a[lane + 32], ... (i < n) in that order, with the loads issued
+// B at a time before their additions (the order of the additions is the plain loop's: the same
+// bits). Used by the Lanczos kernel, whose grid-wide sums wait on nothing else.
+template <int B = 8>
+RECON_DEV double lane_sum(const double* a, int lane, int n) {
+    double v = 0.0;
+    int i = lane;
+    for (; i + 32 * (B - 1) < n; i += 32 * B) {
+        double t[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) t[k] = a[i + 32 * k];
+#pragma unroll
+        for (int k = 0; k < B; ++k) v += t[k];
+    }
+    double t[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) t[k] = i + 32 * k < n ? a[i + 32 * k] : 0.0;
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+        if (i + 32 * k < n) v += t[k];
+    return v;
+}
+
 // Deterministic sum of n doubles in global memory by warp 0 alone (FP64 in 32 lanes only);
-// the result is valid in every lane of warp 0.
+// the result is valid in every lane of warp 0. (The plain loop: in the CG passes, whose own
+// loads are in flight meanwhile, lane_sum's batched loads measured slower.)
 RECON_DEV double warp0_sum_array(const double* a, int n) {
     double v = 0.0;
     for (int i = threadIdx.x; i < n; i += 32) v += a[i];

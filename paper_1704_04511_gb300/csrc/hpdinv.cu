@@ -549,7 +549,23 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
                     // row i of the Hermitian G is the conjugate of column i (contiguous)
                     double2 acc = make_double2(0.0, 0.0);
                     const double2* gcol = L.G + (size_t)i * L.s;
-                    for (int j = lane; j < L.s; j += 32) {
+                    int j = lane;
+                    for (; j + 32 * 3 < L.s; j += 32 * 4) {  // four loads of each in flight
+                        double2 g[4], uj[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            g[q] = gcol[j + 32 * q];
+                            uj[q] = L.u[j + 32 * q];
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            acc.x = fma(g[q].x, uj[q].x, acc.x);
+                            acc.x = fma(g[q].y, uj[q].y, acc.x);
+                            acc.y = fma(g[q].x, uj[q].y, acc.y);
+                            acc.y = fma(-g[q].y, uj[q].x, acc.y);
+                        }
+                    }
+                    for (; j < L.s; j += 32) {
                         const double2 g = gcol[j], uj = L.u[j];
                         acc.x = fma(g.x, uj.x, acc.x);
                         acc.x = fma(g.y, uj.y, acc.x);
@@ -577,9 +593,7 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
         for (int b = warp; b < n; b += kThreads / 32) {
             if (k >= s_m[b]) continue;
             const double* pa = bt.mt[b].part + (size_t)(k & 1) * 2 * gridDim.x;
-            double v = 0.0;
-            for (int c = lane; c < (int)gridDim.x; c += 32) v += pa[c];
-            v = warp_sum(v);
+            const double v = warp_sum(lane_sum(pa, lane, (int)gridDim.x));
             if (lane == 0) s_alpha[b] = v;
         }
         __syncthreads();
@@ -612,9 +626,7 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
         for (int b = warp; b < n; b += kThreads / 32) {
             if (k >= s_m[b]) continue;
             const double* pb = bt.mt[b].part + (size_t)(k & 1) * 2 * gridDim.x + gridDim.x;
-            double v = 0.0;
-            for (int c = lane; c < (int)gridDim.x; c += 32) v += pb[c];
-            const double b2 = warp_sum(v);
+            const double b2 = warp_sum(lane_sum(pb, lane, (int)gridDim.x));
             if (lane == 0) {
                 const double bnew = sqrt(b2);
                 if ((int)blockIdx.x == b) {  // the CTA that reads them for the multisection
