@@ -108,7 +108,7 @@ s_stage1_kernel(const double2* __restrict__ dsum, int N1, int N2, int Q,
     const int row = blockIdx.x;  // pair * L1 + i1
     const double2* drow = dsum + (size_t)row * L2;
     const int d2m0 = (Q - (N2 - 1) % Q) % Q;  // (-(N2 - 1)) mod Q
-    for (int r2 = threadIdx.x; r2 < Q; r2 += blockDim.x) {
+    for (int r2 = blockIdx.y * blockDim.x + threadIdx.x; r2 < Q; r2 += blockDim.x * gridDim.y) {
         double2 acc = make_double2(0.0, 0.0);
         int ti = (d2m0 * r2) % Q;
         for (int i2 = 0; i2 < L2; ++i2) {
@@ -120,8 +120,47 @@ s_stage1_kernel(const double2* __restrict__ dsum, int N1, int N2, int Q,
     }
 }
 
-// S[pair][r1][r2] = sum_{d1} Z[pair][d1][r2] w_P^{d1 r1}  (FP32): one CTA per image row r1, its
-// L1 twiddles in shared memory, every pair and column.
+// S[pair][r1][r2] = sum_{d1} Z[pair][d1][r2] w_P^{d1 r1}  (FP32), for L1 <= kL1Reg: thread
+// (pair, column r2, block of kRB rows r1) holds the L1 values Z[pair][.][r2] in registers and
+// forms its kRB outputs, each summed in d1 order with the twiddles of s_stage2_kernel (the same
+// bits); Z is read once instead of once per image row.
+constexpr int kL1Reg = 20;
+constexpr int kRB = 8;
+__global__ void __launch_bounds__(kThreads)
+s_stage2_reg_kernel(const float2* __restrict__ Z, int N1, int P, int Q, int npair,
+                    const float2* __restrict__ twP, float2* __restrict__ S) {
+    __shared__ float2 tws[kMaxL1];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) tws[i] = twP[i];
+    __syncthreads();
+    const int L1 = 2 * N1 - 1;
+    const int nrb = (P + kRB - 1) / kRB;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)npair * nrb * Q) return;
+    const int r2 = (int)(g % Q), rb = (int)((g / Q) % nrb), pr = (int)(g / ((long long)Q * nrb));
+    const float2* zp = Z + (size_t)pr * L1 * Q + r2;
+    float2 z[kL1Reg];
+#pragma unroll
+    for (int i1 = 0; i1 < kL1Reg; ++i1) z[i1] = i1 < L1 ? zp[(size_t)i1 * Q] : make_float2(0.f, 0.f);
+    const int d1m0 = (P - (N1 - 1) % P) % P;  // (-(N1 - 1)) mod P
+    for (int u = 0; u < kRB; ++u) {
+        const int r1 = rb * kRB + u;
+        if (r1 >= P) break;
+        int ti = (d1m0 * r1) % P;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i1 = 0; i1 < kL1Reg; ++i1) {
+            if (i1 < L1) {
+                acc = cfma(z[i1], tws[ti], acc);
+                ti += r1;
+                if (ti >= P) ti -= P;
+            }
+        }
+        S[((size_t)pr * P + r1) * Q + r2] = acc;
+    }
+}
+
+// The same for any L1: one CTA per image row r1, its L1 twiddles in shared memory, every pair
+// and column.
 __global__ void __launch_bounds__(kThreads)
 s_stage2_kernel(const float2* __restrict__ Z, int N1, int P, int Q, int npair,
                 const float2* __restrict__ twP, float2* __restrict__ S) {
@@ -246,18 +285,28 @@ cudaError_t launch_weight_S(const Dims& d, const Twiddles& tw, const double2* ds
                             float2* S, cudaStream_t st) {
     float2* Z = reinterpret_cast<float2*>(Z_);
     const int planes = d.npair() * d.L3();  // (pair, d3) planes of the summed diagonals
-    s_stage1_kernel<<<planes * d.L1(), kThreads, 0, st>>>(dsum, d.N1, d.N2, d.Q, tw.twQd, Z);
+    // FP64 sums: two CTAs of 128 columns per (plane, d1) row where the columns allow, so that
+    // the FP64 work spreads over more SMs
+    const int s1_threads = d.Q >= 256 ? 128 : kThreads;
+    const dim3 s1_grid(planes * d.L1(), (d.Q + s1_threads - 1) / s1_threads);
+    s_stage1_kernel<<<s1_grid, s1_threads, 0, st>>>(dsum, d.N1, d.N2, d.Q, tw.twQd, Z);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (d.L1() > kMaxL1 || d.L3() > kMaxL1) return cudaErrorInvalidValue;
-    if (d.R == 1) {
-        s_stage2_kernel<<<d.P, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, d.npair(), tw.twP, S);
+    if (d.L1() > kMaxL1 || d.L3() > kMaxL1 || d.P > kMaxL1) return cudaErrorInvalidValue;
+    auto stage2 = [&](int np, float2* out) {
+        if (d.L1() <= kL1Reg) {
+            const long long n = (long long)np * ((d.P + kRB - 1) / kRB) * d.Q;
+            s_stage2_reg_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+                Z, d.N1, d.P, d.Q, np, tw.twP, out);
+        } else {
+            s_stage2_kernel<<<d.P, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, np, tw.twP, out);
+        }
         return cudaGetLastError();
-    }
+    };
+    if (d.R == 1) return stage2(d.npair(), S);
     float2* Z2 = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Z) +
                                            align256((size_t)planes * d.L1() * d.Q * sizeof(float2)));
-    s_stage2_kernel<<<d.P, kThreads, 0, st>>>(Z, d.N1, d.P, d.Q, planes, tw.twP, Z2);
-    e = cudaGetLastError();
+    e = stage2(planes, Z2);
     if (e != cudaSuccess) return e;
     const size_t npx = (size_t)d.P * d.Q;
     const int gx = (int)((npx + kThreads - 1) / kThreads);
