@@ -40,21 +40,17 @@ constexpr long long kSpinLimit = 1LL << 24;  // polls (~1 us each at most) befor
 // gap is ~0.2 %, by ~40 (plain Lanczos from the start vector below, checked in FP64 on the CPU).
 constexpr int kLanczosMax = 64;
 
-struct GridBar {
+struct alignas(8) GridBar {
     unsigned int word;  // bit 31 flips when the last CTA arrives; bits 0-30 count arrivals
-    int err;
+    int err;            // read with `word` in one 8-byte load
     unsigned int pad[2];
 };
 static_assert(sizeof(GridBar) <= kCoopBarrierBytes, "grid barrier exceeds its scratch header");
 
-RECON_DEV unsigned int ld_acquire(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-RECON_DEV int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+// The barrier word and the error word in one acquire load (GridBar: word at offset 0, err at 4).
+RECON_DEV unsigned long long ld_acquire_pair(const GridBar* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 RECON_DEV unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
@@ -68,32 +64,36 @@ RECON_DEV unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
 // last CTA arrives and the low bits return to zero. The barrier only looks at the flip, so a
 // launch that completed every barrier leaves a valid starting state for the next one: the word
 // is zeroed once when its scratch is allocated and again by the host after a reported failure,
-// not before every launch. Thread 0 of each CTA then polls the word with
-// acquire loads. Returns false (and sets gb->err) if the wait exceeded `polls` polls; after a
-// failure every later call returns false at once so the kernel can unwind. Test hook: the CTA
-// numbered `fault.withhold` (> 0) returns false at once without arriving, as a CTA that was lost
-// would, so that the others' waits run out.
+// not before every launch. Thread 0 of each CTA arrives at once (no load before its atomic: the
+// last arrival, which releases the others, then costs one round trip); the arrival that flips
+// bit 31 goes on without reading anything, the others poll the word and the error word together
+// (one acquire load per poll). Returns false (and sets gb->err) if the wait exceeded `polls`
+// polls, or false when a poll finds the error word set, so that after a failure every CTA leaves
+// at its next barrier that it does not complete last (a CTA that completes one goes on to the
+// next, where the error stops it). Test hook: the CTA numbered `fault.withhold` (> 0) returns
+// false at once without arriving, as a CTA that was lost would, so that the others' waits run
+// out.
 RECON_DEV bool grid_barrier(GridBar* gb, const CoopFault& fault) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = (ld_acquire(&gb->err) == 0);
-        if (ok && fault.withhold > 0 && (int)blockIdx.x == fault.withhold) ok = 0;
+        int ok = !(fault.withhold > 0 && (int)blockIdx.x == fault.withhold);
         if (ok) {
             __threadfence();
             const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
             const unsigned int old = atom_add_acq_rel(&gb->word, inc);
-            // the arrival that flips bit 31 is the last one: it need not poll
             const bool last = (((old + inc) ^ old) & 0x80000000u) != 0u;
             const long long limit = fault.polls > 0 ? fault.polls : kSpinLimit;
             long long it = 0;
-            while (!last && ((ld_acquire(&gb->word) ^ old) & 0x80000000u) == 0u) {
-                if (++it > limit) {
-                    atomicExch(&gb->err, 1);
+            while (!last) {
+                const unsigned long long we = ld_acquire_pair(gb);
+                if ((unsigned int)(we >> 32) != 0u) {  // gb->err
                     ok = 0;
                     break;
                 }
-                if ((it & 1023) == 0 && ld_acquire(&gb->err) != 0) {
+                if ((((unsigned int)we ^ old) & 0x80000000u) != 0u) break;
+                if (++it > limit) {
+                    atomicExch(&gb->err, 1);
                     ok = 0;
                     break;
                 }
@@ -105,7 +105,6 @@ RECON_DEV bool grid_barrier(GridBar* gb, const CoopFault& fault) {
     __syncthreads();
     return ok_s != 0;
 }
-
 
 // Synchronise the 64 threads of tile group g (named barrier g + 1; 0 is __syncthreads).
 RECON_DEV void group_sync(int g) {
