@@ -106,6 +106,52 @@ RECON_DEV bool grid_barrier(GridBar* gb, const CoopFault& fault) {
     return ok_s != 0;
 }
 
+// The two halves of grid_barrier for a CTA that arrives at one barrier and waits for its release
+// later or not at all (the pivot CTAs of the sweep). A CTA may arrive at the next barrier only
+// after the previous one was released; every arrival then carries the previous flip, and bit 31
+// flips once per barrier as in grid_barrier. barrier_arrive: thread 0, after a __syncthreads
+// that follows the CTA's writes; returns the word before its add. barrier_wait: one thread;
+// false when the error word is set or the wait exceeded its poll limit (which sets it).
+RECON_DEV unsigned int barrier_arrive(GridBar* gb) {
+    __threadfence();
+    const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    return atom_add_acq_rel(&gb->word, inc);
+}
+RECON_DEV bool barrier_wait(GridBar* gb, unsigned int old, const CoopFault& fault) {
+    const long long limit = fault.polls > 0 ? fault.polls : kSpinLimit;
+    for (long long it = 0;; ++it) {
+        const unsigned long long we = ld_acquire_pair(gb);
+        if ((unsigned int)(we >> 32) != 0u) return false;
+        if ((((unsigned int)we ^ old) & 0x80000000u) != 0u) break;
+        if (it > limit) {
+            atomicExch(&gb->err, 1);
+            return false;
+        }
+    }
+    __threadfence();
+    return true;
+}
+
+// Wait (one thread) until *flag >= want, bounded like the barrier waits; false when the error
+// word of gb is set meanwhile or the wait ran out (which sets it).
+RECON_DEV bool flag_wait(const unsigned int* flag, unsigned int want, GridBar* gb,
+                         const CoopFault& fault) {
+    const long long limit = fault.polls > 0 ? fault.polls : kSpinLimit;
+    for (long long it = 0;; ++it) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v >= want) return true;
+        if ((it & 255) == 255) {
+            const unsigned long long we = ld_acquire_pair(gb);
+            if ((unsigned int)(we >> 32) != 0u) return false;
+        }
+        if (it > limit) {
+            atomicExch(&gb->err, 1);
+            return false;
+        }
+    }
+}
+
 // Synchronise the 64 threads of tile group g (named barrier g + 1; 0 is __syncthreads).
 RECON_DEV void group_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kTileT) : "memory");
@@ -187,7 +233,9 @@ struct SweepMat {
     double2* G;            // s x s column-major; H = (G + eps I)^-1 written over it
     const double* eps;     // device scalar
     double2 *A0, *A1;      // lower tiles, ping-pong
-    double2* Dbuf;         // two pivot inverses
+    double2* Dbuf;         // three pivot inverses (D_K in slot K mod 3)
+    double2* hand;         // the helper's tiles for the chain, two slots of two tiles
+    unsigned int* flag;    // the helper's step count (set to K + 1 once step K's tiles are out)
     int* err_out;          // status word (may be null)
     int s, nt;
 };
@@ -220,12 +268,20 @@ struct SweepSmem {
     int nitem;
 };
 
+// A pivot CTA's inputs for its next chain: A_{K+1,K} and A_{K+1,K+1} after step K - 1, ping-pong
+// over K; its last arrival and a failure flag.
+struct PivotSmem {
+    double2 tp[2][2][kTileT];
+    unsigned int old;
+    int fail;
+};
+
 // Work items of the non-pivot CTAs: chunks of up to four tiles (I, J0 .. J0 + nj - 1) of one tile
 // row, J0 + nj <= I + 1, for every matrix b of the launch: full chunks of four off-diagonal tiles,
 // then the rest of each row together with its diagonal tile (which shares the row's X = A_IK D_K),
 // then the diagonal tiles of the rows that have no rest (I a multiple of four) alone. Listed
 // largest first and dealt to the worker CTAs in a snake order (forward, backward, ...), which
-// balances the FP64 work per SM; at s = 243 that makes 136 items for 151 workers, one pass each
+// balances the FP64 work per SM; at s = 243 that makes 136 items for 150 workers, one pass each
 // (with every diagonal tile an item of its own, 159 items left 8 CTAs two passes per step). Every
 // CTA runs this enumeration and keeps its own items.
 // Item code: (b << 26) | (I << 16) | (J0 << 4) | nj.
@@ -328,17 +384,17 @@ RECON_DEV void sweep_item(SweepSmem& sm, int code, int K, int nt, const double2*
     __syncthreads();
 }
 
-// The pivot CTA at step K: tile (K+1, K+1) with all eight warps, X = A_{K+1,K} D_K and
-// new = own - X (A_{K+1,K})^H (quarters of q), then its inverse D_{K+1} by group 0. The tile's
-// swept value itself is never read again (step K+1 writes -D_{K+1} there).
-RECON_DEV void sweep_pivot(SweepSmem& sm, int K, const double2* Ain, const double2* DK,
-                           double2* Dnext) {
+// The pivot CTA at step K, first half: the next pivot tile's Schur update with all eight warps,
+// X = A_{K+1,K} D_K and S = A_{K+1,K+1} - X (A_{K+1,K})^H (quarters of q), into sm.X; the 8 x 8
+// inverse of S (D_{K+1}) follows on group 0. tp = {A_{K+1,K}, A_{K+1,K+1}} after step K - 1, from
+// the matrix's helper CTA (or the initial matrix at K = 0). The tile's swept value itself is never
+// read again (step K+1 writes -D_{K+1} there).
+RECON_DEV void sweep_pivot(SweepSmem& sm, const double2* DK, const double2 (*tp)[kTileT]) {
     const int tid = threadIdx.x, g = tid / kTileT, e = tid % kTileT;
     const int i = e % kB, j = e / kB;
-    const int piv = K + 1;
     if (tid < kTileT) sm.D[e] = DK[e];
-    else if (tid < 2 * kTileT) sm.P[e] = Ain[tile_off(piv, K) + e];
-    const double2 own = Ain[tile_off(piv, piv) + e];
+    else if (tid < 2 * kTileT) sm.P[e] = tp[0][e];
+    const double2 own = tid < kTileT ? tp[1][e] : make_double2(0.0, 0.0);
     __syncthreads();
     double2 x = make_double2(0.0, 0.0);
 #pragma unroll
@@ -355,19 +411,52 @@ RECON_DEV void sweep_pivot(SweepSmem& sm, int K, const double2* Ain, const doubl
     if (tid < kTileT) {
         const double2 sum = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
         sm.X[e] = make_double2(own.x - sum.x, own.y - sum.y);  // the same thread read X[e] above
-        group_sync(0);
-        tile_inverse(sm.X, sm.T1, Dnext);
+    }
+}
+
+// The helper CTA of a matrix at step K: the tiles (K+2, K+1) and (K+2, K+2) after step K, from
+// A = the matrix after step K - 1 and D_K, by the arithmetic of the workers' items (X = A_{K+2,K} D_K
+// from the same four quarter partials added in the same order, then new = A_{K+2,J} - X A_{K,J}),
+// so that they are bitwise the tiles the workers write; out: the two tiles, the next chain's
+// inputs. Run on an SM of its own so that the chain keeps its SM's FP64 pipe.
+RECON_DEV void helper_tiles(SweepSmem& sm, int K, const double2* A, const double2* DK,
+                            double2* out) {
+    const int tid = threadIdx.x, g = tid / kTileT, e = tid % kTileT;
+    const int i = e % kB, j = e / kB;
+    const int R = K + 2;
+    if (g == 0) sm.D[e] = DK[e];
+    else if (g == 1) sm.P[e] = A[tile_off(R, K) + e];
+    double2 own = make_double2(0.0, 0.0);
+    if (g < 2) {
+        own = A[tile_off(R, K + 1 + g) + e];
+        sm.B[g][e] = block_elem(A, K, K + 1 + g, e);
+    }
+    __syncthreads();
+    double2 x = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 2 * g; q < 2 * g + 2; ++q) x = zfma(sm.P[i + kB * q], sm.D[q + kB * j], x);
+    sm.Xp[g][e] = x;
+    __syncthreads();
+    if (g == 0) sm.X[e] = zadd(zadd(sm.Xp[0][e], sm.Xp[1][e]), zadd(sm.Xp[2][e], sm.Xp[3][e]));
+    __syncthreads();
+    if (g < 2) {
+        double2 v = own;
+#pragma unroll
+        for (int q = 0; q < kB; ++q) v = zfms(sm.X[i + kB * q], sm.B[g][q + kB * j], v);
+        out[g * kTileT + e] = v;
     }
 }
 
 // One cooperative launch sweeps every matrix of the batch: one grid barrier per pivot step serves
 // all of them (the largest tile count sets the number of steps; a matrix with fewer tiles is done
-// earlier and its CTAs skip its later steps). CTA b (< n) carries matrix b's pivot chain, the
-// other CTAs share the work items of all matrices. Every tile is computed by the same arithmetic
-// as in a launch of its matrix alone, so the results do not depend on the batch.
+// earlier and its CTAs skip its later steps). CTA b (< n) carries matrix b's pivot chain, CTA
+// n + b is its helper, the other CTAs share the work items of all matrices. Every tile is computed
+// by the same arithmetic as in a launch of its matrix alone, so the results do not depend on the
+// batch.
 __global__ void __launch_bounds__(kThreads, 2)
 hpd_sweep_kernel(SweepBatch bt, GridBar* gb, CoopFault fault) {
     __shared__ SweepSmem sm;
+    __shared__ PivotSmem ps;
     const int tid = threadIdx.x;
     const int g = tid / kTileT, e = tid % kTileT;
     const int i = e % kB, j = e / kB;
@@ -376,8 +465,10 @@ hpd_sweep_kernel(SweepBatch bt, GridBar* gb, CoopFault fault) {
     if (tid == 0) {
         int nts[kMaxHpdBatch];
         for (int b = 0; b < n; ++b) nts[b] = bt.m[b].nt;
-        sm.nitem = (int)blockIdx.x < n
-                       ? 0 : sweep_items(nts, n, gridDim.x - n, blockIdx.x - n, sm.item, kMaxItems);
+        sm.nitem = (int)blockIdx.x < 2 * n
+                       ? 0 : sweep_items(nts, n, gridDim.x - 2 * n, blockIdx.x - 2 * n, sm.item,
+                                         kMaxItems);
+        if ((int)blockIdx.x < n) *bt.m[blockIdx.x].flag = 0u;  // before the first barrier
         if (sm.nitem > kMaxItems) sm.nitem = kMaxItems;  // the host refuses such sizes
     }
     // A0 = pad(G + eps I), lower tiles; padding is the identity. Only the lower triangle of G is
@@ -410,22 +501,72 @@ hpd_sweep_kernel(SweepBatch bt, GridBar* gb, CoopFault fault) {
     }
     if (!grid_barrier(gb, fault)) return report_batch(bt, 1);
 
-    for (int K = 0; K < bt.nt_max; ++K) {
-        if ((int)blockIdx.x < n) {
-            const SweepMat& mt = bt.m[blockIdx.x];
-            if (K + 1 < mt.nt)
-                sweep_pivot(sm, K, (K & 1) ? mt.A1 : mt.A0, mt.Dbuf + (K & 1) * kTileT,
-                            mt.Dbuf + ((K + 1) & 1) * kTileT);
-        } else {
+    if ((int)blockIdx.x < n) {
+        // Pivot CTA of matrix blockIdx.x, one barrier ahead of the workers. Step K: the chain (the
+        // Schur update of tile (K+1, K+1) on all warps, then its inverse D_{K+1} on group 0) needs
+        // D_K and the row-(K+1) tiles after step K - 1, which the matrix's helper CTA formed
+        // during step K - 1; meanwhile group 1 waits for the helper's step-K tiles (the helper
+        // forms them once it has seen the release of the barrier that ended step K - 1, so they
+        // also tell that this CTA may arrive at the next barrier). Then the CTA arrives at the
+        // barrier that ends step K without waiting for its release: the release latency leaves
+        // the chain's path. D_K lives in slot K mod 3 of Dbuf (the chain writes D_{K+2} while slow
+        // workers may still read D_K).
+        const SweepMat& mt = bt.m[blockIdx.x];
+        if (mt.nt > 1 && tid < 2 * kTileT) ps.tp[0][tid / kTileT][e] = mt.A0[tile_off(1, tid / kTileT) + e];
+        if (tid == 0) ps.fail = 0;
+        __syncthreads();
+        for (int K = 0; K < bt.nt_max; ++K) {
+            const bool chain = K + 1 < mt.nt;
+            if (chain) sweep_pivot(sm, mt.Dbuf + (K % 3) * kTileT, ps.tp[K & 1]);
+            if (g == 0) {
+                if (chain) {
+                    group_sync(0);
+                    tile_inverse(sm.X, sm.T1, mt.Dbuf + ((K + 1) % 3) * kTileT);
+                }
+            } else if (g == 1) {
+                if (e == 0 && !flag_wait(mt.flag, (unsigned int)(K + 1), gb, fault)) ps.fail = 1;
+                group_sync(1);
+                if (!ps.fail && K + 2 < mt.nt) {
+                    const double2* h = mt.hand + ((K + 1) & 1) * 2 * kTileT;
+                    ps.tp[(K + 1) & 1][0][e] = h[e];
+                    ps.tp[(K + 1) & 1][1][e] = h[kTileT + e];
+                }
+            }
+            __syncthreads();
+            if (ps.fail) return report_batch(bt, 1);
+            if (tid == 0) ps.old = barrier_arrive(gb);
+            __syncthreads();
+        }
+        if (tid == 0 && !barrier_wait(gb, ps.old, fault)) ps.fail = 1;
+        __syncthreads();
+        if (ps.fail) return report_batch(bt, 1);
+    } else if ((int)blockIdx.x < 2 * n) {
+        // Helper CTA of matrix blockIdx.x - n: after the release of the barrier that ended step
+        // K - 1, the row-(K+2) tiles after step K for the pivot CTA's next chain, then its flag.
+        const SweepMat& mt = bt.m[blockIdx.x - n];
+        for (int K = 0; K < bt.nt_max; ++K) {
+            if (K + 2 < mt.nt)
+                helper_tiles(sm, K, (K & 1) ? mt.A1 : mt.A0, mt.Dbuf + (K % 3) * kTileT,
+                             mt.hand + ((K + 1) & 1) * 2 * kTileT);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(mt.flag),
+                             "r"((unsigned int)(K + 1)) : "memory");
+            }
+            if (!grid_barrier(gb, fault)) return report_batch(bt, 1);
+        }
+    } else {
+        for (int K = 0; K < bt.nt_max; ++K) {
             for (int it = 0; it < sm.nitem; ++it) {
                 const int code = sm.item[it];
                 const SweepMat& mt = bt.m[code >> 26];
                 if (K < mt.nt)
                     sweep_item(sm, code, K, mt.nt, (K & 1) ? mt.A1 : mt.A0, (K & 1) ? mt.A0 : mt.A1,
-                               mt.Dbuf + (K & 1) * kTileT);
+                               mt.Dbuf + (K % 3) * kTileT);
             }
+            if (!grid_barrier(gb, fault)) return report_batch(bt, 1);
         }
-        if (!grid_barrier(gb, fault)) return report_batch(bt, 1);
     }
     // H = -A (s x s, full, column-major) written over G
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + tid;
@@ -772,7 +913,7 @@ cudaError_t set_barrier_error(void* scratch, cudaStream_t st) {
 size_t hpd_scratch_bytes(const Dims& d) {
     const size_t nt = (size_t)tiles_per_side(d.s());
     const size_t nlt = nt * (nt + 1) / 2;
-    return kCoopBarrierBytes + 2 * nlt * kTileT * sizeof(double2) + 2 * kTileT * sizeof(double2) + 1024;
+    return kCoopBarrierBytes + 2 * nlt * kTileT * sizeof(double2) + 7 * kTileT * sizeof(double2) + 1024;
 }
 
 size_t lanczos_scratch_bytes(const Dims& d, int grid_max) {
@@ -784,7 +925,7 @@ cudaError_t launch_hpd_inverse_batch(const HpdJob* jobs, int n, void* barrier_sc
                                      cudaStream_t st, CoopFault fault) {
     if (n < 1 || n > kMaxHpdBatch || !barrier_scratch) return cudaErrorInvalidValue;
     int grid = 0;
-    if (coop_grid((const void*)hpd_sweep_kernel, &grid) || grid < n + 1)
+    if (coop_grid((const void*)hpd_sweep_kernel, &grid) || grid < 2 * n + 1)
         return cudaErrorInvalidConfiguration;
     SweepBatch bt = {};
     bt.n = n;
@@ -803,6 +944,10 @@ cudaError_t launch_hpd_inverse_batch(const HpdJob* jobs, int n, void* barrier_sc
         mt.A1 = reinterpret_cast<double2*>(p);
         p += nlt * kTileT * sizeof(double2);
         mt.Dbuf = reinterpret_cast<double2*>(p);
+        p += 3 * kTileT * sizeof(double2);
+        mt.hand = reinterpret_cast<double2*>(p);
+        p += 4 * kTileT * sizeof(double2);
+        mt.flag = reinterpret_cast<unsigned int*>(p);
         mt.err_out = jobs[b].err_out;
         mt.s = s;
         mt.nt = nt;
@@ -810,7 +955,7 @@ cudaError_t launch_hpd_inverse_batch(const HpdJob* jobs, int n, void* barrier_sc
         if (nt > bt.nt_max) bt.nt_max = nt;
     }
     // every work item must fit the per-CTA item table
-    if (sweep_items(nts, n, grid - n, -1, nullptr, 0) > kMaxItems) return cudaErrorInvalidValue;
+    if (sweep_items(nts, n, grid - 2 * n, -1, nullptr, 0) > kMaxItems) return cudaErrorInvalidValue;
     GridBar* gb = reinterpret_cast<GridBar*>(barrier_scratch);
     return launch_coop(hpd_sweep_kernel, grid, st, bt, gb, fault);
 }
