@@ -117,6 +117,13 @@ RECON_DEV unsigned int barrier_arrive(GridBar* gb) {
     const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
     return atom_add_acq_rel(&gb->word, inc);
 }
+// The arrival alone, for a CTA that never waits for this barrier: a reduction with release
+// semantics, which does not wait for the word's old value to come back.
+RECON_DEV void barrier_arrive_only(GridBar* gb) {
+    __threadfence();
+    const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&gb->word), "r"(inc) : "memory");
+}
 RECON_DEV bool barrier_wait(GridBar* gb, unsigned int old, const CoopFault& fault) {
     const long long limit = fault.polls > 0 ? fault.polls : kSpinLimit;
     for (long long it = 0;; ++it) {
@@ -534,7 +541,11 @@ hpd_sweep_kernel(SweepBatch bt, GridBar* gb, CoopFault fault) {
             }
             __syncthreads();
             if (ps.fail) return report_batch(bt, 1);
-            if (tid == 0) ps.old = barrier_arrive(gb);
+            // only the last arrival's old value is needed (its release is waited for below)
+            if (tid == 0) {
+                if (K + 1 < bt.nt_max) barrier_arrive_only(gb);
+                else ps.old = barrier_arrive(gb);
+            }
             __syncthreads();
         }
         if (tid == 0 && !barrier_wait(gb, ps.old, fault)) ps.fail = 1;
