@@ -117,12 +117,13 @@ RECON_DEV unsigned int barrier_arrive(GridBar* gb) {
     const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
     return atom_add_acq_rel(&gb->word, inc);
 }
-// The arrival alone, for a CTA that never waits for this barrier: a reduction with release
-// semantics, which does not wait for the word's old value to come back.
+// The arrival alone, for a CTA that never waits for this barrier: an acquire-release fence and a
+// relaxed reduction (together a release of the CTA's writes ordered before it by the caller's
+// __syncthreads), which does not wait for the word's old value to come back.
 RECON_DEV void barrier_arrive_only(GridBar* gb) {
-    __threadfence();
     const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&gb->word), "r"(inc) : "memory");
+    asm volatile("fence.acq_rel.gpu;\n\tred.relaxed.gpu.global.add.u32 [%0], %1;"
+                 ::"l"(&gb->word), "r"(inc) : "memory");
 }
 RECON_DEV bool barrier_wait(GridBar* gb, unsigned int old, const CoopFault& fault) {
     const long long limit = fault.polls > 0 ? fault.polls : kSpinLimit;
@@ -187,7 +188,7 @@ RECON_DEV double rcp_pivot(double a) {
 // while the reciprocal is being computed, so that one FMA per component follows it on the
 // dependent chain. Every thread forms the reciprocal itself: a warp issues the same FP64
 // instructions for one lane or for 32.
-RECON_DEV void tile_inverse(double2* T0, double2* T1, double2* out) {
+RECON_DEV void tile_inverse(double2* T0, double2* T1, double2* out, double2* out_smem = nullptr) {
     const int e = threadIdx.x % kTileT, i = e % kB, j = e / kB;
     double2* a = T0;
     double2* b = T1;
@@ -214,7 +215,9 @@ RECON_DEV void tile_inverse(double2* T0, double2* T1, double2* out) {
     // complements) amplify step after step; its Hermitian part keeps them consistent and is as
     // accurate.
     const double2 v = a[i + j * kB], w = a[j + i * kB];
-    out[i + j * kB] = make_double2(-0.5 * (v.x + w.x), -0.5 * (v.y - w.y));
+    const double2 d = make_double2(-0.5 * (v.x + w.x), -0.5 * (v.y - w.y));
+    out[i + j * kB] = d;
+    if (out_smem) out_smem[i + j * kB] = d;  // the pivot CTA's own copy for its next chain
 }
 
 // Lower tile (I, J), J <= I: offset of its 64 elements, element (i, j) at i + 8 j.
@@ -279,6 +282,7 @@ struct SweepSmem {
 // over K; its last arrival and a failure flag.
 struct PivotSmem {
     double2 tp[2][2][kTileT];
+    double2 D[kTileT];  // D_K, as written to Dbuf
     unsigned int old;
     int fail;
 };
@@ -504,7 +508,7 @@ hpd_sweep_kernel(SweepBatch bt, GridBar* gb, CoopFault fault) {
         const SweepMat& mt = bt.m[blockIdx.x];
         sm.X[e] = mt.A0[e];
         group_sync(0);
-        tile_inverse(sm.X, sm.T1, mt.Dbuf);
+        tile_inverse(sm.X, sm.T1, mt.Dbuf, ps.D);
     }
     if (!grid_barrier(gb, fault)) return report_batch(bt, 1);
 
@@ -524,11 +528,11 @@ hpd_sweep_kernel(SweepBatch bt, GridBar* gb, CoopFault fault) {
         __syncthreads();
         for (int K = 0; K < bt.nt_max; ++K) {
             const bool chain = K + 1 < mt.nt;
-            if (chain) sweep_pivot(sm, mt.Dbuf + (K % 3) * kTileT, ps.tp[K & 1]);
+            if (chain) sweep_pivot(sm, ps.D, ps.tp[K & 1]);
             if (g == 0) {
                 if (chain) {
                     group_sync(0);
-                    tile_inverse(sm.X, sm.T1, mt.Dbuf + ((K + 1) % 3) * kTileT);
+                    tile_inverse(sm.X, sm.T1, mt.Dbuf + ((K + 1) % 3) * kTileT, ps.D);
                 }
             } else if (g == 1) {
                 if (e == 0 && !flag_wait(mt.flag, (unsigned int)(K + 1), gb, fault)) ps.fail = 1;
