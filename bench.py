@@ -66,10 +66,13 @@ def alg_bytes(kind: str, w, n_cg: int) -> float:
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 dense FP64, nominal (a probe here measured ~1056)
 ALU_KINDS = ("hpd_inverse", "lanczos")
 # DRAM bytes (read + write) per launch from one ncu capture of the launch class's kernel at the
-# benchmark workload (the first sweep of the bench's first solve; profiles/hpd_sweep_kernel_s243.md
-# gives the command). Only for the kernel versions those captures measured: drop an entry when
-# its kernel changes.
-TRAFFIC_BYTES = {"hpd_inverse": 551680}
+# benchmark workload (full-set captures, caches flushed before each pass: the first sweep of the
+# bench's first solve, profiles/hpd_sweep_kernel_s243.md; a CG pass of it,
+# profiles/cg_kernels_perf_256x256x16.md, which give the commands). Only for the kernel versions
+# those captures measured: drop an entry when its kernel changes.
+TRAFFIC_BYTES = {"hpd_inverse": 563968, "cg_row_inv_w": 19943168}
+# steps of the batch, after the timed region, whose dominant-class launches are timed by events
+DOM_STEPS = 3
 
 
 def alg_flops(kind: str, w) -> float:
@@ -657,11 +660,10 @@ def main():
         pass
     sampler = ClockSampler(gpu_id) if rank == 0 else None
 
-    # ---- timed region: K steps of B concurrent solves; only the dominant launch class is
-    # bracketed by events inside it (event nodes of the captured solve graphs, read after the
-    # region: the last step's launches); L2 flushed before each step (outside the events). One
-    # untimed step first captures the graphs with those event nodes.
-    recon.recon_profile(ctx.h, 1 << dom_kind)
+    # ---- timed region: K steps of B concurrent solves replayed from their captured graphs, no
+    # instrumentation inside; L2 flushed before each step (outside the events). One untimed step
+    # first captures the graphs.
+    recon.recon_profile(ctx.h, 0)
     step()
     torch.cuda.synchronize(dev)
     if dist:
@@ -672,8 +674,20 @@ def main():
     total_ms = timed(step, args.steps)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop() if sampler else None
+    # ---- the dominant launch class timed live on the same batch right after the timed region:
+    # CUDA events around each of its launches (event nodes in the solve graphs, on the slots'
+    # streams), read from the last of DOM_STEPS steps under the same conditions. Not inside the
+    # timed region: event nodes around each launch of a CG pass (hundreds per solve) cut the
+    # programmatic-dependent-launch overlap and slowed the step by a third.
+    recon.recon_profile(ctx.h, 1 << dom_kind)
+    step()
+    torch.cuda.synchronize(dev)
+    timed(step, DOM_STEPS)
+    torch.cuda.synchronize(dev)
     dom_ms, dom_n = recon.recon_profile_read(ctx.h, dom_kind)
     recon.recon_profile(ctx.h, 0)
+    step()  # recapture the graphs without event nodes for the sections below
+    torch.cuda.synchronize(dev)
     t_max_ms, value = whole_job_rate(total_ms, args.steps * B * w.n_irls, dist, dev)
     single_max_ms, single_value = whole_job_rate(single_ms, args.steps * w.n_irls, dist, dev)
     if dist:
@@ -748,8 +762,10 @@ def main():
             dist.destroy_process_group()
         return
 
-    # dominant kernel of this library (timed live in the timed region); per-class shares from
-    # the profiled solve before it
+    # dominant kernel of this library (the largest class of the profiled single solve, timed live
+    # on the batch right after the timed region); per-class shares from the profiled solve
+    DOM_NOTE = (f"CUDA events around every launch of the class in the last of {DOM_STEPS} steps of "
+                "the same batch run right after the timed region (L2 flushed before each)")
     peak, peak_src = load_peaks()
     if dom in ALU_KINDS:
         work = alg_flops(dom, w)
@@ -760,7 +776,7 @@ def main():
                 "peak_source": "nominal FP64 rate of the part (no measured FP64 peak provided)",
                 "alg_flops_per_launch": work,
                 "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
-                "traffic": TRAFFIC_BYTES.get(dom)}
+                "timed": DOM_NOTE, "traffic": TRAFFIC_BYTES.get(dom)}
     else:
         work = alg_bytes(dom, w, w.n_cg)
         achieved = work / (dom_ms / dom_n / 1000.0) / 1e9 if dom_n else 0.0
@@ -768,7 +784,7 @@ def main():
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "alg_bytes_per_launch": work,
                 "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
-                "traffic": TRAFFIC_BYTES.get(dom)}
+                "timed": DOM_NOTE, "traffic": TRAFFIC_BYTES.get(dom)}
     # the memory-bound CG passes (per-launch time from the profiled solve)
     cg_roof = {}
     for k in ("cg_row_fwd", "cg_col_mask", "cg_row_inv_w",
