@@ -61,7 +61,7 @@ gram_rows_kernel(const float2* __restrict__ x, int T, int P, int Q, int N2, int 
         for (int e = threadIdx.x; e < L2 * Q; e += blockDim.x) {
             const int i2 = e / Q, c = e % Q;
             const int d2m = (i2 - (N2 - 1) + Q) % Q;
-            dtab[e] = tw[(int)(((long long)d2m * c) % Q)];
+            dtab[e] = tw[(d2m * c) % Q];  // d2m, c < Q <= 512: no overflow in 32 bits
         }
     }
     // q_ab(c) = sum_j conj(x_{j+M-1-a}(c)) x_{j+M-1-b}(c): window w[m] = x_{j+M-1-m}(c)
