@@ -11,14 +11,18 @@
 // barrier per pivot step, the lower tiles ping-ponging between two buffers so that a step reads
 // only the previous step's values and any CTA may update any tile:
 //   - CTA 0 carries the serial chain alone: at step K it updates tile (K+1, K+1) and inverts it
-//     (the next pivot, D_{K+1}) with no other FP64 work on its SM;
+//     (the next pivot, D_{K+1}) with no other FP64 work on its SM, one barrier ahead of the
+//     others: it arrives at each barrier without waiting for its release;
+//   - CTA 1, its helper, forms the chain's next input tiles (row K+2 after step K) right after
+//     each release, with the workers' arithmetic, and hands them over through a flag;
 //   - the other CTAs own fixed work items (chunks of up to four tiles of one tile row, which
-//     form X = A_IK D_K once and apply A_IJ - X A_KJ per tile, and the diagonal tiles), dealt so
-//     that the FP64 work per SM is even.
+//     form X = A_IK D_K once and apply A_IJ - X A_KJ per tile, the last chunk of a row carrying
+//     its diagonal tile), dealt so that the FP64 work per SM is even.
 // FP64 on this part issues one warp instruction per ~19 cycles per SM whatever the active lanes,
 // and one warp at most one per ~64 cycles, so the products use full warps spread over every SM
-// and the pivot chain keeps its SM to itself. Grid barriers are bounded spin-waits: on timeout
-// the kernel records an error flag and returns.
+// and the pivot chain keeps its SM to itself. Grid barriers and the helper's flag are bounded
+// spin-waits: on timeout the kernel records an error flag and returns. (With n matrices in one
+// launch, CTAs 0..n-1 are their pivot CTAs and CTAs n..2n-1 their helpers.)
 #include <cstddef>
 
 #include "common.cuh"
