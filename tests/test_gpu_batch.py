@@ -210,14 +210,18 @@ def test_batch_over_budget_fails_cleanly(R):
         small.close()
 
 
-@pytest.mark.parametrize("pinned,group", [(True, 0), (False, 0), (True, 2)])
-def test_host_batch_equals_device_batch(R, pinned, group):
+@pytest.mark.parametrize("pinned,group,bf16", [(True, 0, False), (False, 0, False),
+                                               (True, 2, False), (True, 0, True)])
+def test_host_batch_equals_device_batch(R, pinned, group, bf16):
     """recon_solve_batch_host (k-space, masks and images in host memory, copied per slot on the
     slot's own stream) gives bitwise the images of recon_solve_batch on device copies of the same
-    inputs: page-locked and pageable host memory, independent slots and a lockstep group."""
+    inputs: page-locked and pageable host memory, independent slots and a lockstep group, and
+    k-space stored as bfloat16 pairs (half the bytes copied)."""
     recon, ctx = R
     w = synth.workload("tiny_32x32x8", n_irls=4)
     ks, ms = _inputs(w, [0, 1, 2])
+    if bf16:
+        ks = [torch.view_as_real(k).to(torch.bfloat16).contiguous() for k in ks]
     filt = (w.N1, w.N2, w.M)
     shape = tuple(ms[0].shape)
     ref = [torch.empty(shape, dtype=torch.complex64, device="cuda") for _ in ms]
