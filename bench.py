@@ -684,6 +684,15 @@ def main():
     torch.cuda.synchronize(dev)
     timed(step, DOM_STEPS)
     torch.cuda.synchronize(dev)
+    batch_dom_ms, batch_dom_n = recon.recon_profile_read(ctx.h, dom_kind)
+    # and on the plain single solve, where no other solve's kernels share the GPU while it runs
+    # (inside the batch a launch's duration includes the time-sharing with three other solves);
+    # the totals restart here (same mask)
+    recon.recon_profile(ctx.h, 1 << dom_kind)
+    solve_one()
+    torch.cuda.synchronize(dev)
+    timed(solve_one, DOM_STEPS)
+    torch.cuda.synchronize(dev)
     dom_ms, dom_n = recon.recon_profile_read(ctx.h, dom_kind)
     recon.recon_profile(ctx.h, 0)
     step()  # recapture the graphs without event nodes for the sections below
@@ -764,8 +773,11 @@ def main():
 
     # dominant kernel of this library (the largest class of the profiled single solve, timed live
     # on the batch right after the timed region); per-class shares from the profiled solve
-    DOM_NOTE = (f"CUDA events around every launch of the class in the last of {DOM_STEPS} steps of "
-                "the same batch run right after the timed region (L2 flushed before each)")
+    DOM_NOTE = (f"CUDA events around every launch of the class in the last of {DOM_STEPS} plain "
+                "single solves of the workload run right after the timed region (L2 flushed "
+                "before each); in_batch_avg_launch_us: the same inside the last of "
+                f"{DOM_STEPS} steps of the {B}-solve batch, where the launch shares the GPU")
+    batch_us = round(1000.0 * batch_dom_ms / batch_dom_n, 3) if batch_dom_n else None
     peak, peak_src = load_peaks()
     if dom in ALU_KINDS:
         work = alg_flops(dom, w)
@@ -776,7 +788,8 @@ def main():
                 "peak_source": "nominal FP64 rate of the part (no measured FP64 peak provided)",
                 "alg_flops_per_launch": work,
                 "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
-                "timed": DOM_NOTE, "traffic": TRAFFIC_BYTES.get(dom)}
+                "in_batch_avg_launch_us": batch_us, "timed": DOM_NOTE,
+                "traffic": TRAFFIC_BYTES.get(dom)}
     else:
         work = alg_bytes(dom, w, w.n_cg)
         achieved = work / (dom_ms / dom_n / 1000.0) / 1e9 if dom_n else 0.0
@@ -784,7 +797,8 @@ def main():
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "alg_bytes_per_launch": work,
                 "avg_launch_us": round(1000.0 * dom_ms / dom_n, 3) if dom_n else None,
-                "timed": DOM_NOTE, "traffic": TRAFFIC_BYTES.get(dom)}
+                "in_batch_avg_launch_us": batch_us, "timed": DOM_NOTE,
+                "traffic": TRAFFIC_BYTES.get(dom)}
     # the memory-bound CG passes (per-launch time from the profiled solve)
     cg_roof = {}
     for k in ("cg_row_fwd", "cg_col_mask", "cg_row_inv_w",
