@@ -33,6 +33,10 @@ namespace recon {
 namespace {
 
 constexpr int kThreads = 256;
+// The Lanczos kernel: four warps per CTA (so that up to four launches fit on an SM at once, as
+// when several solves start together), each warp holding up to kLancRows rows of a matrix.
+constexpr int kLancThreads = 128;
+constexpr int kLancRows = 8;
 constexpr int kB = 8;                        // tile edge
 constexpr int kTileT = kB * kB;              // elements of a tile = threads of a tile group
 constexpr int kGroups = kThreads / kTileT;   // tile groups per CTA
@@ -662,14 +666,14 @@ RECON_DEV void report_lanc(const LancBatch& bt, int v) {
 // Several matrices per launch, two grid barriers per step for all of them. Row i of matrix b goes
 // to global warp i mod (warps of the grid), as in a launch of that matrix alone, and every sum is
 // taken in the same order, so each matrix's lambda_max is bitwise the one its own launch gives.
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kLancThreads, 4)
 lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
-    __shared__ double red[kMaxHpdBatch][kThreads / 32];
-    __shared__ double2 ys[kMaxHpdBatch][4][kThreads / 32];  // G v of the warp's rows (lane 0)
+    __shared__ double red[kMaxHpdBatch][kLancThreads / 32];
+    __shared__ double2 ys[kMaxHpdBatch][kLancRows][kLancThreads / 32];  // G v of the warp's rows (lane 0)
     __shared__ double s_beta[kMaxHpdBatch], s_ib[kMaxHpdBatch], s_alpha[kMaxHpdBatch];
     __shared__ int s_m[kMaxHpdBatch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (kThreads / 32);
+    const int nw = gridDim.x * (kLancThreads / 32);
     const int gw = warp * gridDim.x + blockIdx.x;  // rows spread over every SM (FP64 unit per SM)
     const int n = bt.n;
     // deterministic start vector, unnormalised: u_i = 1 + 0.5 sin(i) + i 0.25 i cos(3 i) / s
@@ -681,7 +685,7 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
         }
     }
     if (!grid_barrier(gb, fault)) return report_lanc(bt, 1);
-    for (int b = warp; b < n; b += kThreads / 32) {
+    for (int b = warp; b < n; b += kLancThreads / 32) {
         const LancMat& L = bt.mt[b];
         double acc = 0.0;
         for (int i = lane; i < L.s; i += 32) acc += L.u[i].x * L.u[i].x + L.u[i].y * L.u[i].y;
@@ -704,7 +708,7 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
             if (act) {
                 const double ib = s_ib[b];
                 int nrow = 0;
-                for (int i = gw; i < L.s && nrow < 4; i += nw, ++nrow) {
+                for (int i = gw; i < L.s && nrow < kLancRows; i += nw, ++nrow) {
                     // row i of the Hermitian G is the conjugate of column i (contiguous)
                     double2 acc = make_double2(0.0, 0.0);
                     const double2* gcol = L.G + (size_t)i * L.s;
@@ -745,11 +749,11 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
         if ((int)threadIdx.x < n && k < s_m[threadIdx.x]) {
             const int b = threadIdx.x;
             double t = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) t += red[b][w];
+            for (int w = 0; w < kLancThreads / 32; ++w) t += red[b][w];
             bt.mt[b].part[(size_t)(k & 1) * 2 * gridDim.x + blockIdx.x] = t;
         }
         if (!grid_barrier(gb, fault)) return report_lanc(bt, 1);
-        for (int b = warp; b < n; b += kThreads / 32) {
+        for (int b = warp; b < n; b += kLancThreads / 32) {
             if (k >= s_m[b]) continue;
             const double* pa = bt.mt[b].part + (size_t)(k & 1) * 2 * gridDim.x;
             const double v = warp_sum(lane_sum(pa, lane, (int)gridDim.x));
@@ -762,7 +766,7 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
             if (k < s_m[b] && lane == 0) {
                 const double alpha = s_alpha[b], beta = s_beta[b], ib = s_ib[b];
                 int nrow = 0;
-                for (int i = gw; i < L.s && nrow < 4; i += nw, ++nrow) {
+                for (int i = gw; i < L.s && nrow < kLancRows; i += nw, ++nrow) {
                     const double2 vi = make_double2(L.u[i].x * ib, L.u[i].y * ib);
                     const double2 vp = L.vprev[i], yi = ys[b][nrow][warp];
                     const double2 un = make_double2(yi.x - alpha * vi.x - beta * vp.x,
@@ -778,11 +782,11 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
         if ((int)threadIdx.x < n && k < s_m[threadIdx.x]) {
             const int b = threadIdx.x;
             double t = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) t += red[b][w];
+            for (int w = 0; w < kLancThreads / 32; ++w) t += red[b][w];
             bt.mt[b].part[(size_t)(k & 1) * 2 * gridDim.x + gridDim.x + blockIdx.x] = t;
         }
         if (!grid_barrier(gb, fault)) return report_lanc(bt, 1);
-        for (int b = warp; b < n; b += kThreads / 32) {
+        for (int b = warp; b < n; b += kLancThreads / 32) {
             if (k >= s_m[b]) continue;
             const double* pb = bt.mt[b].part + (size_t)(k & 1) * 2 * gridDim.x + gridDim.x;
             const double b2 = warp_sum(lane_sum(pb, lane, (int)gridDim.x));
@@ -894,11 +898,11 @@ lanczos_kernel(LancBatch bt, GridBar* gb, CoopFault fault) {
 }
 
 
-int coop_grid(const void* kern, int* grid) {
+int coop_grid(const void* kern, int threads, int* grid) {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, 0) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess) return -1;
     if (per < 1) return -1;
     *grid = sms;  // one CTA per SM
     return 0;
@@ -909,10 +913,11 @@ int tiles_per_side(int s) { return (s + kB - 1) / kB; }
 // Cooperative launch (all CTAs co-resident, required by the grid barriers) through
 // cudaLaunchKernelEx so that it can be captured into a CUDA graph.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_coop(void (*kern)(KArgs...), int grid, cudaStream_t st, Args... args) {
+cudaError_t launch_coop(void (*kern)(KArgs...), int grid, int threads, cudaStream_t st,
+                        Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(threads);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -944,7 +949,7 @@ cudaError_t launch_hpd_inverse_batch(const HpdJob* jobs, int n, void* barrier_sc
                                      cudaStream_t st, CoopFault fault) {
     if (n < 1 || n > kMaxHpdBatch || !barrier_scratch) return cudaErrorInvalidValue;
     int grid = 0;
-    if (coop_grid((const void*)hpd_sweep_kernel, &grid) || grid < 2 * n + 1)
+    if (coop_grid((const void*)hpd_sweep_kernel, kThreads, &grid) || grid < 2 * n + 1)
         return cudaErrorInvalidConfiguration;
     SweepBatch bt = {};
     bt.n = n;
@@ -976,7 +981,7 @@ cudaError_t launch_hpd_inverse_batch(const HpdJob* jobs, int n, void* barrier_sc
     // every work item must fit the per-CTA item table
     if (sweep_items(nts, n, grid - 2 * n, -1, nullptr, 0) > kMaxItems) return cudaErrorInvalidValue;
     GridBar* gb = reinterpret_cast<GridBar*>(barrier_scratch);
-    return launch_coop(hpd_sweep_kernel, grid, st, bt, gb, fault);
+    return launch_coop(hpd_sweep_kernel, grid, kThreads, st, bt, gb, fault);
 }
 
 cudaError_t launch_hpd_inverse(const Dims& d, double2* G, const double* eps, void* scratch,
@@ -997,14 +1002,15 @@ cudaError_t launch_lanczos_batch(const LanczosJob* jobs, int n, void* barrier_sc
                                  cudaStream_t st, CoopFault fault) {
     if (n < 1 || n > kMaxHpdBatch || !barrier_scratch) return cudaErrorInvalidValue;
     int grid = 0;
-    if (coop_grid((const void*)lanczos_kernel, &grid) || grid < n) return cudaErrorInvalidConfiguration;
-    const int nw = grid * (kThreads / 32);
+    if (coop_grid((const void*)lanczos_kernel, kLancThreads, &grid) || grid < n)
+        return cudaErrorInvalidConfiguration;
+    const int nw = grid * (kLancThreads / 32);
     LancBatch bt = {};
     bt.n = n;
     for (int b = 0; b < n; ++b) {
         const int s = jobs[b].s;
-        // each warp holds at most four rows of a matrix
-        if (s < 1 || s > 4 * nw || !jobs[b].G || !jobs[b].scratch || !jobs[b].lmax)
+        // each warp holds at most kLancRows rows of a matrix
+        if (s < 1 || s > kLancRows * nw || !jobs[b].G || !jobs[b].scratch || !jobs[b].lmax)
             return cudaErrorInvalidValue;
         unsigned char* p = reinterpret_cast<unsigned char*>(jobs[b].scratch) + kCoopBarrierBytes;
         LancMat& L = bt.mt[b];
@@ -1023,7 +1029,7 @@ cudaError_t launch_lanczos_batch(const LanczosJob* jobs, int n, void* barrier_sc
         if (L.m > bt.m_max) bt.m_max = L.m;
     }
     GridBar* gb = reinterpret_cast<GridBar*>(barrier_scratch);
-    return launch_coop(lanczos_kernel, grid, st, bt, gb, fault);
+    return launch_coop(lanczos_kernel, grid, kLancThreads, st, bt, gb, fault);
 }
 
 cudaError_t launch_lanczos_lmax(const Dims& d, const double2* G, void* scratch, double* lmax,
