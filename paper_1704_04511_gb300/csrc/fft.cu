@@ -551,6 +551,247 @@ col_mask_64_kernel(float2* t, const uint8_t* __restrict__ mask, int Q, float sca
     for (int n1 = 0; n1 < 8; ++n1) t[fbase + (size_t)(j + 8 * n1) * Q + col] = u[n1];
 }
 
+// ---- volumes of 128 x 128 slices and depth 64: the length-P DFT split over two passes ----
+// With p = 8 p1 + p2 and kp = k1 + 16 k2 the length-128 column DFT is
+//   X[k1 + 16 k2] = sum_p2 w8^(p2 k2) Y[k1][p2],  Y[k1][p2] = w128^(p2 k1) sum_p1 x[8 p1 + p2] w16^(p1 k1),
+// and its inverse, with p = p2 + 8 p1,
+//   x[p2 + 8 p1] = sum_k1 w16^(-p1 k1) Z[k1][p2],  Z[k1][p2] = w128^(-p2 k1) sum_k2 X[k1 + 16 k2] w8^(-p2 k2).
+// The row pass of a CG step, holding the 16 rows 8 p1 + p2 of one slice (one p2), computes Y and
+// stores Y[k1][p2] at row 8 k1 + p2. The depth pass, holding the rows 8 k1 + p2 of one k1 in every
+// slice of a frame for 8 columns, runs the 8-point DFT over p2 (giving X), the depth DFT, the
+// mask, the depth IDFT and the 8-point IDFT over k2, and stores Z[k1][p2] at row 8 k1 + p2 again.
+// The last pass runs the 16-point IDFT over k1 in place. The column stage is then two launches
+// (33 E bytes) instead of three (49 E): the length-P forward pass is folded away.
+// vol_fold selects this path.
+
+// Pass A of a CG step for such volumes: p = r + beta p and the row DFT of 16 rows of one slice
+// (rows 8 p1 + p2, p2 = blockIdx.x % 8, 8 lanes per row as in row_fwd_pupdate_128_kernel), then the
+// 16-point DFT over p1 of each of the 128 columns and the twiddle w128^(p2 k1) (P = Q = 128, so the
+// one length-128 table serves both directions); Y[k1][p2] goes to row 8 k1 + p2 of t.
+__global__ void __launch_bounds__(128)
+row_fwd_col1_128_kernel(const float2* __restrict__ r, float2* __restrict__ p,
+                        float2* __restrict__ t, const double* __restrict__ rr_parts, int n_rr,
+                        const double* __restrict__ rr_prev, double* __restrict__ rr_out,
+                        int first, const float2* __restrict__ tw_g) {
+    __shared__ float2 tw8[128];
+    __shared__ float2 sx[16][kX128];
+    __shared__ __align__(16) float2 cb[16][128];
+    __shared__ float beta_s;
+    fill_tw128(tw8, tw_g);
+    pdl_wait();
+    const int p1 = threadIdx.x / 8, j = threadIdx.x % 8;
+    const int p2 = blockIdx.x % 8;
+    const size_t sbase = (size_t)(blockIdx.x / 8) * 128 * 128;
+    const size_t base = sbase + (size_t)(8 * p1 + p2) * 128 + j;
+    float2 u[16], pv[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) u[n1] = r[base + 8 * n1];
+    if (!first) {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) pv[n1] = p[base + 8 * n1];
+    }
+    if (!first && threadIdx.x < 32) {  // |r|^2 from the update pass's partials, loads in flight
+        const double rr_new = warp0_sum_array(rr_parts, n_rr);
+        if (threadIdx.x == 0) {
+            beta_s = (float)(rr_new * rcp_nr(rr_prev[0]));
+            if (blockIdx.x == 0) rr_out[0] = rr_new;
+        }
+    }
+    __syncthreads();  // tw8, beta
+    if (!first) {
+        const float beta = beta_s;
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) {
+            u[n1].x = fmaf(beta, pv[n1].x, u[n1].x);
+            u[n1].y = fmaf(beta, pv[n1].y, u[n1].y);
+        }
+    }
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) p[base + 8 * n1] = u[n1];
+    float2 a[8], b[8];
+    row_dft128<false>(u, a, b, sx[p1], tw8, j);  // a[k2] = X[2j + 16 k2], b[k2] = X[2j + 1 + 16 k2]
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2)  // one 16-byte store per pair: eight lanes fill 128 bytes
+        *reinterpret_cast<float4*>(&cb[p1][2 * j + 16 * k2]) =
+            make_float4(a[k2].x, a[k2].y, b[k2].x, b[k2].y);
+    __syncthreads();
+    const int kq = threadIdx.x;
+    float2 v[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) v[n] = cb[n][kq];
+    dft16<false>(v);  // v[k1] = sum_p1 x[8 p1 + p2] w16^(p1 k1) in column kq
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw8[k1 * 8 + p2]);
+    pdl_trigger();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) t[sbase + (size_t)(8 * k1 + p2) * 128 + kq] = v[k1];
+}
+
+// The depth pass of the split: one frame, one k1 (blockIdx.y), 8 columns (blockIdx.x), all 64
+// slices; 256 threads. Stage A: thread (q, d) holds rows 8 k1 + p2 (p2 < 8) of depths d and d + 32
+// and runs the 8-point DFT over p2 -> X[k1 + 16 k2]. Stage B: the 64 columns (k2, q) of 64 depths
+// get the depth DFT, mask, 1/(PQR) scale and depth IDFT of col_mask_64_kernel (lane j holding depths
+// 8 n1 + j of columns c and c + 32). Stage A again: the 8-point IDFT over k2 and the twiddle
+// w128^(-p2 k1), stored at rows 8 k1 + p2 (the rows loaded). The exchange buffer holds a depth row
+// of 64 columns every 72 float2, so that every exchange is free of bank conflicts; the mask bytes
+// of the 8 columns arrive in 8-byte runs into shared memory while stage A loads.
+constexpr int kFoldPitch = 72;
+
+constexpr int kFoldQ = 128;  // P and Q of the volumes the split serves
+
+__global__ void __launch_bounds__(256, 4)  // 64 registers: four CTAs per SM
+depth_fold_64_kernel(float2* t, const uint8_t* __restrict__ mask, float scale,
+                     const float2* __restrict__ twP_g, const float2* __restrict__ twR_g) {
+    constexpr int Q = kFoldQ;
+    constexpr size_t PQ = (size_t)128 * Q;
+    __shared__ float2 tw8[128];  // w128^(j k1) at [k1 * 8 + j]
+    __shared__ float2 tw64[64];  // w64^(j k1) at [k1 * 8 + j]
+    __shared__ float2 E[64 * kFoldPitch];
+    __shared__ __align__(8) uint8_t Mk[64 * 64];  // mask at depth frequency kr, column (k2, q): [kr * 64 + 8 k2 + q]
+    fill_tw128(tw8, twP_g);
+    for (int e = threadIdx.x; e < 64; e += blockDim.x) tw64[e] = twR_g[(e / 8) * (e % 8)];
+    pdl_wait();
+    const int q0 = blockIdx.x * 8, k1 = blockIdx.y;
+    const size_t fbase = (size_t)blockIdx.z * 64 * PQ;
+    const int qa = threadIdx.x % 8, da = threadIdx.x / 8;  // stage A: column q0 + qa, depths da, da + 32
+    const int cb = threadIdx.x % 32, jb = threadIdx.x / 32;  // stage B: columns cb, cb + 32; lane jb
+    float2 x0[8], x1[8];
+    const size_t a0 = fbase + (size_t)da * PQ + (size_t)(8 * k1) * Q + q0 + qa;
+    const size_t a1 = a0 + 32 * PQ;
+#pragma unroll
+    for (int p2 = 0; p2 < 8; ++p2) {
+        x0[p2] = t[a0 + (size_t)p2 * Q];
+        x1[p2] = t[a1 + (size_t)p2 * Q];
+    }
+    {   // the mask bytes of the CTA's 8 columns: 512 runs of 8 (depth frequency kr, k2)
+        const uint8_t* mb = mask + fbase + (size_t)k1 * Q + q0;
+        const bool al8 = (reinterpret_cast<uintptr_t>(mask) & 7) == 0;
+#pragma unroll
+        for (int i = threadIdx.x; i < 512; i += 256) {
+            const int kr = i / 8, k2 = i % 8;
+            const uint8_t* src = mb + (size_t)kr * PQ + (size_t)(16 * k2) * Q;
+            uint8_t* dst = &Mk[kr * 64 + 8 * k2];
+            if (al8) {
+                *reinterpret_cast<uint2*>(dst) = __ldg(reinterpret_cast<const uint2*>(src));
+            } else {
+#pragma unroll
+                for (int b = 0; b < 8; ++b) dst[b] = src[b];
+            }
+        }
+    }
+    __syncthreads();  // tables
+    SmallDFT<8, false>::run(x0);  // x0[k2] = X[k1 + 16 k2] at depth da
+    SmallDFT<8, false>::run(x1);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        E[da * kFoldPitch + 8 * k2 + qa] = x0[k2];
+        E[(da + 32) * kFoldPitch + 8 * k2 + qa] = x1[k2];
+    }
+    __syncthreads();
+    float2 u0[8], u1[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) {
+        u0[n1] = E[(8 * n1 + jb) * kFoldPitch + cb];
+        u1[n1] = E[(8 * n1 + jb) * kFoldPitch + cb + 32];
+    }
+    SmallDFT<8, false>::run(u0);
+    SmallDFT<8, false>::run(u1);
+#pragma unroll
+    for (int kd = 1; kd < 8; ++kd) {
+        const float2 w = tw64[kd * 8 + jb];
+        u0[kd] = cmul(u0[kd], w);
+        u1[kd] = cmul(u1[kd], w);
+    }
+    __syncthreads();  // stage A rows read
+#pragma unroll
+    for (int kd = 0; kd < 8; ++kd) {
+        E[(kd * 8 + jb) * kFoldPitch + cb] = u0[kd];
+        E[(kd * 8 + jb) * kFoldPitch + cb + 32] = u1[kd];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        u0[jj] = E[(jb * 8 + jj) * kFoldPitch + cb];
+        u1[jj] = E[(jb * 8 + jj) * kFoldPitch + cb + 32];
+    }
+    SmallDFT<8, false>::run(u0);  // u0[m] = X[jb + 8 m] along the depth
+    SmallDFT<8, false>::run(u1);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const uint8_t* mk = &Mk[(jb + 8 * m) * 64 + cb];
+        u0[m] = mk[0] ? cscale(u0[m], scale) : make_float2(0.f, 0.f);
+        u1[m] = mk[32] ? cscale(u1[m], scale) : make_float2(0.f, 0.f);
+    }
+    SmallDFT<8, true>::run(u0);  // u0[n2] = sum_m Y[jb + 8 m] w8^(-m n2)
+    SmallDFT<8, true>::run(u1);
+#pragma unroll
+    for (int n2 = 1; n2 < 8; ++n2) {
+        float2 w = tw64[n2 * 8 + jb];
+        w.y = -w.y;
+        u0[n2] = cmul(u0[n2], w);
+        u1[n2] = cmul(u1[n2], w);
+    }
+    __syncthreads();  // the depth exchange is read
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) {
+        E[(n2 * 8 + jb) * kFoldPitch + cb] = u0[n2];
+        E[(n2 * 8 + jb) * kFoldPitch + cb + 32] = u1[n2];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        u0[jj] = E[(jb * 8 + jj) * kFoldPitch + cb];
+        u1[jj] = E[(jb * 8 + jj) * kFoldPitch + cb + 32];
+    }
+    SmallDFT<8, true>::run(u0);  // u0[n1] = y at depth jb + 8 n1
+    SmallDFT<8, true>::run(u1);
+    __syncthreads();  // the second depth exchange is read
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) {
+        E[(jb + 8 * n1) * kFoldPitch + cb] = u0[n1];
+        E[(jb + 8 * n1) * kFoldPitch + cb + 32] = u1[n1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        x0[k2] = E[da * kFoldPitch + 8 * k2 + qa];
+        x1[k2] = E[(da + 32) * kFoldPitch + 8 * k2 + qa];
+    }
+    SmallDFT<8, true>::run(x0);  // x0[p2] = sum_k2 X[k1 + 16 k2] w8^(-p2 k2)
+    SmallDFT<8, true>::run(x1);
+#pragma unroll
+    for (int p2 = 1; p2 < 8; ++p2) {
+        float2 w = tw8[k1 * 8 + p2];
+        w.y = -w.y;
+        x0[p2] = cmul(x0[p2], w);
+        x1[p2] = cmul(x1[p2], w);
+    }
+    pdl_trigger();
+#pragma unroll
+    for (int p2 = 0; p2 < 8; ++p2) {
+        t[a0 + (size_t)p2 * Q] = x0[p2];
+        t[a1 + (size_t)p2 * Q] = x1[p2];
+    }
+}
+
+// The last pass of the split: lane j of column c loads Z[k1][j] from rows 8 k1 + j (k1 < 16), runs
+// the 16-point IDFT over k1 and stores x[j + 8 p1] at rows 8 p1 + j, the rows it loaded. 16 columns
+// of one slice per 128-thread CTA, unnormalised.
+__global__ void __launch_bounds__(128)
+col_fold_inv_kernel(float2* t) {
+    constexpr int Q = kFoldQ;
+    pdl_wait();
+    const int c = threadIdx.x % 16, j = threadIdx.x / 16;
+    const size_t base = (size_t)blockIdx.y * 128 * Q + (size_t)j * Q + blockIdx.x * 16 + c;
+    float2 u[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) u[n] = t[base + (size_t)(8 * n) * Q];
+    dft16<true>(u);
+    pdl_trigger();
+#pragma unroll
+    for (int n = 0; n < 16; ++n) t[base + (size_t)(8 * n) * Q] = u[n];
+}
+
 template <int N>
 size_t row_smem() { return (size_t)(2 * rows_per_cta<N>() * N + N) * sizeof(float2); }
 template <int N, int C>
@@ -664,6 +905,8 @@ int col_tile_for(const Dims& d, bool depth) {
     return wide_cols(depth ? d.R : d.P);
 }
 
+bool vol_fold(const Dims& d) { return d.R == 64 && d.P == 128 && d.Q == 128 && d.nc == 1; }
+
 bool col_register(const Dims& d, bool depth) {
     if (depth) return d.R == 64 && (d.P * d.Q) % 32 == 0;
     if (d.R == 1 && d.P == 256) return true;
@@ -712,6 +955,9 @@ cudaError_t launch_row_fwd_pupdate(const Dims& d, const Twiddles& tw, const floa
                                    float2* t, const Partials& rr, const double* rr_prev,
                                    double* rr_out, int first, cudaStream_t st) {
     const int nrows = d.T * d.rows();
+    if (vol_fold(d))  // the row DFT and the first half of the length-P DFT (see vol_fold)
+        return launch_pdl(row_fwd_col1_128_kernel, dim3(d.T * d.R * 8), dim3(128), 0, st, r, p, t,
+                          (const double*)rr.parts, rr.n, rr_prev, rr_out, first, tw.twQ);
     if (d.Q == 256) {
         const int grid = (nrows + kR256Rows - 1) / kR256Rows;
         return launch_pdl(row_fwd_pupdate_256_kernel, dim3(grid), dim3(64), 0, st, r, p, t, nrows,
@@ -774,6 +1020,12 @@ cudaError_t launch_col_mask(const Dims& d, const Twiddles& tw, float2* t, const 
         // of the two unnormalised transforms), column IDFT of every slice
         const int pq = d.P * d.Q, slices = d.T * d.R;
         const float sc3 = 1.0f / ((float)d.P * (float)d.Q * (float)d.R);
+        if (vol_fold(d)) {  // the row pass did the first half of the length-P DFT
+            cudaError_t e = launch_pdl(depth_fold_64_kernel, dim3(d.Q / 8, 16, d.T), dim3(256), 0,
+                                       st, t, mask, sc3, tw.twP, tw.twR);
+            if (e != cudaSuccess) return e;
+            return launch_pdl(col_fold_inv_kernel, dim3(d.Q / 16, slices), dim3(128), 0, st, t);
+        }
         const int cP = col_tile_for(d, false), cR = col_tile_for(d, true);
         const bool reg128 = col_register(d, false);  // register transforms where they exist
         const bool reg64 = col_register(d, true);

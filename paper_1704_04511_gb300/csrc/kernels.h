@@ -89,6 +89,9 @@ int col_sched_for(const Dims& d, bool depth);
 constexpr int kFftSchedules = 2;
 // True where the column stage of the CG operator runs register transforms without tiles.
 bool col_register(const Dims& d, bool depth);
+// True for volumes of 128 x 128 slices and depth 64 (single coil): the row pass of a CG step also
+// runs the first half of the length-P DFT and the column stage is two launches (fft.cu).
+bool vol_fold(const Dims& d);
 // Message returned by recon_last_error(NULL) (calls that have no context).
 void set_context_free_error(const std::string& msg);
 int w_max_M();

@@ -54,6 +54,10 @@ def _case(kw):
 
 
 CASES = SMALL + [("128x128x64x12", None)]
+# 128 x 128 slices of depth 64: the shapes whose length-P DFT is split between the row pass and
+# the depth pass of the CG operator (two column launches instead of three)
+FOLD = ("128x128x64x4-M3", dict(P=128, Q=128, depth=64, T=4, N1=3, N2=3, N3=2, M=3,
+                                times_ms=(10.0, 20.0, 30.0, 40.0)))
 
 
 def _filt(w):
@@ -151,7 +155,7 @@ def test_weight3_parity(R, case, p):
     assert ed < 1e-8 and es < 1e-5
 
 
-@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("case", CASES + [FOLD], ids=[c[0] for c in CASES + [FOLD]])
 def test_normal3_operator_parity(R, case):
     recon, ctx = R
     w, prob = _case(case[1])
@@ -202,6 +206,13 @@ def test_solve3_parity_m3(R):
     recon, ctx = R
     w, prob = _small(**SMALL[1][1])
     _check_solve(recon, ctx, w, prob, "32x32x64x5 M=3 3 x 6", 3, 6)
+
+
+def test_solve3_parity_fold(R):
+    """A 128 x 128 x 64 volume series (the split length-P DFT in every CG step), 2 x 4."""
+    recon, ctx = R
+    w, prob = _small(**FOLD[1])
+    _check_solve(recon, ctx, w, prob, "128x128x64x4 M=3 2 x 4", 2, 4)
 
 
 def test_solve3_eig_path_matches(R):
