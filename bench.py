@@ -40,8 +40,9 @@ KERNELS_PER_SCOPE = {"adjoint": 2, "gram": 2, "eps": 1, "diag_sums": 1, "weight_
 
 def alg_bytes(kind: str, w, n_cg: int) -> float:
     """Algorithmic bytes per launch (complex64 elements E = T*P*Q, pixels N = P*Q; volumes:
-    E = T*D*P*Q, N = D*P*Q). For volumes the column class holds three launches (column DFT,
-    masked depth pass, column IDFT); its algorithmic bytes stay those of the operation."""
+    E = T*D*P*Q, N = D*P*Q). For volumes the column class holds two or three launches (the
+    masked depth pass and the column transforms); its algorithmic bytes stay those of the
+    operation."""
     D = getattr(w, "depth", 1)
     E = w.T * w.P * w.Q * D
     N = w.P * w.Q * D
