@@ -93,9 +93,9 @@ def test_adjoint3_parity(R, case):
     b = c64(prob["kspace"])
     x = torch.empty(masks.shape, dtype=torch.complex64, device="cuda")
     recon.recon_adjoint3(ctx.h, to_dev(b), to_dev(masks), x)
-    err, m = assert_close(x.cpu().numpy(), slr3.AH3(b.astype(np.complex128), masks), 2e-6,
+    err, peak = assert_close(x.cpu().numpy(), slr3.AH3(b.astype(np.complex128), masks), 2e-6,
                           "adjoint3")
-    print(f"\n[adjoint3 {case[0]}] rel. error {err:.2e} (peak-relative element {m:.2e})")
+    print(f"\n[adjoint3 {case[0]}] rel. error {err:.2e} (peak-relative element {peak:.2e})")
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -173,8 +173,8 @@ def test_normal3_operator_parity(R, case):
     recon.recon_apply_normal3(ctx.h, to_dev(masks), _filt(w), to_dev(c64(pairs_from_full(S))), lam,
                               to_dev(v), y)
     ref = slr3.normal_op3(v.astype(np.complex128), masks, S, lam)
-    err, m = assert_close(y.cpu().numpy(), ref, 1e-5, "normal3")
-    print(f"\n[normal3 {case[0]}] rel. error {err:.2e} (peak-relative element {m:.2e}; lambda "
+    err, peak = assert_close(y.cpu().numpy(), ref, 1e-5, "normal3")
+    print(f"\n[normal3 {case[0]}] rel. error {err:.2e} (peak-relative element {peak:.2e}; lambda "
           f"{lam:.3g})")
 
 
@@ -188,9 +188,9 @@ def _check_solve(recon, ctx, w, prob, tag, n_irls, n_cg):
                        n_cg)
     xt = prob["x_true"]
     x0 = slr3.AH3(b.astype(np.complex128), masks)
-    err, m = assert_close(x_gpu, x_ref, 1e-4, f"solve3 {tag}")
+    err, peak = assert_close(x_gpu, x_ref, 1e-4, f"solve3 {tag}")
     print(f"\n[solve3 {tag}] |x_gpu - x_oracle| / |x_oracle| = {err:.2e} (peak-relative element "
-          f"{m:.2e}); NRMSE gpu {rel(x_gpu, xt):.5f} oracle {rel(x_ref, xt):.5f} adjoint "
+          f"{peak:.2e}); NRMSE gpu {rel(x_gpu, xt):.5f} oracle {rel(x_ref, xt):.5f} adjoint "
           f"{rel(x0, xt):.5f}")
     return x_gpu, x0, xt
 
@@ -280,6 +280,6 @@ def test_solve3_bf16_kspace(R):
     out = torch.empty(masks.shape, dtype=torch.complex64, device="cuda")
     recon.recon_solve3(ctx.h, bt.cuda(), to_dev(masks), _filt(w), w.lam, w.p, w.n_irls, w.n_cg, out)
     x_ref = slr3.irls3(b_rounded, masks, w.N1, w.N2, w.N3, w.M, w.lam, w.p, w.n_irls, w.n_cg)
-    err, m = assert_close(out.cpu().numpy(), x_ref, 1e-4, "solve3 bf16 k-space")
-    print(f"\n[solve3 bf16 k-space] {err:.2e} (peak-relative element {m:.2e}); NRMSE "
+    err, peak = assert_close(out.cpu().numpy(), x_ref, 1e-4, "solve3 bf16 k-space")
+    print(f"\n[solve3 bf16 k-space] {err:.2e} (peak-relative element {peak:.2e}); NRMSE "
           f"{rel(out.cpu().numpy(), prob['x_true']):.5f}")

@@ -11,7 +11,7 @@ import pytest
 import synth
 from oracle import slr
 
-from gpu_util import c64, crandn, pairs_from_full, rel, to_dev
+from gpu_util import assert_close, c64, crandn, pairs_from_full, rel, to_dev
 
 torch = pytest.importorskip("torch")
 
@@ -58,9 +58,8 @@ def test_coil_adjoint_parity(R, case):
     x = torch.empty(masks.shape, dtype=torch.complex64, device="cuda")
     recon.recon_adjoint_coils(ctx.h, to_dev(b), to_dev(masks), to_dev(c64(C)), x)
     ref = slr.AH_coils(b.astype(np.complex128), masks, c64(C).astype(np.complex128))
-    err = rel(x.cpu().numpy(), ref)
-    print(f"\n[coil adjoint {case[0]}] rel. error {err:.2e}")
-    assert err < 2e-6
+    err, peak = assert_close(x.cpu().numpy(), ref, 2e-6, "coil adjoint")
+    print(f"\n[coil adjoint {case[0]}] rel. error {err:.2e} (peak-relative element {peak:.2e})")
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -80,9 +79,8 @@ def test_coil_normal_operator_parity(R, case):
     recon.recon_apply_normal_coils(ctx.h, to_dev(masks), to_dev(c64(C)), (w.N1, w.N2, w.M),
                                    to_dev(c64(pairs_from_full(S))), lam, to_dev(v), y)
     ref = slr.normal_op(v.astype(np.complex128), masks, S, lam, C)
-    err = rel(y.cpu().numpy(), ref)
-    print(f"\n[coil normal operator {case[0]}] rel. error {err:.2e}")
-    assert err < 1e-5
+    err, peak = assert_close(y.cpu().numpy(), ref, 1e-5, "coil normal operator")
+    print(f"\n[coil normal operator {case[0]}] rel. error {err:.2e} (peak-relative element {peak:.2e})")
 
 
 def _check_solve(recon, ctx, w, prob, tag):
@@ -95,11 +93,11 @@ def _check_solve(recon, ctx, w, prob, tag):
     x_ref = slr.irls(c64(prob["kspace"]).astype(np.complex128), masks, w.N1, w.N2, w.M, w.lam,
                      w.p, w.n_irls, w.n_cg, coils=C.astype(np.complex128))
     xt = prob["x_true"]
-    err = rel(x_gpu, x_ref)
+    err, peak = assert_close(x_gpu, x_ref, 1e-4, f"coil solve {tag}")
     x0 = slr.AH_coils(prob["kspace"], masks, C.astype(np.complex128))
-    print(f"\n[coil solve {tag}] |x_gpu - x_oracle| / |x_oracle| = {err:.2e}; NRMSE gpu "
-          f"{rel(x_gpu, xt):.5f} oracle {rel(x_ref, xt):.5f} adjoint {rel(x0, xt):.5f}")
-    assert err < 1e-4
+    print(f"\n[coil solve {tag}] |x_gpu - x_oracle| / |x_oracle| = {err:.2e} (peak-relative "
+          f"element {peak:.2e}); NRMSE gpu {rel(x_gpu, xt):.5f} oracle {rel(x_ref, xt):.5f} adjoint "
+          f"{rel(x0, xt):.5f}")
     assert rel(x_gpu, xt) < rel(x0, xt)
 
 
