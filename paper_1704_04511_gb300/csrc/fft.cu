@@ -663,20 +663,15 @@ depth_fold_64_kernel(float2* t, const uint8_t* __restrict__ mask, float scale,
         x0[p2] = t[a0 + (size_t)p2 * Q];
         x1[p2] = t[a1 + (size_t)p2 * Q];
     }
-    {   // the mask bytes of the CTA's 8 columns: 512 runs of 8 (depth frequency kr, k2)
+    {   // the mask bytes of the CTA's 8 columns: 512 runs of 8 (depth frequency kr, k2), each an
+        // aligned 8-byte load (the entry points take 16-byte aligned masks; q0 is a multiple of 8)
         const uint8_t* mb = mask + fbase + (size_t)k1 * Q + q0;
-        const bool al8 = (reinterpret_cast<uintptr_t>(mask) & 7) == 0;
 #pragma unroll
         for (int i = threadIdx.x; i < 512; i += 256) {
             const int kr = i / 8, k2 = i % 8;
             const uint8_t* src = mb + (size_t)kr * PQ + (size_t)(16 * k2) * Q;
-            uint8_t* dst = &Mk[kr * 64 + 8 * k2];
-            if (al8) {
-                *reinterpret_cast<uint2*>(dst) = __ldg(reinterpret_cast<const uint2*>(src));
-            } else {
-#pragma unroll
-                for (int b = 0; b < 8; ++b) dst[b] = src[b];
-            }
+            *reinterpret_cast<uint2*>(&Mk[kr * 64 + 8 * k2]) =
+                __ldg(reinterpret_cast<const uint2*>(src));
         }
     }
     __syncthreads();  // tables
